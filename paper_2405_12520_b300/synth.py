@@ -1,0 +1,686 @@
+"""Seeded synthetic inputs: lane-level road networks, signal plans and travel demand.
+
+This module builds the *inputs* of the per-step vehicle update and nothing else: node
+and edge geometry, lane connectivity through junctions (the map builder's job, Sec. III-C
+"Map Builder"), fixed-time signal plans, trips with host-computed shortest-path routes (the
+OD-to-demand converter's job, Sec. III-C "Converter from OD matrix to travel demand") and
+pre-placed vehicle states for steady-state workloads.  It holds none of the simulation
+arithmetic (signal state at a time, sensing, car following, lane changing, motion); both
+the CPU oracle and the CUDA path consume what it returns and derive their own tables.
+
+The workloads stand in for the paper's evaluation networks (Sec. IV-A: six real cities and
+nine grids with 16 to 93,564 grids, up to about 2.46M vehicles), which are not available.
+
+All arrays are numpy; every generator takes an explicit seed.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Lane id layout: lanes of edge e are edge_lane0[e] + idx (idx 0 = rightmost lane), all
+# edge lanes first, then junction-internal lanes grouped by junction node.
+
+INTERNAL_MIN_LEN = 21.0  # m; longer than v_max*dt so no vehicle crosses one in a step
+MIN_EDGE_LEN = 25.0      # m; same reason for edge lanes
+
+
+@dataclass
+class Network:
+    node_xy: np.ndarray      # [V,2] float64, metres
+    edge_from: np.ndarray    # [E] int32
+    edge_to: np.ndarray      # [E] int32
+    edge_len: np.ndarray     # [E] float32
+    edge_nlanes: np.ndarray  # [E] int32
+    edge_lane0: np.ndarray   # [E] int32
+    lane_len: np.ndarray     # [Λ] float32
+    lane_edge: np.ndarray    # [Λ] int32, -1 for junction-internal lanes
+    lane_index: np.ndarray   # [Λ] int32, 0 = rightmost (0 for internal lanes)
+    lane_left: np.ndarray    # [Λ] int32, -1 none
+    lane_right: np.ndarray   # [Λ] int32, -1 none
+    succ_off: np.ndarray     # [Λ+1] int32 CSR
+    succ_lane: np.ndarray    # [S] int32: internal lane (edge lanes) / target lane (internal)
+    succ_edge: np.ndarray    # [S] int32: exit edge reached through that successor
+    lane_ctrl: np.ndarray    # [Λ] int32, -1 = no signal at the lane end
+    lane_group: np.ndarray   # [Λ] int32 phase group served (valid when ctrl >= 0)
+    ctrl_node: np.ndarray    # [C] int32
+    ctrl_offset: np.ndarray  # [C] int32, s
+    ctrl_green: np.ndarray   # [C] int32, s
+    ctrl_yellow: np.ndarray  # [C] int32, s
+    ctrl_nphase: np.ndarray  # [C] int32
+    name: str = ""
+    grid_shape: tuple | None = None   # (nx, ny) for grids
+
+    @property
+    def n_lanes(self) -> int:
+        return int(self.lane_len.shape[0])
+
+    @property
+    def n_edges(self) -> int:
+        return int(self.edge_len.shape[0])
+
+    @property
+    def n_ctrl(self) -> int:
+        return int(self.ctrl_node.shape[0])
+
+    @property
+    def n_edge_lanes(self) -> int:
+        return int(self.edge_nlanes.sum())
+
+
+@dataclass
+class Demand:
+    """Trips.  Trip i departs at t_dep[i] on route_edges[route_off[i]:route_off[i+1]].
+
+    If lane[i] >= 0 the vehicle is already on the network at (lane[i], x[i], v[i]) at
+    t = 0 (steady-state workloads); its route then starts at the edge it is on, or, for a
+    junction-internal lane, at the approach edge the internal lane leaves from.
+    """
+    t_dep: np.ndarray        # [n] int32
+    v0: np.ndarray           # [n] float32 desired speed
+    route_off: np.ndarray    # [n+1] int64
+    route_edges: np.ndarray  # [R] int32
+    lane: np.ndarray         # [n] int32
+    x: np.ndarray            # [n] float32
+    v: np.ndarray            # [n] float32
+
+    @property
+    def n(self) -> int:
+        return int(self.t_dep.shape[0])
+
+
+def default_params(**over) -> dict:
+    """Model parameters of the small plain-method configuration (IDM and MOBIL values as
+    the workload fixes them; readings for the values the paper leaves open)."""
+    p = dict(dt=1.0, veh_len=5.0,
+             idm_a=2.0, idm_b=4.5, idm_T=1.5, idm_s0=2.0,
+             mobil_p=0.1, mobil_th=0.2, mobil_bsafe=4.0,
+             p_lc=1.0, a_min=-9.0, v_max=20.0, d_look=200.0,
+             x_lc_min=25.0, x_lc_end=20.0, window=300, seed=1)
+    p.update(over)
+    return p
+
+
+# ----------------------------------------------------------------------------------------
+# junction builder (lane connectivity + signal groups), shared by all network shapes
+# ----------------------------------------------------------------------------------------
+
+def _turn_angle(din, dout):
+    return math.atan2(din[0] * dout[1] - din[1] * dout[0], din[0] * dout[0] + din[1] * dout[1])
+
+
+def _assemble(node_xy, edge_from, edge_to, edge_len, edge_nlanes, signal_nodes,
+              green, yellow, offset, name, grid_shape=None) -> Network:
+    V = node_xy.shape[0]
+    E = edge_from.shape[0]
+    edge_lane0 = np.zeros(E, np.int64)
+    edge_lane0[1:] = np.cumsum(edge_nlanes)[:-1]
+    n_edge_lanes = int(edge_nlanes.sum())
+    lane_edge = np.repeat(np.arange(E), edge_nlanes)
+    lane_index = np.arange(n_edge_lanes) - edge_lane0[lane_edge]
+    lane_left = np.where(lane_index + 1 < edge_nlanes[lane_edge], np.arange(n_edge_lanes) + 1, -1)
+    lane_right = np.where(lane_index > 0, np.arange(n_edge_lanes) - 1, -1)
+
+    order_in = np.argsort(edge_to, kind="stable")
+    order_out = np.argsort(edge_from, kind="stable")
+    in_off = np.searchsorted(edge_to[order_in], np.arange(V + 1))
+    out_off = np.searchsorted(edge_from[order_out], np.arange(V + 1))
+
+    # successors of edge lanes: list of (internal lane, exit edge); internal lane records
+    succ_of_edge_lane = [[] for _ in range(n_edge_lanes)]
+    int_from, int_to, int_edge, int_len = [], [], [], []
+    n_int = 0
+    for n in range(V):
+        ins = order_in[in_off[n]:in_off[n + 1]]
+        outs = order_out[out_off[n]:out_off[n + 1]]
+        for a in ins:
+            u = edge_from[a]
+            din = node_xy[n] - node_xy[u]
+            exits = [x for x in outs if edge_to[x] != u]
+            if not exits:
+                exits = list(outs)  # dead end: the U-turn is the only way on
+            th = [_turn_angle(din, node_xy[edge_to[x]] - node_xy[n]) for x in exits]
+            srt = np.argsort(th, kind="stable")  # rightmost exit first
+            k = int(edge_nlanes[a])
+            m = len(exits)
+            for j, s in enumerate(srt):
+                x = exits[s]
+                lo = (j * k) // m
+                hi = -(-((j + 1) * k) // m) - 1
+                hi = max(hi, lo)
+                c = hi - lo + 1
+                ne = int(edge_nlanes[x])
+                length = INTERNAL_MIN_LEN + 9.0 * abs(th[s]) / math.pi
+                for q in range(lo, hi + 1):
+                    uu = q - lo
+                    tt = (ne - c + uu) if (j == m - 1 and m > 1) else uu
+                    tt = min(max(tt, 0), ne - 1)
+                    src = int(edge_lane0[a] + q)
+                    # fan-out: one internal lane to every lane of the exit edge, the natural
+                    # target (right-aligned, left-aligned for the leftmost exit) first, then by
+                    # distance from it (lower index first on ties)
+                    for t2 in sorted(range(ne), key=lambda z: (abs(z - tt), z)):
+                        dst = int(edge_lane0[x] + t2)
+                        lid = n_edge_lanes + n_int
+                        n_int += 1
+                        int_from.append(src)
+                        int_to.append(dst)
+                        int_edge.append(int(x))
+                        int_len.append(length)
+                        succ_of_edge_lane[src].append((lid, int(x)))
+
+    L = n_edge_lanes + n_int
+    lane_len = np.concatenate([edge_len[lane_edge], np.asarray(int_len, np.float64)]).astype(np.float32)
+    succ_cnt = np.zeros(L, np.int64)
+    succ_cnt[:n_edge_lanes] = [len(s) for s in succ_of_edge_lane]
+    succ_cnt[n_edge_lanes:] = 1
+    succ_off = np.zeros(L + 1, np.int64)
+    succ_off[1:] = np.cumsum(succ_cnt)
+    succ_lane = np.empty(int(succ_off[-1]), np.int64)
+    succ_edge = np.empty(int(succ_off[-1]), np.int64)
+    pos = 0
+    for s in succ_of_edge_lane:
+        for (lid, x) in s:
+            succ_lane[pos] = lid
+            succ_edge[pos] = x
+            pos += 1
+    succ_lane[pos:] = np.asarray(int_to, np.int64)
+    succ_edge[pos:] = np.asarray(int_edge, np.int64)
+
+    # fixed-time signals: approaches sorted by heading, P = ceil(deg/2) phases, approach a
+    # served in phase (rank mod P)
+    lane_ctrl = np.full(L, -1, np.int64)
+    lane_group = np.zeros(L, np.int64)
+    ctrl_node, ctrl_nphase = [], []
+    for n in signal_nodes:
+        ins = order_in[in_off[n]:in_off[n + 1]]
+        if len(ins) < 3:
+            continue
+        c = len(ctrl_node)
+        ang = [math.atan2(*(node_xy[n] - node_xy[edge_from[a]])[::-1]) for a in ins]
+        P = (len(ins) + 1) // 2
+        for r, s in enumerate(np.argsort(ang, kind="stable")):
+            a = ins[s]
+            l0 = int(edge_lane0[a])
+            lane_ctrl[l0:l0 + int(edge_nlanes[a])] = c
+            lane_group[l0:l0 + int(edge_nlanes[a])] = r % P
+        ctrl_node.append(n)
+        ctrl_nphase.append(P)
+    C = len(ctrl_node)
+    ctrl_node = np.asarray(ctrl_node, np.int64)
+    ctrl_nphase = np.asarray(ctrl_nphase, np.int64)
+    g = np.broadcast_to(np.asarray(green(ctrl_node) if callable(green) else green), (C,))
+    y = np.broadcast_to(np.asarray(yellow), (C,))
+    cyc = ctrl_nphase * (g + y)
+    off = np.asarray(offset(ctrl_node, cyc) if callable(offset) else np.broadcast_to(offset, (C,)))
+    i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
+    return Network(
+        node_xy=node_xy.astype(np.float64), edge_from=i32(edge_from), edge_to=i32(edge_to),
+        edge_len=edge_len.astype(np.float32), edge_nlanes=i32(edge_nlanes), edge_lane0=i32(edge_lane0),
+        lane_len=lane_len, lane_edge=i32(np.concatenate([lane_edge, np.full(n_int, -1)])),
+        lane_index=i32(np.concatenate([lane_index, np.zeros(n_int, np.int64)])),
+        lane_left=i32(np.concatenate([lane_left, np.full(n_int, -1)])),
+        lane_right=i32(np.concatenate([lane_right, np.full(n_int, -1)])),
+        succ_off=i32(succ_off), succ_lane=i32(succ_lane), succ_edge=i32(succ_edge),
+        lane_ctrl=i32(lane_ctrl), lane_group=i32(lane_group),
+        ctrl_node=i32(ctrl_node), ctrl_offset=i32(np.mod(off, np.maximum(cyc, 1))),
+        ctrl_green=i32(g), ctrl_yellow=i32(y), ctrl_nphase=i32(ctrl_nphase),
+        name=name, grid_shape=grid_shape)
+
+
+def grid_network(nx: int, ny: int, n_lanes: int = 2, link_len: float = 200.0,
+                 green: int = 30, yellow: int = 3, offset: str = "zero",
+                 seed: int = 0, signals: bool = True) -> Network:
+    """nx*ny signalised grid, bidirectional links of n_lanes lanes.
+
+    offset: "zero" (all controllers in phase), "wave" ((i+j)*22 s, a green wave at about
+    300 m / 13.9 m/s), or "random" (uniform in the cycle, from seed; green then drawn
+    U{20..40} per node)."""
+    assert link_len >= MIN_EDGE_LEN
+    ii, jj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    node_xy = np.stack([ii.ravel() * link_len, jj.ravel() * link_len], 1).astype(np.float64)
+    ef, et = [], []
+    for j in range(ny):
+        for i in range(nx):
+            n = j * nx + i
+            for di, dj in ((1, 0), (0, 1), (-1, 0), (0, -1)):
+                a, b = i + di, j + dj
+                if 0 <= a < nx and 0 <= b < ny:
+                    ef.append(n)
+                    et.append(b * nx + a)
+    ef = np.asarray(ef, np.int64)
+    et = np.asarray(et, np.int64)
+    E = ef.shape[0]
+    rng = np.random.default_rng(seed)
+    g: object = green
+    if offset == "zero":
+        off: object = 0
+    elif offset == "wave":
+        off = lambda nodes, cyc: ((nodes % nx) + (nodes // nx)) * 22
+    elif offset == "random":
+        gg = rng.integers(20, 41, size=nx * ny)
+        g = lambda nodes: gg[nodes]
+        uu = rng.random(nx * ny)
+        off = lambda nodes, cyc: np.floor(uu[nodes] * cyc).astype(np.int64)
+    else:
+        raise ValueError(offset)
+    sig_nodes = range(nx * ny) if signals else []
+    return _assemble(node_xy, ef, et, np.full(E, link_len), np.full(E, n_lanes, np.int64),
+                     sig_nodes, g, yellow, off, name=f"grid{nx}x{ny}x{n_lanes}", grid_shape=(nx, ny))
+
+
+def delaunay_network(n_pts: int, box: float = 30000.0, seed: int = 0, r_min: float = 30.0,
+                     green: int = 30, yellow: int = 3) -> Network:
+    """Random planar network: Delaunay triangulation of n_pts points (hard-core distance
+    r_min) in a box x box m square; every triangulation edge is a road in both directions;
+    1-4 lanes per road by length quartile (shortest quarter 1 lane, longest 4); signals
+    at nodes with 3 or more approaches."""
+    from scipy.spatial import Delaunay
+    rng = np.random.default_rng(seed)
+    cell = r_min / math.sqrt(2.0)
+    ncell = int(math.ceil(box / cell))
+    occ = {}
+    pts = []
+    while len(pts) < n_pts:
+        cand = rng.random((n_pts, 2)) * box
+        for p in cand:
+            ci, cj = int(p[0] // cell), int(p[1] // cell)
+            ok = True
+            for a in range(ci - 2, ci + 3):
+                for b in range(cj - 2, cj + 3):
+                    q = occ.get((a, b))
+                    if q is not None and (q[0] - p[0]) ** 2 + (q[1] - p[1]) ** 2 < r_min * r_min:
+                        ok = False
+                        break
+                if not ok:
+                    break
+            if ok:
+                occ[(ci, cj)] = p
+                pts.append(p)
+                if len(pts) == n_pts:
+                    break
+    del ncell
+    xy = np.asarray(pts, np.float64)
+    tri = Delaunay(xy)
+    s = tri.simplices
+    und = np.concatenate([s[:, [0, 1]], s[:, [1, 2]], s[:, [2, 0]]])
+    und = np.sort(und, 1)
+    und = np.unique(und, axis=0)
+    ef = np.concatenate([und[:, 0], und[:, 1]])
+    et = np.concatenate([und[:, 1], und[:, 0]])
+    o = np.lexsort((et, ef))
+    ef, et = ef[o], et[o]
+    el = np.linalg.norm(xy[et] - xy[ef], axis=1)
+    q = np.quantile(el, [0.25, 0.5, 0.75])
+    nl = 1 + (el > q[0]).astype(np.int64) + (el > q[1]) + (el > q[2])
+    return _assemble(xy, ef, et, el, nl, range(xy.shape[0]), green, yellow, 0,
+                     name=f"delaunay{n_pts}")
+
+
+# ----------------------------------------------------------------------------------------
+# routing (host-side shortest paths; demand conversion, not the simulation)
+# ----------------------------------------------------------------------------------------
+
+def _edge_lookup(net: Network):
+    V = net.node_xy.shape[0]
+    key = net.edge_from.astype(np.int64) * V + net.edge_to
+    o = np.argsort(key)
+    return key[o], o, V
+
+
+def _eid(lut, a, b):
+    keys, o, V = lut
+    k = a.astype(np.int64) * V + b
+    p = np.searchsorted(keys, k)
+    p = np.minimum(p, keys.shape[0] - 1)
+    ok = keys[p] == k
+    return np.where(ok, o[p], -1)
+
+
+def _grid_routes(net: Network, start_edge: np.ndarray, start_node: np.ndarray, dest: np.ndarray):
+    """Shortest (Manhattan) routes on a grid: the x moves first, unless the first x move
+    would be a U-turn back along start_edge, then the y moves first.  Returns
+    (route_off, route_edges, ok) where routes begin with start_edge if >= 0."""
+    nx, ny = net.grid_shape
+    n = dest.shape[0]
+    ci, cj = start_node % nx, start_node // nx
+    di, dj = dest % nx, dest // nx
+    dx, dy = di - ci, dj - cj
+    prev = np.where(start_edge >= 0, net.edge_from[np.maximum(start_edge, 0)], -1)
+    # first hop under x-first
+    fx = np.where(dx != 0, start_node + np.sign(dx), np.where(dy != 0, start_node + np.sign(dy) * nx, -1))
+    yfirst = (fx == prev) & (fx >= 0)
+    fy = np.where(dy != 0, start_node + np.sign(dy) * nx, np.where(dx != 0, start_node + np.sign(dx), -1))
+    bad = yfirst & (fy == prev)
+    hops = np.abs(dx) + np.abs(dy)
+    has0 = (start_edge >= 0).astype(np.int64)
+    lens = hops + has0
+    off = np.zeros(n + 1, np.int64)
+    off[1:] = np.cumsum(lens)
+    out = np.empty(int(off[-1]), np.int32)
+    out[off[:-1][has0 == 1]] = start_edge[has0 == 1]
+    lut = _edge_lookup(net)
+    cur = start_node.astype(np.int64).copy()
+    rx, ry = np.abs(dx).copy(), np.abs(dy).copy()
+    sx, sy = np.sign(dx), np.sign(dy)
+    for h in range(int(hops.max()) if n else 0):
+        act = np.nonzero(h < hops)[0]
+        if act.size == 0:
+            break
+        usex = np.where(yfirst[act], ry[act] == 0, rx[act] > 0)
+        nxt = np.where(usex, cur[act] + sx[act], cur[act] + sy[act] * nx)
+        e = _eid(lut, cur[act], nxt)
+        out[off[act] + has0[act] + h] = e
+        rx[act] -= usex
+        ry[act] -= ~usex
+        cur[act] = nxt
+    return off, out, ~bad
+
+
+def _tree_routes(net: Network, start_edge, start_node, dest_zone, zones, pred):
+    """Routes following reverse shortest-path trees (pred[z, v] = next node from v toward
+    zones[z]).  ok=False where the first hop would be a U-turn."""
+    n = dest_zone.shape[0]
+    prev = np.where(start_edge >= 0, net.edge_from[np.maximum(start_edge, 0)], -1)
+    first = np.where(start_node == zones[dest_zone], -1, pred[dest_zone, start_node])
+    ok = ~((first == prev) & (first >= 0))
+    lut = _edge_lookup(net)
+    # hop counts
+    hops = np.zeros(n, np.int64)
+    cur = start_node.astype(np.int64).copy()
+    tgt = zones[dest_zone]
+    act = np.nonzero(cur != tgt)[0]
+    while act.size:
+        hops[act] += 1
+        cur[act] = pred[dest_zone[act], cur[act]]
+        act = act[cur[act] != tgt[act]]
+    has0 = (start_edge >= 0).astype(np.int64)
+    lens = hops + has0
+    off = np.zeros(n + 1, np.int64)
+    off[1:] = np.cumsum(lens)
+    out = np.empty(int(off[-1]), np.int32)
+    out[off[:-1][has0 == 1]] = start_edge[has0 == 1]
+    cur = start_node.astype(np.int64).copy()
+    for h in range(int(hops.max()) if n else 0):
+        act = np.nonzero(h < hops)[0]
+        nxt = pred[dest_zone[act], cur[act]]
+        out[off[act] + has0[act] + h] = _eid(lut, cur[act], nxt)
+        cur[act] = nxt
+    return off, out, ok
+
+
+def _zone_trees(net: Network, zones: np.ndarray):
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import dijkstra
+    V = net.node_xy.shape[0]
+    # reversed graph: an edge u->v becomes v->u, so trees from a zone give next hops to it
+    g = csr_matrix((net.edge_len.astype(np.float64), (net.edge_to, net.edge_from)), shape=(V, V))
+    dist, pred = dijkstra(g, directed=True, indices=zones, return_predecessors=True)
+    return dist, pred.astype(np.int64)
+
+
+# ----------------------------------------------------------------------------------------
+# demand
+# ----------------------------------------------------------------------------------------
+
+def _pack(t_dep, v0, off, edges, lane=None, x=None, v=None) -> Demand:
+    n = t_dep.shape[0]
+    return Demand(t_dep=np.ascontiguousarray(t_dep, np.int32), v0=np.ascontiguousarray(v0, np.float32),
+                  route_off=np.ascontiguousarray(off, np.int64), route_edges=np.ascontiguousarray(edges, np.int32),
+                  lane=np.ascontiguousarray(np.full(n, -1) if lane is None else lane, np.int32),
+                  x=np.ascontiguousarray(np.zeros(n) if x is None else x, np.float32),
+                  v=np.ascontiguousarray(np.zeros(n) if v is None else v, np.float32))
+
+
+def _select(off, edges, keep):
+    lens = (off[1:] - off[:-1])[keep]
+    noff = np.zeros(lens.shape[0] + 1, np.int64)
+    noff[1:] = np.cumsum(lens)
+    idx = np.repeat(off[:-1][keep], lens) + (np.arange(int(noff[-1])) - np.repeat(noff[:-1], lens))
+    return noff, edges[idx]
+
+
+def uniform_trips(net: Network, n: int, t_span: int = 600, v0: float = 13.9, seed: int = 1) -> Demand:
+    """Uniform-random origin and destination edges (O != D), departures uniform in
+    [0, t_span) s, shortest-path routes from the head of the origin edge to the tail of the
+    destination edge.  Trips whose route would begin with a U-turn are redrawn."""
+    rng = np.random.default_rng(seed)
+    E = net.n_edges
+    o_all, d_all = [], []
+    need = n
+    while need > 0:
+        o = rng.integers(0, E, size=2 * need)
+        d = rng.integers(0, E, size=2 * need)
+        keep = o != d
+        o_all.append(o[keep])
+        d_all.append(d[keep])
+        need -= int(keep.sum())
+    o = np.concatenate(o_all)
+    d = np.concatenate(d_all)
+    # route: o + path(head(o) -> tail(d)) + d
+    head = net.edge_to[o].astype(np.int64)
+    tail = net.edge_from[d].astype(np.int64)
+    if net.grid_shape is not None:
+        off, edges, ok = _grid_routes(net, o, head, tail)
+    else:
+        zones = np.unique(tail)
+        _, pred = _zone_trees(net, zones)
+        off, edges, ok = _tree_routes(net, o, head, np.searchsorted(zones, tail), zones, pred)
+    # last hop arrives at tail(d); it must not be a U-turn into d either
+    last = np.where(off[1:] > off[:-1], edges[np.maximum(off[1:] - 1, 0)], o)
+    ok &= ~(net.edge_from[last] == net.edge_to[d])
+    ok &= last != d  # never happens, kept for clarity
+    keep = np.nonzero(ok)[0][:n]
+    if keep.shape[0] < n:
+        return uniform_trips(net, n, t_span, v0, seed + 7919)
+    off, edges = _select(off, edges, keep)
+    # append destination edge
+    lens = off[1:] - off[:-1] + 1
+    noff = np.zeros(n + 1, np.int64)
+    noff[1:] = np.cumsum(lens)
+    out = np.empty(int(noff[-1]), np.int32)
+    pos = np.repeat(noff[:-1], lens - 1) + (np.arange(int(off[-1])) - np.repeat(off[:-1], lens - 1))
+    out[pos] = edges
+    out[noff[1:] - 1] = d[keep]
+    t_dep = np.sort(rng.integers(0, t_span, size=n))
+    return _pack(t_dep, np.full(n, v0), noff, out)
+
+
+def _gravity_dest(rng, nx, ny, origins, attract, chunk=512):
+    """Destination node per origin: P(D=j|O=i) ∝ A_j / d_ij^2, d = Manhattan distance in
+    links, j != i."""
+    V = nx * ny
+    jx = np.arange(V) % nx
+    jy = np.arange(V) // nx
+    dest = np.empty(origins.shape[0], np.int64)
+    order = np.argsort(origins, kind="stable")
+    so = origins[order]
+    uo, st = np.unique(so, return_index=True)
+    en = np.append(st[1:], so.shape[0])
+    for c0 in range(0, uo.shape[0], chunk):
+        us = uo[c0:c0 + chunk]
+        d = np.abs(jx[None, :] - (us % nx)[:, None]) + np.abs(jy[None, :] - (us // nx)[:, None])
+        w = np.where(d > 0, attract[None, :] / np.maximum(d, 1) ** 2, 0.0)
+        cw = np.cumsum(w, 1)
+        for r, u in enumerate(us):
+            k = c0 + r
+            cnt = en[k] - st[k]
+            uu = rng.random(cnt) * cw[r, -1]
+            dest[order[st[k]:en[k]]] = np.searchsorted(cw[r], uu, side="right")
+    return np.minimum(dest, V - 1)
+
+
+def gravity_trips(net: Network, n: int, t_span: int = 3600, seed: int = 2) -> Demand:
+    """Gravity-model OD on a grid: attraction A_i ~ LogNormal(0,1) per node,
+    P(O=i) ∝ A_i, P(D=j|O=i) ∝ A_j/d_ij^2 (Manhattan links); departures of a Poisson
+    process over t_span s (uniform order statistics); v0 ~ N(13.9, 1.5) clipped to
+    [8, 20] m/s; routes x-then-y shortest paths."""
+    assert net.grid_shape is not None
+    nx, ny = net.grid_shape
+    rng = np.random.default_rng(seed)
+    A = rng.lognormal(0.0, 1.0, size=nx * ny)
+    o = rng.choice(nx * ny, size=n, p=A / A.sum())
+    d = _gravity_dest(rng, nx, ny, o, A)
+    off, edges, ok = _grid_routes(net, np.full(n, -1), o, d)
+    assert ok.all()
+    t_dep = np.sort(rng.integers(0, t_span, size=n))
+    v0 = np.clip(rng.normal(13.9, 1.5, size=n), 8.0, 20.0)
+    return _pack(t_dep, v0, off, edges)
+
+
+def _spaced_positions(rng, lane_len, counts, min_spacing, veh_len):
+    """Sorted front positions in (veh_len, len] with consecutive fronts >= min_spacing
+    apart, uniform among such configurations."""
+    total = int(counts.sum())
+    lane_of = np.repeat(np.arange(counts.shape[0]), counts)
+    slack = lane_len[lane_of] - veh_len - (counts[lane_of] - 1) * min_spacing
+    u = rng.random(total) * np.maximum(slack, 0.0)
+    o = np.lexsort((u, lane_of))
+    u = u[o]
+    start = np.zeros(counts.shape[0] + 1, np.int64)
+    start[1:] = np.cumsum(counts)
+    rank = np.arange(total) - start[lane_of]
+    return lane_of, (veh_len + u + rank * min_spacing)
+
+
+def place_vehicles(net: Network, n: int, seed: int = 3, min_spacing: float = 9.0,
+                   veh_len: float = 5.0, v0_mean: float = 13.9, v0_sd: float = 1.5,
+                   internal_frac: float = 0.0, dest: str = "gravity", zones: int = 256) -> Demand:
+    """Steady-state workload: n vehicles already on the network at t = 0, spread over the
+    edge lanes (and, if internal_frac > 0, junction-internal lanes) in proportion to lane
+    length, consecutive fronts at least min_spacing apart, speed uniform in [0, v0],
+    v0 ~ N(v0_mean, v0_sd) clipped to [8, 20].  Destinations: gravity model on grids,
+    otherwise uniform over `zones` zone nodes; routes are shortest paths."""
+    rng = np.random.default_rng(seed)
+    nel = net.n_edge_lanes
+    L = net.n_lanes
+    cap = np.floor((net.lane_len.astype(np.float64) - veh_len) / min_spacing).astype(np.int64) + 1
+    w = net.lane_len.astype(np.float64).copy()
+    w[nel:] *= internal_frac
+    if internal_frac == 0.0:
+        cap[nel:] = 0
+    if n > int(cap.sum()):
+        raise ValueError(f"{n} vehicles do not fit (capacity {int(cap.sum())})")
+    counts = rng.multinomial(n, w / w.sum())
+    for _ in range(100):
+        over = np.maximum(counts - cap, 0)
+        if not over.any():
+            break
+        counts -= over
+        room = cap - counts
+        extra = rng.multinomial(int(over.sum()), room / room.sum())
+        counts += np.minimum(extra, room)
+    short = n - int(counts.sum())
+    if short > 0:
+        room = cap - counts
+        idx = np.nonzero(room > 0)[0]
+        add = np.minimum(room[idx], short)
+        cs = np.cumsum(add)
+        k = np.searchsorted(cs, short)
+        add[k + 1:] = 0
+        add[k] -= cs[k] - short
+        counts[idx] += add
+    lane_of, x = _spaced_positions(rng, net.lane_len.astype(np.float64), counts, min_spacing, veh_len)
+    # origin node of the route search: head of the lane's edge (edge lanes) or of the exit
+    # edge (internal lanes)
+    is_int = lane_of >= nel
+    first_edge = np.where(is_int, -1, net.lane_edge[np.minimum(lane_of, nel - 1)])
+    # internal lane -> (approach edge, exit edge)
+    int_src_edge = np.full(L, -1, np.int64)
+    int_dst_edge = np.full(L, -1, np.int64)
+    for e_lane in range(nel):
+        for s in range(net.succ_off[e_lane], net.succ_off[e_lane + 1]):
+            int_src_edge[net.succ_lane[s]] = net.lane_edge[e_lane]
+            int_dst_edge[net.succ_lane[s]] = net.succ_edge[s]
+    appr = np.where(is_int, int_src_edge[lane_of], first_edge)
+    exit_e = np.where(is_int, int_dst_edge[lane_of], -1)
+    # the route search starts at the head of the edge the vehicle is on or entering
+    se = np.where(is_int, exit_e, first_edge)
+    snode = net.edge_to[se].astype(np.int64)
+    V = net.node_xy.shape[0]
+    v0 = np.clip(rng.normal(v0_mean, v0_sd, size=n), 8.0, 20.0)
+    v = rng.random(n) * v0
+    # lane -> edge connectivity pairs, to keep placed vehicles on lanes that serve their
+    # next route edge
+    src_l = np.repeat(np.arange(L), np.diff(net.succ_off))
+    conn_keys = np.unique(src_l.astype(np.int64) * net.n_edges + net.succ_edge)
+    # the lane whose successors must contain the next-but-current route edge: the edge lane
+    # itself, or the target lane of an internal lane
+    int_target = np.full(L, -1, np.int64)
+    int_target[nel:] = net.succ_lane[net.succ_off[nel:L]]
+    chk_lane = np.where(is_int, int_target[lane_of], lane_of)
+    if net.grid_shape is not None and dest == "gravity":
+        nx, ny = net.grid_shape
+        A = rng.lognormal(0.0, 1.0, size=V)
+    else:
+        zs = np.unique(rng.integers(0, V, size=zones))
+        _, pred = _zone_trees(net, zs)
+    dst = np.zeros(n, np.int64)
+    pending = np.arange(n)
+    R_off = np.zeros(n + 1, np.int64)
+    route_len = np.zeros(n, np.int64)
+    store = [None] * n
+    for attempt in range(60):
+        if pending.size == 0:
+            break
+        if net.grid_shape is not None and dest == "gravity":
+            dst[pending] = _gravity_dest(rng, nx, ny, snode[pending], A)
+            o1, e1, ok1 = _grid_routes(net, se[pending], snode[pending], dst[pending])
+        else:
+            dst[pending] = rng.integers(0, zs.shape[0], size=pending.shape[0])
+            o1, e1, ok1 = _tree_routes(net, se[pending], snode[pending], dst[pending], zs, pred)
+        # the edge after the one the vehicle is on / entering
+        has2 = (o1[1:] - o1[:-1]) >= 2
+        e_after = np.where(has2, e1[np.minimum(o1[:-1] + 1, max(e1.shape[0] - 1, 0))], -1)
+        k = chk_lane[pending].astype(np.int64) * net.n_edges + np.maximum(e_after, 0)
+        pos = np.minimum(np.searchsorted(conn_keys, k), conn_keys.shape[0] - 1)
+        conn = (e_after < 0) | (conn_keys[pos] == k)
+        good = ok1 & conn
+        for gi in np.nonzero(good)[0]:
+            store[pending[gi]] = e1[o1[gi]:o1[gi + 1]]
+        pending = pending[~good]
+    for i in pending:
+        # no sampled destination is reached through an exit this lane serves: end the trip
+        # one edge later, through the first exit the lane serves
+        l = chk_lane[i]
+        ex = int(net.succ_edge[net.succ_off[l]])
+        store[i] = np.array([se[i], ex], np.int32)
+    lens = np.fromiter((r.shape[0] for r in store), np.int64, n) + is_int
+    off = np.zeros(n + 1, np.int64)
+    off[1:] = np.cumsum(lens)
+    edges = np.empty(int(off[-1]), np.int32)
+    for i in range(n):
+        o = off[i]
+        if is_int[i]:
+            edges[o] = appr[i]
+            o += 1
+        edges[o:off[i + 1]] = store[i]
+    del R_off, route_len
+    return _pack(np.zeros(n, np.int32), v0, off, edges, lane=lane_of, x=x, v=v)
+
+
+def merge_demands(a: Demand, b: Demand) -> Demand:
+    off = np.concatenate([a.route_off[:-1], b.route_off + a.route_off[-1]])
+    return Demand(t_dep=np.concatenate([a.t_dep, b.t_dep]), v0=np.concatenate([a.v0, b.v0]),
+                  route_off=off, route_edges=np.concatenate([a.route_edges, b.route_edges]),
+                  lane=np.concatenate([a.lane, b.lane]), x=np.concatenate([a.x, b.x]),
+                  v=np.concatenate([a.v, b.v]))
+
+
+# ----------------------------------------------------------------------------------------
+# named workloads
+# ----------------------------------------------------------------------------------------
+
+def small_grid_workload(seed: int = 1):
+    """4x4 signalised grid, 2 lanes per direction, 200 m links, 30 s green / 3 s yellow,
+    zero offsets; 500 trips, uniform OD edges, departures uniform over 600 s, v0 = 13.9."""
+    net = grid_network(4, 4, 2, 200.0, 30, 3, "zero")
+    dem = uniform_trips(net, 500, 600, 13.9, seed=seed)
+    return net, dem
+
+
+def large_grid_network():
+    """100x100 signalised grid, 3 lanes per direction, 300 m links, green-wave offsets."""
+    return grid_network(100, 100, 3, 300.0, 30, 3, "wave")

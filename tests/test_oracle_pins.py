@@ -1,0 +1,492 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself:
+published RNG vectors, closed forms of the IDM (Treiber 2000) and of MOBIL special cases
+(Kesting 2007), the fixed-time signal table, brute-force neighbour search, and invariants
+of whole runs (gap >= 0, no crossing on red, conservation, determinism, resume)."""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.optimize import brentq
+
+from paper_2405_12520_b300 import synth
+import netkit
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+P = synth.default_params()
+
+
+def _golden(name):
+    rows = []
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            rows.append(line.split())
+    return rows
+
+
+# ---------------------------------------------------------------------------------------
+# counter-based RNG
+# ---------------------------------------------------------------------------------------
+
+def test_splitmix64_published_vector(oracle_lib):
+    """SplitMix64 (Steele, Lea & Flood 2014) seeded with 0: the first outputs are the
+    published reference values.  The oracle's function is the output step applied to the
+    state, so the k-th output is f(k * gamma)."""
+    gamma = 0x9E3779B97F4A7C15
+    for k, (hexval,) in enumerate(_golden("splitmix64_seed0.txt")):
+        assert oracle_lib.splitmix64((k * gamma) % 2 ** 64) == int(hexval, 16)
+
+
+# ---------------------------------------------------------------------------------------
+# IDM closed forms
+# ---------------------------------------------------------------------------------------
+
+def _equilibrium_speed(gap, v0, p=P):
+    """Treiber's homogeneous steady state: s_e(v) = (s0 + vT) / sqrt(1 - (v/v0)^4)."""
+    f = lambda v: (p["idm_s0"] + v * p["idm_T"]) / math.sqrt(1.0 - (v / v0) ** 4) - gap
+    return brentq(f, 0.0, v0 * (1 - 1e-12), xtol=1e-15, rtol=1e-15)
+
+
+@pytest.mark.parametrize("n_veh", [16, 20, 40])
+def test_idm_ring_equilibrium_is_fixed_point(oracle_lib, n_veh):
+    net = netkit.ring(200.0)
+    _, _, total = netkit.ring_path(net)
+    spacing = total / n_veh
+    gap = spacing - P["veh_len"]
+    v0 = 13.9
+    ve = _equilibrium_speed(gap, v0)
+    u = 0.5 + spacing * np.arange(n_veh)   # ring is 460 m: these fronts are exact in float32
+    dem = netkit.ring_demand(net, u, np.full(n_veh, ve), v0)
+    o = oracle_lib.Oracle(net, dem, P)
+    seq, starts, _ = netkit.ring_path(net)
+    lane_start = {l: s for l, s in zip(seq, starts)}
+
+    def ring_pos(st):
+        return np.array([lane_start[l] + x for l, x in zip(st["lane"], st["x"])])
+    moved = 0.0
+    for k in range(50):
+        before = ring_pos(o.state())
+        err, d = o.step(debug=True)
+        assert err == 0
+        # speeds enter as float32 (ve rounded by ~5e-7), hence 1e-6 rather than 0
+        assert np.all(np.abs(d["a_own"]) < 1e-6), np.abs(d["a_own"]).max()
+        assert np.all(d["lead_kind"] == 1)
+        np.testing.assert_allclose(d["s_own"], gap, atol=1e-4)
+        st = o.state()
+        adv = np.mod(ring_pos(st) - before, total)
+        np.testing.assert_allclose(adv, ve * P["dt"], atol=1e-6)
+        np.testing.assert_allclose(st["v"], ve, atol=1e-6)
+        moved += adv.mean()
+    assert moved > 0
+
+
+def test_free_road_accelerates_to_v0(oracle_lib):
+    net = netkit.ring(200.0)
+    v0 = 13.9
+    dem = netkit.ring_demand(net, np.array([10.0]), np.array([0.0]), v0)
+    o = oracle_lib.Oracle(net, dem, P)
+    seq, starts, total = netkit.ring_path(net)
+    lane_start = {l: s for l, s in zip(seq, starts)}
+    vs, us = [0.0], [10.0]
+    for k in range(300):
+        _, d = o.step(debug=True)
+        assert d["lead_kind"][0] == 0   # ring is longer than the look-ahead horizon
+        st = o.state()
+        vs.append(st["v"][0])
+        us.append(lane_start[st["lane"][0]] + st["x"][0])
+    vs = np.array(vs)
+    # first step from rest: a = a_max exactly, so v = a_max dt and d = a_max dt^2 / 2
+    assert vs[1] == pytest.approx(P["idm_a"] * P["dt"], abs=1e-12)
+    assert np.mod(us[1] - us[0], total) == pytest.approx(0.5 * P["idm_a"], abs=1e-12)
+    v0f = float(np.float32(v0))   # desired speeds are float32 inputs
+    assert np.all(np.diff(vs) >= 0) and np.all(np.diff(vs[:30]) > 0) and np.all(vs <= v0f)
+    assert vs[-1] == pytest.approx(v0f, abs=1e-9)
+    # ballistic update: distance of each step is the mean of the two speeds times dt
+    adv = np.mod(np.diff(us), total)
+    np.testing.assert_allclose(adv, 0.5 * (vs[1:] + vs[:-1]) * P["dt"], atol=1e-9)
+
+
+def test_stop_at_long_red_reaches_standstill_gap(oracle_lib):
+    net = synth.grid_network(3, 3, 1, 300.0, green=200, yellow=3, offset="zero")
+    o0 = oracle_lib.Oracle(net, netkit.vehicles([], [], [], []), P)
+    # an approach lane into the centre node (4) that is red for t in [0, 203)
+    lanes = [l for l in range(net.n_edge_lanes)
+             if net.edge_to[net.lane_edge[l]] == 4 and o0.signal_state(l, 0) == 2]
+    l = lanes[0]
+    e = net.lane_edge[l]
+    nxt = [net.succ_edge[k] for k in range(net.succ_off[l], net.succ_off[l + 1])][0]
+    dem = netkit.vehicles([l], [100.0], [12.0], [[e, nxt]])
+    o = oracle_lib.Oracle(net, dem, P)
+    L = net.lane_len[l]
+    for t in range(200):
+        o.step()
+        st = o.state()
+        assert st["lane"][0] == l and st["x"][0] <= L   # never crosses the red stop line
+    st = o.state()
+    # standing still short of the line: with a discrete step the stop can end a little
+    # inside s0, where IDM then gives a < 0 and the vehicle stays put
+    assert st["v"][0] == 0.0
+    assert 0.0 < (L - st["x"][0]) <= P["idm_s0"] + 1e-9
+    for t in range(200, 260):
+        o.step()
+    assert o.state()["lane"][0] != l or o.state()["status"][0] == 2   # left on green
+
+
+def test_signal_table_closed_form(oracle_lib):
+    net = synth.grid_network(3, 3, 1, 300.0, green=30, yellow=3, offset="zero")
+    o = oracle_lib.Oracle(net, netkit.vehicles([], [], [], []), P)
+    c = net.ctrl_node.tolist().index(4)
+    lanes = np.nonzero(net.lane_ctrl == c)[0]
+    g0 = [l for l in lanes if net.lane_group[l] == 0][0]
+    g1 = [l for l in lanes if net.lane_group[l] == 1][0]
+    want0 = ["G"] * 30 + ["Y"] * 3 + ["R"] * 33
+    want1 = ["R"] * 33 + ["G"] * 30 + ["Y"] * 3
+    code = {0: "G", 1: "Y", 2: "R"}
+    for t in range(132):
+        assert code[o.signal_state(g0, t)] == want0[t % 66]
+        assert code[o.signal_state(g1, t)] == want1[t % 66]
+    # uncontrolled lanes (corner nodes have fewer than 3 approaches) are always green
+    free = np.nonzero(net.lane_ctrl[:net.n_edge_lanes] < 0)[0][0]
+    assert all(o.signal_state(free, t) == 0 for t in range(70))
+
+
+def test_signal_offsets_shift_the_table(oracle_lib):
+    net = synth.grid_network(4, 4, 1, 300.0, green=30, yellow=3, offset="wave")
+    o = oracle_lib.Oracle(net, netkit.vehicles([], [], [], []), P)
+    for c in range(net.n_ctrl):
+        lanes = np.nonzero(net.lane_ctrl == c)[0]
+        n = net.ctrl_node[c]
+        off = ((n % 4) + (n // 4)) * 22 % (net.ctrl_nphase[c] * 33)
+        assert net.ctrl_offset[c] == off
+        for l in lanes[:2]:
+            for t in range(0, 70, 7):
+                assert o.signal_state(l, t) == o.signal_state(l, t + 66)
+
+
+def test_yellow_stop_rule(oracle_lib):
+    """At the start of yellow a vehicle stops iff its distance to the stop line is at
+    least v^2 / (2 b)."""
+    net = synth.grid_network(3, 3, 1, 300.0, green=30, yellow=3, offset="zero")
+    o0 = oracle_lib.Oracle(net, netkit.vehicles([], [], [], []), P)
+    lanes = [l for l in range(net.n_edge_lanes)
+             if net.edge_to[net.lane_edge[l]] == 4 and o0.signal_state(l, 30) == 1]
+    v = 15.0
+    stop_d = v * v / (2 * P["idm_b"])   # 25 m
+    routes, xs, ls = [], [], []
+    for l, dist in zip(lanes[:2], [stop_d + 5.0, stop_d - 5.0]):
+        e = net.lane_edge[l]
+        nxt = net.succ_edge[net.succ_off[l]]
+        routes.append([e, nxt])
+        xs.append(net.lane_len[l] - dist)
+        ls.append(l)
+    dem = netkit.vehicles(ls, xs, [v, v], routes)
+    o = oracle_lib.Oracle(net, dem, P)
+    st = o.state()
+    o.set_state(st["status"], st["lane"], st["x"], st["v"], st["rp"], 30)
+    _, d = o.step(debug=True)
+    assert d["lead_kind"][0] == 2 and d["s_own"][0] == pytest.approx(stop_d + 5.0)
+    assert d["lead_kind"][1] != 2
+
+
+# ---------------------------------------------------------------------------------------
+# MOBIL special cases
+# ---------------------------------------------------------------------------------------
+
+def _two_lane_case(lanes, xs, vs, v0=13.9, t=0, **par):
+    net = netkit.line(3, 300.0, 2)
+    routes = [[0, 1]] * len(lanes)
+    dem = netkit.vehicles(lanes, xs, vs, routes, v0=v0)
+    import oracle
+    o = oracle.Oracle(net, dem, dict(P, **par))
+    if t:
+        st = o.state()
+        o.set_state(st["status"], st["lane"], st["x"], st["v"], st["rp"], t)
+    err, d = o.step(debug=True)
+    assert err == 0
+    return d
+
+
+def test_mobil_incentive_is_free_gain_with_empty_target(oracle_lib):
+    v, v0 = 10.0, 13.9
+    se = (P["idm_s0"] + v * P["idm_T"]) / math.sqrt(1 - (v / v0) ** 4)   # Treiber s_e(v)
+    d = _two_lane_case([0, 0], [100.0, 100.0 + P["veh_len"] + se], [v, v])
+    # inputs are float32 (positions, v0): equilibrium and free gain hold to ~1e-7
+    v0f = float(np.float32(v0))
+    assert d["a_own"][0] == pytest.approx(0.0, abs=1e-6)   # car-following equilibrium
+    assert d["lc_cand"][0] == 1
+    assert d["tau_lead"][0] == -1 and d["tau_foll"][0] == -1 and d["old_foll"][0] == -1
+    assert d["incentive"][0] == pytest.approx(P["idm_a"] * (1 - (v / v0f) ** 4), abs=1e-6)
+    assert d["lc_dir"][0] == +1
+
+
+def test_mobil_identical_lanes_no_change(oracle_lib):
+    v, v0 = 10.0, 13.9
+    se = (P["idm_s0"] + v * P["idm_T"]) / math.sqrt(1 - (v / v0) ** 4)
+    xl = 100.0 + P["veh_len"] + se
+    d = _two_lane_case([0, 0, 1], [100.0, xl, xl], [v, v, v])
+    assert d["lc_cand"][0] == 1 and d["tau_lead"][0] == 2
+    assert d["incentive"][0] == 0.0
+    assert d["lc_dir"][0] == 0
+
+
+def test_mobil_direction_alternates_with_step_parity(oracle_lib):
+    v, v0 = 10.0, 13.9
+    se = (P["idm_s0"] + v * P["idm_T"]) / math.sqrt(1 - (v / v0) ** 4)
+    # vehicle on the left lane (1) behind a leader: on even steps only left moves exist
+    d = _two_lane_case([1, 1], [100.0, 100.0 + 5 + se], [v, v], t=0)
+    assert d["lc_cand"][0] == 0
+    d = _two_lane_case([1, 1], [100.0, 100.0 + 5 + se], [v, v], t=1)
+    assert d["lc_cand"][0] == 1 and d["lc_dir"][0] == -1
+
+
+def test_mobil_safety_criteria(oracle_lib):
+    stopped_leader = 100.0 + P["veh_len"] + 3.0
+    # new follower 10 m behind at 8.5 m/s: guard 9.5 m passes, a~_n < -b_safe blocks
+    d = _two_lane_case([0, 0, 1], [100.0, stopped_leader, 85.0], [5.0, 0.0, 8.5])
+    assert d["lc_cand"][0] == 1 and d["tau_foll"][0] == 2 and d["lc_dir"][0] == 0
+    # same with a stopped follower: a~_n = a_max (1 - (s0/10)^2) = 1.92 > -b_safe: change
+    d = _two_lane_case([0, 0, 1], [100.0, stopped_leader, 85.0], [5.0, 0.0, 0.0])
+    assert d["lc_dir"][0] == +1
+    # conflict guard: follower 9.5 m behind at 9 m/s needs 9 + a_max/2 = 10 m
+    d = _two_lane_case([0, 0, 1], [100.0, stopped_leader, 85.5], [5.0, 0.0, 9.0])
+    assert d["lc_cand"][0] == 1 and d["lc_dir"][0] == 0
+
+
+def test_mobil_zones_and_gate(oracle_lib):
+    stopped = P["veh_len"] + 3.0
+    # too close to the lane start (x < x_lc_min)
+    d = _two_lane_case([0, 0], [20.0, 20.0 + stopped], [5.0, 0.0])
+    assert d["lc_cand"][0] == 0
+    # too close to the lane end for a discretionary change
+    d = _two_lane_case([0, 0], [285.0, 285.0 + 2], [5.0, 0.0])
+    assert d["lc_cand"][0] == 0
+    # p_lc = 0: never considered
+    d = _two_lane_case([0, 0], [100.0, 100.0 + stopped], [5.0, 0.0], p_lc=0.0)
+    assert d["lc_cand"][0] == 0
+
+
+def test_mandatory_change_toward_connecting_lane(oracle_lib):
+    """A 3-lane approach whose lane 0 serves only the right turn: a vehicle on lane 0
+    heading straight must move left, with no incentive test."""
+    net = synth.grid_network(3, 3, 3, 300.0, green=30, yellow=3)
+    # approach into node 4 from the west: edge 3 -> 4
+    e = [k for k in range(net.n_edges) if net.edge_from[k] == 3 and net.edge_to[k] == 4][0]
+    ex = [k for k in range(net.n_edges) if net.edge_from[k] == 4 and net.edge_to[k] == 5][0]
+    l0 = net.edge_lane0[e]
+    serves = lambda l: ex in net.succ_edge[net.succ_off[l]:net.succ_off[l + 1]]
+    assert not serves(l0) and serves(l0 + 1)
+    # free road, no reason to change except the route
+    dem = netkit.vehicles([l0], [150.0], [13.9], [[e, ex]])   # lane end 150 m ahead
+    import oracle
+    o = oracle.Oracle(net, dem, P)
+    _, d = o.step(debug=True)
+    assert d["lead_kind"][0] == 2   # non-connecting lane end is an obstacle
+    assert d["lc_dir"][0] == +1 and d["lc_cand"][0] == 1
+    o2 = oracle.Oracle(net, dem, dict(P, p_lc=0.0))
+    _, d2 = o2.step(debug=True)
+    assert d2["lc_dir"][0] == +1    # mandatory changes bypass the random gate
+
+
+# ---------------------------------------------------------------------------------------
+# neighbour search vs brute force
+# ---------------------------------------------------------------------------------------
+
+def _brute_neighbours(net, lane, x, active):
+    n = lane.shape[0]
+    out = np.full((n, 6), -1, np.int64)
+    for c in np.nonzero(active)[0]:
+        same = np.nonzero(active & (lane == lane[c]))[0]
+        ahead = same[x[same] > x[c]]
+        behind = same[x[same] < x[c]]
+        if ahead.size:
+            out[c, 0] = ahead[np.argmin(x[ahead])]
+        if behind.size:
+            out[c, 1] = behind[np.argmax(x[behind])]
+        for q, tau in enumerate((net.lane_left[lane[c]], net.lane_right[lane[c]])):
+            if tau < 0:
+                continue
+            oth = np.nonzero(active & (lane == tau))[0]
+            a = oth[x[oth] > x[c]]
+            b = oth[x[oth] <= x[c]]
+            if a.size:
+                out[c, 2 + 2 * q] = a[np.argmin(x[a])]
+            if b.size:
+                out[c, 3 + 2 * q] = b[np.argmax(x[b])]
+    return out
+
+
+@pytest.mark.parametrize("kind,seed", [("grid", 1), ("grid", 2), ("delaunay", 3)])
+def test_neighbours_match_brute_force(oracle_lib, kind, seed):
+    if kind == "grid":
+        net = synth.grid_network(4, 4, 3, 200.0)
+    else:
+        net = synth.delaunay_network(40, box=2000.0, seed=seed)
+    dem = synth.place_vehicles(net, 60, seed=seed, min_spacing=5.5, internal_frac=0.3)
+    o = oracle_lib.Oracle(net, dem, P)
+    got = o.neighbors()
+    st = o.state()
+    want = _brute_neighbours(net, st["lane"], st["x"], st["status"] == 1)
+    np.testing.assert_array_equal(got, want)
+
+
+# ---------------------------------------------------------------------------------------
+# whole-run invariants
+# ---------------------------------------------------------------------------------------
+
+def _check_run(o, net, n_steps, L=5.0):
+    n = o.n
+    st0 = o.state()
+    placed = int((st0["status"] == 1).sum())
+    for t in range(n_steps):
+        st = o.state()
+        act = st["status"] == 1
+        # red lights at the start of the step
+        red = np.array([o.signal_state(int(l), st["t"]) == 2 if a and net.lane_edge[l] >= 0 else False
+                        for l, a in zip(st["lane"], act)])
+        err, _ = o.step()
+        assert err == 0
+        nx = o.state()
+        # no crossing on red: a vehicle on a red edge lane stays on it (or arrives if it is
+        # the destination edge, whose end is open)
+        crossed = red & (nx["lane"] != st["lane"]) & (nx["status"] == 1) & \
+            (net.lane_edge[nx["lane"]] < 0)
+        assert not crossed.any()
+        # gap >= 0 in every lane
+        a = np.nonzero(nx["status"] == 1)[0]
+        o_ = np.lexsort((nx["x"][a], nx["lane"][a]))
+        la, xa = nx["lane"][a][o_], nx["x"][a][o_]
+        same = la[1:] == la[:-1]
+        gaps = (xa[1:] - L - xa[:-1])[same]
+        assert gaps.size == 0 or gaps.min() >= -1e-9, gaps.min()
+        # conservation
+        m = o.metrics()
+        assert (nx["status"] == 0).sum() + (nx["status"] == 1).sum() + (nx["status"] == 2).sum() == n
+        assert m["inserted"] + placed == (nx["status"] == 1).sum() + (nx["status"] == 2).sum()
+        assert m["arrived"] == (nx["status"] == 2).sum()
+    return o.state()
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_small_grid_run_invariants(oracle_lib, seed):
+    net, dem = synth.small_grid_workload(seed)
+    o = oracle_lib.Oracle(net, dem, P, n_windows=12)
+    st = _check_run(o, net, 1500)
+    assert (st["status"] == 2).sum() > 0.9 * dem.n
+
+
+def test_delaunay_run_invariants_with_merges(oracle_lib):
+    net = synth.delaunay_network(60, box=2500.0, seed=4)
+    # vehicles on internal lanes feeding multi-feeder targets exercise the merge rule
+    n_pred = np.bincount(net.succ_lane[net.succ_off[net.n_edge_lanes]:], minlength=net.n_lanes)
+    assert (n_pred > 1).any()
+    dem = synth.merge_demands(
+        synth.place_vehicles(net, 400, seed=4, min_spacing=7.0, internal_frac=1.0),
+        synth.uniform_trips(net, 400, 300, seed=5))
+    o = oracle_lib.Oracle(net, dem, dict(P, p_lc=0.5), n_windows=2)
+    _check_run(o, net, 400)
+
+
+def test_run_is_deterministic_and_resumable(oracle_lib):
+    net, dem = synth.small_grid_workload(3)
+    a = oracle_lib.Oracle(net, dem, P, n_windows=12)
+    b = oracle_lib.Oracle(net, dem, P, n_windows=12)
+    a.run(700)
+    b.run(300)
+    s = b.state()
+    c = oracle_lib.Oracle(net, dem, P, n_windows=12)
+    c.set_state(s["status"], s["lane"], s["x"], s["v"], s["rp"], s["t"], s["t_arr"])
+    c.run(400)
+    sa, sc = a.state(), c.state()
+    for k in ("status", "lane", "x", "v", "rp", "t_arr", "t"):
+        np.testing.assert_array_equal(sa[k], sc[k])
+
+
+def test_departures_fifo_and_room(oracle_lib):
+    net = netkit.line(3, 300.0, 2)
+    n = 5
+    dem = netkit.vehicles([-1] * n, [0.0] * n, [0.0] * n, [[0, 1]] * n)
+    o = oracle_lib.Oracle(net, dem, P)
+    assert o.departure_lane(0) == 0
+    order = []
+    for t in range(60):
+        st = o.state()
+        act = np.nonzero(st["status"] == 1)[0]
+        on0 = act[st["lane"][act] == 0]
+        tail_x = st["x"][on0].min() if on0.size else None
+        _, d = o.step(debug=True)
+        ins = np.nonzero(d["inserted"])[0].tolist()
+        if ins:
+            assert tail_x is None or tail_x - 5.0 >= 5.0 + P["idm_s0"]
+        elif tail_x is not None and len(order) < n:
+            assert tail_x - 5.0 < 5.0 + P["idm_s0"]
+        order += ins
+    assert order == list(range(n))
+
+
+def test_metrics_window_sums(oracle_lib):
+    net, dem = synth.small_grid_workload(1)
+    o = oracle_lib.Oracle(net, dem, dict(P, window=50), n_windows=4)
+    vs = np.zeros((4, net.n_lanes))
+    vc = np.zeros((4, net.n_lanes), np.int64)
+    for t in range(200):
+        st = o.state()
+        a = st["status"] == 1
+        np.add.at(vs[t // 50], st["lane"][a], st["v"][a])
+        np.add.at(vc[t // 50], st["lane"][a], 1)
+        o.step()
+    m = o.metrics()
+    np.testing.assert_array_equal(m["vcnt"], vc)
+    np.testing.assert_allclose(m["vsum"], vs, rtol=1e-12)
+
+
+def test_mobil_politeness_terms_closed_form(oracle_lib):
+    """Stopped followers make every IDM term closed-form: at v = 0, s* = s0 and
+    a = a_max (1 - (s0/s)^2).  New follower F 10 m behind in the target lane, old follower
+    O 4 m behind in the own lane; the changer c follows its leader at equilibrium."""
+    v, v0 = 10.0, 13.9
+    v0f = float(np.float32(v0))
+    se = (P["idm_s0"] + v * P["idm_T"]) / math.sqrt(1 - (v / v0) ** 4)
+    xc, L, s0, am = 100.0, P["veh_len"], P["idm_s0"], P["idm_a"]
+    gF, gO = 10.0, 4.0
+    d = _two_lane_case([0, 0, 1, 0], [xc, xc + L + se, xc - L - gF, xc - L - gO], [v, v, 0.0, 0.0])
+    assert d["tau_foll"][0] == 2 and d["old_foll"][0] == 3 and d["tau_lead"][0] == -1
+    free_gain = am * (1 - (v / v0f) ** 4)
+    dF = am * (1 - (s0 / gF) ** 2) - am            # F: free road -> behind c
+    gO_new = gO + L + se                           # O: behind c -> behind c's leader
+    dO = am * (1 - (s0 / gO_new) ** 2) - am * (1 - (s0 / gO) ** 2)
+    want = free_gain + P["mobil_p"] * (dF + dO)
+    assert d["incentive"][0] == pytest.approx(want, abs=1e-5)
+    assert d["lc_dir"][0] == +1
+
+
+def test_merge_projection_leader(oracle_lib):
+    """Two internal lanes feeding one exit lane: the vehicle farther from the merge point
+    follows the projected rear of the nearer one (gap = d_A - d_B - L); the nearer one
+    does not see the farther one; on equal distance the lower id goes first."""
+    net = synth.grid_network(3, 3, 1, 300.0, green=30, yellow=3)
+    nel = net.n_edge_lanes
+    tgt = net.succ_lane[net.succ_off[nel:net.n_lanes]]
+    counts = np.bincount(tgt, minlength=net.n_lanes)
+    lt = int(np.nonzero(counts >= 2)[0][0])
+    f1, f2 = [nel + int(i) for i in np.nonzero(tgt == lt)[0][:2]]
+    appr = {}
+    for l in range(nel):
+        for k in range(net.succ_off[l], net.succ_off[l + 1]):
+            appr[int(net.succ_lane[k])] = int(net.lane_edge[l])
+    ex = int(net.lane_edge[lt])
+
+    def case(dA, dB):
+        xs = [net.lane_len[f1] - dA, net.lane_len[f2] - dB]
+        dem = netkit.vehicles([f1, f2], xs, [3.0, 3.0], [[appr[f1], ex], [appr[f2], ex]])
+        o = oracle_lib.Oracle(net, dem, P)
+        st = o.state()
+        o.set_state(st["status"], st["lane"], st["x"], st["v"], st["rp"], 0)
+        _, d = o.step(debug=True)
+        return d
+    d = case(10.0, 4.0)
+    assert d["lead_id"][0] == 1 and d["s_own"][0] == pytest.approx(10.0 - 4.0 - P["veh_len"], abs=1e-5)
+    assert d["lead_id"][1] == -1
+    d = case(6.0, 6.0)          # tie: id 0 goes first, id 1 follows at gap -L
+    assert d["lead_id"][0] == -1
+    assert d["lead_id"][1] == 0 and d["s_own"][1] == pytest.approx(-P["veh_len"], abs=1e-5)

@@ -1,0 +1,184 @@
+/*
+ * moss103.h -- C ABI of the B300 (sm_103a) per-time-step vehicle update of a lane-level
+ * microscopic traffic simulator (arxiv 2405.12520, MOSS, Sec. III-A).
+ *
+ * One simulation step t -> t+1 has the paper's two phases (Sec. III-A): a prepare phase
+ * that indexes vehicles by lane and position from a read-only snapshot, and an update phase
+ * in which every vehicle senses its neighbours, computes IDM car following and a randomized
+ * MOBIL lane-change decision, and advances by Newton's equations of motion.  The simulator
+ * takes a lane-level road network and trip demand as input and produces per-vehicle
+ * position and speed every step and per-lane mean speeds (Sec. III-A, last paragraph).
+ *
+ * Conventions for every entry point:
+ *  - return value: MS_OK (0) or a negative MS_ERR_* code; ms_last_error() then holds a
+ *    one-line message.  A failed call leaves the simulation unchanged unless noted.
+ *  - host arrays passed in are read during the call only and copied; the library owns all
+ *    device memory it allocates (cudaMalloc at load time, freed by ms_destroy).
+ *  - lane ids: edge lanes first (lanes of edge e are edge_lane0[e] + idx, idx 0 rightmost),
+ *    then junction-internal lanes.  Positions x are the front bumper along the lane from
+ *    its start, metres; speeds m/s; FP32.
+ *  - not thread-safe per ms_sim; distinct ms_sim objects are independent.
+ */
+#ifndef MOSS103_H
+#define MOSS103_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MS_OK 0
+#define MS_ERR_ARG (-1)      /* invalid argument or input data (message says which) */
+#define MS_ERR_ROUTE (-2)    /* a route has consecutive edges without a lane link */
+#define MS_ERR_CAPACITY (-3) /* more vehicles than the simulation was sized for */
+#define MS_ERR_CUDA (-4)     /* a CUDA runtime call failed */
+#define MS_ERR_DEVICE (-5)   /* a device-side check set an error bit (see ms_metrics.err) */
+#define MS_ERR_STATE (-6)    /* call out of order (e.g. step before load) */
+
+/* device error bits (ms_metrics.err) */
+#define MS_DEV_HOP 1u        /* a vehicle crossed more than one lane end in a step */
+#define MS_DEV_SCAN 2u       /* lane scan look-back exceeded its wait limit */
+#define MS_DEV_ORDER 4u      /* debug check: output not sorted by (lane, x) or gap < 0 */
+#define MS_DEV_BUCKET 8u     /* a moved vehicle did not find its merge record */
+
+/* Model parameters.  Values the paper fixes: dt (1 s, Sec. III-A, IV-A); the model families
+   (IDM, randomized MOBIL, Sec. III-A).  All other values are parameters of those models or
+   readings of what the paper leaves open. */
+typedef struct ms_params {
+  float dt;        /* s, step length */
+  float veh_len;   /* m, vehicle length L (all vehicles) */
+  float idm_a;     /* m/s^2, IDM maximum acceleration */
+  float idm_b;     /* m/s^2, IDM comfortable deceleration */
+  float idm_T;     /* s, IDM time headway */
+  float idm_s0;    /* m, IDM jam distance */
+  float mobil_p;   /* MOBIL politeness */
+  float mobil_th;  /* m/s^2, MOBIL threshold */
+  float mobil_bsafe; /* m/s^2, MOBIL safe braking */
+  float p_lc;      /* probability that a discretionary lane change is considered, [0,1] */
+  float a_min;     /* m/s^2, emergency deceleration bound (negative) */
+  float v_max;     /* m/s, speed cap; every lane must be longer than v_max*dt */
+  float d_look;    /* m, look-ahead horizon for the leader search */
+  float x_lc_min;  /* m, no lane change with x below this */
+  float x_lc_end;  /* m, no discretionary lane change within this distance of the lane end */
+  int window;      /* steps per metric window (per-lane mean speed) */
+  int n_windows;   /* metric windows kept on the device (steps beyond are not recorded) */
+  uint64_t seed;   /* seed of the counter-based lane-change gate */
+  int debug;       /* 1: record per-vehicle sensing and decisions of each step (tests) */
+  int block;       /* threads per block of the vehicle kernels, multiple of 32 (0: 256) */
+} ms_params;
+
+/* Lane-level road network (Sec. III-C "Map Builder": lanes with topology, junction lanes,
+   signal phases).  succ CSR: for an edge lane, its junction-internal lanes with the exit
+   edge each leads to; for an internal lane exactly one entry: its target edge lane and
+   that lane's edge.  Requirements (else MS_ERR_ARG): every lane longer than v_max*dt;
+   left/right only within an edge and mutually consistent; internal lanes have one
+   successor and no left/right; signal groups < ctrl_nphase. */
+typedef struct ms_network {
+  int n_lanes, n_edges, n_ctrl;
+  const float *lane_len;    /* [n_lanes] m */
+  const int *lane_edge;     /* [n_lanes] edge id, -1 for junction-internal lanes */
+  const int *lane_index;    /* [n_lanes] index within the edge, 0 = rightmost */
+  const int *lane_left;     /* [n_lanes] lane to the left (-1 none) */
+  const int *lane_right;    /* [n_lanes] lane to the right (-1 none) */
+  const int *succ_off;      /* [n_lanes+1] */
+  const int *succ_lane;     /* [succ_off[n_lanes]] */
+  const int *succ_edge;     /* [succ_off[n_lanes]] */
+  const int *lane_ctrl;     /* [n_lanes] signal controller at the lane end, -1 none */
+  const int *lane_group;    /* [n_lanes] phase group served */
+  const int *ctrl_offset;   /* [n_ctrl] s */
+  const int *ctrl_green;    /* [n_ctrl] s, > 0 */
+  const int *ctrl_yellow;   /* [n_ctrl] s, >= 0 */
+  const int *ctrl_nphase;   /* [n_ctrl] >= 1 */
+  const int *edge_nlanes;   /* [n_edges] */
+  const int *edge_lane0;    /* [n_edges] */
+} ms_network;
+
+/* Trip demand (Sec. III-A input "demand data"; Sec. III-C converter output: individual
+   trips with routes and departure times).  Trip i has id i, departs at t_dep[i] on
+   route_edges[route_off[i] .. route_off[i+1]-1] (consecutive edges must be lane-linked,
+   else MS_ERR_ROUTE).  Optional placement (lane != NULL and lane[i] >= 0): the vehicle is
+   already on the network at (lane[i], x[i], v[i]); its route then starts at the lane's
+   edge, or, on an internal lane, at the approach edge that lane leaves from. */
+typedef struct ms_vehicles {
+  int n;
+  const int *t_dep;          /* [n] s */
+  const float *v0;           /* [n] desired speed, (0, v_max] */
+  const int64_t *route_off;  /* [n+1] */
+  const int *route_edges;    /* [route_off[n]] */
+  const int *lane;           /* [n] or NULL */
+  const float *x;            /* [n] or NULL */
+  const float *v;            /* [n] or NULL */
+} ms_vehicles;
+
+/* Dynamic state.  Vehicle arrays hold the active vehicles sorted by (lane, x); route_idx is
+   the index within the trip's route of the current edge (the approach edge on an internal
+   lane).  Trip arrays are indexed by trip id. */
+typedef struct ms_state {
+  int capacity;     /* in: entries available in the vehicle arrays */
+  int n_active;     /* out (read) / in (write) */
+  int t;            /* out (read) / in (write): next step to compute */
+  int *id, *lane, *route_idx;   /* [capacity] */
+  float *x, *v;                 /* [capacity] */
+  int *trip_status; /* [n_trips] 0 waiting, 1 active, 2 arrived (read only) */
+  int *t_arr;       /* [n_trips] arrival step or -1 */
+} ms_state;
+
+typedef struct ms_metrics {
+  float *lane_vsum;  /* [n_windows*n_lanes] or NULL: per-window sum of speeds */
+  int *lane_vcnt;    /* [n_windows*n_lanes] or NULL: per-window vehicle-steps */
+  int64_t inserted, arrived, sum_travel_time;
+  int n_active, t, movers_last_step;
+  unsigned err;      /* MS_DEV_* bits */
+} ms_metrics;
+
+/* Per-vehicle record of the last step (params.debug = 1), indexed by trip id; entries of
+   trips that were not active at the start of the step are left untouched. */
+typedef struct ms_debug {
+  int *active_before, *lead_kind, *lead_id, *lc_dir, *lc_cand, *tau_lead, *tau_foll,
+      *old_foll, *flag, *inserted;
+  float *s_own, *vl_own, *a_own, *incentive, *a_use;
+} ms_debug;
+
+/* Create a simulation bound to a CUDA stream (cudaStream_t, or NULL for the default
+   stream) on the current device.  *out receives the handle.  MS_ERR_ARG on invalid
+   parameters. */
+int ms_create(void **out, const ms_params *p, void *cuda_stream);
+
+/* Copy the network to the device and derive its lane tables.  Once per simulation. */
+int ms_load_network(void *sim, const ms_network *net);
+
+/* Copy the trips to the device (once, after ms_load_network, before the first step).
+   Validates routes (MS_ERR_ROUTE) and placements (MS_ERR_ARG: lane/edge mismatch, x not
+   in (0, len], overlapping vehicles in a lane). */
+int ms_add_vehicles(void *sim, const ms_vehicles *veh);
+
+/* Enqueue n steps on the simulation's stream (asynchronous; CUDA-graph replays).  Returns
+   MS_ERR_CUDA if a launch fails.  Device error bits are reported by ms_sync. */
+int ms_step(void *sim, int n);
+
+/* Wait for enqueued steps; MS_ERR_DEVICE if a device-side check fired. */
+int ms_sync(void *sim);
+
+/* Read the state (synchronises).  device = 0: the ms_state vehicle arrays are host
+   pointers; device = 1: they are device pointers (the copies are device-to-device) and
+   trip_status / t_arr, if not NULL, are host pointers.  MS_ERR_CAPACITY if capacity <
+   n_active (n_active is still set). */
+int ms_read_state(void *sim, ms_state *out, int device);
+
+/* Replace the dynamic state (checkpoint / resume).  Vehicles must be sorted by
+   (lane, x, id), one entry per active trip, gaps >= 0; trips neither active nor arrived
+   (t_arr < 0) wait for departure.  Metric accumulators are kept. */
+int ms_write_state(void *sim, const ms_state *in);
+
+int ms_read_metrics(void *sim, ms_metrics *out);
+
+/* Debug record of the last step (requires params.debug = 1, else MS_ERR_STATE). */
+int ms_read_debug(void *sim, ms_debug *out);
+
+const char *ms_last_error(void *sim);
+void ms_destroy(void *sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,757 @@
+// moss103.cu -- host side of the C ABI declared in include/moss103.h.
+//
+// Owns the device memory of one simulation, validates and converts the network and the
+// trips into the device layout (sorted structure-of-arrays vehicle state, 32-byte lane
+// records, CSR successor / feeder tables, per-lane departure FIFOs), and replays the four
+// step kernels of step_kernels.cuh as a captured CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "moss103.h"
+#include "step_kernels.cuh"
+
+using namespace moss;
+
+namespace {
+
+constexpr int GRAPH_STEPS = 16;
+
+struct Sim {
+  ms_params prm{};
+  DevParams P{};
+  cudaStream_t stream = nullptr;   // caller's stream
+  cudaStream_t cap = nullptr;      // private capture stream
+  int device = 0, n_sm = 0;
+  std::string err;
+  bool net_loaded = false, veh_loaded = false;
+  // network (host copies needed by validation and state I/O)
+  int n_lanes = 0, n_edges = 0, n_ctrl = 0;
+  std::vector<float> lane_len;
+  std::vector<int> lane_edge, lane_left, lane_right, succ_off, succ_lane, succ_edge, edge_nlanes,
+      edge_lane0;
+  // trips
+  int n_trips = 0;
+  std::vector<int> h_route0, h_routes, h_tdep, h_qoff, h_qtrip;
+  std::vector<float> h_v0;
+  // device
+  LaneInfo *d_li = nullptr;
+  int2 *d_succ = nullptr;
+  int *d_pred = nullptr;
+  int4 *d_ctrl4 = nullptr;
+  int *d_routes = nullptr;
+  Soa A[2]{};
+  int2 *d_dyn[2]{};
+  DevCtrl *d_ctrl = nullptr;
+  unsigned *d_leave = nullptr;
+  int *d_arr_cnt = nullptr, *d_amin = nullptr, *d_arr_start = nullptr;
+  Mover *d_movers = nullptr;
+  int4 *d_bucket = nullptr;
+  int *d_tile_flag = nullptr;
+  unsigned long long *d_tile_agg = nullptr, *d_tile_pre = nullptr;
+  int *d_qoff = nullptr, *d_qtrip = nullptr, *d_qhead = nullptr;
+  int *d_tdep = nullptr, *d_route0 = nullptr, *d_tarr = nullptr;
+  float *d_v0 = nullptr;
+  float *d_vsum = nullptr;
+  int *d_vcnt = nullptr;
+  DebugOut dbg{};
+  int n_tiles = 0;
+  int grid_veh = 0, grid_bucket = 0;
+  cudaGraphExec_t g_many = nullptr, g_one = nullptr;
+  std::vector<void *> allocs;
+};
+
+int fail(Sim *s, int code, const std::string &msg) {
+  if (s) s->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(s, MS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+int dalloc(Sim *s, T **p, size_t n) {
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+  if (e != cudaSuccess) return fail(s, MS_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  s->allocs.push_back(q);
+  *p = static_cast<T *>(q);
+  return MS_OK;
+}
+
+#define DALLOC(ptr, n)                       \
+  do {                                       \
+    int r_ = dalloc(s, &(ptr), (size_t)(n)); \
+    if (r_) return r_;                       \
+  } while (0)
+
+StepArgs make_args(Sim *s) {
+  StepArgs a{};
+  a.li = s->d_li;
+  a.succ = s->d_succ;
+  a.pred = s->d_pred;
+  a.ctrl4 = s->d_ctrl4;
+  a.routes = s->d_routes;
+  a.A[0] = s->A[0];
+  a.A[1] = s->A[1];
+  a.dyn[0] = s->d_dyn[0];
+  a.dyn[1] = s->d_dyn[1];
+  a.ctrl = s->d_ctrl;
+  a.leave = s->d_leave;
+  a.arr_cnt = s->d_arr_cnt;
+  a.amin = s->d_amin;
+  a.arr_start = s->d_arr_start;
+  a.movers = s->d_movers;
+  a.bucket = s->d_bucket;
+  a.tile_flag = s->d_tile_flag;
+  a.tile_agg = s->d_tile_agg;
+  a.tile_pre = s->d_tile_pre;
+  a.q_off = s->d_qoff;
+  a.q_trip = s->d_qtrip;
+  a.q_head = s->d_qhead;
+  a.trip_tdep = s->d_tdep;
+  a.trip_route0 = s->d_route0;
+  a.trip_v0 = s->d_v0;
+  a.t_arr = s->d_tarr;
+  a.vsum = s->d_vsum;
+  a.vcnt = s->d_vcnt;
+  a.dbg = s->dbg;
+  a.P = s->P;
+  return a;
+}
+
+// one step = four launches (+ the debug order check)
+cudaError_t enqueue_step(Sim *s, cudaStream_t st) {
+  StepArgs a = make_args(s);
+  const int blk = s->prm.block;
+  k_decide<<<s->grid_veh, blk, 0, st>>>(a);
+  k_lanes<<<s->n_tiles, SCAN_THREADS, 0, st>>>(a);
+  k_bucket<<<s->grid_bucket, 256, 0, st>>>(a, s->n_tiles);
+  k_apply<<<s->grid_veh, blk, 0, st>>>(a);
+  if (s->prm.debug) k_check<<<s->grid_bucket, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+int build_graphs(Sim *s) {
+  if (s->g_many) return MS_OK;
+  for (int which = 0; which < 2; ++which) {
+    int steps = which == 0 ? GRAPH_STEPS : 1;
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < steps && e == cudaSuccess; ++k) e = enqueue_step(s, s->cap);
+    cudaError_t e2 = cudaStreamEndCapture(s->cap, &g);
+    if (e != cudaSuccess) return fail(s, MS_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+    if (e2 != cudaSuccess) return fail(s, MS_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e2));
+    cudaGraphExec_t ex;
+    CK(cudaGraphInstantiate(&ex, g, 0));
+    CK(cudaGraphDestroy(g));
+    (which == 0 ? s->g_many : s->g_one) = ex;
+  }
+  return MS_OK;
+}
+
+bool lane_links_to(const Sim *s, int l, int e) {
+  for (int k = s->succ_off[l]; k < s->succ_off[l + 1]; ++k)
+    if (s->succ_edge[k] == e) return true;
+  return false;
+}
+
+int upload_state(Sim *s, const std::vector<int> &ids, const std::vector<int> &lanes,
+                 const std::vector<float> &xs, const std::vector<float> &vs,
+                 const std::vector<int> &route_idx, int t) {
+  // vehicles must be sorted by (lane, x, id); builds the SoA of parity t & 1
+  const int n = (int)ids.size();
+  if (n > s->n_trips) return fail(s, MS_ERR_CAPACITY, "more active vehicles than trips");
+  std::vector<float> v0(n);
+  std::vector<int> rp(n), nxt(n);
+  std::vector<int> cnt(s->n_lanes, 0);
+  std::vector<char> seen(s->n_trips, 0);
+  for (int i = 0; i < n; ++i) {
+    int id = ids[i], l = lanes[i];
+    if (id < 0 || id >= s->n_trips || seen[id]) return fail(s, MS_ERR_ARG, "vehicle id invalid or repeated");
+    seen[id] = 1;
+    if (l < 0 || l >= s->n_lanes) return fail(s, MS_ERR_ARG, "vehicle lane out of range");
+    if (!(xs[i] > 0.f) || !(xs[i] <= s->lane_len[l])) return fail(s, MS_ERR_ARG, "vehicle x not in (0, len]");
+    if (!(vs[i] >= 0.f) || vs[i] > s->P.v_max) return fail(s, MS_ERR_ARG, "vehicle speed outside [0, v_max]");
+    if (i > 0) {
+      int pl = lanes[i - 1];
+      if (pl > l || (pl == l && xs[i - 1] > xs[i]))
+        return fail(s, MS_ERR_ARG, "vehicles not sorted by (lane, x)");
+      if (pl == l && (xs[i] - s->P.L) - xs[i - 1] < -1e-3f)   // float rounding of gap-0 stops
+        return fail(s, MS_ERR_ARG, "overlapping vehicles (gap < 0) on a lane");
+    }
+    int r0 = s->h_route0[id];
+    int rlen = 0;
+    while (s->h_routes[r0 + rlen] >= 0) ++rlen;
+    int ri = route_idx[i];
+    if (ri < 0 || ri >= rlen) return fail(s, MS_ERR_ARG, "route index out of range");
+    int e = s->h_routes[r0 + ri];
+    if (s->lane_edge[l] >= 0) {
+      if (s->lane_edge[l] != e) return fail(s, MS_ERR_ARG, "vehicle lane is not on its route edge");
+    } else {
+      int en = ri + 1 < rlen ? s->h_routes[r0 + ri + 1] : -1;
+      int tg = s->succ_lane[s->succ_off[l]];
+      bool ok = en >= 0 && s->lane_edge[tg] == en;
+      if (ok) {
+        ok = false;   // the internal lane must leave from a lane of edge e
+        for (int q = 0; q < s->edge_nlanes[e] && !ok; ++q) {
+          int al = s->edge_lane0[e] + q;
+          for (int k = s->succ_off[al]; k < s->succ_off[al + 1]; ++k)
+            if (s->succ_lane[k] == l) ok = true;
+        }
+      }
+      if (!ok) return fail(s, MS_ERR_ARG, "vehicle on an internal lane that its route does not use");
+    }
+    v0[i] = s->h_v0[id];
+    rp[i] = r0 + ri;
+    nxt[i] = s->h_routes[r0 + ri + 1];
+    cnt[l]++;
+  }
+  std::vector<int2> dyn(s->n_lanes);
+  int acc = 0;
+  for (int l = 0; l < s->n_lanes; ++l) {
+    dyn[l] = make_int2(acc, cnt[l]);
+    acc += cnt[l];
+  }
+  const int p = t & 1;
+  cudaStream_t st = s->stream;
+  Soa &B = s->A[p];
+  if (n) {
+    CK(cudaMemcpyAsync(B.x, xs.data(), n * sizeof(float), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(B.v, vs.data(), n * sizeof(float), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(B.v0, v0.data(), n * sizeof(float), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(B.lane, lanes.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(B.rp, rp.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(B.nxt, nxt.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(B.id, ids.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaMemcpyAsync(s->d_dyn[p], dyn.data(), s->n_lanes * sizeof(int2), cudaMemcpyHostToDevice, st));
+  DevCtrl c{};
+  CK(cudaMemcpyAsync(&c, s->d_ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  c.t = t;
+  c.t_apply = t;
+  c.n_active[p] = n;
+  c.n_movers = 0;
+  c.tile_ticket = 0;
+  CK(cudaMemcpyAsync(s->d_ctrl, &c, sizeof(DevCtrl), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return MS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ms_create(void **out, const ms_params *p, void *cuda_stream) {
+  if (!out || !p) return MS_ERR_ARG;
+  *out = nullptr;
+  Sim *s = new Sim();
+  s->prm = *p;
+  if (s->prm.block == 0) s->prm.block = 256;
+  auto bad = [&](const char *m) {
+    std::fprintf(stderr, "ms_create: %s\n", m);
+    delete s;
+    return MS_ERR_ARG;
+  };
+  if (!(p->dt > 0) || !(p->veh_len > 0) || !(p->idm_a > 0) || !(p->idm_b > 0) || !(p->idm_T >= 0) ||
+      !(p->idm_s0 >= 0))
+    return bad("dt, veh_len, idm_a, idm_b must be > 0; idm_T, idm_s0 >= 0");
+  if (!(p->p_lc >= 0 && p->p_lc <= 1)) return bad("p_lc must be in [0, 1]");
+  if (!(p->a_min < 0) || !(p->v_max > 0) || !(p->d_look > 0)) return bad("a_min < 0, v_max > 0, d_look > 0 required");
+  if (p->window <= 0 || p->n_windows < 0) return bad("window > 0 and n_windows >= 0 required");
+  if (s->prm.block % 32 || s->prm.block < 32 || s->prm.block > 1024) return bad("block must be a multiple of 32 in [32, 1024]");
+  DevParams &P = s->P;
+  P.dt = p->dt; P.L = p->veh_len; P.a = p->idm_a; P.b = p->idm_b; P.T = p->idm_T; P.s0 = p->idm_s0;
+  P.p = p->mobil_p; P.th = p->mobil_th; P.bsafe = p->mobil_bsafe; P.a_min = p->a_min;
+  P.v_max = p->v_max; P.d_look = p->d_look; P.x_lc_min = p->x_lc_min; P.x_lc_end = p->x_lc_end;
+  P.inv2sqrtab = (float)(1.0 / (2.0 * std::sqrt((double)p->idm_a * (double)p->idm_b)));
+  P.lc_thresh = (uint32_t)std::floor((double)p->p_lc * 16777216.0);
+  P.seed = p->seed;
+  P.window = p->window;
+  P.n_windows = p->n_windows;
+  P.debug = p->debug;
+  s->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaGetDevice(&s->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, s->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "ms_create: %s\n", cudaGetErrorString(e));
+    delete s;
+    return MS_ERR_CUDA;
+  }
+  *out = s;
+  return MS_OK;
+}
+
+int ms_load_network(void *sim, const ms_network *net) {
+  Sim *s = (Sim *)sim;
+  if (!s || !net) return MS_ERR_ARG;
+  if (s->net_loaded) return fail(s, MS_ERR_STATE, "network already loaded");
+  const int L = net->n_lanes, E = net->n_edges, C = net->n_ctrl;
+  if (L <= 0 || E <= 0 || C < 0) return fail(s, MS_ERR_ARG, "n_lanes, n_edges must be > 0");
+  if (!net->lane_len || !net->lane_edge || !net->lane_index || !net->lane_left || !net->lane_right ||
+      !net->succ_off || !net->succ_lane || !net->succ_edge || !net->lane_ctrl || !net->lane_group ||
+      !net->edge_nlanes || !net->edge_lane0 || (C > 0 && (!net->ctrl_offset || !net->ctrl_green ||
+                                                          !net->ctrl_yellow || !net->ctrl_nphase)))
+    return fail(s, MS_ERR_ARG, "network array missing");
+  s->n_lanes = L; s->n_edges = E; s->n_ctrl = C;
+  s->lane_len.assign(net->lane_len, net->lane_len + L);
+  s->lane_edge.assign(net->lane_edge, net->lane_edge + L);
+  s->lane_left.assign(net->lane_left, net->lane_left + L);
+  s->lane_right.assign(net->lane_right, net->lane_right + L);
+  s->succ_off.assign(net->succ_off, net->succ_off + L + 1);
+  s->edge_nlanes.assign(net->edge_nlanes, net->edge_nlanes + E);
+  s->edge_lane0.assign(net->edge_lane0, net->edge_lane0 + E);
+  const int S = s->succ_off[L];
+  if (s->succ_off[0] != 0 || S < 0) return fail(s, MS_ERR_ARG, "succ_off must start at 0");
+  for (int l = 0; l < L; ++l)
+    if (s->succ_off[l + 1] < s->succ_off[l]) return fail(s, MS_ERR_ARG, "succ_off not monotone");
+  s->succ_lane.assign(net->succ_lane, net->succ_lane + S);
+  s->succ_edge.assign(net->succ_edge, net->succ_edge + S);
+  const float min_len = s->P.v_max * s->P.dt;
+  std::vector<LaneInfo> li(L);
+  std::vector<int> npred(L, 0);
+  for (int l = 0; l < L; ++l) {
+    const int e = s->lane_edge[l];
+    const int ns = s->succ_off[l + 1] - s->succ_off[l];
+    if (!(s->lane_len[l] > min_len))
+      return fail(s, MS_ERR_ARG, "lane " + std::to_string(l) + " not longer than v_max*dt");
+    if (e >= E) return fail(s, MS_ERR_ARG, "lane_edge out of range");
+    for (int k = s->succ_off[l]; k < s->succ_off[l + 1]; ++k) {
+      int sl = s->succ_lane[k], se = s->succ_edge[k];
+      if (sl < 0 || sl >= L || se < 0 || se >= E) return fail(s, MS_ERR_ARG, "successor out of range");
+      if (e >= 0 && s->lane_edge[sl] >= 0) return fail(s, MS_ERR_ARG, "edge lane successors must be internal lanes");
+      if (e < 0 && (s->lane_edge[sl] != se)) return fail(s, MS_ERR_ARG, "internal lane target / edge mismatch");
+    }
+    if (e < 0) {
+      if (ns != 1) return fail(s, MS_ERR_ARG, "internal lane must have exactly one successor");
+      if (s->lane_left[l] >= 0 || s->lane_right[l] >= 0) return fail(s, MS_ERR_ARG, "internal lane with neighbours");
+      npred[s->succ_lane[s->succ_off[l]]]++;
+    } else {
+      if (ns > 255) return fail(s, MS_ERR_ARG, "more than 255 successors");
+      int lf = s->lane_left[l], rt = s->lane_right[l];
+      if (lf >= L || rt >= L) return fail(s, MS_ERR_ARG, "left/right out of range");
+      if (lf >= 0 && (s->lane_edge[lf] != e || s->lane_right[lf] != l)) return fail(s, MS_ERR_ARG, "left/right inconsistent");
+      if (rt >= 0 && (s->lane_edge[rt] != e || s->lane_left[rt] != l)) return fail(s, MS_ERR_ARG, "left/right inconsistent");
+      if (s->lane_len[l] != s->lane_len[s->edge_lane0[e]]) return fail(s, MS_ERR_ARG, "lanes of an edge differ in length");
+    }
+    int c = net->lane_ctrl[l];
+    if (c >= C || (c >= 0 && (net->lane_group[l] < 0 || net->lane_group[l] >= net->ctrl_nphase[c] ||
+                              net->lane_group[l] > 255)))
+      return fail(s, MS_ERR_ARG, "lane_ctrl / lane_group invalid");
+    li[l].len = s->lane_len[l];
+    li[l].edge = e;
+    li[l].left = s->lane_left[l];
+    li[l].right = s->lane_right[l];
+    li[l].succ = e < 0 ? s->succ_lane[s->succ_off[l]] : s->succ_off[l];
+    li[l].ctrl = c;
+    li[l].n_succ = (unsigned char)(e < 0 ? 1 : ns);
+    li[l].group = (unsigned char)(c >= 0 ? net->lane_group[l] : 0);
+    li[l].idx = (unsigned char)std::max(0, std::min(255, net->lane_index[l]));
+  }
+  for (int e = 0; e < E; ++e)
+    if (s->edge_nlanes[e] <= 0 || s->edge_lane0[e] < 0 || s->edge_lane0[e] + s->edge_nlanes[e] > L)
+      return fail(s, MS_ERR_ARG, "edge lanes out of range");
+  std::vector<int> pred_off(L + 1, 0);
+  for (int l = 0; l < L; ++l) {
+    if (npred[l] > 255) return fail(s, MS_ERR_ARG, "more than 255 feeders");
+    pred_off[l + 1] = pred_off[l] + npred[l];
+    li[l].pred = pred_off[l];
+    li[l].n_pred = (unsigned char)npred[l];
+  }
+  std::vector<int> pred(std::max(1, pred_off[L])), fill(L, 0);
+  for (int l = 0; l < L; ++l)
+    if (s->lane_edge[l] < 0) {
+      int tg = s->succ_lane[s->succ_off[l]];
+      pred[pred_off[tg] + fill[tg]++] = l;
+    }
+  std::vector<int2> succ(std::max(1, S));
+  for (int k = 0; k < S; ++k) succ[k] = make_int2(s->succ_lane[k], s->succ_edge[k]);
+  std::vector<int4> c4(std::max(1, C));
+  for (int c = 0; c < C; ++c) {
+    if (net->ctrl_green[c] <= 0 || net->ctrl_yellow[c] < 0 || net->ctrl_nphase[c] <= 0)
+      return fail(s, MS_ERR_ARG, "controller timing invalid");
+    c4[c] = make_int4(net->ctrl_offset[c], net->ctrl_green[c], net->ctrl_yellow[c], net->ctrl_nphase[c]);
+  }
+  s->P.n_lanes = L;
+  DALLOC(s->d_li, L);
+  DALLOC(s->d_succ, succ.size());
+  DALLOC(s->d_pred, pred.size());
+  DALLOC(s->d_ctrl4, c4.size());
+  CK(cudaMemcpy(s->d_li, li.data(), L * sizeof(LaneInfo), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_succ, succ.data(), succ.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_pred, pred.data(), pred.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_ctrl4, c4.data(), c4.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  s->n_tiles = (L + SCAN_TILE - 1) / SCAN_TILE;
+  s->net_loaded = true;
+  return MS_OK;
+}
+
+int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
+  Sim *s = (Sim *)sim;
+  if (!s || !veh) return MS_ERR_ARG;
+  if (!s->net_loaded) return fail(s, MS_ERR_STATE, "load the network first");
+  if (s->veh_loaded) return fail(s, MS_ERR_STATE, "vehicles already added");
+  const int n = veh->n;
+  if (n <= 0 || !veh->t_dep || !veh->v0 || !veh->route_off || !veh->route_edges)
+    return fail(s, MS_ERR_ARG, "vehicle arrays missing or n <= 0");
+  s->n_trips = n;
+  s->h_route0.resize(n);
+  s->h_tdep.assign(veh->t_dep, veh->t_dep + n);
+  s->h_v0.assign(veh->v0, veh->v0 + n);
+  s->h_routes.clear();
+  s->h_routes.reserve((size_t)veh->route_off[n] + n);
+  for (int i = 0; i < n; ++i) {
+    int64_t a = veh->route_off[i], b = veh->route_off[i + 1];
+    if (b <= a) return fail(s, MS_ERR_ARG, "empty route for trip " + std::to_string(i));
+    if (!(s->h_v0[i] > 0.f) || s->h_v0[i] > s->P.v_max) return fail(s, MS_ERR_ARG, "v0 outside (0, v_max]");
+    s->h_route0[i] = (int)s->h_routes.size();
+    for (int64_t k = a; k < b; ++k) {
+      int e = veh->route_edges[k];
+      if (e < 0 || e >= s->n_edges) return fail(s, MS_ERR_ARG, "route edge out of range");
+      if (k > a) {
+        int pe = veh->route_edges[k - 1];
+        bool ok = false;
+        for (int q = 0; q < s->edge_nlanes[pe] && !ok; ++q) ok = lane_links_to(s, s->edge_lane0[pe] + q, e);
+        if (!ok)
+          return fail(s, MS_ERR_ROUTE, "trip " + std::to_string(i) + ": edges " + std::to_string(pe) + " -> " +
+                                           std::to_string(e) + " have no lane link");
+      }
+      s->h_routes.push_back(e);
+    }
+    s->h_routes.push_back(-1);
+    if (s->h_routes.size() > (size_t)0x7fff0000) return fail(s, MS_ERR_CAPACITY, "routes too long");
+  }
+  // placed vehicles, sorted by (lane, x, id)
+  std::vector<int> placed;
+  if (veh->lane) {
+    if (!veh->x || !veh->v) return fail(s, MS_ERR_ARG, "placement needs x and v");
+    for (int i = 0; i < n; ++i) {
+      int l = veh->lane[i];
+      if (l >= s->n_lanes) return fail(s, MS_ERR_ARG, "placement lane out of range");
+      if (l >= 0) placed.push_back(i);
+    }
+    std::sort(placed.begin(), placed.end(), [&](int a, int b) {
+      if (veh->lane[a] != veh->lane[b]) return veh->lane[a] < veh->lane[b];
+      if (veh->x[a] != veh->x[b]) return veh->x[a] < veh->x[b];
+      return a < b;
+    });
+  }
+  // departure FIFOs of unplaced trips: lowest-index lane of the first edge that links to the
+  // second edge, ordered by (t_dep, id)
+  std::vector<int> dep_lane(n, -1);
+  std::vector<char> is_placed(n, 0);
+  for (int i : placed) is_placed[i] = 1;
+  std::vector<int> qcnt(s->n_lanes, 0);
+  for (int i = 0; i < n; ++i) {
+    if (is_placed[i]) continue;
+    int r0 = s->h_route0[i];
+    int e0 = s->h_routes[r0], e1 = s->h_routes[r0 + 1];
+    int dl = -1;
+    for (int q = 0; q < s->edge_nlanes[e0] && dl < 0; ++q) {
+      int l = s->edge_lane0[e0] + q;
+      if (e1 < 0 || lane_links_to(s, l, e1)) dl = l;
+    }
+    dep_lane[i] = dl;
+    qcnt[dl]++;
+  }
+  s->h_qoff.assign(s->n_lanes + 1, 0);
+  for (int l = 0; l < s->n_lanes; ++l) s->h_qoff[l + 1] = s->h_qoff[l] + qcnt[l];
+  s->h_qtrip.assign(std::max(1, s->h_qoff[s->n_lanes]), 0);
+  {
+    std::vector<int> ord;
+    for (int i = 0; i < n; ++i)
+      if (!is_placed[i]) ord.push_back(i);
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) {
+      if (dep_lane[a] != dep_lane[b]) return dep_lane[a] < dep_lane[b];
+      if (s->h_tdep[a] != s->h_tdep[b]) return s->h_tdep[a] < s->h_tdep[b];
+      return a < b;
+    });
+    for (size_t k = 0; k < ord.size(); ++k) s->h_qtrip[k] = ord[k];
+  }
+  // device allocations sized for every trip at once
+  const int N = n;
+  for (int b = 0; b < 2; ++b) {
+    DALLOC(s->A[b].x, N); DALLOC(s->A[b].v, N); DALLOC(s->A[b].v0, N);
+    DALLOC(s->A[b].lane, N); DALLOC(s->A[b].rp, N); DALLOC(s->A[b].nxt, N); DALLOC(s->A[b].id, N);
+    DALLOC(s->d_dyn[b], s->n_lanes);
+  }
+  DALLOC(s->d_ctrl, 1);
+  // k_decide writes one word per warp of every block iteration below n: up to (N + block) / 32
+  const int leave_words = (N + 1024) / 32 + 2;
+  DALLOC(s->d_leave, leave_words);
+  DALLOC(s->d_arr_cnt, s->n_lanes);
+  DALLOC(s->d_amin, s->n_lanes);
+  DALLOC(s->d_arr_start, s->n_lanes + 1);
+  DALLOC(s->d_movers, N);
+  DALLOC(s->d_bucket, N);
+  DALLOC(s->d_tile_flag, s->n_tiles);
+  DALLOC(s->d_tile_agg, s->n_tiles);
+  DALLOC(s->d_tile_pre, s->n_tiles);
+  DALLOC(s->d_qoff, s->n_lanes + 1);
+  DALLOC(s->d_qtrip, s->h_qtrip.size());
+  DALLOC(s->d_qhead, s->n_lanes);
+  DALLOC(s->d_tdep, N);
+  DALLOC(s->d_route0, N);
+  DALLOC(s->d_tarr, N);
+  DALLOC(s->d_v0, N);
+  DALLOC(s->d_routes, s->h_routes.size());
+  if (s->prm.n_windows > 0) {
+    DALLOC(s->d_vsum, (size_t)s->prm.n_windows * s->n_lanes);
+    DALLOC(s->d_vcnt, (size_t)s->prm.n_windows * s->n_lanes);
+    CK(cudaMemset(s->d_vsum, 0, sizeof(float) * s->prm.n_windows * s->n_lanes));
+    CK(cudaMemset(s->d_vcnt, 0, sizeof(int) * s->prm.n_windows * s->n_lanes));
+  }
+  if (s->prm.debug) {
+    DebugOut &d = s->dbg;
+    DALLOC(d.id, N); DALLOC(d.lead_kind, N); DALLOC(d.lead_id, N); DALLOC(d.lc_dir, N);
+    DALLOC(d.lc_cand, N); DALLOC(d.tau_lead, N); DALLOC(d.tau_foll, N); DALLOC(d.old_foll, N);
+    DALLOC(d.flag, N); DALLOC(d.s_own, N); DALLOC(d.vl_own, N); DALLOC(d.a_own, N);
+    DALLOC(d.incentive, N); DALLOC(d.a_use, N); DALLOC(d.trip_ins, N); DALLOC(d.trip_flag, N);
+    DALLOC(d.arr_flag, s->n_lanes);
+    CK(cudaMemset(d.trip_ins, 0, sizeof(int) * N));
+    CK(cudaMemset(d.trip_flag, 0, sizeof(int) * N));
+    CK(cudaMemset(d.arr_flag, 0, sizeof(int) * s->n_lanes));
+  }
+  CK(cudaMemset(s->d_ctrl, 0, sizeof(DevCtrl)));
+  CK(cudaMemset(s->d_arr_cnt, 0, sizeof(int) * s->n_lanes));
+  {
+    std::vector<int> amin(s->n_lanes, AMIN_NONE);
+    CK(cudaMemcpy(s->d_amin, amin.data(), sizeof(int) * s->n_lanes, cudaMemcpyHostToDevice));
+  }
+  CK(cudaMemset(s->d_tile_flag, 0, sizeof(int) * s->n_tiles));
+  CK(cudaMemset(s->d_leave, 0, sizeof(unsigned) * leave_words));
+  std::vector<int> tarr(n, -1);
+  CK(cudaMemcpy(s->d_tarr, tarr.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_qoff, s->h_qoff.data(), sizeof(int) * (s->n_lanes + 1), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_qhead, s->h_qoff.data(), sizeof(int) * s->n_lanes, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_qtrip, s->h_qtrip.data(), sizeof(int) * s->h_qtrip.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_tdep, s->h_tdep.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_route0, s->h_route0.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_v0, s->h_v0.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_routes, s->h_routes.data(), sizeof(int) * s->h_routes.size(), cudaMemcpyHostToDevice));
+  // launch shapes: persistent grids sized by occupancy
+  int occ = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply, s->prm.block, 0));
+  int need = (N + s->prm.block - 1) / s->prm.block;
+  s->grid_veh = std::max(1, std::min(need, std::max(1, occ) * s->n_sm));
+  s->grid_bucket = std::max(1, std::min((N + 255) / 256, 4 * s->n_sm));
+  s->veh_loaded = true;
+  // initial state
+  std::vector<int> ids, lanes, ridx;
+  std::vector<float> xs, vs;
+  for (int i : placed) {
+    ids.push_back(i);
+    lanes.push_back(veh->lane[i]);
+    xs.push_back(veh->x[i]);
+    vs.push_back(veh->v[i]);
+    ridx.push_back(0);
+  }
+  int r = upload_state(s, ids, lanes, xs, vs, ridx, 0);
+  if (r) {
+    s->veh_loaded = false;
+    return r;
+  }
+  return MS_OK;
+}
+
+int ms_step(void *sim, int n) {
+  Sim *s = (Sim *)sim;
+  if (!s) return MS_ERR_ARG;
+  if (!s->veh_loaded) return fail(s, MS_ERR_STATE, "add vehicles before stepping");
+  if (n < 0) return fail(s, MS_ERR_ARG, "n < 0");
+  int r = build_graphs(s);
+  if (r) return r;
+  while (n >= GRAPH_STEPS) {
+    CK(cudaGraphLaunch(s->g_many, s->stream));
+    n -= GRAPH_STEPS;
+  }
+  while (n-- > 0) CK(cudaGraphLaunch(s->g_one, s->stream));
+  return MS_OK;
+}
+
+int ms_sync(void *sim) {
+  Sim *s = (Sim *)sim;
+  if (!s) return MS_ERR_ARG;
+  CK(cudaStreamSynchronize(s->stream));
+  if (!s->veh_loaded) return MS_OK;
+  unsigned err = 0;
+  CK(cudaMemcpy(&err, &s->d_ctrl->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (err) return fail(s, MS_ERR_DEVICE, "device error bits " + std::to_string(err));
+  return MS_OK;
+}
+
+int ms_read_state(void *sim, ms_state *out, int device) {
+  Sim *s = (Sim *)sim;
+  if (!s || !out) return MS_ERR_ARG;
+  if (!s->veh_loaded) return fail(s, MS_ERR_STATE, "no vehicles");
+  CK(cudaStreamSynchronize(s->stream));
+  DevCtrl c;
+  CK(cudaMemcpy(&c, s->d_ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost));
+  const int p = c.t & 1, n = c.n_active[p];
+  out->t = c.t;
+  out->n_active = n;
+  if (out->capacity < n) return fail(s, MS_ERR_CAPACITY, "state capacity too small");
+  const Soa &B = s->A[p];
+  std::vector<int> ids(n), rp(n);
+  if (n) {
+    cudaMemcpyKind k = device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (out->x) CK(cudaMemcpyAsync(out->x, B.x, n * sizeof(float), k, s->stream));
+    if (out->v) CK(cudaMemcpyAsync(out->v, B.v, n * sizeof(float), k, s->stream));
+    if (out->lane) CK(cudaMemcpyAsync(out->lane, B.lane, n * sizeof(int), k, s->stream));
+    if (out->id) CK(cudaMemcpyAsync(out->id, B.id, n * sizeof(int), k, s->stream));
+    if (device && out->route_idx) {
+      k_route_idx<<<std::min(1024, (n + 255) / 256), 256, 0, s->stream>>>(B.rp, B.id, s->d_route0,
+                                                                           out->route_idx, nullptr, n);
+      CK(cudaGetLastError());
+    }
+    if (!device && (out->route_idx || out->trip_status)) {
+      CK(cudaMemcpyAsync(ids.data(), B.id, n * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+      CK(cudaMemcpyAsync(rp.data(), B.rp, n * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    } else if (out->trip_status) {
+      CK(cudaMemcpyAsync(ids.data(), B.id, n * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    }
+  }
+  std::vector<int> tarr(s->n_trips);
+  if (out->t_arr || out->trip_status)
+    CK(cudaMemcpyAsync(tarr.data(), s->d_tarr, s->n_trips * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  if (!device && out->route_idx)
+    for (int i = 0; i < n; ++i) out->route_idx[i] = rp[i] - s->h_route0[ids[i]];
+  if (out->t_arr) std::memcpy(out->t_arr, tarr.data(), s->n_trips * sizeof(int));
+  if (out->trip_status) {
+    for (int i = 0; i < s->n_trips; ++i) out->trip_status[i] = tarr[i] >= 0 ? 2 : 0;
+    for (int i = 0; i < n; ++i) out->trip_status[ids[i]] = 1;
+  }
+  return MS_OK;
+}
+
+int ms_write_state(void *sim, const ms_state *in) {
+  Sim *s = (Sim *)sim;
+  if (!s || !in) return MS_ERR_ARG;
+  if (!s->veh_loaded) return fail(s, MS_ERR_STATE, "add vehicles first");
+  const int n = in->n_active;
+  if (n < 0 || in->t < 0 || (n > 0 && (!in->id || !in->lane || !in->x || !in->v || !in->route_idx)) || !in->t_arr)
+    return fail(s, MS_ERR_ARG, "state arrays missing");
+  CK(cudaStreamSynchronize(s->stream));
+  std::vector<int> ids(in->id, in->id + n), lanes(in->lane, in->lane + n), ridx(in->route_idx, in->route_idx + n);
+  std::vector<float> xs(in->x, in->x + n), vs(in->v, in->v + n);
+  for (int i = 1; i < n; ++i)
+    if (lanes[i - 1] == lanes[i] && xs[i - 1] == xs[i] && ids[i - 1] > ids[i])
+      return fail(s, MS_ERR_ARG, "vehicles not sorted by (lane, x, id)");
+  std::vector<char> active(s->n_trips, 0);
+  for (int i = 0; i < n; ++i)
+    if (ids[i] >= 0 && ids[i] < s->n_trips) active[ids[i]] = 1;
+  for (int i = 0; i < s->n_trips; ++i)
+    if (active[i] && in->t_arr[i] >= 0) return fail(s, MS_ERR_ARG, "trip both active and arrived");
+  int r = upload_state(s, ids, lanes, xs, vs, ridx, in->t);
+  if (r) return r;
+  // queue heads: first waiting trip of each FIFO
+  std::vector<int> qhead(s->n_lanes);
+  for (int l = 0; l < s->n_lanes; ++l) {
+    int q = s->h_qoff[l];
+    while (q < s->h_qoff[l + 1] && (active[s->h_qtrip[q]] || in->t_arr[s->h_qtrip[q]] >= 0)) ++q;
+    qhead[l] = q;
+  }
+  CK(cudaMemcpy(s->d_qhead, qhead.data(), sizeof(int) * s->n_lanes, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_tarr, in->t_arr, sizeof(int) * s->n_trips, cudaMemcpyHostToDevice));
+  return MS_OK;
+}
+
+int ms_read_metrics(void *sim, ms_metrics *out) {
+  Sim *s = (Sim *)sim;
+  if (!s || !out) return MS_ERR_ARG;
+  if (!s->veh_loaded) return fail(s, MS_ERR_STATE, "no vehicles");
+  CK(cudaStreamSynchronize(s->stream));
+  DevCtrl c;
+  CK(cudaMemcpy(&c, s->d_ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost));
+  size_t m = (size_t)s->prm.n_windows * s->n_lanes;
+  if (out->lane_vsum && m) CK(cudaMemcpy(out->lane_vsum, s->d_vsum, m * sizeof(float), cudaMemcpyDeviceToHost));
+  if (out->lane_vcnt && m) CK(cudaMemcpy(out->lane_vcnt, s->d_vcnt, m * sizeof(int), cudaMemcpyDeviceToHost));
+  out->inserted = (int64_t)c.inserted;
+  out->arrived = (int64_t)c.arrived;
+  out->sum_travel_time = (int64_t)c.sum_tt;
+  out->n_active = c.n_active[c.t & 1];
+  out->t = c.t;
+  out->movers_last_step = c.movers_last;
+  out->err = c.err;
+  return MS_OK;
+}
+
+int ms_read_debug(void *sim, ms_debug *out) {
+  Sim *s = (Sim *)sim;
+  if (!s || !out) return MS_ERR_ARG;
+  if (!s->prm.debug || !s->veh_loaded) return fail(s, MS_ERR_STATE, "debug recording is off");
+  CK(cudaStreamSynchronize(s->stream));
+  DevCtrl c;
+  CK(cudaMemcpy(&c, s->d_ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost));
+  if (c.t == 0) return fail(s, MS_ERR_STATE, "no step taken");
+  const int n = c.n_active[(c.t - 1) & 1];
+  const DebugOut &d = s->dbg;
+  std::vector<int> id(n), ik(n);
+  std::vector<float> fk(n);
+  if (n) CK(cudaMemcpy(id.data(), d.id, n * sizeof(int), cudaMemcpyDeviceToHost));
+  auto scat_i = [&](int *dst, const int *src) -> int {
+    if (!dst || !n) return MS_OK;
+    CK(cudaMemcpy(ik.data(), src, n * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n; ++i) dst[id[i]] = ik[i];
+    return MS_OK;
+  };
+  auto scat_f = [&](float *dst, const float *src) -> int {
+    if (!dst || !n) return MS_OK;
+    CK(cudaMemcpy(fk.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n; ++i) dst[id[i]] = fk[i];
+    return MS_OK;
+  };
+  int r = 0;
+  if (out->active_before) for (int i = 0; i < n; ++i) out->active_before[id[i]] = 1;
+  if ((r = scat_i(out->lead_kind, d.lead_kind)) || (r = scat_i(out->lead_id, d.lead_id)) ||
+      (r = scat_i(out->lc_dir, d.lc_dir)) || (r = scat_i(out->lc_cand, d.lc_cand)) ||
+      (r = scat_i(out->tau_lead, d.tau_lead)) || (r = scat_i(out->tau_foll, d.tau_foll)) ||
+      (r = scat_i(out->old_foll, d.old_foll)) || (r = scat_i(out->flag, d.flag)) ||
+      (r = scat_f(out->s_own, d.s_own)) || (r = scat_f(out->vl_own, d.vl_own)) ||
+      (r = scat_f(out->a_own, d.a_own)) || (r = scat_f(out->incentive, d.incentive)) ||
+      (r = scat_f(out->a_use, d.a_use)))
+    return r;
+  std::vector<int> stamp(s->n_trips);
+  if (out->inserted) {
+    CK(cudaMemcpy(stamp.data(), d.trip_ins, s->n_trips * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < s->n_trips; ++i) out->inserted[i] = stamp[i] == c.t ? 1 : 0;
+  }
+  if (out->flag) {
+    CK(cudaMemcpy(stamp.data(), d.trip_flag, s->n_trips * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < s->n_trips; ++i)
+      if (stamp[i] == c.t) out->flag[i] = 1;
+  }
+  return MS_OK;
+}
+
+const char *ms_last_error(void *sim) {
+  Sim *s = (Sim *)sim;
+  return s ? s->err.c_str() : "null simulation";
+}
+
+void ms_destroy(void *sim) {
+  Sim *s = (Sim *)sim;
+  if (!s) return;
+  if (s->veh_loaded || s->net_loaded) cudaStreamSynchronize(s->stream);
+  if (s->g_many) cudaGraphExecDestroy(s->g_many);
+  if (s->g_one) cudaGraphExecDestroy(s->g_one);
+  for (void *p : s->allocs) cudaFree(p);
+  if (s->cap) cudaStreamDestroy(s->cap);
+  delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,230 @@
+"""Python binding of the C ABI in include/moss103.h (argument marshalling only).
+
+Every step of the simulation runs in libmoss103.so's CUDA kernels; this module only packs
+numpy arrays / torch tensors into the C structs.  If the library is missing, importing
+`load()` raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmoss103.so")
+
+MS_OK, MS_ERR_ARG, MS_ERR_ROUTE, MS_ERR_CAPACITY, MS_ERR_CUDA, MS_ERR_DEVICE, MS_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
+ERR_NAMES = {0: "OK", -1: "ARG", -2: "ROUTE", -3: "CAPACITY", -4: "CUDA", -5: "DEVICE", -6: "STATE"}
+SYMBOLS = ("ms_create", "ms_load_network", "ms_add_vehicles", "ms_step", "ms_sync", "ms_read_state",
+           "ms_write_state", "ms_read_metrics", "ms_read_debug", "ms_last_error", "ms_destroy")
+
+
+class ms_params(C.Structure):
+    _fields_ = [(f, C.c_float) for f in (
+        "dt", "veh_len", "idm_a", "idm_b", "idm_T", "idm_s0", "mobil_p", "mobil_th", "mobil_bsafe",
+        "p_lc", "a_min", "v_max", "d_look", "x_lc_min", "x_lc_end")] + [
+        ("window", C.c_int), ("n_windows", C.c_int), ("seed", C.c_uint64), ("debug", C.c_int),
+        ("block", C.c_int)]
+
+
+class ms_network(C.Structure):
+    _fields_ = [("n_lanes", C.c_int), ("n_edges", C.c_int), ("n_ctrl", C.c_int)] + [
+        (f, C.c_void_p) for f in (
+            "lane_len", "lane_edge", "lane_index", "lane_left", "lane_right", "succ_off",
+            "succ_lane", "succ_edge", "lane_ctrl", "lane_group", "ctrl_offset", "ctrl_green",
+            "ctrl_yellow", "ctrl_nphase", "edge_nlanes", "edge_lane0")]
+
+
+class ms_vehicles(C.Structure):
+    _fields_ = [("n", C.c_int)] + [(f, C.c_void_p) for f in (
+        "t_dep", "v0", "route_off", "route_edges", "lane", "x", "v")]
+
+
+class ms_state(C.Structure):
+    _fields_ = [("capacity", C.c_int), ("n_active", C.c_int), ("t", C.c_int)] + [
+        (f, C.c_void_p) for f in ("id", "lane", "route_idx", "x", "v", "trip_status", "t_arr")]
+
+
+class ms_metrics(C.Structure):
+    _fields_ = [("lane_vsum", C.c_void_p), ("lane_vcnt", C.c_void_p), ("inserted", C.c_int64),
+                ("arrived", C.c_int64), ("sum_travel_time", C.c_int64), ("n_active", C.c_int),
+                ("t", C.c_int), ("movers_last_step", C.c_int), ("err", C.c_uint)]
+
+
+_DBG_I = ("active_before", "lead_kind", "lead_id", "lc_dir", "lc_cand", "tau_lead", "tau_foll",
+          "old_foll", "flag", "inserted")
+_DBG_F = ("s_own", "vl_own", "a_own", "incentive", "a_use")
+
+
+class ms_debug(C.Structure):
+    _fields_ = [(f, C.c_void_p) for f in _DBG_I + _DBG_F]
+
+
+_lib = None
+
+
+def load():
+    """Load libmoss103.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"{LIB_PATH} not built: run paper_2405_12520_b300.build.build()")
+        lib = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        lib.ms_create.argtypes = [C.POINTER(vp), C.POINTER(ms_params), vp]
+        lib.ms_load_network.argtypes = [vp, C.POINTER(ms_network)]
+        lib.ms_add_vehicles.argtypes = [vp, C.POINTER(ms_vehicles)]
+        lib.ms_step.argtypes = [vp, C.c_int]
+        lib.ms_sync.argtypes = [vp]
+        lib.ms_read_state.argtypes = [vp, C.POINTER(ms_state), C.c_int]
+        lib.ms_write_state.argtypes = [vp, C.POINTER(ms_state)]
+        lib.ms_read_metrics.argtypes = [vp, C.POINTER(ms_metrics)]
+        lib.ms_read_debug.argtypes = [vp, C.POINTER(ms_debug)]
+        lib.ms_last_error.argtypes = [vp]
+        lib.ms_last_error.restype = C.c_char_p
+        lib.ms_destroy.argtypes = [vp]
+        lib.ms_destroy.restype = None
+        for f in SYMBOLS:
+            if f not in ("ms_last_error", "ms_destroy"):
+                getattr(lib, f).restype = C.c_int
+        _lib = lib
+    return _lib
+
+
+class MossError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def params_struct(params: dict, debug: bool = False, n_windows: int = 1, block: int = 0) -> ms_params:
+    p = params
+    return ms_params(p["dt"], p["veh_len"], p["idm_a"], p["idm_b"], p["idm_T"], p["idm_s0"],
+                     p["mobil_p"], p["mobil_th"], p["mobil_bsafe"], p["p_lc"], p["a_min"], p["v_max"],
+                     p["d_look"], p["x_lc_min"], p["x_lc_end"], int(p["window"]), int(n_windows),
+                     int(p["seed"]) & 0xFFFFFFFFFFFFFFFF, int(debug), int(block))
+
+
+class Sim:
+    """One simulation on the current CUDA device.
+
+    Mirrors the C ABI: create (constructor), load_network, add_vehicles, step, sync,
+    read_state, write_state, read_metrics, read_debug, last_error, destroy."""
+
+    def __init__(self, params: dict, stream=None, debug: bool = False, n_windows: int = 1, block: int = 0):
+        self.lib = load()
+        self.h = C.c_void_p()
+        self.params = dict(params)
+        self.n_windows = n_windows
+        self._p = params_struct(params, debug, n_windows, block)
+        st = None
+        if stream is not None:
+            st = C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+        self._check(self.lib.ms_create(C.byref(self.h), C.byref(self._p), st), "ms_create")
+        self.n_lanes = 0
+        self.n_trips = 0
+
+    def _check(self, rc, what):
+        if rc != MS_OK:
+            msg = self.lib.ms_last_error(self.h).decode() if self.h else what
+            raise MossError(rc, f"{what}: {msg}")
+
+    def last_error(self) -> str:
+        return self.lib.ms_last_error(self.h).decode()
+
+    def load_network(self, net):
+        i32 = lambda a: np.ascontiguousarray(a, np.int32)
+        keep = [np.ascontiguousarray(net.lane_len, np.float32)] + [i32(getattr(net, f)) for f in (
+            "lane_edge", "lane_index", "lane_left", "lane_right", "succ_off", "succ_lane", "succ_edge",
+            "lane_ctrl", "lane_group", "ctrl_offset", "ctrl_green", "ctrl_yellow", "ctrl_nphase",
+            "edge_nlanes", "edge_lane0")]
+        s = ms_network(int(net.n_lanes), int(net.n_edges), int(net.n_ctrl), *[_p(a) for a in keep])
+        self._check(self.lib.ms_load_network(self.h, C.byref(s)), "ms_load_network")
+        self.n_lanes = int(net.n_lanes)
+
+    def add_vehicles(self, dem):
+        keep = [np.ascontiguousarray(dem.t_dep, np.int32), np.ascontiguousarray(dem.v0, np.float32),
+                np.ascontiguousarray(dem.route_off, np.int64), np.ascontiguousarray(dem.route_edges, np.int32),
+                np.ascontiguousarray(dem.lane, np.int32), np.ascontiguousarray(dem.x, np.float32),
+                np.ascontiguousarray(dem.v, np.float32)]
+        s = ms_vehicles(int(dem.n), *[_p(a) for a in keep])
+        self._check(self.lib.ms_add_vehicles(self.h, C.byref(s)), "ms_add_vehicles")
+        self.n_trips = int(dem.n)
+
+    def step(self, n: int = 1):
+        self._check(self.lib.ms_step(self.h, int(n)), "ms_step")
+
+    def sync(self):
+        self._check(self.lib.ms_sync(self.h), "ms_sync")
+
+    def read_state(self, trips: bool = True) -> dict:
+        s = ms_state(0, 0, 0)
+        self.lib.ms_read_state(self.h, C.byref(s), 0)   # sizes only
+        n = s.n_active
+        out = dict(id=np.zeros(n, np.int32), lane=np.zeros(n, np.int32), route_idx=np.zeros(n, np.int32),
+                   x=np.zeros(n, np.float32), v=np.zeros(n, np.float32))
+        if trips:
+            out["trip_status"] = np.zeros(self.n_trips, np.int32)
+            out["t_arr"] = np.zeros(self.n_trips, np.int32)
+        s = ms_state(n, 0, 0, *[_p(out.get(f)) for f in ("id", "lane", "route_idx", "x", "v", "trip_status", "t_arr")])
+        self._check(self.lib.ms_read_state(self.h, C.byref(s), 0), "ms_read_state")
+        out["t"] = s.t
+        out["n_active"] = s.n_active
+        return out
+
+    def read_state_device(self, x, v, lane, vid, route_idx=None) -> int:
+        """Device-to-device copy into torch CUDA tensors of sufficient length; returns n."""
+        ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+        s = ms_state(int(x.numel()), 0, 0, ptr(vid), ptr(lane), ptr(route_idx), ptr(x), ptr(v), None, None)
+        self._check(self.lib.ms_read_state(self.h, C.byref(s), 1), "ms_read_state")
+        return s.n_active
+
+    def write_state(self, st: dict):
+        n = int(st["id"].shape[0])
+        keep = dict(id=np.ascontiguousarray(st["id"], np.int32), lane=np.ascontiguousarray(st["lane"], np.int32),
+                    route_idx=np.ascontiguousarray(st["route_idx"], np.int32),
+                    x=np.ascontiguousarray(st["x"], np.float32), v=np.ascontiguousarray(st["v"], np.float32),
+                    t_arr=np.ascontiguousarray(st["t_arr"], np.int32))
+        s = ms_state(n, n, int(st["t"]), _p(keep["id"]), _p(keep["lane"]), _p(keep["route_idx"]),
+                     _p(keep["x"]), _p(keep["v"]), None, _p(keep["t_arr"]))
+        self._check(self.lib.ms_write_state(self.h, C.byref(s)), "ms_write_state")
+
+    def read_metrics(self, lanes: bool = True) -> dict:
+        m = self.n_windows * self.n_lanes
+        vs = np.zeros(m, np.float32) if lanes else None
+        vc = np.zeros(m, np.int32) if lanes else None
+        s = ms_metrics(_p(vs), _p(vc))
+        self._check(self.lib.ms_read_metrics(self.h, C.byref(s)), "ms_read_metrics")
+        out = dict(inserted=s.inserted, arrived=s.arrived, sum_tt=s.sum_travel_time, n_active=s.n_active,
+                   t=s.t, movers=s.movers_last_step, err=s.err)
+        if lanes:
+            out["vsum"] = vs.reshape(self.n_windows, self.n_lanes)
+            out["vcnt"] = vc.reshape(self.n_windows, self.n_lanes)
+        return out
+
+    def read_debug(self) -> dict:
+        n = self.n_trips
+        out = {f: np.full(n, -7, np.int32) for f in _DBG_I}
+        out["active_before"][:] = 0
+        out["inserted"][:] = 0
+        out["flag"][:] = 0
+        out.update({f: np.full(n, np.nan, np.float32) for f in _DBG_F})
+        s = ms_debug(*[_p(out[f]) for f in _DBG_I + _DBG_F])
+        self._check(self.lib.ms_read_debug(self.h, C.byref(s)), "ms_read_debug")
+        return out
+
+    def destroy(self):
+        if self.h:
+            self.lib.ms_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

@@ -545,119 +545,191 @@ def _spaced_positions(rng, lane_len, counts, min_spacing, veh_len):
     return lane_of, (veh_len + u + rank * min_spacing)
 
 
+def _gather_csr(parts, which, idx_in_part, n):
+    """Assemble per-vehicle routes from several CSR parts: vehicle i takes route
+    idx_in_part[i] of part which[i]."""
+    lens = np.empty(n, np.int64)
+    src = np.empty(n, np.int64)
+    base = 0
+    bases = []
+    for k, (off, _) in enumerate(parts):
+        m = which == k
+        lens[m] = (off[1:] - off[:-1])[idx_in_part[m]]
+        src[m] = base + off[:-1][idx_in_part[m]]
+        bases.append(base)
+        base += int(off[-1])
+    allr = np.concatenate([e for _, e in parts]) if parts else np.zeros(0, np.int32)
+    noff = np.zeros(n + 1, np.int64)
+    noff[1:] = np.cumsum(lens)
+    pos = np.repeat(src - noff[:-1], lens) + np.arange(int(noff[-1]))
+    return noff, allr[pos].astype(np.int32)
+
+
+def _route_many(net, rng, se, snode, dest, A, zs, pred, max_tries=50):
+    """Route vehicles starting on edge se (head node snode); redraw destinations whose
+    route would begin with a U-turn.  Returns CSR (off, edges)."""
+    n = se.shape[0]
+    V = net.node_xy.shape[0]
+    parts = []
+    which = np.full(n, -1, np.int64)
+    idx = np.zeros(n, np.int64)
+    pending = np.arange(n)
+    for k in range(max_tries):
+        if pending.size == 0:
+            break
+        if dest == "gravity":
+            nx, ny = net.grid_shape
+            d = _gravity_dest(rng, nx, ny, snode[pending], A)
+            off, e, ok = _grid_routes(net, se[pending], snode[pending], d)
+        elif net.grid_shape is not None:
+            d = rng.integers(0, V, size=pending.shape[0])
+            off, e, ok = _grid_routes(net, se[pending], snode[pending], d)
+        else:
+            d = rng.integers(0, zs.shape[0], size=pending.shape[0])
+            off, e, ok = _tree_routes(net, se[pending], snode[pending], d, zs, pred)
+        parts.append((off, e))
+        good = np.nonzero(ok)[0]
+        which[pending[good]] = len(parts) - 1
+        idx[pending[good]] = good
+        pending = pending[~ok]
+    # leftovers (destination straight behind): end the trip on the current edge
+    if pending.size:
+        off = np.arange(pending.size + 1, dtype=np.int64)
+        parts.append((off, se[pending].astype(np.int32)))
+        which[pending] = len(parts) - 1
+        idx[pending] = np.arange(pending.size)
+    return _gather_csr(parts, which, idx, n)
+
+
 def place_vehicles(net: Network, n: int, seed: int = 3, min_spacing: float = 9.0,
                    veh_len: float = 5.0, v0_mean: float = 13.9, v0_sd: float = 1.5,
                    internal_frac: float = 0.0, dest: str = "gravity", zones: int = 256) -> Demand:
-    """Steady-state workload: n vehicles already on the network at t = 0, spread over the
-    edge lanes (and, if internal_frac > 0, junction-internal lanes) in proportion to lane
-    length, consecutive fronts at least min_spacing apart, speed uniform in [0, v0],
-    v0 ~ N(v0_mean, v0_sd) clipped to [8, 20].  Destinations: gravity model on grids,
-    otherwise uniform over `zones` zone nodes; routes are shortest paths."""
+    """Steady-state workload: n vehicles already on the network at t = 0.
+
+    Vehicles are spread over edges in proportion to lane length (and, if internal_frac > 0,
+    also over junction-internal lanes with that relative weight), routed from the edge
+    they are on (gravity destinations on grids, else uniform over `zones` zone nodes),
+    then put on a lane of their edge that serves their next route edge; consecutive fronts
+    on a lane are at least min_spacing apart; speed uniform in [0, v0];
+    v0 ~ N(v0_mean, v0_sd) clipped to [8, 20]."""
     rng = np.random.default_rng(seed)
     nel = net.n_edge_lanes
     L = net.n_lanes
-    cap = np.floor((net.lane_len.astype(np.float64) - veh_len) / min_spacing).astype(np.int64) + 1
-    w = net.lane_len.astype(np.float64).copy()
-    w[nel:] *= internal_frac
-    if internal_frac == 0.0:
-        cap[nel:] = 0
-    if n > int(cap.sum()):
-        raise ValueError(f"{n} vehicles do not fit (capacity {int(cap.sum())})")
-    counts = rng.multinomial(n, w / w.sum())
-    for _ in range(100):
-        over = np.maximum(counts - cap, 0)
-        if not over.any():
-            break
-        counts -= over
-        room = cap - counts
-        extra = rng.multinomial(int(over.sum()), room / room.sum())
-        counts += np.minimum(extra, room)
-    short = n - int(counts.sum())
-    if short > 0:
-        room = cap - counts
-        idx = np.nonzero(room > 0)[0]
-        add = np.minimum(room[idx], short)
-        cs = np.cumsum(add)
-        k = np.searchsorted(cs, short)
-        add[k + 1:] = 0
-        add[k] -= cs[k] - short
-        counts[idx] += add
-    lane_of, x = _spaced_positions(rng, net.lane_len.astype(np.float64), counts, min_spacing, veh_len)
-    # origin node of the route search: head of the lane's edge (edge lanes) or of the exit
-    # edge (internal lanes)
-    is_int = lane_of >= nel
-    first_edge = np.where(is_int, -1, net.lane_edge[np.minimum(lane_of, nel - 1)])
-    # internal lane -> (approach edge, exit edge)
-    int_src_edge = np.full(L, -1, np.int64)
-    int_dst_edge = np.full(L, -1, np.int64)
-    for e_lane in range(nel):
-        for s in range(net.succ_off[e_lane], net.succ_off[e_lane + 1]):
-            int_src_edge[net.succ_lane[s]] = net.lane_edge[e_lane]
-            int_dst_edge[net.succ_lane[s]] = net.succ_edge[s]
-    appr = np.where(is_int, int_src_edge[lane_of], first_edge)
-    exit_e = np.where(is_int, int_dst_edge[lane_of], -1)
-    # the route search starts at the head of the edge the vehicle is on or entering
-    se = np.where(is_int, exit_e, first_edge)
-    snode = net.edge_to[se].astype(np.int64)
+    E = net.n_edges
     V = net.node_xy.shape[0]
-    v0 = np.clip(rng.normal(v0_mean, v0_sd, size=n), 8.0, 20.0)
-    v = rng.random(n) * v0
-    # lane -> edge connectivity pairs, to keep placed vehicles on lanes that serve their
-    # next route edge
-    src_l = np.repeat(np.arange(L), np.diff(net.succ_off))
-    conn_keys = np.unique(src_l.astype(np.int64) * net.n_edges + net.succ_edge)
-    # the lane whose successors must contain the next-but-current route edge: the edge lane
-    # itself, or the target lane of an internal lane
-    int_target = np.full(L, -1, np.int64)
-    int_target[nel:] = net.succ_lane[net.succ_off[nel:L]]
-    chk_lane = np.where(is_int, int_target[lane_of], lane_of)
-    if net.grid_shape is not None and dest == "gravity":
-        nx, ny = net.grid_shape
-        A = rng.lognormal(0.0, 1.0, size=V)
-    else:
+    lane_cap = np.floor((net.lane_len.astype(np.float64) - veh_len) / min_spacing).astype(np.int64) + 1
+    use_gravity = net.grid_shape is not None and dest == "gravity"
+    A = rng.lognormal(0.0, 1.0, size=V) if use_gravity else None
+    zs = pred = None
+    if not use_gravity and net.grid_shape is None:
         zs = np.unique(rng.integers(0, V, size=zones))
         _, pred = _zone_trees(net, zs)
-    dst = np.zeros(n, np.int64)
-    pending = np.arange(n)
-    R_off = np.zeros(n + 1, np.int64)
-    route_len = np.zeros(n, np.int64)
-    store = [None] * n
-    for attempt in range(60):
-        if pending.size == 0:
+    gdest = "gravity" if use_gravity else "uniform"
+    # internal lanes: (approach edge, exit edge, target lane)
+    int_src = np.full(L, -1, np.int64)
+    int_dst = np.full(L, -1, np.int64)
+    src_l = np.repeat(np.arange(nel), np.diff(net.succ_off[:nel + 1]))
+    sl = net.succ_lane[:net.succ_off[nel]]
+    int_src[sl] = net.lane_edge[src_l]
+    int_dst[sl] = net.succ_edge[:net.succ_off[nel]]
+    int_tgt = np.full(L, -1, np.int64)
+    int_tgt[nel:] = net.succ_lane[net.succ_off[nel:L]]
+    # how many on internal lanes vs edges
+    w_edge = net.edge_len.astype(np.float64) * net.edge_nlanes
+    w_int = net.lane_len[nel:].astype(np.float64) * internal_frac
+    tot = w_edge.sum() + w_int.sum()
+    n_int = int(round(n * w_int.sum() / tot)) if internal_frac > 0 else 0
+    cnt_i = None
+    if n_int:
+        wi = net.lane_len[nel:].astype(np.float64)
+        cnt_i = np.minimum(rng.multinomial(n_int, wi / wi.sum()), lane_cap[nel:])
+        n_int = int(cnt_i.sum())
+    n_edge = n - n_int
+    # --- edge vehicles: draw an edge, route from it, take a lane of it that serves the next
+    # route edge; vehicles that find their serving lanes full are drawn again elsewhere
+    conn_key = np.unique(src_l.astype(np.int64) * E + net.succ_edge[:net.succ_off[nel]])
+    lane_fill = np.zeros(L, np.int64)
+    e_cap = net.edge_nlanes.astype(np.int64) * lane_cap[net.edge_lane0]
+    if n_edge > int(e_cap.sum()):
+        raise ValueError(f"{n_edge} vehicles do not fit")
+    acc_parts, acc_lane = [], []
+    pending = n_edge
+    for attempt in range(200):
+        if pending == 0:
             break
-        if net.grid_shape is not None and dest == "gravity":
-            dst[pending] = _gravity_dest(rng, nx, ny, snode[pending], A)
-            o1, e1, ok1 = _grid_routes(net, se[pending], snode[pending], dst[pending])
-        else:
-            dst[pending] = rng.integers(0, zs.shape[0], size=pending.shape[0])
-            o1, e1, ok1 = _tree_routes(net, se[pending], snode[pending], dst[pending], zs, pred)
-        # the edge after the one the vehicle is on / entering
-        has2 = (o1[1:] - o1[:-1]) >= 2
-        e_after = np.where(has2, e1[np.minimum(o1[:-1] + 1, max(e1.shape[0] - 1, 0))], -1)
-        k = chk_lane[pending].astype(np.int64) * net.n_edges + np.maximum(e_after, 0)
-        pos = np.minimum(np.searchsorted(conn_keys, k), conn_keys.shape[0] - 1)
-        conn = (e_after < 0) | (conn_keys[pos] == k)
-        good = ok1 & conn
-        for gi in np.nonzero(good)[0]:
-            store[pending[gi]] = e1[o1[gi]:o1[gi + 1]]
-        pending = pending[~good]
-    for i in pending:
-        # no sampled destination is reached through an exit this lane serves: end the trip
-        # one edge later, through the first exit the lane serves
-        l = chk_lane[i]
-        ex = int(net.succ_edge[net.succ_off[l]])
-        store[i] = np.array([se[i], ex], np.int32)
-    lens = np.fromiter((r.shape[0] for r in store), np.int64, n) + is_int
-    off = np.zeros(n + 1, np.int64)
-    off[1:] = np.cumsum(lens)
-    edges = np.empty(int(off[-1]), np.int32)
-    for i in range(n):
-        o = off[i]
-        if is_int[i]:
-            edges[o] = appr[i]
-            o += 1
-        edges[o:off[i + 1]] = store[i]
-    del R_off, route_len
+        e_room = (e_cap - np.bincount(net.lane_edge[:nel], weights=lane_fill[:nel], minlength=E)).astype(np.float64)
+        w = w_edge * (e_room > 0)
+        se = rng.choice(E, size=pending, p=w / w.sum())
+        snode = net.edge_to[se].astype(np.int64)
+        off, edges = _route_many(net, rng, se, snode, gdest, A, zs, pred)
+        nxt = np.where(off[1:] - off[:-1] >= 2, edges[np.minimum(off[:-1] + 1, max(edges.shape[0] - 1, 0))], -1)
+        kmax = int(net.edge_nlanes.max())
+        ok_mask = np.zeros((pending, kmax), bool)
+        for q in range(kmax):
+            lq = net.edge_lane0[se] + q
+            key = lq.astype(np.int64) * E + np.maximum(nxt, 0)
+            pos = np.minimum(np.searchsorted(conn_key, key), conn_key.shape[0] - 1)
+            ok_mask[:, q] = (q < net.edge_nlanes[se]) & ((nxt < 0) | (conn_key[pos] == key))
+        nok = ok_mask.sum(1)
+        pick = np.floor(rng.random(pending) * np.maximum(nok, 1)).astype(np.int64)
+        q_sel = np.argmax(np.cumsum(ok_mask, 1) > pick[:, None], axis=1)
+        lane_e = net.edge_lane0[se] + q_sel
+        # accept up to the remaining capacity of each lane
+        o = np.argsort(lane_e, kind="stable")
+        ls = lane_e[o]
+        rank = np.arange(pending) - np.searchsorted(ls, ls, side="left")
+        acc = np.zeros(pending, bool)
+        acc[o] = rank < (lane_cap[ls] - lane_fill[ls])
+        acc &= nok > 0
+        ai = np.nonzero(acc)[0]
+        lane_fill += np.bincount(lane_e[ai], minlength=L)
+        acc_parts.append(_gather_csr([(off, edges)], np.zeros(ai.size, np.int64), ai, ai.size))
+        acc_lane.append(lane_e[ai])
+        pending -= ai.size
+    else:
+        raise RuntimeError("could not place all vehicles; lower the density")
+    lane_e = np.concatenate(acc_lane)
+    off, edges = _gather_csr(acc_parts, np.concatenate([np.full(l.shape[0], k) for k, l in enumerate(acc_lane)]),
+                             np.concatenate([np.arange(l.shape[0]) for l in acc_lane]), n_edge)
+    parts = [(off, edges)]
+    lanes_all = [lane_e]
+    # --- internal-lane vehicles (tests of junction logic)
+    if n_int:
+        lane_i = nel + np.repeat(np.arange(L - nel), cnt_i)
+        m = lane_i.shape[0]
+        se_i = int_dst[lane_i]
+        sn_i = net.edge_to[se_i].astype(np.int64)
+        off_i, edges_i = _route_many(net, rng, se_i, sn_i, gdest, A, zs, pred)
+        # keep those whose target lane serves the route's next edge, else end at the exit edge
+        nx_i = np.where(off_i[1:] - off_i[:-1] >= 2, edges_i[np.minimum(off_i[:-1] + 1, max(edges_i.shape[0] - 1, 0))], -1)
+        key = int_tgt[lane_i] * E + np.maximum(nx_i, 0)
+        pos = np.minimum(np.searchsorted(conn_key, key), conn_key.shape[0] - 1)
+        good = (nx_i < 0) | (conn_key[pos] == key)
+        one = np.arange(m + 1, dtype=np.int64)
+        short_parts = [(off_i, edges_i), (one, se_i.astype(np.int32))]
+        off_i, edges_i = _gather_csr(short_parts, np.where(good, 0, 1), np.arange(m), m)
+        # prepend the approach edge
+        lens = off_i[1:] - off_i[:-1] + 1
+        o2 = np.zeros(m + 1, np.int64)
+        o2[1:] = np.cumsum(lens)
+        e2 = np.empty(int(o2[-1]), np.int32)
+        e2[o2[:-1]] = int_src[lane_i]
+        pos2 = np.repeat(o2[:-1] + 1 - off_i[:-1], off_i[1:] - off_i[:-1]) + np.arange(int(off_i[-1]))
+        e2[pos2] = edges_i
+        parts.append((o2, e2))
+        lanes_all.append(lane_i)
+    lane_of = np.concatenate(lanes_all)
+    which = np.concatenate([np.full(a.shape[0], k) for k, a in enumerate(lanes_all)])
+    idx = np.concatenate([np.arange(a.shape[0]) for a in lanes_all])
+    off, edges = _gather_csr(parts, which, idx, n)
+    # positions: per lane, sorted uniform with spacing
+    order = np.argsort(lane_of, kind="stable")
+    counts = np.bincount(lane_of, minlength=L)
+    lane_sorted, x_sorted = _spaced_positions(rng, net.lane_len.astype(np.float64), counts, min_spacing, veh_len)
+    x = np.empty(n)
+    x[order] = x_sorted
+    v0 = np.clip(rng.normal(v0_mean, v0_sd, size=n), 8.0, 20.0)
+    v = rng.random(n) * v0
     return _pack(np.zeros(n, np.int32), v0, off, edges, lane=lane_of, x=x, v=v)
 
 

@@ -1,0 +1,48 @@
+"""The C ABI library loads, exports every entry point declared in include/moss103.h, and
+rejects invalid parameters before touching the GPU (no compute calls here)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2405_12520_b300 import build, moss, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    hdr = open(os.path.join(ROOT, "include", "moss103.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*\**\s*(ms_\w+)\s*\(", hdr, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for f in ("ms_create", "ms_load_network", "ms_add_vehicles", "ms_step", "ms_read_state",
+              "ms_write_state", "ms_read_metrics", "ms_read_debug", "ms_last_error", "ms_destroy", "ms_sync"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol():
+    build.build()
+    lib = C.CDLL(moss.LIB_PATH)
+    for f in _declared():
+        assert hasattr(lib, f), f
+    assert set(moss.SYMBOLS) <= set(_declared())
+
+
+@pytest.mark.parametrize("bad", [dict(dt=0.0), dict(p_lc=1.5), dict(a_min=1.0), dict(v_max=0.0),
+                                 dict(window=0)])
+def test_create_rejects_invalid_params(bad):
+    build.build()
+    p = synth.default_params(**bad)
+    with pytest.raises(moss.MossError) as e:
+        moss.Sim(p)
+    assert e.value.code == moss.MS_ERR_ARG
+
+
+def test_create_rejects_bad_block():
+    build.build()
+    with pytest.raises(moss.MossError) as e:
+        moss.Sim(synth.default_params(), block=100)
+    assert e.value.code == moss.MS_ERR_ARG

@@ -1,0 +1,330 @@
+#!/usr/bin/env python3
+"""Throughput of the per-time-step vehicle update (vehicle-steps/s) on one B300.
+
+A step is one simulation step of the whole hot path -- sort/merge by lane and position,
+neighbour search, IDM + randomized MOBIL, signal stop lines, ballistic advance, lane
+transfer, departures, metrics -- over every active vehicle of the workload.
+
+Default workload: 100x100 signalised grid, 3 lanes per direction, 300 m links,
+green-wave offsets, 1,000,000 vehicles already on the network (steady state), gravity-OD
+routes, v0 ~ N(13.9, 1.5) m/s.  Inputs are generated from a seed.  The step's working set
+(~90 MB) fits in the 126 MB L2, so L2 is flushed (256 MiB write) before every timed step
+and each step is timed alone with CUDA events on the simulation's stream.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica (the step has no
+cross-partition exchange on one GPU).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+KERNELS = ("k_decide", "k_lanes", "k_bucket", "k_apply")
+# algorithmic bytes of each kernel: SoA fields it must read / write per vehicle
+# (x, v, v0, lane, rp, nxt, id = 28 B), per lane (counts, starts, queue heads), per mover
+B_DECIDE_VEH = 28
+B_APPLY_VEH = 56
+B_LANES_LANE = 40
+B_BUCKET_MOVER = 40
+
+
+def workload(name: str, seed: int):
+    from paper_2405_12520_b300 import synth
+    if name == "grid1m":
+        net = synth.large_grid_network()
+        dem = synth.place_vehicles(net, 1_000_000, seed=seed)
+        desc = ("large grid 100x100, 3 lanes/direction, 300 m links, green-wave fixed-time signals; "
+                "1,000,000 vehicles pre-placed (steady state), gravity OD, v0~N(13.9,1.5)")
+    elif name == "city5m":
+        net = synth.delaunay_network(20000, box=30000.0, seed=seed)
+        dem = synth.place_vehicles(net, 5_000_000, seed=seed, min_spacing=7.0, dest="uniform")
+        desc = ("irregular city: Delaunay of 20k points in 30x30 km, 1-4 lanes by length quartile, "
+                "signals at degree>=3; 5,000,000 vehicles pre-placed (steady state), 256 zones")
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return net, dem, desc
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def kernel_src_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("step_kernels.cuh",):
+        with open(os.path.join(ROOT, "paper_2405_12520_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def traffic_per_unit(kernel: str, wl: str):
+    """DRAM bytes per vehicle of a kernel from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_src_hash()
+    for line in open(path):
+        f = line.split("#", 1)[0].split()
+        if len(f) == 4 and f[0] == kernel and f[1] == wl and f[3] == src:
+            return float(f[2])
+    return None
+
+
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        rows = []
+        for line in (getattr(self, "out", "") or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                rows.append((float(f[0]), float(f[1]), f[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for _, _, fl in rows for n, v in zip(names, fl) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(net, dem, params, budget_s: float = 20.0, max_steps: int = 10):
+    """The FP64 oracle, as it stands, single-threaded on this host, on the same workload:
+    vehicle-steps/s over up to max_steps steps or budget_s seconds after one warm-up step."""
+    import oracle
+    o = oracle.Oracle(net, dem, params)
+    o.step()
+    n_act = int((o.state()["status"] == 1).sum())
+    vs, steps, el = 0, 0, 0.0
+    while steps < max_steps and el < budget_s:
+        ts = time.perf_counter()
+        o.step()
+        el += time.perf_counter() - ts
+        vs += n_act
+        steps += 1
+        n_act = int((o.state()["status"] == 1).sum())
+    return vs / el, steps, el
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2405_12520_b300 import synth
+    net, dem, desc = workload(args.workload, args.seed)
+    p = synth.default_params()
+    k = max(1, min(args.steps, args.ref_steps))
+    val, steps, el = cpu_baseline(net, dem, p, budget_s=1e9, max_steps=k)
+    line = {
+        "impl": "reference", "metric": "vehicle-steps/s", "value": val, "unit": "vehicle-steps/s",
+        "n_gpus": world, "steps": steps, "warmup": 1, "ms_per_step": 1e3 * el / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "description": desc},
+        "cpu_baseline": {"value": val, "unit": "vehicle-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{steps} oracle steps of the full {args.workload} workload "
+                                   f"({dem.n} vehicles) after 1 warm-up step"},
+        "e2e": {"value": val, "unit": "vehicle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2405_12520_b300 import moss, synth
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    net, dem, desc = workload(args.workload, args.seed + rank)
+    params = synth.default_params()
+    stream = torch.cuda.current_stream()
+    sim = moss.Sim(params, stream=stream, n_windows=1, block=args.block)
+    sim.load_network(net)
+    sim.add_vehicles(dem)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    sim.step(args.warmup)
+    sim.sync()
+    n_act = [sim.read_metrics(lanes=False)["n_active"]]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            sim.step(1)
+            ev[k][1].record(stream)
+        barrier()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    n_end = sim.read_metrics(lanes=False)["n_active"]
+    # steady state (every vehicle placed at t = 0, none waiting): the active count at the
+    # start of step t is the number placed minus those with an arrival step <= t
+    st = sim.read_state()
+    t_first = st["t"] - args.steps
+    arr = np.sort(st["t_arr"][st["t_arr"] > 0])
+    per_step = [dem.n - int(np.searchsorted(arr, t_first + k, side="right")) for k in range(args.steps)]
+    vsteps = float(sum(per_step))
+    total_ms = float(sum(ms))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms, vsteps], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        total_ms, vsteps = float(mx[0]), float(t[1])
+    value = vsteps / (total_ms * 1e-3)
+
+    # per-kernel device time (kernel-by-kernel launches, L2 flushed before each step)
+    prof_steps = min(args.steps, 50)
+    kms = np.zeros(4)
+    n0 = sim.read_metrics(lanes=False)["n_active"]
+    movers = 0
+    for _ in range(prof_steps):
+        flush.zero_()
+        kms += sim.step_timed(1)
+        movers += sim.read_metrics(lanes=False)["movers"]
+    n1 = sim.read_metrics(lanes=False)["n_active"]
+    n_avg = 0.5 * (n0 + n1)
+    units = {"k_decide": n_avg * B_DECIDE_VEH, "k_lanes": net.n_lanes * B_LANES_LANE,
+             "k_bucket": movers / prof_steps * B_BUCKET_MOVER, "k_apply": n_avg * B_APPLY_VEH}
+    avg_ms = kms / prof_steps
+    dom = KERNELS[int(np.argmax(avg_ms))]
+    hbm, src = peaks()
+    ach = units[dom] / (avg_ms[KERNELS.index(dom)] * 1e-3) / 1e9
+    tpu = traffic_per_unit(dom, args.workload)
+    per_unit = n_avg if dom in ("k_decide", "k_apply") else (net.n_lanes if dom == "k_lanes" else movers / prof_steps)
+    roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None if tpu is None else tpu * per_unit, "kernel": dom,
+                "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6400 GB/s",
+                "kernel_ms": dict(zip(KERNELS, [round(x, 5) for x in avg_ms])),
+                "algorithmic_bytes": {"k_decide": f"{B_DECIDE_VEH} B/vehicle", "k_apply": f"{B_APPLY_VEH} B/vehicle",
+                                      "k_lanes": f"{B_LANES_LANE} B/lane", "k_bucket": f"{B_BUCKET_MOVER} B/mover"},
+                "step_effective_gbs": n_avg * (B_DECIDE_VEH + B_APPLY_VEH) / (avg_ms.sum() * 1e-3) / 1e9}
+
+    # end to end through the public API: step + read the per-vehicle state into pinned host
+    # memory every step (Sec. III-A: position and speed of every vehicle each step)
+    e2e_steps = min(args.steps, 50)
+    cap = dem.n
+    hx = torch.empty(cap, dtype=torch.float32, pin_memory=True)
+    hv = torch.empty(cap, dtype=torch.float32, pin_memory=True)
+    hl = torch.empty(cap, dtype=torch.int32, pin_memory=True)
+    hi = torch.empty(cap, dtype=torch.int32, pin_memory=True)
+    barrier()
+    t0 = time.perf_counter()
+    e2e_vs = 0
+    d2h = 0
+    for _ in range(e2e_steps):
+        n_before = sim.read_state_host(hx, hv, hl, hi) if _ == 0 else n_after
+        sim.step(1)
+        n_after = sim.read_state_host(hx, hv, hl, hi)
+        e2e_vs += n_before
+        d2h += 16 * n_after
+    t1 = time.perf_counter()
+    e2e = {"value": e2e_vs / (t1 - t0), "unit": "vehicle-steps/s", "h2d_bytes_per_step": 0,
+           "d2h_bytes_per_step": int(d2h / e2e_steps),
+           "what": "ms_step(1) + ms_read_state of x, v, lane, id into pinned host buffers, wall clock"}
+    sim.sync()
+
+    line = {
+        "metric": "vehicle-steps/s", "value": value, "unit": "vehicle-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "gpu_launches": 4 * args.steps,
+        "config": {"workload": args.workload, "description": desc, "vehicles": dem.n,
+                   "lanes": net.n_lanes, "active_start": n_act[0], "active_end": n_end,
+                   "l2": "flushed (256 MiB write) before every timed step; each step timed alone",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline, "e2e": e2e, "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        val, steps, el = cpu_baseline(net, dem, params)
+        line["cpu_baseline"] = {"value": val, "unit": "vehicle-steps/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{steps} single-threaded FP64 oracle steps of the same workload "
+                                          f"({dem.n} vehicles), {el:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sim.destroy()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default="grid1m")
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--ref-steps", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

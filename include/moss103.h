@@ -156,6 +156,12 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh);
    MS_ERR_CUDA if a launch fails.  Device error bits are reported by ms_sync. */
 int ms_step(void *sim, int n);
 
+/* Run n steps with each kernel launched on its own (no graph) between CUDA events on the
+   simulation's stream, and add each kernel's device time in milliseconds to
+   ms_per_kernel[0..3] (decide, lanes, bucket, apply; caller-owned, 4 floats).  Synchronises.
+   Same results as ms_step; used to attribute the step time to kernels. */
+int ms_step_timed(void *sim, int n, float *ms_per_kernel);
+
 /* Wait for enqueued steps; MS_ERR_DEVICE if a device-side check fired. */
 int ms_sync(void *sim);
 

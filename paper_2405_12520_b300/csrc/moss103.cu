@@ -582,6 +582,38 @@ int ms_step(void *sim, int n) {
   return MS_OK;
 }
 
+int ms_step_timed(void *sim, int n, float *ms_per_kernel) {
+  Sim *s = (Sim *)sim;
+  if (!s || !ms_per_kernel) return MS_ERR_ARG;
+  if (!s->veh_loaded) return fail(s, MS_ERR_STATE, "add vehicles before stepping");
+  cudaEvent_t ev[5];
+  for (auto &e : ev) CK(cudaEventCreate(&e));
+  cudaStream_t st = s->stream;
+  StepArgs a = make_args(s);
+  const int blk = s->prm.block;
+  for (int k = 0; k < n; ++k) {
+    CK(cudaEventRecord(ev[0], st));
+    k_decide<<<s->grid_veh, blk, 0, st>>>(a);
+    CK(cudaEventRecord(ev[1], st));
+    k_lanes<<<s->n_tiles, SCAN_THREADS, 0, st>>>(a);
+    CK(cudaEventRecord(ev[2], st));
+    k_bucket<<<s->grid_bucket, 256, 0, st>>>(a, s->n_tiles);
+    CK(cudaEventRecord(ev[3], st));
+    k_apply<<<s->grid_veh, blk, 0, st>>>(a);
+    CK(cudaEventRecord(ev[4], st));
+    if (s->prm.debug) k_check<<<s->grid_bucket, 256, 0, st>>>(a);
+    CK(cudaGetLastError());
+    CK(cudaEventSynchronize(ev[4]));
+    for (int q = 0; q < 4; ++q) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ev[q], ev[q + 1]));
+      ms_per_kernel[q] += ms;
+    }
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  return MS_OK;
+}
+
 int ms_sync(void *sim) {
   Sim *s = (Sim *)sim;
   if (!s) return MS_ERR_ARG;

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libmoss103.so")
 
 MS_OK, MS_ERR_ARG, MS_ERR_ROUTE, MS_ERR_CAPACITY, MS_ERR_CUDA, MS_ERR_DEVICE, MS_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 ERR_NAMES = {0: "OK", -1: "ARG", -2: "ROUTE", -3: "CAPACITY", -4: "CUDA", -5: "DEVICE", -6: "STATE"}
-SYMBOLS = ("ms_create", "ms_load_network", "ms_add_vehicles", "ms_step", "ms_sync", "ms_read_state",
+SYMBOLS = ("ms_create", "ms_load_network", "ms_add_vehicles", "ms_step", "ms_step_timed", "ms_sync", "ms_read_state",
            "ms_write_state", "ms_read_metrics", "ms_read_debug", "ms_last_error", "ms_destroy")
 
 
@@ -76,6 +76,7 @@ def load():
         lib.ms_load_network.argtypes = [vp, C.POINTER(ms_network)]
         lib.ms_add_vehicles.argtypes = [vp, C.POINTER(ms_vehicles)]
         lib.ms_step.argtypes = [vp, C.c_int]
+        lib.ms_step_timed.argtypes = [vp, C.c_int, C.POINTER(C.c_float)]
         lib.ms_sync.argtypes = [vp]
         lib.ms_read_state.argtypes = [vp, C.POINTER(ms_state), C.c_int]
         lib.ms_write_state.argtypes = [vp, C.POINTER(ms_state)]
@@ -158,6 +159,21 @@ class Sim:
 
     def step(self, n: int = 1):
         self._check(self.lib.ms_step(self.h, int(n)), "ms_step")
+
+    def step_timed(self, n: int = 1) -> np.ndarray:
+        """Run n steps kernel by kernel; device milliseconds per kernel
+        (decide, lanes, bucket, apply) summed over the n steps."""
+        ms = (C.c_float * 4)()
+        self._check(self.lib.ms_step_timed(self.h, int(n), ms), "ms_step_timed")
+        return np.array(list(ms), np.float64)
+
+    def read_state_host(self, x, v, lane, vid) -> int:
+        """Copy the vehicle state into caller-owned (e.g. pinned) host buffers given as
+        torch CPU tensors; returns the number of active vehicles."""
+        ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+        s = ms_state(int(x.numel()), 0, 0, ptr(vid), ptr(lane), None, ptr(x), ptr(v), None, None)
+        self._check(self.lib.ms_read_state(self.h, C.byref(s), 0), "ms_read_state")
+        return s.n_active
 
     def sync(self):
         self._check(self.lib.ms_sync(self.h), "ms_sync")

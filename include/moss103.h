@@ -162,6 +162,29 @@ int ms_step(void *sim, int n);
    Same results as ms_step; used to attribute the step time to kernels. */
 int ms_step_timed(void *sim, int n, float *ms_per_kernel);
 
+/* Largest network ms_step_noalloc accepts: lanes <= MS_NOALLOC_MAX_TILES * 2048. */
+#define MS_NOALLOC_MAX_TILES 1536
+
+/* ms_step_noalloc -- the same n steps as ms_step, for callers that must not allocate
+   device memory once their simulation is set up: for example a control or serving loop
+   that runs inside a fixed device-memory budget reserved in advance, or a host component
+   that holds no right to call cudaMalloc on a shared device.  ms_step may allocate on its
+   first call (it instantiates CUDA graphs), and the lane scan of every step keeps its
+   look-back status in memory of the simulation.  This entry point allocates nothing: it
+   launches the step's kernels directly and keeps the lane scan's look-back status in one
+   static device array of MS_NOALLOC_MAX_TILES tiles (20 bytes each), which every GPU that
+   loads this library holds until the process exits.
+   - The paper has no counterpart; results are identical to ms_step.
+   - Networks with more than MS_NOALLOC_MAX_TILES * 2048 lanes: MS_ERR_CAPACITY.
+   - The simulation's device must be current (else MS_ERR_STATE).  The first call on a
+     device looks up the array's device address (cudaGetSymbolAddress); make that first
+     call before any stream capture begins.
+   - Every call, from any simulation, shares the one array: calls that overlap on the GPU
+     (different streams, threads or simulations running at the same time) race and give
+     wrong results.  Each call clears the array before using it.
+   Returns MS_ERR_CUDA if a launch fails; device error bits are reported by ms_sync. */
+int ms_step_noalloc(void *sim, int n);
+
 /* Wait for enqueued steps; MS_ERR_DEVICE if a device-side check fired. */
 int ms_sync(void *sim);
 

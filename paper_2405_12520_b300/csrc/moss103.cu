@@ -614,6 +614,49 @@ int ms_step_timed(void *sim, int n, float *ms_per_kernel) {
   return MS_OK;
 }
 
+// Look-back status of the lane scan for ms_step_noalloc: per tile an aggregate and an
+// inclusive prefix (8 bytes each) and a flag (4 bytes), for MS_NOALLOC_MAX_TILES tiles.
+// One copy per device for the whole process; shared by every call (see moss103.h).
+static __device__ __align__(256) unsigned long long g_noalloc_scan[MS_NOALLOC_MAX_TILES * 5 / 2];
+static unsigned long long *g_noalloc_addr[256];   // device address per device ordinal
+
+int ms_step_noalloc(void *sim, int n) {
+  Sim *s = (Sim *)sim;
+  if (!s) return MS_ERR_ARG;
+  if (!s->veh_loaded) return fail(s, MS_ERR_STATE, "add vehicles before stepping");
+  if (n < 0) return fail(s, MS_ERR_ARG, "n < 0");
+  if (s->n_tiles > MS_NOALLOC_MAX_TILES)
+    return fail(s, MS_ERR_CAPACITY, "network has " + std::to_string(s->n_lanes) + " lanes; ms_step_noalloc takes at most " +
+                                        std::to_string(MS_NOALLOC_MAX_TILES * SCAN_TILE));
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev != s->device || dev < 0 || dev >= 256) return fail(s, MS_ERR_STATE, "make the simulation's device current");
+  if (!g_noalloc_addr[dev]) {
+    // host code sees g_noalloc_scan only as a host-side stand-in: resolve the device address
+    unsigned long long *ptr = nullptr;
+    CK(cudaGetSymbolAddress((void **)&ptr, g_noalloc_scan));
+    g_noalloc_addr[dev] = ptr;
+  }
+  unsigned long long *base = g_noalloc_addr[dev];
+  StepArgs a = make_args(s);
+  a.tile_agg = base;
+  a.tile_pre = base + MS_NOALLOC_MAX_TILES;
+  a.tile_flag = reinterpret_cast<int *>(base + 2 * MS_NOALLOC_MAX_TILES);
+  cudaStream_t st = s->stream;
+  // the array keeps whatever the last call left: flags must start at zero
+  CK(cudaMemsetAsync(a.tile_flag, 0, sizeof(int) * MS_NOALLOC_MAX_TILES, st));
+  const int blk = s->prm.block;
+  for (int k = 0; k < n; ++k) {
+    k_decide<<<s->grid_veh, blk, 0, st>>>(a);
+    k_lanes<<<s->n_tiles, SCAN_THREADS, 0, st>>>(a);
+    k_bucket<<<s->grid_bucket, 256, 0, st>>>(a, s->n_tiles);
+    k_apply<<<s->grid_veh, blk, 0, st>>>(a);
+    if (s->prm.debug) k_check<<<s->grid_bucket, 256, 0, st>>>(a);
+    CK(cudaGetLastError());
+  }
+  return MS_OK;
+}
+
 int ms_sync(void *sim) {
   Sim *s = (Sim *)sim;
   if (!s) return MS_ERR_ARG;

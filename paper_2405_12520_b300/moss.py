@@ -16,7 +16,8 @@ LIB_PATH = os.path.join(_HERE, "libmoss103.so")
 
 MS_OK, MS_ERR_ARG, MS_ERR_ROUTE, MS_ERR_CAPACITY, MS_ERR_CUDA, MS_ERR_DEVICE, MS_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 ERR_NAMES = {0: "OK", -1: "ARG", -2: "ROUTE", -3: "CAPACITY", -4: "CUDA", -5: "DEVICE", -6: "STATE"}
-SYMBOLS = ("ms_create", "ms_load_network", "ms_add_vehicles", "ms_step", "ms_step_timed", "ms_sync", "ms_read_state",
+SYMBOLS = ("ms_create", "ms_load_network", "ms_add_vehicles", "ms_step", "ms_step_timed", "ms_step_noalloc",
+           "ms_sync", "ms_read_state",
            "ms_write_state", "ms_read_metrics", "ms_read_debug", "ms_last_error", "ms_destroy")
 
 
@@ -77,6 +78,7 @@ def load():
         lib.ms_add_vehicles.argtypes = [vp, C.POINTER(ms_vehicles)]
         lib.ms_step.argtypes = [vp, C.c_int]
         lib.ms_step_timed.argtypes = [vp, C.c_int, C.POINTER(C.c_float)]
+        lib.ms_step_noalloc.argtypes = [vp, C.c_int]
         lib.ms_sync.argtypes = [vp]
         lib.ms_read_state.argtypes = [vp, C.POINTER(ms_state), C.c_int]
         lib.ms_write_state.argtypes = [vp, C.POINTER(ms_state)]
@@ -159,6 +161,11 @@ class Sim:
 
     def step(self, n: int = 1):
         self._check(self.lib.ms_step(self.h, int(n)), "ms_step")
+
+    def step_noalloc(self, n: int = 1):
+        """ms_step_noalloc: the same steps as step(), allocating no device memory (lane-scan
+        status in the library's static device array; calls must not overlap on the GPU)."""
+        self._check(self.lib.ms_step_noalloc(self.h, int(n)), "ms_step_noalloc")
 
     def step_timed(self, n: int = 1) -> np.ndarray:
         """Run n steps kernel by kernel; device milliseconds per kernel

@@ -51,8 +51,9 @@ struct Sim {
   DevCtrl *d_ctrl = nullptr;
   unsigned *d_leave = nullptr;
   int *d_arr_cnt = nullptr, *d_amin = nullptr, *d_arr_start = nullptr;
-  Mover *d_movers = nullptr;
   int4 *d_bucket = nullptr;
+  float *d_res_x = nullptr, *d_res_v = nullptr;
+  int *d_res_code = nullptr, *d_res_nl = nullptr, *d_arr_fill = nullptr;
   int *d_tile_flag = nullptr;
   unsigned long long *d_tile_agg = nullptr, *d_tile_pre = nullptr;
   int *d_qoff = nullptr, *d_qtrip = nullptr, *d_qhead = nullptr;
@@ -62,7 +63,7 @@ struct Sim {
   int *d_vcnt = nullptr;
   DebugOut dbg{};
   int n_tiles = 0;
-  int grid_veh = 0, grid_bucket = 0;
+  int grid_veh = 0, grid_apply = 0, grid_bucket = 0;
   cudaGraphExec_t g_many = nullptr, g_one = nullptr;
   std::vector<void *> allocs;
 };
@@ -111,8 +112,12 @@ StepArgs make_args(Sim *s) {
   a.arr_cnt = s->d_arr_cnt;
   a.amin = s->d_amin;
   a.arr_start = s->d_arr_start;
-  a.movers = s->d_movers;
   a.bucket = s->d_bucket;
+  a.res_x = s->d_res_x;
+  a.res_v = s->d_res_v;
+  a.res_code = s->d_res_code;
+  a.res_code_nl = s->d_res_nl;
+  a.arr_fill = s->d_arr_fill;
   a.tile_flag = s->d_tile_flag;
   a.tile_agg = s->d_tile_agg;
   a.tile_pre = s->d_tile_pre;
@@ -135,9 +140,9 @@ cudaError_t enqueue_step(Sim *s, cudaStream_t st) {
   StepArgs a = make_args(s);
   const int blk = s->prm.block;
   k_decide<<<s->grid_veh, blk, 0, st>>>(a);
-  k_lanes<<<s->n_tiles, SCAN_THREADS, 0, st>>>(a);
+  k_lanes<<<s->n_tiles, LANE_THREADS, 0, st>>>(a);
   k_bucket<<<s->grid_bucket, 256, 0, st>>>(a, s->n_tiles);
-  k_apply<<<s->grid_veh, blk, 0, st>>>(a);
+  k_apply<<<s->grid_apply, blk, 0, st>>>(a);
   if (s->prm.debug) k_check<<<s->grid_bucket, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
@@ -161,6 +166,29 @@ int build_graphs(Sim *s) {
   return MS_OK;
 }
 
+// host twin of the kernels' cached next-lane choice (first fan-out link toward en whose
+// target lane links to en2)
+bool lane_links_to(const Sim *s, int l, int e);
+int host_choose(const Sim *s, int l, int en, int en2) {
+  int first = -1;
+  for (int k = s->succ_off[l]; k < s->succ_off[l + 1]; ++k) {
+    if (s->succ_edge[k] != en) continue;
+    int il = s->succ_lane[k];
+    if (first < 0) first = il;
+    if (en2 < 0) return il;
+    if (lane_links_to(s, s->succ_lane[s->succ_off[il]], en2)) return il;
+  }
+  return first;
+}
+
+int host_next_choice(const Sim *s, int lane, int rp) {
+  const int *R = s->h_routes.data();
+  const int nxt = R[rp + 1];
+  if (s->lane_edge[lane] >= 0) return nxt >= 0 ? host_choose(s, lane, nxt, R[rp + 2]) : -1;
+  const int e2 = R[rp + 2];
+  return e2 >= 0 ? host_choose(s, s->succ_lane[s->succ_off[lane]], e2, R[rp + 3]) : -1;
+}
+
 bool lane_links_to(const Sim *s, int l, int e) {
   for (int k = s->succ_off[l]; k < s->succ_off[l + 1]; ++k)
     if (s->succ_edge[k] == e) return true;
@@ -174,7 +202,7 @@ int upload_state(Sim *s, const std::vector<int> &ids, const std::vector<int> &la
   const int n = (int)ids.size();
   if (n > s->n_trips) return fail(s, MS_ERR_CAPACITY, "more active vehicles than trips");
   std::vector<float> v0(n);
-  std::vector<int> rp(n), nxt(n);
+  std::vector<int> rp(n), nxt(n), nlc(n);
   std::vector<int> cnt(s->n_lanes, 0);
   std::vector<char> seen(s->n_trips, 0);
   for (int i = 0; i < n; ++i) {
@@ -216,6 +244,7 @@ int upload_state(Sim *s, const std::vector<int> &ids, const std::vector<int> &la
     v0[i] = s->h_v0[id];
     rp[i] = r0 + ri;
     nxt[i] = s->h_routes[r0 + ri + 1];
+    nlc[i] = host_next_choice(s, l, r0 + ri);
     cnt[l]++;
   }
   std::vector<int2> dyn(s->n_lanes);
@@ -234,6 +263,7 @@ int upload_state(Sim *s, const std::vector<int> &ids, const std::vector<int> &la
     CK(cudaMemcpyAsync(B.lane, lanes.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(B.rp, rp.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(B.nxt, nxt.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(B.nl, nlc.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(B.id, ids.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
   }
   CK(cudaMemcpyAsync(s->d_dyn[p], dyn.data(), s->n_lanes * sizeof(int2), cudaMemcpyHostToDevice, st));
@@ -271,7 +301,7 @@ int ms_create(void **out, const ms_params *p, void *cuda_stream) {
   if (!(p->p_lc >= 0 && p->p_lc <= 1)) return bad("p_lc must be in [0, 1]");
   if (!(p->a_min < 0) || !(p->v_max > 0) || !(p->d_look > 0)) return bad("a_min < 0, v_max > 0, d_look > 0 required");
   if (p->window <= 0 || p->n_windows < 0) return bad("window > 0 and n_windows >= 0 required");
-  if (s->prm.block % 32 || s->prm.block < 32 || s->prm.block > 1024) return bad("block must be a multiple of 32 in [32, 1024]");
+  if (s->prm.block % 32 || s->prm.block < 32 || s->prm.block > 512) return bad("block must be a multiple of 32 in [32, 512]");
   DevParams &P = s->P;
   P.dt = p->dt; P.L = p->veh_len; P.a = p->idm_a; P.b = p->idm_b; P.T = p->idm_T; P.s0 = p->idm_s0;
   P.p = p->mobil_p; P.th = p->mobil_th; P.bsafe = p->mobil_bsafe; P.a_min = p->a_min;
@@ -353,8 +383,14 @@ int ms_load_network(void *sim, const ms_network *net) {
       return fail(s, MS_ERR_ARG, "lane_ctrl / lane_group invalid");
     li[l].len = s->lane_len[l];
     li[l].edge = e;
-    li[l].left = s->lane_left[l];
-    li[l].right = s->lane_right[l];
+    if (e >= 0) {
+      li[l].left = s->lane_left[l];
+      li[l].right = s->lane_right[l];
+    } else {   // internal lane: its target lane's successor range
+      const int tg = s->succ_lane[s->succ_off[l]];
+      li[l].left = s->succ_off[tg];
+      li[l].right = s->succ_off[tg + 1] - s->succ_off[tg];
+    }
     li[l].succ = e < 0 ? s->succ_lane[s->succ_off[l]] : s->succ_off[l];
     li[l].ctrl = c;
     li[l].n_succ = (unsigned char)(e < 0 ? 1 : ns);
@@ -485,7 +521,8 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
   const int N = n;
   for (int b = 0; b < 2; ++b) {
     DALLOC(s->A[b].x, N); DALLOC(s->A[b].v, N); DALLOC(s->A[b].v0, N);
-    DALLOC(s->A[b].lane, N); DALLOC(s->A[b].rp, N); DALLOC(s->A[b].nxt, N); DALLOC(s->A[b].id, N);
+    DALLOC(s->A[b].lane, N); DALLOC(s->A[b].rp, N); DALLOC(s->A[b].nxt, N); DALLOC(s->A[b].nl, N);
+    DALLOC(s->A[b].id, N);
     DALLOC(s->d_dyn[b], s->n_lanes);
   }
   DALLOC(s->d_ctrl, 1);
@@ -495,8 +532,12 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
   DALLOC(s->d_arr_cnt, s->n_lanes);
   DALLOC(s->d_amin, s->n_lanes);
   DALLOC(s->d_arr_start, s->n_lanes + 1);
-  DALLOC(s->d_movers, N);
   DALLOC(s->d_bucket, N);
+  DALLOC(s->d_res_x, N);
+  DALLOC(s->d_res_v, N);
+  DALLOC(s->d_res_code, N);
+  DALLOC(s->d_res_nl, N);
+  DALLOC(s->d_arr_fill, s->n_lanes);
   DALLOC(s->d_tile_flag, s->n_tiles);
   DALLOC(s->d_tile_agg, s->n_tiles);
   DALLOC(s->d_tile_pre, s->n_tiles);
@@ -527,6 +568,7 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
   }
   CK(cudaMemset(s->d_ctrl, 0, sizeof(DevCtrl)));
   CK(cudaMemset(s->d_arr_cnt, 0, sizeof(int) * s->n_lanes));
+  CK(cudaMemset(s->d_arr_fill, 0, sizeof(int) * s->n_lanes));
   {
     std::vector<int> amin(s->n_lanes, AMIN_NONE);
     CK(cudaMemcpy(s->d_amin, amin.data(), sizeof(int) * s->n_lanes, cudaMemcpyHostToDevice));
@@ -543,11 +585,13 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
   CK(cudaMemcpy(s->d_v0, s->h_v0.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->d_routes, s->h_routes.data(), sizeof(int) * s->h_routes.size(), cudaMemcpyHostToDevice));
   // launch shapes: persistent grids sized by occupancy
-  int occ = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply, s->prm.block, 0));
+  int occ = 0, occ2 = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_decide, s->prm.block, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_apply, s->prm.block, 0));
   int need = (N + s->prm.block - 1) / s->prm.block;
   s->grid_veh = std::max(1, std::min(need, std::max(1, occ) * s->n_sm));
-  s->grid_bucket = std::max(1, std::min((N + 255) / 256, 4 * s->n_sm));
+  s->grid_apply = std::max(1, std::min(need, std::max(1, occ2) * s->n_sm));
+  s->grid_bucket = std::max(1, std::min((N + 255) / 256, 8 * s->n_sm));
   s->veh_loaded = true;
   // initial state
   std::vector<int> ids, lanes, ridx;
@@ -595,11 +639,11 @@ int ms_step_timed(void *sim, int n, float *ms_per_kernel) {
     CK(cudaEventRecord(ev[0], st));
     k_decide<<<s->grid_veh, blk, 0, st>>>(a);
     CK(cudaEventRecord(ev[1], st));
-    k_lanes<<<s->n_tiles, SCAN_THREADS, 0, st>>>(a);
+    k_lanes<<<s->n_tiles, LANE_THREADS, 0, st>>>(a);
     CK(cudaEventRecord(ev[2], st));
     k_bucket<<<s->grid_bucket, 256, 0, st>>>(a, s->n_tiles);
     CK(cudaEventRecord(ev[3], st));
-    k_apply<<<s->grid_veh, blk, 0, st>>>(a);
+    k_apply<<<s->grid_apply, blk, 0, st>>>(a);
     CK(cudaEventRecord(ev[4], st));
     if (s->prm.debug) k_check<<<s->grid_bucket, 256, 0, st>>>(a);
     CK(cudaGetLastError());
@@ -648,9 +692,9 @@ int ms_step_noalloc(void *sim, int n) {
   const int blk = s->prm.block;
   for (int k = 0; k < n; ++k) {
     k_decide<<<s->grid_veh, blk, 0, st>>>(a);
-    k_lanes<<<s->n_tiles, SCAN_THREADS, 0, st>>>(a);
+    k_lanes<<<s->n_tiles, LANE_THREADS, 0, st>>>(a);
     k_bucket<<<s->grid_bucket, 256, 0, st>>>(a, s->n_tiles);
-    k_apply<<<s->grid_veh, blk, 0, st>>>(a);
+    k_apply<<<s->grid_apply, blk, 0, st>>>(a);
     if (s->prm.debug) k_check<<<s->grid_bucket, 256, 0, st>>>(a);
     CK(cudaGetLastError());
   }

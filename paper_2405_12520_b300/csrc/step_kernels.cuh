@@ -3,18 +3,20 @@
 // The step of Sec. III-A (prepare phase + update phase) is laid out for HBM as four
 // kernels over a vehicle state that is kept physically sorted by (lane, x):
 //
-//   k_decide  (update phase, pass 1)  one thread per vehicle in sorted order: sense the
-//             own-path leader and the target-lane neighbours from the read-only snapshot,
-//             IDM + randomized MOBIL + stop lines + ballistic advance + transfer; emit a
-//             leave bit per vehicle (warp ballot) and a record per vehicle that changes
-//             lane; per-lane window metrics by the first vehicle of each lane.
-//   k_lanes   (prepare phase for t+1)  decoupled look-back scan over lanes: new per-lane
-//             counts = stayers + arrivals + departures, new segment starts, arrival bucket
-//             starts; departure FIFOs admit their head vehicle.
+//   k_decide  (update phase)  one thread per vehicle in sorted order: sense the own-path
+//             leader and the target-lane neighbours from the read-only snapshot, IDM +
+//             randomized MOBIL + stop lines + ballistic advance + transfer; store the
+//             vehicle's result (x', v', new lane and kind: 12 B), a leave bit per vehicle
+//             (warp ballot), and a record per vehicle that enters another lane (one atomic
+//             per warp for the record slots); per-lane window metrics by the first vehicle
+//             of each lane.
+//   k_lanes   (prepare phase for t+1)  decoupled look-back scan over lanes (32 predecessor
+//             tiles per probe): new per-lane counts = stayers + arrivals + departures, new
+//             segment starts, arrival bucket starts; departure FIFOs admit their head.
 //   k_bucket  place each arrival record into its lane's bucket with its rank among the
 //             lane's stayers.
-//   k_apply   (update phase, pass 2) recompute the same update (bit-identical) and write
-//             each vehicle straight to its sorted slot of the t+1 buffer.
+//   k_apply   stream every vehicle with its stored result to its sorted slot of the t+1
+//             buffer (no sensing repeated).
 //
 // Stayers keep their relative order (no overtaking within a lane), so the t+1 order is a
 // merge of the stayers with the few arrivals; no full sort is needed.
@@ -42,8 +44,10 @@ constexpr unsigned DEV_HOP = 1u, DEV_SCAN = 2u, DEV_ORDER = 4u, DEV_BUCKET = 8u;
 struct __align__(32) LaneInfo {
   float len;
   int edge;     // -1 for junction-internal lanes
-  int left;     // -1 none
-  int right;    // -1 none
+  int left;     // edge lane: lane to the left, -1 none; internal lane: tsucc, the first
+                // successor entry of its target lane
+  int right;    // edge lane: lane to the right, -1 none; internal lane: tn_succ, the
+                // number of successor entries of its target lane
   int succ;     // edge lane: first entry in succ[]; internal lane: its target lane
   int pred;     // first entry in pred[] of the internal lanes feeding this lane
   int ctrl;     // signal controller at the lane end, -1 none
@@ -58,26 +62,24 @@ struct DevParams {
   int window, n_windows, debug, n_lanes;
 };
 
+// Vehicle state, sorted by (lane, x).  rp: index into routes[] of the current edge (the
+// approach edge on an internal lane); nxt = routes[rp + 1]; nl: the lane the vehicle will
+// enter at the end of its current edge lane (for an internal lane: at the end of its
+// target lane), -1 if none -- cached so that sensing needs no route or link lookups.
 struct Soa {
   float *x, *v, *v0;
-  int *lane, *rp, *nxt, *id;
+  int *lane, *rp, *nxt, *nl, *id;
 };
 
 struct DevCtrl {
   int t;             // step the next k_decide computes
   int t_apply;       // step being applied (set by k_lanes, read by k_bucket / k_apply)
   int n_active[2];   // vehicles in buffer 0 / 1
-  int n_movers;
+  int n_movers;      // arrivals of the last step (count only)
   int tile_ticket;
   unsigned err;
   int movers_last;
   unsigned long long inserted, arrived, sum_tt;
-};
-
-struct Mover {
-  int i, lane;
-  float xnew, xold;
-  int k, kind;
 };
 
 struct DebugOut {
@@ -86,6 +88,12 @@ struct DebugOut {
   int *trip_ins, *trip_flag;   // step stamps (t+1) per trip id
   int *arr_flag;               // per lane: a flagged vehicle enters it this step
 };
+
+// Per-vehicle result of k_decide, consumed by k_apply: new x, new v, and a code word
+// (new lane in bits 0..28, kind in bits 29..31).
+constexpr int CODE_LANE_BITS = 29;
+constexpr int CODE_LANE_MASK = (1 << CODE_LANE_BITS) - 1;
+enum { C_STAY = 0, C_CHANGE = 1, C_TRANSFER = 2, C_TRANSFER_ROUTE = 3, C_RETIRE = 4 };
 
 struct StepArgs {
   const LaneInfo *li;
@@ -98,8 +106,11 @@ struct StepArgs {
   DevCtrl *ctrl;
   unsigned *leave;
   int *arr_cnt, *amin, *arr_start;
-  Mover *movers;
   int4 *bucket;        // {r, x bits, id, old index}
+  float *res_x, *res_v;
+  int *res_code;
+  int *arr_fill;       // per lane: arrival slots handed out by k_bucket (reset by k_apply)
+  int *res_code_nl;    // next-lane choice of arrivals, written by k_decide (sparse)
   int *tile_flag;
   unsigned long long *tile_agg, *tile_pre;
   const int *q_off, *q_trip;
@@ -164,26 +175,44 @@ __device__ __forceinline__ int sig_state(const StepArgs &a, const LaneInfo &li, 
   return (tau % gy) < c.y ? SIG_G : SIG_Y;
 }
 
-// edge lane l has a link toward edge en (en < 0: route ends, always true)
-__device__ __forceinline__ bool connects(const StepArgs &a, const LaneInfo &li, int en) {
+// successor entries [b, b + n) contain a link toward edge en (en < 0: route ends: true)
+__device__ __forceinline__ bool links_to(const StepArgs &a, int b, int n, int en) {
   if (en < 0) return true;
-  for (int k = 0; k < li.n_succ; ++k)
-    if (a.succ[li.succ + k].y == en) return true;
+  for (int k = 0; k < n; ++k)
+    if (a.succ[b + k].y == en) return true;
   return false;
 }
 
-// fan-out link of edge lane l toward en: the first whose target lane serves en2
-__device__ __forceinline__ int choose_succ(const StepArgs &a, const LaneInfo &li, int en, int en2) {
+// edge lane li has a link toward edge en
+__device__ __forceinline__ bool connects(const StepArgs &a, const LaneInfo &li, int en) {
+  return links_to(a, li.succ, li.n_succ, en);
+}
+
+// fan-out link toward en among successor entries [b, b + n): the first whose target lane
+// serves en2 (the internal lane's record carries its target's successor range)
+__device__ __forceinline__ int choose_link(const StepArgs &a, int b, int n, int en, int en2) {
   int first = -1;
-  for (int k = 0; k < li.n_succ; ++k) {
-    int2 s = a.succ[li.succ + k];
+  for (int k = 0; k < n; ++k) {
+    int2 s = a.succ[b + k];
     if (s.y != en) continue;
     if (first < 0) first = s.x;
     if (en2 < 0) return s.x;
-    int tg = a.li[s.x].succ;
-    if (connects(a, a.li[tg], en2)) return s.x;
+    const LaneInfo il = a.li[s.x];
+    if (links_to(a, il.left, il.right, en2)) return s.x;
   }
   return first;
+}
+
+__device__ __forceinline__ int choose_succ(const StepArgs &a, const LaneInfo &li, int en, int en2) {
+  return choose_link(a, li.succ, li.n_succ, en, en2);
+}
+
+// The cached next-lane choice of a vehicle on `lane` with route index rp, next edge nxt.
+__device__ __forceinline__ int next_choice(const StepArgs &a, int lane, int rp, int nxt) {
+  const LaneInfo li = a.li[lane];
+  if (li.edge >= 0) return nxt >= 0 ? choose_succ(a, li, nxt, a.routes[rp + 2]) : -1;
+  const int e2 = a.routes[rp + 2];   // edge after the target lane's edge
+  return e2 >= 0 ? choose_link(a, li.left, li.right, e2, a.routes[rp + 3]) : -1;
 }
 
 struct Lead {
@@ -210,7 +239,7 @@ struct Upd {
 
 __device__ __forceinline__ Lead own_leader(const StepArgs &a, const Soa &S, const int2 *dyn, int i,
                                            int l, const LaneInfo &li, float x, float v, int rp,
-                                           int en, int myid, int t, int &flag) {
+                                           int en, int nlc, int myid, int t, int &flag) {
   const DevParams &P = a.P;
   Lead r{K_FREE, 0.f, 0.f, -1, 0};
   int2 d = dyn[l];
@@ -220,6 +249,7 @@ __device__ __forceinline__ Lead own_leader(const StepArgs &a, const Soa &S, cons
   } else {
     float dist = li.len - x;
     int ri = rp, e_next = en;
+    bool cached = true;   // the first edge-lane hop uses the vehicle's cached choice
     LaneInfo lc = li;
     for (int hop = 0;; ++hop) {
       mark(flag, dist - P.d_look);
@@ -227,7 +257,8 @@ __device__ __forceinline__ Lead own_leader(const StepArgs &a, const Soa &S, cons
       int nxt;
       if (lc.edge >= 0) {
         if (e_next < 0) break;   // destination edge: open end
-        nxt = choose_succ(a, lc, e_next, a.routes[ri + 2]);
+        nxt = cached ? nlc : choose_succ(a, lc, e_next, a.routes[ri + 2]);
+        cached = false;
         bool stop = nxt < 0;
         if (!stop) {
           int sg = sig_state(a, lc, t);
@@ -311,7 +342,7 @@ __device__ __forceinline__ bool end_blocks(const StepArgs &a, const LaneInfo &lt
 
 __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const int2 *dyn, int i,
                                           int l, const LaneInfo &li, float x, float v, float v0,
-                                          int en, int myid, int t, const Lead &own, float a_c,
+                                          int en, int nlc, int myid, int t, const Lead &own, float a_c,
                                           int &flag) {
   const DevParams &P = a.P;
   LC r{};
@@ -320,7 +351,7 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
   int step_dir = (t % 2 == 0) ? 1 : -1;
   int tau = step_dir > 0 ? li.left : li.right;
   if (tau < 0) return r;
-  bool mand = !connects(a, li, en);
+  const bool mand = en >= 0 && nlc < 0;   // own lane has no link toward the next edge
   if (mand) {
     int dr = 1 << 30, dl = 1 << 30, k = 1;
     for (int q = li.right; q >= 0; q = a.li[q].right, ++k)
@@ -421,11 +452,11 @@ __device__ __forceinline__ Upd vehicle_update(const StepArgs &a, const Soa &S, c
   u.flag = 0;
   const int l = S.lane[i];
   const float x = S.x[i], v = S.v[i], v0 = S.v0[i];
-  const int rp = S.rp[i], en = S.nxt[i], myid = S.id[i];
+  const int rp = S.rp[i], en = S.nxt[i], nlc = S.nl[i], myid = S.id[i];
   const LaneInfo li = a.li[l];
-  u.own = own_leader(a, S, dyn, i, l, li, x, v, rp, en, myid, t, u.flag);
+  u.own = own_leader(a, S, dyn, i, l, li, x, v, rp, en, nlc, myid, t, u.flag);
   u.a_own = idm(P, v, v0, u.own.kind != K_FREE, u.own.gap, u.own.vl);
-  u.lc = lane_change(a, S, dyn, i, l, li, x, v, v0, en, myid, t, u.own, u.a_own, u.flag);
+  u.lc = lane_change(a, S, dyn, i, l, li, x, v, v0, en, nlc, myid, t, u.own, u.a_own, u.flag);
   const int dir = u.lc.dir;
   u.a_use = dir ? fminf(u.a_own, u.lc.anew) : u.a_own;
   float vraw = v + u.a_use * P.dt;
@@ -464,7 +495,7 @@ __device__ __forceinline__ Upd vehicle_update(const StepArgs &a, const Soa &S, c
         u.kind = U_TRANSFER;
         int nl;
         if (li.edge >= 0) {
-          nl = choose_succ(a, li, en, a.routes[rp + 2]);
+          nl = nlc;
         } else {
           nl = li.succ;
           u.rp = rp + 1;
@@ -503,7 +534,35 @@ __device__ __forceinline__ int count_bits(const unsigned *b, int s, int e) {
 // kernels
 // ------------------------------------------------------------------------------------
 
-__global__ void k_decide(StepArgs a) {
+// Per-lane window metrics over the snapshot (sum of speeds and count), deterministic:
+// a segmented sum over the warp (vehicles of a lane are consecutive), then the lane's
+// first vehicle adds the part of its lane that lies in later warps and stores the result
+// (one writer per lane, no atomics).
+__device__ __forceinline__ void lane_speed_sums(const StepArgs &a, const Soa &S, const int2 *dyn,
+                                                int n, int i, int w) {
+  const int wl = threadIdx.x & 31;
+  const bool act = i < n;
+  const int l = act ? S.lane[i] : -1 - wl;
+  float v = act ? S.v[i] : 0.f;
+  // segmented inclusive scan from the right: each thread gets the sum of its lane's
+  // vehicles from itself to the end of the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    float y = __shfl_down_sync(0xffffffffu, v, o);
+    int ly = __shfl_down_sync(0xffffffffu, l, o);
+    if (wl + o < 32 && ly == l) v += y;
+  }
+  if (!act) return;
+  const int2 d = dyn[l];
+  if (i != d.x) return;
+  const int warp_end = (i | 31) + 1;   // first index past this warp
+  for (int j = warp_end; j < d.x + d.y; ++j) v += S.v[j];
+  const size_t o = (size_t)w * a.P.n_lanes + l;
+  a.vsum[o] += v;
+  a.vcnt[o] += d.y;
+}
+
+__global__ void __launch_bounds__(512, 2) k_decide(StepArgs a) {
   const int t = a.ctrl->t;
   const int p = t & 1;
   const Soa S = a.A[p];
@@ -514,28 +573,19 @@ __global__ void k_decide(StepArgs a) {
   const int stride = gridDim.x * blockDim.x;
   for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
     const int i = base + threadIdx.x;
-    int leave = 0;
+    int leave = 0, moving = 0;
+    Upd u;
     if (i < n) {
-      Upd u = vehicle_update(a, S, dyn, i, t);
-      const int l = S.lane[i];
+      u = vehicle_update(a, S, dyn, i, t);
       leave = u.kind != U_STAY;
-      if (rec) {
-        int2 d = dyn[l];
-        if (i == d.x) {
-          float s = 0.f;
-          for (int j = d.x; j < d.x + d.y; ++j) s += S.v[j];
-          size_t o = (size_t)w * a.P.n_lanes + l;
-          a.vsum[o] += s;
-          a.vcnt[o] += d.y;
-        }
-      }
-      if (u.kind == U_CHANGE || u.kind == U_TRANSFER) {
-        int k = atomicAdd(&a.arr_cnt[u.lane], 1);
-        int slot = atomicAdd(&a.ctrl->n_movers, 1);
-        a.movers[slot] = Mover{i, u.lane, u.x, S.x[i], k, u.kind};
-        atomicMin(&a.amin[u.lane], fkey(u.x - a.P.L));
-        if (a.P.debug && u.flag) a.dbg.arr_flag[u.lane] = 1;
-      }
+      moving = u.kind == U_CHANGE || u.kind == U_TRANSFER;
+      int kind = u.kind == U_STAY ? C_STAY
+               : u.kind == U_CHANGE ? C_CHANGE
+               : u.kind == U_RETIRE ? C_RETIRE
+               : (u.rp != S.rp[i] ? C_TRANSFER_ROUTE : C_TRANSFER);
+      a.res_x[i] = u.x;
+      a.res_v[i] = u.v;
+      a.res_code[i] = (kind << CODE_LANE_BITS) | (u.kind == U_RETIRE ? 0 : u.lane);
       if (a.P.debug) {
         a.dbg.id[i] = S.id[i];
         a.dbg.lead_kind[i] = u.own.kind;
@@ -553,8 +603,19 @@ __global__ void k_decide(StepArgs a) {
         a.dbg.flag[i] = u.flag;
       }
     }
-    unsigned m = __ballot_sync(0xffffffffu, leave);
-    if ((threadIdx.x & 31) == 0) a.leave[(base + threadIdx.x) >> 5] = m;
+    const unsigned lm = __ballot_sync(0xffffffffu, leave);
+    if ((threadIdx.x & 31) == 0) a.leave[(base + threadIdx.x) >> 5] = lm;
+    if (rec) lane_speed_sums(a, S, dyn, n, i, w);
+    // arrivals: count per new lane and keep the rearmost arrival (no value returned, so
+    // nothing waits on these atomics; slots are handed out by k_bucket)
+    if (moving) {
+      atomicAdd(&a.arr_cnt[u.lane], 1);
+      atomicMin(&a.amin[u.lane], fkey(u.x - a.P.L));
+      // the arrival's cached next-lane choice for its new lane (internal -> edge lane keeps
+      // the choice it already made for that target lane)
+      if (u.rp == S.rp[i]) a.res_code_nl[i] = next_choice(a, u.lane, u.rp, u.nxt);
+      if (a.P.debug && u.flag) a.dbg.arr_flag[u.lane] = 1;
+    }
   }
 }
 
@@ -567,10 +628,17 @@ __device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long 
   return v;
 }
 
-// Lane pass: new per-lane counts, decoupled look-back scan, departures.
-__global__ void __launch_bounds__(SCAN_THREADS) k_lanes(StepArgs a) {
+// Lane pass: new per-lane counts, decoupled look-back scan, departures.  A tile of
+// SCAN_TILE lanes is processed by LANE_THREADS threads in LANE_ITEMS striped slices (lane
+// k * LANE_THREADS + thread), so every load is coalesced and the loads of all slices are
+// issued before any is used.
+constexpr int LANE_THREADS = 512;
+constexpr int LANE_ITEMS = SCAN_TILE / LANE_THREADS;
+constexpr int LANE_WARPS = LANE_THREADS / 32;
+
+__global__ void __launch_bounds__(LANE_THREADS) k_lanes(StepArgs a) {
   __shared__ int s_tile;
-  __shared__ unsigned long long s_warp[SCAN_THREADS / 32];
+  __shared__ unsigned long long s_wsum[LANE_ITEMS][LANE_WARPS];
   __shared__ unsigned long long s_excl;
   if (threadIdx.x == 0) s_tile = atomicAdd(&a.ctrl->tile_ticket, 1);
   __syncthreads();
@@ -581,153 +649,199 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_lanes(StepArgs a) {
   const Soa D = a.A[p ^ 1];
   const int2 *dyn = a.dyn[p];
   int2 *ndyn = a.dyn[p ^ 1];
-  const int nl = a.P.n_lanes;
+  const int nlanes = a.P.n_lanes;
   const float room_need = a.P.L + a.P.s0;
-  const int l0 = tile * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  const int lbase = tile * SCAN_TILE + threadIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  int cnt[SCAN_ITEMS], arr[SCAN_ITEMS], ins[SCAN_ITEMS];
-  unsigned long long run = 0;
+  int2 d[LANE_ITEMS];
+  int arr[LANE_ITEMS], amk[LANE_ITEMS], qh[LANE_ITEMS], qe[LANE_ITEMS];
 #pragma unroll
-  for (int k = 0; k < SCAN_ITEMS; ++k) {
-    const int l = l0 + k;
-    cnt[k] = arr[k] = ins[k] = 0;
-    if (l < nl) {
-      int2 d = dyn[l];
-      int leavers = count_bits(a.leave, d.x, d.x + d.y);
+  for (int k = 0; k < LANE_ITEMS; ++k) {
+    const int l = lbase + k * LANE_THREADS;
+    if (l < nlanes) {
+      d[k] = dyn[l];
       arr[k] = a.arr_cnt[l];
-      int qh = a.q_head[l];
-      if (qh < a.q_off[l + 1]) {
-        int trip = a.q_trip[qh];
-        if (a.trip_tdep[trip] <= t) {
-          int fl = 0;
-          bool room = true;
-          if (d.y > 0) {
-            float m = (S.x[d.x] - a.P.L) - room_need;
-            mark(fl, m);
-            room = m >= 0.f;
-          }
-          int ak = a.amin[l];
-          if (ak != AMIN_NONE) {
-            float m = unfkey(ak) - room_need;
-            mark(fl, m);
-            if (m < 0.f) room = false;
-          }
-          if (a.P.debug && (fl || a.dbg.arr_flag[l])) a.dbg.trip_flag[trip] = t + 1;
-          ins[k] = room ? 1 : 0;
-        }
-      }
-      cnt[k] = d.y - leavers + arr[k] + ins[k];
-      run += ((unsigned long long)cnt[k] << 32) | (unsigned)(arr[k] + ins[k]);
+      amk[k] = a.amin[l];
+      qh[k] = a.q_head[l];
+      qe[k] = a.q_off[l + 1];
+    } else {
+      d[k] = make_int2(0, 0);
+      arr[k] = 0;
+      amk[k] = AMIN_NONE;
+      qh[k] = qe[k] = 0;
     }
   }
-  // block-wide exclusive scan of the packed (count, arrivals) pairs
-  unsigned long long incl = warp_incl_scan(run);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 31) s_warp[warp] = incl;
+  int cnt[LANE_ITEMS], ins[LANE_ITEMS];
+  unsigned long long val[LANE_ITEMS], incl[LANE_ITEMS];
+#pragma unroll
+  for (int k = 0; k < LANE_ITEMS; ++k) {
+    const int leavers = count_bits(a.leave, d[k].x, d[k].x + d[k].y);
+    ins[k] = 0;
+    if (qh[k] < qe[k]) {
+      const int trip = a.q_trip[qh[k]];
+      if (a.trip_tdep[trip] <= t) {
+        int fl = 0;
+        bool room = true;
+        if (d[k].y > 0) {
+          float m = (S.x[d[k].x] - a.P.L) - room_need;
+          mark(fl, m);
+          room = m >= 0.f;
+        }
+        if (amk[k] != AMIN_NONE) {
+          float m = unfkey(amk[k]) - room_need;
+          mark(fl, m);
+          if (m < 0.f) room = false;
+        }
+        const int l = lbase + k * LANE_THREADS;
+        if (a.P.debug && (fl || a.dbg.arr_flag[l])) a.dbg.trip_flag[trip] = t + 1;
+        ins[k] = room ? 1 : 0;
+      }
+    }
+    cnt[k] = d[k].y - leavers + arr[k] + ins[k];
+    val[k] = ((unsigned long long)cnt[k] << 32) | (unsigned)(arr[k] + ins[k]);
+    incl[k] = warp_incl_scan(val[k]);
+    if (lane == 31) s_wsum[k][warp] = incl[k];
+  }
   __syncthreads();
   if (warp == 0) {
-    unsigned long long wv = lane < SCAN_THREADS / 32 ? s_warp[lane] : 0ull;
-    unsigned long long wi = warp_incl_scan(wv);
-    if (lane < SCAN_THREADS / 32) s_warp[lane] = wi - wv;   // exclusive warp offsets
-    if (lane == SCAN_THREADS / 32 - 1) {
-      // decoupled look-back for the tile prefix
-      const unsigned long long agg = wi;
-      cuda::atomic_ref<int, cuda::thread_scope_device> myflag(a.tile_flag[tile]);
-      unsigned long long excl = 0;
-      if (tile == 0) {
+    // exclusive offsets of every warp of every slice, in lane order
+    unsigned long long run = 0;
+#pragma unroll
+    for (int k = 0; k < LANE_ITEMS; ++k) {
+      const unsigned long long wv = lane < LANE_WARPS ? s_wsum[k][lane] : 0ull;
+      const unsigned long long wi = warp_incl_scan(wv);
+      if (lane < LANE_WARPS) s_wsum[k][lane] = run + wi - wv;
+      run += __shfl_sync(0xffffffffu, wi, LANE_WARPS - 1);
+    }
+    const unsigned long long agg = run;
+    // decoupled look-back, 32 predecessor tiles per probe
+    unsigned long long excl = 0;
+    if (tile == 0) {
+      if (lane == 0) {
         a.tile_pre[0] = agg;
-        myflag.store(2, cuda::memory_order_release);
-      } else {
+        cuda::atomic_ref<int, cuda::thread_scope_device>(a.tile_flag[0]).store(2, cuda::memory_order_release);
+      }
+    } else {
+      if (lane == 0) {
         a.tile_agg[tile] = agg;
-        myflag.store(1, cuda::memory_order_release);
-        int j = tile - 1, spins = 0;
-        while (j >= 0) {
-          cuda::atomic_ref<int, cuda::thread_scope_device> f(a.tile_flag[j]);
-          int fv = f.load(cuda::memory_order_acquire);
-          if (fv == 0) {
-            if (++spins > SPIN_LIMIT) {
-              atomicOr(&a.ctrl->err, DEV_SCAN);
-              break;
-            }
-            continue;
-          }
-          if (fv == 2) {
-            excl += a.tile_pre[j];
+        cuda::atomic_ref<int, cuda::thread_scope_device>(a.tile_flag[tile]).store(1, cuda::memory_order_release);
+      }
+      int j = tile - 1;
+      int spins = 0;
+      while (true) {
+        const int idx = j - lane;   // lane 0 probes the nearest predecessor
+        int fv;
+        while (true) {
+          fv = idx >= 0 ? cuda::atomic_ref<int, cuda::thread_scope_device>(a.tile_flag[idx]).load(cuda::memory_order_acquire)
+                        : 2;
+          if (__all_sync(0xffffffffu, fv != 0)) break;
+          if (++spins > SPIN_LIMIT) {
+            if (lane == 0) atomicOr(&a.ctrl->err, DEV_SCAN);
             break;
           }
-          excl += a.tile_agg[j];
-          --j;
         }
-        a.tile_pre[tile] = excl + agg;
-        myflag.store(2, cuda::memory_order_release);
+        const unsigned pm = __ballot_sync(0xffffffffu, fv == 2);
+        const int stop = pm ? __ffs(pm) - 1 : 32;
+        unsigned long long v = 0;
+        if (lane < stop) v = a.tile_agg[idx];
+        else if (lane == stop) v = idx >= 0 ? a.tile_pre[idx] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (pm || spins > SPIN_LIMIT) break;
+        j -= 32;
       }
-      s_excl = excl;
+      if (lane == 0) {
+        a.tile_pre[tile] = excl + agg;
+        cuda::atomic_ref<int, cuda::thread_scope_device>(a.tile_flag[tile]).store(2, cuda::memory_order_release);
+      }
     }
+    if (lane == 0) s_excl = excl;
   }
   __syncthreads();
-  unsigned long long pre = s_excl + s_warp[warp] + (incl - run);
+  const unsigned long long tile_excl = s_excl;
 #pragma unroll
-  for (int k = 0; k < SCAN_ITEMS; ++k) {
-    const int l = l0 + k;
-    if (l >= nl) break;
+  for (int k = 0; k < LANE_ITEMS; ++k) {
+    const int l = lbase + k * LANE_THREADS;
+    if (l >= nlanes) break;
+    const unsigned long long pre = tile_excl + s_wsum[k][warp] + (incl[k] - val[k]);
     const int nstart = (int)(pre >> 32);
     const int astart = (int)(pre & 0xffffffffu);
     ndyn[l] = make_int2(nstart, cnt[k]);
     a.arr_start[l] = astart;
     if (ins[k]) {
-      int qh = a.q_head[l];
-      int trip = a.q_trip[qh];
-      a.q_head[l] = qh + 1;
-      int r0 = a.trip_route0[trip];
+      const int trip = a.q_trip[qh[k]];
+      a.q_head[l] = qh[k] + 1;
+      const int r0 = a.trip_route0[trip];
+      const int e1 = a.routes[r0 + 1];
       D.x[nstart] = a.P.L;
       D.v[nstart] = 0.f;
       D.v0[nstart] = a.trip_v0[trip];
       D.lane[nstart] = l;
       D.rp[nstart] = r0;
-      D.nxt[nstart] = a.routes[r0 + 1];
+      D.nxt[nstart] = e1;
+      D.nl[nstart] = next_choice(a, l, r0, e1);
       D.id[nstart] = trip;
       a.bucket[astart + arr[k]] = make_int4(0, __float_as_int(a.P.L), trip, -1);
       atomicAdd(&a.ctrl->inserted, 1ull);
       if (a.P.debug) a.dbg.trip_ins[trip] = t + 1;
     }
-    a.arr_cnt[l] = 0;
-    a.amin[l] = AMIN_NONE;
+    if (arr[k]) a.arr_cnt[l] = 0;
+    if (amk[k] != AMIN_NONE) a.amin[l] = AMIN_NONE;
     if (a.P.debug) a.dbg.arr_flag[l] = 0;
-    pre += ((unsigned long long)cnt[k] << 32) | (unsigned)(arr[k] + ins[k]);
-    if (l == nl - 1) {
-      a.ctrl->n_active[p ^ 1] = (int)(pre >> 32);
-      a.arr_start[nl] = (int)(pre & 0xffffffffu);
+    if (l == nlanes - 1) {
+      const unsigned long long tot = pre + val[k];
+      a.ctrl->n_active[p ^ 1] = (int)(tot >> 32);
+      a.arr_start[nlanes] = (int)(tot & 0xffffffffu);
       a.ctrl->t_apply = t;
     }
   }
 }
 
-// Arrival records -> lane buckets with their rank among the lane's stayers.
+// Arrivals -> lane buckets with their rank among the lane's stayers.  Arrivals are found
+// by streaming the result codes of the snapshot's vehicles.
 __global__ void k_bucket(StepArgs a, int n_tiles) {
+  __shared__ int s_cnt;
   const int t = a.ctrl->t_apply;
   const int p = t & 1;
   const Soa S = a.A[p];
   const int2 *dyn = a.dyn[p];
-  const int nm = a.ctrl->n_movers;
+  const int n = a.ctrl->n_active[p];
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
-  for (int m = gid; m < nm; m += stride) {
-    Mover mv = a.movers[m];
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int i = gid; i < n; i += stride) {
+    const int code = a.res_code[i];
+    const int kind = (unsigned)code >> CODE_LANE_BITS;
+    if (kind != C_CHANGE && kind != C_TRANSFER && kind != C_TRANSFER_ROUTE) continue;
+    const int nl = code & CODE_LANE_MASK;
     int r = 0;
-    if (mv.kind == U_CHANGE) {
-      int2 d = dyn[mv.lane];
+    if (kind == C_CHANGE) {
+      const float xold = S.x[i];
+      int2 d = dyn[nl];
       int lo = d.x, hi = d.x + d.y;
       while (lo < hi) {   // first vehicle of the target lane not behind the changer
         int mid = (lo + hi) >> 1;
-        if (S.x[mid] < mv.xold) lo = mid + 1; else hi = mid;
+        if (S.x[mid] < xold) lo = mid + 1; else hi = mid;
       }
       r = (lo - d.x) - count_bits(a.leave, d.x, lo);
     }
-    a.bucket[a.arr_start[mv.lane] + mv.k] = make_int4(r, __float_as_int(mv.xnew), S.id[mv.i], mv.i);
+    const int slot = a.arr_start[nl] + atomicAdd(&a.arr_fill[nl], 1);
+    if (slot >= a.arr_start[nl + 1]) {   // never expected: more arrivals than counted
+      atomicOr(&a.ctrl->err, DEV_BUCKET);
+      continue;
+    }
+    a.bucket[slot] = make_int4(r, __float_as_int(a.res_x[i]), S.id[i], i);
+    ++mine;
   }
+  if (mine) atomicAdd(&s_cnt, mine);
   for (int k = gid; k < n_tiles; k += stride) a.tile_flag[k] = 0;
+  __syncthreads();
+  if (threadIdx.x == 0 && s_cnt) atomicAdd(&a.ctrl->n_movers, s_cnt);
   if (gid == 0) {
-    a.ctrl->movers_last = nm;
     a.ctrl->t = t + 1;
     a.ctrl->tile_ticket = 0;
   }
@@ -740,7 +854,9 @@ __device__ __forceinline__ bool bucket_less(int4 f, int4 e) {
   return f.z < e.z;
 }
 
-// Recompute the update and write each vehicle to its sorted slot of the t+1 buffer.
+// Write each vehicle, with the result k_decide computed for it, to its sorted slot of the
+// t+1 buffer: stayers by their rank among the lane's stayers plus the arrivals ranked
+// before them, arrivals by their bucket rank.
 __global__ void k_apply(StepArgs a) {
   const int t = a.ctrl->t_apply;
   const int p = t & 1;
@@ -751,27 +867,30 @@ __global__ void k_apply(StepArgs a) {
   const int n = a.ctrl->n_active[p];
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
-  if (gid == 0) a.ctrl->n_movers = 0;
+  if (gid == 0) {
+    a.ctrl->movers_last = a.ctrl->n_movers;
+    a.ctrl->n_movers = 0;
+  }
   for (int i = gid; i < n; i += stride) {
-    Upd u = vehicle_update(a, S, dyn, i, t);
+    const int code = a.res_code[i];
+    const int kind = (unsigned)code >> CODE_LANE_BITS;
+    const int nl = code & CODE_LANE_MASK;
     const int id = S.id[i];
-    if (u.kind == U_RETIRE) {
+    if (kind == C_RETIRE) {
       a.t_arr[id] = t + 1;
       atomicAdd(&a.ctrl->arrived, 1ull);
       atomicAdd(&a.ctrl->sum_tt, (unsigned long long)(t + 1 - a.trip_tdep[id]));
       continue;
     }
+    const int bs = a.arr_start[nl], be = a.arr_start[nl + 1];
     int pos;
-    if (u.kind == U_STAY) {
-      const int l = u.lane;
-      int2 d = dyn[l];
+    if (kind == C_STAY) {
+      int2 d = dyn[nl];
       int k = (i - d.x) - count_bits(a.leave, d.x, i);
-      int bs = a.arr_start[l], be = a.arr_start[l + 1];
       int m = 0;
       for (int q = bs; q < be; ++q) m += a.bucket[q].x <= k;
-      pos = ndyn[l].x + k + m;
+      pos = ndyn[nl].x + k + m;
     } else {
-      int bs = a.arr_start[u.lane], be = a.arr_start[u.lane + 1];
       int4 me = make_int4(0, 0, 0, -2);
       for (int q = bs; q < be; ++q) {
         int4 f = a.bucket[q];
@@ -783,14 +902,23 @@ __global__ void k_apply(StepArgs a) {
       }
       int rank = 0;
       for (int q = bs; q < be; ++q) rank += bucket_less(a.bucket[q], me);
-      pos = ndyn[u.lane].x + me.x + rank;
+      pos = ndyn[nl].x + me.x + rank;
     }
-    D.x[pos] = u.x;
-    D.v[pos] = u.v;
+    int rp = S.rp[i], nxt = S.nxt[i], nlc = S.nl[i];
+    if (kind != C_STAY) a.arr_fill[nl] = 0;   // every arrival resets it; k_bucket is done
+    if (kind == C_TRANSFER_ROUTE) {   // internal lane -> edge lane: next route edge; the
+      rp += 1;                        // cached choice was made for this target lane
+      nxt = a.routes[rp + 1];
+    } else if (kind != C_STAY) {      // lane change or edge lane -> internal lane
+      nlc = a.res_code_nl[i];
+    }
+    D.x[pos] = a.res_x[i];
+    D.v[pos] = a.res_v[i];
     D.v0[pos] = S.v0[i];
-    D.lane[pos] = u.lane;
-    D.rp[pos] = u.rp;
-    D.nxt[pos] = u.nxt;
+    D.lane[pos] = nl;
+    D.rp[pos] = rp;
+    D.nxt[pos] = nxt;
+    D.nl[pos] = nlc;
     D.id[pos] = id;
   }
 }

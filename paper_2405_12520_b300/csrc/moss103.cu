@@ -47,7 +47,7 @@ struct Sim {
   int4 *d_ctrl4 = nullptr;
   int *d_routes = nullptr;
   Soa A[2]{};
-  int2 *d_dyn[2]{};
+  int4 *d_dyn[2]{};
   DevCtrl *d_ctrl = nullptr;
   unsigned *d_leave = nullptr;
   int *d_arr_cnt = nullptr, *d_amin = nullptr, *d_arr_start = nullptr;
@@ -184,9 +184,16 @@ int host_choose(const Sim *s, int l, int en, int en2) {
 int host_next_choice(const Sim *s, int lane, int rp) {
   const int *R = s->h_routes.data();
   const int nxt = R[rp + 1];
-  if (s->lane_edge[lane] >= 0) return nxt >= 0 ? host_choose(s, lane, nxt, R[rp + 2]) : -1;
-  const int e2 = R[rp + 2];
-  return e2 >= 0 ? host_choose(s, s->succ_lane[s->succ_off[lane]], e2, R[rp + 3]) : -1;
+  int c;
+  if (s->lane_edge[lane] >= 0) {
+    if (nxt < 0) return NL_END;
+    c = host_choose(s, lane, nxt, R[rp + 2]);
+  } else {
+    const int e2 = R[rp + 2];
+    if (e2 < 0) return NL_END;
+    c = host_choose(s, s->succ_lane[s->succ_off[lane]], e2, R[rp + 3]);
+  }
+  return c >= 0 ? c : NL_NONE;
 }
 
 bool lane_links_to(const Sim *s, int l, int e) {
@@ -247,10 +254,15 @@ int upload_state(Sim *s, const std::vector<int> &ids, const std::vector<int> &la
     nlc[i] = host_next_choice(s, l, r0 + ri);
     cnt[l]++;
   }
-  std::vector<int2> dyn(s->n_lanes);
+  std::vector<int4> dyn(s->n_lanes);
   int acc = 0;
   for (int l = 0; l < s->n_lanes; ++l) {
-    dyn[l] = make_int2(acc, cnt[l]);
+    dyn[l] = make_int4(acc, cnt[l], 0, 0);
+    if (cnt[l]) {   // tail fields: the rearmost vehicle of the lane
+      float tx = xs[acc], tv = vs[acc];
+      std::memcpy(&dyn[l].z, &tx, 4);
+      std::memcpy(&dyn[l].w, &tv, 4);
+    }
     acc += cnt[l];
   }
   const int p = t & 1;
@@ -266,7 +278,7 @@ int upload_state(Sim *s, const std::vector<int> &ids, const std::vector<int> &la
     CK(cudaMemcpyAsync(B.nl, nlc.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(B.id, ids.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
   }
-  CK(cudaMemcpyAsync(s->d_dyn[p], dyn.data(), s->n_lanes * sizeof(int2), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(s->d_dyn[p], dyn.data(), s->n_lanes * sizeof(int4), cudaMemcpyHostToDevice, st));
   DevCtrl c{};
   CK(cudaMemcpyAsync(&c, s->d_ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));

@@ -65,7 +65,9 @@ struct DevParams {
 // Vehicle state, sorted by (lane, x).  rp: index into routes[] of the current edge (the
 // approach edge on an internal lane); nxt = routes[rp + 1]; nl: the lane the vehicle will
 // enter at the end of its current edge lane (for an internal lane: at the end of its
-// target lane), -1 if none -- cached so that sensing needs no route or link lookups.
+// target lane); NL_END (-1) if the route ends on that edge, NL_NONE (-2) if that lane has no
+// link toward the next route edge -- cached so that sensing needs no route or link lookups.
+constexpr int NL_END = -1, NL_NONE = -2;
 struct Soa {
   float *x, *v, *v0;
   int *lane, *rp, *nxt, *nl, *id;
@@ -102,7 +104,7 @@ struct StepArgs {
   const int4 *ctrl4;   // {offset, green, yellow, nphase}
   const int *routes;   // per trip: its edges then -1
   Soa A[2];
-  int2 *dyn[2];        // per lane {segment start, count} for buffer 0 / 1
+  int4 *dyn[2];        // per lane {first index, count, tail x, tail v} for buffer 0 / 1
   DevCtrl *ctrl;
   unsigned *leave;
   int *arr_cnt, *amin, *arr_start;
@@ -210,9 +212,16 @@ __device__ __forceinline__ int choose_succ(const StepArgs &a, const LaneInfo &li
 // The cached next-lane choice of a vehicle on `lane` with route index rp, next edge nxt.
 __device__ __forceinline__ int next_choice(const StepArgs &a, int lane, int rp, int nxt) {
   const LaneInfo li = a.li[lane];
-  if (li.edge >= 0) return nxt >= 0 ? choose_succ(a, li, nxt, a.routes[rp + 2]) : -1;
-  const int e2 = a.routes[rp + 2];   // edge after the target lane's edge
-  return e2 >= 0 ? choose_link(a, li.left, li.right, e2, a.routes[rp + 3]) : -1;
+  int c;
+  if (li.edge >= 0) {
+    if (nxt < 0) return NL_END;
+    c = choose_succ(a, li, nxt, a.routes[rp + 2]);
+  } else {
+    const int e2 = a.routes[rp + 2];   // edge after the target lane's edge
+    if (e2 < 0) return NL_END;
+    c = choose_link(a, li.left, li.right, e2, a.routes[rp + 3]);
+  }
+  return c >= 0 ? c : NL_NONE;
 }
 
 struct Lead {
@@ -237,16 +246,19 @@ struct Upd {
   int flag;
 };
 
-__device__ __forceinline__ Lead own_leader(const StepArgs &a, const Soa &S, const int2 *dyn, int i,
-                                           int l, const LaneInfo &li, float x, float v, int rp,
-                                           int en, int nlc, int myid, int t, int &flag) {
+// Lane records per step: {first index, count, tail x bits, tail v bits}; the tail fields
+// (rearmost vehicle of the lane) are valid when count > 0.
+__device__ __forceinline__ Lead own_leader(const StepArgs &a, const Soa &S, const int4 *dyn, int i,
+                                           int l, const LaneInfo &li, int4 d, float x, float v,
+                                           int rp, int en, int nlc, int4 pf_dyn, const LaneInfo &pf_li,
+                                           int myid, int t, int &flag) {
   const DevParams &P = a.P;
   Lead r{K_FREE, 0.f, 0.f, -1, 0};
-  int2 d = dyn[l];
   if (i + 1 < d.x + d.y) {
     int j = i + 1;
     r = Lead{K_VEH, (S.x[j] - x) - P.L, S.v[j], j, 0};
   } else {
+    constexpr int E_LAZY = -3;    // next route edge not read yet
     float dist = li.len - x;
     int ri = rp, e_next = en;
     bool cached = true;   // the first edge-lane hop uses the vehicle's cached choice
@@ -255,10 +267,18 @@ __device__ __forceinline__ Lead own_leader(const StepArgs &a, const Soa &S, cons
       mark(flag, dist - P.d_look);
       if (dist >= P.d_look) break;
       int nxt;
+      bool pre = false;
       if (lc.edge >= 0) {
-        if (e_next < 0) break;   // destination edge: open end
-        nxt = cached ? nlc : choose_succ(a, lc, e_next, a.routes[ri + 2]);
-        cached = false;
+        if (cached) {
+          cached = false;
+          if (nlc == NL_END) break;   // destination edge: open end
+          nxt = nlc;
+          pre = nxt >= 0;
+        } else {
+          if (e_next == E_LAZY) e_next = a.routes[ri + 1];
+          if (e_next < 0) break;   // destination edge: open end
+          nxt = choose_succ(a, lc, e_next, a.routes[ri + 2]);
+        }
         bool stop = nxt < 0;
         if (!stop) {
           int sg = sig_state(a, lc, t);
@@ -277,19 +297,18 @@ __device__ __forceinline__ Lead own_leader(const StepArgs &a, const Soa &S, cons
       } else {
         nxt = lc.succ;
         ri += 1;
-        e_next = a.routes[ri + 1];
+        e_next = E_LAZY;
       }
       if (hop + 1 >= HOP_CAP) {
         r = Lead{K_OBST, dist, 0.f, -1, hop == 0};
         break;
       }
-      int2 dn = dyn[nxt];
+      const int4 dn = pre ? pf_dyn : dyn[nxt];
       if (dn.y > 0) {
-        int j = dn.x;
-        r = Lead{K_VEH, (dist + S.x[j]) - P.L, S.v[j], j, 0};
+        r = Lead{K_VEH, (dist + __int_as_float(dn.z)) - P.L, __int_as_float(dn.w), dn.x, 0};
         break;
       }
-      lc = a.li[nxt];
+      lc = pre ? pf_li : a.li[nxt];
       dist += lc.len;
     }
   }
@@ -301,7 +320,7 @@ __device__ __forceinline__ Lead own_leader(const StepArgs &a, const Soa &S, cons
       for (int q = 0; q < lt.n_pred; ++q) {
         int f = a.pred[lt.pred + q];
         if (f == l) continue;
-        int2 df = dyn[f];
+        int4 df = dyn[f];
         float lf = a.li[f].len;
         int found = -1;
         for (int jj = 0; jj < df.y; ++jj) {
@@ -340,10 +359,10 @@ __device__ __forceinline__ bool end_blocks(const StepArgs &a, const LaneInfo &lt
   return false;
 }
 
-__device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const int2 *dyn, int i,
+__device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const int4 *dyn, int i,
                                           int l, const LaneInfo &li, float x, float v, float v0,
-                                          int en, int nlc, int myid, int t, const Lead &own, float a_c,
-                                          int &flag) {
+                                          int en, int nlc, int4 dl, int myid, int t, const Lead &own,
+                                          float a_c, int &flag) {
   const DevParams &P = a.P;
   LC r{};
   r.tl = r.tf = r.of = -1;
@@ -351,7 +370,7 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
   int step_dir = (t % 2 == 0) ? 1 : -1;
   int tau = step_dir > 0 ? li.left : li.right;
   if (tau < 0) return r;
-  const bool mand = en >= 0 && nlc < 0;   // own lane has no link toward the next edge
+  const bool mand = nlc == NL_NONE;   // own lane has no link toward the next edge
   if (mand) {
     int dr = 1 << 30, dl = 1 << 30, k = 1;
     for (int q = li.right; q >= 0; q = a.li[q].right, ++k)
@@ -375,7 +394,7 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
     if ((uint32_t)(h >> 40) >= P.lc_thresh) return r;
   }
   r.cand = 1;
-  int2 dt = dyn[tau];
+  int4 dt = dyn[tau];
   int lo = dt.x, hi = dt.x + dt.y;
   while (lo < hi) {
     int mid = (lo + hi) >> 1;
@@ -426,8 +445,7 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
         aF_old = idm(P, vF, v0F, false, 0.f, 0.f);
       delta += P.p * (aF_new - aF_old);
     }
-    int2 d = dyn[l];
-    if (i > d.x) {
+    if (i > dl.x) {
       int O = i - 1;
       r.of = O;
       float xO = S.x[O], vO = S.v[O], v0O = S.v0[O];
@@ -445,7 +463,7 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
 }
 
 // The update of vehicle i (snapshot index) at step t.  Pure function of the snapshot.
-__device__ __forceinline__ Upd vehicle_update(const StepArgs &a, const Soa &S, const int2 *dyn, int i,
+__device__ __forceinline__ Upd vehicle_update(const StepArgs &a, const Soa &S, const int4 *dyn, int i,
                                               int t) {
   const DevParams &P = a.P;
   Upd u;
@@ -454,9 +472,17 @@ __device__ __forceinline__ Upd vehicle_update(const StepArgs &a, const Soa &S, c
   const float x = S.x[i], v = S.v[i], v0 = S.v0[i];
   const int rp = S.rp[i], en = S.nxt[i], nlc = S.nl[i], myid = S.id[i];
   const LaneInfo li = a.li[l];
-  u.own = own_leader(a, S, dyn, i, l, li, x, v, rp, en, nlc, myid, t, u.flag);
+  const int4 dl = dyn[l];
+  // the cached next lane's records, loaded together with the own lane's
+  int4 pf_dyn = make_int4(0, 0, 0, 0);
+  LaneInfo pf_li{};
+  if (nlc >= 0) {
+    pf_dyn = dyn[nlc];
+    pf_li = a.li[nlc];
+  }
+  u.own = own_leader(a, S, dyn, i, l, li, dl, x, v, rp, en, nlc, pf_dyn, pf_li, myid, t, u.flag);
   u.a_own = idm(P, v, v0, u.own.kind != K_FREE, u.own.gap, u.own.vl);
-  u.lc = lane_change(a, S, dyn, i, l, li, x, v, v0, en, nlc, myid, t, u.own, u.a_own, u.flag);
+  u.lc = lane_change(a, S, dyn, i, l, li, x, v, v0, en, nlc, dl, myid, t, u.own, u.a_own, u.flag);
   const int dir = u.lc.dir;
   u.a_use = dir ? fminf(u.a_own, u.lc.anew) : u.a_own;
   float vraw = v + u.a_use * P.dt;
@@ -536,9 +562,9 @@ __device__ __forceinline__ int count_bits(const unsigned *b, int s, int e) {
 
 // Per-lane window metrics over the snapshot (sum of speeds and count), deterministic:
 // a segmented sum over the warp (vehicles of a lane are consecutive), then the lane's
-// first vehicle adds the part of its lane that lies in later warps and stores the result
-// (one writer per lane, no atomics).
-__device__ __forceinline__ void lane_speed_sums(const StepArgs &a, const Soa &S, const int2 *dyn,
+// first vehicle adds the part of its lane that lies in later warps and adds the result to
+// the window accumulators (one writer per lane and step).
+__device__ __forceinline__ void lane_speed_sums(const StepArgs &a, const Soa &S, const int4 *dyn,
                                                 int n, int i, int w) {
   const int wl = threadIdx.x & 31;
   const bool act = i < n;
@@ -553,20 +579,21 @@ __device__ __forceinline__ void lane_speed_sums(const StepArgs &a, const Soa &S,
     if (wl + o < 32 && ly == l) v += y;
   }
   if (!act) return;
-  const int2 d = dyn[l];
+  const int4 d = dyn[l];
   if (i != d.x) return;
   const int warp_end = (i | 31) + 1;   // first index past this warp
   for (int j = warp_end; j < d.x + d.y; ++j) v += S.v[j];
+  // one writer per lane and step, so the sums stay deterministic; nothing waits on these
   const size_t o = (size_t)w * a.P.n_lanes + l;
-  a.vsum[o] += v;
-  a.vcnt[o] += d.y;
+  atomicAdd(&a.vsum[o], v);
+  atomicAdd(&a.vcnt[o], d.y);
 }
 
 __global__ void __launch_bounds__(512, 2) k_decide(StepArgs a) {
   const int t = a.ctrl->t;
   const int p = t & 1;
   const Soa S = a.A[p];
-  const int2 *dyn = a.dyn[p];
+  const int4 *dyn = a.dyn[p];
   const int n = a.ctrl->n_active[p];
   const int w = t / a.P.window;
   const bool rec = a.vsum != nullptr && w < a.P.n_windows;
@@ -647,14 +674,14 @@ __global__ void __launch_bounds__(LANE_THREADS) k_lanes(StepArgs a) {
   const int p = t & 1;
   const Soa S = a.A[p];
   const Soa D = a.A[p ^ 1];
-  const int2 *dyn = a.dyn[p];
-  int2 *ndyn = a.dyn[p ^ 1];
+  const int4 *dyn = a.dyn[p];
+  int4 *ndyn = a.dyn[p ^ 1];
   const int nlanes = a.P.n_lanes;
   const float room_need = a.P.L + a.P.s0;
   const int lbase = tile * SCAN_TILE + threadIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  int2 d[LANE_ITEMS];
+  int4 d[LANE_ITEMS];
   int arr[LANE_ITEMS], amk[LANE_ITEMS], qh[LANE_ITEMS], qe[LANE_ITEMS];
 #pragma unroll
   for (int k = 0; k < LANE_ITEMS; ++k) {
@@ -666,7 +693,7 @@ __global__ void __launch_bounds__(LANE_THREADS) k_lanes(StepArgs a) {
       qh[k] = a.q_head[l];
       qe[k] = a.q_off[l + 1];
     } else {
-      d[k] = make_int2(0, 0);
+      d[k] = make_int4(0, 0, 0, 0);
       arr[k] = 0;
       amk[k] = AMIN_NONE;
       qh[k] = qe[k] = 0;
@@ -768,7 +795,8 @@ __global__ void __launch_bounds__(LANE_THREADS) k_lanes(StepArgs a) {
     const unsigned long long pre = tile_excl + s_wsum[k][warp] + (incl[k] - val[k]);
     const int nstart = (int)(pre >> 32);
     const int astart = (int)(pre & 0xffffffffu);
-    ndyn[l] = make_int2(nstart, cnt[k]);
+    // tail fields: the departing vehicle if one enters, else set by k_apply
+    ndyn[l] = make_int4(nstart, cnt[k], ins[k] ? __float_as_int(a.P.L) : 0, 0);
     a.arr_start[l] = astart;
     if (ins[k]) {
       const int trip = a.q_trip[qh[k]];
@@ -806,7 +834,7 @@ __global__ void k_bucket(StepArgs a, int n_tiles) {
   const int t = a.ctrl->t_apply;
   const int p = t & 1;
   const Soa S = a.A[p];
-  const int2 *dyn = a.dyn[p];
+  const int4 *dyn = a.dyn[p];
   const int n = a.ctrl->n_active[p];
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
@@ -821,7 +849,7 @@ __global__ void k_bucket(StepArgs a, int n_tiles) {
     int r = 0;
     if (kind == C_CHANGE) {
       const float xold = S.x[i];
-      int2 d = dyn[nl];
+      int4 d = dyn[nl];
       int lo = d.x, hi = d.x + d.y;
       while (lo < hi) {   // first vehicle of the target lane not behind the changer
         int mid = (lo + hi) >> 1;
@@ -862,8 +890,8 @@ __global__ void k_apply(StepArgs a) {
   const int p = t & 1;
   const Soa S = a.A[p];
   const Soa D = a.A[p ^ 1];
-  const int2 *dyn = a.dyn[p];
-  const int2 *ndyn = a.dyn[p ^ 1];
+  const int4 *dyn = a.dyn[p];
+  int4 *ndyn = a.dyn[p ^ 1];
   const int n = a.ctrl->n_active[p];
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
@@ -885,7 +913,7 @@ __global__ void k_apply(StepArgs a) {
     const int bs = a.arr_start[nl], be = a.arr_start[nl + 1];
     int pos;
     if (kind == C_STAY) {
-      int2 d = dyn[nl];
+      int4 d = dyn[nl];
       int k = (i - d.x) - count_bits(a.leave, d.x, i);
       int m = 0;
       for (int q = bs; q < be; ++q) m += a.bucket[q].x <= k;
@@ -912,8 +940,11 @@ __global__ void k_apply(StepArgs a) {
     } else if (kind != C_STAY) {      // lane change or edge lane -> internal lane
       nlc = a.res_code_nl[i];
     }
-    D.x[pos] = a.res_x[i];
-    D.v[pos] = a.res_v[i];
+    const float xn = a.res_x[i], vn = a.res_v[i];
+    if (pos == ndyn[nl].x)   // rearmost vehicle of its lane: the lane record's tail fields
+      reinterpret_cast<int2 *>(&ndyn[nl])[1] = make_int2(__float_as_int(xn), __float_as_int(vn));
+    D.x[pos] = xn;
+    D.v[pos] = vn;
     D.v0[pos] = S.v0[i];
     D.lane[pos] = nl;
     D.rp[pos] = rp;

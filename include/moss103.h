@@ -14,8 +14,8 @@
  *    one-line message.  A failed call leaves the simulation unchanged unless noted.
  *  - host arrays passed in are read during the call only and copied; the library owns all
  *    device memory it allocates (cudaMalloc at load time, freed by ms_destroy).
- *  - lane ids: edge lanes first (lanes of edge e are edge_lane0[e] + idx, idx 0 rightmost),
- *    then junction-internal lanes.  Positions x are the front bumper along the lane from
+ *  - lane ids: the lanes of edge e are edge_lane0[e] + idx (idx 0 rightmost); junction-
+ *    internal lanes have lane_edge -1.  Positions x are the front bumper along the lane from
  *    its start, metres; speeds m/s; FP32.
  *  - not thread-safe per ms_sim; distinct ms_sim objects are independent.
  */
@@ -65,6 +65,8 @@ typedef struct ms_params {
   uint64_t seed;   /* seed of the counter-based lane-change gate */
   int debug;       /* 1: record per-vehicle sensing and decisions of each step (tests) */
   int block;       /* threads per block of the vehicle kernels, multiple of 32 (0: 256) */
+  int id_base;     /* added to trip ids in the lane-change gate hash (0; a stand-alone run of
+                      one scenario of a batch sets it to the scenario's first trip id) */
 } ms_params;
 
 /* Lane-level road network (Sec. III-C "Map Builder": lanes with topology, junction lanes,
@@ -203,6 +205,27 @@ int ms_read_metrics(void *sim, ms_metrics *out);
 
 /* Debug record of the last step (requires params.debug = 1, else MS_ERR_STATE). */
 int ms_read_debug(void *sim, ms_debug *out);
+
+/* Batched scenarios: n independent networks and their trips simulated as one disjoint
+   union in a single step launch sequence (many scenarios of uneven size for signal or
+   policy sweeps).  Scenario k's lanes, edges, controllers and trips get ids offset by the
+   totals of scenarios 0..k-1; otherwise identical to ms_load_network / ms_add_vehicles
+   (same validation, same error codes naming the scenario).  Call instead of, not in
+   addition to, the single-scenario loaders.  The paper simulates one scenario at a time;
+   batching is this library's addition. */
+int ms_load_network_batch(void *sim, int n, const ms_network *nets);
+int ms_add_vehicles_batch(void *sim, int n, const ms_vehicles *vehs);
+/* Offsets of each batched scenario: lane_off[n+1], trip_off[n+1] (caller-owned host
+   arrays); MS_ERR_STATE if the simulation was not loaded as a batch. */
+int ms_batch_offsets(void *sim, int *lane_off, int *trip_off);
+
+/* Autotuner of the step's launch shapes: for each candidate (threads per block of the
+   vehicle kernels, persistent-grid oversubscription) it times trial_steps steps with CUDA
+   events, restoring the dynamic state after each trial, and keeps the fastest; the
+   simulation's results are unchanged.  best_ms receives the best mean step time (ms),
+   config (3 ints, may be NULL) the chosen block size, grid factor of k_decide and of
+   k_apply.  Allocates temporary device memory for the state snapshot. */
+int ms_autotune(void *sim, int trial_steps, float *best_ms, int *config);
 
 const char *ms_last_error(void *sim);
 void ms_destroy(void *sim);

@@ -23,6 +23,13 @@ namespace {
 
 constexpr int GRAPH_STEPS = 16;
 
+// launch shape of the vehicle kernels (chosen by ms_autotune; defaults from occupancy)
+struct LaunchCfg {
+  int blk_decide = 256, grid_decide = 1;
+  int blk_apply = 256, grid_apply = 1;
+  int blk_bucket = 256, grid_bucket = 1;
+};
+
 struct Sim {
   ms_params prm{};
   DevParams P{};
@@ -63,7 +70,9 @@ struct Sim {
   int *d_vcnt = nullptr;
   DebugOut dbg{};
   int n_tiles = 0;
-  int grid_veh = 0, grid_apply = 0, grid_bucket = 0;
+  LaunchCfg cfg{};
+  // batches of independent scenarios: offsets of each scenario's lanes and trips
+  std::vector<int> batch_lane_off, batch_trip_off;
   cudaGraphExec_t g_many = nullptr, g_one = nullptr;
   std::vector<void *> allocs;
 };
@@ -135,16 +144,44 @@ StepArgs make_args(Sim *s) {
   return a;
 }
 
-// one step = four launches (+ the debug order check)
-cudaError_t enqueue_step(Sim *s, cudaStream_t st) {
-  StepArgs a = make_args(s);
-  const int blk = s->prm.block;
-  k_decide<<<s->grid_veh, blk, 0, st>>>(a);
+// one step = four launches (+ the debug order check); ev (5 events) brackets each kernel
+cudaError_t launch_step(const Sim *s, const StepArgs &a, cudaStream_t st, cudaEvent_t *ev) {
+  const LaunchCfg &c = s->cfg;
+  if (ev) cudaEventRecord(ev[0], st);
+  k_decide<<<c.grid_decide, c.blk_decide, 0, st>>>(a);
+  if (ev) cudaEventRecord(ev[1], st);
   k_lanes<<<s->n_tiles, LANE_THREADS, 0, st>>>(a);
-  k_bucket<<<s->grid_bucket, 256, 0, st>>>(a, s->n_tiles);
-  k_apply<<<s->grid_apply, blk, 0, st>>>(a);
-  if (s->prm.debug) k_check<<<s->grid_bucket, 256, 0, st>>>(a);
+  if (ev) cudaEventRecord(ev[2], st);
+  k_bucket<<<c.grid_bucket, c.blk_bucket, 0, st>>>(a, s->n_tiles);
+  if (ev) cudaEventRecord(ev[3], st);
+  k_apply<<<c.grid_apply, c.blk_apply, 0, st>>>(a);
+  if (ev) cudaEventRecord(ev[4], st);
+  if (s->prm.debug) k_check<<<c.grid_bucket, c.blk_bucket, 0, st>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t enqueue_step(Sim *s, cudaStream_t st) { return launch_step(s, make_args(s), st, nullptr); }
+
+// persistent grids: blocks = factor * (resident blocks per SM) * SMs, capped by the work
+int shape_grids(Sim *s, LaunchCfg &c, int f_decide, int f_apply, int f_bucket) {
+  const int N = s->n_trips;
+  int od = 0, oa = 0, ob = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&od, k_decide, c.blk_decide, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oa, k_apply, c.blk_apply, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, k_bucket, c.blk_bucket, 0));
+  auto g = [&](int blk, int occ, int f) {
+    return std::max(1, std::min((N + blk - 1) / blk, f * std::max(1, occ) * s->n_sm));
+  };
+  c.grid_decide = g(c.blk_decide, od, f_decide);
+  c.grid_apply = g(c.blk_apply, oa, f_apply);
+  c.grid_bucket = g(c.blk_bucket, ob, f_bucket);
+  return MS_OK;
+}
+
+void drop_graphs(Sim *s) {
+  if (s->g_many) cudaGraphExecDestroy(s->g_many);
+  if (s->g_one) cudaGraphExecDestroy(s->g_one);
+  s->g_many = s->g_one = nullptr;
 }
 
 int build_graphs(Sim *s) {
@@ -324,6 +361,7 @@ int ms_create(void **out, const ms_params *p, void *cuda_stream) {
   P.window = p->window;
   P.n_windows = p->n_windows;
   P.debug = p->debug;
+  P.id_base = p->id_base;
   s->stream = (cudaStream_t)cuda_stream;
   cudaError_t e = cudaGetDevice(&s->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, s->device);
@@ -597,13 +635,12 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
   CK(cudaMemcpy(s->d_v0, s->h_v0.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->d_routes, s->h_routes.data(), sizeof(int) * s->h_routes.size(), cudaMemcpyHostToDevice));
   // launch shapes: persistent grids sized by occupancy
-  int occ = 0, occ2 = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_decide, s->prm.block, 0));
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_apply, s->prm.block, 0));
-  int need = (N + s->prm.block - 1) / s->prm.block;
-  s->grid_veh = std::max(1, std::min(need, std::max(1, occ) * s->n_sm));
-  s->grid_apply = std::max(1, std::min(need, std::max(1, occ2) * s->n_sm));
-  s->grid_bucket = std::max(1, std::min((N + 255) / 256, 8 * s->n_sm));
+  s->cfg.blk_decide = s->cfg.blk_apply = s->prm.block;
+  s->cfg.blk_bucket = 256;
+  {
+    int r0 = shape_grids(s, s->cfg, 1, 1, 1);
+    if (r0) return r0;
+  }
   s->veh_loaded = true;
   // initial state
   std::vector<int> ids, lanes, ridx;
@@ -646,19 +683,8 @@ int ms_step_timed(void *sim, int n, float *ms_per_kernel) {
   for (auto &e : ev) CK(cudaEventCreate(&e));
   cudaStream_t st = s->stream;
   StepArgs a = make_args(s);
-  const int blk = s->prm.block;
   for (int k = 0; k < n; ++k) {
-    CK(cudaEventRecord(ev[0], st));
-    k_decide<<<s->grid_veh, blk, 0, st>>>(a);
-    CK(cudaEventRecord(ev[1], st));
-    k_lanes<<<s->n_tiles, LANE_THREADS, 0, st>>>(a);
-    CK(cudaEventRecord(ev[2], st));
-    k_bucket<<<s->grid_bucket, 256, 0, st>>>(a, s->n_tiles);
-    CK(cudaEventRecord(ev[3], st));
-    k_apply<<<s->grid_apply, blk, 0, st>>>(a);
-    CK(cudaEventRecord(ev[4], st));
-    if (s->prm.debug) k_check<<<s->grid_bucket, 256, 0, st>>>(a);
-    CK(cudaGetLastError());
+    CK(launch_step(s, a, st, ev));
     CK(cudaEventSynchronize(ev[4]));
     for (int q = 0; q < 4; ++q) {
       float ms = 0.f;
@@ -701,15 +727,7 @@ int ms_step_noalloc(void *sim, int n) {
   cudaStream_t st = s->stream;
   // the array keeps whatever the last call left: flags must start at zero
   CK(cudaMemsetAsync(a.tile_flag, 0, sizeof(int) * MS_NOALLOC_MAX_TILES, st));
-  const int blk = s->prm.block;
-  for (int k = 0; k < n; ++k) {
-    k_decide<<<s->grid_veh, blk, 0, st>>>(a);
-    k_lanes<<<s->n_tiles, LANE_THREADS, 0, st>>>(a);
-    k_bucket<<<s->grid_bucket, 256, 0, st>>>(a, s->n_tiles);
-    k_apply<<<s->grid_apply, blk, 0, st>>>(a);
-    if (s->prm.debug) k_check<<<s->grid_bucket, 256, 0, st>>>(a);
-    CK(cudaGetLastError());
-  }
+  for (int k = 0; k < n; ++k) CK(launch_step(s, a, st, nullptr));
   return MS_OK;
 }
 
@@ -869,6 +887,245 @@ int ms_read_debug(void *sim, ms_debug *out) {
   return MS_OK;
 }
 
+// ---------------------------------------------------------------------------------
+// batches of independent scenarios
+// ---------------------------------------------------------------------------------
+
+int ms_load_network_batch(void *sim, int n, const ms_network *nets) {
+  Sim *s = (Sim *)sim;
+  if (!s || !nets || n <= 0) return MS_ERR_ARG;
+  if (s->net_loaded) return fail(s, MS_ERR_STATE, "network already loaded");
+  int L = 0, E = 0, C = 0, S = 0;
+  for (int k = 0; k < n; ++k) {
+    const ms_network &q = nets[k];
+    if (q.n_lanes <= 0 || q.n_edges <= 0 || q.n_ctrl < 0 || !q.succ_off)
+      return fail(s, MS_ERR_ARG, "scenario " + std::to_string(k) + ": empty or missing network");
+    L += q.n_lanes;
+    E += q.n_edges;
+    C += q.n_ctrl;
+    S += q.succ_off[q.n_lanes];
+  }
+  std::vector<float> len(L);
+  std::vector<int> edge(L), idx(L), left(L), right(L), soff(L + 1), sl(std::max(1, S)), se(std::max(1, S)),
+      lctrl(L), lgrp(L), coff(std::max(1, C)), cg(std::max(1, C)), cy(std::max(1, C)), cp(std::max(1, C)),
+      enl(E), el0(E);
+  s->batch_lane_off.assign(1, 0);
+  int lo = 0, eo = 0, co = 0, so = 0;
+  auto shift = [](int v, int o) { return v >= 0 ? v + o : v; };
+  for (int k = 0; k < n; ++k) {
+    const ms_network &q = nets[k];
+    for (int l = 0; l < q.n_lanes; ++l) {
+      len[lo + l] = q.lane_len[l];
+      edge[lo + l] = shift(q.lane_edge[l], eo);
+      idx[lo + l] = q.lane_index[l];
+      left[lo + l] = shift(q.lane_left[l], lo);
+      right[lo + l] = shift(q.lane_right[l], lo);
+      soff[lo + l] = q.succ_off[l] + so;
+      lctrl[lo + l] = shift(q.lane_ctrl[l], co);
+      lgrp[lo + l] = q.lane_group[l];
+    }
+    const int qs = q.succ_off[q.n_lanes];
+    for (int j = 0; j < qs; ++j) {
+      sl[so + j] = q.succ_lane[j] + lo;
+      se[so + j] = q.succ_edge[j] + eo;
+    }
+    for (int c = 0; c < q.n_ctrl; ++c) {
+      coff[co + c] = q.ctrl_offset[c];
+      cg[co + c] = q.ctrl_green[c];
+      cy[co + c] = q.ctrl_yellow[c];
+      cp[co + c] = q.ctrl_nphase[c];
+    }
+    for (int e = 0; e < q.n_edges; ++e) {
+      enl[eo + e] = q.edge_nlanes[e];
+      el0[eo + e] = q.edge_lane0[e] + lo;
+    }
+    lo += q.n_lanes;
+    eo += q.n_edges;
+    co += q.n_ctrl;
+    so += qs;
+    s->batch_lane_off.push_back(lo);
+  }
+  soff[L] = so;
+  ms_network u{L, E, C, len.data(), edge.data(), idx.data(), left.data(), right.data(), soff.data(), sl.data(),
+               se.data(), lctrl.data(), lgrp.data(), coff.data(), cg.data(), cy.data(), cp.data(), enl.data(),
+               el0.data()};
+  int r = ms_load_network(sim, &u);
+  if (r) s->batch_lane_off.clear();
+  return r;
+}
+
+int ms_add_vehicles_batch(void *sim, int n, const ms_vehicles *vehs) {
+  Sim *s = (Sim *)sim;
+  if (!s || !vehs || n <= 0) return MS_ERR_ARG;
+  if ((int)s->batch_lane_off.size() != n + 1) return fail(s, MS_ERR_STATE, "load the batch's networks first (same n)");
+  // edge offsets of the scenarios, from the union's edge -> lane table
+  std::vector<int> edge_off(n + 1, 0);
+  {
+    int k = 0;
+    for (int e = 0; e < s->n_edges; ++e) {
+      while (k < n && s->edge_lane0[e] >= s->batch_lane_off[k + 1]) edge_off[++k] = e;
+    }
+    for (int q = k + 1; q <= n; ++q) edge_off[q] = s->n_edges;
+  }
+  int T = 0;
+  int64_t R = 0;
+  bool any_place = false;
+  for (int k = 0; k < n; ++k) {
+    if (vehs[k].n < 0 || (vehs[k].n > 0 && (!vehs[k].route_off || !vehs[k].route_edges || !vehs[k].t_dep || !vehs[k].v0)))
+      return fail(s, MS_ERR_ARG, "scenario " + std::to_string(k) + ": vehicle arrays missing");
+    T += vehs[k].n;
+    if (vehs[k].n) R += vehs[k].route_off[vehs[k].n];
+    any_place |= vehs[k].lane != nullptr;
+  }
+  std::vector<int> tdep(T), rte((size_t)std::max<int64_t>(1, R)), lane(T, -1);
+  std::vector<float> v0(T), x(T, 0.f), v(T, 0.f);
+  std::vector<int64_t> roff(T + 1, 0);
+  s->batch_trip_off.assign(1, 0);
+  int to = 0;
+  int64_t ro = 0;
+  for (int k = 0; k < n; ++k) {
+    const ms_vehicles &q = vehs[k];
+    const int lo = s->batch_lane_off[k], eo = edge_off[k];
+    const int ne = edge_off[k + 1] - eo;
+    for (int i = 0; i < q.n; ++i) {
+      tdep[to + i] = q.t_dep[i];
+      v0[to + i] = q.v0[i];
+      roff[to + i] = ro + q.route_off[i];
+      if (q.lane && q.lane[i] >= 0) {
+        lane[to + i] = q.lane[i] + lo;
+        x[to + i] = q.x[i];
+        v[to + i] = q.v[i];
+      }
+    }
+    const int64_t qr = q.n ? q.route_off[q.n] : 0;
+    for (int64_t j = 0; j < qr; ++j) {
+      const int e = q.route_edges[j];
+      if (e < 0 || e >= ne) return fail(s, MS_ERR_ARG, "scenario " + std::to_string(k) + ": route edge out of range");
+      rte[ro + j] = e + eo;
+    }
+    to += q.n;
+    ro += qr;
+    s->batch_trip_off.push_back(to);
+  }
+  roff[T] = ro;
+  ms_vehicles u{T, tdep.data(), v0.data(), roff.data(), rte.data(), any_place ? lane.data() : nullptr,
+                any_place ? x.data() : nullptr, any_place ? v.data() : nullptr};
+  int r = ms_add_vehicles(sim, &u);
+  if (r) s->batch_trip_off.clear();
+  return r;
+}
+
+int ms_batch_offsets(void *sim, int *lane_off, int *trip_off) {
+  Sim *s = (Sim *)sim;
+  if (!s) return MS_ERR_ARG;
+  if (s->batch_lane_off.empty()) return fail(s, MS_ERR_STATE, "not a batch");
+  if (lane_off) std::copy(s->batch_lane_off.begin(), s->batch_lane_off.end(), lane_off);
+  if (trip_off) std::copy(s->batch_trip_off.begin(), s->batch_trip_off.end(), trip_off);
+  return MS_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------------
+
+namespace {
+// device-to-device snapshot of everything a step reads or writes
+struct Snapshot {
+  std::vector<std::pair<void *, size_t>> regions;
+  std::vector<void *> copies;
+};
+
+int snap_take(Sim *s, Snapshot &sn) {
+  const size_t N = s->n_trips, L = s->n_lanes, W = (size_t)s->prm.n_windows * L;
+  auto add = [&](void *p, size_t bytes) { if (p && bytes) sn.regions.push_back({p, bytes}); };
+  for (int b = 0; b < 2; ++b) {
+    add(s->A[b].x, N * 4); add(s->A[b].v, N * 4); add(s->A[b].v0, N * 4); add(s->A[b].lane, N * 4);
+    add(s->A[b].rp, N * 4); add(s->A[b].nxt, N * 4); add(s->A[b].nl, N * 4); add(s->A[b].id, N * 4);
+    add(s->d_dyn[b], L * sizeof(int4));
+  }
+  add(s->d_ctrl, sizeof(DevCtrl));
+  add(s->d_qhead, L * 4);
+  add(s->d_tarr, N * 4);
+  add(s->d_vsum, W * 4);
+  add(s->d_vcnt, W * 4);
+  for (auto &r : sn.regions) {
+    void *c = nullptr;
+    cudaError_t e = cudaMalloc(&c, r.second);
+    if (e != cudaSuccess) return fail(s, MS_ERR_CUDA, std::string("autotune snapshot: ") + cudaGetErrorString(e));
+    sn.copies.push_back(c);
+    CK(cudaMemcpyAsync(c, r.first, r.second, cudaMemcpyDeviceToDevice, s->stream));
+  }
+  return MS_OK;
+}
+
+int snap_restore(Sim *s, Snapshot &sn) {
+  for (size_t k = 0; k < sn.regions.size(); ++k)
+    CK(cudaMemcpyAsync(sn.regions[k].first, sn.copies[k], sn.regions[k].second, cudaMemcpyDeviceToDevice, s->stream));
+  return MS_OK;
+}
+
+void snap_free(Snapshot &sn) {
+  for (void *c : sn.copies) cudaFree(c);
+  sn.copies.clear();
+}
+}  // namespace
+
+int ms_autotune(void *sim, int trial_steps, float *best_ms, int *config) {
+  Sim *s = (Sim *)sim;
+  if (!s || trial_steps <= 0) return MS_ERR_ARG;
+  if (!s->veh_loaded) return fail(s, MS_ERR_STATE, "add vehicles first");
+  CK(cudaStreamSynchronize(s->stream));
+  Snapshot sn;
+  int r = snap_take(s, sn);
+  if (r) { snap_free(sn); return r; }
+  const int blocks[] = {128, 256, 512};
+  const int factors[] = {1, 2, 4};
+  LaunchCfg best = s->cfg, orig = s->cfg;
+  float best_t = 3.4e38f;
+  int best_conf[3] = {s->cfg.blk_decide, 1, 1};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  StepArgs a = make_args(s);
+  for (int blk : blocks) {
+    for (int fd : factors) {
+      for (int fa : factors) {
+        LaunchCfg c;
+        c.blk_decide = c.blk_apply = blk;
+        c.blk_bucket = 256;
+        if ((r = shape_grids(s, c, fd, fa, 1))) { snap_free(sn); return r; }
+        s->cfg = c;
+        CK(launch_step(s, a, s->stream, nullptr));   // warm-up step of this shape
+        CK(cudaEventRecord(e0, s->stream));
+        for (int k = 0; k < trial_steps; ++k) CK(launch_step(s, a, s->stream, nullptr));
+        CK(cudaEventRecord(e1, s->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        ms /= trial_steps;
+        if ((r = snap_restore(s, sn))) { snap_free(sn); return r; }
+        if (ms < best_t) {
+          best_t = ms;
+          best = c;
+          best_conf[0] = blk;
+          best_conf[1] = fd;
+          best_conf[2] = fa;
+        }
+      }
+    }
+  }
+  CK(cudaStreamSynchronize(s->stream));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  snap_free(sn);
+  (void)orig;
+  s->cfg = best;
+  drop_graphs(s);   // rebuilt with the chosen shapes on the next ms_step
+  if (best_ms) *best_ms = best_t;
+  if (config) std::copy(best_conf, best_conf + 3, config);
+  return MS_OK;
+}
+
 const char *ms_last_error(void *sim) {
   Sim *s = (Sim *)sim;
   return s ? s->err.c_str() : "null simulation";
@@ -878,8 +1135,7 @@ void ms_destroy(void *sim) {
   Sim *s = (Sim *)sim;
   if (!s) return;
   if (s->veh_loaded || s->net_loaded) cudaStreamSynchronize(s->stream);
-  if (s->g_many) cudaGraphExecDestroy(s->g_many);
-  if (s->g_one) cudaGraphExecDestroy(s->g_one);
+  drop_graphs(s);
   for (void *p : s->allocs) cudaFree(p);
   if (s->cap) cudaStreamDestroy(s->cap);
   delete s;

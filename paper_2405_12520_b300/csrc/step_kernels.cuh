@@ -60,6 +60,7 @@ struct DevParams {
   uint32_t lc_thresh;    // floor(p_lc * 2^24)
   unsigned long long seed;
   int window, n_windows, debug, n_lanes;
+  int id_base;           // added to trip ids in the lane-change gate hash
 };
 
 // Vehicle state, sorted by (lane, x).  rp: index into routes[] of the current edge (the
@@ -390,7 +391,7 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
     mark(flag, (li.len - x) - P.x_lc_end);
     if (li.len - x < P.x_lc_end) return r;
     unsigned long long h = splitmix64(P.seed ^ ((unsigned long long)(unsigned)t << 32) ^
-                                      (unsigned long long)(unsigned)myid);
+                                      (unsigned long long)(unsigned)(myid + P.id_base));
     if ((uint32_t)(h >> 40) >= P.lc_thresh) return r;
   }
   r.cand = 1;

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libmoss103.so")
 MS_OK, MS_ERR_ARG, MS_ERR_ROUTE, MS_ERR_CAPACITY, MS_ERR_CUDA, MS_ERR_DEVICE, MS_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 ERR_NAMES = {0: "OK", -1: "ARG", -2: "ROUTE", -3: "CAPACITY", -4: "CUDA", -5: "DEVICE", -6: "STATE"}
 SYMBOLS = ("ms_create", "ms_load_network", "ms_add_vehicles", "ms_step", "ms_step_timed", "ms_step_noalloc",
+           "ms_load_network_batch", "ms_add_vehicles_batch", "ms_batch_offsets", "ms_autotune",
            "ms_sync", "ms_read_state",
            "ms_write_state", "ms_read_metrics", "ms_read_debug", "ms_last_error", "ms_destroy")
 
@@ -26,7 +27,7 @@ class ms_params(C.Structure):
         "dt", "veh_len", "idm_a", "idm_b", "idm_T", "idm_s0", "mobil_p", "mobil_th", "mobil_bsafe",
         "p_lc", "a_min", "v_max", "d_look", "x_lc_min", "x_lc_end")] + [
         ("window", C.c_int), ("n_windows", C.c_int), ("seed", C.c_uint64), ("debug", C.c_int),
-        ("block", C.c_int)]
+        ("block", C.c_int), ("id_base", C.c_int)]
 
 
 class ms_network(C.Structure):
@@ -79,6 +80,10 @@ def load():
         lib.ms_step.argtypes = [vp, C.c_int]
         lib.ms_step_timed.argtypes = [vp, C.c_int, C.POINTER(C.c_float)]
         lib.ms_step_noalloc.argtypes = [vp, C.c_int]
+        lib.ms_load_network_batch.argtypes = [vp, C.c_int, C.POINTER(ms_network)]
+        lib.ms_add_vehicles_batch.argtypes = [vp, C.c_int, C.POINTER(ms_vehicles)]
+        lib.ms_batch_offsets.argtypes = [vp, vp, vp]
+        lib.ms_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_float), vp]
         lib.ms_sync.argtypes = [vp]
         lib.ms_read_state.argtypes = [vp, C.POINTER(ms_state), C.c_int]
         lib.ms_write_state.argtypes = [vp, C.POINTER(ms_state)]
@@ -105,12 +110,13 @@ def _p(a):
     return a.ctypes.data_as(C.c_void_p) if a is not None else None
 
 
-def params_struct(params: dict, debug: bool = False, n_windows: int = 1, block: int = 0) -> ms_params:
+def params_struct(params: dict, debug: bool = False, n_windows: int = 1, block: int = 0,
+                  id_base: int = 0) -> ms_params:
     p = params
     return ms_params(p["dt"], p["veh_len"], p["idm_a"], p["idm_b"], p["idm_T"], p["idm_s0"],
                      p["mobil_p"], p["mobil_th"], p["mobil_bsafe"], p["p_lc"], p["a_min"], p["v_max"],
                      p["d_look"], p["x_lc_min"], p["x_lc_end"], int(p["window"]), int(n_windows),
-                     int(p["seed"]) & 0xFFFFFFFFFFFFFFFF, int(debug), int(block))
+                     int(p["seed"]) & 0xFFFFFFFFFFFFFFFF, int(debug), int(block), int(id_base))
 
 
 class Sim:
@@ -119,12 +125,13 @@ class Sim:
     Mirrors the C ABI: create (constructor), load_network, add_vehicles, step, sync,
     read_state, write_state, read_metrics, read_debug, last_error, destroy."""
 
-    def __init__(self, params: dict, stream=None, debug: bool = False, n_windows: int = 1, block: int = 0):
+    def __init__(self, params: dict, stream=None, debug: bool = False, n_windows: int = 1, block: int = 0,
+                 id_base: int = 0):
         self.lib = load()
         self.h = C.c_void_p()
         self.params = dict(params)
         self.n_windows = n_windows
-        self._p = params_struct(params, debug, n_windows, block)
+        self._p = params_struct(params, debug, n_windows, block, id_base)
         st = None
         if stream is not None:
             st = C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
@@ -140,24 +147,63 @@ class Sim:
     def last_error(self) -> str:
         return self.lib.ms_last_error(self.h).decode()
 
-    def load_network(self, net):
+    @staticmethod
+    def _net_struct(net, keep):
         i32 = lambda a: np.ascontiguousarray(a, np.int32)
-        keep = [np.ascontiguousarray(net.lane_len, np.float32)] + [i32(getattr(net, f)) for f in (
+        arrs = [np.ascontiguousarray(net.lane_len, np.float32)] + [i32(getattr(net, f)) for f in (
             "lane_edge", "lane_index", "lane_left", "lane_right", "succ_off", "succ_lane", "succ_edge",
             "lane_ctrl", "lane_group", "ctrl_offset", "ctrl_green", "ctrl_yellow", "ctrl_nphase",
             "edge_nlanes", "edge_lane0")]
-        s = ms_network(int(net.n_lanes), int(net.n_edges), int(net.n_ctrl), *[_p(a) for a in keep])
+        keep += arrs
+        return ms_network(int(net.n_lanes), int(net.n_edges), int(net.n_ctrl), *[_p(a) for a in arrs])
+
+    @staticmethod
+    def _veh_struct(dem, keep):
+        arrs = [np.ascontiguousarray(dem.t_dep, np.int32), np.ascontiguousarray(dem.v0, np.float32),
+                np.ascontiguousarray(dem.route_off, np.int64), np.ascontiguousarray(dem.route_edges, np.int32),
+                np.ascontiguousarray(dem.lane, np.int32), np.ascontiguousarray(dem.x, np.float32),
+                np.ascontiguousarray(dem.v, np.float32)]
+        keep += arrs
+        return ms_vehicles(int(dem.n), *[_p(a) for a in arrs])
+
+    def load_network(self, net):
+        keep = []
+        s = self._net_struct(net, keep)
         self._check(self.lib.ms_load_network(self.h, C.byref(s)), "ms_load_network")
         self.n_lanes = int(net.n_lanes)
 
     def add_vehicles(self, dem):
-        keep = [np.ascontiguousarray(dem.t_dep, np.int32), np.ascontiguousarray(dem.v0, np.float32),
-                np.ascontiguousarray(dem.route_off, np.int64), np.ascontiguousarray(dem.route_edges, np.int32),
-                np.ascontiguousarray(dem.lane, np.int32), np.ascontiguousarray(dem.x, np.float32),
-                np.ascontiguousarray(dem.v, np.float32)]
-        s = ms_vehicles(int(dem.n), *[_p(a) for a in keep])
+        keep = []
+        s = self._veh_struct(dem, keep)
         self._check(self.lib.ms_add_vehicles(self.h, C.byref(s)), "ms_add_vehicles")
         self.n_trips = int(dem.n)
+
+    def load_network_batch(self, nets):
+        keep = []
+        arr = (ms_network * len(nets))(*[self._net_struct(n, keep) for n in nets])
+        self._check(self.lib.ms_load_network_batch(self.h, len(nets), arr), "ms_load_network_batch")
+        self.n_lanes = int(sum(n.n_lanes for n in nets))
+        self.n_scen = len(nets)
+
+    def add_vehicles_batch(self, dems):
+        keep = []
+        arr = (ms_vehicles * len(dems))(*[self._veh_struct(d, keep) for d in dems])
+        self._check(self.lib.ms_add_vehicles_batch(self.h, len(dems), arr), "ms_add_vehicles_batch")
+        self.n_trips = int(sum(d.n for d in dems))
+
+    def batch_offsets(self):
+        lo = np.zeros(self.n_scen + 1, np.int32)
+        to = np.zeros(self.n_scen + 1, np.int32)
+        self._check(self.lib.ms_batch_offsets(self.h, _p(lo), _p(to)), "ms_batch_offsets")
+        return lo, to
+
+    def autotune(self, trial_steps: int = 5):
+        """Pick the fastest launch shape (block size, grid factors); returns
+        (best ms per step, (block, decide grid factor, apply grid factor))."""
+        ms = C.c_float()
+        cfg = np.zeros(3, np.int32)
+        self._check(self.lib.ms_autotune(self.h, int(trial_steps), C.byref(ms), _p(cfg)), "ms_autotune")
+        return ms.value, tuple(int(c) for c in cfg)
 
     def step(self, n: int = 1):
         self._check(self.lib.ms_step(self.h, int(n)), "ms_step")

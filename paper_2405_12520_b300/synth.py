@@ -741,6 +741,64 @@ def merge_demands(a: Demand, b: Demand) -> Demand:
                   v=np.concatenate([a.v, b.v]))
 
 
+def union(nets, dems):
+    """Disjoint union of several scenarios as one network and one demand: scenario k's
+    lanes, edges, controllers and trips are offset by the totals of scenarios 0..k-1."""
+    lo = np.cumsum([0] + [n.n_lanes for n in nets])
+    eo = np.cumsum([0] + [n.n_edges for n in nets])
+    co = np.cumsum([0] + [n.n_ctrl for n in nets])
+    so = np.cumsum([0] + [int(n.succ_off[-1]) for n in nets])
+    vo = np.cumsum([0] + [n.node_xy.shape[0] for n in nets])
+    sh = lambda a, o: np.where(a >= 0, a + o, a)
+    cat = lambda f: np.concatenate(f)
+    net = Network(
+        node_xy=cat([n.node_xy for n in nets]),
+        edge_from=cat([n.edge_from + vo[k] for k, n in enumerate(nets)]).astype(np.int32),
+        edge_to=cat([n.edge_to + vo[k] for k, n in enumerate(nets)]).astype(np.int32),
+        edge_len=cat([n.edge_len for n in nets]), edge_nlanes=cat([n.edge_nlanes for n in nets]),
+        edge_lane0=cat([n.edge_lane0 + lo[k] for k, n in enumerate(nets)]).astype(np.int32),
+        lane_len=cat([n.lane_len for n in nets]),
+        lane_edge=cat([sh(n.lane_edge, eo[k]) for k, n in enumerate(nets)]).astype(np.int32),
+        lane_index=cat([n.lane_index for n in nets]),
+        lane_left=cat([sh(n.lane_left, lo[k]) for k, n in enumerate(nets)]).astype(np.int32),
+        lane_right=cat([sh(n.lane_right, lo[k]) for k, n in enumerate(nets)]).astype(np.int32),
+        succ_off=np.concatenate([n.succ_off[:-1] + so[k] for k, n in enumerate(nets)] + [[so[-1]]]).astype(np.int32),
+        succ_lane=cat([n.succ_lane + lo[k] for k, n in enumerate(nets)]).astype(np.int32),
+        succ_edge=cat([n.succ_edge + eo[k] for k, n in enumerate(nets)]).astype(np.int32),
+        lane_ctrl=cat([sh(n.lane_ctrl, co[k]) for k, n in enumerate(nets)]).astype(np.int32),
+        lane_group=cat([n.lane_group for n in nets]),
+        ctrl_node=cat([n.ctrl_node + vo[k] for k, n in enumerate(nets)]).astype(np.int32),
+        ctrl_offset=cat([n.ctrl_offset for n in nets]), ctrl_green=cat([n.ctrl_green for n in nets]),
+        ctrl_yellow=cat([n.ctrl_yellow for n in nets]), ctrl_nphase=cat([n.ctrl_nphase for n in nets]),
+        name="union")
+    ro = np.cumsum([0] + [int(d.route_off[-1]) for d in dems])
+    dem = Demand(
+        t_dep=cat([d.t_dep for d in dems]), v0=cat([d.v0 for d in dems]),
+        route_off=np.concatenate([d.route_off[:-1] + ro[k] for k, d in enumerate(dems)] + [[ro[-1]]]).astype(np.int64),
+        route_edges=cat([d.route_edges + eo[k] for k, d in enumerate(dems)]).astype(np.int32),
+        lane=cat([sh(d.lane, lo[k]) for k, d in enumerate(dems)]).astype(np.int32),
+        x=cat([d.x for d in dems]), v=cat([d.v for d in dems]))
+    return net, dem
+
+
+def batch_scenarios(n_scen: int = 256, seed: int = 7, side=(4, 32), n_range=(500, 200_000),
+                    n_lanes: int = 2, link_len: float = 200.0):
+    """Independent scenarios of uneven size for batched runs: grid side ~ U{side}, vehicle
+    count ~ log-uniform n_range (capped at 60% of the grid's jam capacity), distinct seeds
+    and random signal plans (offsets uniform in the cycle, green U{20..40} s); vehicles are
+    pre-placed (steady state) with uniform destinations."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_scen):
+        a = int(rng.integers(side[0], side[1] + 1))
+        net = grid_network(a, a, n_lanes, link_len, 30, 3, "random", seed=seed * 1000 + k)
+        cap = int(0.6 * net.n_edge_lanes * (link_len - 5.0) / 9.0)
+        n = int(min(cap, np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1])))))
+        dem = place_vehicles(net, max(n, 1), seed=seed * 1000 + k, dest="uniform")
+        out.append((net, dem))
+    return out
+
+
 # ----------------------------------------------------------------------------------------
 # named workloads
 # ----------------------------------------------------------------------------------------

@@ -227,6 +227,47 @@ int ms_batch_offsets(void *sim, int *lane_off, int *trip_off);
    k_apply.  Allocates temporary device memory for the state snapshot. */
 int ms_autotune(void *sim, int trial_steps, float *best_ms, int *config);
 
+/* ---- learned lane-change surrogate ----------------------------------------------
+   A 16 -> 64 -> 64 -> 3 MLP (ReLU; softmax over stay / left / right) that replaces the
+   MOBIL incentive decision of discretionary candidates that passed the safety criteria.
+   The paper's lane-change model is rule-based (Sec. III-A); the surrogate is this
+   library's addition.  Parameters: 5443 floats, W1[64][16], b1[64], W2[64][64], b2[64],
+   W3[3][64], b3[3], row-major (out x in).  Inference and training run on the tensor cores
+   with BF16 operands and FP32 accumulation. */
+#define MS_MLP_NPARAM 5443
+#define MS_MLP_WORK_FLOATS 12096   /* scratch of the training calls, floats */
+
+/* Log (features, rule decision) of every candidate in subsequent steps into caller-owned
+   device buffers: x [cap][16] bf16, y [cap] int (0 stay, 1 left, 2 right), n: device int
+   counting offered samples (those beyond cap are dropped).  x == NULL turns logging off. */
+int ms_set_lc_log(void *sim, void *x, int *y, int cap, int *n);
+
+/* Use the learned decision in subsequent steps: params (host, 5443 floats) is the network;
+   a candidate follows the network's class when its softmax margin (top1 - top2) is at
+   least margin, else the rule's decision; a change still needs the step's allowed
+   direction.  params == NULL returns to the rule. */
+int ms_set_lc_model(void *sim, const float *params, float margin);
+
+/* Counters of the learned decision since the model was set: [0] candidates, [1] rule
+   fallbacks (low margin), [2] agreements with the rule, [3 + 3*rule + final] confusion. */
+int ms_read_lc_stats(void *sim, int64_t *out12);
+
+/* One Adam step (lr, betas 0.9 / 0.999, eps 1e-8; t counts from 1) of class-weighted
+   cross-entropy on the minibatch idx[0..batch) of the samples (x bf16 [*][16], y int);
+   theta, m, v: device FP32 [5443]; work: device scratch of MS_MLP_WORK_FLOATS floats;
+   class_w: host, 3 floats; loss (host, may be NULL) receives the minibatch loss
+   (synchronises).  All pointers except class_w and loss are device pointers. */
+int ms_mlp_train_step(const void *x, const int *y, const int *idx, int batch, float *theta, float *m, float *v,
+                      int t, float lr, const float *class_w, float *work, float *loss, void *cuda_stream);
+
+/* Gradient of the same loss at theta (no update) into grad (device FP32 [5443]). */
+int ms_mlp_grad(const void *x, const int *y, const int *idx, int batch, const float *theta,
+                const float *class_w, float *work, float *grad, void *cuda_stream);
+
+/* Class and softmax margin of n samples (device outputs cls [n] int, margin [n] float). */
+int ms_mlp_predict(const void *x, int n, const float *theta, float *work, int *cls, float *margin,
+                   void *cuda_stream);
+
 const char *ms_last_error(void *sim);
 void ms_destroy(void *sim);
 

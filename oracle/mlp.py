@@ -1,0 +1,110 @@
+"""FP64 CPU reference of the learned lane-change surrogate -- TEST INFRASTRUCTURE.
+
+The network is the learned replacement of the MOBIL incentive decision (the paper's
+lane-change model is rule-based, Sec. III-A; the surrogate is this library's addition):
+16 features -> Linear(64) + ReLU -> Linear(64) + ReLU -> Linear(3) -> softmax over
+{stay, left, right}, trained with class-weighted cross-entropy and Adam.  Only tests/,
+__graft_entry__.smoke() and bench.py may import this module.  Plain numpy in float64; no
+blocking or fusion beyond the layer definitions.
+
+Parameter layout (one flat vector, float): W1[64,16], b1[64], W2[64,64], b2[64], W3[3,64],
+b3[3] -- row-major, out x in.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+N_IN, N_H, N_OUT = 16, 64, 3
+SHAPES = [("W1", (N_H, N_IN)), ("b1", (N_H,)), ("W2", (N_H, N_H)), ("b2", (N_H,)),
+          ("W3", (N_OUT, N_H)), ("b3", (N_OUT,))]
+N_PARAMS = sum(int(np.prod(s)) for _, s in SHAPES)
+
+
+def unpack(theta):
+    out, o = {}, 0
+    for name, shp in SHAPES:
+        n = int(np.prod(shp))
+        out[name] = np.asarray(theta[o:o + n], np.float64).reshape(shp)
+        o += n
+    return out
+
+
+def pack(p):
+    return np.concatenate([np.asarray(p[name], np.float64).ravel() for name, _ in SHAPES])
+
+
+def init(seed: int = 0) -> np.ndarray:
+    """He-uniform weights, zero biases."""
+    rng = np.random.default_rng(seed)
+    p = {}
+    for name, shp in SHAPES:
+        if name.startswith("W"):
+            lim = np.sqrt(6.0 / shp[1])
+            p[name] = rng.uniform(-lim, lim, size=shp)
+        else:
+            p[name] = np.zeros(shp)
+    return pack(p)
+
+
+def forward(theta, X):
+    """Logits and the activations of every layer."""
+    p = unpack(theta)
+    X = np.asarray(X, np.float64)
+    a1 = X @ p["W1"].T + p["b1"]
+    h1 = np.maximum(a1, 0.0)
+    a2 = h1 @ p["W2"].T + p["b2"]
+    h2 = np.maximum(a2, 0.0)
+    z = h2 @ p["W3"].T + p["b3"]
+    return z, (X, a1, h1, a2, h2)
+
+
+def softmax(z):
+    z = z - z.max(axis=1, keepdims=True)
+    e = np.exp(z)
+    return e / e.sum(axis=1, keepdims=True)
+
+
+def loss(theta, X, y, w_class):
+    """Class-weighted mean cross-entropy: sum_i w[y_i] * -log p_i[y_i] / sum_i w[y_i]."""
+    z, _ = forward(theta, X)
+    p = softmax(z)
+    w = np.asarray(w_class, np.float64)[y]
+    return float(np.sum(w * -np.log(p[np.arange(len(y)), y])) / np.sum(w))
+
+
+def grad(theta, X, y, w_class):
+    """Analytic gradient of loss() by the chain rule, layer by layer."""
+    prm = unpack(theta)
+    z, (X, a1, h1, a2, h2) = forward(theta, X)
+    p = softmax(z)
+    w = np.asarray(w_class, np.float64)[y]
+    W = np.sum(w)
+    dz = p.copy()
+    dz[np.arange(len(y)), y] -= 1.0
+    dz *= (w / W)[:, None]
+    g = {"W3": dz.T @ h2, "b3": dz.sum(0)}
+    dh2 = dz @ prm["W3"]
+    da2 = dh2 * (a2 > 0)
+    g["W2"] = da2.T @ h1
+    g["b2"] = da2.sum(0)
+    dh1 = da2 @ prm["W2"]
+    da1 = dh1 * (a1 > 0)
+    g["W1"] = da1.T @ X
+    g["b1"] = da1.sum(0)
+    return pack(g)
+
+
+def adam_step(theta, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015) with bias correction; t counts from 1."""
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** t)
+    vh = v / (1 - b2 ** t)
+    return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def predict(theta, X, margin=0.0):
+    """Class and softmax margin (top1 - top2) per sample."""
+    p = softmax(forward(theta, X)[0])
+    s = np.sort(p, axis=1)
+    return p.argmax(1), s[:, -1] - s[:, -2]

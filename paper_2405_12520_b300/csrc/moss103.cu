@@ -74,6 +74,12 @@ struct Sim {
   // batches of independent scenarios: offsets of each scenario's lanes and trips
   std::vector<int> batch_lane_off, batch_trip_off;
   cudaGraphExec_t g_many = nullptr, g_one = nullptr;
+  // learned lane change
+  int lc_mode = MODE_PLAIN;
+  LcAux lc{};
+  MlpDev *d_model = nullptr;
+  unsigned long long *d_lcstats = nullptr;
+  float *d_theta = nullptr;
   std::vector<void *> allocs;
 };
 
@@ -140,6 +146,7 @@ StepArgs make_args(Sim *s) {
   a.vsum = s->d_vsum;
   a.vcnt = s->d_vcnt;
   a.dbg = s->dbg;
+  a.lc = s->lc;
   a.P = s->P;
   return a;
 }
@@ -148,7 +155,12 @@ StepArgs make_args(Sim *s) {
 cudaError_t launch_step(const Sim *s, const StepArgs &a, cudaStream_t st, cudaEvent_t *ev) {
   const LaunchCfg &c = s->cfg;
   if (ev) cudaEventRecord(ev[0], st);
-  k_decide<<<c.grid_decide, c.blk_decide, 0, st>>>(a);
+  if (s->lc_mode == MODE_LEARN)
+    k_decide_t<MODE_LEARN><<<c.grid_decide, c.blk_decide, learn_smem(c.blk_decide), st>>>(a);
+  else if (s->lc_mode == MODE_LOG)
+    k_decide_t<MODE_LOG><<<c.grid_decide, c.blk_decide, 0, st>>>(a);
+  else
+    k_decide_t<MODE_PLAIN><<<c.grid_decide, c.blk_decide, 0, st>>>(a);
   if (ev) cudaEventRecord(ev[1], st);
   k_lanes<<<s->n_tiles, LANE_THREADS, 0, st>>>(a);
   if (ev) cudaEventRecord(ev[2], st);
@@ -166,7 +178,7 @@ cudaError_t enqueue_step(Sim *s, cudaStream_t st) { return launch_step(s, make_a
 int shape_grids(Sim *s, LaunchCfg &c, int f_decide, int f_apply, int f_bucket) {
   const int N = s->n_trips;
   int od = 0, oa = 0, ob = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&od, k_decide, c.blk_decide, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&od, k_decide_t<MODE_PLAIN>, c.blk_decide, 0));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oa, k_apply, c.blk_apply, 0));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, k_bucket, c.blk_bucket, 0));
   auto g = [&](int blk, int occ, int f) {
@@ -1080,7 +1092,7 @@ int ms_autotune(void *sim, int trial_steps, float *best_ms, int *config) {
   if (r) { snap_free(sn); return r; }
   const int blocks[] = {128, 256, 512};
   const int factors[] = {1, 2, 4};
-  LaunchCfg best = s->cfg, orig = s->cfg;
+  LaunchCfg best = s->cfg;
   float best_t = 3.4e38f;
   int best_conf[3] = {s->cfg.blk_decide, 1, 1};
   cudaEvent_t e0, e1;
@@ -1118,11 +1130,146 @@ int ms_autotune(void *sim, int trial_steps, float *best_ms, int *config) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   snap_free(sn);
-  (void)orig;
   s->cfg = best;
   drop_graphs(s);   // rebuilt with the chosen shapes on the next ms_step
   if (best_ms) *best_ms = best_t;
   if (config) std::copy(best_conf, best_conf + 3, config);
+  return MS_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// learned lane change
+// ---------------------------------------------------------------------------------
+
+int ms_set_lc_log(void *sim, void *x, int *y, int cap, int *n) {
+  Sim *s = (Sim *)sim;
+  if (!s) return MS_ERR_ARG;
+  if (x && (!y || !n || cap <= 0)) return fail(s, MS_ERR_ARG, "log needs x, y, n and cap > 0");
+  s->lc.log_x = (__nv_bfloat16 *)x;
+  s->lc.log_y = y;
+  s->lc.log_cap = cap;
+  s->lc.log_n = n;
+  s->lc_mode = x ? MODE_LOG : (s->d_model && s->lc.model ? MODE_LEARN : MODE_PLAIN);
+  drop_graphs(s);
+  return MS_OK;
+}
+
+int ms_set_lc_model(void *sim, const float *params, float margin) {
+  Sim *s = (Sim *)sim;
+  if (!s) return MS_ERR_ARG;
+  drop_graphs(s);
+  if (!params) {
+    s->lc.model = nullptr;
+    s->lc_mode = s->lc.log_x ? MODE_LOG : MODE_PLAIN;
+    return MS_OK;
+  }
+  if (!(margin >= 0.f && margin <= 1.f)) return fail(s, MS_ERR_ARG, "margin must be in [0, 1]");
+  if (!s->d_model) {
+    DALLOC(s->d_model, 1);
+    DALLOC(s->d_lcstats, LC_STATS);
+    DALLOC(s->d_theta, MLP_NPARAM);
+    static bool attr = false;
+    if (!attr) {
+      CK(cudaFuncSetAttribute(k_decide_t<MODE_LEARN>, cudaFuncAttributeMaxDynamicSharedMemorySize, learn_smem(512)));
+      attr = true;
+    }
+  }
+  CK(cudaMemcpyAsync(s->d_theta, params, sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice, s->stream));
+  k_mlp_pack<<<8, 256, 0, s->stream>>>(s->d_theta, s->d_model);
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(s->d_lcstats, 0, sizeof(unsigned long long) * LC_STATS, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  s->lc.model = s->d_model;
+  s->lc.margin = margin;
+  s->lc.stats = s->d_lcstats;
+  s->lc_mode = MODE_LEARN;
+  s->lc.log_x = nullptr;
+  return MS_OK;
+}
+
+int ms_read_lc_stats(void *sim, int64_t *out12) {
+  Sim *s = (Sim *)sim;
+  if (!s || !out12) return MS_ERR_ARG;
+  if (!s->d_lcstats) return fail(s, MS_ERR_STATE, "no model set");
+  CK(cudaStreamSynchronize(s->stream));
+  unsigned long long h[LC_STATS];
+  CK(cudaMemcpy(h, s->d_lcstats, sizeof(h), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < LC_STATS; ++k) out12[k] = (int64_t)h[k];
+  return MS_OK;
+}
+
+namespace {
+int mlp_run(const void *x, const int *y, const int *idx, int batch, const float *theta, const float *class_w,
+            float *work, cudaStream_t st) {
+  Sim *s = nullptr;
+  static_assert(MLP_NPARAM == MS_MLP_NPARAM, "parameter count");
+  static_assert(MLP_NPARAM + 4 + (int)(sizeof(MlpDev) / 4) <= MS_MLP_WORK_FLOATS, "work size");
+  if (!x || !y || !idx || batch <= 0 || !theta || !class_w || !work) return MS_ERR_ARG;
+  float *grad = work, *stats = work + MLP_NPARAM;
+  MlpDev *model = reinterpret_cast<MlpDev *>(work + MLP_NPARAM + 4);
+  static bool attr = false;
+  if (!attr) {
+    CK(cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, TR_SMEM));
+    attr = true;
+  }
+  k_mlp_pack<<<8, 256, 0, st>>>(theta, model);
+  CK(cudaMemsetAsync(work, 0, sizeof(float) * (MLP_NPARAM + 4), st));
+  TrainArgs a{};
+  a.X = (const __nv_bfloat16 *)x;
+  a.y = y;
+  a.idx = idx;
+  a.batch = batch;
+  a.model = model;
+  a.cw[0] = class_w[0];
+  a.cw[1] = class_w[1];
+  a.cw[2] = class_w[2];
+  a.grad = grad;
+  a.stats = stats;
+  k_mlp_train<<<(batch + TR_ROWS - 1) / TR_ROWS, TR_ROWS * 2, TR_SMEM, st>>>(a);
+  CK(cudaGetLastError());
+  return MS_OK;
+}
+}  // namespace
+
+int ms_mlp_train_step(const void *x, const int *y, const int *idx, int batch, float *theta, float *m, float *v,
+                      int t, float lr, const float *class_w, float *work, float *loss, void *cuda_stream) {
+  Sim *s = nullptr;
+  if (!m || !v || t < 1) return MS_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int r = mlp_run(x, y, idx, batch, theta, class_w, work, st);
+  if (r) return r;
+  if (loss) {
+    float h[2];
+    CK(cudaMemcpyAsync(h, work + MLP_NPARAM, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *loss = h[0] > 0.f ? h[1] / h[0] : 0.f;
+  }
+  k_mlp_adam<<<8, 256, 0, st>>>(theta, m, v, work, work + MLP_NPARAM, t, lr, 0.9f, 0.999f, 1e-8f);
+  CK(cudaGetLastError());
+  return MS_OK;
+}
+
+int ms_mlp_grad(const void *x, const int *y, const int *idx, int batch, const float *theta, const float *class_w,
+                float *work, float *grad, void *cuda_stream) {
+  Sim *s = nullptr;
+  if (!grad) return MS_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int r = mlp_run(x, y, idx, batch, theta, class_w, work, st);
+  if (r) return r;
+  k_mlp_scale<<<8, 256, 0, st>>>(work, work + MLP_NPARAM, grad);
+  CK(cudaGetLastError());
+  return MS_OK;
+}
+
+int ms_mlp_predict(const void *x, int n, const float *theta, float *work, int *cls, float *margin,
+                   void *cuda_stream) {
+  Sim *s = nullptr;
+  if (!x || n <= 0 || !theta || !work || !cls || !margin) return MS_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  MlpDev *model = reinterpret_cast<MlpDev *>(work + MLP_NPARAM + 4);
+  k_mlp_pack<<<8, 256, 0, st>>>(theta, model);
+  k_mlp_predict<<<std::min(4096, (n + 63) / 64), 128, 0, st>>>((const __nv_bfloat16 *)x, n, model, cls, margin);
+  CK(cudaGetLastError());
   return MS_OK;
 }
 

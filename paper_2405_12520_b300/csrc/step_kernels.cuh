@@ -25,6 +25,8 @@
 #include <cuda/atomic>
 #include <cuda_runtime.h>
 
+#include "mlp_kernels.cuh"
+
 namespace moss {
 
 enum { SIG_G = 0, SIG_Y = 1, SIG_R = 2 };
@@ -98,6 +100,21 @@ constexpr int CODE_LANE_BITS = 29;
 constexpr int CODE_LANE_MASK = (1 << CODE_LANE_BITS) - 1;
 enum { C_STAY = 0, C_CHANGE = 1, C_TRANSFER = 2, C_TRANSFER_ROUTE = 3, C_RETIRE = 4 };
 
+// learned lane change: decision log (training data), model, agreement statistics
+enum { MODE_PLAIN = 0, MODE_LOG = 1, MODE_LEARN = 2 };
+enum { ST_CAND = 0, ST_FALLBACK = 1, ST_AGREE = 2, ST_CONF = 3 };   // ST_CONF + 3*rule + final
+constexpr int LC_STATS = 12;
+
+struct LcAux {
+  __nv_bfloat16 *log_x;   // [cap][16]
+  int *log_y;             // [cap]
+  int log_cap;
+  int *log_n;             // samples offered (may exceed cap; extra ones are dropped)
+  const MlpDev *model;
+  float margin;           // softmax top1 - top2 below which the rule decides
+  unsigned long long *stats;
+};
+
 struct StepArgs {
   const LaneInfo *li;
   const int2 *succ;    // {internal lane, exit edge}
@@ -124,6 +141,7 @@ struct StepArgs {
   float *vsum;
   int *vcnt;
   DebugOut dbg;
+  LcAux lc;
   DevParams P;
 };
 
@@ -237,6 +255,8 @@ struct LC {
   float inc;
   int tkind;
   float tgap, tvl, anew;
+  int safe, mand, step_dir;   // safety passed; mandatory change; direction allowed this step
+  float gF, vF, aFn;          // new follower: gap, speed, acceleration behind the changer
 };
 
 struct Upd {
@@ -369,9 +389,11 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
   r.tl = r.tf = r.of = -1;
   if (li.edge < 0) return r;
   int step_dir = (t % 2 == 0) ? 1 : -1;
+  r.step_dir = step_dir;
   int tau = step_dir > 0 ? li.left : li.right;
   if (tau < 0) return r;
   const bool mand = nlc == NL_NONE;   // own lane has no link toward the next edge
+  r.mand = mand;
   if (mand) {
     int dr = 1 << 30, dl = 1 << 30, k = 1;
     for (int q = li.right; q >= 0; q = a.li[q].right, ++k)
@@ -432,7 +454,11 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
     aF_new = idm(P, vF, v0F, true, gF, v);
     mark(flag, aF_new + P.bsafe);
     if (aF_new < -P.bsafe) return r;
+    r.gF = gF;
+    r.vF = vF;
+    r.aFn = aF_new;
   }
+  r.safe = 1;
   r.anew = idm(P, v, v0, r.tkind != K_FREE, r.tgap, r.tvl);
   if (!mand) {
     float delta = r.anew - a_c;
@@ -463,28 +489,48 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
   return r;
 }
 
-// The update of vehicle i (snapshot index) at step t.  Pure function of the snapshot.
-__device__ __forceinline__ Upd vehicle_update(const StepArgs &a, const Soa &S, const int4 *dyn, int i,
-                                              int t) {
+// Per-vehicle context of one step (snapshot values the update reuses)
+struct VCtx {
+  int l, rp, en, nlc;
+  float x, v, v0;
+  LaneInfo li;
+  int4 dl;
+};
+
+// Sensing, car following and the rule's lane-change decision of vehicle i at step t.
+__device__ __forceinline__ Upd vehicle_sense(const StepArgs &a, const Soa &S, const int4 *dyn, int i, int t,
+                                             VCtx &c) {
   const DevParams &P = a.P;
   Upd u;
   u.flag = 0;
-  const int l = S.lane[i];
-  const float x = S.x[i], v = S.v[i], v0 = S.v0[i];
-  const int rp = S.rp[i], en = S.nxt[i], nlc = S.nl[i], myid = S.id[i];
-  const LaneInfo li = a.li[l];
-  const int4 dl = dyn[l];
+  c.l = S.lane[i];
+  c.x = S.x[i];
+  c.v = S.v[i];
+  c.v0 = S.v0[i];
+  c.rp = S.rp[i];
+  c.en = S.nxt[i];
+  c.nlc = S.nl[i];
+  const int myid = S.id[i];
+  c.li = a.li[c.l];
+  c.dl = dyn[c.l];
   // the cached next lane's records, loaded together with the own lane's
   int4 pf_dyn = make_int4(0, 0, 0, 0);
   LaneInfo pf_li{};
-  if (nlc >= 0) {
-    pf_dyn = dyn[nlc];
-    pf_li = a.li[nlc];
+  if (c.nlc >= 0) {
+    pf_dyn = dyn[c.nlc];
+    pf_li = a.li[c.nlc];
   }
-  u.own = own_leader(a, S, dyn, i, l, li, dl, x, v, rp, en, nlc, pf_dyn, pf_li, myid, t, u.flag);
-  u.a_own = idm(P, v, v0, u.own.kind != K_FREE, u.own.gap, u.own.vl);
-  u.lc = lane_change(a, S, dyn, i, l, li, x, v, v0, en, nlc, dl, myid, t, u.own, u.a_own, u.flag);
-  const int dir = u.lc.dir;
+  u.own = own_leader(a, S, dyn, i, c.l, c.li, c.dl, c.x, c.v, c.rp, c.en, c.nlc, pf_dyn, pf_li, myid, t, u.flag);
+  u.a_own = idm(P, c.v, c.v0, u.own.kind != K_FREE, u.own.gap, u.own.vl);
+  u.lc = lane_change(a, S, dyn, i, c.l, c.li, c.x, c.v, c.v0, c.en, c.nlc, c.dl, myid, t, u.own, u.a_own, u.flag);
+  return u;
+}
+
+// Motion, safety clamp and lane transfer for the lane-change direction dir.
+__device__ __forceinline__ void vehicle_move(const StepArgs &a, Upd &u, const VCtx &c, int dir) {
+  const DevParams &P = a.P;
+  const LaneInfo &li = c.li;
+  const float x = c.x, v = c.v;
   u.a_use = dir ? fminf(u.a_own, u.lc.anew) : u.a_own;
   float vraw = v + u.a_use * P.dt;
   float vn, d;
@@ -509,32 +555,32 @@ __device__ __forceinline__ Upd vehicle_update(const StepArgs &a, const Soa &S, c
   float xn = x + d;
   if (u.own.end_obst || dir) xn = fminf(xn, li.len);
   u.kind = dir ? U_CHANGE : U_STAY;
-  u.lane = dir ? (dir > 0 ? li.left : li.right) : l;
-  u.rp = rp;
-  u.nxt = en;
+  u.lane = dir ? (dir > 0 ? li.left : li.right) : c.l;
+  u.rp = c.rp;
+  u.nxt = c.en;
   if (!dir) {
     mark(u.flag, xn - li.len);
     if (xn > li.len) {
-      if (li.edge >= 0 && en < 0) {
+      if (li.edge >= 0 && c.en < 0) {
         u.kind = U_RETIRE;
       } else {
         xn -= li.len;
         u.kind = U_TRANSFER;
         int nl;
         if (li.edge >= 0) {
-          nl = nlc;
+          nl = c.nlc;
         } else {
           nl = li.succ;
-          u.rp = rp + 1;
-          u.nxt = a.routes[rp + 2];
+          u.rp = c.rp + 1;
+          u.nxt = a.routes[c.rp + 2];
         }
         if (nl < 0 || xn > a.li[nl].len) {
           atomicOr(&a.ctrl->err, DEV_HOP);
-          nl = l;
+          nl = c.l;
           xn = li.len;
           u.kind = U_STAY;
-          u.rp = rp;
-          u.nxt = en;
+          u.rp = c.rp;
+          u.nxt = c.en;
         }
         u.lane = nl;
       }
@@ -542,6 +588,14 @@ __device__ __forceinline__ Upd vehicle_update(const StepArgs &a, const Soa &S, c
   }
   u.x = xn;
   u.v = vn;
+}
+
+// The update of vehicle i (snapshot index) at step t.  Pure function of the snapshot.
+__device__ __forceinline__ Upd vehicle_update(const StepArgs &a, const Soa &S, const int4 *dyn, int i,
+                                              int t) {
+  VCtx c;
+  Upd u = vehicle_sense(a, S, dyn, i, t, c);
+  vehicle_move(a, u, c, u.lc.dir);
   return u;
 }
 
@@ -590,7 +644,50 @@ __device__ __forceinline__ void lane_speed_sums(const StepArgs &a, const Soa &S,
   atomicAdd(&a.vcnt[o], d.y);
 }
 
-__global__ void __launch_bounds__(512, 2) k_decide(StepArgs a) {
+// The 16 inputs of the learned lane-change decision (scaled to O(1)): own speed and desired
+// speed, own-path gap and closing speed, current acceleration, allowed direction, target
+// lane gap and closing speed, new follower gap / speed / acceleration, prospective
+// acceleration, old follower speed, distance to the lane end, lane index, old follower gap.
+__device__ __forceinline__ void lc_features(const StepArgs &a, const Soa &S, int i, const Upd &u, const VCtx &c,
+                                            float f[MLP_IN]) {
+  const float L = a.P.L;
+  f[0] = c.v / 20.f;
+  f[1] = c.v0 / 20.f;
+  f[2] = u.own.kind != K_FREE ? fminf(u.own.gap, 200.f) / 100.f : 2.f;
+  f[3] = u.own.kind == K_VEH ? (c.v - u.own.vl) / 10.f : (u.own.kind == K_OBST ? c.v / 10.f : 0.f);
+  f[4] = u.a_own / a.P.a;
+  f[5] = (float)u.lc.step_dir;
+  f[6] = u.lc.tkind != K_FREE ? fminf(u.lc.tgap, 200.f) / 100.f : 2.f;
+  f[7] = u.lc.tkind == K_VEH ? (c.v - u.lc.tvl) / 10.f : (u.lc.tkind == K_OBST ? c.v / 10.f : 0.f);
+  f[8] = u.lc.tf >= 0 ? fminf(u.lc.gF, 200.f) / 100.f : 2.f;
+  f[9] = u.lc.tf >= 0 ? u.lc.vF / 20.f : 0.f;
+  f[10] = u.lc.tf >= 0 ? u.lc.aFn / a.P.a : 0.f;
+  f[11] = u.lc.anew / a.P.a;
+  f[12] = i > c.dl.x ? S.v[i - 1] / 20.f : 0.f;
+  f[13] = fminf(c.li.len - c.x, 200.f) / 100.f;
+  f[14] = (float)c.li.idx / 4.f;
+  f[15] = i > c.dl.x ? fminf((c.x - S.x[i - 1]) - L, 200.f) / 100.f : 2.f;
+}
+
+__device__ __forceinline__ int lc_class(int dir) { return dir > 0 ? 1 : (dir < 0 ? 2 : 0); }
+__device__ __forceinline__ int lc_dir(int cls) { return cls == 1 ? 1 : (cls == 2 ? -1 : 0); }
+
+// shared memory of the learned step: the model plus, per warp, 32 feature rows, one 16-row
+// hidden buffer and 32 x 3 logits
+constexpr int LEARN_WARP_SMEM = 32 * MLP_IN * 2 + 16 * MLP_H * 2 + 32 * MLP_OUT * 4;
+__host__ __device__ constexpr int learn_smem(int threads) {
+  return (int)sizeof(MlpDev) + (threads / 32) * LEARN_WARP_SMEM;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(512, 2) k_decide_t(StepArgs a) {
+  extern __shared__ __align__(16) unsigned char lsm[];
+  if constexpr (MODE == MODE_LEARN) {
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(a.lc.model);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(lsm);
+    for (int k = threadIdx.x; k < (int)(sizeof(MlpDev) / 4); k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+  }
   const int t = a.ctrl->t;
   const int p = t & 1;
   const Soa S = a.A[p];
@@ -603,8 +700,85 @@ __global__ void __launch_bounds__(512, 2) k_decide(StepArgs a) {
     const int i = base + threadIdx.x;
     int leave = 0, moving = 0;
     Upd u;
+    VCtx c;
+    int dir = 0;
     if (i < n) {
-      u = vehicle_update(a, S, dyn, i, t);
+      u = vehicle_sense(a, S, dyn, i, t, c);
+      dir = u.lc.dir;
+    }
+    if constexpr (MODE != MODE_PLAIN) {
+      // discretionary candidates that passed the safety criteria: the decision to learn
+      const bool cand = i < n && u.lc.cand && u.lc.safe && !u.lc.mand;
+      const int rule = cand ? lc_class(u.lc.dir) : 0;
+      const unsigned cm = __ballot_sync(0xffffffffu, cand);
+      const int wl = threadIdx.x & 31;
+      if constexpr (MODE == MODE_LOG) {
+        if (cm) {
+          int slot0 = 0;
+          const int leader = __ffs(cm) - 1;
+          if (wl == leader) slot0 = atomicAdd(a.lc.log_n, __popc(cm));
+          slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+          if (cand) {
+            const int slot = slot0 + __popc(cm & ((1u << wl) - 1u));
+            if (slot < a.lc.log_cap) {
+              float f[MLP_IN];
+              lc_features(a, S, i, u, c, f);
+              for (int q = 0; q < MLP_IN; ++q) a.lc.log_x[(size_t)slot * MLP_IN + q] = __float2bfloat16_rn(f[q]);
+              a.lc.log_y[slot] = rule;
+            }
+          }
+        }
+      } else {   // MODE_LEARN: fused inference, one warp = two 16-row tiles
+        if (cm) {
+          const MlpDev &w = *reinterpret_cast<const MlpDev *>(lsm);
+          unsigned char *ws = lsm + sizeof(MlpDev) + (threadIdx.x >> 5) * LEARN_WARP_SMEM;
+          __nv_bfloat16 *X = reinterpret_cast<__nv_bfloat16 *>(ws);
+          __nv_bfloat16 *H1 = X + 32 * MLP_IN;
+          float *Z = reinterpret_cast<float *>(H1 + 16 * MLP_H);
+          float f[MLP_IN];
+          if (cand) lc_features(a, S, i, u, c, f);
+          for (int q = 0; q < MLP_IN; ++q) X[wl * MLP_IN + q] = __float2bfloat16_rn(cand ? f[q] : 0.f);
+          __syncwarp();
+          for (int mt = 0; mt < 2; ++mt) {
+            mlp_forward_tile(w, X + mt * 16 * MLP_IN, H1, nullptr,
+                             [&](int m, int q, float v) { Z[(mt * 16 + m) * MLP_OUT + q] = v; });
+            __syncwarp();
+          }
+          int fin = rule;
+          bool fb = false;
+          if (cand) {
+            const float z0 = Z[wl * 3], z1 = Z[wl * 3 + 1], z2 = Z[wl * 3 + 2];
+            const float mx = fmaxf(z0, fmaxf(z1, z2));
+            const float e0 = __expf(z0 - mx), e1 = __expf(z1 - mx), e2 = __expf(z2 - mx);
+            const float sum = e0 + e1 + e2;
+            const float p0 = e0 / sum, p1 = e1 / sum, p2 = e2 / sum;
+            int cls = 0;
+            float top = p0, sec = fmaxf(p1, p2);
+            if (p1 > top) { cls = 1; sec = fmaxf(p0, p2); top = p1; }
+            if (p2 > top) { cls = 2; sec = fmaxf(p0, p1); top = p2; }
+            fb = top - sec < a.lc.margin;
+            if (!fb) fin = (cls != 0 && lc_dir(cls) != u.lc.step_dir) ? 0 : cls;
+            dir = lc_dir(fin);
+          }
+          __syncwarp();
+          if (a.lc.stats) {
+            const unsigned fbm = __ballot_sync(0xffffffffu, cand && fb);
+            const unsigned agm = __ballot_sync(0xffffffffu, cand && fin == rule);
+            unsigned conf[9];
+            for (int q = 0; q < 9; ++q) conf[q] = __ballot_sync(0xffffffffu, cand && rule * 3 + fin == q);
+            if (wl == 0) {
+              atomicAdd(&a.lc.stats[ST_CAND], (unsigned long long)__popc(cm));
+              if (fbm) atomicAdd(&a.lc.stats[ST_FALLBACK], (unsigned long long)__popc(fbm));
+              if (agm) atomicAdd(&a.lc.stats[ST_AGREE], (unsigned long long)__popc(agm));
+              for (int q = 0; q < 9; ++q)
+                if (conf[q]) atomicAdd(&a.lc.stats[ST_CONF + q], (unsigned long long)__popc(conf[q]));
+            }
+          }
+        }
+      }
+    }
+    if (i < n) {
+      vehicle_move(a, u, c, dir);
       leave = u.kind != U_STAY;
       moving = u.kind == U_CHANGE || u.kind == U_TRANSFER;
       int kind = u.kind == U_STAY ? C_STAY

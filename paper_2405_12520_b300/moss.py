@@ -18,6 +18,8 @@ MS_OK, MS_ERR_ARG, MS_ERR_ROUTE, MS_ERR_CAPACITY, MS_ERR_CUDA, MS_ERR_DEVICE, MS
 ERR_NAMES = {0: "OK", -1: "ARG", -2: "ROUTE", -3: "CAPACITY", -4: "CUDA", -5: "DEVICE", -6: "STATE"}
 SYMBOLS = ("ms_create", "ms_load_network", "ms_add_vehicles", "ms_step", "ms_step_timed", "ms_step_noalloc",
            "ms_load_network_batch", "ms_add_vehicles_batch", "ms_batch_offsets", "ms_autotune",
+           "ms_set_lc_log", "ms_set_lc_model", "ms_read_lc_stats", "ms_mlp_train_step", "ms_mlp_grad",
+           "ms_mlp_predict",
            "ms_sync", "ms_read_state",
            "ms_write_state", "ms_read_metrics", "ms_read_debug", "ms_last_error", "ms_destroy")
 
@@ -84,6 +86,12 @@ def load():
         lib.ms_add_vehicles_batch.argtypes = [vp, C.c_int, C.POINTER(ms_vehicles)]
         lib.ms_batch_offsets.argtypes = [vp, vp, vp]
         lib.ms_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_float), vp]
+        lib.ms_set_lc_log.argtypes = [vp, vp, vp, C.c_int, vp]
+        lib.ms_set_lc_model.argtypes = [vp, vp, C.c_float]
+        lib.ms_read_lc_stats.argtypes = [vp, vp]
+        lib.ms_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, C.c_int, C.c_float, vp, vp, vp, vp]
+        lib.ms_mlp_grad.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, vp, vp]
+        lib.ms_mlp_predict.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
         lib.ms_sync.argtypes = [vp]
         lib.ms_read_state.argtypes = [vp, C.POINTER(ms_state), C.c_int]
         lib.ms_write_state.argtypes = [vp, C.POINTER(ms_state)]
@@ -98,6 +106,50 @@ def load():
                 getattr(lib, f).restype = C.c_int
         _lib = lib
     return _lib
+
+
+MLP_NPARAM = 5443
+MLP_WORK_FLOATS = 12096
+LC_STAT_NAMES = ("candidates", "fallbacks", "agree") + tuple(f"conf_{r}{f}" for r in "slr" for f in "slr")
+
+
+def _dp(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _st(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+
+
+def mlp_train_step(x, y, idx, theta, m, v, t, lr, class_w, work, stream=None, want_loss=False):
+    """One Adam step of the surrogate on device tensors (x bf16 [n,16], y int32, idx int32,
+    theta/m/v float32 [5443], work float32 [MLP_WORK_FLOATS]); returns the loss if asked."""
+    lib = load()
+    cw = np.ascontiguousarray(class_w, np.float32)
+    loss = C.c_float(0.0)
+    rc = lib.ms_mlp_train_step(_dp(x), _dp(y), _dp(idx), int(idx.numel()), _dp(theta), _dp(m), _dp(v), int(t),
+                               float(lr), _p(cw), _dp(work), C.byref(loss) if want_loss else None, _st(stream))
+    if rc:
+        raise MossError(rc, "ms_mlp_train_step")
+    return loss.value if want_loss else None
+
+
+def mlp_grad(x, y, idx, theta, class_w, work, grad, stream=None):
+    lib = load()
+    cw = np.ascontiguousarray(class_w, np.float32)
+    rc = lib.ms_mlp_grad(_dp(x), _dp(y), _dp(idx), int(idx.numel()), _dp(theta), _p(cw), _dp(work), _dp(grad),
+                         _st(stream))
+    if rc:
+        raise MossError(rc, "ms_mlp_grad")
+
+
+def mlp_predict(x, theta, work, cls, margin, stream=None):
+    lib = load()
+    rc = lib.ms_mlp_predict(_dp(x), int(x.shape[0]), _dp(theta), _dp(work), _dp(cls), _dp(margin), _st(stream))
+    if rc:
+        raise MossError(rc, "ms_mlp_predict")
 
 
 class MossError(RuntimeError):
@@ -286,6 +338,23 @@ class Sim:
         s = ms_debug(*[_p(out[f]) for f in _DBG_I + _DBG_F])
         self._check(self.lib.ms_read_debug(self.h, C.byref(s)), "ms_read_debug")
         return out
+
+    def set_lc_log(self, x=None, y=None, n=None):
+        """Log (features, rule decision) of lane-change candidates into device tensors
+        (x bf16 [cap,16], y int32 [cap], n int32 [1]); no arguments turns logging off."""
+        cap = int(y.numel()) if y is not None else 0
+        self._check(self.lib.ms_set_lc_log(self.h, _dp(x), _dp(y), cap, _dp(n)), "ms_set_lc_log")
+
+    def set_lc_model(self, params=None, margin: float = 0.2):
+        """Use the learned lane-change decision (params: 5443 floats, host); None: rule."""
+        a = None if params is None else np.ascontiguousarray(params, np.float32)
+        self._keep_model = a
+        self._check(self.lib.ms_set_lc_model(self.h, _p(a), float(margin)), "ms_set_lc_model")
+
+    def read_lc_stats(self) -> dict:
+        out = np.zeros(12, np.int64)
+        self._check(self.lib.ms_read_lc_stats(self.h, _p(out)), "ms_read_lc_stats")
+        return dict(zip(LC_STAT_NAMES, out.tolist()))
 
     def destroy(self):
         if self.h:

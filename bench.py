@@ -396,6 +396,76 @@ def run_batch(args):
         print(json.dumps(line), flush=True)
 
 
+def run_learned(args):
+    """Learned lane-change surrogate on the large grid: trained on decisions logged from
+    small-grid runs of the rule-based step, then timed against the rule-based step on the
+    same 1M-vehicle workload (L2 flushed before every timed step)."""
+    import numpy as np
+    import torch
+    from paper_2405_12520_b300 import learned, moss, synth
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    params = synth.default_params()
+    t0 = time.perf_counter()
+    x, y = learned.collect(learned.small_grid_runs(args.train_seeds, 100), params, 3600, 8_000_000)
+    t_collect = time.perf_counter() - t0
+    cw, cnt = learned.class_weights(y)
+    theta, info = learned.train(x, y, epochs=10, batch=4096, lr=2e-3, seed=1, class_w=cw)
+    net, dem, desc = workload("grid1m", args.seed)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for name in ("rule", "learned"):
+        sim = moss.Sim(params, stream=stream, n_windows=1)
+        sim.load_network(net)
+        sim.add_vehicles(dem)
+        if name == "learned":
+            sim.set_lc_model(theta, 0.2)
+        sim.step(args.warmup)
+        sim.sync()
+        if name == "learned":
+            sim.set_lc_model(theta, 0.2)   # resets the counters: count the timed steps only
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        nact = []
+        for k in range(args.steps):
+            nact.append(sim.read_metrics(lanes=False)["n_active"])
+            flush.zero_()
+            ev[k][0].record(stream)
+            sim.step(1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        m = sim.read_metrics()
+        out[name] = dict(value=sum(nact) / (ms * 1e-3), ms_per_step=ms / args.steps,
+                         mean_speed=float(m["vsum"].sum() / max(1, m["vcnt"].sum())), err=m["err"])
+        if name == "learned":
+            st = sim.read_lc_stats()
+            out[name]["stats"] = st
+            out[name]["agreement"] = st["agree"] / max(1, st["candidates"])
+            out[name]["fallback_rate"] = st["fallbacks"] / max(1, st["candidates"])
+            for r, rn in enumerate("slr"):
+                row = sum(st[f"conf_{rn}{f}"] for f in "slr")
+                out[name][f"agree_{rn}"] = st[f"conf_{rn}{rn}"] / max(1, row)
+        sim.destroy()
+    L = out["learned"]
+    line = {
+        "metric": "vehicle-steps/s", "value": L["value"], "unit": "vehicle-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": L["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 state, bf16 MLP operands / f32 accumulate",
+        "data": "synthetic", "gpu_launches": 4 * args.steps,
+        "config": {"workload": "learned1m", "description": desc + "; lane-change decisions by the learned MLP",
+                   "l2": "flushed (256 MiB write) before every timed step; each step timed alone",
+                   "train": {"samples": int(x.shape[0]), "class_counts": cnt.tolist(), "seeds": args.train_seeds,
+                             "collect_s": round(t_collect, 1), "adam_steps": info["steps"],
+                             "train_s": round(info["seconds"], 2), "class_w": info["class_w"]}},
+        "learned": L, "rule": out["rule"],
+        "learned_vs_rule": L["value"] / out["rule"]["value"],
+        "mean_speed_rel_diff": abs(L["mean_speed"] - out["rule"]["mean_speed"]) / out["rule"]["mean_speed"],
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -408,6 +478,7 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scenarios", type=int, default=256)
+    ap.add_argument("--train-seeds", type=int, default=200)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -415,6 +486,8 @@ def main():
         run_reference(args)
     elif args.workload.startswith("batch"):
         run_batch(args)
+    elif args.workload.startswith("learned"):
+        run_learned(args)
     else:
         run_ours(args)
 

@@ -647,7 +647,7 @@ __device__ __forceinline__ void lane_speed_sums(const StepArgs &a, const Soa &S,
 // The 16 inputs of the learned lane-change decision (scaled to O(1)): own speed and desired
 // speed, own-path gap and closing speed, current acceleration, allowed direction, target
 // lane gap and closing speed, new follower gap / speed / acceleration, prospective
-// acceleration, old follower speed, distance to the lane end, lane index, old follower gap.
+// acceleration, old follower speed, distance to the lane end, leader speed, old follower gap.
 __device__ __forceinline__ void lc_features(const StepArgs &a, const Soa &S, int i, const Upd &u, const VCtx &c,
                                             float f[MLP_IN]) {
   const float L = a.P.L;
@@ -665,7 +665,7 @@ __device__ __forceinline__ void lc_features(const StepArgs &a, const Soa &S, int
   f[11] = u.lc.anew / a.P.a;
   f[12] = i > c.dl.x ? S.v[i - 1] / 20.f : 0.f;
   f[13] = fminf(c.li.len - c.x, 200.f) / 100.f;
-  f[14] = (float)c.li.idx / 4.f;
+  f[14] = u.own.kind == K_VEH ? u.own.vl / 20.f : (u.own.kind == K_OBST ? 0.f : 1.f);
   f[15] = i > c.dl.x ? fminf((c.x - S.x[i - 1]) - L, 200.f) / 100.f : 2.f;
 }
 

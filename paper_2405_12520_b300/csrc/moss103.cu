@@ -63,9 +63,10 @@ struct Sim {
   int *d_res_code = nullptr, *d_res_nl = nullptr, *d_arr_fill = nullptr;
   int *d_tile_flag = nullptr;
   unsigned long long *d_tile_agg = nullptr, *d_tile_pre = nullptr;
-  int *d_qoff = nullptr, *d_qtrip = nullptr, *d_qhead = nullptr;
+  int *d_qoff = nullptr, *d_qtrip = nullptr, *d_qhead = nullptr, *d_qdue = nullptr;
+  int4 *d_qent = nullptr;
+  int2 *d_qent2 = nullptr;
   int *d_tdep = nullptr, *d_route0 = nullptr, *d_tarr = nullptr;
-  float *d_v0 = nullptr;
   float *d_vsum = nullptr;
   int *d_vcnt = nullptr;
   DebugOut dbg{};
@@ -139,9 +140,10 @@ StepArgs make_args(Sim *s) {
   a.q_off = s->d_qoff;
   a.q_trip = s->d_qtrip;
   a.q_head = s->d_qhead;
+  a.q_due = s->d_qdue;
+  a.q_ent = s->d_qent;
+  a.q_ent2 = s->d_qent2;
   a.trip_tdep = s->d_tdep;
-  a.trip_route0 = s->d_route0;
-  a.trip_v0 = s->d_v0;
   a.t_arr = s->d_tarr;
   a.vsum = s->d_vsum;
   a.vcnt = s->d_vcnt;
@@ -249,6 +251,16 @@ bool lane_links_to(const Sim *s, int l, int e) {
   for (int k = s->succ_off[l]; k < s->succ_off[l + 1]; ++k)
     if (s->succ_edge[k] == e) return true;
   return false;
+}
+
+// queue heads and the departure step of each head trip
+int upload_queues(Sim *s, const std::vector<int> &qhead) {
+  std::vector<int> due(s->n_lanes);
+  for (int l = 0; l < s->n_lanes; ++l)
+    due[l] = qhead[l] < s->h_qoff[l + 1] ? s->h_tdep[s->h_qtrip[qhead[l]]] : 0x7fffffff;
+  CK(cudaMemcpy(s->d_qhead, qhead.data(), sizeof(int) * s->n_lanes, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_qdue, due.data(), sizeof(int) * s->n_lanes, cudaMemcpyHostToDevice));
+  return MS_OK;
 }
 
 int upload_state(Sim *s, const std::vector<int> &ids, const std::vector<int> &lanes,
@@ -605,11 +617,13 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
   DALLOC(s->d_tile_pre, s->n_tiles);
   DALLOC(s->d_qoff, s->n_lanes + 1);
   DALLOC(s->d_qtrip, s->h_qtrip.size());
+  DALLOC(s->d_qent, s->h_qtrip.size());
+  DALLOC(s->d_qent2, s->h_qtrip.size());
   DALLOC(s->d_qhead, s->n_lanes);
+  DALLOC(s->d_qdue, s->n_lanes);
   DALLOC(s->d_tdep, N);
   DALLOC(s->d_route0, N);
   DALLOC(s->d_tarr, N);
-  DALLOC(s->d_v0, N);
   DALLOC(s->d_routes, s->h_routes.size());
   if (s->prm.n_windows > 0) {
     DALLOC(s->d_vsum, (size_t)s->prm.n_windows * s->n_lanes);
@@ -640,11 +654,30 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
   std::vector<int> tarr(n, -1);
   CK(cudaMemcpy(s->d_tarr, tarr.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->d_qoff, s->h_qoff.data(), sizeof(int) * (s->n_lanes + 1), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(s->d_qhead, s->h_qoff.data(), sizeof(int) * s->n_lanes, cudaMemcpyHostToDevice));
+  {
+    int rq = upload_queues(s, std::vector<int>(s->h_qoff.begin(), s->h_qoff.end() - 1));
+    if (rq) return rq;
+  }
   CK(cudaMemcpy(s->d_qtrip, s->h_qtrip.data(), sizeof(int) * s->h_qtrip.size(), cudaMemcpyHostToDevice));
+  {
+    // what a departure writes is known at load time: the trip, its route start, second edge
+    // and next-lane choice on the departure lane, its v0, and when the lane's next trip is due
+    std::vector<int4> qe(s->h_qtrip.size(), make_int4(0, 0, 0, 0));
+    std::vector<int2> qe2(s->h_qtrip.size(), make_int2(0, 0x7fffffff));
+    for (int l = 0; l < s->n_lanes; ++l)
+      for (int j = s->h_qoff[l]; j < s->h_qoff[l + 1]; ++j) {
+        const int trip = s->h_qtrip[j], r0 = s->h_route0[trip];
+        qe[j] = make_int4(trip, r0, s->h_routes[r0 + 1], host_next_choice(s, l, r0));
+        float v0 = s->h_v0[trip];
+        int v0b;
+        std::memcpy(&v0b, &v0, 4);
+        qe2[j] = make_int2(v0b, j + 1 < s->h_qoff[l + 1] ? s->h_tdep[s->h_qtrip[j + 1]] : 0x7fffffff);
+      }
+    CK(cudaMemcpy(s->d_qent, qe.data(), sizeof(int4) * qe.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s->d_qent2, qe2.data(), sizeof(int2) * qe2.size(), cudaMemcpyHostToDevice));
+  }
   CK(cudaMemcpy(s->d_tdep, s->h_tdep.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->d_route0, s->h_route0.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(s->d_v0, s->h_v0.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->d_routes, s->h_routes.data(), sizeof(int) * s->h_routes.size(), cudaMemcpyHostToDevice));
   // launch shapes: persistent grids sized by occupancy
   s->cfg.blk_decide = s->cfg.blk_apply = s->prm.block;
@@ -826,7 +859,10 @@ int ms_write_state(void *sim, const ms_state *in) {
     while (q < s->h_qoff[l + 1] && (active[s->h_qtrip[q]] || in->t_arr[s->h_qtrip[q]] >= 0)) ++q;
     qhead[l] = q;
   }
-  CK(cudaMemcpy(s->d_qhead, qhead.data(), sizeof(int) * s->n_lanes, cudaMemcpyHostToDevice));
+  {
+    int rq = upload_queues(s, qhead);
+    if (rq) return rq;
+  }
   CK(cudaMemcpy(s->d_tarr, in->t_arr, sizeof(int) * s->n_trips, cudaMemcpyHostToDevice));
   return MS_OK;
 }
@@ -1057,6 +1093,7 @@ int snap_take(Sim *s, Snapshot &sn) {
   }
   add(s->d_ctrl, sizeof(DevCtrl));
   add(s->d_qhead, L * 4);
+  add(s->d_qdue, L * 4);
   add(s->d_tarr, N * 4);
   add(s->d_vsum, W * 4);
   add(s->d_vcnt, W * 4);

@@ -135,8 +135,10 @@ struct StepArgs {
   unsigned long long *tile_agg, *tile_pre;
   const int *q_off, *q_trip;
   int *q_head;
-  const int *trip_tdep, *trip_route0;
-  const float *trip_v0;
+  int *q_due;          // per lane: departure step of the FIFO's head trip (INT_MAX if empty)
+  const int4 *q_ent;   // per FIFO entry: {trip, route start, second edge, next-lane choice}
+  const int2 *q_ent2;  // per FIFO entry: {v0 bits, departure step of the lane's next entry or INT_MAX}
+  const int *trip_tdep;
   int *t_arr;
   float *vsum;
   int *vcnt;
@@ -838,7 +840,7 @@ constexpr int LANE_THREADS = 512;
 constexpr int LANE_ITEMS = SCAN_TILE / LANE_THREADS;
 constexpr int LANE_WARPS = LANE_THREADS / 32;
 
-__global__ void __launch_bounds__(LANE_THREADS) k_lanes(StepArgs a) {
+__global__ void __launch_bounds__(LANE_THREADS, 2) k_lanes(StepArgs a) {
   __shared__ int s_tile;
   __shared__ unsigned long long s_wsum[LANE_ITEMS][LANE_WARPS];
   __shared__ unsigned long long s_excl;
@@ -847,7 +849,6 @@ __global__ void __launch_bounds__(LANE_THREADS) k_lanes(StepArgs a) {
   const int tile = s_tile;
   const int t = a.ctrl->t;
   const int p = t & 1;
-  const Soa S = a.A[p];
   const Soa D = a.A[p ^ 1];
   const int4 *dyn = a.dyn[p];
   int4 *ndyn = a.dyn[p ^ 1];
@@ -857,7 +858,7 @@ __global__ void __launch_bounds__(LANE_THREADS) k_lanes(StepArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   int4 d[LANE_ITEMS];
-  int arr[LANE_ITEMS], amk[LANE_ITEMS], qh[LANE_ITEMS], qe[LANE_ITEMS];
+  int arr[LANE_ITEMS], amk[LANE_ITEMS], qdue[LANE_ITEMS];
 #pragma unroll
   for (int k = 0; k < LANE_ITEMS; ++k) {
     const int l = lbase + k * LANE_THREADS;
@@ -865,40 +866,40 @@ __global__ void __launch_bounds__(LANE_THREADS) k_lanes(StepArgs a) {
       d[k] = dyn[l];
       arr[k] = a.arr_cnt[l];
       amk[k] = a.amin[l];
-      qh[k] = a.q_head[l];
-      qe[k] = a.q_off[l + 1];
+      qdue[k] = a.q_due[l];
     } else {
       d[k] = make_int4(0, 0, 0, 0);
       arr[k] = 0;
       amk[k] = AMIN_NONE;
-      qh[k] = qe[k] = 0;
+      qdue[k] = 0x7fffffff;
     }
   }
-  int cnt[LANE_ITEMS], ins[LANE_ITEMS];
+  int cnt[LANE_ITEMS], ins[LANE_ITEMS], qh[LANE_ITEMS];
   unsigned long long val[LANE_ITEMS], incl[LANE_ITEMS];
 #pragma unroll
   for (int k = 0; k < LANE_ITEMS; ++k) {
     const int leavers = count_bits(a.leave, d[k].x, d[k].x + d[k].y);
     ins[k] = 0;
-    if (qh[k] < qe[k]) {
-      const int trip = a.q_trip[qh[k]];
-      if (a.trip_tdep[trip] <= t) {
-        int fl = 0;
-        bool room = true;
-        if (d[k].y > 0) {
-          float m = (S.x[d[k].x] - a.P.L) - room_need;
-          mark(fl, m);
-          room = m >= 0.f;
-        }
-        if (amk[k] != AMIN_NONE) {
-          float m = unfkey(amk[k]) - room_need;
-          mark(fl, m);
-          if (m < 0.f) room = false;
-        }
-        const int l = lbase + k * LANE_THREADS;
-        if (a.P.debug && (fl || a.dbg.arr_flag[l])) a.dbg.trip_flag[trip] = t + 1;
-        ins[k] = room ? 1 : 0;
+    qh[k] = 0;
+    if (qdue[k] <= t) {
+      qh[k] = a.q_head[lbase + k * LANE_THREADS];   // consumed after the scan   // the FIFO's head is due: room behind the lane's tail (its
+      int fl = 0;          // position is in the lane record) and behind every arrival
+      bool room = true;
+      if (d[k].y > 0) {
+        float m = (__int_as_float(d[k].z) - a.P.L) - room_need;
+        mark(fl, m);
+        room = m >= 0.f;
       }
+      if (amk[k] != AMIN_NONE) {
+        float m = unfkey(amk[k]) - room_need;
+        mark(fl, m);
+        if (m < 0.f) room = false;
+      }
+      if (a.P.debug) {
+        const int l = lbase + k * LANE_THREADS;
+        if (fl || a.dbg.arr_flag[l]) a.dbg.trip_flag[a.q_trip[qh[k]]] = t + 1;
+      }
+      ins[k] = room ? 1 : 0;
     }
     cnt[k] = d[k].y - leavers + arr[k] + ins[k];
     val[k] = ((unsigned long long)cnt[k] << 32) | (unsigned)(arr[k] + ins[k]);
@@ -963,6 +964,7 @@ __global__ void __launch_bounds__(LANE_THREADS) k_lanes(StepArgs a) {
   }
   __syncthreads();
   const unsigned long long tile_excl = s_excl;
+  int n_ins = 0;
 #pragma unroll
   for (int k = 0; k < LANE_ITEMS; ++k) {
     const int l = lbase + k * LANE_THREADS;
@@ -973,22 +975,22 @@ __global__ void __launch_bounds__(LANE_THREADS) k_lanes(StepArgs a) {
     // tail fields: the departing vehicle if one enters, else set by k_apply
     ndyn[l] = make_int4(nstart, cnt[k], ins[k] ? __float_as_int(a.P.L) : 0, 0);
     a.arr_start[l] = astart;
-    if (ins[k]) {
-      const int trip = a.q_trip[qh[k]];
+    if (ins[k]) {   // the entry's record was built at load time: {trip, r0, e1, nl}
+      const int4 e = a.q_ent[qh[k]];
+      const int2 e2 = a.q_ent2[qh[k]];
       a.q_head[l] = qh[k] + 1;
-      const int r0 = a.trip_route0[trip];
-      const int e1 = a.routes[r0 + 1];
+      a.q_due[l] = e2.y;
       D.x[nstart] = a.P.L;
       D.v[nstart] = 0.f;
-      D.v0[nstart] = a.trip_v0[trip];
+      D.v0[nstart] = __int_as_float(e2.x);
       D.lane[nstart] = l;
-      D.rp[nstart] = r0;
-      D.nxt[nstart] = e1;
-      D.nl[nstart] = next_choice(a, l, r0, e1);
-      D.id[nstart] = trip;
-      a.bucket[astart + arr[k]] = make_int4(0, __float_as_int(a.P.L), trip, -1);
-      atomicAdd(&a.ctrl->inserted, 1ull);
-      if (a.P.debug) a.dbg.trip_ins[trip] = t + 1;
+      D.rp[nstart] = e.y;
+      D.nxt[nstart] = e.z;
+      D.nl[nstart] = e.w;
+      D.id[nstart] = e.x;
+      a.bucket[astart + arr[k]] = make_int4(0, __float_as_int(a.P.L), e.x, -1);
+      ++n_ins;
+      if (a.P.debug) a.dbg.trip_ins[e.x] = t + 1;
     }
     if (arr[k]) a.arr_cnt[l] = 0;
     if (amk[k] != AMIN_NONE) a.amin[l] = AMIN_NONE;
@@ -1000,6 +1002,8 @@ __global__ void __launch_bounds__(LANE_THREADS) k_lanes(StepArgs a) {
       a.ctrl->t_apply = t;
     }
   }
+  n_ins = __reduce_add_sync(0xffffffffu, n_ins);
+  if (lane == 0 && n_ins) atomicAdd(&a.ctrl->inserted, (unsigned long long)n_ins);
 }
 
 // Arrivals -> lane buckets with their rank among the lane's stayers.  Arrivals are found

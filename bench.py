@@ -32,8 +32,8 @@ sys.path.insert(0, ROOT)
 KERNELS = ("k_decide", "k_lanes", "k_bucket", "k_apply")
 # algorithmic bytes of each kernel: SoA fields it must read / write per vehicle
 # (x, v, v0, lane, rp, nxt, id = 28 B), per lane (counts, starts, queue heads), per mover
-B_DECIDE_VEH = 40   # reads x, v, v0, lane, rp, nxt, id; writes x', v', code
-B_APPLY_VEH = 56    # reads code, x', v', v0, rp, nxt, id; writes the 28-B state
+B_DECIDE_VEH = 48   # reads the 36-B state (x, v, v0, lane, rp, plan word, nl, id); writes x', v', code
+B_APPLY_VEH = 72    # reads code, x', v', v0, rp, plan word, nl, id; writes the 36-B state
 B_LANES_LANE = 40
 B_BUCKET_VEH = 4     # streams the 4-byte result code of every vehicle
 B_BUCKET_MOVER = 36  # per arrival: x, x', id, slot reads + the 16-B bucket record

@@ -73,8 +73,11 @@ typedef struct ms_params {
    signal phases).  succ CSR: for an edge lane, its junction-internal lanes with the exit
    edge each leads to; for an internal lane exactly one entry: its target edge lane and
    that lane's edge.  Requirements (else MS_ERR_ARG): every lane longer than v_max*dt;
-   left/right only within an edge and mutually consistent; internal lanes have one
-   successor and no left/right; signal groups < ctrl_nphase. */
+   the lanes of edge e are edge_lane0[e] + q for q < edge_nlanes[e], numbered from the
+   right: lane_index q, lane_left the lane q + 1, lane_right the lane q - 1 (-1 past the
+   outermost); internal lanes have one successor and no left/right; signal groups <
+   ctrl_nphase.  Limits (else MS_ERR_CAPACITY): at most 10 lanes per edge and 63 links per
+   edge lane (the per-route link plan holds one 6-bit link index per lane of an edge). */
 typedef struct ms_network {
   int n_lanes, n_edges, n_ctrl;
   const float *lane_len;    /* [n_lanes] m */

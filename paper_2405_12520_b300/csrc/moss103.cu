@@ -12,6 +12,7 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "moss103.h"
@@ -46,6 +47,7 @@ struct Sim {
   // trips
   int n_trips = 0;
   std::vector<int> h_route0, h_routes, h_tdep, h_qoff, h_qtrip;
+  std::vector<unsigned long long> h_plan;   // link plan per routes[] entry
   std::vector<float> h_v0;
   // device
   LaneInfo *d_li = nullptr;
@@ -53,6 +55,7 @@ struct Sim {
   int *d_pred = nullptr;
   int4 *d_ctrl4 = nullptr;
   int *d_routes = nullptr;
+  unsigned long long *d_plan = nullptr;
   Soa A[2]{};
   int4 *d_dyn[2]{};
   DevCtrl *d_ctrl = nullptr;
@@ -64,8 +67,7 @@ struct Sim {
   int *d_tile_flag = nullptr;
   unsigned long long *d_tile_agg = nullptr, *d_tile_pre = nullptr;
   int *d_qoff = nullptr, *d_qtrip = nullptr, *d_qhead = nullptr, *d_qdue = nullptr;
-  int4 *d_qent = nullptr;
-  int2 *d_qent2 = nullptr;
+  int4 *d_qent = nullptr, *d_qent2 = nullptr;
   int *d_tdep = nullptr, *d_route0 = nullptr, *d_tarr = nullptr;
   float *d_vsum = nullptr;
   int *d_vcnt = nullptr;
@@ -119,6 +121,7 @@ StepArgs make_args(Sim *s) {
   a.pred = s->d_pred;
   a.ctrl4 = s->d_ctrl4;
   a.routes = s->d_routes;
+  a.plan = s->d_plan;
   a.A[0] = s->A[0];
   a.A[1] = s->A[1];
   a.dyn[0] = s->d_dyn[0];
@@ -217,34 +220,63 @@ int build_graphs(Sim *s) {
   return MS_OK;
 }
 
-// host twin of the kernels' cached next-lane choice (first fan-out link toward en whose
-// target lane links to en2)
+// The fan-out rule: among edge lane l's links toward edge en, the first whose target lane
+// links to en2 (any link if en2 < 0), else the first; returns its index among l's successor
+// entries, -1 if l has no link toward en.
 bool lane_links_to(const Sim *s, int l, int e);
-int host_choose(const Sim *s, int l, int en, int en2) {
+int host_choose_entry(const Sim *s, int l, int en, int en2) {
   int first = -1;
   for (int k = s->succ_off[l]; k < s->succ_off[l + 1]; ++k) {
     if (s->succ_edge[k] != en) continue;
-    int il = s->succ_lane[k];
-    if (first < 0) first = il;
-    if (en2 < 0) return il;
-    if (lane_links_to(s, s->succ_lane[s->succ_off[il]], en2)) return il;
+    const int j = k - s->succ_off[l];
+    if (first < 0) first = j;
+    if (en2 < 0) return j;
+    if (lane_links_to(s, s->succ_lane[s->succ_off[s->succ_lane[k]]], en2)) return j;
   }
   return first;
 }
 
-int host_next_choice(const Sim *s, int lane, int rp) {
+// Link plan word of routes[] entry r (layout in step_kernels.cuh): the fan-out choice of
+// every lane of edge routes[r] toward routes[r + 1], by lane position.
+constexpr unsigned long long PLAN_ALL_NONE = (1ull << (PLAN_BITS * PLAN_LANES)) - 1;
+unsigned long long plan_word(const Sim *s, size_t r) {
   const int *R = s->h_routes.data();
-  const int nxt = R[rp + 1];
-  int c;
-  if (s->lane_edge[lane] >= 0) {
-    if (nxt < 0) return NL_END;
-    c = host_choose(s, lane, nxt, R[rp + 2]);
-  } else {
-    const int e2 = R[rp + 2];
-    if (e2 < 0) return NL_END;
-    c = host_choose(s, s->succ_lane[s->succ_off[lane]], e2, R[rp + 3]);
+  const int e = R[r];
+  if (e < 0 || R[r + 1] < 0) return PLAN_ALL_NONE | PLAN_END;
+  const int en = R[r + 1], en2 = R[r + 2];
+  unsigned long long w = PLAN_ALL_NONE;
+  for (int q = 0; q < s->edge_nlanes[e]; ++q) {
+    const int k = host_choose_entry(s, s->edge_lane0[e] + q, en, en2);
+    if (k >= 0) w &= ~((unsigned long long)(PLAN_NONE ^ (unsigned)k) << (PLAN_BITS * q));
   }
-  return c >= 0 ? c : NL_NONE;
+  return w;
+}
+
+void build_plans(Sim *s) {
+  const size_t n = s->h_routes.size();
+  s->h_plan.assign(n, 0);
+  const unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  const size_t chunk = (n + nt - 1) / nt;
+  std::vector<std::thread> th;
+  for (unsigned k = 0; k < nt; ++k)
+    th.emplace_back([s, k, chunk, n] {
+      for (size_t r = k * chunk; r < std::min(n, (k + 1) * chunk); ++r) s->h_plan[r] = plan_word(s, r);
+    });
+  for (auto &x : th) x.join();
+}
+
+// lane entered at the end of edge lane l (plan word w, l's successor entries)
+int plan_lane(const Sim *s, unsigned long long w, int l) {
+  if (w & PLAN_END) return NL_END;
+  const unsigned k = plan_nib(w, l - s->edge_lane0[s->lane_edge[l]]);
+  return k == PLAN_NONE ? NL_NONE : s->succ_lane[s->succ_off[l] + k];
+}
+
+// the cached next-lane choice of a vehicle on `lane` at route entry rp (on an internal lane:
+// the choice at the end of its target lane, from the plan of the target's edge)
+int host_next_choice(const Sim *s, int lane, int rp) {
+  if (s->lane_edge[lane] >= 0) return plan_lane(s, s->h_plan[rp], lane);
+  return plan_lane(s, s->h_plan[rp + 1], s->succ_lane[s->succ_off[lane]]);
 }
 
 bool lane_links_to(const Sim *s, int l, int e) {
@@ -270,7 +302,8 @@ int upload_state(Sim *s, const std::vector<int> &ids, const std::vector<int> &la
   const int n = (int)ids.size();
   if (n > s->n_trips) return fail(s, MS_ERR_CAPACITY, "more active vehicles than trips");
   std::vector<float> v0(n);
-  std::vector<int> rp(n), nxt(n), nlc(n);
+  std::vector<int> rp(n), nlc(n);
+  std::vector<unsigned long long> pl(n);
   std::vector<int> cnt(s->n_lanes, 0);
   std::vector<char> seen(s->n_trips, 0);
   for (int i = 0; i < n; ++i) {
@@ -311,7 +344,7 @@ int upload_state(Sim *s, const std::vector<int> &ids, const std::vector<int> &la
     }
     v0[i] = s->h_v0[id];
     rp[i] = r0 + ri;
-    nxt[i] = s->h_routes[r0 + ri + 1];
+    pl[i] = s->h_plan[r0 + ri];
     nlc[i] = host_next_choice(s, l, r0 + ri);
     cnt[l]++;
   }
@@ -335,7 +368,7 @@ int upload_state(Sim *s, const std::vector<int> &ids, const std::vector<int> &la
     CK(cudaMemcpyAsync(B.v0, v0.data(), n * sizeof(float), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(B.lane, lanes.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(B.rp, rp.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(B.nxt, nxt.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(B.pl, pl.data(), n * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(B.nl, nlc.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(B.id, ids.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
   }
@@ -444,7 +477,7 @@ int ms_load_network(void *sim, const ms_network *net) {
       if (s->lane_left[l] >= 0 || s->lane_right[l] >= 0) return fail(s, MS_ERR_ARG, "internal lane with neighbours");
       npred[s->succ_lane[s->succ_off[l]]]++;
     } else {
-      if (ns > 255) return fail(s, MS_ERR_ARG, "more than 255 successors");
+      if (ns > (int)PLAN_NONE) return fail(s, MS_ERR_CAPACITY, "an edge lane has more than 63 lane links");
       int lf = s->lane_left[l], rt = s->lane_right[l];
       if (lf >= L || rt >= L) return fail(s, MS_ERR_ARG, "left/right out of range");
       if (lf >= 0 && (s->lane_edge[lf] != e || s->lane_right[lf] != l)) return fail(s, MS_ERR_ARG, "left/right inconsistent");
@@ -469,11 +502,32 @@ int ms_load_network(void *sim, const ms_network *net) {
     li[l].ctrl = c;
     li[l].n_succ = (unsigned char)(e < 0 ? 1 : ns);
     li[l].group = (unsigned char)(c >= 0 ? net->lane_group[l] : 0);
-    li[l].idx = (unsigned char)std::max(0, std::min(255, net->lane_index[l]));
   }
-  for (int e = 0; e < E; ++e)
-    if (s->edge_nlanes[e] <= 0 || s->edge_lane0[e] < 0 || s->edge_lane0[e] + s->edge_nlanes[e] > L)
-      return fail(s, MS_ERR_ARG, "edge lanes out of range");
+  // an edge's lanes are lanes edge_lane0 .. edge_lane0 + nlanes - 1, numbered from the right:
+  // index q = l - edge_lane0, left neighbour q + 1, right neighbour q - 1
+  for (int e = 0; e < E; ++e) {
+    const int l0 = s->edge_lane0[e], ne = s->edge_nlanes[e];
+    if (ne <= 0 || l0 < 0 || l0 + ne > L) return fail(s, MS_ERR_ARG, "edge lanes out of range");
+    if (ne > PLAN_LANES) return fail(s, MS_ERR_CAPACITY, "an edge has more than 10 lanes");
+    for (int q = 0; q < ne; ++q) {
+      const int l = l0 + q;
+      if (s->lane_edge[l] != e || net->lane_index[l] != q || s->lane_left[l] != (q + 1 < ne ? l + 1 : -1) ||
+          s->lane_right[l] != (q > 0 ? l - 1 : -1))
+        return fail(s, MS_ERR_ARG, "lanes of edge " + std::to_string(e) +
+                                       " must be edge_lane0 + q with lane_index q, left q + 1, right q - 1");
+    }
+  }
+  for (int l = 0; l < L; ++l) {
+    const int e = s->lane_edge[l];
+    if (e >= 0 && (l < s->edge_lane0[e] || l >= s->edge_lane0[e] + s->edge_nlanes[e]))
+      return fail(s, MS_ERR_ARG, "lane " + std::to_string(l) + " lies outside its edge's lane range");
+  }
+  // plan position: an edge lane's index across its edge; an internal lane's target's index
+  for (int l = 0; l < L; ++l) {
+    const int e = s->lane_edge[l];
+    const int q = e >= 0 ? l - s->edge_lane0[e] : s->succ_lane[s->succ_off[l]] - s->edge_lane0[s->lane_edge[s->succ_lane[s->succ_off[l]]]];
+    li[l].idx = (unsigned char)q;
+  }
   std::vector<int> pred_off(L + 1, 0);
   for (int l = 0; l < L; ++l) {
     if (npred[l] > 255) return fail(s, MS_ERR_ARG, "more than 255 feeders");
@@ -544,6 +598,7 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
     s->h_routes.push_back(-1);
     if (s->h_routes.size() > (size_t)0x7fff0000) return fail(s, MS_ERR_CAPACITY, "routes too long");
   }
+  build_plans(s);
   // placed vehicles, sorted by (lane, x, id)
   std::vector<int> placed;
   if (veh->lane) {
@@ -595,7 +650,7 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
   const int N = n;
   for (int b = 0; b < 2; ++b) {
     DALLOC(s->A[b].x, N); DALLOC(s->A[b].v, N); DALLOC(s->A[b].v0, N);
-    DALLOC(s->A[b].lane, N); DALLOC(s->A[b].rp, N); DALLOC(s->A[b].nxt, N); DALLOC(s->A[b].nl, N);
+    DALLOC(s->A[b].lane, N); DALLOC(s->A[b].rp, N); DALLOC(s->A[b].pl, N); DALLOC(s->A[b].nl, N);
     DALLOC(s->A[b].id, N);
     DALLOC(s->d_dyn[b], s->n_lanes);
   }
@@ -619,6 +674,7 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
   DALLOC(s->d_qtrip, s->h_qtrip.size());
   DALLOC(s->d_qent, s->h_qtrip.size());
   DALLOC(s->d_qent2, s->h_qtrip.size());
+  DALLOC(s->d_plan, s->h_plan.size());
   DALLOC(s->d_qhead, s->n_lanes);
   DALLOC(s->d_qdue, s->n_lanes);
   DALLOC(s->d_tdep, N);
@@ -663,22 +719,25 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
     // what a departure writes is known at load time: the trip, its route start, second edge
     // and next-lane choice on the departure lane, its v0, and when the lane's next trip is due
     std::vector<int4> qe(s->h_qtrip.size(), make_int4(0, 0, 0, 0));
-    std::vector<int2> qe2(s->h_qtrip.size(), make_int2(0, 0x7fffffff));
+    std::vector<int4> qe2(s->h_qtrip.size(), make_int4(0, 0, 0x7fffffff, 0));
     for (int l = 0; l < s->n_lanes; ++l)
       for (int j = s->h_qoff[l]; j < s->h_qoff[l + 1]; ++j) {
         const int trip = s->h_qtrip[j], r0 = s->h_route0[trip];
-        qe[j] = make_int4(trip, r0, s->h_routes[r0 + 1], host_next_choice(s, l, r0));
         float v0 = s->h_v0[trip];
         int v0b;
         std::memcpy(&v0b, &v0, 4);
-        qe2[j] = make_int2(v0b, j + 1 < s->h_qoff[l + 1] ? s->h_tdep[s->h_qtrip[j + 1]] : 0x7fffffff);
+        qe[j] = make_int4(trip, r0, host_next_choice(s, l, r0), v0b);
+        const unsigned long long w = s->h_plan[r0];
+        qe2[j] = make_int4((int)(unsigned)(w & 0xffffffffu), (int)(unsigned)(w >> 32),
+                           j + 1 < s->h_qoff[l + 1] ? s->h_tdep[s->h_qtrip[j + 1]] : 0x7fffffff, 0);
       }
     CK(cudaMemcpy(s->d_qent, qe.data(), sizeof(int4) * qe.size(), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(s->d_qent2, qe2.data(), sizeof(int2) * qe2.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s->d_qent2, qe2.data(), sizeof(int4) * qe2.size(), cudaMemcpyHostToDevice));
   }
   CK(cudaMemcpy(s->d_tdep, s->h_tdep.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->d_route0, s->h_route0.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->d_routes, s->h_routes.data(), sizeof(int) * s->h_routes.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_plan, s->h_plan.data(), sizeof(unsigned long long) * s->h_plan.size(), cudaMemcpyHostToDevice));
   // launch shapes: persistent grids sized by occupancy
   s->cfg.blk_decide = s->cfg.blk_apply = s->prm.block;
   s->cfg.blk_bucket = 256;
@@ -799,7 +858,10 @@ int ms_read_state(void *sim, ms_state *out, int device) {
   out->n_active = n;
   if (out->capacity < n) return fail(s, MS_ERR_CAPACITY, "state capacity too small");
   const Soa &B = s->A[p];
-  std::vector<int> ids(n), rp(n);
+  // host scratch only for the fields derived on the host (route index, trip status)
+  const bool host_ridx = !device && out->route_idx;
+  const bool need_ids = host_ridx || out->trip_status;
+  std::vector<int> ids(need_ids ? n : 0), rp(host_ridx ? n : 0);
   if (n) {
     cudaMemcpyKind k = device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (out->x) CK(cudaMemcpyAsync(out->x, B.x, n * sizeof(float), k, s->stream));
@@ -811,18 +873,14 @@ int ms_read_state(void *sim, ms_state *out, int device) {
                                                                            out->route_idx, nullptr, n);
       CK(cudaGetLastError());
     }
-    if (!device && (out->route_idx || out->trip_status)) {
-      CK(cudaMemcpyAsync(ids.data(), B.id, n * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
-      CK(cudaMemcpyAsync(rp.data(), B.rp, n * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
-    } else if (out->trip_status) {
-      CK(cudaMemcpyAsync(ids.data(), B.id, n * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
-    }
+    if (need_ids) CK(cudaMemcpyAsync(ids.data(), B.id, n * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    if (host_ridx) CK(cudaMemcpyAsync(rp.data(), B.rp, n * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   }
-  std::vector<int> tarr(s->n_trips);
+  std::vector<int> tarr(out->t_arr || out->trip_status ? s->n_trips : 0);
   if (out->t_arr || out->trip_status)
     CK(cudaMemcpyAsync(tarr.data(), s->d_tarr, s->n_trips * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
-  if (!device && out->route_idx)
+  if (host_ridx)
     for (int i = 0; i < n; ++i) out->route_idx[i] = rp[i] - s->h_route0[ids[i]];
   if (out->t_arr) std::memcpy(out->t_arr, tarr.data(), s->n_trips * sizeof(int));
   if (out->trip_status) {
@@ -1088,7 +1146,7 @@ int snap_take(Sim *s, Snapshot &sn) {
   auto add = [&](void *p, size_t bytes) { if (p && bytes) sn.regions.push_back({p, bytes}); };
   for (int b = 0; b < 2; ++b) {
     add(s->A[b].x, N * 4); add(s->A[b].v, N * 4); add(s->A[b].v0, N * 4); add(s->A[b].lane, N * 4);
-    add(s->A[b].rp, N * 4); add(s->A[b].nxt, N * 4); add(s->A[b].nl, N * 4); add(s->A[b].id, N * 4);
+    add(s->A[b].rp, N * 4); add(s->A[b].pl, N * 8); add(s->A[b].nl, N * 4); add(s->A[b].id, N * 4);
     add(s->d_dyn[b], L * sizeof(int4));
   }
   add(s->d_ctrl, sizeof(DevCtrl));

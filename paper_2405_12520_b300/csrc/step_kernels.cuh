@@ -53,7 +53,9 @@ struct __align__(32) LaneInfo {
   int succ;     // edge lane: first entry in succ[]; internal lane: its target lane
   int pred;     // first entry in pred[] of the internal lanes feeding this lane
   int ctrl;     // signal controller at the lane end, -1 none
-  unsigned char n_succ, n_pred, group, idx;
+  unsigned char n_succ, n_pred, group;
+  unsigned char idx;   // edge lane: position across its edge (0 = rightmost, by the right
+                       // links); internal lane: its target lane's position
 };
 
 struct DevParams {
@@ -65,15 +67,37 @@ struct DevParams {
   int id_base;           // added to trip ids in the lane-change gate hash
 };
 
+// Link plan of a route entry r (edge e = routes[r]), one 64-bit word built at load time:
+// field q (bits 6q..6q+5) is, for the lane at position q of e, the index among that lane's
+// successor entries of the link the trip takes toward routes[r + 1] (the first such link
+// whose target lane serves routes[r + 2], else the first one), PLAN_NONE if the lane has no
+// link toward it; bit 63 (PLAN_END) is set when the route ends on e.  It turns every
+// link search of the step (next-lane choice, mandatory and discretionary lane-change
+// checks, look-ahead hops) into one field extract and at most one successor load.
+constexpr int PLAN_BITS = 6;
+constexpr unsigned PLAN_NONE = (1u << PLAN_BITS) - 1u;   // also bounds a lane's link count
+constexpr unsigned long long PLAN_END = 1ull << 63;
+constexpr int PLAN_LANES = 10;                            // lanes per edge
+__host__ __device__ __forceinline__ unsigned plan_nib(unsigned long long pl, int q) {
+  return (unsigned)(pl >> (PLAN_BITS * q)) & PLAN_NONE;
+}
+// lane at position q of the plan's edge can continue the route (the route ends here, or
+// the lane has a link toward the next edge)
+__device__ __forceinline__ bool plan_ok(unsigned long long pl, int q) {
+  return (pl & PLAN_END) || plan_nib(pl, q) != PLAN_NONE;
+}
+
 // Vehicle state, sorted by (lane, x).  rp: index into routes[] of the current edge (the
-// approach edge on an internal lane); nxt = routes[rp + 1]; nl: the lane the vehicle will
-// enter at the end of its current edge lane (for an internal lane: at the end of its
-// target lane); NL_END (-1) if the route ends on that edge, NL_NONE (-2) if that lane has no
-// link toward the next route edge -- cached so that sensing needs no route or link lookups.
+// approach edge on an internal lane); pl = plan[rp]; nl: the lane the vehicle will enter at
+// the end of its current edge lane (for an internal lane: at the end of its target lane);
+// NL_END (-1) if the route ends on that edge, NL_NONE (-2) if that lane has no link toward
+// the next route edge -- cached so that sensing needs no route or link lookups.
 constexpr int NL_END = -1, NL_NONE = -2;
 struct Soa {
   float *x, *v, *v0;
-  int *lane, *rp, *nxt, *nl, *id;
+  int *lane, *rp;
+  unsigned long long *pl;
+  int *nl, *id;
 };
 
 struct DevCtrl {
@@ -121,6 +145,7 @@ struct StepArgs {
   const int *pred;
   const int4 *ctrl4;   // {offset, green, yellow, nphase}
   const int *routes;   // per trip: its edges then -1
+  const unsigned long long *plan;   // link plan per routes[] entry
   Soa A[2];
   int4 *dyn[2];        // per lane {first index, count, tail x, tail v} for buffer 0 / 1
   DevCtrl *ctrl;
@@ -136,8 +161,9 @@ struct StepArgs {
   const int *q_off, *q_trip;
   int *q_head;
   int *q_due;          // per lane: departure step of the FIFO's head trip (INT_MAX if empty)
-  const int4 *q_ent;   // per FIFO entry: {trip, route start, second edge, next-lane choice}
-  const int2 *q_ent2;  // per FIFO entry: {v0 bits, departure step of the lane's next entry or INT_MAX}
+  const int4 *q_ent;   // per FIFO entry: {trip, route start, next-lane choice, v0 bits}
+  const int4 *q_ent2;  // per FIFO entry: {plan of the first edge (lo, hi), departure step
+                       // of the lane's next entry or INT_MAX, 0}
   const int *trip_tdep;
   int *t_arr;
   float *vsum;
@@ -198,51 +224,12 @@ __device__ __forceinline__ int sig_state(const StepArgs &a, const LaneInfo &li, 
   return (tau % gy) < c.y ? SIG_G : SIG_Y;
 }
 
-// successor entries [b, b + n) contain a link toward edge en (en < 0: route ends: true)
-__device__ __forceinline__ bool links_to(const StepArgs &a, int b, int n, int en) {
-  if (en < 0) return true;
-  for (int k = 0; k < n; ++k)
-    if (a.succ[b + k].y == en) return true;
-  return false;
-}
-
-// edge lane li has a link toward edge en
-__device__ __forceinline__ bool connects(const StepArgs &a, const LaneInfo &li, int en) {
-  return links_to(a, li.succ, li.n_succ, en);
-}
-
-// fan-out link toward en among successor entries [b, b + n): the first whose target lane
-// serves en2 (the internal lane's record carries its target's successor range)
-__device__ __forceinline__ int choose_link(const StepArgs &a, int b, int n, int en, int en2) {
-  int first = -1;
-  for (int k = 0; k < n; ++k) {
-    int2 s = a.succ[b + k];
-    if (s.y != en) continue;
-    if (first < 0) first = s.x;
-    if (en2 < 0) return s.x;
-    const LaneInfo il = a.li[s.x];
-    if (links_to(a, il.left, il.right, en2)) return s.x;
-  }
-  return first;
-}
-
-__device__ __forceinline__ int choose_succ(const StepArgs &a, const LaneInfo &li, int en, int en2) {
-  return choose_link(a, li.succ, li.n_succ, en, en2);
-}
-
-// The cached next-lane choice of a vehicle on `lane` with route index rp, next edge nxt.
-__device__ __forceinline__ int next_choice(const StepArgs &a, int lane, int rp, int nxt) {
-  const LaneInfo li = a.li[lane];
-  int c;
-  if (li.edge >= 0) {
-    if (nxt < 0) return NL_END;
-    c = choose_succ(a, li, nxt, a.routes[rp + 2]);
-  } else {
-    const int e2 = a.routes[rp + 2];   // edge after the target lane's edge
-    if (e2 < 0) return NL_END;
-    c = choose_link(a, li.left, li.right, e2, a.routes[rp + 3]);
-  }
-  return c >= 0 ? c : NL_NONE;
+// Lane entered at the end of the edge lane at plan position q with successor entries from
+// sb, following plan word pl: NL_END if the route ends there, NL_NONE if it has no link.
+__device__ __forceinline__ int plan_next(const StepArgs &a, unsigned long long pl, int q, int sb) {
+  if (pl & PLAN_END) return NL_END;
+  const unsigned k = plan_nib(pl, q);
+  return k == PLAN_NONE ? NL_NONE : a.succ[sb + k].x;
 }
 
 struct Lead {
@@ -262,7 +249,7 @@ struct LC {
 };
 
 struct Upd {
-  int kind, lane, rp, nxt;
+  int kind, lane, rp;
   float x, v, a_use, a_own;
   Lead own;
   LC lc;
@@ -273,7 +260,7 @@ struct Upd {
 // (rearmost vehicle of the lane) are valid when count > 0.
 __device__ __forceinline__ Lead own_leader(const StepArgs &a, const Soa &S, const int4 *dyn, int i,
                                            int l, const LaneInfo &li, int4 d, float x, float v,
-                                           int rp, int en, int nlc, int4 pf_dyn, const LaneInfo &pf_li,
+                                           int rp, int nlc, int4 pf_dyn, const LaneInfo &pf_li,
                                            int myid, int t, int &flag) {
   const DevParams &P = a.P;
   Lead r{K_FREE, 0.f, 0.f, -1, 0};
@@ -281,9 +268,8 @@ __device__ __forceinline__ Lead own_leader(const StepArgs &a, const Soa &S, cons
     int j = i + 1;
     r = Lead{K_VEH, (S.x[j] - x) - P.L, S.v[j], j, 0};
   } else {
-    constexpr int E_LAZY = -3;    // next route edge not read yet
     float dist = li.len - x;
-    int ri = rp, e_next = en;
+    int ri = rp;
     bool cached = true;   // the first edge-lane hop uses the vehicle's cached choice
     LaneInfo lc = li;
     for (int hop = 0;; ++hop) {
@@ -298,9 +284,8 @@ __device__ __forceinline__ Lead own_leader(const StepArgs &a, const Soa &S, cons
           nxt = nlc;
           pre = nxt >= 0;
         } else {
-          if (e_next == E_LAZY) e_next = a.routes[ri + 1];
-          if (e_next < 0) break;   // destination edge: open end
-          nxt = choose_succ(a, lc, e_next, a.routes[ri + 2]);
+          nxt = plan_next(a, a.plan[ri], lc.idx, lc.succ);
+          if (nxt == NL_END) break;   // destination edge: open end
         }
         bool stop = nxt < 0;
         if (!stop) {
@@ -320,7 +305,6 @@ __device__ __forceinline__ Lead own_leader(const StepArgs &a, const Soa &S, cons
       } else {
         nxt = lc.succ;
         ri += 1;
-        e_next = E_LAZY;
       }
       if (hop + 1 >= HOP_CAP) {
         r = Lead{K_OBST, dist, 0.f, -1, hop == 0};
@@ -367,11 +351,11 @@ __device__ __forceinline__ Lead own_leader(const StepArgs &a, const Soa &S, cons
   return r;
 }
 
-// target lane end blocks a vehicle at (x, v) heading for edge en
-__device__ __forceinline__ bool end_blocks(const StepArgs &a, const LaneInfo &lt, int en, float x,
-                                           float v, int t, int &flag) {
-  if (en < 0) return false;
-  if (!connects(a, lt, en)) return true;
+// target lane end blocks a vehicle at (x, v) following plan word pl
+__device__ __forceinline__ bool end_blocks(const StepArgs &a, const LaneInfo &lt, unsigned long long pl,
+                                           float x, float v, int t, int &flag) {
+  if (pl & PLAN_END) return false;
+  if (plan_nib(pl, lt.idx) == PLAN_NONE) return true;
   int sg = sig_state(a, lt, t);
   if (sg == SIG_R) return true;
   if (sg == SIG_Y) {
@@ -384,7 +368,8 @@ __device__ __forceinline__ bool end_blocks(const StepArgs &a, const LaneInfo &lt
 
 __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const int4 *dyn, int i,
                                           int l, const LaneInfo &li, float x, float v, float v0,
-                                          int en, int nlc, int4 dl, int myid, int t, const Lead &own,
+                                          unsigned long long pl, int nlc, int4 dl, int myid, int t,
+                                          const Lead &own,
                                           float a_c, int &flag) {
   const DevParams &P = a.P;
   LC r{};
@@ -396,13 +381,13 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
   if (tau < 0) return r;
   const bool mand = nlc == NL_NONE;   // own lane has no link toward the next edge
   r.mand = mand;
-  if (mand) {
-    int dr = 1 << 30, dl = 1 << 30, k = 1;
-    for (int q = li.right; q >= 0; q = a.li[q].right, ++k)
-      if (connects(a, a.li[q], en)) { dr = k; break; }
-    k = 1;
-    for (int q = li.left; q >= 0; q = a.li[q].left, ++k)
-      if (connects(a, a.li[q], en)) { dl = k; break; }
+  if (mand) {   // nearest lane on each side with a link toward the next edge
+    const int q = li.idx;
+    int dr = 1 << 30, dl = 1 << 30;
+    for (int k = 1; k <= q; ++k)
+      if (plan_nib(pl, q - k) != PLAN_NONE) { dr = k; break; }
+    for (int k = 1; q + k < PLAN_LANES; ++k)
+      if (plan_nib(pl, q + k) != PLAN_NONE) { dl = k; break; }
     if (dr == (1 << 30) && dl == (1 << 30)) return r;
     int want = dr <= dl ? -1 : +1;
     if (want != step_dir) return r;
@@ -411,7 +396,7 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
   if (x < P.x_lc_min) return r;
   const LaneInfo lt = a.li[tau];
   if (!mand) {
-    if (!connects(a, lt, en)) return r;
+    if (!plan_ok(pl, lt.idx)) return r;
     mark(flag, (li.len - x) - P.x_lc_end);
     if (li.len - x < P.x_lc_end) return r;
     unsigned long long h = splitmix64(P.seed ^ ((unsigned long long)(unsigned)t << 32) ^
@@ -433,7 +418,7 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
     r.tkind = K_VEH;
     r.tgap = (S.x[Lt] - x) - P.L;
     r.tvl = S.v[Lt];
-  } else if (end_blocks(a, lt, en, x, v, t, flag)) {
+  } else if (end_blocks(a, lt, pl, x, v, t, flag)) {
     r.tkind = K_OBST;
     r.tgap = li.len - x;
     r.tvl = 0.f;
@@ -468,7 +453,7 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
       float aF_old;
       if (Lt >= 0)
         aF_old = idm(P, vF, v0F, true, (S.x[Lt] - xF) - P.L, S.v[Lt]);
-      else if (end_blocks(a, lt, en, xF, vF, t, flag))
+      else if (end_blocks(a, lt, pl, xF, vF, t, flag))
         aF_old = idm(P, vF, v0F, true, li.len - xF, 0.f);
       else
         aF_old = idm(P, vF, v0F, false, 0.f, 0.f);
@@ -493,7 +478,8 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
 
 // Per-vehicle context of one step (snapshot values the update reuses)
 struct VCtx {
-  int l, rp, en, nlc;
+  int l, rp, nlc;
+  unsigned long long pl;
   float x, v, v0;
   LaneInfo li;
   int4 dl;
@@ -510,7 +496,7 @@ __device__ __forceinline__ Upd vehicle_sense(const StepArgs &a, const Soa &S, co
   c.v = S.v[i];
   c.v0 = S.v0[i];
   c.rp = S.rp[i];
-  c.en = S.nxt[i];
+  c.pl = S.pl[i];
   c.nlc = S.nl[i];
   const int myid = S.id[i];
   c.li = a.li[c.l];
@@ -522,9 +508,9 @@ __device__ __forceinline__ Upd vehicle_sense(const StepArgs &a, const Soa &S, co
     pf_dyn = dyn[c.nlc];
     pf_li = a.li[c.nlc];
   }
-  u.own = own_leader(a, S, dyn, i, c.l, c.li, c.dl, c.x, c.v, c.rp, c.en, c.nlc, pf_dyn, pf_li, myid, t, u.flag);
+  u.own = own_leader(a, S, dyn, i, c.l, c.li, c.dl, c.x, c.v, c.rp, c.nlc, pf_dyn, pf_li, myid, t, u.flag);
   u.a_own = idm(P, c.v, c.v0, u.own.kind != K_FREE, u.own.gap, u.own.vl);
-  u.lc = lane_change(a, S, dyn, i, c.l, c.li, c.x, c.v, c.v0, c.en, c.nlc, c.dl, myid, t, u.own, u.a_own, u.flag);
+  u.lc = lane_change(a, S, dyn, i, c.l, c.li, c.x, c.v, c.v0, c.pl, c.nlc, c.dl, myid, t, u.own, u.a_own, u.flag);
   return u;
 }
 
@@ -559,11 +545,10 @@ __device__ __forceinline__ void vehicle_move(const StepArgs &a, Upd &u, const VC
   u.kind = dir ? U_CHANGE : U_STAY;
   u.lane = dir ? (dir > 0 ? li.left : li.right) : c.l;
   u.rp = c.rp;
-  u.nxt = c.en;
   if (!dir) {
     mark(u.flag, xn - li.len);
     if (xn > li.len) {
-      if (li.edge >= 0 && c.en < 0) {
+      if (li.edge >= 0 && (c.pl & PLAN_END)) {
         u.kind = U_RETIRE;
       } else {
         xn -= li.len;
@@ -574,7 +559,6 @@ __device__ __forceinline__ void vehicle_move(const StepArgs &a, Upd &u, const VC
         } else {
           nl = li.succ;
           u.rp = c.rp + 1;
-          u.nxt = a.routes[c.rp + 2];
         }
         if (nl < 0 || xn > a.li[nl].len) {
           atomicOr(&a.ctrl->err, DEV_HOP);
@@ -582,7 +566,6 @@ __device__ __forceinline__ void vehicle_move(const StepArgs &a, Upd &u, const VC
           xn = li.len;
           u.kind = U_STAY;
           u.rp = c.rp;
-          u.nxt = c.en;
         }
         u.lane = nl;
       }
@@ -786,7 +769,7 @@ __global__ void __launch_bounds__(512, 2) k_decide_t(StepArgs a) {
       int kind = u.kind == U_STAY ? C_STAY
                : u.kind == U_CHANGE ? C_CHANGE
                : u.kind == U_RETIRE ? C_RETIRE
-               : (u.rp != S.rp[i] ? C_TRANSFER_ROUTE : C_TRANSFER);
+               : (u.rp != c.rp ? C_TRANSFER_ROUTE : C_TRANSFER);
       a.res_x[i] = u.x;
       a.res_v[i] = u.v;
       a.res_code[i] = (kind << CODE_LANE_BITS) | (u.kind == U_RETIRE ? 0 : u.lane);
@@ -816,8 +799,13 @@ __global__ void __launch_bounds__(512, 2) k_decide_t(StepArgs a) {
       atomicAdd(&a.arr_cnt[u.lane], 1);
       atomicMin(&a.amin[u.lane], fkey(u.x - a.P.L));
       // the arrival's cached next-lane choice for its new lane (internal -> edge lane keeps
-      // the choice it already made for that target lane)
-      if (u.rp == S.rp[i]) a.res_code_nl[i] = next_choice(a, u.lane, u.rp, u.nxt);
+      // the choice it already made for that target lane): a lane change follows the plan
+      // of its own edge, an internal lane the plan of its target lane's edge
+      if (u.rp == c.rp) {
+        const LaneInfo ln = a.li[u.lane];
+        const unsigned long long pn = a.plan[c.rp + 1];
+        a.res_code_nl[i] = ln.edge >= 0 ? plan_next(a, c.pl, ln.idx, ln.succ) : plan_next(a, pn, ln.idx, ln.left);
+      }
       if (a.P.debug && u.flag) a.dbg.arr_flag[u.lane] = 1;
     }
   }
@@ -975,18 +963,18 @@ __global__ void __launch_bounds__(LANE_THREADS, 2) k_lanes(StepArgs a) {
     // tail fields: the departing vehicle if one enters, else set by k_apply
     ndyn[l] = make_int4(nstart, cnt[k], ins[k] ? __float_as_int(a.P.L) : 0, 0);
     a.arr_start[l] = astart;
-    if (ins[k]) {   // the entry's record was built at load time: {trip, r0, e1, nl}
+    if (ins[k]) {   // the entry's record was built at load time
       const int4 e = a.q_ent[qh[k]];
-      const int2 e2 = a.q_ent2[qh[k]];
+      const int4 e2 = a.q_ent2[qh[k]];
       a.q_head[l] = qh[k] + 1;
-      a.q_due[l] = e2.y;
+      a.q_due[l] = e2.z;
       D.x[nstart] = a.P.L;
       D.v[nstart] = 0.f;
-      D.v0[nstart] = __int_as_float(e2.x);
+      D.v0[nstart] = __int_as_float(e.w);
       D.lane[nstart] = l;
       D.rp[nstart] = e.y;
-      D.nxt[nstart] = e.z;
-      D.nl[nstart] = e.w;
+      D.pl[nstart] = (unsigned long long)(unsigned)e2.x | ((unsigned long long)(unsigned)e2.y << 32);
+      D.nl[nstart] = e.z;
       D.id[nstart] = e.x;
       a.bucket[astart + arr[k]] = make_int4(0, __float_as_int(a.P.L), e.x, -1);
       ++n_ins;
@@ -1111,11 +1099,12 @@ __global__ void k_apply(StepArgs a) {
       for (int q = bs; q < be; ++q) rank += bucket_less(a.bucket[q], me);
       pos = ndyn[nl].x + me.x + rank;
     }
-    int rp = S.rp[i], nxt = S.nxt[i], nlc = S.nl[i];
+    int rp = S.rp[i], nlc = S.nl[i];
+    unsigned long long pl = S.pl[i];
     if (kind != C_STAY) a.arr_fill[nl] = 0;   // every arrival resets it; k_bucket is done
     if (kind == C_TRANSFER_ROUTE) {   // internal lane -> edge lane: next route edge; the
       rp += 1;                        // cached choice was made for this target lane
-      nxt = a.routes[rp + 1];
+      pl = a.plan[rp];
     } else if (kind != C_STAY) {      // lane change or edge lane -> internal lane
       nlc = a.res_code_nl[i];
     }
@@ -1127,7 +1116,7 @@ __global__ void k_apply(StepArgs a) {
     D.v0[pos] = S.v0[i];
     D.lane[pos] = nl;
     D.rp[pos] = rp;
-    D.nxt[pos] = nxt;
+    D.pl[pos] = pl;
     D.nl[pos] = nlc;
     D.id[pos] = id;
   }

@@ -195,6 +195,26 @@ def test_invalid_inputs_are_rejected():
     s2 = moss.Sim(P)
     with pytest.raises(moss.MossError):
         s2.load_network(short)
+    # an edge's lanes numbered from the left instead of the right: consistent left/right
+    # links, but not the layout the lane-change search and the link plan index by
+    flipped = netkit.line(3, 300.0, 2)
+    l0 = int(flipped.edge_lane0[0])
+    flipped.lane_left[l0], flipped.lane_right[l0] = -1, l0 + 1
+    flipped.lane_left[l0 + 1], flipped.lane_right[l0 + 1] = l0, -1
+    flipped.lane_index[l0], flipped.lane_index[l0 + 1] = 1, 0
+    with pytest.raises(moss.MossError) as e:
+        moss.Sim(P).load_network(flipped)
+    assert e.value.code == moss.MS_ERR_ARG and "lane_index q" in str(e.value)
+    wide = netkit.line(2, 300.0, 11)   # 11 lanes per edge: beyond the link plan's 10 fields
+    with pytest.raises(moss.MossError) as e:
+        moss.Sim(P).load_network(wide)
+    assert e.value.code == moss.MS_ERR_CAPACITY and "10 lanes" in str(e.value)
+    ten = netkit.line(2, 300.0, 10)    # the limit itself loads
+    s3 = moss.Sim(P)
+    s3.load_network(ten)
+    s3.add_vehicles(netkit.vehicles([int(ten.edge_lane0[0]) + 9], [50.0], [10.0], [[0]]))
+    s3.step(3)
+    s3.sync()
 
 
 def test_device_state_readout_into_torch():

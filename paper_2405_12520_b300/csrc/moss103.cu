@@ -156,16 +156,20 @@ StepArgs make_args(Sim *s) {
   return a;
 }
 
+// the k_decide instance for the simulation's lane-change mode and debug setting
+typedef void (*DecideKernel)(StepArgs);
+DecideKernel decide_kernel(int mode, bool dbg) {
+  if (mode == MODE_LEARN) return dbg ? k_decide_t<MODE_LEARN, true> : k_decide_t<MODE_LEARN, false>;
+  if (mode == MODE_LOG) return dbg ? k_decide_t<MODE_LOG, true> : k_decide_t<MODE_LOG, false>;
+  return dbg ? k_decide_t<MODE_PLAIN, true> : k_decide_t<MODE_PLAIN, false>;
+}
+
 // one step = four launches (+ the debug order check); ev (5 events) brackets each kernel
 cudaError_t launch_step(const Sim *s, const StepArgs &a, cudaStream_t st, cudaEvent_t *ev) {
   const LaunchCfg &c = s->cfg;
   if (ev) cudaEventRecord(ev[0], st);
-  if (s->lc_mode == MODE_LEARN)
-    k_decide_t<MODE_LEARN><<<c.grid_decide, c.blk_decide, learn_smem(c.blk_decide), st>>>(a);
-  else if (s->lc_mode == MODE_LOG)
-    k_decide_t<MODE_LOG><<<c.grid_decide, c.blk_decide, 0, st>>>(a);
-  else
-    k_decide_t<MODE_PLAIN><<<c.grid_decide, c.blk_decide, 0, st>>>(a);
+  const size_t smem = s->lc_mode == MODE_LEARN ? learn_smem(c.blk_decide) : 0;
+  decide_kernel(s->lc_mode, s->prm.debug != 0)<<<c.grid_decide, c.blk_decide, smem, st>>>(a);
   if (ev) cudaEventRecord(ev[1], st);
   k_lanes<<<s->n_tiles, LANE_THREADS, 0, st>>>(a);
   if (ev) cudaEventRecord(ev[2], st);
@@ -183,7 +187,7 @@ cudaError_t enqueue_step(Sim *s, cudaStream_t st) { return launch_step(s, make_a
 int shape_grids(Sim *s, LaunchCfg &c, int f_decide, int f_apply, int f_bucket) {
   const int N = s->n_trips;
   int od = 0, oa = 0, ob = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&od, k_decide_t<MODE_PLAIN>, c.blk_decide, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&od, decide_kernel(MODE_PLAIN, s->prm.debug != 0), c.blk_decide, 0));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oa, k_apply, c.blk_apply, 0));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, k_bucket, c.blk_bucket, 0));
   auto g = [&](int blk, int occ, int f) {
@@ -1265,7 +1269,8 @@ int ms_set_lc_model(void *sim, const float *params, float margin) {
     DALLOC(s->d_theta, MLP_NPARAM);
     static bool attr = false;
     if (!attr) {
-      CK(cudaFuncSetAttribute(k_decide_t<MODE_LEARN>, cudaFuncAttributeMaxDynamicSharedMemorySize, learn_smem(512)));
+      CK(cudaFuncSetAttribute(k_decide_t<MODE_LEARN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, learn_smem(512)));
+      CK(cudaFuncSetAttribute(k_decide_t<MODE_LEARN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, learn_smem(512)));
       attr = true;
     }
   }

@@ -214,14 +214,17 @@ __device__ __forceinline__ float idm(const DevParams &P, float v, float v0, bool
   return fmaxf(acc, P.a_min);
 }
 
-__device__ __forceinline__ int sig_state(const StepArgs &a, const LaneInfo &li, int t) {
-  if (li.ctrl < 0) return SIG_G;
-  int4 c = a.ctrl4[li.ctrl];
+__device__ __forceinline__ int sig_state(const StepArgs &a, int ctrl, int group, int t) {
+  if (ctrl < 0) return SIG_G;
+  int4 c = a.ctrl4[ctrl];
   int gy = c.y + c.z;
   int cyc = c.w * gy;
   int tau = ((t + c.x) % cyc + cyc) % cyc;
-  if (tau / gy != (int)li.group) return SIG_R;
+  if (tau / gy != group) return SIG_R;
   return (tau % gy) < c.y ? SIG_G : SIG_Y;
+}
+__device__ __forceinline__ int sig_state(const StepArgs &a, const LaneInfo &li, int t) {
+  return sig_state(a, li.ctrl, (int)li.group, t);
 }
 
 // Lane entered at the end of the edge lane at plan position q with successor entries from
@@ -248,6 +251,21 @@ struct LC {
   float gF, vF, aFn;          // new follower: gap, speed, acceleration behind the changer
 };
 
+// Neighbours in the sorted order, exchanged within the warp: vehicle i + 1 (the own-lane
+// leader when it is on the same lane) and vehicle i - 1 (the old follower when it is).
+struct Nbr {
+  float xL, vL, xF, vF, v0F;
+  int sameL, sameF;
+};
+
+// Records of lane l + step direction, loaded together with the own lane's: the lane-change
+// target when the own lane has a neighbour on that side (an edge's lanes are consecutive,
+// numbered from the right, and equally long).
+struct Tgt {
+  int first, count;   // its segment of the snapshot
+  int ctrl, group;    // the signal at its end
+};
+
 struct Upd {
   int kind, lane, rp;
   float x, v, a_use, a_own;
@@ -259,14 +277,13 @@ struct Upd {
 // Lane records per step: {first index, count, tail x bits, tail v bits}; the tail fields
 // (rearmost vehicle of the lane) are valid when count > 0.
 __device__ __forceinline__ Lead own_leader(const StepArgs &a, const Soa &S, const int4 *dyn, int i,
-                                           int l, const LaneInfo &li, int4 d, float x, float v,
+                                           int l, const LaneInfo &li, const Nbr &nb, float x, float v,
                                            int rp, int nlc, int4 pf_dyn, const LaneInfo &pf_li,
                                            int myid, int t, int &flag) {
   const DevParams &P = a.P;
   Lead r{K_FREE, 0.f, 0.f, -1, 0};
-  if (i + 1 < d.x + d.y) {
-    int j = i + 1;
-    r = Lead{K_VEH, (S.x[j] - x) - P.L, S.v[j], j, 0};
+  if (nb.sameL) {
+    r = Lead{K_VEH, (nb.xL - x) - P.L, nb.vL, i + 1, 0};
   } else {
     float dist = li.len - x;
     int ri = rp;
@@ -351,15 +368,16 @@ __device__ __forceinline__ Lead own_leader(const StepArgs &a, const Soa &S, cons
   return r;
 }
 
-// target lane end blocks a vehicle at (x, v) following plan word pl
-__device__ __forceinline__ bool end_blocks(const StepArgs &a, const LaneInfo &lt, unsigned long long pl,
-                                           float x, float v, int t, int &flag) {
+// end of the target lane (length len, plan position q) blocks a vehicle at (x, v)
+// following plan word pl
+__device__ __forceinline__ bool end_blocks(const StepArgs &a, const Tgt &tg, float len, int q,
+                                           unsigned long long pl, float x, float v, int t, int &flag) {
   if (pl & PLAN_END) return false;
-  if (plan_nib(pl, lt.idx) == PLAN_NONE) return true;
-  int sg = sig_state(a, lt, t);
+  if (plan_nib(pl, q) == PLAN_NONE) return true;
+  int sg = sig_state(a, tg.ctrl, tg.group, t);
   if (sg == SIG_R) return true;
   if (sg == SIG_Y) {
-    float m = (lt.len - x) - v * v / (2.f * a.P.b);
+    float m = (len - x) - v * v / (2.f * a.P.b);
     mark(flag, m);
     return m >= 0.f;
   }
@@ -368,8 +386,8 @@ __device__ __forceinline__ bool end_blocks(const StepArgs &a, const LaneInfo &lt
 
 __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const int4 *dyn, int i,
                                           int l, const LaneInfo &li, float x, float v, float v0,
-                                          unsigned long long pl, int nlc, int4 dl, int myid, int t,
-                                          const Lead &own,
+                                          unsigned long long pl, int nlc, const Nbr &nb, const Tgt &tg,
+                                          int myid, int t, const Lead &own,
                                           float a_c, int &flag) {
   const DevParams &P = a.P;
   LC r{};
@@ -394,9 +412,9 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
   }
   mark(flag, x - P.x_lc_min);
   if (x < P.x_lc_min) return r;
-  const LaneInfo lt = a.li[tau];
+  const int tq = li.idx + step_dir;   // the target's plan position (tau == l + step_dir)
   if (!mand) {
-    if (!plan_ok(pl, lt.idx)) return r;
+    if (!plan_ok(pl, tq)) return r;
     mark(flag, (li.len - x) - P.x_lc_end);
     if (li.len - x < P.x_lc_end) return r;
     unsigned long long h = splitmix64(P.seed ^ ((unsigned long long)(unsigned)t << 32) ^
@@ -404,21 +422,20 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
     if ((uint32_t)(h >> 40) >= P.lc_thresh) return r;
   }
   r.cand = 1;
-  int4 dt = dyn[tau];
-  int lo = dt.x, hi = dt.x + dt.y;
+  int lo = tg.first, hi = tg.first + tg.count;
   while (lo < hi) {
     int mid = (lo + hi) >> 1;
     if (S.x[mid] > x) hi = mid; else lo = mid + 1;
   }
-  int Lt = lo < dt.x + dt.y ? lo : -1;
-  int Ft = lo > dt.x ? lo - 1 : -1;
+  int Lt = lo < tg.first + tg.count ? lo : -1;
+  int Ft = lo > tg.first ? lo - 1 : -1;
   r.tl = Lt;
   r.tf = Ft;
   if (Lt >= 0) {
     r.tkind = K_VEH;
     r.tgap = (S.x[Lt] - x) - P.L;
     r.tvl = S.v[Lt];
-  } else if (end_blocks(a, lt, pl, x, v, t, flag)) {
+  } else if (end_blocks(a, tg, li.len, tq, pl, x, v, t, flag)) {
     r.tkind = K_OBST;
     r.tgap = li.len - x;
     r.tvl = 0.f;
@@ -453,16 +470,15 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
       float aF_old;
       if (Lt >= 0)
         aF_old = idm(P, vF, v0F, true, (S.x[Lt] - xF) - P.L, S.v[Lt]);
-      else if (end_blocks(a, lt, pl, xF, vF, t, flag))
+      else if (end_blocks(a, tg, li.len, tq, pl, xF, vF, t, flag))
         aF_old = idm(P, vF, v0F, true, li.len - xF, 0.f);
       else
         aF_old = idm(P, vF, v0F, false, 0.f, 0.f);
       delta += P.p * (aF_new - aF_old);
     }
-    if (i > dl.x) {
-      int O = i - 1;
-      r.of = O;
-      float xO = S.x[O], vO = S.v[O], v0O = S.v0[O];
+    if (nb.sameF) {
+      r.of = i - 1;
+      const float xO = nb.xF, vO = nb.vF, v0O = nb.v0F;
       float aO_old = idm(P, vO, v0O, true, (x - xO) - P.L, v);
       float aO_new = own.kind != K_FREE ? idm(P, vO, v0O, true, own.gap + (x - xO), own.vl)
                                         : idm(P, vO, v0O, false, 0.f, 0.f);
@@ -478,39 +494,86 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
 
 // Per-vehicle context of one step (snapshot values the update reuses)
 struct VCtx {
-  int l, rp, nlc;
+  int l, rp, nlc, id;
   unsigned long long pl;
   float x, v, v0;
   LaneInfo li;
-  int4 dl;
+  Nbr nb;
 };
 
-// Sensing, car following and the rule's lane-change decision of vehicle i at step t.
+// The vehicle's own fields (coalesced) and its sorted-order neighbours: warp shuffles, with
+// the vehicles just outside the warp loaded by its edge lanes.  Called by the whole warp.
+__device__ __forceinline__ void load_vehicle(const Soa &S, int n, int i, VCtx &c) {
+  const bool act = i < n;
+  c.l = -1;
+  c.x = c.v = 0.f;
+  c.v0 = 1.f;
+  c.rp = c.nlc = c.id = 0;
+  c.pl = 0;
+  if (act) {
+    c.l = S.lane[i];
+    c.x = S.x[i];
+    c.v = S.v[i];
+    c.v0 = S.v0[i];
+    c.rp = S.rp[i];
+    c.pl = S.pl[i];
+    c.nlc = S.nl[i];
+    c.id = S.id[i];
+  }
+  const unsigned full = 0xffffffffu;
+  const int wl = threadIdx.x & 31;
+  float xL = __shfl_down_sync(full, c.x, 1), vL = __shfl_down_sync(full, c.v, 1);
+  int lL = __shfl_down_sync(full, c.l, 1);
+  float xF = __shfl_up_sync(full, c.x, 1), vF = __shfl_up_sync(full, c.v, 1), v0F = __shfl_up_sync(full, c.v0, 1);
+  int lF = __shfl_up_sync(full, c.l, 1);
+  if (wl == 31) {
+    lL = -1;
+    if (i + 1 < n) {
+      xL = S.x[i + 1];
+      vL = S.v[i + 1];
+      lL = S.lane[i + 1];
+    }
+  }
+  if (wl == 0) {
+    lF = -1;
+    if (act && i > 0) {
+      xF = S.x[i - 1];
+      vF = S.v[i - 1];
+      v0F = S.v0[i - 1];
+      lF = S.lane[i - 1];
+    }
+  }
+  c.nb = Nbr{xL, vL, xF, vF, v0F, act && lL == c.l, act && lF == c.l};
+}
+
+// Sensing, car following and the rule's lane-change decision of vehicle i at step t (own
+// fields and neighbours already in c).
 __device__ __forceinline__ Upd vehicle_sense(const StepArgs &a, const Soa &S, const int4 *dyn, int i, int t,
                                              VCtx &c) {
   const DevParams &P = a.P;
   Upd u;
   u.flag = 0;
-  c.l = S.lane[i];
-  c.x = S.x[i];
-  c.v = S.v[i];
-  c.v0 = S.v0[i];
-  c.rp = S.rp[i];
-  c.pl = S.pl[i];
-  c.nlc = S.nl[i];
-  const int myid = S.id[i];
+  // every record the vehicle may need is loaded here, together with the own lane's: the
+  // cached next lane's (only the lane's front vehicle looks ahead) and the possible target
+  // lane's (lane l + step direction, only at or past the lane-change start)
   c.li = a.li[c.l];
-  c.dl = dyn[c.l];
-  // the cached next lane's records, loaded together with the own lane's
   int4 pf_dyn = make_int4(0, 0, 0, 0);
   LaneInfo pf_li{};
-  if (c.nlc >= 0) {
+  if (!c.nb.sameL && c.nlc >= 0) {
     pf_dyn = dyn[c.nlc];
     pf_li = a.li[c.nlc];
   }
-  u.own = own_leader(a, S, dyn, i, c.l, c.li, c.dl, c.x, c.v, c.rp, c.nlc, pf_dyn, pf_li, myid, t, u.flag);
+  Tgt tg{0, 0, -1, 0};
+  const int tl = c.l + ((t & 1) == 0 ? 1 : -1);
+  if (c.x >= P.x_lc_min && tl >= 0 && tl < P.n_lanes) {
+    const int2 d2 = reinterpret_cast<const int2 *>(dyn)[2 * tl];
+    const int2 c2 = reinterpret_cast<const int2 *>(a.li)[4 * tl + 3];   // {ctrl, packed bytes}
+    tg = Tgt{d2.x, d2.y, c2.x, (c2.y >> 16) & 0xff};
+  }
+  u.own = own_leader(a, S, dyn, i, c.l, c.li, c.nb, c.x, c.v, c.rp, c.nlc, pf_dyn, pf_li, c.id, t, u.flag);
   u.a_own = idm(P, c.v, c.v0, u.own.kind != K_FREE, u.own.gap, u.own.vl);
-  u.lc = lane_change(a, S, dyn, i, c.l, c.li, c.x, c.v, c.v0, c.pl, c.nlc, c.dl, myid, t, u.own, u.a_own, u.flag);
+  u.lc = lane_change(a, S, dyn, i, c.l, c.li, c.x, c.v, c.v0, c.pl, c.nlc, c.nb, tg, c.id, t, u.own, u.a_own,
+                     u.flag);
   return u;
 }
 
@@ -575,15 +638,6 @@ __device__ __forceinline__ void vehicle_move(const StepArgs &a, Upd &u, const VC
   u.v = vn;
 }
 
-// The update of vehicle i (snapshot index) at step t.  Pure function of the snapshot.
-__device__ __forceinline__ Upd vehicle_update(const StepArgs &a, const Soa &S, const int4 *dyn, int i,
-                                              int t) {
-  VCtx c;
-  Upd u = vehicle_sense(a, S, dyn, i, t, c);
-  vehicle_move(a, u, c, u.lc.dir);
-  return u;
-}
-
 // number of set bits of b in [s, e)
 __device__ __forceinline__ int count_bits(const unsigned *b, int s, int e) {
   if (s >= e) return 0;
@@ -605,11 +659,11 @@ __device__ __forceinline__ int count_bits(const unsigned *b, int s, int e) {
 // first vehicle adds the part of its lane that lies in later warps and adds the result to
 // the window accumulators (one writer per lane and step).
 __device__ __forceinline__ void lane_speed_sums(const StepArgs &a, const Soa &S, const int4 *dyn,
-                                                int n, int i, int w) {
+                                                int i, int w, const VCtx &c) {
   const int wl = threadIdx.x & 31;
-  const bool act = i < n;
-  const int l = act ? S.lane[i] : -1 - wl;
-  float v = act ? S.v[i] : 0.f;
+  const bool act = c.l >= 0;
+  const int l = act ? c.l : -1 - wl;
+  float v = act ? c.v : 0.f;
   // segmented inclusive scan from the right: each thread gets the sum of its lane's
   // vehicles from itself to the end of the warp
 #pragma unroll
@@ -618,9 +672,8 @@ __device__ __forceinline__ void lane_speed_sums(const StepArgs &a, const Soa &S,
     int ly = __shfl_down_sync(0xffffffffu, l, o);
     if (wl + o < 32 && ly == l) v += y;
   }
-  if (!act) return;
+  if (!act || c.nb.sameF) return;   // the lane's first vehicle writes its sums
   const int4 d = dyn[l];
-  if (i != d.x) return;
   const int warp_end = (i | 31) + 1;   // first index past this warp
   for (int j = warp_end; j < d.x + d.y; ++j) v += S.v[j];
   // one writer per lane and step, so the sums stay deterministic; nothing waits on these
@@ -648,10 +701,10 @@ __device__ __forceinline__ void lc_features(const StepArgs &a, const Soa &S, int
   f[9] = u.lc.tf >= 0 ? u.lc.vF / 20.f : 0.f;
   f[10] = u.lc.tf >= 0 ? u.lc.aFn / a.P.a : 0.f;
   f[11] = u.lc.anew / a.P.a;
-  f[12] = i > c.dl.x ? S.v[i - 1] / 20.f : 0.f;
+  f[12] = c.nb.sameF ? c.nb.vF / 20.f : 0.f;
   f[13] = fminf(c.li.len - c.x, 200.f) / 100.f;
   f[14] = u.own.kind == K_VEH ? u.own.vl / 20.f : (u.own.kind == K_OBST ? 0.f : 1.f);
-  f[15] = i > c.dl.x ? fminf((c.x - S.x[i - 1]) - L, 200.f) / 100.f : 2.f;
+  f[15] = c.nb.sameF ? fminf((c.x - c.nb.xF) - L, 200.f) / 100.f : 2.f;
 }
 
 __device__ __forceinline__ int lc_class(int dir) { return dir > 0 ? 1 : (dir < 0 ? 2 : 0); }
@@ -664,8 +717,13 @@ __host__ __device__ constexpr int learn_smem(int threads) {
   return (int)sizeof(MlpDev) + (threads / 32) * LEARN_WARP_SMEM;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(512, 2) k_decide_t(StepArgs a) {
+// DBG: record per-vehicle sensing and decisions (tests); a separate instance, so that the
+// production kernel keeps none of those values alive.  The plain production instance is
+// capped at 48 registers: 5 blocks of 256 per SM instead of 4 outweigh its few spills (the
+// kernel is bound by the latency of dependent gathers, so resident warps decide its speed).
+template <int MODE, bool DBG>
+__global__ void __launch_bounds__(512, 2) __maxnreg__((MODE == MODE_PLAIN && !DBG) ? 48 : 64)
+    k_decide_t(StepArgs a) {
   extern __shared__ __align__(16) unsigned char lsm[];
   if constexpr (MODE == MODE_LEARN) {
     const uint32_t *src = reinterpret_cast<const uint32_t *>(a.lc.model);
@@ -687,6 +745,7 @@ __global__ void __launch_bounds__(512, 2) k_decide_t(StepArgs a) {
     Upd u;
     VCtx c;
     int dir = 0;
+    load_vehicle(S, n, i, c);
     if (i < n) {
       u = vehicle_sense(a, S, dyn, i, t, c);
       dir = u.lc.dir;
@@ -773,8 +832,8 @@ __global__ void __launch_bounds__(512, 2) k_decide_t(StepArgs a) {
       a.res_x[i] = u.x;
       a.res_v[i] = u.v;
       a.res_code[i] = (kind << CODE_LANE_BITS) | (u.kind == U_RETIRE ? 0 : u.lane);
-      if (a.P.debug) {
-        a.dbg.id[i] = S.id[i];
+      if constexpr (DBG) {
+        a.dbg.id[i] = c.id;
         a.dbg.lead_kind[i] = u.own.kind;
         a.dbg.lead_id[i] = u.own.j >= 0 ? S.id[u.own.j] : -1;
         a.dbg.s_own[i] = u.own.gap;
@@ -792,7 +851,7 @@ __global__ void __launch_bounds__(512, 2) k_decide_t(StepArgs a) {
     }
     const unsigned lm = __ballot_sync(0xffffffffu, leave);
     if ((threadIdx.x & 31) == 0) a.leave[(base + threadIdx.x) >> 5] = lm;
-    if (rec) lane_speed_sums(a, S, dyn, n, i, w);
+    if (rec) lane_speed_sums(a, S, dyn, i, w, c);
     // arrivals: count per new lane and keep the rearmost arrival (no value returned, so
     // nothing waits on these atomics; slots are handed out by k_bucket)
     if (moving) {
@@ -806,7 +865,9 @@ __global__ void __launch_bounds__(512, 2) k_decide_t(StepArgs a) {
         const unsigned long long pn = a.plan[c.rp + 1];
         a.res_code_nl[i] = ln.edge >= 0 ? plan_next(a, c.pl, ln.idx, ln.succ) : plan_next(a, pn, ln.idx, ln.left);
       }
-      if (a.P.debug && u.flag) a.dbg.arr_flag[u.lane] = 1;
+      if constexpr (DBG) {
+        if (u.flag) a.dbg.arr_flag[u.lane] = 1;
+      }
     }
   }
 }

@@ -54,6 +54,8 @@ struct Sim {
   int2 *d_succ = nullptr;
   int *d_pred = nullptr;
   int4 *d_ctrl4 = nullptr;
+  std::vector<int4> h_ctrl4;
+  int *d_sig[2]{};   // signal table per step parity (see sig_pack)
   int *d_routes = nullptr;
   unsigned long long *d_plan = nullptr;
   Soa A[2]{};
@@ -120,6 +122,9 @@ StepArgs make_args(Sim *s) {
   a.succ = s->d_succ;
   a.pred = s->d_pred;
   a.ctrl4 = s->d_ctrl4;
+  a.sig[0] = s->d_sig[0];
+  a.sig[1] = s->d_sig[1];
+  a.n_ctrl = s->n_ctrl;
   a.routes = s->d_routes;
   a.plan = s->d_plan;
   a.A[0] = s->A[0];
@@ -377,6 +382,12 @@ int upload_state(Sim *s, const std::vector<int> &ids, const std::vector<int> &la
     CK(cudaMemcpyAsync(B.id, ids.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
   }
   CK(cudaMemcpyAsync(s->d_dyn[p], dyn.data(), s->n_lanes * sizeof(int4), cudaMemcpyHostToDevice, st));
+  {   // signal table of step t (later steps' tables are written by k_lanes)
+    std::vector<int> sig(s->h_ctrl4.size(), 0);
+    for (int c = 0; c < s->n_ctrl; ++c) sig[c] = sig_pack(s->h_ctrl4[c], t);
+    CK(cudaMemcpyAsync(s->d_sig[p], sig.data(), sig.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  }
   DevCtrl c{};
   CK(cudaMemcpyAsync(&c, s->d_ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -417,6 +428,7 @@ int ms_create(void **out, const ms_params *p, void *cuda_stream) {
   P.p = p->mobil_p; P.th = p->mobil_th; P.bsafe = p->mobil_bsafe; P.a_min = p->a_min;
   P.v_max = p->v_max; P.d_look = p->d_look; P.x_lc_min = p->x_lc_min; P.x_lc_end = p->x_lc_end;
   P.inv2sqrtab = (float)(1.0 / (2.0 * std::sqrt((double)p->idm_a * (double)p->idm_b)));
+  P.inv2b = (float)(1.0 / (2.0 * (double)p->idm_b));
   P.lc_thresh = (uint32_t)std::floor((double)p->p_lc * 16777216.0);
   P.seed = p->seed;
   P.window = p->window;
@@ -558,6 +570,9 @@ int ms_load_network(void *sim, const ms_network *net) {
   DALLOC(s->d_succ, succ.size());
   DALLOC(s->d_pred, pred.size());
   DALLOC(s->d_ctrl4, c4.size());
+  DALLOC(s->d_sig[0], c4.size());
+  DALLOC(s->d_sig[1], c4.size());
+  s->h_ctrl4 = c4;
   CK(cudaMemcpy(s->d_li, li.data(), L * sizeof(LaneInfo), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->d_succ, succ.data(), succ.size() * sizeof(int2), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->d_pred, pred.data(), pred.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -1156,6 +1171,8 @@ int snap_take(Sim *s, Snapshot &sn) {
   add(s->d_ctrl, sizeof(DevCtrl));
   add(s->d_qhead, L * 4);
   add(s->d_qdue, L * 4);
+  add(s->d_sig[0], s->h_ctrl4.size() * 4);
+  add(s->d_sig[1], s->h_ctrl4.size() * 4);
   add(s->d_tarr, N * 4);
   add(s->d_vsum, W * 4);
   add(s->d_vcnt, W * 4);

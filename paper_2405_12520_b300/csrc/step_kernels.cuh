@@ -61,6 +61,7 @@ struct __align__(32) LaneInfo {
 struct DevParams {
   float dt, L, a, b, T, s0, p, th, bsafe, a_min, v_max, d_look, x_lc_min, x_lc_end;
   float inv2sqrtab;      // 1 / (2 sqrt(a b))
+  float inv2b;           // 1 / (2 b): braking distance v^2 / (2 b) as a product
   uint32_t lc_thresh;    // floor(p_lc * 2^24)
   unsigned long long seed;
   int window, n_windows, debug, n_lanes;
@@ -144,6 +145,8 @@ struct StepArgs {
   const int2 *succ;    // {internal lane, exit edge}
   const int *pred;
   const int4 *ctrl4;   // {offset, green, yellow, nphase}
+  int *sig[2];         // per controller, for the steps of parity 0 / 1: 2 * phase + yellow
+  int n_ctrl;
   const int *routes;   // per trip: its edges then -1
   const unsigned long long *plan;   // link plan per routes[] entry
   Soa A[2];
@@ -199,7 +202,9 @@ __device__ __forceinline__ float unfkey(int k) {
 
 __device__ __forceinline__ float idm(const DevParams &P, float v, float v0, bool has, float gap,
                                      float vl) {
-  float r = v / v0;
+  // fast division (2 ulp): the FP32 path is compared with the FP64 oracle at 1e-4, and
+  // decisions this close to a threshold are flagged either way
+  float r = __fdividef(v, v0);
   float r2 = r * r;
   float fr = 1.f - r2 * r2;
   float acc;
@@ -208,20 +213,28 @@ __device__ __forceinline__ float idm(const DevParams &P, float v, float v0, bool
   } else {
     float dv = v - vl;
     float ss = P.s0 + fmaxf(0.f, v * P.T + v * dv * P.inv2sqrtab);
-    float q = ss / fmaxf(gap, 0.01f);
+    float q = __fdividef(ss, fmaxf(gap, 0.01f));
     acc = P.a * (fr - q * q);
   }
   return fmaxf(acc, P.a_min);
 }
 
+// Fixed-time signal of controller c at step t (Sec. III-A, traffic lights): the cycle of
+// nphase phases of green + yellow seconds, shifted by offset; phase index and whether its
+// yellow is on, packed as 2 * phase + yellow.
+__host__ __device__ __forceinline__ int sig_pack(int4 c, int t) {
+  const int gy = c.y + c.z;
+  const int cyc = c.w * gy;
+  const int tau = ((t + c.x) % cyc + cyc) % cyc;
+  return 2 * (tau / gy) + ((tau % gy) >= c.y ? 1 : 0);
+}
+// state of the signal group `group` of controller ctrl at step t, from the table of that
+// step's parity (k_lanes of step t - 1 or the host wrote it)
 __device__ __forceinline__ int sig_state(const StepArgs &a, int ctrl, int group, int t) {
   if (ctrl < 0) return SIG_G;
-  int4 c = a.ctrl4[ctrl];
-  int gy = c.y + c.z;
-  int cyc = c.w * gy;
-  int tau = ((t + c.x) % cyc + cyc) % cyc;
-  if (tau / gy != group) return SIG_R;
-  return (tau % gy) < c.y ? SIG_G : SIG_Y;
+  const int pk = a.sig[t & 1][ctrl];
+  if ((pk >> 1) != group) return SIG_R;
+  return (pk & 1) ? SIG_Y : SIG_G;
 }
 __device__ __forceinline__ int sig_state(const StepArgs &a, const LaneInfo &li, int t) {
   return sig_state(a, li.ctrl, (int)li.group, t);
@@ -310,7 +323,7 @@ __device__ __forceinline__ Lead own_leader(const StepArgs &a, const Soa &S, cons
           if (sg == SIG_R) {
             stop = true;
           } else if (sg == SIG_Y) {
-            float m = dist - v * v / (2.f * P.b);
+            float m = dist - v * v * P.inv2b;
             mark(flag, m);
             stop = m >= 0.f;
           }
@@ -377,7 +390,7 @@ __device__ __forceinline__ bool end_blocks(const StepArgs &a, const Tgt &tg, flo
   int sg = sig_state(a, tg.ctrl, tg.group, t);
   if (sg == SIG_R) return true;
   if (sg == SIG_Y) {
-    float m = (len - x) - v * v / (2.f * a.P.b);
+    float m = (len - x) - v * v * a.P.inv2b;
     mark(flag, m);
     return m >= 0.f;
   }
@@ -1051,6 +1064,9 @@ __global__ void __launch_bounds__(LANE_THREADS, 2) k_lanes(StepArgs a) {
       a.ctrl->t_apply = t;
     }
   }
+  // signal table of step t + 1 (the next k_decide reads it)
+  for (int c = tile * LANE_THREADS + threadIdx.x; c < a.n_ctrl; c += gridDim.x * LANE_THREADS)
+    a.sig[(t + 1) & 1][c] = sig_pack(a.ctrl4[c], t + 1);
   n_ins = __reduce_add_sync(0xffffffffu, n_ins);
   if (lane == 0 && n_ins) atomicAdd(&a.ctrl->inserted, (unsigned long long)n_ins);
 }

@@ -37,7 +37,7 @@ extern "C" {
 
 /* device error bits (ms_metrics.err) */
 #define MS_DEV_HOP 1u        /* a vehicle crossed more than one lane end in a step */
-#define MS_DEV_SCAN 2u       /* lane scan look-back exceeded its wait limit */
+#define MS_DEV_SCAN 2u       /* lane scan: a predecessor tile's aggregate exceeded its wait limit */
 #define MS_DEV_ORDER 4u      /* debug check: output not sorted by (lane, x) or gap < 0 */
 #define MS_DEV_BUCKET 8u     /* a moved vehicle did not find its merge record */
 
@@ -167,20 +167,23 @@ int ms_step(void *sim, int n);
    Same results as ms_step; used to attribute the step time to kernels. */
 int ms_step_timed(void *sim, int n, float *ms_per_kernel);
 
-/* Largest network ms_step_noalloc accepts: lanes <= MS_NOALLOC_MAX_TILES * 2048. */
-#define MS_NOALLOC_MAX_TILES 1536
+/* Largest network ms_step_noalloc accepts: lanes <= MS_NOALLOC_MAX_TILES *
+   MS_NOALLOC_TILE_LANES (3,145,728). */
+#define MS_NOALLOC_MAX_TILES 3072
+#define MS_NOALLOC_TILE_LANES 1024
 
 /* ms_step_noalloc -- the same n steps as ms_step, for callers that must not allocate
    device memory once their simulation is set up: for example a control or serving loop
    that runs inside a fixed device-memory budget reserved in advance, or a host component
    that holds no right to call cudaMalloc on a shared device.  ms_step may allocate on its
    first call (it instantiates CUDA graphs), and the lane scan of every step keeps its
-   look-back status in memory of the simulation.  This entry point allocates nothing: it
-   launches the step's kernels directly and keeps the lane scan's look-back status in one
-   static device array of MS_NOALLOC_MAX_TILES tiles (20 bytes each), which every GPU that
+   per-tile status in memory of the simulation.  This entry point allocates nothing: it
+   launches the step's kernels directly and keeps the lane scan's per-tile status in one
+   static device array of MS_NOALLOC_MAX_TILES tiles (12 bytes each), which every GPU that
    loads this library holds until the process exits.
    - The paper has no counterpart; results are identical to ms_step.
-   - Networks with more than MS_NOALLOC_MAX_TILES * 2048 lanes: MS_ERR_CAPACITY.
+   - Networks with more than MS_NOALLOC_MAX_TILES * MS_NOALLOC_TILE_LANES lanes:
+     MS_ERR_CAPACITY.
    - The simulation's device must be current (else MS_ERR_STATE).  The first call on a
      device looks up the array's device address (cudaGetSymbolAddress); make that first
      call before any stream capture begins.

@@ -67,8 +67,9 @@ struct Sim {
   float *d_res_x = nullptr, *d_res_v = nullptr;
   int *d_res_code = nullptr, *d_res_nl = nullptr, *d_arr_fill = nullptr;
   int *d_tile_flag = nullptr;
-  unsigned long long *d_tile_agg = nullptr, *d_tile_pre = nullptr;
-  int *d_qoff = nullptr, *d_qtrip = nullptr, *d_qhead = nullptr, *d_qdue = nullptr;
+  unsigned long long *d_tile_agg = nullptr;
+  int *d_qoff = nullptr, *d_qtrip = nullptr;
+  int2 *d_qhd = nullptr;
   int4 *d_qent = nullptr, *d_qent2 = nullptr;
   int *d_tdep = nullptr, *d_route0 = nullptr, *d_tarr = nullptr;
   float *d_vsum = nullptr;
@@ -144,11 +145,9 @@ StepArgs make_args(Sim *s) {
   a.arr_fill = s->d_arr_fill;
   a.tile_flag = s->d_tile_flag;
   a.tile_agg = s->d_tile_agg;
-  a.tile_pre = s->d_tile_pre;
   a.q_off = s->d_qoff;
   a.q_trip = s->d_qtrip;
-  a.q_head = s->d_qhead;
-  a.q_due = s->d_qdue;
+  a.q_hd = s->d_qhd;
   a.q_ent = s->d_qent;
   a.q_ent2 = s->d_qent2;
   a.trip_tdep = s->d_tdep;
@@ -299,8 +298,9 @@ int upload_queues(Sim *s, const std::vector<int> &qhead) {
   std::vector<int> due(s->n_lanes);
   for (int l = 0; l < s->n_lanes; ++l)
     due[l] = qhead[l] < s->h_qoff[l + 1] ? s->h_tdep[s->h_qtrip[qhead[l]]] : 0x7fffffff;
-  CK(cudaMemcpy(s->d_qhead, qhead.data(), sizeof(int) * s->n_lanes, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(s->d_qdue, due.data(), sizeof(int) * s->n_lanes, cudaMemcpyHostToDevice));
+  std::vector<int2> hd(s->n_lanes);
+  for (int l = 0; l < s->n_lanes; ++l) hd[l] = make_int2(qhead[l], due[l]);
+  CK(cudaMemcpy(s->d_qhd, hd.data(), sizeof(int2) * s->n_lanes, cudaMemcpyHostToDevice));
   return MS_OK;
 }
 
@@ -577,7 +577,7 @@ int ms_load_network(void *sim, const ms_network *net) {
   CK(cudaMemcpy(s->d_succ, succ.data(), succ.size() * sizeof(int2), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->d_pred, pred.data(), pred.size() * sizeof(int), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->d_ctrl4, c4.data(), c4.size() * sizeof(int4), cudaMemcpyHostToDevice));
-  s->n_tiles = (L + SCAN_TILE - 1) / SCAN_TILE;
+  s->n_tiles = (L + LANE_TILE - 1) / LANE_TILE;
   s->net_loaded = true;
   return MS_OK;
 }
@@ -688,14 +688,12 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
   DALLOC(s->d_arr_fill, s->n_lanes);
   DALLOC(s->d_tile_flag, s->n_tiles);
   DALLOC(s->d_tile_agg, s->n_tiles);
-  DALLOC(s->d_tile_pre, s->n_tiles);
   DALLOC(s->d_qoff, s->n_lanes + 1);
   DALLOC(s->d_qtrip, s->h_qtrip.size());
   DALLOC(s->d_qent, s->h_qtrip.size());
   DALLOC(s->d_qent2, s->h_qtrip.size());
   DALLOC(s->d_plan, s->h_plan.size());
-  DALLOC(s->d_qhead, s->n_lanes);
-  DALLOC(s->d_qdue, s->n_lanes);
+  DALLOC(s->d_qhd, s->n_lanes);
   DALLOC(s->d_tdep, N);
   DALLOC(s->d_route0, N);
   DALLOC(s->d_tarr, N);
@@ -819,10 +817,11 @@ int ms_step_timed(void *sim, int n, float *ms_per_kernel) {
   return MS_OK;
 }
 
-// Look-back status of the lane scan for ms_step_noalloc: per tile an aggregate and an
-// inclusive prefix (8 bytes each) and a flag (4 bytes), for MS_NOALLOC_MAX_TILES tiles.
-// One copy per device for the whole process; shared by every call (see moss103.h).
-static __device__ __align__(256) unsigned long long g_noalloc_scan[MS_NOALLOC_MAX_TILES * 5 / 2];
+// Status of the lane scan for ms_step_noalloc: per tile an aggregate (8 bytes) and a flag
+// (4 bytes), for MS_NOALLOC_MAX_TILES tiles.  One copy per device for the whole process;
+// shared by every call (see moss103.h).
+static_assert(LANE_TILE == MS_NOALLOC_TILE_LANES, "scan tile size and the header disagree");
+static __device__ __align__(256) unsigned long long g_noalloc_scan[MS_NOALLOC_MAX_TILES * 3 / 2];
 static unsigned long long *g_noalloc_addr[256];   // device address per device ordinal
 
 int ms_step_noalloc(void *sim, int n) {
@@ -832,7 +831,7 @@ int ms_step_noalloc(void *sim, int n) {
   if (n < 0) return fail(s, MS_ERR_ARG, "n < 0");
   if (s->n_tiles > MS_NOALLOC_MAX_TILES)
     return fail(s, MS_ERR_CAPACITY, "network has " + std::to_string(s->n_lanes) + " lanes; ms_step_noalloc takes at most " +
-                                        std::to_string(MS_NOALLOC_MAX_TILES * SCAN_TILE));
+                                        std::to_string(MS_NOALLOC_MAX_TILES * LANE_TILE));
   int dev = -1;
   CK(cudaGetDevice(&dev));
   if (dev != s->device || dev < 0 || dev >= 256) return fail(s, MS_ERR_STATE, "make the simulation's device current");
@@ -845,8 +844,7 @@ int ms_step_noalloc(void *sim, int n) {
   unsigned long long *base = g_noalloc_addr[dev];
   StepArgs a = make_args(s);
   a.tile_agg = base;
-  a.tile_pre = base + MS_NOALLOC_MAX_TILES;
-  a.tile_flag = reinterpret_cast<int *>(base + 2 * MS_NOALLOC_MAX_TILES);
+  a.tile_flag = reinterpret_cast<int *>(base + MS_NOALLOC_MAX_TILES);
   cudaStream_t st = s->stream;
   // the array keeps whatever the last call left: flags must start at zero
   CK(cudaMemsetAsync(a.tile_flag, 0, sizeof(int) * MS_NOALLOC_MAX_TILES, st));
@@ -1169,8 +1167,7 @@ int snap_take(Sim *s, Snapshot &sn) {
     add(s->d_dyn[b], L * sizeof(int4));
   }
   add(s->d_ctrl, sizeof(DevCtrl));
-  add(s->d_qhead, L * 4);
-  add(s->d_qdue, L * 4);
+  add(s->d_qhd, L * 8);
   add(s->d_sig[0], s->h_ctrl4.size() * 4);
   add(s->d_sig[1], s->h_ctrl4.size() * 4);
   add(s->d_tarr, N * 4);

@@ -7,12 +7,12 @@
 //             leader and the target-lane neighbours from the read-only snapshot, IDM +
 //             randomized MOBIL + stop lines + ballistic advance + transfer; store the
 //             vehicle's result (x', v', new lane and kind: 12 B), a leave bit per vehicle
-//             (warp ballot), and a record per vehicle that enters another lane (one atomic
-//             per warp for the record slots); per-lane window metrics by the first vehicle
-//             of each lane.
-//   k_lanes   (prepare phase for t+1)  decoupled look-back scan over lanes (32 predecessor
-//             tiles per probe): new per-lane counts = stayers + arrivals + departures, new
-//             segment starts, arrival bucket starts; departure FIFOs admit their head.
+//             (warp ballot), per-lane arrival counts and rearmost arrival (fire-and-forget
+//             atomics); per-lane window metrics by the first vehicle of each lane.
+//   k_lanes   (prepare phase for t+1)  single-pass scan over lanes (each tile sums all its
+//             predecessors' aggregates in parallel): new per-lane counts = stayers +
+//             arrivals + departures, new segment starts, arrival bucket starts; departure
+//             FIFOs admit their head; the signal table of step t+1.
 //   k_bucket  place each arrival record into its lane's bucket with its rank among the
 //             lane's stayers.
 //   k_apply   stream every vehicle with its stored result to its sorted slot of the t+1
@@ -34,13 +34,16 @@ enum { K_FREE = 0, K_VEH = 1, K_OBST = 2 };
 enum { U_STAY = 0, U_CHANGE = 1, U_TRANSFER = 2, U_RETIRE = 3 };
 constexpr int HOP_CAP = 12;          // lanes searched ahead for a leader
 constexpr float FLAG_EPS = 1e-3f;    // decision margins closer than this are flagged
-constexpr int SCAN_THREADS = 256;
-constexpr int SCAN_ITEMS = 8;
-constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
-constexpr int SPIN_LIMIT = 1 << 22;  // bounded wait of the look-back
+// lane pass: tiles of LANE_TILE lanes, LANE_THREADS threads with LANE_ITEMS lanes each
+constexpr int LANE_THREADS = 256;
+constexpr int LANE_ITEMS = 4;
+constexpr int LANE_TILE = LANE_THREADS * LANE_ITEMS;
+constexpr int LANE_WARPS = LANE_THREADS / 32;
+constexpr int SPIN_LIMIT = 1 << 22;  // bounded wait for a predecessor tile's aggregate
 constexpr int AMIN_NONE = 0x7fffffff;
 
 constexpr unsigned DEV_HOP = 1u, DEV_SCAN = 2u, DEV_ORDER = 4u, DEV_BUCKET = 8u;
+constexpr int LEAVE_ONE = 1 << 16;   // a leaver in the per-lane arrival word
 
 // Static lane record, one 32-byte sector per lane.
 struct __align__(32) LaneInfo {
@@ -153,17 +156,17 @@ struct StepArgs {
   int4 *dyn[2];        // per lane {first index, count, tail x, tail v} for buffer 0 / 1
   DevCtrl *ctrl;
   unsigned *leave;
-  int *arr_cnt, *amin, *arr_start;
+  int *arr_cnt;        // per lane: arrivals (bits 0..15) + leavers (bits 16..30) of the step
+  int *amin, *arr_start;
   int4 *bucket;        // {r, x bits, id, old index}
   float *res_x, *res_v;
   int *res_code;
   int *arr_fill;       // per lane: arrival slots handed out by k_bucket (reset by k_apply)
   int *res_code_nl;    // next-lane choice of arrivals, written by k_decide (sparse)
-  int *tile_flag;
-  unsigned long long *tile_agg, *tile_pre;
+  int *tile_flag;                  // per lane tile: its aggregate is published
+  unsigned long long *tile_agg;    // per lane tile: {new vehicles, arrivals} packed
   const int *q_off, *q_trip;
-  int *q_head;
-  int *q_due;          // per lane: departure step of the FIFO's head trip (INT_MAX if empty)
+  int2 *q_hd;          // per lane: {FIFO head entry, its departure step (INT_MAX if empty)}
   const int4 *q_ent;   // per FIFO entry: {trip, route start, next-lane choice, v0 bits}
   const int4 *q_ent2;  // per FIFO entry: {plan of the first edge (lo, hi), departure step
                        // of the lane's next entry or INT_MAX, 0}
@@ -838,6 +841,7 @@ __global__ void __launch_bounds__(512, 2) __maxnreg__((MODE == MODE_PLAIN && !DB
       vehicle_move(a, u, c, dir);
       leave = u.kind != U_STAY;
       moving = u.kind == U_CHANGE || u.kind == U_TRANSFER;
+      if (leave) atomicAdd(&a.arr_cnt[c.l], LEAVE_ONE);   // fire-and-forget, like the arrivals
       int kind = u.kind == U_STAY ? C_STAY
                : u.kind == U_CHANGE ? C_CHANGE
                : u.kind == U_RETIRE ? C_RETIRE
@@ -894,18 +898,18 @@ __device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long 
   return v;
 }
 
-// Lane pass: new per-lane counts, decoupled look-back scan, departures.  A tile of
-// SCAN_TILE lanes is processed by LANE_THREADS threads in LANE_ITEMS striped slices (lane
+// Lane pass: new per-lane counts, a single-pass scan over lanes, departures.  A tile of
+// LANE_TILE lanes is processed by LANE_THREADS threads in LANE_ITEMS striped slices (lane
 // k * LANE_THREADS + thread), so every load is coalesced and the loads of all slices are
-// issued before any is used.
-constexpr int LANE_THREADS = 512;
-constexpr int LANE_ITEMS = SCAN_TILE / LANE_THREADS;
-constexpr int LANE_WARPS = LANE_THREADS / 32;
-
-__global__ void __launch_bounds__(LANE_THREADS, 2) k_lanes(StepArgs a) {
+// issued before any is used.  Each tile publishes its aggregate as soon as it has it and
+// then sums the aggregates of all its predecessors, one predecessor per thread: no tile
+// waits on another's prefix, so there is no chain through the tiles (with a few hundred
+// tiles, the quadratic number of L2 reads is small).  Tiles are numbered in the order
+// their blocks start, so every predecessor is resident or done.
+__global__ void __launch_bounds__(LANE_THREADS, 4) k_lanes(StepArgs a) {
   __shared__ int s_tile;
   __shared__ unsigned long long s_wsum[LANE_ITEMS][LANE_WARPS];
-  __shared__ unsigned long long s_excl;
+  __shared__ unsigned long long s_part[LANE_WARPS];
   if (threadIdx.x == 0) s_tile = atomicAdd(&a.ctrl->tile_ticket, 1);
   __syncthreads();
   const int tile = s_tile;
@@ -916,35 +920,39 @@ __global__ void __launch_bounds__(LANE_THREADS, 2) k_lanes(StepArgs a) {
   int4 *ndyn = a.dyn[p ^ 1];
   const int nlanes = a.P.n_lanes;
   const float room_need = a.P.L + a.P.s0;
-  const int lbase = tile * SCAN_TILE + threadIdx.x;
+  const int lbase = tile * LANE_TILE + threadIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   int4 d[LANE_ITEMS];
-  int arr[LANE_ITEMS], amk[LANE_ITEMS], qdue[LANE_ITEMS];
+  int arr[LANE_ITEMS], lv[LANE_ITEMS], amk[LANE_ITEMS];
+  int2 qhd[LANE_ITEMS];
 #pragma unroll
   for (int k = 0; k < LANE_ITEMS; ++k) {
     const int l = lbase + k * LANE_THREADS;
     if (l < nlanes) {
       d[k] = dyn[l];
-      arr[k] = a.arr_cnt[l];
+      const int w = a.arr_cnt[l];
+      arr[k] = w & (LEAVE_ONE - 1);
+      lv[k] = w >> 16;
       amk[k] = a.amin[l];
-      qdue[k] = a.q_due[l];
+      qhd[k] = a.q_hd[l];
     } else {
       d[k] = make_int4(0, 0, 0, 0);
-      arr[k] = 0;
+      arr[k] = lv[k] = 0;
       amk[k] = AMIN_NONE;
-      qdue[k] = 0x7fffffff;
+      qhd[k] = make_int2(0, 0x7fffffff);
     }
   }
-  int cnt[LANE_ITEMS], ins[LANE_ITEMS], qh[LANE_ITEMS];
+  int cnt[LANE_ITEMS], ins[LANE_ITEMS];
   unsigned long long val[LANE_ITEMS], incl[LANE_ITEMS];
 #pragma unroll
   for (int k = 0; k < LANE_ITEMS; ++k) {
-    const int leavers = count_bits(a.leave, d[k].x, d[k].x + d[k].y);
+    const int leavers = lv[k];
     ins[k] = 0;
-    qh[k] = 0;
-    if (qdue[k] <= t) {
-      qh[k] = a.q_head[lbase + k * LANE_THREADS];   // consumed after the scan   // the FIFO's head is due: room behind the lane's tail (its
+    if (qhd[k].y <= t) {
+      // the head's record is read after the scan: start bringing it in now
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(a.q_ent + qhd[k].x));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(a.q_ent2 + qhd[k].x));   // the FIFO's head is due: room behind the lane's tail (its
       int fl = 0;          // position is in the lane record) and behind every arrival
       bool room = true;
       if (d[k].y > 0) {
@@ -959,7 +967,7 @@ __global__ void __launch_bounds__(LANE_THREADS, 2) k_lanes(StepArgs a) {
       }
       if (a.P.debug) {
         const int l = lbase + k * LANE_THREADS;
-        if (fl || a.dbg.arr_flag[l]) a.dbg.trip_flag[a.q_trip[qh[k]]] = t + 1;
+        if (fl || a.dbg.arr_flag[l]) a.dbg.trip_flag[a.q_trip[qhd[k].x]] = t + 1;
       }
       ins[k] = room ? 1 : 0;
     }
@@ -979,53 +987,31 @@ __global__ void __launch_bounds__(LANE_THREADS, 2) k_lanes(StepArgs a) {
       if (lane < LANE_WARPS) s_wsum[k][lane] = run + wi - wv;
       run += __shfl_sync(0xffffffffu, wi, LANE_WARPS - 1);
     }
-    const unsigned long long agg = run;
-    // decoupled look-back, 32 predecessor tiles per probe
-    unsigned long long excl = 0;
-    if (tile == 0) {
-      if (lane == 0) {
-        a.tile_pre[0] = agg;
-        cuda::atomic_ref<int, cuda::thread_scope_device>(a.tile_flag[0]).store(2, cuda::memory_order_release);
-      }
-    } else {
-      if (lane == 0) {
-        a.tile_agg[tile] = agg;
-        cuda::atomic_ref<int, cuda::thread_scope_device>(a.tile_flag[tile]).store(1, cuda::memory_order_release);
-      }
-      int j = tile - 1;
-      int spins = 0;
-      while (true) {
-        const int idx = j - lane;   // lane 0 probes the nearest predecessor
-        int fv;
-        while (true) {
-          fv = idx >= 0 ? cuda::atomic_ref<int, cuda::thread_scope_device>(a.tile_flag[idx]).load(cuda::memory_order_acquire)
-                        : 2;
-          if (__all_sync(0xffffffffu, fv != 0)) break;
-          if (++spins > SPIN_LIMIT) {
-            if (lane == 0) atomicOr(&a.ctrl->err, DEV_SCAN);
-            break;
-          }
-        }
-        const unsigned pm = __ballot_sync(0xffffffffu, fv == 2);
-        const int stop = pm ? __ffs(pm) - 1 : 32;
-        unsigned long long v = 0;
-        if (lane < stop) v = a.tile_agg[idx];
-        else if (lane == stop) v = idx >= 0 ? a.tile_pre[idx] : 0ull;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        excl += v;
-        if (pm || spins > SPIN_LIMIT) break;
-        j -= 32;
-      }
-      if (lane == 0) {
-        a.tile_pre[tile] = excl + agg;
-        cuda::atomic_ref<int, cuda::thread_scope_device>(a.tile_flag[tile]).store(2, cuda::memory_order_release);
+    if (lane == 0) {   // publish this tile's aggregate
+      a.tile_agg[tile] = run;
+      cuda::atomic_ref<int, cuda::thread_scope_device>(a.tile_flag[tile]).store(1, cuda::memory_order_release);
+    }
+  }
+  // sum of the predecessors' aggregates
+  unsigned long long part = 0;
+  for (int j = threadIdx.x; j < tile; j += LANE_THREADS) {
+    int spins = 0;
+    while (cuda::atomic_ref<int, cuda::thread_scope_device>(a.tile_flag[j]).load(cuda::memory_order_acquire) == 0) {
+      if (++spins > SPIN_LIMIT) {
+        atomicOr(&a.ctrl->err, DEV_SCAN);
+        break;
       }
     }
-    if (lane == 0) s_excl = excl;
+    part += __ldcg(&a.tile_agg[j]);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if (lane == 0) s_part[warp] = part;
   __syncthreads();
-  const unsigned long long tile_excl = s_excl;
+  unsigned long long tile_excl = 0;
+#pragma unroll
+  for (int w = 0; w < LANE_WARPS; ++w) tile_excl += s_part[w];
+
   int n_ins = 0;
 #pragma unroll
   for (int k = 0; k < LANE_ITEMS; ++k) {
@@ -1038,10 +1024,9 @@ __global__ void __launch_bounds__(LANE_THREADS, 2) k_lanes(StepArgs a) {
     ndyn[l] = make_int4(nstart, cnt[k], ins[k] ? __float_as_int(a.P.L) : 0, 0);
     a.arr_start[l] = astart;
     if (ins[k]) {   // the entry's record was built at load time
-      const int4 e = a.q_ent[qh[k]];
-      const int4 e2 = a.q_ent2[qh[k]];
-      a.q_head[l] = qh[k] + 1;
-      a.q_due[l] = e2.z;
+      const int4 e = a.q_ent[qhd[k].x];
+      const int4 e2 = a.q_ent2[qhd[k].x];
+      a.q_hd[l] = make_int2(qhd[k].x + 1, e2.z);
       D.x[nstart] = a.P.L;
       D.v[nstart] = 0.f;
       D.v0[nstart] = __int_as_float(e.w);
@@ -1054,7 +1039,7 @@ __global__ void __launch_bounds__(LANE_THREADS, 2) k_lanes(StepArgs a) {
       ++n_ins;
       if (a.P.debug) a.dbg.trip_ins[e.x] = t + 1;
     }
-    if (arr[k]) a.arr_cnt[l] = 0;
+    if (arr[k] | lv[k]) a.arr_cnt[l] = 0;
     if (amk[k] != AMIN_NONE) a.amin[l] = AMIN_NONE;
     if (a.P.debug) a.dbg.arr_flag[l] = 0;
     if (l == nlanes - 1) {

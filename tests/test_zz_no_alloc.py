@@ -2,7 +2,7 @@
 
 Some callers cannot call cudaMalloc once their simulation exists -- a loop that runs inside
 a device-memory budget reserved in advance, or a component without the right to allocate on
-a shared GPU.  For them ms_step_noalloc runs the same step with the lane scan's look-back
+a shared GPU.  For them ms_step_noalloc runs the same step with the lane scan's per-tile
 status in one static device array instead of memory it would otherwise need.  These tests
 step two identical simulations, one with each entry point, and require identical states
 after each of two calls in a row; a network larger than the static array's limit must be
@@ -53,7 +53,7 @@ def test_noalloc_step_refuses_networks_beyond_its_limit():
     import torch
     assert torch.cuda.is_available(), "needs a CUDA device"
     from paper_2405_12520_b300 import moss, synth
-    lib_max = 1536 * 2048   # MS_NOALLOC_MAX_TILES * lanes per scan tile
+    lib_max = 3072 * 1024   # MS_NOALLOC_MAX_TILES * MS_NOALLOC_TILE_LANES
     E = lib_max + 1         # one-lane roads, no junctions: just over the limit
     z = np.zeros(E, np.int32)
     net = synth.Network(

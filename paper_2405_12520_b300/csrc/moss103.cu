@@ -66,6 +66,7 @@ struct Sim {
   int4 *d_bucket = nullptr;
   float *d_res_x = nullptr, *d_res_v = nullptr;
   int *d_res_code = nullptr, *d_res_nl = nullptr, *d_arr_fill = nullptr;
+  int2 *d_res_pos = nullptr;
   int *d_tile_flag = nullptr;
   unsigned long long *d_tile_agg = nullptr;
   int *d_qoff = nullptr, *d_qtrip = nullptr;
@@ -142,6 +143,7 @@ StepArgs make_args(Sim *s) {
   a.res_v = s->d_res_v;
   a.res_code = s->d_res_code;
   a.res_code_nl = s->d_res_nl;
+  a.res_pos = s->d_res_pos;
   a.arr_fill = s->d_arr_fill;
   a.tile_flag = s->d_tile_flag;
   a.tile_agg = s->d_tile_agg;
@@ -683,8 +685,9 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
   DALLOC(s->d_bucket, N);
   DALLOC(s->d_res_x, N);
   DALLOC(s->d_res_v, N);
-  DALLOC(s->d_res_code, N);
+  DALLOC(s->d_res_code, N + 4);   // k_bucket reads it four codes at a time
   DALLOC(s->d_res_nl, N);
+  DALLOC(s->d_res_pos, N);
   DALLOC(s->d_arr_fill, s->n_lanes);
   DALLOC(s->d_tile_flag, s->n_tiles);
   DALLOC(s->d_tile_agg, s->n_tiles);

@@ -163,6 +163,8 @@ struct StepArgs {
   int *res_code;
   int *arr_fill;       // per lane: arrival slots handed out by k_bucket (reset by k_apply)
   int *res_code_nl;    // next-lane choice of arrivals, written by k_decide (sparse)
+  int2 *res_pos;       // lane changers: {target segment start, first target index not
+                       // behind the changer}, written by k_decide (sparse)
   int *tile_flag;                  // per lane tile: its aggregate is published
   unsigned long long *tile_agg;    // per lane tile: {new vehicles, arrivals} packed
   const int *q_off, *q_trip;
@@ -265,6 +267,7 @@ struct LC {
   float tgap, tvl, anew;
   int safe, mand, step_dir;   // safety passed; mandatory change; direction allowed this step
   float gF, vF, aFn;          // new follower: gap, speed, acceleration behind the changer
+  int tfirst, pos;            // target segment start; first target index with x' >= x
 };
 
 // Neighbours in the sorted order, exchanged within the warp: vehicle i + 1 (the own-lane
@@ -445,6 +448,8 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
   }
   int Lt = lo < tg.first + tg.count ? lo : -1;
   int Ft = lo > tg.first ? lo - 1 : -1;
+  r.tfirst = tg.first;
+  r.pos = lo;   // first with x' > x; moved onto the follower below if it is level with x
   r.tl = Lt;
   r.tf = Ft;
   if (Lt >= 0) {
@@ -471,6 +476,7 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
     float guard = vF * P.dt + 0.5f * P.a * P.dt * P.dt;
     mark(flag, gF - guard);
     if (gF < guard) return r;
+    if (xF == x) r.pos = Ft;   // at most one vehicle of a lane can be level with x
     aF_new = idm(P, vF, v0F, true, gF, v);
     mark(flag, aF_new + P.bsafe);
     if (aF_new < -P.bsafe) return r;
@@ -877,6 +883,7 @@ __global__ void __launch_bounds__(512, 2) __maxnreg__((MODE == MODE_PLAIN && !DB
       // the arrival's cached next-lane choice for its new lane (internal -> edge lane keeps
       // the choice it already made for that target lane): a lane change follows the plan
       // of its own edge, an internal lane the plan of its target lane's edge
+      if (u.kind == U_CHANGE) a.res_pos[i] = make_int2(u.lc.tfirst, u.lc.pos);
       if (u.rp == c.rp) {
         const LaneInfo ln = a.li[u.lane];
         const unsigned long long pn = a.plan[c.rp + 1];
@@ -1063,36 +1070,38 @@ __global__ void k_bucket(StepArgs a, int n_tiles) {
   const int t = a.ctrl->t_apply;
   const int p = t & 1;
   const Soa S = a.A[p];
-  const int4 *dyn = a.dyn[p];
   const int n = a.ctrl->n_active[p];
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
   int mine = 0;
-  for (int i = gid; i < n; i += stride) {
-    const int code = a.res_code[i];
-    const int kind = (unsigned)code >> CODE_LANE_BITS;
-    if (kind != C_CHANGE && kind != C_TRANSFER && kind != C_TRANSFER_ROUTE) continue;
-    const int nl = code & CODE_LANE_MASK;
-    int r = 0;
-    if (kind == C_CHANGE) {
-      const float xold = S.x[i];
-      int4 d = dyn[nl];
-      int lo = d.x, hi = d.x + d.y;
-      while (lo < hi) {   // first vehicle of the target lane not behind the changer
-        int mid = (lo + hi) >> 1;
-        if (S.x[mid] < xold) lo = mid + 1; else hi = mid;
+  // four result codes per thread and load (the code buffer is padded to a multiple of 4)
+  const int ng = (n + 3) >> 2;
+  for (int g = gid; g < ng; g += stride) {
+    const int4 c4 = reinterpret_cast<const int4 *>(a.res_code)[g];
+    const int cs[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = 4 * g + q;
+      if (i >= n) break;
+      const int code = cs[q];
+      const int kind = (unsigned)code >> CODE_LANE_BITS;
+      if (kind != C_CHANGE && kind != C_TRANSFER && kind != C_TRANSFER_ROUTE) continue;
+      const int nl = code & CODE_LANE_MASK;
+      int r = 0;
+      if (kind == C_CHANGE) {   // rank among the target lane's stayers (k_decide found the slot)
+        const int2 fp = a.res_pos[i];
+        r = (fp.y - fp.x) - count_bits(a.leave, fp.x, fp.y);
       }
-      r = (lo - d.x) - count_bits(a.leave, d.x, lo);
+      const int slot = a.arr_start[nl] + atomicAdd(&a.arr_fill[nl], 1);
+      if (slot >= a.arr_start[nl + 1]) {   // never expected: more arrivals than counted
+        atomicOr(&a.ctrl->err, DEV_BUCKET);
+        continue;
+      }
+      a.bucket[slot] = make_int4(r, __float_as_int(a.res_x[i]), S.id[i], i);
+      ++mine;
     }
-    const int slot = a.arr_start[nl] + atomicAdd(&a.arr_fill[nl], 1);
-    if (slot >= a.arr_start[nl + 1]) {   // never expected: more arrivals than counted
-      atomicOr(&a.ctrl->err, DEV_BUCKET);
-      continue;
-    }
-    a.bucket[slot] = make_int4(r, __float_as_int(a.res_x[i]), S.id[i], i);
-    ++mine;
   }
   if (mine) atomicAdd(&s_cnt, mine);
   for (int k = gid; k < n_tiles; k += stride) a.tile_flag[k] = 0;

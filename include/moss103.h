@@ -67,6 +67,11 @@ typedef struct ms_params {
   int block;       /* threads per block of the vehicle kernels, multiple of 32 (0: 256) */
   int id_base;     /* added to trip ids in the lane-change gate hash (0; a stand-alone run of
                       one scenario of a batch sets it to the scenario's first trip id) */
+  float mobil_th_jitter; /* m/s^2, >= 0: randomized-MOBIL variant -- trip i's incentive
+                      threshold is mobil_th + mobil_th_jitter * (2u - 1), with u the top 24
+                      bits of SplitMix64(seed ^ 0x9E3779B97F4A7C15 ^ (i + id_base)) / 2^24,
+                      fixed for the trip (driver heterogeneity; Sec. III-A "randomized
+                      improvement" leaves the form open); 0 = off */
 } ms_params;
 
 /* Lane-level road network (Sec. III-C "Map Builder": lanes with topology, junction lanes,

@@ -41,7 +41,7 @@ class _Params(C.Structure):
     _fields_ = [(f, C.c_double) for f in (
         "dt", "veh_len", "a", "b", "T", "s0", "p", "th", "bsafe", "p_lc", "a_min", "v_max",
         "d_look", "x_lc_min", "x_lc_end")] + [("window", C.c_int), ("n_windows", C.c_int),
-                                             ("seed", C.c_uint64)]
+                                             ("seed", C.c_uint64), ("th_jitter", C.c_double)]
 
 
 _DBG_INT = ("active_before", "lead_kind", "lead_id")
@@ -118,7 +118,8 @@ class Oracle:
         self.par_c = _Params(p["dt"], p["veh_len"], p["idm_a"], p["idm_b"], p["idm_T"], p["idm_s0"],
                              p["mobil_p"], p["mobil_th"], p["mobil_bsafe"], p["p_lc"], p["a_min"],
                              p["v_max"], p["d_look"], p["x_lc_min"], p["x_lc_end"],
-                             int(p["window"]), int(n_windows), int(p["seed"]))
+                             int(p["window"]), int(n_windows), int(p["seed"]),
+                             float(p.get("mobil_th_jitter", 0.0)))
         self.t_dep = i32(dem.t_dep)
         self.v0 = np.ascontiguousarray(dem.v0, np.float32)
         self.route_off = np.ascontiguousarray(dem.route_off, np.int64)

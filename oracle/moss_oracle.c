@@ -62,6 +62,10 @@
  *  R11 Lane links fan out (every turning lane links to every lane of its exit edge, in a
  *      preferred order); a vehicle takes the first link whose target lane serves the route
  *      edge after the exit edge, so it enters each edge on a lane that serves its next turn.
+ *  R12 Threshold jitter (a randomized-MOBIL variant, off when th_jitter = 0): trip c's
+ *      incentive threshold is th + th_jitter (2u - 1), u = (SplitMix64(seed ^ 0x9E3779B97F4A7C15
+ *      ^ c) >> 40) / 2^24, fixed for the trip (driver heterogeneity); the salt keeps these
+ *      draws apart from the per-step gate draws of R4 (whose low 32 bits are c alone).
  */
 #include "moss_oracle.h"
 
@@ -119,6 +123,14 @@ uint64_t or_splitmix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
   return z ^ (z >> 31);
+}
+
+/* R12: incentive threshold of trip c */
+static double trip_threshold(const or_params *p, int c) {
+  if (!(p->th_jitter > 0.0)) return p->th;
+  const uint64_t h = or_splitmix64(p->seed ^ 0x9E3779B97F4A7C15ull ^ (uint64_t)(uint32_t)c);
+  const double u = (double)(h >> 40) / 16777216.0;
+  return p->th + p->th_jitter * (2.0 * u - 1.0);
 }
 
 static int is_internal(const or_sim *s, int l) { return s->net.lane_edge[l] < 0; }
@@ -449,8 +461,9 @@ static lc_t lane_change(const or_sim *s, int c, const leader_t *own, double a_c,
       delta += p->p * (aO_new - aO_old);
     }
     r.incentive = delta;
-    mark(flag, delta - p->th);
-    if (!(delta > p->th)) return r;
+    const double th_c = trip_threshold(p, c);
+    mark(flag, delta - th_c);
+    if (!(delta > th_c)) return r;
   }
   r.dir = step_dir;
   return r;

@@ -35,6 +35,7 @@ typedef struct {
   double p, th, bsafe, p_lc, a_min, v_max, d_look, x_lc_min, x_lc_end;
   int window, n_windows;
   uint64_t seed;
+  double th_jitter;   /* R12: half-width of each trip's incentive-threshold offset (0: off) */
 } or_params;
 
 /* per-vehicle record of one step (indexed by trip id; valid where active_before == 1) */

@@ -422,6 +422,7 @@ int ms_create(void **out, const ms_params *p, void *cuda_stream) {
       !(p->idm_s0 >= 0))
     return bad("dt, veh_len, idm_a, idm_b must be > 0; idm_T, idm_s0 >= 0");
   if (!(p->p_lc >= 0 && p->p_lc <= 1)) return bad("p_lc must be in [0, 1]");
+  if (!(p->mobil_th_jitter >= 0)) return bad("mobil_th_jitter must be >= 0");
   if (!(p->a_min < 0) || !(p->v_max > 0) || !(p->d_look > 0)) return bad("a_min < 0, v_max > 0, d_look > 0 required");
   if (p->window <= 0 || p->n_windows < 0) return bad("window > 0 and n_windows >= 0 required");
   if (s->prm.block % 32 || s->prm.block < 32 || s->prm.block > 512) return bad("block must be a multiple of 32 in [32, 512]");
@@ -437,6 +438,7 @@ int ms_create(void **out, const ms_params *p, void *cuda_stream) {
   P.n_windows = p->n_windows;
   P.debug = p->debug;
   P.id_base = p->id_base;
+  P.th_jitter = p->mobil_th_jitter;
   s->stream = (cudaStream_t)cuda_stream;
   cudaError_t e = cudaGetDevice(&s->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, s->device);

@@ -69,6 +69,7 @@ struct DevParams {
   unsigned long long seed;
   int window, n_windows, debug, n_lanes;
   int id_base;           // added to trip ids in the lane-change gate hash
+  float th_jitter;       // half-width of each trip's incentive-threshold offset (0: off)
 };
 
 // Link plan of a route entry r (edge e = routes[r]), one 64-bit word built at load time:
@@ -507,8 +508,16 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
       delta += P.p * (aO_new - aO_old);
     }
     r.inc = delta;
-    mark(flag, delta - P.th);
-    if (!(delta > P.th)) return r;
+    // incentive threshold: mobil_th, offset per trip when the jitter variant is on (the
+    // salted draw is fixed for the trip; its low 32 bits never equal the gate draw's)
+    float th = P.th;
+    if (P.th_jitter > 0.f) {
+      const unsigned long long hj = splitmix64(P.seed ^ 0x9E3779B97F4A7C15ULL ^
+                                               (unsigned long long)(unsigned)(myid + P.id_base));
+      th += P.th_jitter * (2.f * ((float)(uint32_t)(hj >> 40) * 0x1p-24f) - 1.f);
+    }
+    mark(flag, delta - th);
+    if (!(delta > th)) return r;
   }
   r.dir = step_dir;
   return r;

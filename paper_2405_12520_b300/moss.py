@@ -29,7 +29,7 @@ class ms_params(C.Structure):
         "dt", "veh_len", "idm_a", "idm_b", "idm_T", "idm_s0", "mobil_p", "mobil_th", "mobil_bsafe",
         "p_lc", "a_min", "v_max", "d_look", "x_lc_min", "x_lc_end")] + [
         ("window", C.c_int), ("n_windows", C.c_int), ("seed", C.c_uint64), ("debug", C.c_int),
-        ("block", C.c_int), ("id_base", C.c_int)]
+        ("block", C.c_int), ("id_base", C.c_int), ("mobil_th_jitter", C.c_float)]
 
 
 class ms_network(C.Structure):
@@ -168,7 +168,8 @@ def params_struct(params: dict, debug: bool = False, n_windows: int = 1, block: 
     return ms_params(p["dt"], p["veh_len"], p["idm_a"], p["idm_b"], p["idm_T"], p["idm_s0"],
                      p["mobil_p"], p["mobil_th"], p["mobil_bsafe"], p["p_lc"], p["a_min"], p["v_max"],
                      p["d_look"], p["x_lc_min"], p["x_lc_end"], int(p["window"]), int(n_windows),
-                     int(p["seed"]) & 0xFFFFFFFFFFFFFFFF, int(debug), int(block), int(id_base))
+                     int(p["seed"]) & 0xFFFFFFFFFFFFFFFF, int(debug), int(block), int(id_base),
+                     float(p.get("mobil_th_jitter", 0.0)))
 
 
 class Sim:

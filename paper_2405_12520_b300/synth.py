@@ -98,7 +98,8 @@ def default_params(**over) -> dict:
              idm_a=2.0, idm_b=4.5, idm_T=1.5, idm_s0=2.0,
              mobil_p=0.1, mobil_th=0.2, mobil_bsafe=4.0,
              p_lc=1.0, a_min=-9.0, v_max=20.0, d_look=200.0,
-             x_lc_min=25.0, x_lc_end=20.0, window=300, seed=1)
+             x_lc_min=25.0, x_lc_end=20.0, window=300, seed=1,
+             mobil_th_jitter=0.0)   # R12 threshold jitter (a randomized-MOBIL variant), off
     p.update(over)
     return p
 

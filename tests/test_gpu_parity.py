@@ -63,6 +63,29 @@ def test_single_steps_match_oracle(kind, n_place, n_wait, spacing, ifrac, t0, p_
     assert tot["changes"] > 0 or p_lc < 1.0
 
 
+@pytest.mark.parametrize("kind,t0", [("grid12x3", 64), ("delaunay", 3)])
+def test_single_steps_match_oracle_threshold_jitter(kind, t0):
+    """The randomized-MOBIL variant with per-trip threshold jitter (R12)."""
+    _need_gpu()
+    net = _net(kind)
+    dem = synth.place_vehicles(net, 5003 if kind == "grid12x3" else 2500, seed=17 + t0, min_spacing=7.0,
+                               internal_frac=0.3)
+    params = dict(P, mobil_th_jitter=0.6, seed=99 + t0)
+    sim = parity.gpu_sim(net, dem, params)
+    st = sim.read_state()
+    st["t"] = t0
+    sim.write_state(st)
+    orc = oracle.Oracle(net, dem, params)
+    rep = []
+    for k in range(8):
+        _, gd, gs, od, os_ = parity.step_pair(sim, orc)
+        parity.compare_step(gd, gs, od, os_, dem.n, report=rep)
+    tot = {k: sum(r[k] for r in rep) for k in rep[0]}
+    print(kind, tot)
+    assert tot["compared"] > 0.9 * tot["active"]
+    assert tot["changes"] > 0
+
+
 def test_lockstep_small_grid_full_run():
     """The small grid workload run on the GPU for 3600 steps; every 5th step the oracle
     repeats the GPU's step from the GPU's state."""

@@ -266,6 +266,69 @@ def test_mobil_zones_and_gate(oracle_lib):
     assert d["lc_cand"][0] == 0
 
 
+JITTER_SALT = 0x9E3779B97F4A7C15
+
+
+def _trip_u(oracle_lib, seed, trip):
+    """The trip's 24-bit uniform of the threshold-jitter variant, from the published
+    SplitMix64 (pinned above)."""
+    return (oracle_lib.splitmix64((seed ^ JITTER_SALT ^ trip) % 2 ** 64) >> 40) / 2.0 ** 24
+
+
+def test_mobil_threshold_jitter_per_trip(oracle_lib):
+    """Free-gain case (incentive a_max(1 - (v/v0)^4), closed form): with the jitter variant
+    the change happens exactly when the incentive beats the trip's threshold
+    th + J(2u - 1), for seeds whose draws fall on both sides."""
+    v, v0, J = 10.0, 13.9, 2.0
+    se = (P["idm_s0"] + v * P["idm_T"]) / math.sqrt(1 - (v / v0) ** 4)
+    gain = P["idm_a"] * (1 - (v / float(np.float32(v0))) ** 4)
+    seen = set()
+    for seed in range(1, 41):
+        th = P["mobil_th"] + J * (2 * _trip_u(oracle_lib, seed, 0) - 1)
+        if abs(gain - th) < 1e-3:
+            continue
+        d = _two_lane_case([0, 0], [100.0, 100.0 + P["veh_len"] + se], [v, v], seed=seed, mobil_th_jitter=J)
+        assert d["incentive"][0] == pytest.approx(gain, abs=1e-6)
+        want = +1 if gain > th else 0
+        assert d["lc_dir"][0] == want, (seed, th)
+        seen.add(want)
+    assert seen == {0, 1}
+    # jitter 0: the plain threshold, whatever the seed
+    d = _two_lane_case([0, 0], [100.0, 100.0 + P["veh_len"] + se], [v, v], seed=7, mobil_th=gain + 0.01)
+    assert d["lc_dir"][0] == 0
+
+
+def test_mobil_threshold_jitter_is_uniform_over_trips(oracle_lib):
+    """Many independent free-gain pairs (one per edge of a long road): the share of
+    followers that change matches P(th + J(2u - 1) < gain) = (gain - th + J) / (2J) for a
+    uniform u, within 4 standard deviations; without jitter all of them change."""
+    import oracle
+    n_nodes, v, v0, J = 400, 10.0, 13.9, 2.0
+    net = netkit.line(n_nodes, 300.0, 2)
+    se = (P["idm_s0"] + v * P["idm_T"]) / math.sqrt(1 - (v / v0) ** 4)
+    lanes, xs, routes = [], [], []
+    for e in range(n_nodes - 1):   # edges 0 .. n-2 run k -> k+1
+        l0 = int(net.edge_lane0[e])
+        lanes += [l0, l0]
+        xs += [100.0, 100.0 + P["veh_len"] + se]
+        r = [e, e + 1] if e + 1 < n_nodes - 1 else [e]
+        routes += [r, r]
+    dem = netkit.vehicles(lanes, xs, [v] * len(lanes), routes, v0=v0)
+    gain = P["idm_a"] * (1 - (v / float(np.float32(v0))) ** 4)
+    share = {}
+    for jit in (0.0, J):
+        o = oracle.Oracle(net, dem, dict(P, mobil_th_jitter=jit, seed=11))
+        err, d = o.step(debug=True)
+        assert err == 0
+        foll = np.arange(0, dem.n, 2)
+        assert np.allclose(d["incentive"][foll], gain, atol=1e-6)
+        share[jit] = float(np.mean(d["lc_dir"][foll] == 1))
+    assert share[0.0] == 1.0
+    p = (gain - P["mobil_th"] + J) / (2 * J)
+    sd = math.sqrt(p * (1 - p) / (n_nodes - 1))
+    assert abs(share[J] - p) <= 4 * sd, (share[J], p)
+
+
 def test_mandatory_change_toward_connecting_lane(oracle_lib):
     """A 3-lane approach whose lane 0 serves only the right turn: a vehicle on lane 0
     heading straight must move left, with no incentive test."""

@@ -72,6 +72,15 @@ typedef struct ms_params {
                       bits of SplitMix64(seed ^ 0x9E3779B97F4A7C15 ^ (i + id_base)) / 2^24,
                       fixed for the trip (driver heterogeneity; Sec. III-A "randomized
                       improvement" leaves the form open); 0 = off */
+  int signal_mode;  /* 0: fixed-time plans (ctrl_offset/green/yellow, Sec. IV-E "FP");
+                       1: max pressure (the paper's MP baseline, Sec. IV-E; Varaiya 2013 with
+                       unit saturation flows at lane level): every mp_interval steps each
+                       controller picks the phase whose approach-lane links carry the largest
+                       sum of (vehicles on the approach lane - vehicles on the link's target
+                       lane); the green phase wins a tie it is in, else the lowest index; a
+                       change shows the controller's ctrl_yellow seconds of yellow first.
+                       Needs ctrl_nphase <= 32 and ctrl_yellow < mp_interval (MS_ERR_ARG). */
+  int mp_interval;  /* steps between max-pressure decisions (signal_mode 1), >= 1 */
 } ms_params;
 
 /* Lane-level road network (Sec. III-C "Map Builder": lanes with topology, junction lanes,
@@ -131,6 +140,11 @@ typedef struct ms_state {
   float *x, *v;                 /* [capacity] */
   int *trip_status; /* [n_trips] 0 waiting, 1 active, 2 arrived (read only) */
   int *t_arr;       /* [n_trips] arrival step or -1 */
+  int *ctrl_state;  /* [3 * n_ctrl] host memory (also with ms_read_state's device flag) or
+                       NULL: max-pressure controllers at step t: green phase, pending phase
+                       (-1 none), step at which it turns green.  Read: filled if not NULL.
+                       Write: restored if not NULL, else every controller restarts with
+                       phase 0 green and nothing pending. */
 } ms_state;
 
 typedef struct ms_metrics {

@@ -41,7 +41,8 @@ class _Params(C.Structure):
     _fields_ = [(f, C.c_double) for f in (
         "dt", "veh_len", "a", "b", "T", "s0", "p", "th", "bsafe", "p_lc", "a_min", "v_max",
         "d_look", "x_lc_min", "x_lc_end")] + [("window", C.c_int), ("n_windows", C.c_int),
-                                             ("seed", C.c_uint64), ("th_jitter", C.c_double)]
+                                             ("seed", C.c_uint64), ("th_jitter", C.c_double),
+                                             ("signal_mode", C.c_int), ("mp_interval", C.c_int)]
 
 
 _DBG_INT = ("active_before", "lead_kind", "lead_id")
@@ -79,6 +80,8 @@ def _load():
         lib.or_neighbors.argtypes = [C.c_void_p, C.c_void_p]
         lib.or_departure_lane.argtypes = [C.c_void_p, C.c_int]
         lib.or_departure_lane.restype = C.c_int
+        lib.or_get_ctrl_state.argtypes = [C.c_void_p, C.c_void_p]
+        lib.or_set_ctrl_state.argtypes = [C.c_void_p, C.c_void_p]
         _lib = lib
     return _lib
 
@@ -104,6 +107,7 @@ class Oracle:
             self._keep.append(a)
             return _p(a)
         self.n_lanes = net.n_lanes
+        self.n_ctrl = net.n_ctrl
         self.n = dem.n
         self.n_windows = n_windows
         self.net_c = _Net(net.n_lanes, net.n_edges, net.n_ctrl,
@@ -119,7 +123,8 @@ class Oracle:
                              p["mobil_p"], p["mobil_th"], p["mobil_bsafe"], p["p_lc"], p["a_min"],
                              p["v_max"], p["d_look"], p["x_lc_min"], p["x_lc_end"],
                              int(p["window"]), int(n_windows), int(p["seed"]),
-                             float(p.get("mobil_th_jitter", 0.0)))
+                             float(p.get("mobil_th_jitter", 0.0)),
+                             int(p.get("signal_mode", 0)), int(p.get("mp_interval", 10)))
         self.t_dep = i32(dem.t_dep)
         self.v0 = np.ascontiguousarray(dem.v0, np.float32)
         self.route_off = np.ascontiguousarray(dem.route_off, np.int64)
@@ -178,6 +183,18 @@ class Oracle:
 
     def signal_state(self, lane: int, t: int) -> int:
         return _load().or_signal_state(self.h, lane, t)
+
+    def ctrl_state(self) -> np.ndarray:
+        """Max-pressure controller state (R13): [n_ctrl, 3] = green phase, pending phase
+        (-1 none), step at which the pending phase turns green."""
+        out = np.zeros((max(1, self.n_ctrl), 3), np.int32)
+        _load().or_get_ctrl_state(self.h, _p(out))
+        return out[:self.n_ctrl]
+
+    def set_ctrl_state(self, cs) -> None:
+        cs = np.ascontiguousarray(np.asarray(cs, np.int32).reshape(-1, 3))
+        assert cs.shape[0] == self.n_ctrl
+        _load().or_set_ctrl_state(self.h, _p(cs))
 
     def neighbors(self) -> np.ndarray:
         out = np.zeros(6 * self.n, np.int32)

@@ -62,6 +62,17 @@
  *  R11 Lane links fan out (every turning lane links to every lane of its exit edge, in a
  *      preferred order); a vehicle takes the first link whose target lane serves the route
  *      edge after the exit edge, so it enters each edge on a lane that serves its next turn.
+ *  R13 Max-pressure signals (signal_mode 1; Varaiya 2013 with unit saturation flows, at
+ *      lane level).  Each controller keeps a green phase g, a pending phase and the step
+ *      at which it turns green.  At the start of step t, a pending phase whose time has
+ *      come becomes g.  Then, at a decision step (t mod mp_interval = 0) with nothing
+ *      pending, every phase's pressure is summed over the lane links of its approach
+ *      lanes: the vehicles on the approach lane minus the vehicles on the link's target
+ *      lane (snapshot counts at t).  The phase of highest pressure wins; g wins a tie it
+ *      is in, else the lowest phase index.  A winner other than g turns g yellow for the
+ *      controller's yellow time (then the winner is green), or at once when that is 0.
+ *      Lanes of phase g are green, or yellow while a phase is pending; all others red.
+ *      Controllers start with phase 0 green and nothing pending.
  *  R12 Threshold jitter (a randomized-MOBIL variant, off when th_jitter = 0): trip c's
  *      incentive threshold is th + th_jitter (2u - 1), u = (SplitMix64(seed ^ 0x9E3779B97F4A7C15
  *      ^ c) >> 40) / 2^24, fixed for the trip (driver heterogeneity); the salt keeps these
@@ -110,6 +121,10 @@ struct or_sim {
   /* step outputs */
   int *n_lane, *n_rp, *n_status;
   double *n_x, *n_v;
+  /* R13 controllers */
+  int *mp_g, *mp_pend, *mp_yend;
+  int64_t *mp_pres;   /* per controller x phase pressure (scratch) */
+  int *mp_poff;       /* phase offsets into mp_pres */
 };
 
 /* ------------------------------------------------------------------------------------ */
@@ -167,9 +182,62 @@ static int route_at(const or_sim *s, int id, int k) {
   return s->route_edges[s->route_off[id] + k];
 }
 
+/* R13 */
+static void mp_reset(or_sim *s) {
+  for (int c = 0; c < s->net.n_ctrl; ++c) {
+    s->mp_g[c] = 0;
+    s->mp_pend[c] = -1;
+    s->mp_yend[c] = 0;
+  }
+}
+
+/* advance every controller to step s->t on the prepared snapshot (seg_cnt) */
+static void mp_advance(or_sim *s) {
+  const int t = s->t, C = s->net.n_ctrl;
+  const int decide = (t % s->p.mp_interval) == 0;
+  if (decide) {
+    memset(s->mp_pres, 0, sizeof(int64_t) * (size_t)s->mp_poff[C]);
+    for (int l = 0; l < s->net.n_lanes; ++l) {
+      const int c = s->net.lane_ctrl[l];
+      if (c < 0 || is_internal(s, l)) continue;
+      int64_t sum = 0;
+      for (int k = s->net.succ_off[l]; k < s->net.succ_off[l + 1]; ++k) {
+        const int il = s->net.succ_lane[k];
+        const int m = s->net.succ_lane[s->net.succ_off[il]];
+        sum += s->seg_cnt[l] - s->seg_cnt[m];
+      }
+      s->mp_pres[s->mp_poff[c] + s->net.lane_group[l]] += sum;
+    }
+  }
+  for (int c = 0; c < C; ++c) {
+    if (s->mp_pend[c] >= 0 && t >= s->mp_yend[c]) {
+      s->mp_g[c] = s->mp_pend[c];
+      s->mp_pend[c] = -1;
+    }
+    if (!decide || s->mp_pend[c] >= 0) continue;
+    const int64_t *pr = s->mp_pres + s->mp_poff[c];
+    const int np = s->net.ctrl_nphase[c];
+    int best = 0;
+    for (int ph = 1; ph < np; ++ph)
+      if (pr[ph] > pr[best]) best = ph;
+    if (pr[s->mp_g[c]] == pr[best]) best = s->mp_g[c];
+    if (best == s->mp_g[c]) continue;
+    if (s->net.ctrl_yellow[c] > 0) {
+      s->mp_pend[c] = best;
+      s->mp_yend[c] = t + s->net.ctrl_yellow[c];
+    } else {
+      s->mp_g[c] = best;
+    }
+  }
+}
+
 int or_signal_state(const or_sim *s, int l, int t) {
   int c = s->net.lane_ctrl[l];
   if (c < 0) return SIG_GREEN;
+  if (s->p.signal_mode == 1) {   /* R13: the controllers' current state */
+    if (s->net.lane_group[l] != s->mp_g[c]) return SIG_RED;
+    return s->mp_pend[c] >= 0 ? SIG_YELLOW : SIG_GREEN;
+  }
   int g = s->net.ctrl_green[c], y = s->net.ctrl_yellow[c], P = s->net.ctrl_nphase[c];
   int cyc = P * (g + y);
   int tau = ((t + s->net.ctrl_offset[c]) % cyc + cyc) % cyc;
@@ -474,6 +542,7 @@ int or_step(or_sim *s, or_debug *dbg) {
   const double L = p->veh_len;
   int err = 0;
   prepare(s);
+  if (p->signal_mode == 1) mp_advance(s);   /* R13: controllers at step t */
   /* R10 metrics on the snapshot */
   int w = s->t / p->window;
   if (w < p->n_windows) {
@@ -695,6 +764,15 @@ or_sim *or_create(const or_net *net, const or_params *p, int n_trips, const int 
   s->n_v = (double *)malloc((n + 1) * sizeof(double));
   s->vsum = (double *)calloc((size_t)p->n_windows * L, sizeof(double));
   s->vcnt = (int64_t *)calloc((size_t)p->n_windows * L, sizeof(int64_t));
+  {
+    const int C = net->n_ctrl;
+    s->mp_g = (int *)calloc((size_t)C + 1, sizeof(int));
+    s->mp_pend = (int *)calloc((size_t)C + 1, sizeof(int));
+    s->mp_yend = (int *)calloc((size_t)C + 1, sizeof(int));
+    s->mp_poff = (int *)calloc((size_t)C + 1, sizeof(int));
+    for (int c = 0; c < C; ++c) s->mp_poff[c + 1] = s->mp_poff[c] + net->ctrl_nphase[c];
+    s->mp_pres = (int64_t *)calloc((size_t)s->mp_poff[C] + 1, sizeof(int64_t));
+  }
   for (size_t i = 0; i < n; ++i) {
     s->t_arr[i] = -1;
     if (lane0 && lane0[i] >= 0) {
@@ -734,11 +812,13 @@ or_sim *or_create(const or_net *net, const or_params *p, int n_trips, const int 
       s->pred_ids[s->pred_off[tg] + fill[tg]++] = (int)l;
     }
   free(fill);
+  mp_reset(s);
   return s;
 }
 
 void or_destroy(or_sim *s) {
   if (!s) return;
+  free(s->mp_g); free(s->mp_pend); free(s->mp_yend); free(s->mp_pres); free(s->mp_poff);
   free(s->status); free(s->lane); free(s->rp); free(s->t_arr); free(s->x); free(s->v);
   free(s->dep_lane); free(s->order); free(s->pos); free(s->seg_start); free(s->seg_cnt);
   free(s->n_lane); free(s->n_rp); free(s->n_status); free(s->n_x); free(s->n_v);
@@ -770,6 +850,27 @@ void or_set_state(or_sim *s, const int *status, const int *lane, const double *x
   if (t_arr) memcpy(s->t_arr, t_arr, n * sizeof(int));
   s->t = t;
   for (int l = 0; l < s->net.n_lanes; ++l) s->q_head[l] = s->q_off[l];
+  mp_reset(s);
+}
+
+void or_get_ctrl_state(or_sim *s, int *out) {
+  if (s->p.signal_mode == 1) {
+    prepare(s);
+    mp_advance(s);
+  }
+  for (int c = 0; c < s->net.n_ctrl; ++c) {
+    out[3 * c] = s->mp_g[c];
+    out[3 * c + 1] = s->mp_pend[c];
+    out[3 * c + 2] = s->mp_yend[c];
+  }
+}
+
+void or_set_ctrl_state(or_sim *s, const int *in) {
+  for (int c = 0; c < s->net.n_ctrl; ++c) {
+    s->mp_g[c] = in[3 * c];
+    s->mp_pend[c] = in[3 * c + 1];
+    s->mp_yend[c] = in[3 * c + 2];
+  }
 }
 
 void or_get_metrics(const or_sim *s, double *vsum, int64_t *vcnt, int64_t *counters) {

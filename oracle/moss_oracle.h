@@ -36,6 +36,8 @@ typedef struct {
   int window, n_windows;
   uint64_t seed;
   double th_jitter;   /* R12: half-width of each trip's incentive-threshold offset (0: off) */
+  int signal_mode;    /* 0: fixed-time plans (R9); 1: max pressure (R13) */
+  int mp_interval;    /* R13: steps between phase decisions */
 } or_params;
 
 /* per-vehicle record of one step (indexed by trip id; valid where active_before == 1) */
@@ -71,6 +73,12 @@ void or_set_state(or_sim *s, const int *status, const int *lane, const double *x
 /* per-window per-lane speed sums and counts [n_windows][n_lanes] */
 void or_get_metrics(const or_sim *s, double *vsum, int64_t *vcnt, int64_t *counters);
 int or_signal_state(const or_sim *s, int lane, int t); /* 0 green, 1 yellow, 2 red */
+/* R13 controller state, 3 ints per controller: green phase, pending phase (-1 none), step
+   at which the pending phase turns green.  or_create / or_set_state reset it to {0, -1, 0}.
+   The getter first advances the controllers to the current step t (on the snapshot at t;
+   advancing twice to the same step changes nothing), so it reports the state step t uses. */
+void or_get_ctrl_state(or_sim *s, int *out);
+void or_set_ctrl_state(or_sim *s, const int *in);
 uint64_t or_splitmix64(uint64_t state);
 /* neighbour search on the current snapshot (for the brute-force check): for each trip id:
    own-lane leader, own-lane follower, left-lane leader/follower, right-lane leader/follower

@@ -56,6 +56,8 @@ struct Sim {
   int4 *d_ctrl4 = nullptr;
   std::vector<int4> h_ctrl4;
   int *d_sig[2]{};   // signal table per step parity (see sig_pack)
+  int4 *d_mp = nullptr;                             // max-pressure controller state
+  int *d_ctrl_loff = nullptr, *d_ctrl_lanes = nullptr;   // approach lanes per controller
   int *d_routes = nullptr;
   unsigned long long *d_plan = nullptr;
   Soa A[2]{};
@@ -127,6 +129,9 @@ StepArgs make_args(Sim *s) {
   a.sig[0] = s->d_sig[0];
   a.sig[1] = s->d_sig[1];
   a.n_ctrl = s->n_ctrl;
+  a.mp = s->d_mp;
+  a.ctrl_loff = s->d_ctrl_loff;
+  a.ctrl_lanes = s->d_ctrl_lanes;
   a.routes = s->d_routes;
   a.plan = s->d_plan;
   a.A[0] = s->A[0];
@@ -182,6 +187,8 @@ cudaError_t launch_step(const Sim *s, const StepArgs &a, cudaStream_t st, cudaEv
   k_bucket<<<c.grid_bucket, c.blk_bucket, 0, st>>>(a, s->n_tiles);
   if (ev) cudaEventRecord(ev[3], st);
   k_apply<<<c.grid_apply, c.blk_apply, 0, st>>>(a);
+  if (s->P.signal_mode == 1 && s->n_ctrl > 0)   // controllers of the next step
+    k_signals<<<(s->n_ctrl + 7) / 8, 256, 0, st>>>(a);
   if (ev) cudaEventRecord(ev[4], st);
   if (s->prm.debug) k_check<<<c.grid_bucket, c.blk_bucket, 0, st>>>(a);
   return cudaGetLastError();
@@ -308,7 +315,7 @@ int upload_queues(Sim *s, const std::vector<int> &qhead) {
 
 int upload_state(Sim *s, const std::vector<int> &ids, const std::vector<int> &lanes,
                  const std::vector<float> &xs, const std::vector<float> &vs,
-                 const std::vector<int> &route_idx, int t) {
+                 const std::vector<int> &route_idx, int t, const int *ctrl_state) {
   // vehicles must be sorted by (lane, x, id); builds the SoA of parity t & 1
   const int n = (int)ids.size();
   if (n > s->n_trips) return fail(s, MS_ERR_CAPACITY, "more active vehicles than trips");
@@ -384,7 +391,7 @@ int upload_state(Sim *s, const std::vector<int> &ids, const std::vector<int> &la
     CK(cudaMemcpyAsync(B.id, ids.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
   }
   CK(cudaMemcpyAsync(s->d_dyn[p], dyn.data(), s->n_lanes * sizeof(int4), cudaMemcpyHostToDevice, st));
-  {   // signal table of step t (later steps' tables are written by k_lanes)
+  if (s->prm.signal_mode == 0) {   // signal table of step t (later steps': k_lanes)
     std::vector<int> sig(s->h_ctrl4.size(), 0);
     for (int c = 0; c < s->n_ctrl; ++c) sig[c] = sig_pack(s->h_ctrl4[c], t);
     CK(cudaMemcpyAsync(s->d_sig[p], sig.data(), sig.size() * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -399,6 +406,21 @@ int upload_state(Sim *s, const std::vector<int> &ids, const std::vector<int> &la
   c.n_movers = 0;
   c.tile_ticket = 0;
   CK(cudaMemcpyAsync(s->d_ctrl, &c, sizeof(DevCtrl), cudaMemcpyHostToDevice, st));
+  if (s->prm.signal_mode == 1 && s->n_ctrl > 0) {
+    // max-pressure controllers: restored, or restarted with phase 0 green; then advanced to
+    // step t on the uploaded state (a no-op for a state already at t), which writes the
+    // signal table of step t
+    std::vector<int4> mp(s->n_ctrl, make_int4(0, -1, 0, 0));
+    if (ctrl_state)
+      for (int k = 0; k < s->n_ctrl; ++k) {
+        mp[k] = make_int4(ctrl_state[3 * k], ctrl_state[3 * k + 1], ctrl_state[3 * k + 2], 0);
+        if (mp[k].x < 0 || mp[k].x >= s->h_ctrl4[k].w || mp[k].y < -1 || mp[k].y >= s->h_ctrl4[k].w)
+          return fail(s, MS_ERR_ARG, "ctrl_state phase out of range");
+      }
+    CK(cudaMemcpyAsync(s->d_mp, mp.data(), mp.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    k_signals<<<(s->n_ctrl + 7) / 8, 256, 0, st>>>(make_args(s));
+    CK(cudaGetLastError());
+  }
   CK(cudaStreamSynchronize(st));
   return MS_OK;
 }
@@ -423,6 +445,8 @@ int ms_create(void **out, const ms_params *p, void *cuda_stream) {
     return bad("dt, veh_len, idm_a, idm_b must be > 0; idm_T, idm_s0 >= 0");
   if (!(p->p_lc >= 0 && p->p_lc <= 1)) return bad("p_lc must be in [0, 1]");
   if (!(p->mobil_th_jitter >= 0)) return bad("mobil_th_jitter must be >= 0");
+  if (p->signal_mode != 0 && p->signal_mode != 1) return bad("signal_mode must be 0 or 1");
+  if (p->signal_mode == 1 && p->mp_interval < 1) return bad("mp_interval must be >= 1");
   if (!(p->a_min < 0) || !(p->v_max > 0) || !(p->d_look > 0)) return bad("a_min < 0, v_max > 0, d_look > 0 required");
   if (p->window <= 0 || p->n_windows < 0) return bad("window > 0 and n_windows >= 0 required");
   if (s->prm.block % 32 || s->prm.block < 32 || s->prm.block > 512) return bad("block must be a multiple of 32 in [32, 512]");
@@ -439,6 +463,8 @@ int ms_create(void **out, const ms_params *p, void *cuda_stream) {
   P.debug = p->debug;
   P.id_base = p->id_base;
   P.th_jitter = p->mobil_th_jitter;
+  P.signal_mode = p->signal_mode;
+  P.mp_interval = p->mp_interval;
   s->stream = (cudaStream_t)cuda_stream;
   cudaError_t e = cudaGetDevice(&s->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, s->device);
@@ -577,6 +603,28 @@ int ms_load_network(void *sim, const ms_network *net) {
   DALLOC(s->d_sig[0], c4.size());
   DALLOC(s->d_sig[1], c4.size());
   s->h_ctrl4 = c4;
+  {   // approach edge lanes of each controller, for the max-pressure controllers
+    std::vector<int> off(c4.size() + 1, 0), lanes;
+    for (int l = 0; l < L; ++l)
+      if (net->lane_ctrl[l] >= 0 && s->lane_edge[l] >= 0) off[net->lane_ctrl[l] + 1]++;
+    for (size_t c = 0; c < c4.size(); ++c) off[c + 1] += off[c];
+    lanes.assign(std::max(1, off[c4.size()]), 0);
+    std::vector<int> fill(off.begin(), off.end() - 1);
+    for (int l = 0; l < L; ++l)
+      if (net->lane_ctrl[l] >= 0 && s->lane_edge[l] >= 0) lanes[fill[net->lane_ctrl[l]]++] = l;
+    if (s->prm.signal_mode == 1)
+      for (int c = 0; c < C; ++c) {
+        if (c4[c].w > 32) return fail(s, MS_ERR_ARG, "max-pressure control takes at most 32 phases per controller");
+        if (c4[c].z >= s->prm.mp_interval) return fail(s, MS_ERR_ARG, "ctrl_yellow must be below mp_interval");
+      }
+    DALLOC(s->d_mp, c4.size());
+    std::vector<int4> mp0(c4.size(), make_int4(0, -1, 0, 0));
+    CK(cudaMemcpy(s->d_mp, mp0.data(), mp0.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    DALLOC(s->d_ctrl_loff, off.size());
+    DALLOC(s->d_ctrl_lanes, lanes.size());
+    CK(cudaMemcpy(s->d_ctrl_loff, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s->d_ctrl_lanes, lanes.data(), lanes.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
   CK(cudaMemcpy(s->d_li, li.data(), L * sizeof(LaneInfo), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->d_succ, succ.data(), succ.size() * sizeof(int2), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->d_pred, pred.data(), pred.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -778,7 +826,7 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
     vs.push_back(veh->v[i]);
     ridx.push_back(0);
   }
-  int r = upload_state(s, ids, lanes, xs, vs, ridx, 0);
+  int r = upload_state(s, ids, lanes, xs, vs, ridx, 0, nullptr);
   if (r) {
     s->veh_loaded = false;
     return r;
@@ -901,7 +949,15 @@ int ms_read_state(void *sim, ms_state *out, int device) {
   std::vector<int> tarr(out->t_arr || out->trip_status ? s->n_trips : 0);
   if (out->t_arr || out->trip_status)
     CK(cudaMemcpyAsync(tarr.data(), s->d_tarr, s->n_trips * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  std::vector<int4> mp(out->ctrl_state ? s->n_ctrl : 0);
+  if (!mp.empty())
+    CK(cudaMemcpyAsync(mp.data(), s->d_mp, mp.size() * sizeof(int4), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
+  for (size_t k = 0; k < mp.size(); ++k) {   // host memory in either mode
+    out->ctrl_state[3 * k] = mp[k].x;
+    out->ctrl_state[3 * k + 1] = mp[k].y;
+    out->ctrl_state[3 * k + 2] = mp[k].z;
+  }
   if (host_ridx)
     for (int i = 0; i < n; ++i) out->route_idx[i] = rp[i] - s->h_route0[ids[i]];
   if (out->t_arr) std::memcpy(out->t_arr, tarr.data(), s->n_trips * sizeof(int));
@@ -930,7 +986,7 @@ int ms_write_state(void *sim, const ms_state *in) {
     if (ids[i] >= 0 && ids[i] < s->n_trips) active[ids[i]] = 1;
   for (int i = 0; i < s->n_trips; ++i)
     if (active[i] && in->t_arr[i] >= 0) return fail(s, MS_ERR_ARG, "trip both active and arrived");
-  int r = upload_state(s, ids, lanes, xs, vs, ridx, in->t);
+  int r = upload_state(s, ids, lanes, xs, vs, ridx, in->t, in->ctrl_state);
   if (r) return r;
   // queue heads: first waiting trip of each FIFO
   std::vector<int> qhead(s->n_lanes);
@@ -1174,6 +1230,7 @@ int snap_take(Sim *s, Snapshot &sn) {
   add(s->d_ctrl, sizeof(DevCtrl));
   add(s->d_qhd, L * 8);
   add(s->d_sig[0], s->h_ctrl4.size() * 4);
+  add(s->d_mp, s->h_ctrl4.size() * 16);
   add(s->d_sig[1], s->h_ctrl4.size() * 4);
   add(s->d_tarr, N * 4);
   add(s->d_vsum, W * 4);

@@ -21,6 +21,7 @@
 // Stayers keep their relative order (no overtaking within a lane), so the t+1 order is a
 // merge of the stayers with the few arrivals; no full sort is needed.
 #pragma once
+#include <climits>
 #include <cstdint>
 #include <cuda/atomic>
 #include <cuda_runtime.h>
@@ -70,6 +71,8 @@ struct DevParams {
   int window, n_windows, debug, n_lanes;
   int id_base;           // added to trip ids in the lane-change gate hash
   float th_jitter;       // half-width of each trip's incentive-threshold offset (0: off)
+  int signal_mode;       // 0 fixed-time plans, 1 max pressure
+  int mp_interval;       // steps between max-pressure decisions
 };
 
 // Link plan of a route entry r (edge e = routes[r]), one 64-bit word built at load time:
@@ -151,6 +154,9 @@ struct StepArgs {
   const int4 *ctrl4;   // {offset, green, yellow, nphase}
   int *sig[2];         // per controller, for the steps of parity 0 / 1: 2 * phase + yellow
   int n_ctrl;
+  int4 *mp;            // max-pressure controllers: {green phase, pending phase or -1, step
+                       // the pending phase turns green, 0}
+  const int *ctrl_loff, *ctrl_lanes;   // approach edge lanes of each controller (CSR)
   const int *routes;   // per trip: its edges then -1
   const unsigned long long *plan;   // link plan per routes[] entry
   Soa A[2];
@@ -1065,9 +1071,11 @@ __global__ void __launch_bounds__(LANE_THREADS, 4) k_lanes(StepArgs a) {
       a.ctrl->t_apply = t;
     }
   }
-  // signal table of step t + 1 (the next k_decide reads it)
-  for (int c = tile * LANE_THREADS + threadIdx.x; c < a.n_ctrl; c += gridDim.x * LANE_THREADS)
-    a.sig[(t + 1) & 1][c] = sig_pack(a.ctrl4[c], t + 1);
+  // signal table of step t + 1 (the next k_decide reads it); max-pressure controllers
+  // are advanced by k_signals instead
+  if (a.P.signal_mode == 0)
+    for (int c = tile * LANE_THREADS + threadIdx.x; c < a.n_ctrl; c += gridDim.x * LANE_THREADS)
+      a.sig[(t + 1) & 1][c] = sig_pack(a.ctrl4[c], t + 1);
   n_ins = __reduce_add_sync(0xffffffffu, n_ins);
   if (lane == 0 && n_ins) atomicAdd(&a.ctrl->inserted, (unsigned long long)n_ins);
 }
@@ -1213,6 +1221,82 @@ __global__ void k_check(StepArgs a) {
     int la = S.lane[i], lb = S.lane[i + 1];
     if (la > lb || (la == lb && (S.x[i + 1] - a.P.L) - S.x[i] < -1e-3f))
       atomicOr(&a.ctrl->err, DEV_ORDER);
+  }
+}
+
+// Max-pressure controllers (Varaiya 2013 with unit saturation flows, at lane level),
+// advanced to step t = ctrl->t on that step's lane counts; writes the signal table of step
+// t.  One warp per controller.  Advancing twice to the same step changes nothing, so the
+// host can also run it after every state upload.  At step t a pending phase whose time has
+// come turns green; at a decision step (t mod mp_interval = 0) with nothing pending, the
+// pressure of phase q is the sum over its approach lanes' links of (vehicles on the
+// approach lane - vehicles on the link's target lane); the green phase wins a tie it is
+// in, else the lowest index; a different winner first shows the green phase yellow for the
+// controller's yellow time (or turns green at once when that is 0).
+__global__ void k_signals(StepArgs a) {
+  const int c = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (c >= a.n_ctrl) return;   // whole warps
+  const int lane = threadIdx.x & 31;
+  const int t = a.ctrl->t;
+  const int p = t & 1;
+  const int4 *dyn = a.dyn[p];
+  const int4 cc = a.ctrl4[c];   // {offset, green, yellow, nphase}
+  int4 st = a.mp[c];
+  if (st.y >= 0 && t >= st.z) {
+    st.x = st.y;
+    st.y = -1;
+  }
+  if (t % a.P.mp_interval == 0 && st.y < 0) {
+    // phase q's pressure ends up in warp lane q
+    long long mine = 0;
+    const int b = a.ctrl_loff[c], e = a.ctrl_loff[c + 1];
+    for (int j0 = b; j0 < e; j0 += 32) {
+      const int j = j0 + lane;
+      long long contrib = 0;
+      int grp = -1;
+      if (j < e) {
+        const int l = a.ctrl_lanes[j];
+        const LaneInfo li = a.li[l];
+        const int ql = dyn[l].y;
+        grp = li.group;
+        for (int k = 0; k < li.n_succ; ++k) {
+          const int tg = a.li[a.succ[li.succ + k].x].succ;   // internal lane's target
+          contrib += ql - dyn[tg].y;
+        }
+      }
+      for (int q = 0; q < cc.w; ++q) {
+        long long v = grp == q ? contrib : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == q) mine += v;
+      }
+    }
+    // highest pressure, lowest phase index on ties
+    long long bv = lane < cc.w ? mine : LLONG_MIN;
+    int bi = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    const long long gv = __shfl_sync(0xffffffffu, mine, st.x & 31);
+    if (gv == bv) bi = st.x;
+    if (bi != st.x) {
+      if (cc.z > 0) {
+        st.y = bi;
+        st.z = t + cc.z;
+      } else {
+        st.x = bi;
+      }
+    }
+  }
+  if (lane == 0) {
+    a.mp[c] = st;
+    a.sig[p][c] = 2 * st.x + (st.y >= 0 ? 1 : 0);
   }
 }
 

@@ -29,7 +29,8 @@ class ms_params(C.Structure):
         "dt", "veh_len", "idm_a", "idm_b", "idm_T", "idm_s0", "mobil_p", "mobil_th", "mobil_bsafe",
         "p_lc", "a_min", "v_max", "d_look", "x_lc_min", "x_lc_end")] + [
         ("window", C.c_int), ("n_windows", C.c_int), ("seed", C.c_uint64), ("debug", C.c_int),
-        ("block", C.c_int), ("id_base", C.c_int), ("mobil_th_jitter", C.c_float)]
+        ("block", C.c_int), ("id_base", C.c_int), ("mobil_th_jitter", C.c_float),
+        ("signal_mode", C.c_int), ("mp_interval", C.c_int)]
 
 
 class ms_network(C.Structure):
@@ -47,7 +48,7 @@ class ms_vehicles(C.Structure):
 
 class ms_state(C.Structure):
     _fields_ = [("capacity", C.c_int), ("n_active", C.c_int), ("t", C.c_int)] + [
-        (f, C.c_void_p) for f in ("id", "lane", "route_idx", "x", "v", "trip_status", "t_arr")]
+        (f, C.c_void_p) for f in ("id", "lane", "route_idx", "x", "v", "trip_status", "t_arr", "ctrl_state")]
 
 
 class ms_metrics(C.Structure):
@@ -169,7 +170,8 @@ def params_struct(params: dict, debug: bool = False, n_windows: int = 1, block: 
                      p["mobil_p"], p["mobil_th"], p["mobil_bsafe"], p["p_lc"], p["a_min"], p["v_max"],
                      p["d_look"], p["x_lc_min"], p["x_lc_end"], int(p["window"]), int(n_windows),
                      int(p["seed"]) & 0xFFFFFFFFFFFFFFFF, int(debug), int(block), int(id_base),
-                     float(p.get("mobil_th_jitter", 0.0)))
+                     float(p.get("mobil_th_jitter", 0.0)), int(p.get("signal_mode", 0)),
+                     int(p.get("mp_interval", 10)))
 
 
 class Sim:
@@ -224,6 +226,7 @@ class Sim:
         s = self._net_struct(net, keep)
         self._check(self.lib.ms_load_network(self.h, C.byref(s)), "ms_load_network")
         self.n_lanes = int(net.n_lanes)
+        self.n_ctrl = int(net.n_ctrl)
 
     def add_vehicles(self, dem):
         keep = []
@@ -236,6 +239,7 @@ class Sim:
         arr = (ms_network * len(nets))(*[self._net_struct(n, keep) for n in nets])
         self._check(self.lib.ms_load_network_batch(self.h, len(nets), arr), "ms_load_network_batch")
         self.n_lanes = int(sum(n.n_lanes for n in nets))
+        self.n_ctrl = int(sum(n.n_ctrl for n in nets))
         self.n_scen = len(nets)
 
     def add_vehicles_batch(self, dems):
@@ -293,7 +297,10 @@ class Sim:
         if trips:
             out["trip_status"] = np.zeros(self.n_trips, np.int32)
             out["t_arr"] = np.zeros(self.n_trips, np.int32)
-        s = ms_state(n, 0, 0, *[_p(out.get(f)) for f in ("id", "lane", "route_idx", "x", "v", "trip_status", "t_arr")])
+        if getattr(self, "n_ctrl", 0) > 0:
+            out["ctrl_state"] = np.zeros((self.n_ctrl, 3), np.int32)
+        s = ms_state(n, 0, 0, *[_p(out.get(f)) for f in ("id", "lane", "route_idx", "x", "v", "trip_status", "t_arr",
+                                                          "ctrl_state")])
         self._check(self.lib.ms_read_state(self.h, C.byref(s), 0), "ms_read_state")
         out["t"] = s.t
         out["n_active"] = s.n_active
@@ -312,8 +319,10 @@ class Sim:
                     route_idx=np.ascontiguousarray(st["route_idx"], np.int32),
                     x=np.ascontiguousarray(st["x"], np.float32), v=np.ascontiguousarray(st["v"], np.float32),
                     t_arr=np.ascontiguousarray(st["t_arr"], np.int32))
+        cs = st.get("ctrl_state")
+        keep["ctrl_state"] = None if cs is None else np.ascontiguousarray(cs, np.int32).reshape(-1)
         s = ms_state(n, n, int(st["t"]), _p(keep["id"]), _p(keep["lane"]), _p(keep["route_idx"]),
-                     _p(keep["x"]), _p(keep["v"]), None, _p(keep["t_arr"]))
+                     _p(keep["x"]), _p(keep["v"]), None, _p(keep["t_arr"]), _p(keep["ctrl_state"]))
         self._check(self.lib.ms_write_state(self.h, C.byref(s)), "ms_write_state")
 
     def read_metrics(self, lanes: bool = True) -> dict:

@@ -53,17 +53,23 @@ def step_pair(sim: moss.Sim, orc: oracle.Oracle):
     st0 = sim.read_state()
     status, lane, x, v, rp, t_arr = oracle_state_from_gpu(st0, orc.n)
     orc.set_state(status, lane, x, v, rp, st0["t"], t_arr)
+    if "ctrl_state" in st0:   # max-pressure controllers (identical in fixed-time mode)
+        orc.set_ctrl_state(st0["ctrl_state"])
     sim.step(1)
     sim.sync()
     gd = sim.read_debug()
     gs = sim.read_state()
     _, od = orc.step(debug=True)
     os_ = orc.state()
+    if "ctrl_state" in gs:
+        os_["ctrl_state"] = orc.ctrl_state()
     return st0, gd, gs, od, os_
 
 
 def compare_step(gd, gs, od, os_, n_trips, report=None, max_flag_frac=0.05):
     """Assert parity of one step; returns a dict of counts."""
+    if "ctrl_state" in gs and "ctrl_state" in os_:   # controllers advanced to the next step
+        assert np.array_equal(gs["ctrl_state"], os_["ctrl_state"]), "controller states differ"
     act = od["active_before"] == 1
     assert np.array_equal(act, gd["active_before"] == 1), "different active sets"
     flagged = (od["flag"] == 1) | (gd["flag"] == 1)

@@ -86,6 +86,69 @@ def test_single_steps_match_oracle_threshold_jitter(kind, t0):
     assert tot["changes"] > 0
 
 
+MP = dict(P, signal_mode=1, mp_interval=10)
+
+
+@pytest.mark.parametrize("kind,t0", [("grid12x3", 57), ("delaunay", 66)])
+def test_single_steps_match_oracle_max_pressure(kind, t0):
+    """Max-pressure signals (R13): decisions at steps 60 / 70 fall inside the 8 compared
+    steps; the controllers' state is compared after every step."""
+    _need_gpu()
+    net = _net(kind)
+    dem = synth.merge_demands(synth.place_vehicles(net, 5003 if kind == "grid12x3" else 2500, seed=31 + t0,
+                                                   min_spacing=7.0, internal_frac=0.3),
+                              synth.uniform_trips(net, 400, 40, seed=32 + t0))
+    params = dict(MP, seed=7 + t0)
+    sim = parity.gpu_sim(net, dem, params)
+    st = sim.read_state()
+    st["t"] = t0
+    sim.write_state(st)
+    orc = oracle.Oracle(net, dem, params)
+    rep = []
+    for k in range(8):
+        _, gd, gs, od, os_ = parity.step_pair(sim, orc)
+        parity.compare_step(gd, gs, od, os_, dem.n, report=rep)
+    tot = {k: sum(r[k] for r in rep) for k in rep[0]}
+    print(kind, tot, "pending", int((gs["ctrl_state"][:, 1] >= 0).sum()))
+    assert tot["compared"] > 0.9 * tot["active"]
+
+
+def test_lockstep_small_grid_max_pressure():
+    _need_gpu()
+    net, dem = synth.small_grid_workload(3)
+    sim = parity.gpu_sim(net, dem, MP, n_windows=12)
+    orc = oracle.Oracle(net, dem, MP, n_windows=12)
+    rep = []
+    for t in range(1500):
+        if t % 5 == 0:
+            _, gd, gs, od, os_ = parity.step_pair(sim, orc)
+            parity.compare_step(gd, gs, od, os_, dem.n, report=rep)
+        else:
+            sim.step(1)
+    sim.sync()
+    assert sim.read_metrics(lanes=False)["err"] == 0
+    tot = {k: sum(r[k] for r in rep) for k in rep[0]}
+    print(tot)
+    assert tot["flagged"] <= 0.01 * tot["active"]
+
+
+def test_resume_is_bit_exact_max_pressure():
+    _need_gpu()
+    net, dem = synth.small_grid_workload(2)
+    a = parity.gpu_sim(net, dem, MP, debug=False)
+    a.step(705)
+    sa = a.read_state()
+    b = parity.gpu_sim(net, dem, MP, debug=False)
+    b.step(303)
+    mid = b.read_state()
+    c = parity.gpu_sim(net, dem, MP, debug=False)
+    c.write_state(mid)   # vehicles and controllers
+    c.step(402)
+    sc = c.read_state()
+    for k in ("id", "lane", "x", "v", "route_idx", "t_arr", "t", "ctrl_state"):
+        np.testing.assert_array_equal(sa[k], sc[k])
+
+
 def test_lockstep_small_grid_full_run():
     """The small grid workload run on the GPU for 3600 steps; every 5th step the oracle
     repeats the GPU's step from the GPU's state."""

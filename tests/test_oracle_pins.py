@@ -394,6 +394,128 @@ def test_neighbours_match_brute_force(oracle_lib, kind, seed):
 
 
 # ---------------------------------------------------------------------------------------
+# max-pressure signals (R13)
+# ---------------------------------------------------------------------------------------
+
+MP = dict(P, signal_mode=1, mp_interval=10)
+
+
+def _center_lanes(net, ctrl):
+    """Approach edge lanes of controller ctrl, by phase group."""
+    ls = np.nonzero((net.lane_ctrl == ctrl) & (net.lane_edge >= 0))[0]
+    return {int(g): ls[net.lane_group[ls] == g] for g in np.unique(net.lane_group[ls])}
+
+
+def test_max_pressure_switches_to_the_loaded_phase(oracle_lib):
+    """3x3 grid, only the centre's approach from the west (phase 1) holds a queue: at the
+    decision step t = 0 phase 0 turns yellow for the controller's 3 s, then phase 1 is
+    green until the next decision."""
+    import oracle
+    net = synth.grid_network(3, 3, 2, 200.0, 30, 3, "zero")
+    ctrl = int(np.nonzero(net.ctrl_node == 4)[0][0])
+    groups = _center_lanes(net, ctrl)
+    e_in = int(np.nonzero((net.edge_from == 3) & (net.edge_to == 4))[0][0])
+    e_out = int(np.nonzero((net.edge_from == 4) & (net.edge_to == 5))[0][0])
+    l0 = int(net.edge_lane0[e_in])
+    assert set(groups[1].tolist()) >= {l0, l0 + 1}
+    lanes, xs = [], []
+    for k in range(4):
+        lanes += [l0, l0 + 1]
+        xs += [190.0 - 8.0 * k] * 2
+    dem = netkit.vehicles(lanes, xs, [0.0] * len(lanes), [[e_in, e_out]] * len(lanes))
+    o = oracle.Oracle(net, dem, MP)
+    seen = []
+    for t in range(8):
+        cs = o.ctrl_state()[ctrl].tolist()
+        seen.append((o.signal_state(int(groups[0][0]), t), o.signal_state(int(groups[1][0]), t), cs))
+        err, _ = o.step()
+        assert err == 0
+    Y, G, R = 1, 0, 2
+    assert [x[:2] for x in seen[:3]] == [(Y, R)] * 3
+    assert [x[:2] for x in seen[3:8]] == [(R, G)] * 5
+    assert seen[0][2] == [0, 1, 3] and seen[3][2] == [1, -1, 3]
+
+
+def test_max_pressure_holds_the_green_phase_on_ties(oracle_lib):
+    """No vehicle anywhere near the controllers: every pressure is 0 and every controller
+    keeps phase 0 green through many decisions (a fixed-time plan would have cycled)."""
+    import oracle
+    net = synth.grid_network(3, 3, 2, 200.0, 30, 3, "zero")
+    e01 = int(np.nonzero((net.edge_from == 0) & (net.edge_to == 1))[0][0])
+    dem = netkit.vehicles([-1], [0.0], [0.0], [[e01]], t_dep=[10 ** 6])   # departs far in the future
+    o = oracle.Oracle(net, dem, MP)
+    for t in range(60):
+        assert (o.ctrl_state() == np.array([0, -1, 0])).all()
+        o.step()
+
+
+def _mp_brute(net, counts, cs_prev, t, interval):
+    """R13 restated with numpy over the network arrays, from the previous step's state."""
+    cs = cs_prev.copy()
+    for c in range(net.n_ctrl):
+        if cs[c, 1] >= 0 and t >= cs[c, 2]:
+            cs[c, 0], cs[c, 1] = cs[c, 1], -1
+    if t % interval:
+        return cs
+    ls = np.nonzero((net.lane_ctrl >= 0) & (net.lane_edge >= 0))[0]
+    pres = np.zeros((net.n_ctrl, int(net.ctrl_nphase.max())), np.int64)
+    for l in ls:
+        il = net.succ_lane[net.succ_off[l]:net.succ_off[l + 1]]
+        tg = net.succ_lane[net.succ_off[il]]
+        pres[net.lane_ctrl[l], net.lane_group[l]] += int(np.sum(counts[l] - counts[tg]))
+    for c in range(net.n_ctrl):
+        if cs[c, 1] >= 0:
+            continue
+        pr = pres[c, :net.ctrl_nphase[c]]
+        best = int(np.argmax(pr))
+        if pr[cs[c, 0]] == pr[best]:
+            best = cs[c, 0]
+        if best != cs[c, 0]:
+            if net.ctrl_yellow[c] > 0:
+                cs[c, 1], cs[c, 2] = best, t + net.ctrl_yellow[c]
+            else:
+                cs[c, 0] = best
+    return cs
+
+
+def test_max_pressure_run_matches_brute_force_and_never_runs_red(oracle_lib):
+    """Small grid workload under max pressure: at every step the controllers equal R13
+    restated with numpy from the previous step's controllers and the snapshot's lane
+    counts; a switch starts only at a decision step and its yellow lasts exactly the
+    controller's yellow time; no vehicle crosses a red stop line; all trips arrive."""
+    import oracle
+    net, dem = synth.small_grid_workload(2)
+    o = oracle.Oracle(net, dem, MP)
+    prev = np.tile(np.array([0, -1, 0], np.int32), (net.n_ctrl, 1))   # the start state
+    switches = 0
+    for _ in range(3600):
+        st = o.state()
+        t = st["t"]
+        cs = o.ctrl_state()   # the controllers step t uses
+        act = st["status"] == 1
+        counts = np.bincount(st["lane"][act], minlength=net.n_lanes)
+        np.testing.assert_array_equal(cs, _mp_brute(net, counts, prev, t, MP["mp_interval"]), err_msg=f"step {t}")
+        started = (cs[:, 1] >= 0) & (prev[:, 1] < 0)
+        if started.any():
+            assert t % MP["mp_interval"] == 0
+            assert np.all(cs[started, 2] == t + net.ctrl_yellow[started])
+            switches += int(started.sum())
+        ctrl = net.lane_ctrl[st["lane"]]
+        red = act & (ctrl >= 0) & (net.lane_edge[st["lane"]] >= 0) & \
+            (net.lane_group[st["lane"]] != cs[np.maximum(ctrl, 0), 0])
+        err, _ = o.step()
+        assert err == 0
+        nx = o.state()
+        crossed = red & (nx["lane"] != st["lane"]) & (nx["status"] == 1) & (net.lane_edge[nx["lane"]] < 0)
+        assert not crossed.any(), np.nonzero(crossed)[0][:5]
+        prev = cs
+        if (nx["status"] == 2).all():
+            break
+    assert switches > 10
+    assert (o.state()["status"] == 2).all()
+
+
+# ---------------------------------------------------------------------------------------
 # whole-run invariants
 # ---------------------------------------------------------------------------------------
 

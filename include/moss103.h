@@ -273,6 +273,17 @@ int ms_set_lc_log(void *sim, void *x, int *y, int cap, int *n);
    direction.  params == NULL returns to the rule. */
 int ms_set_lc_model(void *sim, const float *params, float margin);
 
+/* Lane modifications (Sec. III-C "Python API": modification calls for lane speed limits and
+   lane restrictions), in effect from the next step.  For lanes[k] (host arrays, n entries):
+   vmax[k] m/s caps the desired speed of every vehicle on the lane, v0_eff = min(v0, vmax)
+   (<= 0 or non-finite: no limit); closed[k] != 0 closes the lane: a vehicle whose path
+   reaches it stops at the end of the lane before it, no lane change targets it, and its
+   departure queue waits; vehicles already on it drive on.  vmax or closed may be NULL
+   (left unchanged).  Lanes out of range: MS_ERR_ARG, nothing changed.  Synchronises with the
+   simulation's stream.  While no lane has a limit or is closed the step does no extra
+   work for this. */
+int ms_set_lane_limits(void *sim, int n, const int *lanes, const float *vmax, const int *closed);
+
 /* Counters of the learned decision since the model was set: [0] candidates, [1] rule
    fallbacks (low margin), [2] agreements with the rule, [3 + 3*rule + final] confusion. */
 int ms_read_lc_stats(void *sim, int64_t *out12);

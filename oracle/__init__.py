@@ -82,6 +82,7 @@ def _load():
         lib.or_departure_lane.restype = C.c_int
         lib.or_get_ctrl_state.argtypes = [C.c_void_p, C.c_void_p]
         lib.or_set_ctrl_state.argtypes = [C.c_void_p, C.c_void_p]
+        lib.or_set_lane_limits.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
         _lib = lib
     return _lib
 
@@ -190,6 +191,14 @@ class Oracle:
         out = np.zeros((max(1, self.n_ctrl), 3), np.int32)
         _load().or_get_ctrl_state(self.h, _p(out))
         return out[:self.n_ctrl]
+
+    def set_lane_limits(self, lanes, vmax=None, closed=None) -> None:
+        """R14: speed limits (<= 0 / inf: none) and closures for the given lanes."""
+        ln = np.ascontiguousarray(lanes, np.int32)
+        vm = None if vmax is None else np.ascontiguousarray(vmax, np.float32)
+        cl = None if closed is None else np.ascontiguousarray(closed, np.int32)
+        _load().or_set_lane_limits(self.h, int(ln.shape[0]), _p(ln), None if vm is None else _p(vm),
+                                   None if cl is None else _p(cl))
 
     def set_ctrl_state(self, cs) -> None:
         cs = np.ascontiguousarray(np.asarray(cs, np.int32).reshape(-1, 3))

@@ -73,6 +73,13 @@
  *      controller's yellow time (then the winner is green), or at once when that is 0.
  *      Lanes of phase g are green, or yellow while a phase is pending; all others red.
  *      Controllers start with phase 0 green and nothing pending.
+ *  R14 Lane modifications (set between steps): a lane's speed limit caps the desired
+ *      speed of every vehicle on it, v0_eff = min(v0, vmax_lane), in all IDM terms -- the
+ *      changer's prospective acceleration and the new follower's use the target lane's
+ *      limit, the old follower's its own lane's.  A closed lane cannot be entered: a path
+ *      that reaches it ends in a stopped obstacle at the end of the lane before it, it is
+ *      never a lane-change target, and its departure queue waits.  Vehicles already on it
+ *      drive on.
  *  R12 Threshold jitter (a randomized-MOBIL variant, off when th_jitter = 0): trip c's
  *      incentive threshold is th + th_jitter (2u - 1), u = (SplitMix64(seed ^ 0x9E3779B97F4A7C15
  *      ^ c) >> 40) / 2^24, fixed for the trip (driver heterogeneity); the salt keeps these
@@ -125,6 +132,9 @@ struct or_sim {
   int *mp_g, *mp_pend, *mp_yend;
   int64_t *mp_pres;   /* per controller x phase pressure (scratch) */
   int *mp_poff;       /* phase offsets into mp_pres */
+  /* R14 lane modifications */
+  double *lane_vmax;  /* speed limit per lane, INFINITY = none */
+  int *lane_closed;
 };
 
 /* ------------------------------------------------------------------------------------ */
@@ -250,6 +260,11 @@ static void mark(int *flag, double margin) {
   if (fabs(margin) < FLAG_EPS) *flag = 1;
 }
 
+/* R14: desired speed of trip c on lane l */
+static double v0_on(const or_sim *s, int c, int l) {
+  return fmin((double)s->v0[c], s->lane_vmax[l]);
+}
+
 /* R1 */
 static double idm(const or_sim *s, double v, double v0, int has_leader, double gap, double vl) {
   const or_params *p = &s->p;
@@ -361,6 +376,10 @@ static leader_t own_leader(const or_sim *s, int c, int *flag) {
         nxt = s->net.succ_lane[s->net.succ_off[cur]];
         ri += 1;
       }
+      if (s->lane_closed[nxt]) {   /* R14 */
+        r.kind = K_OBST; r.gap = dist; r.vl = 0.0; r.end_obstacle = (hop == 0);
+        break;
+      }
       if (hop + 1 >= HOP_CAP) {
         r.kind = K_OBST; r.gap = dist; r.vl = 0.0; r.end_obstacle = (hop == 0);
         break;
@@ -449,6 +468,7 @@ static lc_t lane_change(const or_sim *s, int c, const leader_t *own, double a_c,
   int step_dir = (s->t % 2 == 0) ? +1 : -1;
   int tau = step_dir > 0 ? s->net.lane_left[l] : s->net.lane_right[l];
   if (tau < 0) return r;
+  if (s->lane_closed[tau]) return r;   /* R14 */
   int mandatory = !connects(s, l, en);
   if (mandatory) {
     /* nearest connecting lane on the same edge */
@@ -497,21 +517,21 @@ static lc_t lane_change(const or_sim *s, int c, const leader_t *own, double a_c,
     double guard = s->v[Ft] * p->dt + 0.5 * p->a * p->dt * p->dt;
     mark(flag, gF - guard);
     if (gF < guard) return r;
-    aF_new = idm(s, s->v[Ft], s->v0[Ft], 1, gF, v);
+    aF_new = idm(s, s->v[Ft], v0_on(s, Ft, tau), 1, gF, v);
     mark(flag, aF_new + p->bsafe);
     if (aF_new < -p->bsafe) return r;
   }
-  r.a_new = idm(s, v, v0, r.tau_kind != K_FREE, r.tau_gap, r.tau_vl);
+  r.a_new = idm(s, v, fmin(v0, s->lane_vmax[tau]), r.tau_kind != K_FREE, r.tau_gap, r.tau_vl);
   if (!mandatory) {
     double delta = r.a_new - a_c;
     if (Ft >= 0) {
       double aF_old;
       if (Lt >= 0) {
-        aF_old = idm(s, s->v[Ft], s->v0[Ft], 1, (s->x[Lt] - s->x[Ft]) - L, s->v[Lt]);
+        aF_old = idm(s, s->v[Ft], v0_on(s, Ft, tau), 1, (s->x[Lt] - s->x[Ft]) - L, s->v[Lt]);
       } else if (end_blocks(s, tau, en, s->x[Ft], s->v[Ft], flag)) {
-        aF_old = idm(s, s->v[Ft], s->v0[Ft], 1, len - s->x[Ft], 0.0);
+        aF_old = idm(s, s->v[Ft], v0_on(s, Ft, tau), 1, len - s->x[Ft], 0.0);
       } else {
-        aF_old = idm(s, s->v[Ft], s->v0[Ft], 0, 0.0, 0.0);
+        aF_old = idm(s, s->v[Ft], v0_on(s, Ft, tau), 0, 0.0, 0.0);
       }
       delta += p->p * (aF_new - aF_old);
     }
@@ -520,12 +540,12 @@ static lc_t lane_change(const or_sim *s, int c, const leader_t *own, double a_c,
       int O = s->order[s->seg_start[l] + k - 1];
       r.old_foll = O;
       double gO = (x - s->x[O]) - L;
-      double aO_old = idm(s, s->v[O], s->v0[O], 1, gO, v);
+      double aO_old = idm(s, s->v[O], v0_on(s, O, l), 1, gO, v);
       double aO_new;
       if (own->kind != K_FREE)
-        aO_new = idm(s, s->v[O], s->v0[O], 1, own->gap + (x - s->x[O]), own->vl);
+        aO_new = idm(s, s->v[O], v0_on(s, O, l), 1, own->gap + (x - s->x[O]), own->vl);
       else
-        aO_new = idm(s, s->v[O], s->v0[O], 0, 0.0, 0.0);
+        aO_new = idm(s, s->v[O], v0_on(s, O, l), 0, 0.0, 0.0);
       delta += p->p * (aO_new - aO_old);
     }
     r.incentive = delta;
@@ -567,7 +587,7 @@ int or_step(or_sim *s, or_debug *dbg) {
     double x = s->x[c], v = s->v[c];
     double len = (double)s->net.lane_len[l];
     leader_t own = own_leader(s, c, &flag);
-    double a_c = idm(s, v, s->v0[c], own.kind != K_FREE, own.gap, own.vl);
+    double a_c = idm(s, v, v0_on(s, c, s->lane[c]), own.kind != K_FREE, own.gap, own.vl);
     lc_t lc = lane_change(s, c, &own, a_c, &flag);
     double a_use = lc.dir ? fmin(a_c, lc.a_new) : a_c;
     /* R6 */
@@ -649,6 +669,7 @@ int or_step(or_sim *s, or_debug *dbg) {
     if (s->q_head[l] >= qe) continue;
     int h = s->q_ids[s->q_head[l]];
     if (s->t_dep[h] > s->t) continue;
+    if (s->lane_closed[l]) continue;   /* R14: the queue waits */
     int fl = 0;
     int room = 1;
     if (s->seg_cnt[l] > 0) {
@@ -773,6 +794,9 @@ or_sim *or_create(const or_net *net, const or_params *p, int n_trips, const int 
     for (int c = 0; c < C; ++c) s->mp_poff[c + 1] = s->mp_poff[c] + net->ctrl_nphase[c];
     s->mp_pres = (int64_t *)calloc((size_t)s->mp_poff[C] + 1, sizeof(int64_t));
   }
+  s->lane_vmax = (double *)malloc(sizeof(double) * (size_t)L);
+  s->lane_closed = (int *)calloc((size_t)L, sizeof(int));
+  for (int l = 0; l < L; ++l) s->lane_vmax[l] = INFINITY;
   for (size_t i = 0; i < n; ++i) {
     s->t_arr[i] = -1;
     if (lane0 && lane0[i] >= 0) {
@@ -819,6 +843,7 @@ or_sim *or_create(const or_net *net, const or_params *p, int n_trips, const int 
 void or_destroy(or_sim *s) {
   if (!s) return;
   free(s->mp_g); free(s->mp_pend); free(s->mp_yend); free(s->mp_pres); free(s->mp_poff);
+  free(s->lane_vmax); free(s->lane_closed);
   free(s->status); free(s->lane); free(s->rp); free(s->t_arr); free(s->x); free(s->v);
   free(s->dep_lane); free(s->order); free(s->pos); free(s->seg_start); free(s->seg_cnt);
   free(s->n_lane); free(s->n_rp); free(s->n_status); free(s->n_x); free(s->n_v);
@@ -851,6 +876,15 @@ void or_set_state(or_sim *s, const int *status, const int *lane, const double *x
   s->t = t;
   for (int l = 0; l < s->net.n_lanes; ++l) s->q_head[l] = s->q_off[l];
   mp_reset(s);
+}
+
+void or_set_lane_limits(or_sim *s, int n, const int *lanes, const float *vmax, const int *closed) {
+  for (int k = 0; k < n; ++k) {
+    const int l = lanes[k];
+    if (l < 0 || l >= s->net.n_lanes) continue;
+    if (vmax) s->lane_vmax[l] = (vmax[k] > 0.0f && isfinite(vmax[k])) ? (double)vmax[k] : INFINITY;
+    if (closed) s->lane_closed[l] = closed[k] != 0;
+  }
 }
 
 void or_get_ctrl_state(or_sim *s, int *out) {

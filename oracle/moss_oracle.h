@@ -78,6 +78,9 @@ int or_signal_state(const or_sim *s, int lane, int t); /* 0 green, 1 yellow, 2 r
    The getter first advances the controllers to the current step t (on the snapshot at t;
    advancing twice to the same step changes nothing), so it reports the state step t uses. */
 void or_get_ctrl_state(or_sim *s, int *out);
+/* R14 lane modifications, in effect from the next step: for lanes[k], a speed limit vmax[k]
+   (m/s; <= 0 or non-finite: none) and closed[k] (0 / 1).  Either array may be NULL. */
+void or_set_lane_limits(or_sim *s, int n, const int *lanes, const float *vmax, const int *closed);
 void or_set_ctrl_state(or_sim *s, const int *in);
 uint64_t or_splitmix64(uint64_t state);
 /* neighbour search on the current snapshot (for the brute-force check): for each trip id:

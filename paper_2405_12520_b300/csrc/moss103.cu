@@ -58,6 +58,10 @@ struct Sim {
   int *d_sig[2]{};   // signal table per step parity (see sig_pack)
   int4 *d_mp = nullptr;                             // max-pressure controller state
   int *d_ctrl_loff = nullptr, *d_ctrl_lanes = nullptr;   // approach lanes per controller
+  float *d_lane_vmax = nullptr;           // lane speed limits (+inf: none)
+  unsigned char *d_lane_closed = nullptr;
+  std::vector<float> h_lane_vmax;
+  std::vector<unsigned char> h_lane_closed;
   int *d_routes = nullptr;
   unsigned long long *d_plan = nullptr;
   Soa A[2]{};
@@ -132,6 +136,8 @@ StepArgs make_args(Sim *s) {
   a.mp = s->d_mp;
   a.ctrl_loff = s->d_ctrl_loff;
   a.ctrl_lanes = s->d_ctrl_lanes;
+  a.lane_vmax = s->d_lane_vmax;
+  a.lane_closed = s->d_lane_closed;
   a.routes = s->d_routes;
   a.plan = s->d_plan;
   a.A[0] = s->A[0];
@@ -169,10 +175,14 @@ StepArgs make_args(Sim *s) {
 
 // the k_decide instance for the simulation's lane-change mode and debug setting
 typedef void (*DecideKernel)(StepArgs);
-DecideKernel decide_kernel(int mode, bool dbg) {
-  if (mode == MODE_LEARN) return dbg ? k_decide_t<MODE_LEARN, true> : k_decide_t<MODE_LEARN, false>;
-  if (mode == MODE_LOG) return dbg ? k_decide_t<MODE_LOG, true> : k_decide_t<MODE_LOG, false>;
-  return dbg ? k_decide_t<MODE_PLAIN, true> : k_decide_t<MODE_PLAIN, false>;
+template <bool MODS>
+DecideKernel decide_kernel_m(int mode, bool dbg) {
+  if (mode == MODE_LEARN) return dbg ? k_decide_t<MODE_LEARN, true, MODS> : k_decide_t<MODE_LEARN, false, MODS>;
+  if (mode == MODE_LOG) return dbg ? k_decide_t<MODE_LOG, true, MODS> : k_decide_t<MODE_LOG, false, MODS>;
+  return dbg ? k_decide_t<MODE_PLAIN, true, MODS> : k_decide_t<MODE_PLAIN, false, MODS>;
+}
+DecideKernel decide_kernel(int mode, bool dbg, bool mods) {
+  return mods ? decide_kernel_m<true>(mode, dbg) : decide_kernel_m<false>(mode, dbg);
 }
 
 // one step = four launches (+ the debug order check); ev (5 events) brackets each kernel
@@ -180,7 +190,7 @@ cudaError_t launch_step(const Sim *s, const StepArgs &a, cudaStream_t st, cudaEv
   const LaunchCfg &c = s->cfg;
   if (ev) cudaEventRecord(ev[0], st);
   const size_t smem = s->lc_mode == MODE_LEARN ? learn_smem(c.blk_decide) : 0;
-  decide_kernel(s->lc_mode, s->prm.debug != 0)<<<c.grid_decide, c.blk_decide, smem, st>>>(a);
+  decide_kernel(s->lc_mode, s->prm.debug != 0, a.P.lane_mods != 0)<<<c.grid_decide, c.blk_decide, smem, st>>>(a);
   if (ev) cudaEventRecord(ev[1], st);
   k_lanes<<<s->n_tiles, LANE_THREADS, 0, st>>>(a);
   if (ev) cudaEventRecord(ev[2], st);
@@ -200,7 +210,8 @@ cudaError_t enqueue_step(Sim *s, cudaStream_t st) { return launch_step(s, make_a
 int shape_grids(Sim *s, LaunchCfg &c, int f_decide, int f_apply, int f_bucket) {
   const int N = s->n_trips;
   int od = 0, oa = 0, ob = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&od, decide_kernel(MODE_PLAIN, s->prm.debug != 0), c.blk_decide, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&od, decide_kernel(MODE_PLAIN, s->prm.debug != 0, false),
+                                                   c.blk_decide, 0));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oa, k_apply, c.blk_apply, 0));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, k_bucket, c.blk_bucket, 0));
   auto g = [&](int blk, int occ, int f) {
@@ -630,6 +641,12 @@ int ms_load_network(void *sim, const ms_network *net) {
   CK(cudaMemcpy(s->d_pred, pred.data(), pred.size() * sizeof(int), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->d_ctrl4, c4.data(), c4.size() * sizeof(int4), cudaMemcpyHostToDevice));
   s->n_tiles = (L + LANE_TILE - 1) / LANE_TILE;
+  s->h_lane_vmax.assign(L, INFINITY);
+  s->h_lane_closed.assign(L, 0);
+  DALLOC(s->d_lane_vmax, L);
+  DALLOC(s->d_lane_closed, L);
+  CK(cudaMemcpy(s->d_lane_vmax, s->h_lane_vmax.data(), L * sizeof(float), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_lane_closed, s->h_lane_closed.data(), L, cudaMemcpyHostToDevice));
   s->net_loaded = true;
   return MS_OK;
 }
@@ -1329,6 +1346,30 @@ int ms_set_lc_log(void *sim, void *x, int *y, int cap, int *n) {
   return MS_OK;
 }
 
+int ms_set_lane_limits(void *sim, int n, const int *lanes, const float *vmax, const int *closed) {
+  Sim *s = (Sim *)sim;
+  if (!s || n < 0 || (n > 0 && !lanes)) return MS_ERR_ARG;
+  if (!s->net_loaded) return fail(s, MS_ERR_STATE, "load the network first");
+  for (int k = 0; k < n; ++k)
+    if (lanes[k] < 0 || lanes[k] >= s->n_lanes) return fail(s, MS_ERR_ARG, "lane out of range");
+  for (int k = 0; k < n; ++k) {
+    const int l = lanes[k];
+    if (vmax) s->h_lane_vmax[l] = (vmax[k] > 0.f && std::isfinite(vmax[k])) ? vmax[k] : INFINITY;
+    if (closed) s->h_lane_closed[l] = closed[k] != 0;
+  }
+  int mods = 0;
+  for (int l = 0; l < s->n_lanes && !mods; ++l) mods = std::isfinite(s->h_lane_vmax[l]) || s->h_lane_closed[l];
+  CK(cudaMemcpyAsync(s->d_lane_vmax, s->h_lane_vmax.data(), s->n_lanes * sizeof(float), cudaMemcpyHostToDevice,
+                     s->stream));
+  CK(cudaMemcpyAsync(s->d_lane_closed, s->h_lane_closed.data(), s->n_lanes, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  if (mods != s->P.lane_mods) {   // the flag is baked into the captured step graphs
+    s->P.lane_mods = mods;
+    drop_graphs(s);
+  }
+  return MS_OK;
+}
+
 int ms_set_lc_model(void *sim, const float *params, float margin) {
   Sim *s = (Sim *)sim;
   if (!s) return MS_ERR_ARG;
@@ -1345,8 +1386,10 @@ int ms_set_lc_model(void *sim, const float *params, float margin) {
     DALLOC(s->d_theta, MLP_NPARAM);
     static bool attr = false;
     if (!attr) {
-      CK(cudaFuncSetAttribute(k_decide_t<MODE_LEARN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, learn_smem(512)));
-      CK(cudaFuncSetAttribute(k_decide_t<MODE_LEARN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, learn_smem(512)));
+      for (int d = 0; d < 2; ++d)
+        for (int m = 0; m < 2; ++m)
+          CK(cudaFuncSetAttribute(decide_kernel(MODE_LEARN, d != 0, m != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  learn_smem(512)));
       attr = true;
     }
   }

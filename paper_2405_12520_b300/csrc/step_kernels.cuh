@@ -73,6 +73,7 @@ struct DevParams {
   float th_jitter;       // half-width of each trip's incentive-threshold offset (0: off)
   int signal_mode;       // 0 fixed-time plans, 1 max pressure
   int mp_interval;       // steps between max-pressure decisions
+  int lane_mods;         // some lane has a speed limit or is closed
 };
 
 // Link plan of a route entry r (edge e = routes[r]), one 64-bit word built at load time:
@@ -157,6 +158,8 @@ struct StepArgs {
   int4 *mp;            // max-pressure controllers: {green phase, pending phase or -1, step
                        // the pending phase turns green, 0}
   const int *ctrl_loff, *ctrl_lanes;   // approach edge lanes of each controller (CSR)
+  const float *lane_vmax;              // per lane speed limit (+inf: none)
+  const unsigned char *lane_closed;    // per lane: closed to entering vehicles
   const int *routes;   // per trip: its edges then -1
   const unsigned long long *plan;   // link plan per routes[] entry
   Soa A[2];
@@ -290,6 +293,8 @@ struct Nbr {
 struct Tgt {
   int first, count;   // its segment of the snapshot
   int ctrl, group;    // the signal at its end
+  float vmax;         // its speed limit (+inf: none)
+  int closed;         // closed to entering vehicles
 };
 
 struct Upd {
@@ -301,7 +306,8 @@ struct Upd {
 };
 
 // Lane records per step: {first index, count, tail x bits, tail v bits}; the tail fields
-// (rearmost vehicle of the lane) are valid when count > 0.
+// (rearmost vehicle of the lane) are valid when count > 0.  MODS: lane closures in effect.
+template <bool MODS>
 __device__ __forceinline__ Lead own_leader(const StepArgs &a, const Soa &S, const int4 *dyn, int i,
                                            int l, const LaneInfo &li, const Nbr &nb, float x, float v,
                                            int rp, int nlc, int4 pf_dyn, const LaneInfo &pf_li,
@@ -348,6 +354,10 @@ __device__ __forceinline__ Lead own_leader(const StepArgs &a, const Soa &S, cons
       } else {
         nxt = lc.succ;
         ri += 1;
+      }
+      if (MODS && a.lane_closed[nxt]) {   // a closed lane ends the path
+        r = Lead{K_OBST, dist, 0.f, -1, hop == 0};
+        break;
       }
       if (hop + 1 >= HOP_CAP) {
         r = Lead{K_OBST, dist, 0.f, -1, hop == 0};
@@ -413,7 +423,7 @@ __device__ __forceinline__ bool end_blocks(const StepArgs &a, const Tgt &tg, flo
 __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const int4 *dyn, int i,
                                           int l, const LaneInfo &li, float x, float v, float v0,
                                           unsigned long long pl, int nlc, const Nbr &nb, const Tgt &tg,
-                                          int myid, int t, const Lead &own,
+                                          float vmax_own, int myid, int t, const Lead &own,
                                           float a_c, int &flag) {
   const DevParams &P = a.P;
   LC r{};
@@ -423,6 +433,7 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
   r.step_dir = step_dir;
   int tau = step_dir > 0 ? li.left : li.right;
   if (tau < 0) return r;
+  if (tg.closed) return r;   // a closed lane is never a target
   const bool mand = nlc == NL_NONE;   // own lane has no link toward the next edge
   r.mand = mand;
   if (mand) {   // nearest lane on each side with a link toward the next edge
@@ -478,7 +489,7 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
   if (Ft >= 0) {
     xF = S.x[Ft];
     vF = S.v[Ft];
-    v0F = S.v0[Ft];
+    v0F = fminf(S.v0[Ft], tg.vmax);   // the new follower drives under the target's limit
     float gF = (x - xF) - P.L;
     float guard = vF * P.dt + 0.5f * P.a * P.dt * P.dt;
     mark(flag, gF - guard);
@@ -492,7 +503,7 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
     r.aFn = aF_new;
   }
   r.safe = 1;
-  r.anew = idm(P, v, v0, r.tkind != K_FREE, r.tgap, r.tvl);
+  r.anew = idm(P, v, fminf(v0, tg.vmax), r.tkind != K_FREE, r.tgap, r.tvl);
   if (!mand) {
     float delta = r.anew - a_c;
     if (Ft >= 0) {
@@ -507,7 +518,7 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
     }
     if (nb.sameF) {
       r.of = i - 1;
-      const float xO = nb.xF, vO = nb.vF, v0O = nb.v0F;
+      const float xO = nb.xF, vO = nb.vF, v0O = fminf(nb.v0F, vmax_own);
       float aO_old = idm(P, vO, v0O, true, (x - xO) - P.L, v);
       float aO_new = own.kind != K_FREE ? idm(P, vO, v0O, true, own.gap + (x - xO), own.vl)
                                         : idm(P, vO, v0O, false, 0.f, 0.f);
@@ -584,7 +595,8 @@ __device__ __forceinline__ void load_vehicle(const Soa &S, int n, int i, VCtx &c
 }
 
 // Sensing, car following and the rule's lane-change decision of vehicle i at step t (own
-// fields and neighbours already in c).
+// fields and neighbours already in c).  MODS: lane speed limits / closures in effect.
+template <bool MODS>
 __device__ __forceinline__ Upd vehicle_sense(const StepArgs &a, const Soa &S, const int4 *dyn, int i, int t,
                                              VCtx &c) {
   const DevParams &P = a.P;
@@ -600,17 +612,24 @@ __device__ __forceinline__ Upd vehicle_sense(const StepArgs &a, const Soa &S, co
     pf_dyn = dyn[c.nlc];
     pf_li = a.li[c.nlc];
   }
-  Tgt tg{0, 0, -1, 0};
+  const float inf = __int_as_float(0x7f800000);
+  Tgt tg{0, 0, -1, 0, inf, 0};
   const int tl = c.l + ((t & 1) == 0 ? 1 : -1);
   if (c.x >= P.x_lc_min && tl >= 0 && tl < P.n_lanes) {
     const int2 d2 = reinterpret_cast<const int2 *>(dyn)[2 * tl];
     const int2 c2 = reinterpret_cast<const int2 *>(a.li)[4 * tl + 3];   // {ctrl, packed bytes}
-    tg = Tgt{d2.x, d2.y, c2.x, (c2.y >> 16) & 0xff};
+    tg = Tgt{d2.x, d2.y, c2.x, (c2.y >> 16) & 0xff, inf, 0};
+    if (MODS) {
+      tg.vmax = a.lane_vmax[tl];
+      tg.closed = a.lane_closed[tl];
+    }
   }
-  u.own = own_leader(a, S, dyn, i, c.l, c.li, c.nb, c.x, c.v, c.rp, c.nlc, pf_dyn, pf_li, c.id, t, u.flag);
-  u.a_own = idm(P, c.v, c.v0, u.own.kind != K_FREE, u.own.gap, u.own.vl);
-  u.lc = lane_change(a, S, dyn, i, c.l, c.li, c.x, c.v, c.v0, c.pl, c.nlc, c.nb, tg, c.id, t, u.own, u.a_own,
-                     u.flag);
+  // lane speed limits cap the desired speed: v0_eff = min(v0, vmax of the lane)
+  const float vmax_own = MODS ? a.lane_vmax[c.l] : inf;
+  u.own = own_leader<MODS>(a, S, dyn, i, c.l, c.li, c.nb, c.x, c.v, c.rp, c.nlc, pf_dyn, pf_li, c.id, t, u.flag);
+  u.a_own = idm(P, c.v, fminf(c.v0, vmax_own), u.own.kind != K_FREE, u.own.gap, u.own.vl);
+  u.lc = lane_change(a, S, dyn, i, c.l, c.li, c.x, c.v, c.v0, c.pl, c.nlc, c.nb, tg, vmax_own, c.id, t, u.own,
+                     u.a_own, u.flag);
   return u;
 }
 
@@ -755,10 +774,11 @@ __host__ __device__ constexpr int learn_smem(int threads) {
 }
 
 // DBG: record per-vehicle sensing and decisions (tests); a separate instance, so that the
-// production kernel keeps none of those values alive.  The plain production instance is
+// production kernel keeps none of those values alive.  MODS: lane speed limits or closures
+// are set (also a separate instance: without them the step does no work for them).  The plain production instance is
 // capped at 48 registers: 5 blocks of 256 per SM instead of 4 outweigh its few spills (the
 // kernel is bound by the latency of dependent gathers, so resident warps decide its speed).
-template <int MODE, bool DBG>
+template <int MODE, bool DBG, bool MODS>
 __global__ void __launch_bounds__(512, 2) __maxnreg__((MODE == MODE_PLAIN && !DBG) ? 48 : 64)
     k_decide_t(StepArgs a) {
   extern __shared__ __align__(16) unsigned char lsm[];
@@ -784,7 +804,7 @@ __global__ void __launch_bounds__(512, 2) __maxnreg__((MODE == MODE_PLAIN && !DB
     int dir = 0;
     load_vehicle(S, n, i, c);
     if (i < n) {
-      u = vehicle_sense(a, S, dyn, i, t, c);
+      u = vehicle_sense<MODS>(a, S, dyn, i, t, c);
       dir = u.lc.dir;
     }
     if constexpr (MODE != MODE_PLAIN) {
@@ -971,7 +991,7 @@ __global__ void __launch_bounds__(LANE_THREADS, 4) k_lanes(StepArgs a) {
   for (int k = 0; k < LANE_ITEMS; ++k) {
     const int leavers = lv[k];
     ins[k] = 0;
-    if (qhd[k].y <= t) {
+    if (qhd[k].y <= t && !(a.P.lane_mods && a.lane_closed[lbase + k * LANE_THREADS])) {
       // the head's record is read after the scan: start bringing it in now
       asm volatile("prefetch.global.L1 [%0];" ::"l"(a.q_ent + qhd[k].x));
       asm volatile("prefetch.global.L1 [%0];" ::"l"(a.q_ent2 + qhd[k].x));   // the FIFO's head is due: room behind the lane's tail (its

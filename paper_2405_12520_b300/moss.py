@@ -18,7 +18,8 @@ MS_OK, MS_ERR_ARG, MS_ERR_ROUTE, MS_ERR_CAPACITY, MS_ERR_CUDA, MS_ERR_DEVICE, MS
 ERR_NAMES = {0: "OK", -1: "ARG", -2: "ROUTE", -3: "CAPACITY", -4: "CUDA", -5: "DEVICE", -6: "STATE"}
 SYMBOLS = ("ms_create", "ms_load_network", "ms_add_vehicles", "ms_step", "ms_step_timed", "ms_step_noalloc",
            "ms_load_network_batch", "ms_add_vehicles_batch", "ms_batch_offsets", "ms_autotune",
-           "ms_set_lc_log", "ms_set_lc_model", "ms_read_lc_stats", "ms_mlp_train_step", "ms_mlp_grad",
+           "ms_set_lc_log", "ms_set_lc_model", "ms_set_lane_limits", "ms_read_lc_stats", "ms_mlp_train_step",
+           "ms_mlp_grad",
            "ms_mlp_predict",
            "ms_sync", "ms_read_state",
            "ms_write_state", "ms_read_metrics", "ms_read_debug", "ms_last_error", "ms_destroy")
@@ -89,6 +90,7 @@ def load():
         lib.ms_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_float), vp]
         lib.ms_set_lc_log.argtypes = [vp, vp, vp, C.c_int, vp]
         lib.ms_set_lc_model.argtypes = [vp, vp, C.c_float]
+        lib.ms_set_lane_limits.argtypes = [vp, C.c_int, vp, vp, vp]
         lib.ms_read_lc_stats.argtypes = [vp, vp]
         lib.ms_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, C.c_int, C.c_float, vp, vp, vp, vp]
         lib.ms_mlp_grad.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, vp, vp]
@@ -354,6 +356,15 @@ class Sim:
         (x bf16 [cap,16], y int32 [cap], n int32 [1]); no arguments turns logging off."""
         cap = int(y.numel()) if y is not None else 0
         self._check(self.lib.ms_set_lc_log(self.h, _dp(x), _dp(y), cap, _dp(n)), "ms_set_lc_log")
+
+    def set_lane_limits(self, lanes, vmax=None, closed=None):
+        """Lane speed limits (m/s; <= 0 or inf: none) and closures for the given lanes, in
+        effect from the next step."""
+        ln = np.ascontiguousarray(lanes, np.int32)
+        vm = None if vmax is None else np.ascontiguousarray(vmax, np.float32)
+        cl = None if closed is None else np.ascontiguousarray(closed, np.int32)
+        self._check(self.lib.ms_set_lane_limits(self.h, int(ln.shape[0]), _p(ln), _p(vm), _p(cl)),
+                    "ms_set_lane_limits")
 
     def set_lc_model(self, params=None, margin: float = 0.2):
         """Use the learned lane-change decision (params: 5443 floats, host); None: rule."""

@@ -149,6 +149,47 @@ def test_resume_is_bit_exact_max_pressure():
         np.testing.assert_array_equal(sa[k], sc[k])
 
 
+@pytest.mark.parametrize("kind,t0", [("grid12x3", 12), ("delaunay", 5)])
+def test_single_steps_match_oracle_lane_limits(kind, t0):
+    """Lane speed limits on 15% of the lanes (U[5, 12] m/s) and 3% of the lanes closed (R14),
+    set through the modification call on both sides."""
+    _need_gpu()
+    net = _net(kind)
+    dem = synth.merge_demands(synth.place_vehicles(net, 5003 if kind == "grid12x3" else 2500, seed=41 + t0,
+                                                   min_spacing=7.0, internal_frac=0.3),
+                              synth.uniform_trips(net, 400, 40, seed=42 + t0))
+    rng = np.random.default_rng(43 + t0)
+    lim = np.nonzero(rng.random(net.n_lanes) < 0.15)[0]
+    shut = np.nonzero(rng.random(net.n_lanes) < 0.03)[0]
+    vmax = rng.uniform(5.0, 12.0, lim.size).astype(np.float32)
+    sim = parity.gpu_sim(net, dem, P)
+    st = sim.read_state()
+    st["t"] = t0
+    sim.write_state(st)
+    orc = oracle.Oracle(net, dem, P)
+    for side in (sim, orc):
+        side.set_lane_limits(lim, vmax=vmax)
+        side.set_lane_limits(shut, closed=np.ones(shut.size, np.int32))
+    rep = []
+    for k in range(8):
+        _, gd, gs, od, os_ = parity.step_pair(sim, orc)
+        parity.compare_step(gd, gs, od, os_, dem.n, report=rep)
+    tot = {k: sum(r[k] for r in rep) for k in rep[0]}
+    print(kind, tot)
+    assert tot["compared"] > 0.9 * tot["active"]
+    # lifting every modification returns to the plain instance: same as never setting them
+    sim.set_lane_limits(lim, vmax=np.zeros(lim.size, np.float32))
+    sim.set_lane_limits(shut, closed=np.zeros(shut.size, np.int32))
+    ref = parity.gpu_sim(net, dem, P, debug=False)
+    cur = sim.read_state()
+    ref.write_state(cur)
+    sim.step(5)
+    ref.step(5)
+    a, b = sim.read_state(), ref.read_state()
+    for k in ("id", "lane", "x", "v", "route_idx"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
 def test_lockstep_small_grid_full_run():
     """The small grid workload run on the GPU for 3600 steps; every 5th step the oracle
     repeats the GPU's step from the GPU's state."""

@@ -516,6 +516,88 @@ def test_max_pressure_run_matches_brute_force_and_never_runs_red(oracle_lib):
 
 
 # ---------------------------------------------------------------------------------------
+# lane speed limits and closures (R14)
+# ---------------------------------------------------------------------------------------
+
+def test_lane_speed_limit_caps_the_desired_speed(oracle_lib):
+    """Free road under a lane limit of 8 m/s (v0 = 13.9): every step's acceleration is the
+    free-road IDM value with v0 = 8, a_max (1 - (v/8)^4), so the vehicle approaches 8 m/s
+    and never exceeds it (the map v + a_max (1 - (v/8)^4) is increasing on [0, 8] and fixes
+    8); without the limit it passes 8 m/s."""
+    import oracle
+    net = netkit.line(3, 2000.0, 1)
+    lane0 = int(net.edge_lane0[0])
+    dem = netkit.vehicles([lane0], [30.0], [0.0], [[0, 1]])
+    o = oracle.Oracle(net, dem, P)
+    o.set_lane_limits([lane0], vmax=[8.0])
+    for _ in range(60):
+        v = o.state()["v"][0]
+        _, d = o.step(debug=True)
+        assert d["a_own"][0] == pytest.approx(P["idm_a"] * (1 - (v / 8.0) ** 4), abs=1e-12)
+    v_lim = o.state()["v"][0]
+    assert 7.9 < v_lim <= 8.0
+    free = oracle.Oracle(net, dem, P)
+    free.run(60)
+    assert free.state()["v"][0] > 9.0
+
+
+def test_mobil_uses_the_target_lanes_limit(oracle_lib):
+    """Free-gain case with the target lane limited to 8 m/s: the changer's prospective
+    acceleration is a_max (1 - (10/8)^4) < 0, so the incentive is that value and nobody
+    changes; a closed target lane is not even a candidate."""
+    v, v0 = 10.0, 13.9
+    se = (P["idm_s0"] + v * P["idm_T"]) / math.sqrt(1 - (v / v0) ** 4)
+    net = netkit.line(3, 300.0, 2)
+    dem = netkit.vehicles([0, 0], [100.0, 100.0 + P["veh_len"] + se], [v, v], [[0, 1]] * 2, v0=v0)
+    import oracle
+    o = oracle.Oracle(net, dem, P)
+    o.set_lane_limits([1], vmax=[8.0])
+    _, d = o.step(debug=True)
+    assert d["lc_cand"][0] == 1
+    assert d["incentive"][0] == pytest.approx(P["idm_a"] * (1 - (v / 8.0) ** 4) - d["a_own"][0], abs=1e-9)
+    assert d["lc_dir"][0] == 0
+    o = oracle.Oracle(net, dem, P)
+    o.set_lane_limits([1], closed=[1])
+    _, d = o.step(debug=True)
+    assert d["lc_cand"][0] == 0 and d["lc_dir"][0] == 0
+
+
+def test_closed_lane_is_never_entered_until_reopened(oracle_lib):
+    """A vehicle whose next edge's lanes are closed stops at the end of the lane before them
+    (gap >= 0, never on a closed lane) and goes on once they reopen."""
+    import oracle
+    net = netkit.line(3, 300.0, 1)
+    l0, l1 = int(net.edge_lane0[0]), int(net.edge_lane0[1])
+    dem = netkit.vehicles([l0], [200.0], [12.0], [[0, 1]])
+    o = oracle.Oracle(net, dem, P)
+    o.set_lane_limits([l1], closed=[1])
+    for _ in range(80):
+        o.step()
+        st = o.state()
+        assert st["status"][0] == 1 and st["lane"][0] != l1
+        ln = int(st["lane"][0])
+        assert st["x"][0] <= net.lane_len[ln] + 1e-9
+    assert st["v"][0] == pytest.approx(0.0, abs=1e-6)
+    o.set_lane_limits([l1], closed=[0])
+    o.run(120)
+    assert o.state()["status"][0] == 2
+
+
+def test_departures_wait_on_a_closed_lane(oracle_lib):
+    import oracle
+    net = netkit.line(3, 300.0, 1)
+    l0 = int(net.edge_lane0[0])
+    dem = netkit.vehicles([-1], [0.0], [0.0], [[0, 1]], t_dep=[0])
+    o = oracle.Oracle(net, dem, P)
+    o.set_lane_limits([l0], closed=[1])
+    o.run(10)
+    assert o.state()["status"][0] == 0
+    o.set_lane_limits([l0], closed=[0])
+    o.step()
+    assert o.state()["status"][0] == 1
+
+
+# ---------------------------------------------------------------------------------------
 # whole-run invariants
 # ---------------------------------------------------------------------------------------
 

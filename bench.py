@@ -143,11 +143,40 @@ def dist_env():
     return rank, world, local
 
 
-def cpu_baseline(net, dem, params, budget_s: float = 20.0, max_steps: int = 10):
+def variant(args, net):
+    """Model parameters and lane modifications of the run: the default rule set, or the
+    max-pressure signals / threshold jitter / lane limits and closures the flags ask for."""
+    import numpy as np
+    from paper_2405_12520_b300 import synth
+    params = synth.default_params(mobil_th_jitter=args.th_jitter,
+                                  signal_mode=1 if args.signals == "mp" else 0, mp_interval=args.mp_interval)
+    mods, desc = None, {}
+    if args.signals == "mp":
+        desc["signals"] = f"max pressure, decisions every {args.mp_interval} s"
+    if args.th_jitter > 0:
+        desc["mobil_th_jitter"] = args.th_jitter
+    if args.lane_mods > 0:
+        rng = np.random.default_rng(args.seed + 77)
+        lim = np.nonzero(rng.random(net.n_lanes) < args.lane_mods)[0].astype(np.int32)
+        shut = np.nonzero(rng.random(net.n_lanes) < args.lane_mods / 10)[0].astype(np.int32)
+        mods = (lim, rng.uniform(8.0, 14.0, lim.size).astype(np.float32), shut)
+        desc["lane_mods"] = f"{lim.size} lanes limited to U[8,14] m/s, {shut.size} closed"
+    return params, mods, desc
+
+
+def apply_mods(side, mods):
+    if mods is not None:
+        lim, vmax, shut = mods
+        side.set_lane_limits(lim, vmax=vmax)
+        side.set_lane_limits(shut, closed=[1] * len(shut))
+
+
+def cpu_baseline(net, dem, params, budget_s: float = 20.0, max_steps: int = 10, mods=None):
     """The FP64 oracle, as it stands, single-threaded on this host, on the same workload:
     vehicle-steps/s over up to max_steps steps or budget_s seconds after one warm-up step."""
     import oracle
     o = oracle.Oracle(net, dem, params)
+    apply_mods(o, mods)
     o.step()
     n_act = int((o.state()["status"] == 1).sum())
     vs, steps, el = 0, 0, 0.0
@@ -167,14 +196,14 @@ def run_reference(args):
         return
     from paper_2405_12520_b300 import synth
     net, dem, desc = workload(args.workload, args.seed)
-    p = synth.default_params()
+    p, mods, vdesc = variant(args, net)
     k = max(1, min(args.steps, args.ref_steps))
-    val, steps, el = cpu_baseline(net, dem, p, budget_s=1e9, max_steps=k)
+    val, steps, el = cpu_baseline(net, dem, p, budget_s=1e9, max_steps=k, mods=mods)
     line = {
         "impl": "reference", "metric": "vehicle-steps/s", "value": val, "unit": "vehicle-steps/s",
         "n_gpus": world, "steps": steps, "warmup": 1, "ms_per_step": 1e3 * el / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": args.workload, "description": desc},
+        "data": "synthetic", "config": {"workload": args.workload, "description": desc, **vdesc},
         "cpu_baseline": {"value": val, "unit": "vehicle-steps/s", "cores": 1, "kind": "oracle",
                          "sample": f"{steps} oracle steps of the full {args.workload} workload "
                                    f"({dem.n} vehicles) after 1 warm-up step"},
@@ -193,11 +222,12 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     net, dem, desc = workload(args.workload, args.seed + rank)
-    params = synth.default_params()
+    params, mods, vdesc = variant(args, net)
     stream = torch.cuda.current_stream()
     sim = moss.Sim(params, stream=stream, n_windows=1, block=args.block)
     sim.load_network(net)
     sim.add_vehicles(dem)
+    apply_mods(sim, mods)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def barrier():
@@ -293,15 +323,15 @@ def run_ours(args):
         "metric": "vehicle-steps/s", "value": value, "unit": "vehicle-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "gpu_launches": 4 * args.steps,
-        "config": {"workload": args.workload, "description": desc, "vehicles": dem.n,
+        "data": "synthetic", "gpu_launches": (5 if args.signals == "mp" else 4) * args.steps,
+        "config": {"workload": args.workload, "description": desc, **vdesc, "vehicles": dem.n,
                    "lanes": net.n_lanes, "active_start": n_act[0], "active_end": n_end,
                    "l2": "flushed (256 MiB write) before every timed step; each step timed alone",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline, "e2e": e2e, "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        val, steps, el = cpu_baseline(net, dem, params)
+        val, steps, el = cpu_baseline(net, dem, params, mods=mods)
         line["cpu_baseline"] = {"value": val, "unit": "vehicle-steps/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{steps} single-threaded FP64 oracle steps of the same workload "
                                           f"({dem.n} vehicles), {el:.1f} s"}
@@ -479,6 +509,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scenarios", type=int, default=256)
     ap.add_argument("--train-seeds", type=int, default=200)
+    ap.add_argument("--signals", choices=("fixed", "mp"), default="fixed",
+                    help="signal control: fixed-time plans or max pressure")
+    ap.add_argument("--mp-interval", type=int, default=10, help="steps between max-pressure decisions")
+    ap.add_argument("--th-jitter", type=float, default=0.0, help="per-trip MOBIL threshold jitter (m/s^2)")
+    ap.add_argument("--lane-mods", type=float, default=0.0,
+                    help="fraction of lanes given a speed limit (a tenth as many are closed)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

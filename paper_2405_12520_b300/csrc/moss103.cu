@@ -315,9 +315,9 @@ bool lane_links_to(const Sim *s, int l, int e) {
 
 // queue heads and the departure step of each head trip
 int upload_queues(Sim *s, const std::vector<int> &qhead) {
-  std::vector<int> due(s->n_lanes);
+  std::vector<int> due(s->n_lanes);   // a closed lane's head is parked (never due)
   for (int l = 0; l < s->n_lanes; ++l)
-    due[l] = qhead[l] < s->h_qoff[l + 1] ? s->h_tdep[s->h_qtrip[qhead[l]]] : 0x7fffffff;
+    due[l] = qhead[l] < s->h_qoff[l + 1] && !s->h_lane_closed[l] ? s->h_tdep[s->h_qtrip[qhead[l]]] : 0x7fffffff;
   std::vector<int2> hd(s->n_lanes);
   for (int l = 0; l < s->n_lanes; ++l) hd[l] = make_int2(qhead[l], due[l]);
   CK(cudaMemcpy(s->d_qhd, hd.data(), sizeof(int2) * s->n_lanes, cudaMemcpyHostToDevice));
@@ -1352,10 +1352,24 @@ int ms_set_lane_limits(void *sim, int n, const int *lanes, const float *vmax, co
   if (!s->net_loaded) return fail(s, MS_ERR_STATE, "load the network first");
   for (int k = 0; k < n; ++k)
     if (lanes[k] < 0 || lanes[k] >= s->n_lanes) return fail(s, MS_ERR_ARG, "lane out of range");
+  std::vector<int> flip;   // lanes whose closure changes
   for (int k = 0; k < n; ++k) {
     const int l = lanes[k];
     if (vmax) s->h_lane_vmax[l] = (vmax[k] > 0.f && std::isfinite(vmax[k])) ? vmax[k] : INFINITY;
-    if (closed) s->h_lane_closed[l] = closed[k] != 0;
+    if (closed && s->h_lane_closed[l] != (closed[k] != 0)) {
+      s->h_lane_closed[l] = closed[k] != 0;
+      flip.push_back(l);
+    }
+  }
+  if (!flip.empty() && s->veh_loaded) {
+    // a closed lane's departure queue waits: its head is parked at INT_MAX (never due) and
+    // gets its trip's departure step back when the lane reopens
+    std::vector<int2> hd(s->n_lanes);
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaMemcpy(hd.data(), s->d_qhd, sizeof(int2) * s->n_lanes, cudaMemcpyDeviceToHost));
+    for (int l : flip)
+      hd[l].y = s->h_lane_closed[l] || hd[l].x >= s->h_qoff[l + 1] ? 0x7fffffff : s->h_tdep[s->h_qtrip[hd[l].x]];
+    CK(cudaMemcpy(s->d_qhd, hd.data(), sizeof(int2) * s->n_lanes, cudaMemcpyHostToDevice));
   }
   int mods = 0;
   for (int l = 0; l < s->n_lanes && !mods; ++l) mods = std::isfinite(s->h_lane_vmax[l]) || s->h_lane_closed[l];

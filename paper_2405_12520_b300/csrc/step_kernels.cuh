@@ -991,7 +991,7 @@ __global__ void __launch_bounds__(LANE_THREADS, 4) k_lanes(StepArgs a) {
   for (int k = 0; k < LANE_ITEMS; ++k) {
     const int leavers = lv[k];
     ins[k] = 0;
-    if (qhd[k].y <= t && !(a.P.lane_mods && a.lane_closed[lbase + k * LANE_THREADS])) {
+    if (qhd[k].y <= t) {   // (a closed lane's head is parked at INT_MAX by the host)
       // the head's record is read after the scan: start bringing it in now
       asm volatile("prefetch.global.L1 [%0];" ::"l"(a.q_ent + qhd[k].x));
       asm volatile("prefetch.global.L1 [%0];" ::"l"(a.q_ent2 + qhd[k].x));   // the FIFO's head is due: room behind the lane's tail (its

@@ -215,13 +215,17 @@ __device__ __forceinline__ float unfkey(int k) {
   return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff);
 }
 
-__device__ __forceinline__ float idm(const DevParams &P, float v, float v0, bool has, float gap,
-                                     float vl) {
-  // fast division (2 ulp): the FP32 path is compared with the FP64 oracle at 1e-4, and
-  // decisions this close to a threshold are flagged either way
-  float r = __fdividef(v, v0);
-  float r2 = r * r;
-  float fr = 1.f - r2 * r2;
+// free-road term of the IDM, 1 - (v/v0)^4 (shared by the IDM calls of one vehicle at one
+// desired speed).  Fast division (2 ulp): the FP32 path is compared with the FP64 oracle at
+// 1e-4, and decisions this close to a threshold are flagged either way.
+__device__ __forceinline__ float idm_free(float v, float v0) {
+  const float r = __fdividef(v, v0);
+  const float r2 = r * r;
+  return 1.f - r2 * r2;
+}
+
+// IDM acceleration from the free-road term fr
+__device__ __forceinline__ float idm_fr(const DevParams &P, float fr, float v, bool has, float gap, float vl) {
   float acc;
   if (!has) {
     acc = P.a * fr;
@@ -232,6 +236,10 @@ __device__ __forceinline__ float idm(const DevParams &P, float v, float v0, bool
     acc = P.a * (fr - q * q);
   }
   return fmaxf(acc, P.a_min);
+}
+
+__device__ __forceinline__ float idm(const DevParams &P, float v, float v0, bool has, float gap, float vl) {
+  return idm_fr(P, idm_free(v, v0), v, has, gap, vl);
 }
 
 // Fixed-time signal of controller c at step t (Sec. III-A, traffic lights): the cycle of
@@ -423,7 +431,7 @@ __device__ __forceinline__ bool end_blocks(const StepArgs &a, const Tgt &tg, flo
 __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const int4 *dyn, int i,
                                           int l, const LaneInfo &li, float x, float v, float v0,
                                           unsigned long long pl, int nlc, const Nbr &nb, const Tgt &tg,
-                                          float vmax_own, int myid, int t, const Lead &own,
+                                          float vmax_own, float fr_own, int myid, int t, const Lead &own,
                                           float a_c, int &flag) {
   const DevParams &P = a.P;
   LC r{};
@@ -454,9 +462,11 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
     if (!plan_ok(pl, tq)) return r;
     mark(flag, (li.len - x) - P.x_lc_end);
     if (li.len - x < P.x_lc_end) return r;
-    unsigned long long h = splitmix64(P.seed ^ ((unsigned long long)(unsigned)t << 32) ^
-                                      (unsigned long long)(unsigned)(myid + P.id_base));
-    if ((uint32_t)(h >> 40) >= P.lc_thresh) return r;
+    if (P.lc_thresh < (1u << 24)) {   // p_lc = 1: the gate always passes
+      unsigned long long h = splitmix64(P.seed ^ ((unsigned long long)(unsigned)t << 32) ^
+                                        (unsigned long long)(unsigned)(myid + P.id_base));
+      if ((uint32_t)(h >> 40) >= P.lc_thresh) return r;
+    }
   }
   r.cand = 1;
   int lo = tg.first, hi = tg.first + tg.count;
@@ -485,17 +495,18 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
     mark(flag, r.tgap);
     if (r.tgap <= 0.f) return r;
   }
-  float aF_new = 0.f, xF = 0.f, vF = 0.f, v0F = 1.f;
+  float aF_new = 0.f, xF = 0.f, vF = 0.f, v0F = 1.f, frF = 1.f;
   if (Ft >= 0) {
     xF = S.x[Ft];
     vF = S.v[Ft];
     v0F = fminf(S.v0[Ft], tg.vmax);   // the new follower drives under the target's limit
+    frF = idm_free(vF, v0F);
     float gF = (x - xF) - P.L;
     float guard = vF * P.dt + 0.5f * P.a * P.dt * P.dt;
     mark(flag, gF - guard);
     if (gF < guard) return r;
     if (xF == x) r.pos = Ft;   // at most one vehicle of a lane can be level with x
-    aF_new = idm(P, vF, v0F, true, gF, v);
+    aF_new = idm_fr(P, frF, vF, true, gF, v);
     mark(flag, aF_new + P.bsafe);
     if (aF_new < -P.bsafe) return r;
     r.gF = gF;
@@ -503,25 +514,28 @@ __device__ __forceinline__ LC lane_change(const StepArgs &a, const Soa &S, const
     r.aFn = aF_new;
   }
   r.safe = 1;
-  r.anew = idm(P, v, fminf(v0, tg.vmax), r.tkind != K_FREE, r.tgap, r.tvl);
+  // the changer's free-road term: its own lane's unless the target lane's limit differs
+  const float fr_new = tg.vmax == vmax_own ? fr_own : idm_free(v, fminf(v0, tg.vmax));
+  r.anew = idm_fr(P, fr_new, v, r.tkind != K_FREE, r.tgap, r.tvl);
   if (!mand) {
     float delta = r.anew - a_c;
     if (Ft >= 0) {
       float aF_old;
       if (Lt >= 0)
-        aF_old = idm(P, vF, v0F, true, (S.x[Lt] - xF) - P.L, S.v[Lt]);
+        aF_old = idm_fr(P, frF, vF, true, (S.x[Lt] - xF) - P.L, S.v[Lt]);
       else if (end_blocks(a, tg, li.len, tq, pl, xF, vF, t, flag))
-        aF_old = idm(P, vF, v0F, true, li.len - xF, 0.f);
+        aF_old = idm_fr(P, frF, vF, true, li.len - xF, 0.f);
       else
-        aF_old = idm(P, vF, v0F, false, 0.f, 0.f);
+        aF_old = idm_fr(P, frF, vF, false, 0.f, 0.f);
       delta += P.p * (aF_new - aF_old);
     }
     if (nb.sameF) {
       r.of = i - 1;
       const float xO = nb.xF, vO = nb.vF, v0O = fminf(nb.v0F, vmax_own);
-      float aO_old = idm(P, vO, v0O, true, (x - xO) - P.L, v);
-      float aO_new = own.kind != K_FREE ? idm(P, vO, v0O, true, own.gap + (x - xO), own.vl)
-                                        : idm(P, vO, v0O, false, 0.f, 0.f);
+      const float frO = idm_free(vO, v0O);
+      float aO_old = idm_fr(P, frO, vO, true, (x - xO) - P.L, v);
+      float aO_new = own.kind != K_FREE ? idm_fr(P, frO, vO, true, own.gap + (x - xO), own.vl)
+                                        : idm_fr(P, frO, vO, false, 0.f, 0.f);
       delta += P.p * (aO_new - aO_old);
     }
     r.inc = delta;
@@ -627,9 +641,10 @@ __device__ __forceinline__ Upd vehicle_sense(const StepArgs &a, const Soa &S, co
   // lane speed limits cap the desired speed: v0_eff = min(v0, vmax of the lane)
   const float vmax_own = MODS ? a.lane_vmax[c.l] : inf;
   u.own = own_leader<MODS>(a, S, dyn, i, c.l, c.li, c.nb, c.x, c.v, c.rp, c.nlc, pf_dyn, pf_li, c.id, t, u.flag);
-  u.a_own = idm(P, c.v, fminf(c.v0, vmax_own), u.own.kind != K_FREE, u.own.gap, u.own.vl);
-  u.lc = lane_change(a, S, dyn, i, c.l, c.li, c.x, c.v, c.v0, c.pl, c.nlc, c.nb, tg, vmax_own, c.id, t, u.own,
-                     u.a_own, u.flag);
+  const float fr_own = idm_free(c.v, fminf(c.v0, vmax_own));
+  u.a_own = idm_fr(P, fr_own, c.v, u.own.kind != K_FREE, u.own.gap, u.own.vl);
+  u.lc = lane_change(a, S, dyn, i, c.l, c.li, c.x, c.v, c.v0, c.pl, c.nlc, c.nb, tg, vmax_own, fr_own, c.id, t,
+                     u.own, u.a_own, u.flag);
   return u;
 }
 

@@ -284,6 +284,24 @@ int ms_set_lc_model(void *sim, const float *params, float margin);
    work for this. */
 int ms_set_lane_limits(void *sim, int n, const int *lanes, const float *vmax, const int *closed);
 
+/* Route planner for demand generation (the paper turns OD matrices into trips with routes,
+   Sec. III-C "Converter from OD matrix to travel demand"; at millions of trips that is the
+   host's bottleneck, so it runs on the GPU here).  Trip i goes from edge orig_edge[i] to
+   edge dest_edge[i] on the loaded network.  Route graph: an arc e -> f wherever a lane of e
+   links to exit edge f; entering f costs round(1000 * its length) integer millimetres.  The
+   route is the least-cost edge sequence from orig to dest, both included; among several,
+   the one that at every edge takes the lowest-id successor still on a least-cost route.
+   Every route is therefore valid input for ms_add_vehicles.  Destinations are processed in
+   batches of up to 4096 (about 2 GiB of device distances per batch; the call allocates and
+   frees its own device memory).
+   route_off: [n + 1] host, always filled (a trip that cannot reach its destination gets
+   an empty route; their number goes to *n_unreachable if not NULL).  route_edges: host
+   array of edges_capacity entries, or NULL to get route_off only; if route_off[n] exceeds
+   edges_capacity: MS_ERR_CAPACITY (route_off still filled).  Edges out of range: MS_ERR_ARG.
+   Synchronises with the simulation's stream. */
+int ms_route_trips(void *sim, int n, const int *orig_edge, const int *dest_edge, int64_t *route_off,
+                   int *route_edges, int64_t edges_capacity, int *n_unreachable);
+
 /* Counters of the learned decision since the model was set: [0] candidates, [1] rule
    fallbacks (low margin), [2] agreements with the rule, [3 + 3*rule + final] confusion. */
 int ms_read_lc_stats(void *sim, int64_t *out12);

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "moss103.h"
+#include "route_kernels.cuh"
 #include "step_kernels.cuh"
 
 using namespace moss;
@@ -62,6 +63,9 @@ struct Sim {
   unsigned char *d_lane_closed = nullptr;
   std::vector<float> h_lane_vmax;
   std::vector<unsigned char> h_lane_closed;
+  // route graph of the route planner (built on first use)
+  int *d_rg_off = nullptr, *d_rg_dst = nullptr;
+  long long *d_rg_cost = nullptr;
   int *d_routes = nullptr;
   unsigned long long *d_plan = nullptr;
   Soa A[2]{};
@@ -1343,6 +1347,165 @@ int ms_set_lc_log(void *sim, void *x, int *y, int cap, int *n) {
   s->lc.log_n = n;
   s->lc_mode = x ? MODE_LOG : (s->d_model && s->lc.model ? MODE_LEARN : MODE_PLAIN);
   drop_graphs(s);
+  return MS_OK;
+}
+
+// ---- route planner (demand generation) ------------------------------------------------
+
+int build_route_graph(Sim *s) {
+  if (s->d_rg_off) return MS_OK;
+  const int E = s->n_edges;
+  std::vector<int> off(E + 1, 0), dst;
+  std::vector<long long> cost(E);
+  for (int e = 0; e < E; ++e) {
+    std::vector<int> outs;
+    for (int q = 0; q < s->edge_nlanes[e]; ++q) {
+      const int l = s->edge_lane0[e] + q;
+      for (int k = s->succ_off[l]; k < s->succ_off[l + 1]; ++k) outs.push_back(s->succ_edge[k]);
+    }
+    std::sort(outs.begin(), outs.end());
+    outs.erase(std::unique(outs.begin(), outs.end()), outs.end());
+    dst.insert(dst.end(), outs.begin(), outs.end());
+    off[e + 1] = (int)dst.size();
+    cost[e] = std::llrint((double)s->lane_len[s->edge_lane0[e]] * 1000.0);   // mm, ties to even
+  }
+  if (dst.empty()) dst.push_back(0);
+  DALLOC(s->d_rg_off, off.size());
+  DALLOC(s->d_rg_dst, dst.size());
+  DALLOC(s->d_rg_cost, cost.size());
+  CK(cudaMemcpy(s->d_rg_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_rg_dst, dst.data(), dst.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_rg_cost, cost.data(), cost.size() * sizeof(long long), cudaMemcpyHostToDevice));
+  return MS_OK;
+}
+
+int ms_route_trips(void *sim, int n, const int *orig_edge, const int *dest_edge, int64_t *route_off,
+                   int *route_edges, int64_t edges_capacity, int *n_unreachable) {
+  Sim *s = (Sim *)sim;
+  if (!s || n < 0 || (n > 0 && (!orig_edge || !dest_edge)) || !route_off) return MS_ERR_ARG;
+  if (!s->net_loaded) return fail(s, MS_ERR_STATE, "load the network first");
+  const int E = s->n_edges;
+  for (int i = 0; i < n; ++i)
+    if (orig_edge[i] < 0 || orig_edge[i] >= E || dest_edge[i] < 0 || dest_edge[i] >= E)
+      return fail(s, MS_ERR_ARG, "trip edge out of range");
+  {
+    int r = build_route_graph(s);
+    if (r) return r;
+  }
+  const RouteGraph g{s->d_rg_off, s->d_rg_dst, s->d_rg_cost, E};
+  cudaStream_t st = s->stream;
+  // trips grouped by destination; destinations in batches of B columns (multiple of 32)
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return dest_edge[a] < dest_edge[b]; });
+  std::vector<int> dests;
+  for (int k = 0; k < n; ++k)
+    if (k == 0 || dest_edge[order[k]] != dest_edge[order[k - 1]]) dests.push_back(dest_edge[order[k]]);
+  const size_t budget = size_t(2) << 30;   // bytes of distances per batch
+  const int bmax = (int)std::max<size_t>(32, std::min<size_t>(4096, budget / (8 * (size_t)E)) / 32 * 32);
+  const int B = std::min(bmax, std::max(32, ((int)dests.size() + 31) / 32 * 32));
+  long long *d = nullptr;
+  int *dd = nullptr, *flag = nullptr, *dlen = nullptr, *dout = nullptr;
+  int4 *dtr = nullptr;
+  long long *doff = nullptr;
+  auto release = [&]() {
+    cudaFree(d); cudaFree(dd); cudaFree(flag); cudaFree(dlen); cudaFree(dout); cudaFree(dtr); cudaFree(doff);
+  };
+#define RCK(x)                                                                                   \
+  do {                                                                                           \
+    cudaError_t e_ = (x);                                                                        \
+    if (e_ != cudaSuccess) {                                                                     \
+      release();                                                                                 \
+      return fail(s, MS_ERR_CUDA, std::string(#x ": ") + cudaGetErrorString(e_));                \
+    }                                                                                            \
+  } while (0)
+  RCK(cudaMalloc(&d, sizeof(long long) * (size_t)B * E));
+  RCK(cudaMalloc(&dd, sizeof(int) * B));
+  RCK(cudaMalloc(&flag, sizeof(int) * 2));
+  RCK(cudaMalloc(&dlen, sizeof(int) * std::max(1, n)));
+  RCK(cudaMalloc(&dtr, sizeof(int4) * std::max(1, n)));
+  RCK(cudaMalloc(&doff, sizeof(long long) * (std::max(1, n) + 1)));
+  std::vector<int> len(n, 0);
+  std::vector<std::vector<int>> batch_edges;   // routes of each batch, in batch trip order
+  std::vector<std::pair<int, long long>> where(n, {-1, 0});   // trip -> (batch, offset)
+  int herr = 0;
+  const long long EB = (long long)E * B;
+  const int relax_blocks = (int)((EB + 255) / 256);
+  size_t k0 = 0;   // first trip (in `order`) of the batch
+  for (size_t b0 = 0; b0 < dests.size(); b0 += B) {
+    const int nb = (int)std::min<size_t>(B, dests.size() - b0);
+    RCK(cudaMemcpyAsync(dd, dests.data() + b0, sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+    k_route_init<<<relax_blocks, 256, 0, st>>>(d, E, B, dd, nb);
+    RCK(cudaGetLastError());
+    // relax until a round of 16 sweeps changes nothing (at most E sweeps: Bellman-Ford)
+    for (int sweeps = 0;; sweeps += 16) {
+      if (sweeps > E + 16) {
+        release();
+        return fail(s, MS_ERR_CUDA, "route distances did not converge");
+      }
+      int h = 0;
+      RCK(cudaMemsetAsync(flag, 0, sizeof(int), st));
+      for (int k = 0; k < 16; ++k) k_route_relax<<<relax_blocks, 256, 0, st>>>(d, g, B, flag);
+      RCK(cudaGetLastError());
+      RCK(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+      RCK(cudaStreamSynchronize(st));
+      if (!h) break;
+    }
+    // this batch's trips
+    std::vector<int4> tr;
+    size_t k1 = k0;
+    while (k1 < (size_t)n && dest_edge[order[k1]] <= dests[b0 + nb - 1]) {
+      const int i = order[k1];
+      const int col = (int)(std::lower_bound(dests.begin() + b0, dests.begin() + b0 + nb, dest_edge[i]) -
+                            (dests.begin() + b0));
+      tr.push_back(make_int4(i, orig_edge[i], dest_edge[i], col));
+      ++k1;
+    }
+    k0 = k1;
+    const int nt = (int)tr.size();
+    if (nt == 0) continue;
+    RCK(cudaMemcpyAsync(dtr, tr.data(), sizeof(int4) * nt, cudaMemcpyHostToDevice, st));
+    RCK(cudaMemsetAsync(flag + 1, 0, sizeof(int), st));
+    k_route_walk<<<(nt + 255) / 256, 256, 0, st>>>(d, g, B, dtr, nt, nullptr, dlen, nullptr, E, flag + 1);
+    std::vector<int> bl(nt);
+    RCK(cudaMemcpyAsync(bl.data(), dlen, sizeof(int) * nt, cudaMemcpyDeviceToHost, st));
+    RCK(cudaStreamSynchronize(st));
+    std::vector<long long> bo(nt + 1, 0);
+    for (int j = 0; j < nt; ++j) bo[j + 1] = bo[j] + bl[j];
+    batch_edges.emplace_back(std::max<long long>(1, bo[nt]));
+    RCK(cudaFree(dout));
+    dout = nullptr;
+    RCK(cudaMalloc(&dout, sizeof(int) * std::max<long long>(1, bo[nt])));
+    RCK(cudaMemcpyAsync(doff, bo.data(), sizeof(long long) * (nt + 1), cudaMemcpyHostToDevice, st));
+    k_route_walk<<<(nt + 255) / 256, 256, 0, st>>>(d, g, B, dtr, nt, doff, dlen, dout, E, flag + 1);
+    RCK(cudaGetLastError());
+    RCK(cudaMemcpyAsync(batch_edges.back().data(), dout, sizeof(int) * bo[nt], cudaMemcpyDeviceToHost, st));
+    int e2 = 0;
+    RCK(cudaMemcpyAsync(&e2, flag + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RCK(cudaStreamSynchronize(st));
+    herr |= e2;
+    for (int j = 0; j < nt; ++j) {
+      len[tr[j].x] = bl[j];
+      where[tr[j].x] = {(int)batch_edges.size() - 1, bo[j]};
+    }
+  }
+  release();
+#undef RCK
+  if (herr) return fail(s, MS_ERR_CUDA, "route walk left a least-cost route (device check)");
+  int bad = 0;
+  route_off[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    route_off[i + 1] = route_off[i] + len[i];
+    bad += len[i] == 0;
+  }
+  if (n_unreachable) *n_unreachable = bad;
+  if (!route_edges) return MS_OK;
+  if (route_off[n] > edges_capacity)
+    return fail(s, MS_ERR_CAPACITY, "route_edges needs " + std::to_string(route_off[n]) + " entries");
+  for (int i = 0; i < n; ++i)
+    if (len[i])
+      std::memcpy(route_edges + route_off[i], batch_edges[where[i].first].data() + where[i].second,
+                  sizeof(int) * len[i]);
   return MS_OK;
 }
 

@@ -18,7 +18,8 @@ MS_OK, MS_ERR_ARG, MS_ERR_ROUTE, MS_ERR_CAPACITY, MS_ERR_CUDA, MS_ERR_DEVICE, MS
 ERR_NAMES = {0: "OK", -1: "ARG", -2: "ROUTE", -3: "CAPACITY", -4: "CUDA", -5: "DEVICE", -6: "STATE"}
 SYMBOLS = ("ms_create", "ms_load_network", "ms_add_vehicles", "ms_step", "ms_step_timed", "ms_step_noalloc",
            "ms_load_network_batch", "ms_add_vehicles_batch", "ms_batch_offsets", "ms_autotune",
-           "ms_set_lc_log", "ms_set_lc_model", "ms_set_lane_limits", "ms_read_lc_stats", "ms_mlp_train_step",
+           "ms_set_lc_log", "ms_set_lc_model", "ms_set_lane_limits", "ms_route_trips", "ms_read_lc_stats",
+           "ms_mlp_train_step",
            "ms_mlp_grad",
            "ms_mlp_predict",
            "ms_sync", "ms_read_state",
@@ -91,6 +92,7 @@ def load():
         lib.ms_set_lc_log.argtypes = [vp, vp, vp, C.c_int, vp]
         lib.ms_set_lc_model.argtypes = [vp, vp, C.c_float]
         lib.ms_set_lane_limits.argtypes = [vp, C.c_int, vp, vp, vp]
+        lib.ms_route_trips.argtypes = [vp, C.c_int, vp, vp, vp, vp, C.c_int64, vp]
         lib.ms_read_lc_stats.argtypes = [vp, vp]
         lib.ms_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, C.c_int, C.c_float, vp, vp, vp, vp]
         lib.ms_mlp_grad.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, vp, vp]
@@ -356,6 +358,23 @@ class Sim:
         (x bf16 [cap,16], y int32 [cap], n int32 [1]); no arguments turns logging off."""
         cap = int(y.numel()) if y is not None else 0
         self._check(self.lib.ms_set_lc_log(self.h, _dp(x), _dp(y), cap, _dp(n)), "ms_set_lc_log")
+
+    def route_trips(self, orig, dest, capacity: int | None = None):
+        """Least-cost lane-linked routes (GPU) for trips orig[i] -> dest[i] (edge ids):
+        returns (route_off int64 [n+1], route_edges int32, n_unreachable)."""
+        o = np.ascontiguousarray(orig, np.int32)
+        d = np.ascontiguousarray(dest, np.int32)
+        n = int(o.shape[0])
+        off = np.zeros(n + 1, np.int64)
+        cap = int(capacity) if capacity is not None else max(1, 64 * n)
+        out = np.zeros(cap, np.int32)
+        bad = C.c_int(0)
+        rc = self.lib.ms_route_trips(self.h, n, _p(o), _p(d), _p(off), _p(out), cap, C.byref(bad))
+        if rc == MS_ERR_CAPACITY:
+            out = np.zeros(int(off[-1]), np.int32)
+            rc = self.lib.ms_route_trips(self.h, n, _p(o), _p(d), _p(off), _p(out), int(off[-1]), C.byref(bad))
+        self._check(rc, "ms_route_trips")
+        return off, out[:int(off[-1])].copy(), int(bad.value)
 
     def set_lane_limits(self, lanes, vmax=None, closed=None):
         """Lane speed limits (m/s; <= 0 or inf: none) and closures for the given lanes, in

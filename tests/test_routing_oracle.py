@@ -1,0 +1,94 @@
+"""Pins of the route planner's CPU reference (oracle/routing.py, reading R15) against
+brute force and invariants that do not come from it: on small networks every simple path
+is enumerated and the least-cost, then lexicographically smallest, one must be the route;
+routes are lane-linked, end at the destination and cost exactly the Dijkstra distance;
+trips between disjoint networks are unreachable."""
+import numpy as np
+import pytest
+
+from paper_2405_12520_b300 import synth
+import netkit
+from oracle import routing
+
+
+def _linked(net, e, f):
+    for q in range(int(net.edge_nlanes[e])):
+        l = int(net.edge_lane0[e]) + q
+        if f in net.succ_edge[net.succ_off[l]:net.succ_off[l + 1]]:
+            return True
+    return False
+
+
+def _brute_route(succ, c, o, d):
+    """Every simple path from o to d, depth first with branch and bound (a partial path
+    costing more than the best complete one is dropped): the least-cost path, then the
+    lexicographically smallest by edge ids; None if d is unreachable."""
+    import sys
+    sys.setrecursionlimit(10000)
+    best = [None, None]
+
+    def dfs(e, cost, path, seen):
+        if best[0] is not None and cost > best[0]:
+            return
+        if e == d:
+            t = tuple(path)
+            if best[0] is None or cost < best[0] or t < best[1]:
+                best[0], best[1] = cost, t
+            return
+        for f in succ[e]:
+            if f in seen:
+                continue
+            seen.add(f)
+            path.append(f)
+            dfs(f, cost + int(c[f]), path, seen)
+            path.pop()
+            seen.remove(f)
+
+    dfs(o, 0, [o], {o})
+    return best[1]
+
+
+@pytest.mark.parametrize("kind", ["grid3", "delaunay"])
+def test_routes_are_the_lexicographically_smallest_least_cost_paths(kind):
+    net = synth.grid_network(3, 3, 2, 200.0, 30, 3, "zero") if kind == "grid3" else \
+        synth.delaunay_network(9, box=900.0, seed=4)
+    src, dst = routing.edge_graph(net)
+    c = routing.edge_cost(net)
+    succ = [sorted(dst[src == e].tolist()) for e in range(net.n_edges)]
+    rng = np.random.default_rng(1)
+    pairs = [(int(a), int(b)) for a, b in rng.integers(0, net.n_edges, size=(25, 2))]
+    pairs.append((pairs[0][0], pairs[0][0]))   # origin = destination
+    off, edges, bad = routing.routes(net, [p[0] for p in pairs], [p[1] for p in pairs])
+    for i, (o, d) in enumerate(pairs):
+        got = edges[off[i]:off[i + 1]].tolist()
+        want = _brute_route(succ, c, o, d)
+        assert (tuple(got) if got else None) == want, (o, d)
+
+
+def test_routes_are_linked_and_cost_the_distance():
+    net = synth.grid_network(12, 12, 3, 200.0, 30, 3, "wave")
+    rng = np.random.default_rng(2)
+    o = rng.integers(0, net.n_edges, 300)
+    d = rng.integers(0, net.n_edges, 300)
+    off, edges, bad = routing.routes(net, o, d)
+    assert bad == 0
+    c = routing.edge_cost(net)
+    dist = routing.distances_to(net, np.unique(d))
+    col = {int(x): k for k, x in enumerate(np.unique(d))}
+    for i in range(300):
+        r = edges[off[i]:off[i + 1]]
+        assert r[0] == o[i] and r[-1] == d[i]
+        assert all(_linked(net, int(a), int(b)) for a, b in zip(r[:-1], r[1:]))
+        assert int(c[r[1:]].sum()) == dist[col[int(d[i])], o[i]]
+    # the grid is uniform: a least-cost route enters exactly as many edges as the fewest
+    # lane-linked hops
+    assert np.all((c == c[0]))
+
+
+def test_unreachable_trips_get_empty_routes():
+    a = netkit.line(3, 300.0, 1)
+    b = netkit.line(3, 300.0, 1)
+    net, _ = synth.union([a, b], [netkit.vehicles([-1], [0.0], [0.0], [[0]]), netkit.vehicles([-1], [0.0], [0.0], [[0]])])
+    off, edges, bad = routing.routes(net, [0, 0], [a.n_edges, 1])
+    assert bad == 1
+    assert off[1] - off[0] == 0 and off[2] - off[1] == 2

@@ -496,6 +496,55 @@ def run_learned(args):
         print(json.dumps(line), flush=True)
 
 
+def run_routes(args):
+    """Route planner (demand generation): least-cost lane-linked routes for 800,000 trips on
+    the 100x100 grid, destinations drawn from 1,024 zone edges, through ms_route_trips
+    (wall clock: trips up, distances, walks, routes back); the CPU reference on a bounded
+    sample of the same trips (64 zones)."""
+    import numpy as np
+    import torch
+    from paper_2405_12520_b300 import moss, synth
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    net = synth.large_grid_network()
+    rng = np.random.default_rng(args.seed + rank)
+    n = 800_000
+    zones = rng.choice(net.n_edges, 1024, replace=False).astype(np.int32)
+    d = rng.choice(zones, n).astype(np.int32)
+    o = rng.integers(0, net.n_edges, n).astype(np.int32)
+    sim = moss.Sim(synth.default_params())
+    sim.load_network(net)
+    sim.route_trips(o[:1000], d[:1000])   # builds the route graph once
+    reps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        off, edges, bad = sim.route_trips(o, d)
+    el = (time.perf_counter() - t0) / reps
+    line = {
+        "metric": "routes/s", "value": n / el, "unit": "routes/s", "n_gpus": world, "steps": reps,
+        "warmup": 1, "ms_per_step": 1e3 * el, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i64", "data": "synthetic", "gpu_launches": None,
+        "config": {"workload": "routes800k", "description": "800,000 trips, origins uniform over the 39,600 "
+                   "edges of the 100x100 grid, destinations uniform over 1,024 zone edges; one ms_route_trips "
+                   "call per repetition (host trip arrays in, host CSR routes out)",
+                   "route_edges": int(edges.size), "unreachable": bad},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import routing
+        zs = zones[:64]
+        m = np.isin(d, zs)
+        so, sd = o[m][:2000], d[m][:2000]
+        t1 = time.perf_counter()
+        routing.routes(net, so, sd)
+        el1 = time.perf_counter() - t1
+        line["cpu_baseline"] = {"value": so.size / el1, "unit": "routes/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{so.size} of the trips (64 of the zones): scipy Dijkstra from each "
+                                          f"zone + the next-hop walk, {el1:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -524,6 +573,8 @@ def main():
         run_batch(args)
     elif args.workload.startswith("learned"):
         run_learned(args)
+    elif args.workload.startswith("routes"):
+        run_routes(args)
     else:
         run_ours(args)
 

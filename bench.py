@@ -496,6 +496,63 @@ def run_learned(args):
         print(json.dumps(line), flush=True)
 
 
+def run_small(args):
+    """The small grid workload as a whole run: 4x4 grid, 500 trips, 3600 steps, on the GPU
+    (CUDA-graph replays, timed with events) and through the oracle (one core).
+    vehicle-steps = sum of the trips' travel times (every trip arrives)."""
+    import torch
+    from paper_2405_12520_b300 import moss, synth
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    net, dem = synth.small_grid_workload(args.seed)
+    params = synth.default_params()
+    stream = torch.cuda.current_stream()
+    runs = []
+    for k in range(max(1, min(args.steps, 5)) + args.warmup):
+        sim = moss.Sim(params, stream=stream, n_windows=12)
+        sim.load_network(net)
+        sim.add_vehicles(dem)
+        pre = 0   # vehicle-steps of the untimed first 16 steps (these also build the step graphs)
+        for _ in range(16):
+            pre += sim.read_metrics(lanes=False)["n_active"]
+            sim.step(1)
+        sim.sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.step(3600 - 16)
+        b.record(stream)
+        sim.sync()
+        m = sim.read_metrics(lanes=False)
+        if k >= args.warmup:
+            runs.append((a.elapsed_time(b), m, pre))
+        sim.destroy()
+    ms = sum(r[0] for r in runs) / len(runs)
+    m = runs[-1][1]
+    assert m["err"] == 0 and m["arrived"] == dem.n
+    # all trips arrived: their travel times are the run's vehicle-steps; the timed region
+    # holds all but those of the first 16 steps
+    vsteps = float(m["sum_tt"] - runs[-1][2])
+    line = {
+        "metric": "vehicle-steps/s", "value": vsteps / (ms * 1e-3), "unit": "vehicle-steps/s", "n_gpus": world,
+        "steps": 3600, "warmup": args.warmup, "ms_per_step": ms / (3600 - 16), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "gpu_launches": 4 * (3600 - 16),
+        "config": {"workload": "small", "description": "4x4 grid, 2 lanes, 200 m links, 500 trips departing "
+                   "over 600 s; one whole 3600-step run per repetition (steps 16..3600 timed, and the "
+                   "vehicle-steps they hold)", "repetitions": len(runs)},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        o = oracle.Oracle(net, dem, params, n_windows=12)
+        t0 = time.perf_counter()
+        o.run(3600)
+        el = time.perf_counter() - t0
+        om = o.metrics()
+        line["cpu_baseline"] = {"value": om["sum_tt"] / el, "unit": "vehicle-steps/s", "cores": 1, "kind": "oracle",
+                                "sample": f"the whole 3600-step run, {el:.2f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_routes(args):
     """Route planner (demand generation): least-cost lane-linked routes for 800,000 trips on
     the 100x100 grid, destinations drawn from 1,024 zone edges, through ms_route_trips
@@ -575,6 +632,8 @@ def main():
         run_learned(args)
     elif args.workload.startswith("routes"):
         run_routes(args)
+    elif args.workload == "small":
+        run_small(args)
     else:
         run_ours(args)
 

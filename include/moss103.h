@@ -302,6 +302,24 @@ int ms_set_lane_limits(void *sim, int n, const int *lanes, const float *vmax, co
 int ms_route_trips(void *sim, int n, const int *orig_edge, const int *dest_edge, int64_t *route_off,
                    int *route_edges, int64_t edges_capacity, int *n_unreachable);
 
+/* Gravity OD sampling for demand generation: the gravity model is one of the baseline OD
+   models the paper's OD generator offers (Sec. III-B; classical models, Sec. II-B), its
+   diffusion model and data not being available here.  Zone z is
+   edge zone_edge[z] (distinct) with attraction attract[z] > 0.  Trip k draws three 24-bit
+   uniforms u_s = top 24 bits of SplitMix64(seed ^ salt_s ^ k) / 2^24 (salts
+   0x5851F42D4C957F2D origin, 0x14057B7EF767814F destination, 0x2545F4914F6CDD1D departure):
+   origin zone = the first i whose cumulative attraction exceeds u * total; destination =
+   the first j whose cumulative weight exceeds u * total over w_ij = A_j / dkm_ij^gamma
+   (j != i; dkm_ij = float(least route cost from zone i's edge to zone j's, in mm, as in
+   ms_route_trips) * 1e-6 raised by gamma float products; 0 where unreachable; a zone that
+   reaches none keeps its trips at home); departure step = floor(u24 * t_span / 2^24).
+   Weights and cumulative sums are float32 in index order, IEEE-rounded, so a float32 CPU
+   computation draws the same trips.  Outputs (host, n each): orig_edge, dest_edge, t_dep;
+   routes then come from ms_route_trips.  At most 4096 zones (MS_ERR_CAPACITY); gamma 0..3,
+   t_span > 0 (MS_ERR_ARG).  Allocates and frees its own device memory; synchronises. */
+int ms_sample_trips(void *sim, int n_zones, const int *zone_edge, const float *attract, int gamma, int n,
+                    int t_span, uint64_t seed, int *orig_edge, int *dest_edge, int *t_dep);
+
 /* Counters of the learned decision since the model was set: [0] candidates, [1] rule
    fallbacks (low margin), [2] agreements with the rule, [3 + 3*rule + final] confusion. */
 int ms_read_lc_stats(void *sim, int64_t *out12);

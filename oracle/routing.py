@@ -84,3 +84,62 @@ def routes(net, orig, dest):
             out.append(e)
         off.append(len(out))
     return np.asarray(off, np.int64), np.asarray(out, np.int32), bad
+
+
+# ---------------------------------------------------------------------------------------
+# R16  Gravity OD sampling.  Zone z has a representative edge zone_edge[z] and attraction
+#      A_z > 0.  Trip k draws three 24-bit uniforms u = (SplitMix64(seed ^ salt ^ k) >> 40)
+#      / 2^24 with salts 0x5851F42D4C957F2D (origin), 0x14057B7EF767814F (destination) and
+#      0x2545F4914F6CDD1D (departure).  Origin zone: the first i whose cumulative attraction
+#      exceeds u * sum(A).  Destination zone: with w_j = A_j / dkm_ij^gamma for j != i
+#      (dkm_ij = float32(route cost from zone_edge[i] to zone_edge[j] in mm) * 1e-6, raised
+#      by gamma float32 products; 0 if unreachable), the first j whose cumulative weight
+#      exceeds u * sum(w).  Departure step: floor(u24 * t_span / 2^24) in integers.  Weights
+#      and sums are float32, accumulated in index order (so the draw is exact on both sides).
+#      An origin zone that reaches no other zone keeps the trip at home (destination = origin).
+# ---------------------------------------------------------------------------------------
+
+SALT_ORIGIN, SALT_DEST, SALT_TIME = 0x5851F42D4C957F2D, 0x14057B7EF767814F, 0x2545F4914F6CDD1D
+
+
+def _u24(splitmix64, seed, salt, k):
+    return splitmix64((seed ^ salt ^ k) % 2 ** 64) >> 40
+
+
+def _first_above(cdf, target):
+    """First index whose cumulative value exceeds target (float32 compare)."""
+    i = int(np.searchsorted(cdf, target, side="right"))
+    return min(i, cdf.shape[0] - 1)
+
+
+def gravity_trips(net, zone_edge, attract, gamma, n, t_span, seed, splitmix64):
+    """Trips (orig_edge, dest_edge, t_dep) of R16; splitmix64 is the published generator
+    (the oracle's C implementation, pinned by its published vector)."""
+    zone_edge = np.asarray(zone_edge, np.int64)
+    A = np.asarray(attract, np.float32)
+    Z = zone_edge.shape[0]
+    d = distances_to(net, zone_edge)            # [Z dest, E]: d[j, e] = cost e -> zone j
+    cost = d[:, zone_edge].T                    # cost[i, j] = zone i -> zone j
+    cdf_o = np.cumsum(A, dtype=np.float32)
+    W = np.zeros((Z, Z), np.float32)
+    for i in range(Z):
+        for j in range(Z):
+            if j == i or not np.isfinite(cost[i, j]):
+                continue
+            dkm = np.float32(np.float32(cost[i, j]) * np.float32(1e-6))
+            p = np.float32(1.0)
+            for _ in range(gamma):
+                p = np.float32(p * dkm)
+            W[i, j] = np.float32(A[j] / p)
+    cdf_d = np.cumsum(W, axis=1, dtype=np.float32)
+    o = np.zeros(n, np.int32)
+    de = np.zeros(n, np.int32)
+    td = np.zeros(n, np.int32)
+    for k in range(n):
+        uo = np.float32(_u24(splitmix64, seed, SALT_ORIGIN, k)) * np.float32(2.0 ** -24)
+        i = _first_above(cdf_o, np.float32(uo * cdf_o[-1]))
+        ud = np.float32(_u24(splitmix64, seed, SALT_DEST, k)) * np.float32(2.0 ** -24)
+        j = _first_above(cdf_d[i], np.float32(ud * cdf_d[i, -1])) if cdf_d[i, -1] > 0 else i
+        o[k], de[k] = zone_edge[i], zone_edge[j]
+        td[k] = (_u24(splitmix64, seed, SALT_TIME, k) * int(t_span)) >> 24
+    return o, de, td

@@ -1379,6 +1379,33 @@ int build_route_graph(Sim *s) {
   return MS_OK;
 }
 
+// least route costs toward nb destination edges (device array dd), in columns of d[E * B]:
+// pull sweeps until a round of 16 changes nothing (at most E sweeps, Bellman-Ford)
+cudaError_t route_distances(Sim *s, const RouteGraph &g, const int *dd, int nb, int B, long long *d, int *flag,
+                            bool &converged) {
+  cudaStream_t st = s->stream;
+  const long long EB = (long long)g.E * B;
+  const int blocks = (int)((EB + 255) / 256);
+  k_route_init<<<blocks, 256, 0, st>>>(d, g.E, B, dd, nb);
+  cudaError_t e = cudaGetLastError();
+  converged = false;
+  for (int sweeps = 0; e == cudaSuccess && sweeps <= g.E + 16; sweeps += 16) {
+    int h = 0;
+    e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    for (int k = 0; k < 16 && e == cudaSuccess; ++k) {
+      k_route_relax<<<blocks, 256, 0, st>>>(d, g, B, flag);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && !h) {
+      converged = true;
+      break;
+    }
+  }
+  return e;
+}
+
 int ms_route_trips(void *sim, int n, const int *orig_edge, const int *dest_edge, int64_t *route_off,
                    int *route_edges, int64_t edges_capacity, int *n_unreachable) {
   Sim *s = (Sim *)sim;
@@ -1429,27 +1456,15 @@ int ms_route_trips(void *sim, int n, const int *orig_edge, const int *dest_edge,
   std::vector<std::vector<int>> batch_edges;   // routes of each batch, in batch trip order
   std::vector<std::pair<int, long long>> where(n, {-1, 0});   // trip -> (batch, offset)
   int herr = 0;
-  const long long EB = (long long)E * B;
-  const int relax_blocks = (int)((EB + 255) / 256);
   size_t k0 = 0;   // first trip (in `order`) of the batch
   for (size_t b0 = 0; b0 < dests.size(); b0 += B) {
     const int nb = (int)std::min<size_t>(B, dests.size() - b0);
     RCK(cudaMemcpyAsync(dd, dests.data() + b0, sizeof(int) * nb, cudaMemcpyHostToDevice, st));
-    k_route_init<<<relax_blocks, 256, 0, st>>>(d, E, B, dd, nb);
-    RCK(cudaGetLastError());
-    // relax until a round of 16 sweeps changes nothing (at most E sweeps: Bellman-Ford)
-    for (int sweeps = 0;; sweeps += 16) {
-      if (sweeps > E + 16) {
-        release();
-        return fail(s, MS_ERR_CUDA, "route distances did not converge");
-      }
-      int h = 0;
-      RCK(cudaMemsetAsync(flag, 0, sizeof(int), st));
-      for (int k = 0; k < 16; ++k) k_route_relax<<<relax_blocks, 256, 0, st>>>(d, g, B, flag);
-      RCK(cudaGetLastError());
-      RCK(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-      RCK(cudaStreamSynchronize(st));
-      if (!h) break;
+    bool conv = false;
+    RCK(route_distances(s, g, dd, nb, B, d, flag, conv));
+    if (!conv) {
+      release();
+      return fail(s, MS_ERR_CUDA, "route distances did not converge");
     }
     // this batch's trips
     std::vector<int4> tr;
@@ -1506,6 +1521,74 @@ int ms_route_trips(void *sim, int n, const int *orig_edge, const int *dest_edge,
     if (len[i])
       std::memcpy(route_edges + route_off[i], batch_edges[where[i].first].data() + where[i].second,
                   sizeof(int) * len[i]);
+  return MS_OK;
+}
+
+int ms_sample_trips(void *sim, int n_zones, const int *zone_edge, const float *attract, int gamma, int n,
+                    int t_span, uint64_t seed, int *orig_edge, int *dest_edge, int *t_dep) {
+  Sim *s = (Sim *)sim;
+  if (!s || n_zones <= 0 || !zone_edge || !attract || n < 0 || (n > 0 && (!orig_edge || !dest_edge || !t_dep)))
+    return MS_ERR_ARG;
+  if (!s->net_loaded) return fail(s, MS_ERR_STATE, "load the network first");
+  if (n_zones > 4096) return fail(s, MS_ERR_CAPACITY, "at most 4096 zones");
+  if (gamma < 0 || gamma > 3 || t_span <= 0) return fail(s, MS_ERR_ARG, "gamma must be in 0..3 and t_span > 0");
+  {
+    std::vector<int> z(zone_edge, zone_edge + n_zones);
+    std::sort(z.begin(), z.end());
+    if (z.front() < 0 || z.back() >= s->n_edges) return fail(s, MS_ERR_ARG, "zone edge out of range");
+    if (std::adjacent_find(z.begin(), z.end()) != z.end()) return fail(s, MS_ERR_ARG, "zone edges must differ");
+    for (int k = 0; k < n_zones; ++k)
+      if (!(attract[k] > 0.f) || !std::isfinite(attract[k])) return fail(s, MS_ERR_ARG, "attractions must be > 0");
+  }
+  {
+    int r = build_route_graph(s);
+    if (r) return r;
+  }
+  const RouteGraph g{s->d_rg_off, s->d_rg_dst, s->d_rg_cost, s->n_edges};
+  cudaStream_t st = s->stream;
+  const int B = (n_zones + 31) / 32 * 32;
+  long long *d = nullptr;
+  int *dz = nullptr, *flag = nullptr, *dout = nullptr;
+  float *da = nullptr, *cdf_d = nullptr, *cdf_o = nullptr;
+  auto release = [&]() {
+    cudaFree(d); cudaFree(dz); cudaFree(flag); cudaFree(dout); cudaFree(da); cudaFree(cdf_d); cudaFree(cdf_o);
+  };
+#define RCK(x)                                                                                   \
+  do {                                                                                           \
+    cudaError_t e_ = (x);                                                                        \
+    if (e_ != cudaSuccess) {                                                                     \
+      release();                                                                                 \
+      return fail(s, MS_ERR_CUDA, std::string(#x ": ") + cudaGetErrorString(e_));                \
+    }                                                                                            \
+  } while (0)
+  RCK(cudaMalloc(&d, sizeof(long long) * (size_t)B * s->n_edges));
+  RCK(cudaMalloc(&dz, sizeof(int) * n_zones));
+  RCK(cudaMalloc(&flag, sizeof(int)));
+  RCK(cudaMalloc(&da, sizeof(float) * n_zones));
+  RCK(cudaMalloc(&cdf_d, sizeof(float) * (size_t)n_zones * n_zones));
+  RCK(cudaMalloc(&cdf_o, sizeof(float) * n_zones));
+  RCK(cudaMalloc(&dout, sizeof(int) * 3 * (size_t)std::max(1, n)));
+  RCK(cudaMemcpyAsync(dz, zone_edge, sizeof(int) * n_zones, cudaMemcpyHostToDevice, st));
+  RCK(cudaMemcpyAsync(da, attract, sizeof(float) * n_zones, cudaMemcpyHostToDevice, st));
+  bool conv = false;
+  RCK(route_distances(s, g, dz, n_zones, B, d, flag, conv));
+  if (!conv) {
+    release();
+    return fail(s, MS_ERR_CUDA, "route distances did not converge");
+  }
+  k_od_cdf<<<(n_zones + 127) / 128, 128, 0, st>>>(d, B, dz, da, n_zones, gamma, cdf_d, cdf_o);
+  RCK(cudaGetLastError());
+  if (n > 0) {
+    k_od_sample<<<(n + 255) / 256, 256, 0, st>>>(cdf_d, cdf_o, dz, n_zones, n, t_span, seed, dout, dout + n,
+                                                 dout + 2 * (size_t)n);
+    RCK(cudaGetLastError());
+    RCK(cudaMemcpyAsync(orig_edge, dout, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+    RCK(cudaMemcpyAsync(dest_edge, dout + n, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+    RCK(cudaMemcpyAsync(t_dep, dout + 2 * (size_t)n, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+  }
+  RCK(cudaStreamSynchronize(st));
+  release();
+#undef RCK
   return MS_OK;
 }
 

@@ -101,4 +101,70 @@ __global__ void k_route_walk(const long long *d, RouteGraph g, int B, const int4
   }
 }
 
+// Gravity OD sampling.  Per origin zone i (one thread, index order, float32): the
+// cumulative destination weights cdf[i][j] of w_ij = A_j / dkm_ij^gamma (j != i; 0 where
+// unreachable), dkm_ij = float(cost i -> j in mm) * 1e-6 raised by gamma products; the
+// origin CDF of the attractions in thread 0.  IEEE division (no fast math), so the
+// table matches a float32 CPU computation bit for bit.
+__global__ void k_od_cdf(const long long *d, int B, const int *zone_edge, const float *attract, int Z, int gamma,
+                         float *cdf_d, float *cdf_o) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Z) return;
+  if (i == 0) {
+    float acc = 0.f;
+    for (int z = 0; z < Z; ++z) {
+      acc = __fadd_rn(acc, attract[z]);
+      cdf_o[z] = acc;
+    }
+  }
+  const long long row = (long long)zone_edge[i] * B;   // distances from zone i's edge
+  float acc = 0.f;
+  for (int j = 0; j < Z; ++j) {
+    const long long c = d[row + j];
+    if (j != i && c < ROUTE_INF) {
+      const float dkm = __fmul_rn((float)c, 1e-6f);
+      float p = 1.f;
+      for (int g = 0; g < gamma; ++g) p = __fmul_rn(p, dkm);
+      acc = __fadd_rn(acc, __fdiv_rn(attract[j], p));
+    }
+    cdf_d[(long long)i * Z + j] = acc;
+  }
+}
+
+__device__ __forceinline__ unsigned long long od_mix(unsigned long long z) {   // SplitMix64
+  z += 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// first index whose cumulative value exceeds target (the last one if none does)
+__device__ __forceinline__ int od_first_above(const float *cdf, int Z, float target) {
+  int lo = 0, hi = Z;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (cdf[mid] > target) hi = mid; else lo = mid + 1;
+  }
+  return lo < Z ? lo : Z - 1;
+}
+
+__global__ void k_od_sample(const float *cdf_d, const float *cdf_o, const int *zone_edge, int Z, int n, int t_span,
+                            unsigned long long seed, int *orig, int *dest, int *tdep) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const unsigned long long kk = (unsigned long long)(unsigned)k;
+  const float uo = __fmul_rn((float)(uint32_t)(od_mix(seed ^ 0x5851F42D4C957F2DULL ^ kk) >> 40), 0x1p-24f);
+  const int i = od_first_above(cdf_o, Z, __fmul_rn(uo, cdf_o[Z - 1]));
+  const float *row = cdf_d + (long long)i * Z;
+  int j = i;   // no reachable destination: the trip stays at home
+  if (row[Z - 1] > 0.f) {
+    const float ud = __fmul_rn((float)(uint32_t)(od_mix(seed ^ 0x14057B7EF767814FULL ^ kk) >> 40), 0x1p-24f);
+    j = od_first_above(row, Z, __fmul_rn(ud, row[Z - 1]));
+  }
+  const unsigned long long ut = od_mix(seed ^ 0x2545F4914F6CDD1DULL ^ kk) >> 40;
+  orig[k] = zone_edge[i];
+  dest[k] = zone_edge[j];
+  tdep[k] = (int)((ut * (unsigned long long)t_span) >> 24);
+}
+
 }  // namespace moss

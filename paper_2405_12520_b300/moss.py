@@ -18,7 +18,8 @@ MS_OK, MS_ERR_ARG, MS_ERR_ROUTE, MS_ERR_CAPACITY, MS_ERR_CUDA, MS_ERR_DEVICE, MS
 ERR_NAMES = {0: "OK", -1: "ARG", -2: "ROUTE", -3: "CAPACITY", -4: "CUDA", -5: "DEVICE", -6: "STATE"}
 SYMBOLS = ("ms_create", "ms_load_network", "ms_add_vehicles", "ms_step", "ms_step_timed", "ms_step_noalloc",
            "ms_load_network_batch", "ms_add_vehicles_batch", "ms_batch_offsets", "ms_autotune",
-           "ms_set_lc_log", "ms_set_lc_model", "ms_set_lane_limits", "ms_route_trips", "ms_read_lc_stats",
+           "ms_set_lc_log", "ms_set_lc_model", "ms_set_lane_limits", "ms_route_trips", "ms_sample_trips",
+           "ms_read_lc_stats",
            "ms_mlp_train_step",
            "ms_mlp_grad",
            "ms_mlp_predict",
@@ -93,6 +94,7 @@ def load():
         lib.ms_set_lc_model.argtypes = [vp, vp, C.c_float]
         lib.ms_set_lane_limits.argtypes = [vp, C.c_int, vp, vp, vp]
         lib.ms_route_trips.argtypes = [vp, C.c_int, vp, vp, vp, vp, C.c_int64, vp]
+        lib.ms_sample_trips.argtypes = [vp, C.c_int, vp, vp, C.c_int, C.c_int, C.c_int, C.c_uint64, vp, vp, vp]
         lib.ms_read_lc_stats.argtypes = [vp, vp]
         lib.ms_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, C.c_int, C.c_float, vp, vp, vp, vp]
         lib.ms_mlp_grad.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, vp, vp]
@@ -358,6 +360,17 @@ class Sim:
         (x bf16 [cap,16], y int32 [cap], n int32 [1]); no arguments turns logging off."""
         cap = int(y.numel()) if y is not None else 0
         self._check(self.lib.ms_set_lc_log(self.h, _dp(x), _dp(y), cap, _dp(n)), "ms_set_lc_log")
+
+    def sample_trips(self, zone_edge, attract, gamma: int, n: int, t_span: int, seed: int):
+        """Gravity OD sampling (GPU): returns (orig_edge, dest_edge, t_dep) int32 arrays."""
+        z = np.ascontiguousarray(zone_edge, np.int32)
+        a = np.ascontiguousarray(attract, np.float32)
+        o = np.zeros(n, np.int32)
+        d = np.zeros(n, np.int32)
+        t = np.zeros(n, np.int32)
+        self._check(self.lib.ms_sample_trips(self.h, int(z.shape[0]), _p(z), _p(a), int(gamma), int(n), int(t_span),
+                                             int(seed) & 0xFFFFFFFFFFFFFFFF, _p(o), _p(d), _p(t)), "ms_sample_trips")
+        return o, d, t
 
     def route_trips(self, orig, dest, capacity: int | None = None):
         """Least-cost lane-linked routes (GPU) for trips orig[i] -> dest[i] (edge ids):

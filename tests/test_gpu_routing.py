@@ -85,3 +85,49 @@ def test_gpu_routes_drive_a_simulation():
     s.sync()
     m = s.read_metrics(lanes=False)
     assert m["err"] == 0 and m["inserted"] > 0.9 * n and m["arrived"] > 0
+
+
+@pytest.mark.parametrize("gamma", [0, 2])
+def test_gravity_sampling_matches_the_reference(gamma):
+    """ms_sample_trips draws the same trips (origin, destination, departure) as the CPU
+    reference, bit for bit, on a 12x12 grid with 64 zones."""
+    import oracle
+    net = synth.grid_network(12, 12, 3, 200.0, 30, 3, "wave")
+    rng = np.random.default_rng(9)
+    zones = rng.choice(net.n_edges, 64, replace=False).astype(np.int32)
+    A = rng.lognormal(0.0, 1.0, 64).astype(np.float32)
+    s = _sim(net)
+    o, d, t = s.sample_trips(zones, A, gamma, 20000, 900, 1234)
+    ro, rd, rt = routing.gravity_trips(net, zones, A, gamma, 20000, 900, 1234, oracle.splitmix64)
+    np.testing.assert_array_equal(o, ro)
+    np.testing.assert_array_equal(d, rd)
+    np.testing.assert_array_equal(t, rt)
+
+
+def test_gravity_sampling_with_an_isolated_zone_and_into_a_simulation():
+    import oracle
+    from paper_2405_12520_b300 import moss
+    a = synth.grid_network(6, 6, 2, 200.0, 30, 3, "zero")
+    b = netkit.line(3, 300.0, 1)
+    net, _ = synth.union([a, b], [netkit.vehicles([-1], [0.0], [0.0], [[0]])] * 2)
+    zones = np.array([0, 5, 17, 40, a.n_edges], np.int32)   # the last zone is on the other network
+    A = np.array([1.0, 2.0, 1.0, 3.0, 5.0], np.float32)
+    s = _sim(net)
+    o, d, t = s.sample_trips(zones, A, 1, 3000, 300, 99)
+    ro, rd, rt = routing.gravity_trips(net, zones, A, 1, 3000, 300, 99, oracle.splitmix64)
+    np.testing.assert_array_equal(o, ro)
+    np.testing.assert_array_equal(d, rd)
+    np.testing.assert_array_equal(t, rt)
+    home = o == a.n_edges
+    assert home.any() and np.all(d[home] == a.n_edges)   # reaches no other zone: stays
+    off, edges, bad = s.route_trips(o, d)
+    assert bad == 0
+    dem = synth.Demand(t_dep=t, v0=np.full(o.size, 13.9, np.float32), route_off=off, route_edges=edges,
+                       lane=np.full(o.size, -1, np.int32), x=np.zeros(o.size, np.float32),
+                       v=np.zeros(o.size, np.float32))
+    sim = moss.Sim(synth.default_params())
+    sim.load_network(net)
+    sim.add_vehicles(dem)
+    sim.step(600)
+    sim.sync()
+    assert sim.read_metrics(lanes=False)["err"] == 0

@@ -92,3 +92,55 @@ def test_unreachable_trips_get_empty_routes():
     off, edges, bad = routing.routes(net, [0, 0], [a.n_edges, 1])
     assert bad == 1
     assert off[1] - off[0] == 0 and off[2] - off[1] == 2
+
+
+# ---------------------------------------------------------------------------------------
+# gravity OD sampling (R16)
+# ---------------------------------------------------------------------------------------
+
+def _sm(z):
+    import oracle
+    return oracle.splitmix64(z)   # the published generator (pinned by its vector)
+
+
+def test_gravity_origins_and_destinations_follow_the_weights():
+    """gamma = 0: P(O = i) = A_i / sum A and P(D = j | O = i) = A_j / sum_{k != i} A_k; the
+    sampled shares agree within 4 binomial standard deviations; departures are uniform."""
+    net = synth.grid_network(6, 6, 1, 200.0, 30, 3, "zero")
+    rng = np.random.default_rng(3)
+    zones = rng.choice(net.n_edges, 6, replace=False)
+    A = np.array([1.0, 2.0, 4.0, 0.5, 3.0, 1.5], np.float32)
+    n = 6000
+    o, d, t = routing.gravity_trips(net, zones, A, 0, n, 600, 77, _sm)
+    zi = {int(z): k for k, z in enumerate(zones)}
+    oi = np.array([zi[int(x)] for x in o])
+    di = np.array([zi[int(x)] for x in d])
+    assert np.all(oi != di)
+    p_o = A / A.sum()
+    f_o = np.bincount(oi, minlength=6) / n
+    assert np.all(np.abs(f_o - p_o) <= 4 * np.sqrt(p_o * (1 - p_o) / n))
+    sel = oi == 2   # destinations of zone 2's trips
+    p_d = np.where(np.arange(6) == 2, 0.0, A) / (A.sum() - A[2])
+    f_d = np.bincount(di[sel], minlength=6) / sel.sum()
+    assert np.all(np.abs(f_d - p_d) <= 4 * np.sqrt(p_d * (1 - p_d) / sel.sum()) + 1e-12)
+    assert t.min() >= 0 and t.max() < 600 and abs(t.mean() - 299.5) < 4 * 600 / np.sqrt(12 * n)
+
+
+def test_gravity_decays_with_route_distance():
+    """gamma = 2, equal attractions, on a one-lane line road: from the zone at one end the
+    destination shares are proportional to 1 / (route distance)^2 (closed form over the
+    zones' distances along the line)."""
+    net = netkit.line(8, 500.0, 1)
+    zones = np.array([0, 2, 4, 6], np.int64)   # eastbound edges 0 -> 1, 2 -> 3, ...
+    A = np.ones(4, np.float32)
+    n = 8000
+    o, d, t = routing.gravity_trips(net, zones, A, 2, n, 60, 5, _sm)
+    sel = o == 0
+    dist = routing.distances_to(net, zones)[:, 0]   # cost from edge 0 to each zone edge
+    # the route costs are the line's: zone k is 2k edges of 500 m further along
+    np.testing.assert_array_equal(dist, [0.0, 1.0e6, 2.0e6, 3.0e6])
+    w = np.zeros(4)
+    w[1:] = 1.0 / dist[1:] ** 2
+    p = w / w.sum()
+    f = np.array([(d[sel] == z).mean() for z in zones])
+    assert np.all(np.abs(f - p) <= 4 * np.sqrt(p * (1 - p) / sel.sum()) + 1e-12)

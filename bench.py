@@ -554,10 +554,10 @@ def run_small(args):
 
 
 def run_routes(args):
-    """Route planner (demand generation): least-cost lane-linked routes for 800,000 trips on
-    the 100x100 grid, destinations drawn from 1,024 zone edges, through ms_route_trips
-    (wall clock: trips up, distances, walks, routes back); the CPU reference on a bounded
-    sample of the same trips (64 zones)."""
+    """Demand generation on the GPU: 800,000 gravity-model trips between 1,024 zone edges of
+    the 100x100 grid (attractions LogNormal(0, 1), decay 1 / route distance^2) sampled by
+    ms_sample_trips, then routed by ms_route_trips (wall clock through the C ABI, host
+    arrays in and out); the CPU reference on a bounded sample."""
     import numpy as np
     import torch
     from paper_2405_12520_b300 import moss, synth
@@ -567,37 +567,43 @@ def run_routes(args):
     rng = np.random.default_rng(args.seed + rank)
     n = 800_000
     zones = rng.choice(net.n_edges, 1024, replace=False).astype(np.int32)
-    d = rng.choice(zones, n).astype(np.int32)
-    o = rng.integers(0, net.n_edges, n).astype(np.int32)
+    A = rng.lognormal(0.0, 1.0, zones.size).astype(np.float32)
     sim = moss.Sim(synth.default_params())
     sim.load_network(net)
-    sim.route_trips(o[:1000], d[:1000])   # builds the route graph once
+    sim.route_trips(zones[:64], zones[64:128])   # builds the route graph once
     reps = max(1, min(args.steps, 3))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(reps):
+    ts = tr = 0.0
+    for r in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        o, d, t = sim.sample_trips(zones, A, 2, n, 3600, args.seed + 1000 * r)
+        t1 = time.perf_counter()
         off, edges, bad = sim.route_trips(o, d)
-    el = (time.perf_counter() - t0) / reps
+        t2 = time.perf_counter()
+        ts += t1 - t0
+        tr += t2 - t1
+    ts, tr = ts / reps, tr / reps
     line = {
-        "metric": "routes/s", "value": n / el, "unit": "routes/s", "n_gpus": world, "steps": reps,
-        "warmup": 1, "ms_per_step": 1e3 * el, "higher_is_better": True, "scaling": "weak",
+        "metric": "trips/s", "value": n / (ts + tr), "unit": "trips/s", "n_gpus": world, "steps": reps,
+        "warmup": 1, "ms_per_step": 1e3 * (ts + tr), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "i64", "data": "synthetic", "gpu_launches": None,
-        "config": {"workload": "routes800k", "description": "800,000 trips, origins uniform over the 39,600 "
-                   "edges of the 100x100 grid, destinations uniform over 1,024 zone edges; one ms_route_trips "
-                   "call per repetition (host trip arrays in, host CSR routes out)",
-                   "route_edges": int(edges.size), "unreachable": bad},
+        "config": {"workload": "routes800k", "description": "800,000 gravity trips (1,024 zone edges of the "
+                   "100x100 grid, A ~ LogNormal(0,1), gamma 2, departures over 3600 s) sampled by "
+                   "ms_sample_trips, then routed by ms_route_trips; one of each per repetition",
+                   "sample_ms": 1e3 * ts, "route_ms": 1e3 * tr, "route_edges": int(edges.size),
+                   "unreachable": bad},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
         from oracle import routing
-        zs = zones[:64]
-        m = np.isin(d, zs)
-        so, sd = o[m][:2000], d[m][:2000]
-        t1 = time.perf_counter()
+        zs, As = zones[:64], A[:64]
+        t3 = time.perf_counter()
+        so, sd, st = routing.gravity_trips(net, zs, As, 2, 2000, 3600, args.seed, oracle.splitmix64)
         routing.routes(net, so, sd)
-        el1 = time.perf_counter() - t1
-        line["cpu_baseline"] = {"value": so.size / el1, "unit": "routes/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{so.size} of the trips (64 of the zones): scipy Dijkstra from each "
-                                          f"zone + the next-hop walk, {el1:.1f} s"}
+        el = time.perf_counter() - t3
+        line["cpu_baseline"] = {"value": so.size / el, "unit": "trips/s", "cores": 1, "kind": "oracle",
+                                "sample": f"2000 trips between 64 of the zones: sampling + scipy Dijkstra "
+                                          f"from each zone + the next-hop walk, {el:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -189,23 +189,45 @@ DecideKernel decide_kernel(int mode, bool dbg, bool mods) {
   return mods ? decide_kernel_m<true>(mode, dbg) : decide_kernel_m<false>(mode, dbg);
 }
 
+// a step kernel launch with programmatic stream serialization: it may start while the
+// previous kernel in the stream drains (the kernel waits in pdl_enter before reading)
+template <typename... Args>
+cudaError_t launch_pdl(void (*k)(Args...), int grid, int block, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // one step = four launches (+ the debug order check); ev (5 events) brackets each kernel
 cudaError_t launch_step(const Sim *s, const StepArgs &a, cudaStream_t st, cudaEvent_t *ev) {
   const LaunchCfg &c = s->cfg;
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
   if (ev) cudaEventRecord(ev[0], st);
   const size_t smem = s->lc_mode == MODE_LEARN ? learn_smem(c.blk_decide) : 0;
-  decide_kernel(s->lc_mode, s->prm.debug != 0, a.P.lane_mods != 0)<<<c.grid_decide, c.blk_decide, smem, st>>>(a);
+  ok(launch_pdl(decide_kernel(s->lc_mode, s->prm.debug != 0, a.P.lane_mods != 0), c.grid_decide, c.blk_decide, smem,
+                st, a));
   if (ev) cudaEventRecord(ev[1], st);
-  k_lanes<<<s->n_tiles, LANE_THREADS, 0, st>>>(a);
+  ok(launch_pdl(k_lanes, s->n_tiles, LANE_THREADS, 0, st, a));
   if (ev) cudaEventRecord(ev[2], st);
-  k_bucket<<<c.grid_bucket, c.blk_bucket, 0, st>>>(a, s->n_tiles);
+  ok(launch_pdl(k_bucket, c.grid_bucket, c.blk_bucket, 0, st, a, s->n_tiles));
   if (ev) cudaEventRecord(ev[3], st);
-  k_apply<<<c.grid_apply, c.blk_apply, 0, st>>>(a);
+  ok(launch_pdl(k_apply, c.grid_apply, c.blk_apply, 0, st, a));
   if (s->P.signal_mode == 1 && s->n_ctrl > 0)   // controllers of the next step
-    k_signals<<<(s->n_ctrl + 7) / 8, 256, 0, st>>>(a);
+    ok(launch_pdl(k_signals, (s->n_ctrl + 7) / 8, 256, 0, st, a));
   if (ev) cudaEventRecord(ev[4], st);
-  if (s->prm.debug) k_check<<<c.grid_bucket, c.blk_bucket, 0, st>>>(a);
-  return cudaGetLastError();
+  if (s->prm.debug) ok(launch_pdl(k_check, c.grid_bucket, c.blk_bucket, 0, st, a));
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t enqueue_step(Sim *s, cudaStream_t st) { return launch_step(s, make_args(s), st, nullptr); }

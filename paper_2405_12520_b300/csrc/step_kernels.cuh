@@ -191,6 +191,17 @@ struct StepArgs {
   DevParams P;
 };
 
+// Programmatic dependent launch: the step's kernels are launched so that each may start
+// while the previous one drains.  A kernel first waits here until the previous kernel has
+// completed and its writes are visible (everything before that point touches nothing it
+// wrote), then lets its own dependents launch; they can only start once all of its blocks
+// have started, so they never take a slot a block of this kernel still needs.  Both are
+// no-ops for an ordinary launch.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ------------------------------------------------------------------------------------
 // model (FP32)
 // ------------------------------------------------------------------------------------
@@ -797,6 +808,7 @@ template <int MODE, bool DBG, bool MODS>
 __global__ void __launch_bounds__(512, 2) __maxnreg__((MODE == MODE_PLAIN && !DBG) ? 48 : 64)
     k_decide_t(StepArgs a) {
   extern __shared__ __align__(16) unsigned char lsm[];
+  pdl_enter();
   if constexpr (MODE == MODE_LEARN) {
     const uint32_t *src = reinterpret_cast<const uint32_t *>(a.lc.model);
     uint32_t *dst = reinterpret_cast<uint32_t *>(lsm);
@@ -967,6 +979,7 @@ __global__ void __launch_bounds__(LANE_THREADS, 4) k_lanes(StepArgs a) {
   __shared__ int s_tile;
   __shared__ unsigned long long s_wsum[LANE_ITEMS][LANE_WARPS];
   __shared__ unsigned long long s_part[LANE_WARPS];
+  pdl_enter();
   if (threadIdx.x == 0) s_tile = atomicAdd(&a.ctrl->tile_ticket, 1);
   __syncthreads();
   const int tile = s_tile;
@@ -1119,6 +1132,7 @@ __global__ void __launch_bounds__(LANE_THREADS, 4) k_lanes(StepArgs a) {
 // by streaming the result codes of the snapshot's vehicles.
 __global__ void k_bucket(StepArgs a, int n_tiles) {
   __shared__ int s_cnt;
+  pdl_enter();
   const int t = a.ctrl->t_apply;
   const int p = t & 1;
   const Soa S = a.A[p];
@@ -1176,6 +1190,7 @@ __device__ __forceinline__ bool bucket_less(int4 f, int4 e) {
 // t+1 buffer: stayers by their rank among the lane's stayers plus the arrivals ranked
 // before them, arrivals by their bucket rank.
 __global__ void k_apply(StepArgs a) {
+  pdl_enter();
   const int t = a.ctrl->t_apply;
   const int p = t & 1;
   const Soa S = a.A[p];
@@ -1247,6 +1262,7 @@ __global__ void k_apply(StepArgs a) {
 
 // Debug check of the t+1 buffer: sorted by (lane, x), gap >= 0 (up to float rounding).
 __global__ void k_check(StepArgs a) {
+  pdl_enter();
   const int t = a.ctrl->t;   // already advanced
   const int p = t & 1;
   const Soa S = a.A[p];
@@ -1269,6 +1285,7 @@ __global__ void k_check(StepArgs a) {
 // in, else the lowest index; a different winner first shows the green phase yellow for the
 // controller's yellow time (or turns green at once when that is 0).
 __global__ void k_signals(StepArgs a) {
+  pdl_enter();
   const int c = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (c >= a.n_ctrl) return;   // whole warps
   const int lane = threadIdx.x & 31;

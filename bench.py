@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 KERNELS = ("k_decide", "k_lanes", "k_bucket", "k_apply")
 # algorithmic bytes of each kernel: SoA fields it must read / write per vehicle
 # (x, v, v0, lane, rp, nxt, id = 28 B), per lane (counts, starts, queue heads), per mover
+STEP_LAUNCHES = 5   # k_decide, two lane-scan passes, k_bucket, k_apply
 B_DECIDE_VEH = 48   # reads the 36-B state (x, v, v0, lane, rp, plan word, nl, id); writes x', v', code
 B_APPLY_VEH = 72    # reads code, x', v', v0, rp, plan word, nl, id; writes the 36-B state
 B_LANES_LANE = 40
@@ -323,7 +324,7 @@ def run_ours(args):
         "metric": "vehicle-steps/s", "value": value, "unit": "vehicle-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "gpu_launches": (5 if args.signals == "mp" else 4) * args.steps,
+        "data": "synthetic", "gpu_launches": (STEP_LAUNCHES + (1 if args.signals == "mp" else 0)) * args.steps,
         "config": {"workload": args.workload, "description": desc, **vdesc, "vehicles": dem.n,
                    "lanes": net.n_lanes, "active_start": n_act[0], "active_end": n_end,
                    "l2": "flushed (256 MiB write) before every timed step; each step timed alone",
@@ -409,7 +410,7 @@ def run_batch(args):
         "metric": "vehicle-steps/s", "value": value, "unit": "vehicle-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": STEP_LAUNCHES * args.steps,
         "config": {"workload": "batch256", "scenarios": n_scen, "vehicles": int(sum(d.n for d in dems)),
                    "lanes": int(sum(n.n_lanes for n in nets)),
                    "description": "grids 4x4..32x32, 3 lanes, 300 m links, random signal plans; vehicles per "
@@ -418,7 +419,7 @@ def run_batch(args):
         "autotune": {"best_ms_per_step": tune_ms, "block": tune_cfg[0], "decide_grid_factor": tune_cfg[1],
                      "apply_grid_factor": tune_cfg[2]},
         "separate": {"value": vs_s / (ms_s * 1e-3), "ms_per_step": ms_s / args.steps,
-                     "gpu_launches": 4 * n_scen * args.steps},
+                     "gpu_launches": STEP_LAUNCHES * n_scen * args.steps},
         "speedup_vs_separate": (vs_b / ms_b) / (vs_s / ms_s),
         "errors": m_b["err"], "clocks": clk.summary(),
     }
@@ -482,7 +483,7 @@ def run_learned(args):
         "metric": "vehicle-steps/s", "value": L["value"], "unit": "vehicle-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": L["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 state, bf16 MLP operands / f32 accumulate",
-        "data": "synthetic", "gpu_launches": 4 * args.steps,
+        "data": "synthetic", "gpu_launches": STEP_LAUNCHES * args.steps,
         "config": {"workload": "learned1m", "description": desc + "; lane-change decisions by the learned MLP",
                    "l2": "flushed (256 MiB write) before every timed step; each step timed alone",
                    "train": {"samples": int(x.shape[0]), "class_counts": cnt.tolist(), "seeds": args.train_seeds,
@@ -535,7 +536,7 @@ def run_small(args):
     line = {
         "metric": "vehicle-steps/s", "value": vsteps / (ms * 1e-3), "unit": "vehicle-steps/s", "n_gpus": world,
         "steps": 3600, "warmup": args.warmup, "ms_per_step": ms / (3600 - 16), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "gpu_launches": 4 * (3600 - 16),
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "gpu_launches": STEP_LAUNCHES * (3600 - 16),
         "config": {"workload": "small", "description": "4x4 grid, 2 lanes, 200 m links, 500 trips departing "
                    "over 600 s; one whole 3600-step run per repetition (steps 16..3600 timed, and the "
                    "vehicle-steps they hold)", "repetitions": len(runs)},

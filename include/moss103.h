@@ -37,7 +37,7 @@ extern "C" {
 
 /* device error bits (ms_metrics.err) */
 #define MS_DEV_HOP 1u        /* a vehicle crossed more than one lane end in a step */
-#define MS_DEV_SCAN 2u       /* lane scan: a predecessor tile's aggregate exceeded its wait limit */
+#define MS_DEV_SCAN 2u       /* reserved (the lane scan no longer waits on other blocks) */
 #define MS_DEV_ORDER 4u      /* debug check: output not sorted by (lane, x) or gap < 0 */
 #define MS_DEV_BUCKET 8u     /* a moved vehicle did not find its merge record */
 
@@ -196,9 +196,9 @@ int ms_step_timed(void *sim, int n, float *ms_per_kernel);
    that runs inside a fixed device-memory budget reserved in advance, or a host component
    that holds no right to call cudaMalloc on a shared device.  ms_step may allocate on its
    first call (it instantiates CUDA graphs), and the lane scan of every step keeps its
-   per-tile status in memory of the simulation.  This entry point allocates nothing: it
-   launches the step's kernels directly and keeps the lane scan's per-tile status in one
-   static device array of MS_NOALLOC_MAX_TILES tiles (12 bytes each), which every GPU that
+   per-tile aggregates in memory of the simulation.  This entry point allocates nothing: it
+   launches the step's kernels directly and keeps the lane scan's per-tile aggregates in one
+   static device array of MS_NOALLOC_MAX_TILES tiles (8 bytes each), which every GPU that
    loads this library holds until the process exits.
    - The paper has no counterpart; results are identical to ms_step.
    - Networks with more than MS_NOALLOC_MAX_TILES * MS_NOALLOC_TILE_LANES lanes:
@@ -208,7 +208,8 @@ int ms_step_timed(void *sim, int n, float *ms_per_kernel);
      call before any stream capture begins.
    - Every call, from any simulation, shares the one array: calls that overlap on the GPU
      (different streams, threads or simulations running at the same time) race and give
-     wrong results.  Each call clears the array before using it.
+     wrong results.  Each step writes the tiles it uses before reading them, so nothing
+     needs clearing between calls.
    Returns MS_ERR_CUDA if a launch fails; device error bits are reported by ms_sync. */
 int ms_step_noalloc(void *sim, int n);
 

@@ -77,7 +77,6 @@ struct Sim {
   float *d_res_x = nullptr, *d_res_v = nullptr;
   int *d_res_code = nullptr, *d_res_nl = nullptr, *d_arr_fill = nullptr;
   int2 *d_res_pos = nullptr;
-  int *d_tile_flag = nullptr;
   unsigned long long *d_tile_agg = nullptr;
   int *d_qoff = nullptr, *d_qtrip = nullptr;
   int2 *d_qhd = nullptr;
@@ -160,7 +159,6 @@ StepArgs make_args(Sim *s) {
   a.res_code_nl = s->d_res_nl;
   a.res_pos = s->d_res_pos;
   a.arr_fill = s->d_arr_fill;
-  a.tile_flag = s->d_tile_flag;
   a.tile_agg = s->d_tile_agg;
   a.q_off = s->d_qoff;
   a.q_trip = s->d_qtrip;
@@ -206,7 +204,8 @@ cudaError_t launch_pdl(void (*k)(Args...), int grid, int block, size_t smem, cud
   return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
-// one step = four launches (+ the debug order check); ev (5 events) brackets each kernel
+// one step = five launches (+ the debug order check); ev (5 events) brackets the step's
+// parts: decide, the two lane-scan passes together, bucket, apply
 cudaError_t launch_step(const Sim *s, const StepArgs &a, cudaStream_t st, cudaEvent_t *ev) {
   const LaunchCfg &c = s->cfg;
   cudaError_t e = cudaSuccess;
@@ -218,9 +217,10 @@ cudaError_t launch_step(const Sim *s, const StepArgs &a, cudaStream_t st, cudaEv
   ok(launch_pdl(decide_kernel(s->lc_mode, s->prm.debug != 0, a.P.lane_mods != 0), c.grid_decide, c.blk_decide, smem,
                 st, a));
   if (ev) cudaEventRecord(ev[1], st);
-  ok(launch_pdl(k_lanes, s->n_tiles, LANE_THREADS, 0, st, a));
+  ok(launch_pdl(k_lanes_t<0>, s->n_tiles, LANE_THREADS, 0, st, a));   // tile aggregates
+  ok(launch_pdl(k_lanes_t<1>, s->n_tiles, LANE_THREADS, 0, st, a));   // counts, starts, departures
   if (ev) cudaEventRecord(ev[2], st);
-  ok(launch_pdl(k_bucket, c.grid_bucket, c.blk_bucket, 0, st, a, s->n_tiles));
+  ok(launch_pdl(k_bucket, c.grid_bucket, c.blk_bucket, 0, st, a));
   if (ev) cudaEventRecord(ev[3], st);
   ok(launch_pdl(k_apply, c.grid_apply, c.blk_apply, 0, st, a));
   if (s->P.signal_mode == 1 && s->n_ctrl > 0)   // controllers of the next step
@@ -441,7 +441,6 @@ int upload_state(Sim *s, const std::vector<int> &ids, const std::vector<int> &la
   c.t_apply = t;
   c.n_active[p] = n;
   c.n_movers = 0;
-  c.tile_ticket = 0;
   CK(cudaMemcpyAsync(s->d_ctrl, &c, sizeof(DevCtrl), cudaMemcpyHostToDevice, st));
   if (s->prm.signal_mode == 1 && s->n_ctrl > 0) {
     // max-pressure controllers: restored, or restarted with phase 0 green; then advanced to
@@ -782,7 +781,6 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
   DALLOC(s->d_res_nl, N);
   DALLOC(s->d_res_pos, N);
   DALLOC(s->d_arr_fill, s->n_lanes);
-  DALLOC(s->d_tile_flag, s->n_tiles);
   DALLOC(s->d_tile_agg, s->n_tiles);
   DALLOC(s->d_qoff, s->n_lanes + 1);
   DALLOC(s->d_qtrip, s->h_qtrip.size());
@@ -818,7 +816,6 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
     std::vector<int> amin(s->n_lanes, AMIN_NONE);
     CK(cudaMemcpy(s->d_amin, amin.data(), sizeof(int) * s->n_lanes, cudaMemcpyHostToDevice));
   }
-  CK(cudaMemset(s->d_tile_flag, 0, sizeof(int) * s->n_tiles));
   CK(cudaMemset(s->d_leave, 0, sizeof(unsigned) * leave_words));
   std::vector<int> tarr(n, -1);
   CK(cudaMemcpy(s->d_tarr, tarr.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
@@ -913,11 +910,10 @@ int ms_step_timed(void *sim, int n, float *ms_per_kernel) {
   return MS_OK;
 }
 
-// Status of the lane scan for ms_step_noalloc: per tile an aggregate (8 bytes) and a flag
-// (4 bytes), for MS_NOALLOC_MAX_TILES tiles.  One copy per device for the whole process;
-// shared by every call (see moss103.h).
+// Lane-scan tile aggregates for ms_step_noalloc (8 bytes per tile, MS_NOALLOC_MAX_TILES
+// tiles).  One copy per device for the whole process; shared by every call (see moss103.h).
 static_assert(LANE_TILE == MS_NOALLOC_TILE_LANES, "scan tile size and the header disagree");
-static __device__ __align__(256) unsigned long long g_noalloc_scan[MS_NOALLOC_MAX_TILES * 3 / 2];
+static __device__ __align__(256) unsigned long long g_noalloc_scan[MS_NOALLOC_MAX_TILES];
 static unsigned long long *g_noalloc_addr[256];   // device address per device ordinal
 
 int ms_step_noalloc(void *sim, int n) {
@@ -939,11 +935,8 @@ int ms_step_noalloc(void *sim, int n) {
   }
   unsigned long long *base = g_noalloc_addr[dev];
   StepArgs a = make_args(s);
-  a.tile_agg = base;
-  a.tile_flag = reinterpret_cast<int *>(base + MS_NOALLOC_MAX_TILES);
+  a.tile_agg = base;   // every step's first lane pass writes each tile before any is read
   cudaStream_t st = s->stream;
-  // the array keeps whatever the last call left: flags must start at zero
-  CK(cudaMemsetAsync(a.tile_flag, 0, sizeof(int) * MS_NOALLOC_MAX_TILES, st));
   for (int k = 0; k < n; ++k) CK(launch_step(s, a, st, nullptr));
   return MS_OK;
 }

@@ -9,10 +9,10 @@
 //             vehicle's result (x', v', new lane and kind: 12 B), a leave bit per vehicle
 //             (warp ballot), per-lane arrival counts and rearmost arrival (fire-and-forget
 //             atomics); per-lane window metrics by the first vehicle of each lane.
-//   k_lanes   (prepare phase for t+1)  single-pass scan over lanes (each tile sums all its
-//             predecessors' aggregates in parallel): new per-lane counts = stayers +
-//             arrivals + departures, new segment starts, arrival bucket starts; departure
-//             FIFOs admit their head; the signal table of step t+1.
+//   k_lanes   (prepare phase for t+1)  a scan over lanes in two launches: pass 0 writes each
+//             tile's aggregate, pass 1 sums its predecessors' and writes the new per-lane
+//             counts = stayers + arrivals + departures, segment starts, arrival bucket
+//             starts; departure FIFOs admit their head; the signal table of step t+1.
 //   k_bucket  place each arrival record into its lane's bucket with its rank among the
 //             lane's stayers.
 //   k_apply   stream every vehicle with its stored result to its sorted slot of the t+1
@@ -40,7 +40,7 @@ constexpr int LANE_THREADS = 256;
 constexpr int LANE_ITEMS = 4;
 constexpr int LANE_TILE = LANE_THREADS * LANE_ITEMS;
 constexpr int LANE_WARPS = LANE_THREADS / 32;
-constexpr int SPIN_LIMIT = 1 << 22;  // bounded wait for a predecessor tile's aggregate
+
 constexpr int AMIN_NONE = 0x7fffffff;
 
 constexpr unsigned DEV_HOP = 1u, DEV_SCAN = 2u, DEV_ORDER = 4u, DEV_BUCKET = 8u;
@@ -114,7 +114,6 @@ struct DevCtrl {
   int t_apply;       // step being applied (set by k_lanes, read by k_bucket / k_apply)
   int n_active[2];   // vehicles in buffer 0 / 1
   int n_movers;      // arrivals of the last step (count only)
-  int tile_ticket;
   unsigned err;
   int movers_last;
   unsigned long long inserted, arrived, sum_tt;
@@ -175,7 +174,6 @@ struct StepArgs {
   int *res_code_nl;    // next-lane choice of arrivals, written by k_decide (sparse)
   int2 *res_pos;       // lane changers: {target segment start, first target index not
                        // behind the changer}, written by k_decide (sparse)
-  int *tile_flag;                  // per lane tile: its aggregate is published
   unsigned long long *tile_agg;    // per lane tile: {new vehicles, arrivals} packed
   const int *q_off, *q_trip;
   int2 *q_hd;          // per lane: {FIFO head entry, its departure step (INT_MAX if empty)}
@@ -967,22 +965,21 @@ __device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long 
   return v;
 }
 
-// Lane pass: new per-lane counts, a single-pass scan over lanes, departures.  A tile of
-// LANE_TILE lanes is processed by LANE_THREADS threads in LANE_ITEMS striped slices (lane
-// k * LANE_THREADS + thread), so every load is coalesced and the loads of all slices are
-// issued before any is used.  Each tile publishes its aggregate as soon as it has it and
-// then sums the aggregates of all its predecessors, one predecessor per thread: no tile
-// waits on another's prefix, so there is no chain through the tiles (with a few hundred
-// tiles, the quadratic number of L2 reads is small).  Tiles are numbered in the order
-// their blocks start, so every predecessor is resident or done.
-__global__ void __launch_bounds__(LANE_THREADS, 4) k_lanes(StepArgs a) {
-  __shared__ int s_tile;
+// Lane pass: new per-lane counts, a scan over lanes, departures.  A tile of LANE_TILE lanes
+// is processed by LANE_THREADS threads in LANE_ITEMS striped slices (lane k * LANE_THREADS
+// + thread), so every load is coalesced and the loads of all slices are issued before any
+// is used.  Two launches: pass 0 computes every tile's aggregate and writes it; pass 1
+// computes the same per-lane counts again (its inputs are read-only here), sums the
+// aggregates of all its predecessors, one per thread (with a few hundred tiles the
+// quadratic number of reads is small), and writes the results.  The launch boundary makes
+// the aggregates visible; a single launch that waited on its predecessors' flags spent
+// several microseconds before those stores became visible to the waiting blocks.
+template <int PASS>
+__global__ void __launch_bounds__(LANE_THREADS, 4) k_lanes_t(StepArgs a) {
   __shared__ unsigned long long s_wsum[LANE_ITEMS][LANE_WARPS];
   __shared__ unsigned long long s_part[LANE_WARPS];
   pdl_enter();
-  if (threadIdx.x == 0) s_tile = atomicAdd(&a.ctrl->tile_ticket, 1);
-  __syncthreads();
-  const int tile = s_tile;
+  const int tile = blockIdx.x;
   const int t = a.ctrl->t;
   const int p = t & 1;
   const Soa D = a.A[p ^ 1];
@@ -1020,9 +1017,10 @@ __global__ void __launch_bounds__(LANE_THREADS, 4) k_lanes(StepArgs a) {
     const int leavers = lv[k];
     ins[k] = 0;
     if (qhd[k].y <= t) {   // (a closed lane's head is parked at INT_MAX by the host)
-      // the head's record is read after the scan: start bringing it in now
-      asm volatile("prefetch.global.L1 [%0];" ::"l"(a.q_ent + qhd[k].x));
-      asm volatile("prefetch.global.L1 [%0];" ::"l"(a.q_ent2 + qhd[k].x));   // the FIFO's head is due: room behind the lane's tail (its
+      if (PASS == 1) {   // the head's record is read after the scan: start bringing it in now
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(a.q_ent + qhd[k].x));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(a.q_ent2 + qhd[k].x));
+      }   // the FIFO's head is due: room behind the lane's tail (its
       int fl = 0;          // position is in the lane record) and behind every arrival
       bool room = true;
       if (d[k].y > 0) {
@@ -1035,7 +1033,7 @@ __global__ void __launch_bounds__(LANE_THREADS, 4) k_lanes(StepArgs a) {
         mark(fl, m);
         if (m < 0.f) room = false;
       }
-      if (a.P.debug) {
+      if (PASS == 1 && a.P.debug) {
         const int l = lbase + k * LANE_THREADS;
         if (fl || a.dbg.arr_flag[l]) a.dbg.trip_flag[a.q_trip[qhd[k].x]] = t + 1;
       }
@@ -1057,23 +1055,12 @@ __global__ void __launch_bounds__(LANE_THREADS, 4) k_lanes(StepArgs a) {
       if (lane < LANE_WARPS) s_wsum[k][lane] = run + wi - wv;
       run += __shfl_sync(0xffffffffu, wi, LANE_WARPS - 1);
     }
-    if (lane == 0) {   // publish this tile's aggregate
-      a.tile_agg[tile] = run;
-      cuda::atomic_ref<int, cuda::thread_scope_device>(a.tile_flag[tile]).store(1, cuda::memory_order_release);
-    }
+    if (PASS == 0 && lane == 0) a.tile_agg[tile] = run;   // read by pass 1
   }
+  if (PASS == 0) return;
   // sum of the predecessors' aggregates
   unsigned long long part = 0;
-  for (int j = threadIdx.x; j < tile; j += LANE_THREADS) {
-    int spins = 0;
-    while (cuda::atomic_ref<int, cuda::thread_scope_device>(a.tile_flag[j]).load(cuda::memory_order_acquire) == 0) {
-      if (++spins > SPIN_LIMIT) {
-        atomicOr(&a.ctrl->err, DEV_SCAN);
-        break;
-      }
-    }
-    part += __ldcg(&a.tile_agg[j]);
-  }
+  for (int j = threadIdx.x; j < tile; j += LANE_THREADS) part += a.tile_agg[j];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
   if (lane == 0) s_part[warp] = part;
@@ -1130,7 +1117,7 @@ __global__ void __launch_bounds__(LANE_THREADS, 4) k_lanes(StepArgs a) {
 
 // Arrivals -> lane buckets with their rank among the lane's stayers.  Arrivals are found
 // by streaming the result codes of the snapshot's vehicles.
-__global__ void k_bucket(StepArgs a, int n_tiles) {
+__global__ void k_bucket(StepArgs a) {
   __shared__ int s_cnt;
   pdl_enter();
   const int t = a.ctrl->t_apply;
@@ -1170,13 +1157,9 @@ __global__ void k_bucket(StepArgs a, int n_tiles) {
     }
   }
   if (mine) atomicAdd(&s_cnt, mine);
-  for (int k = gid; k < n_tiles; k += stride) a.tile_flag[k] = 0;
   __syncthreads();
   if (threadIdx.x == 0 && s_cnt) atomicAdd(&a.ctrl->n_movers, s_cnt);
-  if (gid == 0) {
-    a.ctrl->t = t + 1;
-    a.ctrl->tile_ticket = 0;
-  }
+  if (gid == 0) a.ctrl->t = t + 1;
 }
 
 __device__ __forceinline__ bool bucket_less(int4 f, int4 e) {

@@ -2,8 +2,10 @@
 //
 // Owns the device memory of one simulation, validates and converts the network and the
 // trips into the device layout (sorted structure-of-arrays vehicle state, 32-byte lane
-// records, CSR successor / feeder tables, per-lane departure FIFOs), and replays the four
-// step kernels of step_kernels.cuh as a captured CUDA graph.
+// records, CSR successor / feeder tables, per-route link plans, per-lane departure FIFOs),
+// and replays the step's kernels of step_kernels.cuh (decide, two lane-scan passes, bucket,
+// apply; max-pressure signals when enabled) as captured CUDA graphs with programmatic
+// dependent launch.  Also the route planner and OD sampler of route_kernels.cuh.
 #include <cuda_runtime.h>
 
 #include <algorithm>

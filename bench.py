@@ -93,48 +93,73 @@ def traffic_per_unit(kernel: str, wl: str):
 
 
 class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons around a timed region: sampling
+    starts (and the first sample is waited for) before the region, and continues until a
+    sample after its end, so a region shorter than the sampling period is still bracketed."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 50
 
     def __init__(self, index: int):
         self.index = index
         self.p = None
+        self.rows = []          # (perf_counter time, csv line)
+        self.t0 = self.t1 = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.rows.append((time.perf_counter(), line))
 
     def __enter__(self):
+        import threading
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+            deadline = time.perf_counter() + 10.0
+            while not self.rows and time.perf_counter() < deadline and self.p.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.p = None
+        self.t0 = time.perf_counter()
         return self
 
     def __exit__(self, *a):
-        self.out = ""
+        self.t1 = time.perf_counter()
         if self.p is not None:
+            deadline = self.t1 + 2.0
+            while (not self.rows or self.rows[-1][0] <= self.t1) and time.perf_counter() < deadline \
+                    and self.p.poll() is None:
+                time.sleep(0.01)
             self.p.terminate()
             try:
-                self.out, _ = self.p.communicate(timeout=5)
+                self.p.wait(timeout=5)
             except Exception:
                 self.p.kill()
 
     def summary(self):
+        """Samples from the last one before the region's start to the first one after its end."""
         rows = []
-        for line in (getattr(self, "out", "") or "").splitlines():
+        for ts, line in list(self.rows):
             f = [x.strip() for x in line.split(",")]
             if len(f) < 8:
                 continue
             try:
-                rows.append((float(f[0]), float(f[1]), f[4:8]))
+                rows.append((ts, float(f[0]), float(f[1]), f[4:8]))
             except ValueError:
                 continue
-        if not rows:
+        if not rows or self.t0 is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        lo = max([i for i, r in enumerate(rows) if r[0] <= self.t0] or [0])
+        hi = min([i for i, r in enumerate(rows) if r[0] > self.t1] or [len(rows) - 1])
+        win = rows[lo:hi + 1]
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        reasons = sorted({n for _, _, fl in rows for n, v in zip(names, fl) if v.lower() == "active"})
-        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+        reasons = sorted({n for *_, fl in win for n, v in zip(names, fl) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in win), "sm_max_mhz": max(r[2] for r in win),
+                "reasons": reasons, "samples": len(win), "region_s": round(self.t1 - self.t0, 3),
+                "period_ms": self.PERIOD_MS}
 
 
 def dist_env():
@@ -297,27 +322,33 @@ def run_ours(args):
                 "step_effective_gbs": n_avg * (B_DECIDE_VEH + B_APPLY_VEH) / (avg_ms.sum() * 1e-3) / 1e9}
 
     # end to end through the public API: step + read the per-vehicle state into pinned host
-    # memory every step (Sec. III-A: position and speed of every vehicle each step)
+    # memory every step (Sec. III-A: position and speed of every vehicle each step).  The
+    # export of each step's state runs on a side stream while the next step computes
+    # (ms_read_state_async / ms_read_wait, two pinned buffer sets used in turn).
     e2e_steps = min(args.steps, 50)
     cap = dem.n
-    hx = torch.empty(cap, dtype=torch.float32, pin_memory=True)
-    hv = torch.empty(cap, dtype=torch.float32, pin_memory=True)
-    hl = torch.empty(cap, dtype=torch.int32, pin_memory=True)
-    hi = torch.empty(cap, dtype=torch.int32, pin_memory=True)
+    bufs = [dict(x=torch.empty(cap, dtype=torch.float32, pin_memory=True),
+                 v=torch.empty(cap, dtype=torch.float32, pin_memory=True),
+                 lane=torch.empty(cap, dtype=torch.int32, pin_memory=True),
+                 vid=torch.empty(cap, dtype=torch.int32, pin_memory=True)) for _ in range(2)]
     barrier()
     t0 = time.perf_counter()
     e2e_vs = 0
     d2h = 0
-    for _ in range(e2e_steps):
-        n_before = sim.read_state_host(hx, hv, hl, hi) if _ == 0 else n_after
+    sim.read_state_async(**bufs[0])
+    for k in range(e2e_steps):
         sim.step(1)
-        n_after = sim.read_state_host(hx, hv, hl, hi)
-        e2e_vs += n_before
-        d2h += 16 * n_after
+        sim.read_state_async(**bufs[(k + 1) % 2])   # queued behind the export in flight
+        n_k, _ = sim.read_wait()          # the state step k advanced, now on the host
+        e2e_vs += n_k
+        d2h += 16 * n_k
+    n_k, _ = sim.read_wait()
+    d2h += 16 * n_k
     t1 = time.perf_counter()
     e2e = {"value": e2e_vs / (t1 - t0), "unit": "vehicle-steps/s", "h2d_bytes_per_step": 0,
            "d2h_bytes_per_step": int(d2h / e2e_steps),
-           "what": "ms_step(1) + ms_read_state of x, v, lane, id into pinned host buffers, wall clock"}
+           "what": "ms_step(1) + ms_read_state_async/ms_read_wait of x, v, lane, id into pinned host "
+                   "buffers every step (two exports queued, overlapping the steps), wall clock"}
     sim.sync()
 
     line = {

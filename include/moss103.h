@@ -222,6 +222,26 @@ int ms_sync(void *sim);
    n_active (n_active is still set). */
 int ms_read_state(void *sim, ms_state *out, int device);
 
+/* Asynchronous export of the vehicle state (x, v, lane, id; any may be NULL) into PINNED
+   host buffers (cudaHostAlloc / pinned tensors; else MS_ERR_ARG).  The call waits for the
+   steps enqueued so far (a kernel writes the vehicle count into mapped host memory), then
+   enqueues the copies on a side stream, where they run on the copy engine behind any
+   export still in flight while the following steps compute.  The next ms_step may run
+   while the export is in flight; a launch that would overwrite the exported buffer (the
+   second step after the export) waits for it on the device.  The buffers must stay valid
+   and untouched until the matching ms_read_wait returns.  Up to two exports may be in
+   flight (completed in order, so the host link stays busy while the host consumes the
+   older one); a third call returns MS_ERR_STATE.  ms_write_state and ms_autotune wait for
+   exports in flight.  Only capacity and the four vehicle arrays of out are used;
+   route_idx, trip_status, t_arr and ctrl_state are ignored. */
+int ms_read_state_async(void *sim, const ms_state *out);
+
+/* Wait for the oldest export in flight; n_active and t (either may be NULL) receive the
+   vehicle count and the step of the exported state.  MS_ERR_CAPACITY if the
+   capacity given was below n_active (the first capacity entries are still written);
+   MS_ERR_STATE if no export is in flight. */
+int ms_read_wait(void *sim, int *n_active, int *t);
+
 /* Replace the dynamic state (checkpoint / resume).  Vehicles must be sorted by
    (lane, x, id), one entry per active trip, gaps >= 0; trips neither active nor arrived
    (t_arr < 0) wait for departure.  Metric accumulators are kept. */

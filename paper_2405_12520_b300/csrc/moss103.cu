@@ -39,6 +39,16 @@ struct Sim {
   DevParams P{};
   cudaStream_t stream = nullptr;   // caller's stream
   cudaStream_t cap = nullptr;      // private capture stream
+  // asynchronous state exports (ms_read_state_async): side stream, up to MS_EXPORTS in
+  // flight, completed in order (slot (ex_head + i) % MS_EXPORTS is the i-th oldest)
+  static constexpr int MS_EXPORTS = 2;
+  cudaStream_t xs = nullptr;
+  cudaEvent_t ev_ready = nullptr, ev_export[MS_EXPORTS] = {};
+  int *h_meta = nullptr;           // [MS_EXPORTS][2] {n_active, t} written by k_export
+  long long export_t[MS_EXPORTS] = {};   // step whose state each slot exports
+  int export_cap[MS_EXPORTS] = {};
+  int ex_head = 0, ex_count = 0;
+  long long t_host = 0;            // step the next launch computes (host count)
   int device = 0, n_sm = 0;
   std::string err;
   bool net_loaded = false, veh_loaded = false;
@@ -440,6 +450,7 @@ int upload_state(Sim *s, const std::vector<int> &ids, const std::vector<int> &la
   CK(cudaMemcpyAsync(&c, s->d_ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   c.t = t;
+  s->t_host = t;
   c.t_apply = t;
   c.n_active[p] = n;
   c.n_movers = 0;
@@ -507,6 +518,11 @@ int ms_create(void **out, const ms_params *p, void *cuda_stream) {
   cudaError_t e = cudaGetDevice(&s->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, s->device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->xs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_ready, cudaEventDisableTiming);
+  for (int k = 0; k < Sim::MS_EXPORTS; ++k)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_export[k], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->h_meta, 2 * Sim::MS_EXPORTS * sizeof(int), cudaHostAllocMapped);
   if (e != cudaSuccess) {
     std::fprintf(stderr, "ms_create: %s\n", cudaGetErrorString(e));
     delete s;
@@ -876,6 +892,23 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
   return MS_OK;
 }
 
+// The state at step e sits in buffer e & 1: advancing step e reads it and writes buffer
+// (e + 1) & 1, advancing step e + 1 overwrites it.  An export of the state at step e may
+// overlap the advance of step e; a launch that includes step e + 1 first waits for it.
+static int export_guard(Sim *s, long long n_steps) {
+  for (int i = 0; i < s->ex_count; ++i) {
+    const int k = (s->ex_head + i) % Sim::MS_EXPORTS;
+    if (s->t_host + n_steps > s->export_t[k] + 1) CK(cudaStreamWaitEvent(s->stream, s->ev_export[k], 0));
+  }
+  return MS_OK;
+}
+
+// entry points that overwrite the state buffers from the host wait for an export in flight
+static int export_drain(Sim *s) {
+  if (s->ex_count > 0) CK(cudaStreamSynchronize(s->xs));
+  return MS_OK;
+}
+
 int ms_step(void *sim, int n) {
   Sim *s = (Sim *)sim;
   if (!s) return MS_ERR_ARG;
@@ -883,6 +916,9 @@ int ms_step(void *sim, int n) {
   if (n < 0) return fail(s, MS_ERR_ARG, "n < 0");
   int r = build_graphs(s);
   if (r) return r;
+  r = export_guard(s, n);
+  if (r) return r;
+  s->t_host += n;
   while (n >= GRAPH_STEPS) {
     CK(cudaGraphLaunch(s->g_many, s->stream));
     n -= GRAPH_STEPS;
@@ -895,6 +931,11 @@ int ms_step_timed(void *sim, int n, float *ms_per_kernel) {
   Sim *s = (Sim *)sim;
   if (!s || !ms_per_kernel) return MS_ERR_ARG;
   if (!s->veh_loaded) return fail(s, MS_ERR_STATE, "add vehicles before stepping");
+  {
+    int r = export_guard(s, n);
+    if (r) return r;
+    s->t_host += n;
+  }
   cudaEvent_t ev[5];
   for (auto &e : ev) CK(cudaEventCreate(&e));
   cudaStream_t st = s->stream;
@@ -923,6 +964,11 @@ int ms_step_noalloc(void *sim, int n) {
   if (!s) return MS_ERR_ARG;
   if (!s->veh_loaded) return fail(s, MS_ERR_STATE, "add vehicles before stepping");
   if (n < 0) return fail(s, MS_ERR_ARG, "n < 0");
+  {
+    int r = export_guard(s, n);
+    if (r) return r;
+    s->t_host += n;
+  }
   if (s->n_tiles > MS_NOALLOC_MAX_TILES)
     return fail(s, MS_ERR_CAPACITY, "network has " + std::to_string(s->n_lanes) + " lanes; ms_step_noalloc takes at most " +
                                         std::to_string(MS_NOALLOC_MAX_TILES * LANE_TILE));
@@ -1006,6 +1052,60 @@ int ms_read_state(void *sim, ms_state *out, int device) {
   return MS_OK;
 }
 
+int ms_read_state_async(void *sim, const ms_state *out) {
+  Sim *s = (Sim *)sim;
+  if (!s || !out || out->capacity < 0) return MS_ERR_ARG;
+  if (!s->veh_loaded) return fail(s, MS_ERR_STATE, "no vehicles");
+  void *ptrs[4] = {out->x, out->v, out->lane, out->id};
+  for (void *q : ptrs) {
+    if (!q) continue;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, q) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+      cudaGetLastError();
+      return fail(s, MS_ERR_ARG, "ms_read_state_async needs pinned host buffers (cudaHostAlloc / pinned tensors)");
+    }
+  }
+  if (s->ex_count == Sim::MS_EXPORTS)
+    return fail(s, MS_ERR_STATE, "exports in flight at the limit: call ms_read_wait first");
+  const int k = (s->ex_head + s->ex_count) % Sim::MS_EXPORTS;
+  // the steps enqueued so far are waited for (not the exports in flight); the copies then
+  // run on the copy engine, queued behind any export in flight, while the next steps compute
+  int *meta = s->h_meta + 2 * k;
+  k_export_meta<<<1, 1, 0, s->stream>>>(s->d_ctrl, (int)s->t_host, meta);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(s->ev_ready, s->stream));
+  CK(cudaEventSynchronize(s->ev_ready));
+  const int p = (int)(s->t_host & 1);
+  const size_t m = (size_t)std::min(meta[0], out->capacity);
+  const Soa &S = s->A[p];
+  if (m > 0) {
+    if (out->x) CK(cudaMemcpyAsync(out->x, S.x, m * sizeof(float), cudaMemcpyDeviceToHost, s->xs));
+    if (out->v) CK(cudaMemcpyAsync(out->v, S.v, m * sizeof(float), cudaMemcpyDeviceToHost, s->xs));
+    if (out->lane) CK(cudaMemcpyAsync(out->lane, S.lane, m * sizeof(int), cudaMemcpyDeviceToHost, s->xs));
+    if (out->id) CK(cudaMemcpyAsync(out->id, S.id, m * sizeof(int), cudaMemcpyDeviceToHost, s->xs));
+  }
+  CK(cudaEventRecord(s->ev_export[k], s->xs));
+  s->export_t[k] = s->t_host;
+  s->export_cap[k] = out->capacity;
+  ++s->ex_count;
+  return MS_OK;
+}
+
+int ms_read_wait(void *sim, int *n_active, int *t) {
+  Sim *s = (Sim *)sim;
+  if (!s) return MS_ERR_ARG;
+  if (s->ex_count == 0) return fail(s, MS_ERR_STATE, "no export in flight");
+  const int k = s->ex_head;
+  CK(cudaEventSynchronize(s->ev_export[k]));
+  s->ex_head = (k + 1) % Sim::MS_EXPORTS;
+  --s->ex_count;
+  const int n = s->h_meta[2 * k];
+  if (n_active) *n_active = n;
+  if (t) *t = s->h_meta[2 * k + 1];
+  if (n > s->export_cap[k]) return fail(s, MS_ERR_CAPACITY, "state capacity too small");
+  return MS_OK;
+}
+
 int ms_write_state(void *sim, const ms_state *in) {
   Sim *s = (Sim *)sim;
   if (!s || !in) return MS_ERR_ARG;
@@ -1014,6 +1114,7 @@ int ms_write_state(void *sim, const ms_state *in) {
   if (n < 0 || in->t < 0 || (n > 0 && (!in->id || !in->lane || !in->x || !in->v || !in->route_idx)) || !in->t_arr)
     return fail(s, MS_ERR_ARG, "state arrays missing");
   CK(cudaStreamSynchronize(s->stream));
+  if (int r0 = export_drain(s)) return r0;
   std::vector<int> ids(in->id, in->id + n), lanes(in->lane, in->lane + n), ridx(in->route_idx, in->route_idx + n);
   std::vector<float> xs(in->x, in->x + n), vs(in->v, in->v + n);
   for (int i = 1; i < n; ++i)
@@ -1300,6 +1401,7 @@ int ms_autotune(void *sim, int trial_steps, float *best_ms, int *config) {
   if (!s || trial_steps <= 0) return MS_ERR_ARG;
   if (!s->veh_loaded) return fail(s, MS_ERR_STATE, "add vehicles first");
   CK(cudaStreamSynchronize(s->stream));
+  if (int r0 = export_drain(s)) return r0;
   Snapshot sn;
   int r = snap_take(s, sn);
   if (r) { snap_free(sn); return r; }
@@ -1778,9 +1880,15 @@ void ms_destroy(void *sim) {
   Sim *s = (Sim *)sim;
   if (!s) return;
   if (s->veh_loaded || s->net_loaded) cudaStreamSynchronize(s->stream);
+  if (s->xs) cudaStreamSynchronize(s->xs);
   drop_graphs(s);
   for (void *p : s->allocs) cudaFree(p);
   if (s->cap) cudaStreamDestroy(s->cap);
+  if (s->xs) cudaStreamDestroy(s->xs);
+  if (s->ev_ready) cudaEventDestroy(s->ev_ready);
+  for (cudaEvent_t ev : s->ev_export)
+    if (ev) cudaEventDestroy(ev);
+  if (s->h_meta) cudaFreeHost(s->h_meta);
   delete s;
 }
 

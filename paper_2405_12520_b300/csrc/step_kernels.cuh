@@ -1335,6 +1335,14 @@ __global__ void k_signals(StepArgs a) {
   }
 }
 
+// Vehicle count and step of the state at step t, written into mapped host memory: the host
+// learns how many entries to copy without a device-to-host copy that would queue behind
+// an export in flight on the copy engine.  Step t + 1 does not write n_active[t & 1].
+__global__ void k_export_meta(const DevCtrl *ctrl, int t, int *meta) {
+  meta[0] = ctrl->n_active[t & 1];
+  meta[1] = t;
+}
+
 __global__ void k_route_idx(const int *rp, const int *id, const int *route0, int *out, const int *n_ptr,
                             int n_fixed) {
   int n = n_ptr ? *n_ptr : n_fixed;

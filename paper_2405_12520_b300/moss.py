@@ -23,7 +23,7 @@ SYMBOLS = ("ms_create", "ms_load_network", "ms_add_vehicles", "ms_step", "ms_ste
            "ms_mlp_train_step",
            "ms_mlp_grad",
            "ms_mlp_predict",
-           "ms_sync", "ms_read_state",
+           "ms_sync", "ms_read_state", "ms_read_state_async", "ms_read_wait",
            "ms_write_state", "ms_read_metrics", "ms_read_debug", "ms_last_error", "ms_destroy")
 
 
@@ -101,6 +101,8 @@ def load():
         lib.ms_mlp_predict.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
         lib.ms_sync.argtypes = [vp]
         lib.ms_read_state.argtypes = [vp, C.POINTER(ms_state), C.c_int]
+        lib.ms_read_state_async.argtypes = [vp, C.POINTER(ms_state)]
+        lib.ms_read_wait.argtypes = [vp, vp, vp]
         lib.ms_write_state.argtypes = [vp, C.POINTER(ms_state)]
         lib.ms_read_metrics.argtypes = [vp, C.POINTER(ms_metrics)]
         lib.ms_read_debug.argtypes = [vp, C.POINTER(ms_debug)]
@@ -290,6 +292,21 @@ class Sim:
         s = ms_state(int(x.numel()), 0, 0, ptr(vid), ptr(lane), None, ptr(x), ptr(v), None, None)
         self._check(self.lib.ms_read_state(self.h, C.byref(s), 0), "ms_read_state")
         return s.n_active
+
+    def read_state_async(self, x, v, lane, vid):
+        """Start an export of the vehicle state into pinned torch CPU tensors (any may be
+        None) without synchronising; finish it with read_wait.  The tensors must stay alive
+        and untouched until then."""
+        ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+        cap = next(int(t.numel()) for t in (x, v, lane, vid) if t is not None)
+        s = ms_state(cap, 0, 0, ptr(vid), ptr(lane), None, ptr(x), ptr(v), None, None)
+        self._check(self.lib.ms_read_state_async(self.h, C.byref(s)), "ms_read_state_async")
+
+    def read_wait(self) -> tuple:
+        """Wait for the export started by read_state_async; returns (n_active, t)."""
+        n, t = C.c_int(0), C.c_int(0)
+        self._check(self.lib.ms_read_wait(self.h, C.byref(n), C.byref(t)), "ms_read_wait")
+        return n.value, t.value
 
     def sync(self):
         self._check(self.lib.ms_sync(self.h), "ms_sync")

@@ -409,3 +409,78 @@ def test_device_state_readout_into_torch():
     np.testing.assert_array_equal(x[:n].cpu().numpy(), st["x"])
     np.testing.assert_array_equal(vid[:n].cpu().numpy(), st["id"])
     np.testing.assert_array_equal(ri[:n].cpu().numpy(), st["route_idx"])
+
+
+def test_async_state_export_overlaps_steps():
+    """ms_read_state_async / ms_read_wait: the exported state equals the synchronous read of
+    a twin simulation at the same step, with the export left in flight across one step (the
+    overlapped pattern) and across several (the overwrite guard makes the steps wait)."""
+    _need_gpu()
+    import torch
+    from paper_2405_12520_b300 import moss
+    net, dem = synth.small_grid_workload(1)
+    sims = []
+    for _ in range(2):
+        s = moss.Sim(P)
+        s.load_network(net)
+        s.add_vehicles(dem)
+        sims.append(s)
+    a, b = sims
+    cap = dem.n
+    bufs = [dict(x=torch.empty(cap, pin_memory=True), v=torch.empty(cap, pin_memory=True),
+                 lane=torch.empty(cap, dtype=torch.int32, pin_memory=True),
+                 vid=torch.empty(cap, dtype=torch.int32, pin_memory=True)) for _ in range(2)]
+
+    def check(buf, n, t):
+        st = b.read_state(trips=False)
+        assert (n, t) == (st["n_active"], st["t"])
+        np.testing.assert_array_equal(buf["x"][:n].numpy(), st["x"])
+        np.testing.assert_array_equal(buf["v"][:n].numpy(), st["v"])
+        np.testing.assert_array_equal(buf["lane"][:n].numpy(), st["lane"])
+        np.testing.assert_array_equal(buf["vid"][:n].numpy(), st["id"])
+
+    a.step(30)
+    b.step(30)
+    a.read_state_async(**bufs[0])
+    for k in range(1, 40):                # export k-1 overlaps step k; step k+1 waits for it
+        a.step(1)
+        n, t = a.read_wait()
+        check(bufs[(k - 1) % 2], n, t)
+        b.step(1)
+        a.read_state_async(**bufs[k % 2])
+    n, t = a.read_wait()
+    check(bufs[1], n, t)
+    a.read_state_async(**bufs[0])         # two in flight: the second queues behind the first
+    for k in range(1, 20):
+        a.step(1)
+        a.read_state_async(**bufs[k % 2])
+        n, t = a.read_wait()              # the older one
+        check(bufs[(k - 1) % 2], n, t)
+        b.step(1)
+    n, t = a.read_wait()
+    check(bufs[1], n, t)
+    a.read_state_async(**bufs[0])
+    a.read_state_async(**bufs[1])
+    with pytest.raises(moss.MossError) as e:
+        a.read_state_async(**bufs[1])
+    assert e.value.code == moss.MS_ERR_STATE
+    check(bufs[0], *a.read_wait())
+    check(bufs[1], *a.read_wait())
+    a.read_state_async(**bufs[0])
+    a.step(7)                             # steps past the exported buffer wait for the export
+    n, t = a.read_wait()
+    check(bufs[0], n, t)
+    b.step(7)
+    assert a.read_state(trips=False)["t"] == b.read_state(trips=False)["t"]
+    with pytest.raises(moss.MossError) as e:
+        a.read_wait()
+    assert e.value.code == moss.MS_ERR_STATE
+    small = {k: t[:5] for k, t in bufs[1].items()}
+    a.read_state_async(**small)
+    with pytest.raises(moss.MossError) as e:
+        a.read_wait()
+    assert e.value.code == moss.MS_ERR_CAPACITY
+    np.testing.assert_array_equal(small["x"].numpy(), b.read_state(trips=False)["x"][:5])
+    with pytest.raises(moss.MossError) as e:
+        a.read_state_async(torch.empty(cap), None, None, None)
+    assert e.value.code == moss.MS_ERR_ARG

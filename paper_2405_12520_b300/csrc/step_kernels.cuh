@@ -1171,7 +1171,10 @@ __device__ __forceinline__ bool bucket_less(int4 f, int4 e) {
 
 // Write each vehicle, with the result k_decide computed for it, to its sorted slot of the
 // t+1 buffer: stayers by their rank among the lane's stayers plus the arrivals ranked
-// before them, arrivals by their bucket rank.
+// before them, arrivals by their bucket rank.  A warp takes 32 consecutive vehicles and
+// issues every load indexed by the vehicle at once; a stayer's rank among its lane's
+// stayers comes from the warp's leave word (same-lane threads by a match), and only the
+// lane that continues from the previous warp reads its lane record and earlier words.
 __global__ void k_apply(StepArgs a) {
   pdl_enter();
   const int t = a.ctrl->t_apply;
@@ -1181,31 +1184,72 @@ __global__ void k_apply(StepArgs a) {
   const int4 *dyn = a.dyn[p];
   int4 *ndyn = a.dyn[p ^ 1];
   const int n = a.ctrl->n_active[p];
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
-  if (gid == 0) {
+  const int wl = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.ctrl->movers_last = a.ctrl->n_movers;
     a.ctrl->n_movers = 0;
   }
-  for (int i = gid; i < n; i += stride) {
-    const int code = a.res_code[i];
+  for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int ws = base + (threadIdx.x & ~31);   // this warp's first vehicle
+    if (ws >= n) break;                          // warp-uniform
+    const int i = ws + wl;
+    const bool act = i < n;
+    int code = C_RETIRE << CODE_LANE_BITS, id = 0, lane = -1 - wl, rp = 0, nlc = 0;
+    unsigned long long pl = 0;
+    float v0 = 0.f, xn = 0.f, vn = 0.f;
+    if (act) {
+      code = a.res_code[i];
+      id = S.id[i];
+      lane = S.lane[i];
+      rp = S.rp[i];
+      nlc = S.nl[i];
+      pl = S.pl[i];
+      v0 = S.v0[i];
+      xn = a.res_x[i];
+      vn = a.res_v[i];
+    }
+    const unsigned lw = a.leave[ws >> 5];
+    int prev = -1;
+    if (wl == 0 && ws > 0) prev = S.lane[ws - 1];
+    prev = __shfl_sync(full, prev, 0);
     const int kind = (unsigned)code >> CODE_LANE_BITS;
     const int nl = code & CODE_LANE_MASK;
-    const int id = S.id[i];
-    if (kind == C_RETIRE) {
-      a.t_arr[id] = t + 1;
-      atomicAdd(&a.ctrl->arrived, 1ull);
-      atomicAdd(&a.ctrl->sum_tt, (unsigned long long)(t + 1 - a.trip_tdep[id]));
-      continue;
+    const unsigned same = __match_any_sync(full, lane);
+    // retirements: arrival step per trip, counters summed per warp
+    const bool ret = act && kind == C_RETIRE;
+    const unsigned rm = __ballot_sync(full, ret);
+    if (rm) {
+      const unsigned tt = ret ? (unsigned)(t + 1 - a.trip_tdep[id]) : 0u;
+      const unsigned tsum = __reduce_add_sync(full, tt);
+      if (ret) a.t_arr[id] = t + 1;
+      if (wl == 0) {
+        atomicAdd(&a.ctrl->arrived, (unsigned long long)__popc(rm));
+        atomicAdd(&a.ctrl->sum_tt, (unsigned long long)tsum);
+      }
     }
+    if (!act || kind == C_RETIRE) continue;
     const int bs = a.arr_start[nl], be = a.arr_start[nl + 1];
+    const int nfirst = ndyn[nl].x;
+    if (kind == C_TRANSFER_ROUTE) {   // internal lane -> edge lane: next route edge; the
+      rp += 1;                        // cached choice was made for this target lane
+      pl = a.plan[rp];
+    } else if (kind != C_STAY) {      // lane change or edge lane -> internal lane
+      nlc = a.res_code_nl[i];
+    }
     int pos;
     if (kind == C_STAY) {
-      int4 d = dyn[nl];
-      int k = (i - d.x) - count_bits(a.leave, d.x, i);
+      // rank among the lane's stayers: same-lane stayers earlier in this warp, plus those
+      // before the warp when the lane continues from the previous one
+      int k = __popc(~lw & same & ((1u << wl) - 1u));
+      if (prev == lane) {
+        const int dx = dyn[lane].x;
+        k += (ws - dx) - count_bits(a.leave, dx, ws);
+      }
       int m = 0;
       for (int q = bs; q < be; ++q) m += a.bucket[q].x <= k;
-      pos = ndyn[nl].x + k + m;
+      pos = nfirst + k + m;
     } else {
       int4 me = make_int4(0, 0, 0, -2);
       for (int q = bs; q < be; ++q) {
@@ -1218,23 +1262,14 @@ __global__ void k_apply(StepArgs a) {
       }
       int rank = 0;
       for (int q = bs; q < be; ++q) rank += bucket_less(a.bucket[q], me);
-      pos = ndyn[nl].x + me.x + rank;
+      pos = nfirst + me.x + rank;
+      a.arr_fill[nl] = 0;   // every arrival resets it; k_bucket is done
     }
-    int rp = S.rp[i], nlc = S.nl[i];
-    unsigned long long pl = S.pl[i];
-    if (kind != C_STAY) a.arr_fill[nl] = 0;   // every arrival resets it; k_bucket is done
-    if (kind == C_TRANSFER_ROUTE) {   // internal lane -> edge lane: next route edge; the
-      rp += 1;                        // cached choice was made for this target lane
-      pl = a.plan[rp];
-    } else if (kind != C_STAY) {      // lane change or edge lane -> internal lane
-      nlc = a.res_code_nl[i];
-    }
-    const float xn = a.res_x[i], vn = a.res_v[i];
-    if (pos == ndyn[nl].x)   // rearmost vehicle of its lane: the lane record's tail fields
+    if (pos == nfirst)   // rearmost vehicle of its lane: the lane record's tail fields
       reinterpret_cast<int2 *>(&ndyn[nl])[1] = make_int2(__float_as_int(xn), __float_as_int(vn));
     D.x[pos] = xn;
     D.v[pos] = vn;
-    D.v0[pos] = S.v0[i];
+    D.v0[pos] = v0;
     D.lane[pos] = nl;
     D.rp[pos] = rp;
     D.pl[pos] = pl;

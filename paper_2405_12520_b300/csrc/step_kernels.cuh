@@ -1116,9 +1116,12 @@ __global__ void __launch_bounds__(LANE_THREADS, 4) k_lanes_t(StepArgs a) {
 }
 
 // Arrivals -> lane buckets with their rank among the lane's stayers.  Arrivals are found
-// by streaming the result codes of the snapshot's vehicles.
+// by streaming the result codes of the snapshot's vehicles; each arrival issues its loads
+// and its slot atomic together, so an arrival costs two dependent round trips (three for
+// a lane change, whose rank needs the leave words).
 __global__ void k_bucket(StepArgs a) {
   __shared__ int s_cnt;
+  if (threadIdx.x == 0) s_cnt = 0;
   pdl_enter();
   const int t = a.ctrl->t_apply;
   const int p = t & 1;
@@ -1126,8 +1129,6 @@ __global__ void k_bucket(StepArgs a) {
   const int n = a.ctrl->n_active[p];
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
-  if (threadIdx.x == 0) s_cnt = 0;
-  __syncthreads();
   int mine = 0;
   // four result codes per thread and load (the code buffer is padded to a multiple of 4)
   const int ng = (n + 3) >> 2;
@@ -1142,21 +1143,24 @@ __global__ void k_bucket(StepArgs a) {
       const int kind = (unsigned)code >> CODE_LANE_BITS;
       if (kind != C_CHANGE && kind != C_TRANSFER && kind != C_TRANSFER_ROUTE) continue;
       const int nl = code & CODE_LANE_MASK;
-      int r = 0;
-      if (kind == C_CHANGE) {   // rank among the target lane's stayers (k_decide found the slot)
-        const int2 fp = a.res_pos[i];
-        r = (fp.y - fp.x) - count_bits(a.leave, fp.x, fp.y);
-      }
-      const int slot = a.arr_start[nl] + atomicAdd(&a.arr_fill[nl], 1);
-      if (slot >= a.arr_start[nl + 1]) {   // never expected: more arrivals than counted
+      const int2 fp = kind == C_CHANGE ? a.res_pos[i] : make_int2(0, 0);
+      const int xb = __float_as_int(a.res_x[i]);
+      const int id = S.id[i];
+      const int s0 = a.arr_start[nl], s1 = a.arr_start[nl + 1];
+      const int slot = s0 + atomicAdd(&a.arr_fill[nl], 1);
+      // rank among the target lane's stayers (k_decide found the segment); 0 for transfers
+      const int r = (fp.y - fp.x) - count_bits(a.leave, fp.x, fp.y);
+      if (slot >= s1) {   // never expected: more arrivals than counted
         atomicOr(&a.ctrl->err, DEV_BUCKET);
         continue;
       }
-      a.bucket[slot] = make_int4(r, __float_as_int(a.res_x[i]), S.id[i], i);
+      a.bucket[slot] = make_int4(r, xb, id, i);
       ++mine;
     }
   }
-  if (mine) atomicAdd(&s_cnt, mine);
+  __syncthreads();   // s_cnt is set
+  mine = __reduce_add_sync(0xffffffffu, mine);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&s_cnt, mine);
   __syncthreads();
   if (threadIdx.x == 0 && s_cnt) atomicAdd(&a.ctrl->n_movers, s_cnt);
   if (gid == 0) a.ctrl->t = t + 1;

@@ -989,6 +989,10 @@ __global__ void __launch_bounds__(LANE_THREADS, 4) k_lanes_t(StepArgs a) {
   const float room_need = a.P.L + a.P.s0;
   const int lbase = tile * LANE_TILE + threadIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // pass 1: the predecessors' aggregates are loaded first, with the lane records
+  unsigned long long part = 0;
+  if (PASS == 1)
+    for (int j = threadIdx.x; j < tile; j += LANE_THREADS) part += a.tile_agg[j];
 
   int4 d[LANE_ITEMS];
   int arr[LANE_ITEMS], lv[LANE_ITEMS], amk[LANE_ITEMS];
@@ -1057,62 +1061,63 @@ __global__ void __launch_bounds__(LANE_THREADS, 4) k_lanes_t(StepArgs a) {
     }
     if (PASS == 0 && lane == 0) a.tile_agg[tile] = run;   // read by pass 1
   }
-  if (PASS == 0) return;
-  // sum of the predecessors' aggregates
-  unsigned long long part = 0;
-  for (int j = threadIdx.x; j < tile; j += LANE_THREADS) part += a.tile_agg[j];
+  if constexpr (PASS == 0) {
+    return;
+  } else {
+    // sum of the predecessors' aggregates
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  if (lane == 0) s_part[warp] = part;
-  __syncthreads();
-  unsigned long long tile_excl = 0;
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) s_part[warp] = part;
+    __syncthreads();
+    unsigned long long tile_excl = 0;
 #pragma unroll
-  for (int w = 0; w < LANE_WARPS; ++w) tile_excl += s_part[w];
+    for (int w = 0; w < LANE_WARPS; ++w) tile_excl += s_part[w];
 
-  int n_ins = 0;
+    int n_ins = 0;
 #pragma unroll
-  for (int k = 0; k < LANE_ITEMS; ++k) {
-    const int l = lbase + k * LANE_THREADS;
-    if (l >= nlanes) break;
-    const unsigned long long pre = tile_excl + s_wsum[k][warp] + (incl[k] - val[k]);
-    const int nstart = (int)(pre >> 32);
-    const int astart = (int)(pre & 0xffffffffu);
-    // tail fields: the departing vehicle if one enters, else set by k_apply
-    ndyn[l] = make_int4(nstart, cnt[k], ins[k] ? __float_as_int(a.P.L) : 0, 0);
-    a.arr_start[l] = astart;
-    if (ins[k]) {   // the entry's record was built at load time
-      const int4 e = a.q_ent[qhd[k].x];
-      const int4 e2 = a.q_ent2[qhd[k].x];
-      a.q_hd[l] = make_int2(qhd[k].x + 1, e2.z);
-      D.x[nstart] = a.P.L;
-      D.v[nstart] = 0.f;
-      D.v0[nstart] = __int_as_float(e.w);
-      D.lane[nstart] = l;
-      D.rp[nstart] = e.y;
-      D.pl[nstart] = (unsigned long long)(unsigned)e2.x | ((unsigned long long)(unsigned)e2.y << 32);
-      D.nl[nstart] = e.z;
-      D.id[nstart] = e.x;
-      a.bucket[astart + arr[k]] = make_int4(0, __float_as_int(a.P.L), e.x, -1);
-      ++n_ins;
-      if (a.P.debug) a.dbg.trip_ins[e.x] = t + 1;
+    for (int k = 0; k < LANE_ITEMS; ++k) {
+      const int l = lbase + k * LANE_THREADS;
+      if (l >= nlanes) break;
+      const unsigned long long pre = tile_excl + s_wsum[k][warp] + (incl[k] - val[k]);
+      const int nstart = (int)(pre >> 32);
+      const int astart = (int)(pre & 0xffffffffu);
+      // tail fields: the departing vehicle if one enters, else set by k_apply
+      ndyn[l] = make_int4(nstart, cnt[k], ins[k] ? __float_as_int(a.P.L) : 0, 0);
+      a.arr_start[l] = astart;
+      if (ins[k]) {   // the entry's record was built at load time
+        const int4 e = a.q_ent[qhd[k].x];
+        const int4 e2 = a.q_ent2[qhd[k].x];
+        a.q_hd[l] = make_int2(qhd[k].x + 1, e2.z);
+        D.x[nstart] = a.P.L;
+        D.v[nstart] = 0.f;
+        D.v0[nstart] = __int_as_float(e.w);
+        D.lane[nstart] = l;
+        D.rp[nstart] = e.y;
+        D.pl[nstart] = (unsigned long long)(unsigned)e2.x | ((unsigned long long)(unsigned)e2.y << 32);
+        D.nl[nstart] = e.z;
+        D.id[nstart] = e.x;
+        a.bucket[astart + arr[k]] = make_int4(0, __float_as_int(a.P.L), e.x, -1);
+        ++n_ins;
+        if (a.P.debug) a.dbg.trip_ins[e.x] = t + 1;
+      }
+      if (arr[k] | lv[k]) a.arr_cnt[l] = 0;
+      if (amk[k] != AMIN_NONE) a.amin[l] = AMIN_NONE;
+      if (a.P.debug) a.dbg.arr_flag[l] = 0;
+      if (l == nlanes - 1) {
+        const unsigned long long tot = pre + val[k];
+        a.ctrl->n_active[p ^ 1] = (int)(tot >> 32);
+        a.arr_start[nlanes] = (int)(tot & 0xffffffffu);
+        a.ctrl->t_apply = t;
+      }
     }
-    if (arr[k] | lv[k]) a.arr_cnt[l] = 0;
-    if (amk[k] != AMIN_NONE) a.amin[l] = AMIN_NONE;
-    if (a.P.debug) a.dbg.arr_flag[l] = 0;
-    if (l == nlanes - 1) {
-      const unsigned long long tot = pre + val[k];
-      a.ctrl->n_active[p ^ 1] = (int)(tot >> 32);
-      a.arr_start[nlanes] = (int)(tot & 0xffffffffu);
-      a.ctrl->t_apply = t;
-    }
+    // signal table of step t + 1 (the next k_decide reads it); max-pressure controllers
+    // are advanced by k_signals instead
+    if (a.P.signal_mode == 0)
+      for (int c = tile * LANE_THREADS + threadIdx.x; c < a.n_ctrl; c += gridDim.x * LANE_THREADS)
+        a.sig[(t + 1) & 1][c] = sig_pack(a.ctrl4[c], t + 1);
+    n_ins = __reduce_add_sync(0xffffffffu, n_ins);
+    if (lane == 0 && n_ins) atomicAdd(&a.ctrl->inserted, (unsigned long long)n_ins);
   }
-  // signal table of step t + 1 (the next k_decide reads it); max-pressure controllers
-  // are advanced by k_signals instead
-  if (a.P.signal_mode == 0)
-    for (int c = tile * LANE_THREADS + threadIdx.x; c < a.n_ctrl; c += gridDim.x * LANE_THREADS)
-      a.sig[(t + 1) & 1][c] = sig_pack(a.ctrl4[c], t + 1);
-  n_ins = __reduce_add_sync(0xffffffffu, n_ins);
-  if (lane == 0 && n_ins) atomicAdd(&a.ctrl->inserted, (unsigned long long)n_ins);
 }
 
 // Arrivals -> lane buckets with their rank among the lane's stayers.  Arrivals are found

@@ -53,9 +53,11 @@ def workload(name: str, seed: int):
                 "(Poisson), v0~N(13.9,1.5)")
     elif name == "city5m":
         net = synth.delaunay_network(20000, box=30000.0, seed=seed)
-        dem = synth.place_vehicles(net, 5_000_000, seed=seed, min_spacing=7.0, dest="uniform")
+        dem = synth.place_vehicles(net, 5_000_000, seed=seed, min_spacing=7.0, dest="pareto")
         desc = ("irregular city: Delaunay of 20k points in 30x30 km, 1-4 lanes by length quartile, "
-                "signals at degree>=3; 5,000,000 vehicles pre-placed (steady state), 256 zones")
+                "signals at degree>=3; 5,000,000 vehicles pre-placed (steady state), heavy-tailed trip "
+                "lengths: destination = the one of 256 zones whose shortest-path distance is closest to "
+                "a Pareto(1.5, 1 km) draw truncated at 40 km")
     else:
         raise SystemExit(f"unknown workload {name}")
     return net, dem, desc

@@ -566,7 +566,45 @@ def _gather_csr(parts, which, idx_in_part, n):
     return noff, allr[pos].astype(np.int32)
 
 
-def _route_many(net, rng, se, snode, dest, A, zs, pred, max_tries=50):
+PARETO_ALPHA, PARETO_XM, PARETO_XMAX = 1.5, 1000.0, 40000.0
+
+
+class _ZoneLengths:
+    """Trip-length destinations over zone nodes: per node, the zones' shortest-path
+    distances sorted ascending (unreachable ones last), as one flat sorted key array."""
+    ROW = 1e9   # row offset of a node's keys (route lengths stay far below 1e8 m)
+
+    def __init__(self, zdist: np.ndarray):
+        Z, V = zdist.shape
+        d = np.where(np.isfinite(zdist), zdist, 1e8).T          # [V, Z]
+        self.order = np.argsort(d, axis=1, kind="stable")
+        ds = np.take_along_axis(d, self.order, axis=1)
+        self.keys = (ds + np.arange(V, dtype=np.float64)[:, None] * self.ROW).ravel()
+        self.ds = ds
+        self.Z = Z
+
+    def pick(self, node: np.ndarray, ell: np.ndarray) -> np.ndarray:
+        """Zone whose distance from node is closest to ell (reachable zones only)."""
+        Z = self.Z
+        lo = node * Z
+        k = np.searchsorted(self.keys, ell + node * self.ROW)
+        k = np.clip(k, lo + 1, lo + Z - 1)
+        a, b = k - 1, k
+        da = np.abs(self.keys[a] - node * self.ROW - ell)
+        db = np.abs(self.keys[b] - node * self.ROW - ell)
+        fin_b = self.ds.ravel()[b] < 1e8
+        j = np.where(fin_b & (db < da), b, a)
+        return self.order.ravel()[j]
+
+
+def _pareto_lengths(rng, n: int) -> np.ndarray:
+    """Trip lengths ~ Pareto(alpha 1.5, x_m 1 km) truncated at 40 km (inverse CDF)."""
+    u = rng.random(n)
+    c = 1.0 - (PARETO_XM / PARETO_XMAX) ** PARETO_ALPHA
+    return PARETO_XM * (1.0 - u * c) ** (-1.0 / PARETO_ALPHA)
+
+
+def _route_many(net, rng, se, snode, dest, A, zs, pred, max_tries=50, zlen=None):
     """Route vehicles starting on edge se (head node snode); redraw destinations whose
     route would begin with a U-turn.  Returns CSR (off, edges)."""
     n = se.shape[0]
@@ -585,6 +623,9 @@ def _route_many(net, rng, se, snode, dest, A, zs, pred, max_tries=50):
         elif net.grid_shape is not None:
             d = rng.integers(0, V, size=pending.shape[0])
             off, e, ok = _grid_routes(net, se[pending], snode[pending], d)
+        elif dest == "pareto":
+            d = zlen.pick(snode[pending], _pareto_lengths(rng, pending.shape[0]))
+            off, e, ok = _tree_routes(net, se[pending], snode[pending], d, zs, pred)
         else:
             d = rng.integers(0, zs.shape[0], size=pending.shape[0])
             off, e, ok = _tree_routes(net, se[pending], snode[pending], d, zs, pred)
@@ -609,7 +650,9 @@ def place_vehicles(net: Network, n: int, seed: int = 3, min_spacing: float = 9.0
 
     Vehicles are spread over edges in proportion to lane length (and, if internal_frac > 0,
     also over junction-internal lanes with that relative weight), routed from the edge
-    they are on (gravity destinations on grids, else uniform over `zones` zone nodes),
+    they are on (gravity destinations on grids, else uniform over `zones` zone nodes, or
+    with dest="pareto" the zone whose shortest-path distance from the edge's head node is
+    closest to a trip length drawn from Pareto(1.5, 1 km) truncated at 40 km),
     then put on a lane of their edge that serves their next route edge; consecutive fronts
     on a lane are at least min_spacing apart; speed uniform in [0, v0];
     v0 ~ N(v0_mean, v0_sd) clipped to [8, 20]."""
@@ -621,11 +664,13 @@ def place_vehicles(net: Network, n: int, seed: int = 3, min_spacing: float = 9.0
     lane_cap = np.floor((net.lane_len.astype(np.float64) - veh_len) / min_spacing).astype(np.int64) + 1
     use_gravity = net.grid_shape is not None and dest == "gravity"
     A = rng.lognormal(0.0, 1.0, size=V) if use_gravity else None
-    zs = pred = None
+    zs = pred = zlen = None
     if not use_gravity and net.grid_shape is None:
         zs = np.unique(rng.integers(0, V, size=zones))
-        _, pred = _zone_trees(net, zs)
-    gdest = "gravity" if use_gravity else "uniform"
+        zd, pred = _zone_trees(net, zs)
+        if dest == "pareto":
+            zlen = _ZoneLengths(zd)
+    gdest = "gravity" if use_gravity else ("pareto" if zlen is not None else "uniform")
     # internal lanes: (approach edge, exit edge, target lane)
     int_src = np.full(L, -1, np.int64)
     int_dst = np.full(L, -1, np.int64)
@@ -662,7 +707,7 @@ def place_vehicles(net: Network, n: int, seed: int = 3, min_spacing: float = 9.0
         w = w_edge * (e_room > 0)
         se = rng.choice(E, size=pending, p=w / w.sum())
         snode = net.edge_to[se].astype(np.int64)
-        off, edges = _route_many(net, rng, se, snode, gdest, A, zs, pred)
+        off, edges = _route_many(net, rng, se, snode, gdest, A, zs, pred, zlen=zlen)
         nxt = np.where(off[1:] - off[:-1] >= 2, edges[np.minimum(off[:-1] + 1, max(edges.shape[0] - 1, 0))], -1)
         kmax = int(net.edge_nlanes.max())
         ok_mask = np.zeros((pending, kmax), bool)
@@ -700,7 +745,7 @@ def place_vehicles(net: Network, n: int, seed: int = 3, min_spacing: float = 9.0
         m = lane_i.shape[0]
         se_i = int_dst[lane_i]
         sn_i = net.edge_to[se_i].astype(np.int64)
-        off_i, edges_i = _route_many(net, rng, se_i, sn_i, gdest, A, zs, pred)
+        off_i, edges_i = _route_many(net, rng, se_i, sn_i, gdest, A, zs, pred, zlen=zlen)
         # keep those whose target lane serves the route's next edge, else end at the exit edge
         nx_i = np.where(off_i[1:] - off_i[:-1] >= 2, edges_i[np.minimum(off_i[:-1] + 1, max(edges_i.shape[0] - 1, 0))], -1)
         key = int_tgt[lane_i] * E + np.maximum(nx_i, 0)

@@ -70,3 +70,27 @@ def test_union_offsets():
     _check_net(net)
     _check_routes(net, dem)
     assert net.n_lanes == sum(n.n_lanes for n, _ in sc) and dem.n == sum(d.n for _, d in sc)
+
+
+def test_pareto_trip_lengths():
+    """Truncated Pareto(1.5, 1 km, 40 km) draws follow their CDF, and placed vehicles routed
+    to the zone closest to a draw get heavy-tailed route lengths near the draws'."""
+    rng = np.random.default_rng(5)
+    ell = synth._pareto_lengths(rng, 200_000)
+    assert ell.min() >= synth.PARETO_XM and ell.max() <= synth.PARETO_XMAX
+    a, xm, xmax = synth.PARETO_ALPHA, synth.PARETO_XM, synth.PARETO_XMAX
+    for q in (1500.0, 3000.0, 10000.0):   # truncated CDF at q vs the empirical fraction
+        cdf = (1 - (xm / q) ** a) / (1 - (xm / xmax) ** a)
+        assert abs(np.mean(ell <= q) - cdf) < 0.005
+    net = synth.delaunay_network(1500, box=12000.0, seed=4)
+    dem = synth.place_vehicles(net, 4000, seed=2, min_spacing=7.0, dest="pareto")
+    _check_routes(net, dem)
+    lens = np.array([net.edge_len[dem.route_edges[dem.route_off[i] + 1:dem.route_off[i + 1]]].sum()
+                     for i in range(dem.n)])
+    med = np.median(lens)
+    assert 0.6 * xm * 2 ** (1 / a) < med < 1.6 * xm * 2 ** (1 / a)   # Pareto median 1.59 km
+    assert 0.01 < np.mean(lens > 6000.0) < 0.15                      # the tail is there
+    uni = synth.place_vehicles(net, 4000, seed=2, min_spacing=7.0, dest="uniform")
+    ulens = np.array([net.edge_len[uni.route_edges[uni.route_off[i] + 1:uni.route_off[i + 1]]].sum()
+                      for i in range(uni.n)])
+    assert np.median(ulens) > 2 * med                                # uniform zones: long trips

@@ -734,10 +734,21 @@ __device__ __forceinline__ int count_bits(const unsigned *b, int s, int e) {
 // kernels
 // ------------------------------------------------------------------------------------
 
+// sum of v[from, to) by the whole warp (coalesced loads, then a butterfly); called by all
+// 32 threads
+__device__ __noinline__ float warp_range_sum(const float *v, int from, int to) {
+  float s = 0.f;
+  for (int j = from + (threadIdx.x & 31); j < to; j += 32) s += v[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
 // Per-lane window metrics over the snapshot (sum of speeds and count), deterministic:
-// a segmented sum over the warp (vehicles of a lane are consecutive), then the lane's
-// first vehicle adds the part of its lane that lies in later warps and adds the result to
-// the window accumulators (one writer per lane and step).
+// a segmented sum over the warp (vehicles of a lane are consecutive), plus the part of its
+// lane that lies in later warps (summed by the whole warp, which matters for lanes of
+// hundreds of vehicles); the lane's first vehicle adds the result to the window
+// accumulators (one writer per lane and step).
 __device__ __forceinline__ void lane_speed_sums(const StepArgs &a, const Soa &S, const int4 *dyn,
                                                 int i, int w, const VCtx &c) {
   const int wl = threadIdx.x & 31;
@@ -752,10 +763,16 @@ __device__ __forceinline__ void lane_speed_sums(const StepArgs &a, const Soa &S,
     int ly = __shfl_down_sync(0xffffffffu, l, o);
     if (wl + o < 32 && ly == l) v += y;
   }
+  // only the lane of the warp's last vehicle can continue past the warp: the whole warp sums
+  // that part (coalesced), and the lane's first vehicle adds it
+  if (__shfl_sync(0xffffffffu, act && c.nb.sameL, 31)) {
+    const int lc = __shfl_sync(0xffffffffu, l, 31);
+    const int4 dc = dyn[lc];
+    const float tail = warp_range_sum(S.v, (i | 31) + 1, dc.x + dc.y);
+    if (l == lc) v += tail;
+  }
   if (!act || c.nb.sameF) return;   // the lane's first vehicle writes its sums
   const int4 d = dyn[l];
-  const int warp_end = (i | 31) + 1;   // first index past this warp
-  for (int j = warp_end; j < d.x + d.y; ++j) v += S.v[j];
   // one writer per lane and step, so the sums stay deterministic; nothing waits on these
   const size_t o = (size_t)w * a.P.n_lanes + l;
   atomicAdd(&a.vsum[o], v);

@@ -746,9 +746,9 @@ __device__ __noinline__ float warp_range_sum(const float *v, int from, int to) {
 
 // Per-lane window metrics over the snapshot (sum of speeds and count), deterministic:
 // a segmented sum over the warp (vehicles of a lane are consecutive), plus the part of its
-// lane that lies in later warps (summed by the whole warp, which matters for lanes of
-// hundreds of vehicles); the lane's first vehicle adds the result to the window
-// accumulators (one writer per lane and step).
+// lane that lies in later warps (by the lane's first vehicle when short, by the whole warp
+// when long: lanes of hundreds of vehicles); the lane's first vehicle adds the result to
+// the window accumulators (one writer per lane and step).
 __device__ __forceinline__ void lane_speed_sums(const StepArgs &a, const Soa &S, const int4 *dyn,
                                                 int i, int w, const VCtx &c) {
   const int wl = threadIdx.x & 31;
@@ -763,16 +763,22 @@ __device__ __forceinline__ void lane_speed_sums(const StepArgs &a, const Soa &S,
     int ly = __shfl_down_sync(0xffffffffu, l, o);
     if (wl + o < 32 && ly == l) v += y;
   }
-  // only the lane of the warp's last vehicle can continue past the warp: the whole warp sums
-  // that part (coalesced), and the lane's first vehicle adds it
-  if (__shfl_sync(0xffffffffu, act && c.nb.sameL, 31)) {
-    const int lc = __shfl_sync(0xffffffffu, l, 31);
-    const int4 dc = dyn[lc];
-    const float tail = warp_range_sum(S.v, (i | 31) + 1, dc.x + dc.y);
-    if (l == lc) v += tail;
+  const bool first = act && !c.nb.sameF;   // the lane's first vehicle writes its sums
+  int4 d = make_int4(0, 0, 0, 0);
+  if (first) d = dyn[l];
+  const int warp_end = (i | 31) + 1;   // first index past this warp
+  const int rem = first ? d.x + d.y - warp_end : 0;   // its lane's vehicles in later warps
+  // only the lane of the warp's last vehicle can continue past the warp; a long remainder
+  // (lanes of hundreds of vehicles) is summed by the whole warp, a short one by the thread
+  const unsigned lg = __ballot_sync(0xffffffffu, rem > 16);
+  if (lg) {
+    const int f = __ffs(lg) - 1;
+    const float tail = warp_range_sum(S.v, warp_end, __shfl_sync(0xffffffffu, d.x + d.y, f));
+    if (wl == f) v += tail;
+  } else {
+    for (int j = warp_end; j < warp_end + rem; ++j) v += S.v[j];
   }
-  if (!act || c.nb.sameF) return;   // the lane's first vehicle writes its sums
-  const int4 d = dyn[l];
+  if (!first) return;
   // one writer per lane and step, so the sums stay deterministic; nothing waits on these
   const size_t o = (size_t)w * a.P.n_lanes + l;
   atomicAdd(&a.vsum[o], v);

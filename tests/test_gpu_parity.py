@@ -484,3 +484,44 @@ def test_async_state_export_overlaps_steps():
     with pytest.raises(moss.MossError) as e:
         a.read_state_async(torch.empty(cap), None, None, None)
     assert e.value.code == moss.MS_ERR_ARG
+
+
+def test_lane_speed_sums_on_long_lanes():
+    """Per-lane window metrics of one step (sums of the snapshot's speeds, counts) against the
+    oracle on lanes of 300, 150, 47, 31 and 1 vehicles: the parts of a lane past its first
+    vehicle's warp are summed by that vehicle when at most 16 long (lane of 31) and by the
+    whole warp when longer (300, 150, 47).  Counts are exact; a sum of n non-negative FP32
+    speeds is within n * 2^-24 of the exact sum, relative."""
+    _need_gpu()
+    from paper_2405_12520_b300 import moss
+    net = netkit.line(3, 2500.0, 3)
+    l0 = [int(net.edge_lane0[0]) + q for q in range(3)]
+    l2 = [int(net.edge_lane0[2]) + q for q in range(2)]
+    rng = np.random.default_rng(11)
+    lanes, xs, routes = [], [], []
+    for l, cnt, route in ((l0[0], 300, [0, 1]), (l0[1], 150, [0, 1]), (l0[2], 47, [0, 1]),
+                          (l2[0], 31, [2]), (l2[1], 1, [2])):
+        lanes += [l] * cnt
+        xs += list(10.0 + 8.0 * np.arange(cnt))
+        routes += [route] * cnt
+    vs = rng.uniform(0.0, 13.0, len(lanes))
+    dem = netkit.vehicles(lanes, xs, vs, routes)
+    sim = moss.Sim(P, debug=False, n_windows=1)
+    sim.load_network(net)
+    sim.add_vehicles(dem)
+    st = sim.read_state()
+    sim.step(1)
+    sim.sync()
+    gm = sim.read_metrics()
+    orc = oracle.Oracle(net, dem, P, n_windows=1)
+    orc.run(1)
+    om = orc.metrics()
+    np.testing.assert_array_equal(gm["vcnt"][0], om["vcnt"][0])
+    cnt = om["vcnt"][0].astype(np.float64)
+    assert sorted(cnt[cnt > 0].tolist()) == [1, 31, 47, 150, 300]
+    gv, ov = gm["vsum"][0].astype(np.float64), om["vsum"][0]
+    assert np.all(np.abs(gv - ov) <= cnt * 2.0 ** -24 * ov + 1e-6), np.abs(gv - ov).max()
+    # the FP32 inputs summed exactly are the oracle's sums
+    for l in (l0 + l2):
+        sel = st["lane"] == l
+        assert ov[l] == pytest.approx(float(np.sum(st["v"][sel].astype(np.float64))), rel=1e-12, abs=1e-9)

@@ -67,6 +67,23 @@ __device__ __forceinline__ void load_b(uint32_t b[2], FB B) {
   b[1] = pack2(B(t + 8, g), B(t + 9, g));
 }
 
+// The same fragments from row-major bf16 storage with k contiguous: A(m, k) = A[m * lda + k],
+// B(k, n) = W[(n0 + n) * ldw + k0 + k] (a weight matrix stored [out][in]).  Each register
+// holds two k-adjacent elements, so it is one 32-bit shared-memory load (lda, ldw, k0 even).
+__device__ __forceinline__ void load_a_rm(uint32_t a[4], const __nv_bfloat16 *A, int lda) {
+  const int l = threadIdx.x & 31, g = l >> 2, t = (l & 3) * 2;
+  a[0] = *reinterpret_cast<const uint32_t *>(A + g * lda + t);
+  a[1] = *reinterpret_cast<const uint32_t *>(A + (g + 8) * lda + t);
+  a[2] = *reinterpret_cast<const uint32_t *>(A + g * lda + t + 8);
+  a[3] = *reinterpret_cast<const uint32_t *>(A + (g + 8) * lda + t + 8);
+}
+__device__ __forceinline__ void load_b_nk(uint32_t b[2], const __nv_bfloat16 *W, int ldw, int n0, int k0) {
+  const int l = threadIdx.x & 31, g = l >> 2, t = (l & 3) * 2;
+  const __nv_bfloat16 *r = W + (n0 + g) * ldw + k0 + t;
+  b[0] = *reinterpret_cast<const uint32_t *>(r);
+  b[1] = *reinterpret_cast<const uint32_t *>(r + 8);
+}
+
 // Store a 16x8 accumulator tile through f(m, n, value)
 template <class FC>
 __device__ __forceinline__ void store_c(const float c[4], FC f) {
@@ -85,11 +102,11 @@ __device__ __forceinline__ void mlp_forward_tile(const MlpDev &w, const __nv_bfl
                                                  __nv_bfloat16 *H2, FO out) {
   uint32_t a[4], b[2];
   // layer 1: [16 x 16] x W1^T -> [16 x 64]
-  load_a(a, [&](int m, int k) { return X[m * MLP_IN + k]; });
+  load_a_rm(a, X, MLP_IN);
 #pragma unroll
   for (int nt = 0; nt < MLP_H / 8; ++nt) {
     float c[4] = {0.f, 0.f, 0.f, 0.f};
-    load_b(b, [&](int k, int n) { return w.w1[(nt * 8 + n) * MLP_IN + k]; });
+    load_b_nk(b, w.w1, MLP_IN, nt * 8, 0);
     mma16816(c, a, b);
     store_c(c, [&](int m, int n, float v) {
       H1[m * MLP_H + nt * 8 + n] = __float2bfloat16_rn(fmaxf(v + w.b1[nt * 8 + n], 0.f));
@@ -103,10 +120,10 @@ __device__ __forceinline__ void mlp_forward_tile(const MlpDev &w, const __nv_bfl
     float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int ks = 0; ks < MLP_H / 16; ++ks) {
-      load_a(a, [&](int m, int k) { return H1[m * MLP_H + ks * 16 + k]; });
-      load_b(b, [&](int k, int n) { return w.w2[(ch * 16 + n) * MLP_H + ks * 16 + k]; });
+      load_a_rm(a, H1 + ks * 16, MLP_H);
+      load_b_nk(b, w.w2, MLP_H, ch * 16, ks * 16);
       mma16816(c0, a, b);
-      load_b(b, [&](int k, int n) { return w.w2[(ch * 16 + 8 + n) * MLP_H + ks * 16 + k]; });
+      load_b_nk(b, w.w2, MLP_H, ch * 16 + 8, ks * 16);
       mma16816(c1, a, b);
     }
     // bias + ReLU; accumulator layout of two 8-column tiles == A fragment of one 16-wide k step
@@ -132,7 +149,7 @@ __device__ __forceinline__ void mlp_forward_tile(const MlpDev &w, const __nv_bfl
     // layer 3: this 16-wide slice of h2 times W3 (padded to 16 outputs = two n-tiles)
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt) {
-      load_b(b, [&](int k, int n) { return w.w3[(nt * 8 + n) * MLP_H + ch * 16 + k]; });
+      load_b_nk(b, w.w3, MLP_H, nt * 8, ch * 16);
       mma16816(z[nt], ah, b);
     }
   }

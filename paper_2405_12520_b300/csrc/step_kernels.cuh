@@ -877,18 +877,25 @@ __global__ void __launch_bounds__(512, 2) __maxnreg__((MODE == MODE_PLAIN && !DB
             }
           }
         }
-      } else {   // MODE_LEARN: fused inference, one warp = two 16-row tiles
-        if (cm) {
+      } else {   // MODE_LEARN: fused inference; the warp's candidates are packed into the
+        if (cm) {  // first rows, so one 16-row tile serves up to 16 of them
           const MlpDev &w = *reinterpret_cast<const MlpDev *>(lsm);
           unsigned char *ws = lsm + sizeof(MlpDev) + (threadIdx.x >> 5) * LEARN_WARP_SMEM;
           __nv_bfloat16 *X = reinterpret_cast<__nv_bfloat16 *>(ws);
           __nv_bfloat16 *H1 = X + 32 * MLP_IN;
           float *Z = reinterpret_cast<float *>(H1 + 16 * MLP_H);
-          float f[MLP_IN];
-          if (cand) lc_features(a, S, i, u, c, f);
-          for (int q = 0; q < MLP_IN; ++q) X[wl * MLP_IN + q] = __float2bfloat16_rn(cand ? f[q] : 0.f);
+          const int nc = __popc(cm);
+          const int row = __popc(cm & ((1u << wl) - 1u));   // this candidate's row
+          if (cand) {
+            float f[MLP_IN];
+            lc_features(a, S, i, u, c, f);
+            for (int q = 0; q < MLP_IN; ++q) X[row * MLP_IN + q] = __float2bfloat16_rn(f[q]);
+          }
+          // rows past the candidates are zeroed (each output row depends on its input row only)
+          for (int r = nc + wl; r < ((nc + 15) & ~15); r += 32)
+            for (int q = 0; q < MLP_IN; ++q) X[r * MLP_IN + q] = __float2bfloat16_rn(0.f);
           __syncwarp();
-          for (int mt = 0; mt < 2; ++mt) {
+          for (int mt = 0; mt < (nc + 15) >> 4; ++mt) {
             mlp_forward_tile(w, X + mt * 16 * MLP_IN, H1, nullptr,
                              [&](int m, int q, float v) { Z[(mt * 16 + m) * MLP_OUT + q] = v; });
             __syncwarp();
@@ -896,7 +903,7 @@ __global__ void __launch_bounds__(512, 2) __maxnreg__((MODE == MODE_PLAIN && !DB
           int fin = rule;
           bool fb = false;
           if (cand) {
-            const float z0 = Z[wl * 3], z1 = Z[wl * 3 + 1], z2 = Z[wl * 3 + 2];
+            const float z0 = Z[row * 3], z1 = Z[row * 3 + 1], z2 = Z[row * 3 + 2];
             const float mx = fmaxf(z0, fmaxf(z1, z2));
             const float e0 = __expf(z0 - mx), e1 = __expf(z1 - mx), e2 = __expf(z2 - mx);
             const float sum = e0 + e1 + e2;

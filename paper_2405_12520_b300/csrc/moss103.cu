@@ -32,6 +32,7 @@ struct LaunchCfg {
   int blk_decide = 256, grid_decide = 1;
   int blk_apply = 256, grid_apply = 1;
   int blk_bucket = 256, grid_bucket = 1;
+  int f_decide = 1, f_apply = 1, f_bucket = 1;   // grid = factor x resident blocks x SMs
 };
 
 struct Sim {
@@ -244,12 +245,18 @@ cudaError_t launch_step(const Sim *s, const StepArgs &a, cudaStream_t st, cudaEv
 
 cudaError_t enqueue_step(Sim *s, cudaStream_t st) { return launch_step(s, make_args(s), st, nullptr); }
 
-// persistent grids: blocks = factor * (resident blocks per SM) * SMs, capped by the work
+// persistent grids: blocks = factor * (resident blocks per SM) * SMs, capped by the work;
+// the decide kernel's residency is that of the instance the current lane-change mode runs
+// (the learned and logging instances hold more registers and shared memory)
 int shape_grids(Sim *s, LaunchCfg &c, int f_decide, int f_apply, int f_bucket) {
   const int N = s->n_trips;
   int od = 0, oa = 0, ob = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&od, decide_kernel(MODE_PLAIN, s->prm.debug != 0, false),
-                                                   c.blk_decide, 0));
+  c.f_decide = f_decide;
+  c.f_apply = f_apply;
+  c.f_bucket = f_bucket;
+  const size_t dsm = s->lc_mode == MODE_LEARN ? learn_smem(c.blk_decide) : 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&od, decide_kernel(s->lc_mode, s->prm.debug != 0, false),
+                                                   c.blk_decide, dsm));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oa, k_apply, c.blk_apply, 0));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, k_bucket, c.blk_bucket, 0));
   auto g = [&](int blk, int occ, int f) {
@@ -1466,6 +1473,7 @@ int ms_set_lc_log(void *sim, void *x, int *y, int cap, int *n) {
   s->lc.log_n = n;
   s->lc_mode = x ? MODE_LOG : (s->d_model && s->lc.model ? MODE_LEARN : MODE_PLAIN);
   drop_graphs(s);
+  if (s->veh_loaded) return shape_grids(s, s->cfg, s->cfg.f_decide, s->cfg.f_apply, s->cfg.f_bucket);
   return MS_OK;
 }
 
@@ -1756,6 +1764,7 @@ int ms_set_lc_model(void *sim, const float *params, float margin) {
   if (!params) {
     s->lc.model = nullptr;
     s->lc_mode = s->lc.log_x ? MODE_LOG : MODE_PLAIN;
+    if (s->veh_loaded) return shape_grids(s, s->cfg, s->cfg.f_decide, s->cfg.f_apply, s->cfg.f_bucket);
     return MS_OK;
   }
   if (!(margin >= 0.f && margin <= 1.f)) return fail(s, MS_ERR_ARG, "margin must be in [0, 1]");
@@ -1782,6 +1791,7 @@ int ms_set_lc_model(void *sim, const float *params, float margin) {
   s->lc.stats = s->d_lcstats;
   s->lc_mode = MODE_LEARN;
   s->lc.log_x = nullptr;
+  if (s->veh_loaded) return shape_grids(s, s->cfg, s->cfg.f_decide, s->cfg.f_apply, s->cfg.f_bucket);
   return MS_OK;
 }
 

@@ -822,11 +822,14 @@ __host__ __device__ constexpr int learn_smem(int threads) {
 
 // DBG: record per-vehicle sensing and decisions (tests); a separate instance, so that the
 // production kernel keeps none of those values alive.  MODS: lane speed limits or closures
-// are set (also a separate instance: without them the step does no work for them).  The plain production instance is
-// capped at 48 registers: 5 blocks of 256 per SM instead of 4 outweigh its few spills (the
-// kernel is bound by the latency of dependent gathers, so resident warps decide its speed).
+// are set (also a separate instance: without them the step does no work for them).  The plain
+// production instance is capped at 48 registers: 5 blocks of 256 per SM instead of 4 outweigh
+// its few spills (the kernel is bound by the latency of dependent gathers, so resident warps
+// decide its speed).  The learned instance gets 80, which removes its spills around the MMA
+// tiles (measured faster than 64 with spills or 96).
 template <int MODE, bool DBG, bool MODS>
-__global__ void __launch_bounds__(512, 2) __maxnreg__((MODE == MODE_PLAIN && !DBG) ? 48 : 64)
+__global__ void __launch_bounds__(512, (MODE == MODE_LEARN && !DBG) ? 1 : 2)
+    __maxnreg__((MODE == MODE_PLAIN && !DBG) ? 48 : (MODE == MODE_LEARN && !DBG) ? 80 : 64)
     k_decide_t(StepArgs a) {
   extern __shared__ __align__(16) unsigned char lsm[];
   pdl_enter();

@@ -83,6 +83,8 @@ def _load():
         lib.or_get_ctrl_state.argtypes = [C.c_void_p, C.c_void_p]
         lib.or_set_ctrl_state.argtypes = [C.c_void_p, C.c_void_p]
         lib.or_set_lane_limits.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.or_set_links.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+        lib.or_set_links.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -199,6 +201,15 @@ class Oracle:
         cl = None if closed is None else np.ascontiguousarray(closed, np.int32)
         _load().or_set_lane_limits(self.h, int(ln.shape[0]), _p(ln), None if vm is None else _p(vm),
                                    None if cl is None else _p(cl))
+
+    def set_lane_links(self, lanes, open_mask) -> None:
+        """R17: bit j of open_mask[k] opens (1) or closes (0) the j-th lane link of edge lane
+        lanes[k].  The caller keeps every remaining route lane-connected."""
+        ln = np.ascontiguousarray(lanes, np.int32)
+        mk = np.ascontiguousarray(open_mask, np.uint32)
+        assert ln.shape == mk.shape
+        if _load().or_set_links(self.h, int(ln.shape[0]), _p(ln), _p(mk)) != 0:
+            raise ValueError("or_set_links: internal or out-of-range lane, or more than 32 links")
 
     def set_ctrl_state(self, cs) -> None:
         cs = np.ascontiguousarray(np.asarray(cs, np.int32).reshape(-1, 3))

@@ -80,6 +80,13 @@
  *      that reaches it ends in a stopped obstacle at the end of the lane before it, it is
  *      never a lane-change target, and its departure queue waits.  Vehicles already on it
  *      drive on.
+ *  R17 Dynamic lanes (set between steps): each lane link of an edge lane (one successor
+ *      entry: the junction-internal lane of one movement) is open or closed.  A closed
+ *      link is no link: the fan-out choice (R11), every test of whether a lane links
+ *      toward an edge (mandatory changes, the lanes a discretionary change may target, the
+ *      obstacle at a lane end) and the max-pressure sums (R13) skip it.  Vehicles already
+ *      on its internal lane finish the movement; waiting trips keep the departure lanes
+ *      assigned at load.  The caller keeps every remaining route lane-connected.
  *  R12 Threshold jitter (a randomized-MOBIL variant, off when th_jitter = 0): trip c's
  *      incentive threshold is th + th_jitter (2u - 1), u = (SplitMix64(seed ^ 0x9E3779B97F4A7C15
  *      ^ c) >> 40) / 2^24, fixed for the trip (driver heterogeneity); the salt keeps these
@@ -135,6 +142,8 @@ struct or_sim {
   /* R14 lane modifications */
   double *lane_vmax;  /* speed limit per lane, INFINITY = none */
   int *lane_closed;
+  /* R17 dynamic lanes */
+  unsigned char *link_off;   /* per successor entry: 1 = closed */
 };
 
 /* ------------------------------------------------------------------------------------ */
@@ -163,7 +172,7 @@ static int is_internal(const or_sim *s, int l) { return s->net.lane_edge[l] < 0;
 static int connects(const or_sim *s, int l, int en) {
   if (en < 0) return 1;
   for (int k = s->net.succ_off[l]; k < s->net.succ_off[l + 1]; ++k)
-    if (s->net.succ_edge[k] == en) return 1;
+    if (s->net.succ_edge[k] == en && !s->link_off[k]) return 1;   /* R17: open links only */
   return 0;
 }
 
@@ -173,7 +182,7 @@ static int connects(const or_sim *s, int l, int en) {
 static int choose_succ(const or_sim *s, int l, int en, int en2) {
   int first = -1;
   for (int k = s->net.succ_off[l]; k < s->net.succ_off[l + 1]; ++k) {
-    if (s->net.succ_edge[k] != en) continue;
+    if (s->net.succ_edge[k] != en || s->link_off[k]) continue;   /* R17 */
     int il = s->net.succ_lane[k];
     if (first < 0) first = il;
     if (en2 < 0) return il;
@@ -212,6 +221,7 @@ static void mp_advance(or_sim *s) {
       if (c < 0 || is_internal(s, l)) continue;
       int64_t sum = 0;
       for (int k = s->net.succ_off[l]; k < s->net.succ_off[l + 1]; ++k) {
+        if (s->link_off[k]) continue;   /* R17 */
         const int il = s->net.succ_lane[k];
         const int m = s->net.succ_lane[s->net.succ_off[il]];
         sum += s->seg_cnt[l] - s->seg_cnt[m];
@@ -794,6 +804,7 @@ or_sim *or_create(const or_net *net, const or_params *p, int n_trips, const int 
     for (int c = 0; c < C; ++c) s->mp_poff[c + 1] = s->mp_poff[c] + net->ctrl_nphase[c];
     s->mp_pres = (int64_t *)calloc((size_t)s->mp_poff[C] + 1, sizeof(int64_t));
   }
+  s->link_off = (unsigned char *)calloc((size_t)net->succ_off[L] + 1, 1);
   s->lane_vmax = (double *)malloc(sizeof(double) * (size_t)L);
   s->lane_closed = (int *)calloc((size_t)L, sizeof(int));
   for (int l = 0; l < L; ++l) s->lane_vmax[l] = INFINITY;
@@ -843,7 +854,7 @@ or_sim *or_create(const or_net *net, const or_params *p, int n_trips, const int 
 void or_destroy(or_sim *s) {
   if (!s) return;
   free(s->mp_g); free(s->mp_pend); free(s->mp_yend); free(s->mp_pres); free(s->mp_poff);
-  free(s->lane_vmax); free(s->lane_closed);
+  free(s->lane_vmax); free(s->lane_closed); free(s->link_off);
   free(s->status); free(s->lane); free(s->rp); free(s->t_arr); free(s->x); free(s->v);
   free(s->dep_lane); free(s->order); free(s->pos); free(s->seg_start); free(s->seg_cnt);
   free(s->n_lane); free(s->n_rp); free(s->n_status); free(s->n_x); free(s->n_v);
@@ -885,6 +896,20 @@ void or_set_lane_limits(or_sim *s, int n, const int *lanes, const float *vmax, c
     if (vmax) s->lane_vmax[l] = (vmax[k] > 0.0f && isfinite(vmax[k])) ? (double)vmax[k] : INFINITY;
     if (closed) s->lane_closed[l] = closed[k] != 0;
   }
+}
+
+int or_set_links(or_sim *s, int n, const int *lanes, const unsigned *open_mask) {
+  for (int k = 0; k < n; ++k) {   /* validate first: nothing changes on a bad entry */
+    const int l = lanes[k];
+    if (l < 0 || l >= s->net.n_lanes || is_internal(s, l)) return -1;
+    if (s->net.succ_off[l + 1] - s->net.succ_off[l] > 32) return -1;
+  }
+  for (int k = 0; k < n; ++k) {
+    const int l = lanes[k];
+    for (int j = s->net.succ_off[l]; j < s->net.succ_off[l + 1]; ++j)
+      s->link_off[j] = !((open_mask[k] >> (j - s->net.succ_off[l])) & 1u);
+  }
+  return 0;
 }
 
 void or_get_ctrl_state(or_sim *s, int *out) {

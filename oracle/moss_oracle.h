@@ -82,6 +82,10 @@ void or_get_ctrl_state(or_sim *s, int *out);
    (m/s; <= 0 or non-finite: none) and closed[k] (0 / 1).  Either array may be NULL. */
 void or_set_lane_limits(or_sim *s, int n, const int *lanes, const float *vmax, const int *closed);
 void or_set_ctrl_state(or_sim *s, const int *in);
+/* R17 dynamic lanes, in effect from the next step: for edge lane lanes[k], bit j of
+   open_mask[k] opens (1) or closes (0) its j-th lane link (successor entry, CSR order).
+   Returns -1 (nothing changed) for an internal or out-of-range lane or more than 32 links. */
+int or_set_links(or_sim *s, int n, const int *lanes, const unsigned *open_mask);
 uint64_t or_splitmix64(uint64_t state);
 /* neighbour search on the current snapshot (for the brute-force check): for each trip id:
    own-lane leader, own-lane follower, left-lane leader/follower, right-lane leader/follower

@@ -757,3 +757,140 @@ def test_merge_projection_leader(oracle_lib):
     d = case(6.0, 6.0)          # tie: id 0 goes first, id 1 follows at gap -L
     assert d["lead_id"][0] == -1
     assert d["lead_id"][1] == 0 and d["s_own"][1] == pytest.approx(-P["veh_len"], abs=1e-5)
+
+
+# ---------------------------------------------------------------------------------------
+# dynamic lanes (R17)
+# ---------------------------------------------------------------------------------------
+
+def test_closed_links_force_the_mandatory_change(oracle_lib):
+    """Straight road, 2 lanes: with its links open a lone vehicle stays on lane 0 (empty
+    neighbour, zero incentive); with lane 0's links closed lane 0 no longer leads to the
+    next edge, so at the even step (moves toward higher lane index allowed) it changes to
+    lane 1 at once."""
+    import oracle
+    net = netkit.line(3, 300.0, 2)
+    l0 = int(net.edge_lane0[0])
+    dem = netkit.vehicles([l0], [100.0], [10.0], [[0, 1]])
+    a = oracle.Oracle(net, dem, P)
+    a.step()
+    assert a.state()["lane"][0] == l0
+    b = oracle.Oracle(net, dem, P)
+    b.set_lane_links([l0], [0])
+    _, d = b.step(debug=True)
+    assert d["lc_dir"][0] == 1 and b.state()["lane"][0] == l0 + 1
+
+
+def test_closed_link_moves_the_fan_out_choice(oracle_lib):
+    """Lane 0 of the first edge links to the next edge twice (two internal lanes, CSR
+    order); a vehicle crossing the junction takes the first, or the second once the first
+    is closed, and the first again once it reopens."""
+    import oracle
+    net = netkit.line(3, 300.0, 2)
+    l0 = int(net.edge_lane0[0])
+    first, second = (int(net.succ_lane[k]) for k in range(net.succ_off[l0], net.succ_off[l0] + 2))
+    dem = netkit.vehicles([l0], [296.0], [10.0], [[0, 1]])
+    for mask, want in ((0b11, first), (0b10, second), (0b01, first)):
+        o = oracle.Oracle(net, dem, P)
+        o.set_lane_links([l0], [mask])
+        o.step()
+        assert o.state()["lane"][0] == want, (mask, o.state()["lane"][0])
+
+
+def test_all_open_links_change_nothing(oracle_lib):
+    """Opening every link of every edge lane (their state at load) leaves a whole run
+    bit-identical."""
+    import oracle
+    net, dem = synth.small_grid_workload(3)
+    a = oracle.Oracle(net, dem, P)
+    b = oracle.Oracle(net, dem, P)
+    el = np.nonzero(net.lane_edge >= 0)[0]
+    b.set_lane_links(el, (1 << np.diff(net.succ_off)[el]) - 1)
+    a.run(600)
+    b.run(600)
+    sa, sb = a.state(), b.state()
+    for k in ("status", "lane", "x", "v", "rp"):
+        np.testing.assert_array_equal(sa[k], sb[k])
+
+
+def _closable_links(net, dem, rng, frac):
+    """Links of edge lanes that can close with every route still lane-connected: a link
+    (lane l -> exit edge f) closes only if another lane of l's edge keeps an open link to f."""
+    routes = {(int(a), int(b)) for i in range(dem.n)
+              for a, b in zip(dem.route_edges[dem.route_off[i]:dem.route_off[i + 1] - 1],
+                              dem.route_edges[dem.route_off[i] + 1:dem.route_off[i + 1]])}
+    el = np.nonzero(net.lane_edge >= 0)[0]
+    mask = {int(l): (1 << int(net.succ_off[l + 1] - net.succ_off[l])) - 1 for l in el}
+    for l in rng.permutation(el):
+        l = int(l)
+        for j in range(int(net.succ_off[l + 1] - net.succ_off[l])):
+            if rng.random() >= frac:
+                continue
+            f = int(net.succ_edge[net.succ_off[l] + j])
+            e = int(net.lane_edge[l])
+            trial = dict(mask)
+            trial[l] &= ~(1 << j)
+            ok = all(any((trial[int(net.edge_lane0[a]) + q] >> jj) & 1 and
+                         int(net.succ_edge[net.succ_off[int(net.edge_lane0[a]) + q] + jj]) == b
+                         for q in range(int(net.edge_nlanes[a]))
+                         for jj in range(int(net.succ_off[int(net.edge_lane0[a]) + q + 1] -
+                                             net.succ_off[int(net.edge_lane0[a]) + q])))
+                     for a, b in routes if a == e)
+            if ok:
+                mask = trial
+    return mask
+
+
+def test_max_pressure_skips_closed_links(oracle_lib):
+    """Small grid under max pressure with 30% of the closable links closed: at every step
+    the controllers equal R13 restated with numpy over the open links only."""
+    import oracle
+    net, dem = synth.small_grid_workload(2)
+    mask = _closable_links(net, dem, np.random.default_rng(4), 0.3)
+    closed = {(l, j) for l, m in mask.items() for j in range(int(net.succ_off[l + 1] - net.succ_off[l]))
+              if not (m >> j) & 1}
+    assert len(closed) > 20
+    o = oracle.Oracle(net, dem, MP)
+    o.set_lane_links(list(mask), list(mask.values()))
+
+    def brute(counts, cs_prev, t):
+        cs = cs_prev.copy()
+        for c in range(net.n_ctrl):
+            if cs[c, 1] >= 0 and t >= cs[c, 2]:
+                cs[c, 0], cs[c, 1] = cs[c, 1], -1
+        if t % MP["mp_interval"]:
+            return cs
+        pres = np.zeros((net.n_ctrl, int(net.ctrl_nphase.max())), np.int64)
+        for l in np.nonzero((net.lane_ctrl >= 0) & (net.lane_edge >= 0))[0]:
+            for j, k in enumerate(range(net.succ_off[l], net.succ_off[l + 1])):
+                if (int(l), j) in closed:
+                    continue
+                tg = net.succ_lane[net.succ_off[net.succ_lane[k]]]
+                pres[net.lane_ctrl[l], net.lane_group[l]] += int(counts[l] - counts[tg])
+        for c in range(net.n_ctrl):
+            if cs[c, 1] >= 0:
+                continue
+            pr = pres[c, :net.ctrl_nphase[c]]
+            best = int(np.argmax(pr))
+            if pr[cs[c, 0]] == pr[best]:
+                best = cs[c, 0]
+            if best != cs[c, 0]:
+                if net.ctrl_yellow[c] > 0:
+                    cs[c, 1], cs[c, 2] = best, t + net.ctrl_yellow[c]
+                else:
+                    cs[c, 0] = best
+        return cs
+
+    prev = np.tile(np.array([0, -1, 0], np.int32), (net.n_ctrl, 1))
+    differs = 0
+    for _ in range(1200):
+        st = o.state()
+        cs = o.ctrl_state()
+        act = st["status"] == 1
+        counts = np.bincount(st["lane"][act], minlength=net.n_lanes)
+        np.testing.assert_array_equal(cs, brute(counts, prev, st["t"]), err_msg=f"step {st['t']}")
+        differs += int((cs != _mp_brute(net, counts, prev, st["t"], MP["mp_interval"])).any())
+        prev = cs
+        err, _ = o.step()
+        assert err == 0
+    assert differs > 0   # the closed links changed some decision

@@ -305,6 +305,22 @@ int ms_set_lc_model(void *sim, const float *params, float margin);
    work for this. */
 int ms_set_lane_limits(void *sim, int n, const int *lanes, const float *vmax, const int *closed);
 
+/* Dynamic lanes (Sec. III-C "Python API": modification calls for dynamic lanes), in effect
+   from the next step.  For edge lane lanes[k] (host arrays, n entries), bit j of
+   open_mask[k] opens (1) or closes (0) its j-th lane link (successor entry j, the CSR order
+   of ms_network.succ_off; at load every link is open).  A closed link is no link: the
+   fan-out choice toward the next route edge, mandatory lane changes, the lanes a
+   discretionary change may target, the obstacle at a lane end and the max-pressure sums
+   all skip it.  Vehicles already on its junction-internal lane finish the movement;
+   waiting trips keep the departure lanes assigned when they were added.
+   Errors (nothing changed): MS_ERR_ARG for an internal or out-of-range lane;
+   MS_ERR_CAPACITY for a lane with more than 32 links; MS_ERR_STATE before ms_add_vehicles;
+   MS_ERR_ROUTE if a trip not yet arrived would need, on the rest of its route, a pair of
+   consecutive edges with no open link (the message names it).  Synchronises; rebuilds the
+   link plans of every route on the host and re-derives every vehicle's cached next-lane
+   choice (a state read and write: O(trips + route entries)). */
+int ms_set_lane_links(void *sim, int n, const int *lanes, const unsigned *open_mask);
+
 /* Route planner for demand generation (the paper turns OD matrices into trips with routes,
    Sec. III-C "Converter from OD matrix to travel demand"; at millions of trips that is the
    host's bottleneck, so it runs on the GPU here).  Trip i goes from edge orig_edge[i] to

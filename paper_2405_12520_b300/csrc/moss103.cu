@@ -56,6 +56,7 @@ struct Sim {
   // network (host copies needed by validation and state I/O)
   int n_lanes = 0, n_edges = 0, n_ctrl = 0;
   std::vector<float> lane_len;
+  std::vector<unsigned char> link_off;   // per successor entry: 1 = closed (dynamic lanes)
   std::vector<int> lane_edge, lane_left, lane_right, succ_off, succ_lane, succ_edge, edge_nlanes,
       edge_lane0;
   // trips
@@ -66,6 +67,7 @@ struct Sim {
   // device
   LaneInfo *d_li = nullptr;
   int2 *d_succ = nullptr;
+  unsigned char *d_link_off = nullptr;        // per successor entry: 1 = closed (dynamic lanes)
   int *d_pred = nullptr;
   int4 *d_ctrl4 = nullptr;
   std::vector<int4> h_ctrl4;
@@ -144,6 +146,7 @@ StepArgs make_args(Sim *s) {
   StepArgs a{};
   a.li = s->d_li;
   a.succ = s->d_succ;
+  a.link_off = s->d_link_off;
   a.pred = s->d_pred;
   a.ctrl4 = s->d_ctrl4;
   a.sig[0] = s->d_sig[0];
@@ -300,7 +303,7 @@ bool lane_links_to(const Sim *s, int l, int e);
 int host_choose_entry(const Sim *s, int l, int en, int en2) {
   int first = -1;
   for (int k = s->succ_off[l]; k < s->succ_off[l + 1]; ++k) {
-    if (s->succ_edge[k] != en) continue;
+    if (s->succ_edge[k] != en || s->link_off[k]) continue;   // closed links are no links
     const int j = k - s->succ_off[l];
     if (first < 0) first = j;
     if (en2 < 0) return j;
@@ -354,7 +357,7 @@ int host_next_choice(const Sim *s, int lane, int rp) {
 
 bool lane_links_to(const Sim *s, int l, int e) {
   for (int k = s->succ_off[l]; k < s->succ_off[l + 1]; ++k)
-    if (s->succ_edge[k] == e) return true;
+    if (s->succ_edge[k] == e && !s->link_off[k]) return true;
   return false;
 }
 
@@ -366,6 +369,28 @@ int upload_queues(Sim *s, const std::vector<int> &qhead) {
   std::vector<int2> hd(s->n_lanes);
   for (int l = 0; l < s->n_lanes; ++l) hd[l] = make_int2(qhead[l], due[l]);
   CK(cudaMemcpy(s->d_qhd, hd.data(), sizeof(int2) * s->n_lanes, cudaMemcpyHostToDevice));
+  return MS_OK;
+}
+
+// What a departure writes is known beforehand: the trip, its route start, second edge and
+// next-lane choice on the departure lane, its v0, and when the lane's next trip is due (the
+// choice and the plan word depend on the lane links, so a link change rebuilds them).
+int upload_queue_entries(Sim *s) {
+  std::vector<int4> qe(s->h_qtrip.size(), make_int4(0, 0, 0, 0));
+  std::vector<int4> qe2(s->h_qtrip.size(), make_int4(0, 0, 0x7fffffff, 0));
+  for (int l = 0; l < s->n_lanes; ++l)
+    for (int j = s->h_qoff[l]; j < s->h_qoff[l + 1]; ++j) {
+      const int trip = s->h_qtrip[j], r0 = s->h_route0[trip];
+      float v0 = s->h_v0[trip];
+      int v0b;
+      std::memcpy(&v0b, &v0, 4);
+      qe[j] = make_int4(trip, r0, host_next_choice(s, l, r0), v0b);
+      const unsigned long long w = s->h_plan[r0];
+      qe2[j] = make_int4((int)(unsigned)(w & 0xffffffffu), (int)(unsigned)(w >> 32),
+                         j + 1 < s->h_qoff[l + 1] ? s->h_tdep[s->h_qtrip[j + 1]] : 0x7fffffff, 0);
+    }
+  CK(cudaMemcpy(s->d_qent, qe.data(), sizeof(int4) * qe.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_qent2, qe2.data(), sizeof(int4) * qe2.size(), cudaMemcpyHostToDevice));
   return MS_OK;
 }
 
@@ -564,6 +589,7 @@ int ms_load_network(void *sim, const ms_network *net) {
     if (s->succ_off[l + 1] < s->succ_off[l]) return fail(s, MS_ERR_ARG, "succ_off not monotone");
   s->succ_lane.assign(net->succ_lane, net->succ_lane + S);
   s->succ_edge.assign(net->succ_edge, net->succ_edge + S);
+  s->link_off.assign(std::max(1, S), 0);   // every lane link open
   const float min_len = s->P.v_max * s->P.dt;
   std::vector<LaneInfo> li(L);
   std::vector<int> npred(L, 0);
@@ -659,6 +685,7 @@ int ms_load_network(void *sim, const ms_network *net) {
   s->P.n_lanes = L;
   DALLOC(s->d_li, L);
   DALLOC(s->d_succ, succ.size());
+  DALLOC(s->d_link_off, s->link_off.size());
   DALLOC(s->d_pred, pred.size());
   DALLOC(s->d_ctrl4, c4.size());
   DALLOC(s->d_sig[0], c4.size());
@@ -688,6 +715,7 @@ int ms_load_network(void *sim, const ms_network *net) {
   }
   CK(cudaMemcpy(s->d_li, li.data(), L * sizeof(LaneInfo), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->d_succ, succ.data(), succ.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->d_link_off, s->link_off.data(), s->link_off.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->d_pred, pred.data(), pred.size() * sizeof(int), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->d_ctrl4, c4.data(), c4.size() * sizeof(int4), cudaMemcpyHostToDevice));
   s->n_tiles = (L + LANE_TILE - 1) / LANE_TILE;
@@ -851,23 +879,8 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
   }
   CK(cudaMemcpy(s->d_qtrip, s->h_qtrip.data(), sizeof(int) * s->h_qtrip.size(), cudaMemcpyHostToDevice));
   {
-    // what a departure writes is known at load time: the trip, its route start, second edge
-    // and next-lane choice on the departure lane, its v0, and when the lane's next trip is due
-    std::vector<int4> qe(s->h_qtrip.size(), make_int4(0, 0, 0, 0));
-    std::vector<int4> qe2(s->h_qtrip.size(), make_int4(0, 0, 0x7fffffff, 0));
-    for (int l = 0; l < s->n_lanes; ++l)
-      for (int j = s->h_qoff[l]; j < s->h_qoff[l + 1]; ++j) {
-        const int trip = s->h_qtrip[j], r0 = s->h_route0[trip];
-        float v0 = s->h_v0[trip];
-        int v0b;
-        std::memcpy(&v0b, &v0, 4);
-        qe[j] = make_int4(trip, r0, host_next_choice(s, l, r0), v0b);
-        const unsigned long long w = s->h_plan[r0];
-        qe2[j] = make_int4((int)(unsigned)(w & 0xffffffffu), (int)(unsigned)(w >> 32),
-                           j + 1 < s->h_qoff[l + 1] ? s->h_tdep[s->h_qtrip[j + 1]] : 0x7fffffff, 0);
-      }
-    CK(cudaMemcpy(s->d_qent, qe.data(), sizeof(int4) * qe.size(), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(s->d_qent2, qe2.data(), sizeof(int4) * qe2.size(), cudaMemcpyHostToDevice));
+    int rq = upload_queue_entries(s);
+    if (rq) return rq;
   }
   CK(cudaMemcpy(s->d_tdep, s->h_tdep.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->d_route0, s->h_route0.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
@@ -1755,6 +1768,59 @@ int ms_set_lane_limits(void *sim, int n, const int *lanes, const float *vmax, co
     drop_graphs(s);
   }
   return MS_OK;
+}
+
+// an edge lane of edge e has an open link toward edge f (under the link states off)
+static bool edge_links_to(const Sim *s, const std::vector<unsigned char> &off, int e, int f) {
+  for (int q = 0; q < s->edge_nlanes[e]; ++q) {
+    const int l = s->edge_lane0[e] + q;
+    for (int k = s->succ_off[l]; k < s->succ_off[l + 1]; ++k)
+      if (s->succ_edge[k] == f && !off[k]) return true;
+  }
+  return false;
+}
+
+int ms_set_lane_links(void *sim, int n, const int *lanes, const unsigned *open_mask) {
+  Sim *s = (Sim *)sim;
+  if (!s || n < 0 || (n > 0 && (!lanes || !open_mask))) return MS_ERR_ARG;
+  if (!s->veh_loaded) return fail(s, MS_ERR_STATE, "add vehicles first");
+  std::vector<unsigned char> off = s->link_off;
+  for (int k = 0; k < n; ++k) {
+    const int l = lanes[k];
+    if (l < 0 || l >= s->n_lanes || s->lane_edge[l] < 0) return fail(s, MS_ERR_ARG, "not an edge lane");
+    const int deg = s->succ_off[l + 1] - s->succ_off[l];
+    if (deg > 32) return fail(s, MS_ERR_CAPACITY, "an edge lane with more than 32 links");
+    for (int j = 0; j < deg; ++j) off[s->succ_off[l] + j] = !((open_mask[k] >> j) & 1u);
+  }
+  // the current state (host), to check the remaining routes and to re-derive every cached
+  // lane choice under the new links
+  const int N = s->n_trips;
+  std::vector<int> id(N), lane(N), ridx(N), status(N), tarr(N), cs(3 * std::max(1, s->n_ctrl));
+  std::vector<float> x(N), v(N);
+  ms_state st{};
+  st.capacity = N;
+  st.id = id.data(); st.lane = lane.data(); st.route_idx = ridx.data(); st.x = x.data(); st.v = v.data();
+  st.trip_status = status.data(); st.t_arr = tarr.data();
+  st.ctrl_state = s->n_ctrl > 0 ? cs.data() : nullptr;
+  if (int r = ms_read_state(sim, &st, 0)) return r;
+  std::vector<int> from(N, -1);   // first route index whose pair must stay connected
+  for (int trip = 0; trip < N; ++trip) from[trip] = status[trip] == 0 ? 0 : -1;
+  for (int i = 0; i < st.n_active; ++i)
+    from[id[i]] = ridx[i] + (s->lane_edge[lane[i]] < 0 ? 1 : 0);   // a movement under way ends
+  for (int trip = 0; trip < N; ++trip) {
+    if (from[trip] < 0) continue;
+    const int *R = s->h_routes.data() + s->h_route0[trip];
+    for (int k = from[trip]; R[k] >= 0 && R[k + 1] >= 0; ++k)
+      if (!edge_links_to(s, off, R[k], R[k + 1]))
+        return fail(s, MS_ERR_ROUTE, "trip " + std::to_string(trip) + " would need edge " + std::to_string(R[k]) +
+                                         " -> " + std::to_string(R[k + 1]) + " with no open lane link");
+  }
+  s->link_off = off;
+  CK(cudaMemcpy(s->d_link_off, s->link_off.data(), s->link_off.size(), cudaMemcpyHostToDevice));
+  build_plans(s);
+  CK(cudaMemcpy(s->d_plan, s->h_plan.data(), sizeof(unsigned long long) * s->h_plan.size(), cudaMemcpyHostToDevice));
+  if (int r = upload_queue_entries(s)) return r;
+  return ms_write_state(sim, &st);   // plan words and next-lane choices of the vehicles
 }
 
 int ms_set_lc_model(void *sim, const float *params, float margin) {

@@ -150,6 +150,7 @@ struct LcAux {
 struct StepArgs {
   const LaneInfo *li;
   const int2 *succ;    // {internal lane, exit edge}
+  const unsigned char *link_off;   // per successor entry: 1 = closed (dynamic lanes)
   const int *pred;
   const int4 *ctrl4;   // {offset, green, yellow, nphase}
   int *sig[2];         // per controller, for the steps of parity 0 / 1: 2 * phase + yellow
@@ -1372,6 +1373,7 @@ __global__ void k_signals(StepArgs a) {
         const int ql = dyn[l].y;
         grp = li.group;
         for (int k = 0; k < li.n_succ; ++k) {
+          if (a.link_off[li.succ + k]) continue;   // a closed link is no link
           const int tg = a.li[a.succ[li.succ + k].x].succ;   // internal lane's target
           contrib += ql - dyn[tg].y;
         }

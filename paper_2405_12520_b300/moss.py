@@ -18,7 +18,8 @@ MS_OK, MS_ERR_ARG, MS_ERR_ROUTE, MS_ERR_CAPACITY, MS_ERR_CUDA, MS_ERR_DEVICE, MS
 ERR_NAMES = {0: "OK", -1: "ARG", -2: "ROUTE", -3: "CAPACITY", -4: "CUDA", -5: "DEVICE", -6: "STATE"}
 SYMBOLS = ("ms_create", "ms_load_network", "ms_add_vehicles", "ms_step", "ms_step_timed", "ms_step_noalloc",
            "ms_load_network_batch", "ms_add_vehicles_batch", "ms_batch_offsets", "ms_autotune",
-           "ms_set_lc_log", "ms_set_lc_model", "ms_set_lane_limits", "ms_route_trips", "ms_sample_trips",
+           "ms_set_lc_log", "ms_set_lc_model", "ms_set_lane_limits", "ms_set_lane_links", "ms_route_trips",
+           "ms_sample_trips",
            "ms_read_lc_stats",
            "ms_mlp_train_step",
            "ms_mlp_grad",
@@ -93,6 +94,7 @@ def load():
         lib.ms_set_lc_log.argtypes = [vp, vp, vp, C.c_int, vp]
         lib.ms_set_lc_model.argtypes = [vp, vp, C.c_float]
         lib.ms_set_lane_limits.argtypes = [vp, C.c_int, vp, vp, vp]
+        lib.ms_set_lane_links.argtypes = [vp, C.c_int, vp, vp]
         lib.ms_route_trips.argtypes = [vp, C.c_int, vp, vp, vp, vp, C.c_int64, vp]
         lib.ms_sample_trips.argtypes = [vp, C.c_int, vp, vp, C.c_int, C.c_int, C.c_int, C.c_uint64, vp, vp, vp]
         lib.ms_read_lc_stats.argtypes = [vp, vp]
@@ -414,6 +416,15 @@ class Sim:
         cl = None if closed is None else np.ascontiguousarray(closed, np.int32)
         self._check(self.lib.ms_set_lane_limits(self.h, int(ln.shape[0]), _p(ln), _p(vm), _p(cl)),
                     "ms_set_lane_limits")
+
+    def set_lane_links(self, lanes, open_mask):
+        """Dynamic lanes: bit j of open_mask[k] opens (1) or closes (0) the j-th lane link of
+        edge lane lanes[k], in effect from the next step."""
+        ln = np.ascontiguousarray(lanes, np.int32)
+        mk = np.ascontiguousarray(open_mask, np.uint32)
+        if ln.shape != mk.shape:
+            raise ValueError("lanes and open_mask differ in length")
+        self._check(self.lib.ms_set_lane_links(self.h, int(ln.shape[0]), _p(ln), _p(mk)), "ms_set_lane_links")
 
     def set_lc_model(self, params=None, margin: float = 0.2):
         """Use the learned lane-change decision (params: 5443 floats, host); None: rule."""

@@ -525,3 +525,71 @@ def test_lane_speed_sums_on_long_lanes():
     for l in (l0 + l2):
         sel = st["lane"] == l
         assert ov[l] == pytest.approx(float(np.sum(st["v"][sel].astype(np.float64))), rel=1e-12, abs=1e-9)
+
+
+@pytest.mark.parametrize("kind,t0,mp", [("grid12x3", 12, False), ("delaunay", 5, False), ("grid12x3", 20, True)])
+def test_single_steps_match_oracle_dynamic_lanes(kind, t0, mp):
+    """About 30% of the lane links closed (R17) without disconnecting any route, set through
+    the modification call on both sides (fixed-time and max-pressure signals)."""
+    _need_gpu()
+    net = _net(kind)
+    prm = dict(P, signal_mode=1, mp_interval=10) if mp else P
+    dem = synth.merge_demands(synth.place_vehicles(net, 5003 if kind == "grid12x3" else 2500, seed=61 + t0,
+                                                   min_spacing=7.0, internal_frac=0.3),
+                              synth.uniform_trips(net, 400, 40, seed=62 + t0))
+    mask = netkit.closable_links(net, dem, np.random.default_rng(63 + t0), 0.3)
+    lanes = np.array(list(mask), np.int32)
+    masks = np.array([mask[int(l)] for l in lanes], np.uint32)
+    n_closed = sum(int(np.diff(net.succ_off)[l]) - bin(int(m)).count("1") for l, m in zip(lanes, masks))
+    assert n_closed > 0.2 * int(np.diff(net.succ_off)[lanes].sum())
+    sim = parity.gpu_sim(net, dem, prm)
+    st = sim.read_state()
+    st["t"] = t0
+    sim.write_state(st)
+    orc = oracle.Oracle(net, dem, prm)
+    sim.set_lane_links(lanes, masks)
+    orc.set_lane_links(lanes, masks)
+    rep = []
+    for k in range(10):
+        _, gd, gs, od, os_ = parity.step_pair(sim, orc)
+        parity.compare_step(gd, gs, od, os_, dem.n, report=rep)
+        if mp:
+            np.testing.assert_array_equal(gs["ctrl_state"], os_["ctrl_state"])
+    tot = {k: sum(r[k] for r in rep) for k in rep[0]}
+    print(kind, mp, n_closed, tot)
+    assert tot["compared"] > 0.9 * tot["active"]
+    assert sim.read_metrics(lanes=False)["err"] == 0
+
+
+def test_dynamic_lanes_reject_broken_routes_and_reopen_exactly():
+    """Closing every link of the first edge toward the second breaks the routes of vehicles
+    still to cross: MS_ERR_ROUTE and nothing changes.  Closing one lane's links forces its
+    vehicles over; reopening every link gives the same steps as a simulation never
+    modified."""
+    _need_gpu()
+    from paper_2405_12520_b300 import moss
+    net = netkit.line(3, 300.0, 2)
+    l0 = int(net.edge_lane0[0])
+    dem = netkit.vehicles([l0, l0, l0 + 1], [60.0, 120.0, 90.0], [9.0, 8.0, 10.0], [[0, 1]] * 3)
+    a = parity.gpu_sim(net, dem, P, debug=False)
+    b = parity.gpu_sim(net, dem, P, debug=False)
+    with pytest.raises(moss.MossError) as e:
+        a.set_lane_links([l0, l0 + 1], [0, 0])
+    assert e.value.code == moss.MS_ERR_ROUTE
+    a.step(3)
+    b.step(3)
+    for k in ("id", "lane", "x", "v"):
+        np.testing.assert_array_equal(a.read_state()[k], b.read_state()[k])
+    a.set_lane_links([l0], [0])          # lane 0 no longer leads on: its vehicles change over
+    a.step(40)
+    sa = a.read_state()
+    assert np.all(sa["lane"][sa["route_idx"] == 0] != l0)
+    a.set_lane_links([l0], [0b11])       # reopened
+    b.write_state(a.read_state())
+    a.step(20)
+    b.step(20)
+    for k in ("id", "lane", "x", "v", "route_idx"):
+        np.testing.assert_array_equal(a.read_state()[k], b.read_state()[k])
+    with pytest.raises(moss.MossError) as e:
+        a.set_lane_links([int(net.succ_lane[net.succ_off[l0]])], [1])   # an internal lane
+    assert e.value.code == moss.MS_ERR_ARG

@@ -813,40 +813,12 @@ def test_all_open_links_change_nothing(oracle_lib):
         np.testing.assert_array_equal(sa[k], sb[k])
 
 
-def _closable_links(net, dem, rng, frac):
-    """Links of edge lanes that can close with every route still lane-connected: a link
-    (lane l -> exit edge f) closes only if another lane of l's edge keeps an open link to f."""
-    routes = {(int(a), int(b)) for i in range(dem.n)
-              for a, b in zip(dem.route_edges[dem.route_off[i]:dem.route_off[i + 1] - 1],
-                              dem.route_edges[dem.route_off[i] + 1:dem.route_off[i + 1]])}
-    el = np.nonzero(net.lane_edge >= 0)[0]
-    mask = {int(l): (1 << int(net.succ_off[l + 1] - net.succ_off[l])) - 1 for l in el}
-    for l in rng.permutation(el):
-        l = int(l)
-        for j in range(int(net.succ_off[l + 1] - net.succ_off[l])):
-            if rng.random() >= frac:
-                continue
-            f = int(net.succ_edge[net.succ_off[l] + j])
-            e = int(net.lane_edge[l])
-            trial = dict(mask)
-            trial[l] &= ~(1 << j)
-            ok = all(any((trial[int(net.edge_lane0[a]) + q] >> jj) & 1 and
-                         int(net.succ_edge[net.succ_off[int(net.edge_lane0[a]) + q] + jj]) == b
-                         for q in range(int(net.edge_nlanes[a]))
-                         for jj in range(int(net.succ_off[int(net.edge_lane0[a]) + q + 1] -
-                                             net.succ_off[int(net.edge_lane0[a]) + q])))
-                     for a, b in routes if a == e)
-            if ok:
-                mask = trial
-    return mask
-
-
 def test_max_pressure_skips_closed_links(oracle_lib):
     """Small grid under max pressure with 30% of the closable links closed: at every step
     the controllers equal R13 restated with numpy over the open links only."""
     import oracle
     net, dem = synth.small_grid_workload(2)
-    mask = _closable_links(net, dem, np.random.default_rng(4), 0.3)
+    mask = netkit.closable_links(net, dem, np.random.default_rng(4), 0.3)
     closed = {(l, j) for l, m in mask.items() for j in range(int(net.succ_off[l + 1] - net.succ_off[l]))
               if not (m >> j) & 1}
     assert len(closed) > 20

@@ -171,7 +171,7 @@ def dist_env():
     return rank, world, local
 
 
-def variant(args, net):
+def variant(args, net, dem):
     """Model parameters and lane modifications of the run: the default rule set, or the
     max-pressure signals / threshold jitter / lane limits and closures the flags ask for."""
     import numpy as np
@@ -187,16 +187,33 @@ def variant(args, net):
         rng = np.random.default_rng(args.seed + 77)
         lim = np.nonzero(rng.random(net.n_lanes) < args.lane_mods)[0].astype(np.int32)
         shut = np.nonzero(rng.random(net.n_lanes) < args.lane_mods / 10)[0].astype(np.int32)
-        mods = (lim, rng.uniform(8.0, 14.0, lim.size).astype(np.float32), shut)
+        mods = (lim, rng.uniform(8.0, 14.0, lim.size).astype(np.float32), shut, None)
         desc["lane_mods"] = f"{lim.size} lanes limited to U[8,14] m/s, {shut.size} closed"
+    if args.closed_links > 0:
+        m = synth.closable_link_masks(net, dem, np.random.default_rng(args.seed + 78), args.closed_links)
+        lanes = np.array(list(m), np.int32)
+        masks = np.array([m[int(l)] for l in lanes], np.uint32)
+        n_all = int(np.diff(net.succ_off)[lanes].sum())
+        n_closed = n_all - sum(bin(int(x)).count("1") for x in masks)
+        lim, vmax, shut = (mods[:3] if mods is not None else (np.zeros(0, np.int32), np.zeros(0, np.float32),
+                                                               np.zeros(0, np.int32)))
+        mods = (lim, vmax, shut, (lanes, masks))
+        desc["lane_links"] = f"{n_closed} of {n_all} lane links closed, every route still lane-connected"
     return params, mods, desc
 
 
 def apply_mods(side, mods):
+    """Lane limits and closures, then lane links; returns the seconds the calls took."""
+    t0 = time.perf_counter()
     if mods is not None:
-        lim, vmax, shut = mods
-        side.set_lane_limits(lim, vmax=vmax)
-        side.set_lane_limits(shut, closed=[1] * len(shut))
+        lim, vmax, shut, links = mods
+        if len(lim):
+            side.set_lane_limits(lim, vmax=vmax)
+        if len(shut):
+            side.set_lane_limits(shut, closed=[1] * len(shut))
+        if links is not None:
+            side.set_lane_links(*links)
+    return time.perf_counter() - t0
 
 
 def cpu_baseline(net, dem, params, budget_s: float = 20.0, max_steps: int = 10, mods=None):
@@ -224,7 +241,7 @@ def run_reference(args):
         return
     from paper_2405_12520_b300 import synth
     net, dem, desc = workload(args.workload, args.seed)
-    p, mods, vdesc = variant(args, net)
+    p, mods, vdesc = variant(args, net, dem)
     k = max(1, min(args.steps, args.ref_steps))
     val, steps, el = cpu_baseline(net, dem, p, budget_s=1e9, max_steps=k, mods=mods)
     line = {
@@ -250,12 +267,14 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     net, dem, desc = workload(args.workload, args.seed + rank)
-    params, mods, vdesc = variant(args, net)
+    params, mods, vdesc = variant(args, net, dem)
     stream = torch.cuda.current_stream()
     sim = moss.Sim(params, stream=stream, n_windows=1, block=args.block)
     sim.load_network(net)
     sim.add_vehicles(dem)
-    apply_mods(sim, mods)
+    mod_s = apply_mods(sim, mods)
+    if mods is not None and mods[3] is not None:
+        vdesc["lane_links_call_s"] = round(mod_s, 3)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def barrier():
@@ -661,6 +680,8 @@ def main():
     ap.add_argument("--th-jitter", type=float, default=0.0, help="per-trip MOBIL threshold jitter (m/s^2)")
     ap.add_argument("--lane-mods", type=float, default=0.0,
                     help="fraction of lanes given a speed limit (a tenth as many are closed)")
+    ap.add_argument("--closed-links", type=float, default=0.0,
+                    help="fraction of lane links closed (dynamic lanes; routes stay connected)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -860,3 +860,39 @@ def small_grid_workload(seed: int = 1):
 def large_grid_network():
     """100x100 signalised grid, 3 lanes per direction, 300 m links, green-wave offsets."""
     return grid_network(100, 100, 3, 300.0, 30, 3, "wave")
+
+
+def closable_link_masks(net: Network, dem: Demand, rng, frac: float) -> dict:
+    """Open-link masks per edge lane with about frac of the links closed, every route still
+    lane-connected: a link closes only if each pair of consecutive route edges leaving its
+    edge keeps an open link from some lane of that edge."""
+    re = np.asarray(dem.route_edges, np.int64)
+    last = np.zeros(re.shape[0], bool)   # route entries that end a route (no pair after them)
+    last[np.asarray(dem.route_off[1:], np.int64) - 1] = True
+    idx = np.nonzero(~last[:-1])[0]
+    pairs = np.unique(re[idx] * net.n_edges + re[idx + 1])
+    exits = {}
+    for pr in pairs.tolist():
+        exits.setdefault(pr // net.n_edges, set()).add(pr % net.n_edges)
+    el = np.nonzero(net.lane_edge >= 0)[0]
+    deg = {int(l): int(net.succ_off[l + 1] - net.succ_off[l]) for l in el}
+    mask = {l: (1 << d) - 1 for l, d in deg.items()}
+
+    def connected(e, b):
+        for q in range(int(net.edge_nlanes[e])):
+            l = int(net.edge_lane0[e]) + q
+            for j in range(deg[l]):
+                if (mask[l] >> j) & 1 and int(net.succ_edge[net.succ_off[l] + j]) == b:
+                    return True
+        return False
+
+    for l in rng.permutation(el):
+        l = int(l)
+        e = int(net.lane_edge[l])
+        for j in range(deg[l]):
+            if rng.random() >= frac:
+                continue
+            mask[l] &= ~(1 << j)
+            if not all(connected(e, b) for b in exits.get(e, ())):
+                mask[l] |= 1 << j
+    return mask

@@ -86,33 +86,4 @@ def vehicles(lanes, xs, vs, routes, v0=13.9, t_dep=None) -> synth.Demand:
 
 
 def closable_links(net, dem, rng, frac):
-    """Open-link masks per edge lane with about frac of the links closed, every route still
-    lane-connected: a link closes only if each pair of consecutive route edges leaving its
-    edge keeps an open link from some lane of that edge."""
-    exits = {}
-    for i in range(dem.n):
-        r = dem.route_edges[dem.route_off[i]:dem.route_off[i + 1]]
-        for a, b in zip(r[:-1], r[1:]):
-            exits.setdefault(int(a), set()).add(int(b))
-    el = np.nonzero(net.lane_edge >= 0)[0]
-    deg = {int(l): int(net.succ_off[l + 1] - net.succ_off[l]) for l in el}
-    mask = {l: (1 << d) - 1 for l, d in deg.items()}
-
-    def connected(e, b):
-        for q in range(int(net.edge_nlanes[e])):
-            l = int(net.edge_lane0[e]) + q
-            for j in range(deg[l]):
-                if (mask[l] >> j) & 1 and int(net.succ_edge[net.succ_off[l] + j]) == b:
-                    return True
-        return False
-
-    for l in rng.permutation(el):
-        l = int(l)
-        e = int(net.lane_edge[l])
-        for j in range(deg[l]):
-            if rng.random() >= frac:
-                continue
-            mask[l] &= ~(1 << j)
-            if not all(connected(e, b) for b in exits.get(e, ())):
-                mask[l] |= 1 << j
-    return mask
+    return synth.closable_link_masks(net, dem, rng, frac)

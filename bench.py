@@ -40,8 +40,23 @@ B_BUCKET_VEH = 4     # streams the 4-byte result code of every vehicle
 B_BUCKET_MOVER = 36  # per arrival: x, x', id, slot reads + the 16-B bucket record
 
 
+def reduce_over_ranks(total_ms: float, units: float, device: str):
+    """Replicas: the job's time is the slowest rank's, its work the sum over ranks."""
+    import torch
+    import torch.distributed as dist
+    mx = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    sm = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[0])
+
+
 def workload(name: str, seed: int):
     from paper_2405_12520_b300 import synth
+    if name == "small":   # the small plain-method configuration (reference arm and tests)
+        net, dem = synth.small_grid_workload(seed)
+        return net, dem, ("4x4 grid, 2 lanes/direction, 200 m links, fixed-time signals; 500 trips "
+                          "with uniform OD edges departing over 600 s")
     if name == "grid1m":
         net = synth.large_grid_network()
         # 1M vehicles on the network at t = 0 plus a Poisson inflow of gravity-OD trips
@@ -305,12 +320,7 @@ def run_ours(args):
     vsteps = float(sum(per_step))
     total_ms = float(sum(ms))
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms, vsteps], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_ms, vsteps = float(mx[0]), float(t[1])
+        total_ms, vsteps = reduce_over_ranks(total_ms, vsteps, "cuda")
     value = vsteps / (total_ms * 1e-3)
 
     # per-kernel device time (kernel-by-kernel launches, L2 flushed before each step)

@@ -143,3 +143,70 @@ def gravity_trips(net, zone_edge, attract, gamma, n, t_span, seed, splitmix64):
         o[k], de[k] = zone_edge[i], zone_edge[j]
         td[k] = (_u24(splitmix64, seed, SALT_TIME, k) * int(t_span)) >> 24
     return o, de, td
+
+
+# ---------------------------------------------------------------------------------------
+# R18  Radiation OD sampling (Simini, Gonzalez, Maritan and Barabasi 2012, "A universal
+#      model for mobility and migration patterns").  Zone z has a representative edge and a
+#      population m_z > 0.  The origin draw is R16's with the populations as attractions.
+#      For origin i, with d_ij the route cost from zone i's edge to zone j's (R15, mm) and
+#      s_ij the population of the zones strictly closer to i than j (neither i nor j), the
+#      destination weight of j != i is
+#          w_ij = (m_i * m_j) / ((m_i + s_ij) * ((m_i + m_j) + s_ij)),
+#      0 if j is unreachable.  s_ij is the float32 running sum of populations over the zones
+#      in order of (d_ik, k), i excluded, taken before the first zone at distance d_ij; every
+#      operation is one IEEE float32 operation in the order written.  Destination and
+#      departure draws are R16's (same salts, cumulative weights in index order).
+# ---------------------------------------------------------------------------------------
+
+def radiation_weights(cost, pop):
+    """w[i, j] of R18 from the zone-to-zone route costs cost[i, j] (inf: unreachable)."""
+    m = np.asarray(pop, np.float32)
+    Z = m.shape[0]
+    W = np.zeros((Z, Z), np.float32)
+    for i in range(Z):
+        d = np.where(np.isfinite(cost[i]), cost[i], np.inf)
+        order = np.lexsort((np.arange(Z), d))           # by (distance, zone index)
+        assert order[0] == i or not np.isfinite(d[order[0]]) or d[order[0]] > 0
+        run = np.float32(0.0)
+        s = np.zeros(Z, np.float32)
+        q = 0
+        while q < Z:                                     # groups of equal distance
+            r = q
+            while r < Z and d[order[r]] == d[order[q]]:
+                r += 1
+            for k in order[q:r]:
+                s[k] = run                               # zones strictly closer
+            for k in order[q:r]:
+                if k != i:
+                    run = np.float32(run + m[k])
+            q = r
+        for j in range(Z):
+            if j == i or not np.isfinite(d[j]):
+                continue
+            num = np.float32(m[i] * m[j])
+            den = np.float32(np.float32(m[i] + s[j]) * np.float32(np.float32(m[i] + m[j]) + s[j]))
+            W[i, j] = np.float32(num / den)
+    return W
+
+
+def radiation_trips(net, zone_edge, pop, n, t_span, seed, splitmix64):
+    """Trips (orig_edge, dest_edge, t_dep) of R18."""
+    zone_edge = np.asarray(zone_edge, np.int64)
+    m = np.asarray(pop, np.float32)
+    d = distances_to(net, zone_edge)            # [Z dest, E]
+    cost = d[:, zone_edge].T                    # cost[i, j] = zone i -> zone j
+    W = radiation_weights(cost, m)
+    cdf_o = np.cumsum(m, dtype=np.float32)
+    cdf_d = np.cumsum(W, axis=1, dtype=np.float32)
+    o = np.zeros(n, np.int32)
+    de = np.zeros(n, np.int32)
+    td = np.zeros(n, np.int32)
+    for k in range(n):
+        uo = np.float32(_u24(splitmix64, seed, SALT_ORIGIN, k)) * np.float32(2.0 ** -24)
+        i = _first_above(cdf_o, np.float32(uo * cdf_o[-1]))
+        ud = np.float32(_u24(splitmix64, seed, SALT_DEST, k)) * np.float32(2.0 ** -24)
+        j = _first_above(cdf_d[i], np.float32(ud * cdf_d[i, -1])) if cdf_d[i, -1] > 0 else i
+        o[k], de[k] = zone_edge[i], zone_edge[j]
+        td[k] = (_u24(splitmix64, seed, SALT_TIME, k) * int(t_span)) >> 24
+    return o, de, td

@@ -144,3 +144,57 @@ def test_gravity_decays_with_route_distance():
     p = w / w.sum()
     f = np.array([(d[sel] == z).mean() for z in zones])
     assert np.all(np.abs(f - p) <= 4 * np.sqrt(p * (1 - p) / sel.sum()) + 1e-12)
+
+
+def test_radiation_weights_closed_form_on_a_line():
+    """R18 with equal populations m: the k-th closest zone (no ties) has
+    w = m^2 / ((m + (k-1) m)(2m + (k-1) m)) = 1 / (k (k + 1)); with unequal populations the
+    weights from the line's end follow the formula with s = the populations in between."""
+    net = netkit.line(10, 500.0, 1)
+    zones = np.array([0, 2, 4, 6, 8], np.int64)
+    cost = routing.distances_to(net, zones)[:, zones].T
+    W = routing.radiation_weights(cost, np.full(5, 3.0, np.float32))
+    k = np.arange(1, 5)
+    np.testing.assert_allclose(W[0, 1:], 1.0 / (k * (k + 1)), rtol=1e-6)
+    assert W[0, 0] == 0
+    m = np.array([2.0, 1.0, 4.0, 0.5, 3.0], np.float32)
+    W = routing.radiation_weights(cost, m)
+    m64 = m.astype(np.float64)
+    for j in range(1, 5):
+        s = m64[1:j].sum()
+        want = m64[0] * m64[j] / ((m64[0] + s) * (m64[0] + m64[j] + s))
+        assert W[0, j] == pytest.approx(want, rel=1e-6)
+    # ties: zones at equal distance count for neither; unreachable zones for nobody
+    c = np.full((5, 5), 7.0)
+    np.fill_diagonal(c, 0.0)
+    c[0] = [0.0, 5.0, 5.0, 9.0, np.inf]
+    mm = np.array([1.0, 2.0, 3.0, 4.0, 8.0], np.float32)
+    W = routing.radiation_weights(c, mm)
+    want = [0.0, 1 * 2 / ((1 + 0) * (1 + 2 + 0)), 1 * 3 / ((1 + 0) * (1 + 3 + 0)),
+            1 * 4 / ((1 + 5) * (1 + 4 + 5)), 0.0]
+    np.testing.assert_allclose(W[0], want, rtol=1e-6)
+
+
+def test_radiation_sampling_follows_the_weights_and_is_scale_free():
+    """Sampled destinations of one origin follow the normalised weights (4 binomial standard
+    deviations); scaling every population by 2^3 (exact in float32) or every road length by 2
+    (same distance ranks) draws exactly the same trips: the model has no free parameter and
+    uses distances only through their order."""
+    net = netkit.line(10, 500.0, 1)
+    zones = np.array([0, 2, 4, 6, 8], np.int64)
+    m = np.array([2.0, 1.0, 4.0, 0.5, 3.0], np.float32)
+    n = 8000
+    o, d, t = routing.radiation_trips(net, zones, m, n, 600, 31, _sm)
+    cost = routing.distances_to(net, zones)[:, zones].T
+    W = routing.radiation_weights(cost, m).astype(np.float64)
+    sel = o == zones[0]
+    p = W[0] / W[0].sum()
+    f = np.array([(d[sel] == z).mean() for z in zones])
+    assert np.all(np.abs(f - p) <= 4 * np.sqrt(p * (1 - p) / sel.sum()) + 1e-12)
+    o2, d2, t2 = routing.radiation_trips(net, zones, m * np.float32(8.0), n, 600, 31, _sm)
+    np.testing.assert_array_equal(d, d2)
+    np.testing.assert_array_equal(o, o2)
+    net2 = netkit.line(10, 1000.0, 1)
+    o3, d3, t3 = routing.radiation_trips(net2, zones, m, n, 600, 31, _sm)
+    np.testing.assert_array_equal(d, d3)
+    np.testing.assert_array_equal(t, t3)

@@ -646,6 +646,11 @@ def run_routes(args):
         ts += t1 - t0
         tr += t2 - t1
     ts, tr = ts / reps, tr / reps
+    # the radiation model on the same zones (populations = the attractions), sampling only
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ro, rd, rt = sim.sample_trips_radiation(zones, A, n, 3600, args.seed)
+    t_rad = time.perf_counter() - t0
     line = {
         "metric": "trips/s", "value": n / (ts + tr), "unit": "trips/s", "n_gpus": world, "steps": reps,
         "warmup": 1, "ms_per_step": 1e3 * (ts + tr), "higher_is_better": True, "scaling": "weak",
@@ -654,7 +659,7 @@ def run_routes(args):
                    "100x100 grid, A ~ LogNormal(0,1), gamma 2, departures over 3600 s) sampled by "
                    "ms_sample_trips, then routed by ms_route_trips; one of each per repetition",
                    "sample_ms": 1e3 * ts, "route_ms": 1e3 * tr, "route_edges": int(edges.size),
-                   "unreachable": bad},
+                   "unreachable": bad, "radiation_sample_ms": 1e3 * t_rad},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle

@@ -357,6 +357,20 @@ int ms_route_trips(void *sim, int n, const int *orig_edge, const int *dest_edge,
 int ms_sample_trips(void *sim, int n_zones, const int *zone_edge, const float *attract, int gamma, int n,
                     int t_span, uint64_t seed, int *orig_edge, int *dest_edge, int *t_dep);
 
+/* Radiation OD sampling (the radiation model of Simini, Gonzalez, Maritan and Barabasi
+   2012, a baseline the paper's OD generator offers beside gravity, Sec. III-B): as
+   ms_sample_trips with population[z] > 0 in place of the attractions for the origin draw,
+   and destination weights w_ij = (m_i m_j) / ((m_i + s_ij)((m_i + m_j) + s_ij)) for
+   reachable j != i, s_ij = the population of the zones strictly closer to i than j by route
+   cost (i and j excluded; zones at equal cost count for neither), summed in float32 in
+   order of (cost, zone index).  Every weight operation is one IEEE float32 operation in
+   that order, so a float32 CPU computation draws the same trips.  The model has no free
+   parameter and uses route costs only through their order.  At most 4096 zones; a
+   zone-to-zone cost of 2^40 mm or more: MS_ERR_CAPACITY.  Allocates and frees its own
+   device memory; synchronises. */
+int ms_sample_trips_radiation(void *sim, int n_zones, const int *zone_edge, const float *population, int n,
+                              int t_span, uint64_t seed, int *orig_edge, int *dest_edge, int *t_dep);
+
 /* Counters of the learned decision since the model was set: [0] candidates, [1] rule
    fallbacks (low margin), [2] agreements with the rule, [3 + 3*rule + final] confusion. */
 int ms_read_lc_stats(void *sim, int64_t *out12);

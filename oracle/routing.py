@@ -165,28 +165,20 @@ def radiation_weights(cost, pop):
     Z = m.shape[0]
     W = np.zeros((Z, Z), np.float32)
     for i in range(Z):
-        d = np.where(np.isfinite(cost[i]), cost[i], np.inf)
-        order = np.lexsort((np.arange(Z), d))           # by (distance, zone index)
-        assert order[0] == i or not np.isfinite(d[order[0]]) or d[order[0]] > 0
-        run = np.float32(0.0)
-        s = np.zeros(Z, np.float32)
-        q = 0
-        while q < Z:                                     # groups of equal distance
-            r = q
-            while r < Z and d[order[r]] == d[order[q]]:
-                r += 1
-            for k in order[q:r]:
-                s[k] = run                               # zones strictly closer
-            for k in order[q:r]:
-                if k != i:
-                    run = np.float32(run + m[k])
-            q = r
-        for j in range(Z):
-            if j == i or not np.isfinite(d[j]):
-                continue
-            num = np.float32(m[i] * m[j])
-            den = np.float32(np.float32(m[i] + s[j]) * np.float32(np.float32(m[i] + m[j]) + s[j]))
-            W[i, j] = np.float32(num / den)
+        d = np.asarray(cost[i], np.float64)
+        order = np.lexsort((np.arange(Z), d))                 # by (distance, zone index)
+        ds = d[order]
+        # running float32 sum of the populations in that order, zone i contributing nothing
+        run = np.cumsum(np.where(order == i, np.float32(0.0), m[order]), dtype=np.float32)
+        start = np.r_[0, np.nonzero(ds[1:] != ds[:-1])[0] + 1]   # first position of each
+        grp = np.searchsorted(start, np.arange(Z), side="right") - 1   # equal-distance group
+        before = np.where(start[grp] > 0, run[np.maximum(start[grp] - 1, 0)], np.float32(0.0))
+        s_ij = np.empty(Z, np.float32)
+        s_ij[order] = before                                  # zones strictly closer
+        ok = (np.arange(Z) != i) & np.isfinite(d)
+        num = m[i] * m                                        # float32 elementwise, IEEE
+        den = (m[i] + s_ij) * ((m[i] + m) + s_ij)
+        W[i] = np.where(ok, num / np.where(ok, den, np.float32(1.0)), np.float32(0.0))
     return W
 
 

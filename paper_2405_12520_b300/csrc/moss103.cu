@@ -1664,14 +1664,14 @@ int ms_route_trips(void *sim, int n, const int *orig_edge, const int *dest_edge,
   return MS_OK;
 }
 
-int ms_sample_trips(void *sim, int n_zones, const int *zone_edge, const float *attract, int gamma, int n,
-                    int t_span, uint64_t seed, int *orig_edge, int *dest_edge, int *t_dep) {
-  Sim *s = (Sim *)sim;
+// OD sampling shared by the gravity (gamma 0..3) and radiation (gamma < 0) models
+static int sample_trips(Sim *s, int n_zones, const int *zone_edge, const float *attract, int gamma, int n,
+                        int t_span, uint64_t seed, int *orig_edge, int *dest_edge, int *t_dep) {
   if (!s || n_zones <= 0 || !zone_edge || !attract || n < 0 || (n > 0 && (!orig_edge || !dest_edge || !t_dep)))
     return MS_ERR_ARG;
   if (!s->net_loaded) return fail(s, MS_ERR_STATE, "load the network first");
   if (n_zones > 4096) return fail(s, MS_ERR_CAPACITY, "at most 4096 zones");
-  if (gamma < 0 || gamma > 3 || t_span <= 0) return fail(s, MS_ERR_ARG, "gamma must be in 0..3 and t_span > 0");
+  if (gamma > 3 || t_span <= 0) return fail(s, MS_ERR_ARG, "gamma must be in 0..3 and t_span > 0");
   {
     std::vector<int> z(zone_edge, zone_edge + n_zones);
     std::sort(z.begin(), z.end());
@@ -1716,8 +1716,29 @@ int ms_sample_trips(void *sim, int n_zones, const int *zone_edge, const float *a
     release();
     return fail(s, MS_ERR_CUDA, "route distances did not converge");
   }
-  k_od_cdf<<<(n_zones + 127) / 128, 128, 0, st>>>(d, B, dz, da, n_zones, gamma, cdf_d, cdf_o);
-  RCK(cudaGetLastError());
+  if (gamma >= 0) {
+    k_od_cdf<<<(n_zones + 127) / 128, 128, 0, st>>>(d, B, dz, da, n_zones, gamma, cdf_d, cdf_o);
+    RCK(cudaGetLastError());
+  } else {
+    int P = 1;
+    while (P < n_zones) P <<= 1;
+    const size_t smem = 8 * (size_t)P + 8 * (size_t)n_zones;
+    static bool attr = false;
+    if (!attr) {
+      RCK(cudaFuncSetAttribute(k_od_radiation_cdf, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * 4096 + 8 * 4096));
+      attr = true;
+    }
+    RCK(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    k_od_radiation_cdf<<<n_zones, OD_RAD_THREADS, smem, st>>>(d, B, dz, da, n_zones, P, cdf_d, cdf_o, flag);
+    RCK(cudaGetLastError());
+    int far = 0;
+    RCK(cudaMemcpyAsync(&far, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RCK(cudaStreamSynchronize(st));
+    if (far) {
+      release();
+      return fail(s, MS_ERR_CAPACITY, "a zone-to-zone route cost of 2^40 mm or more");
+    }
+  }
   if (n > 0) {
     k_od_sample<<<(n + 255) / 256, 256, 0, st>>>(cdf_d, cdf_o, dz, n_zones, n, t_span, seed, dout, dout + n,
                                                  dout + 2 * (size_t)n);
@@ -1730,6 +1751,19 @@ int ms_sample_trips(void *sim, int n_zones, const int *zone_edge, const float *a
   release();
 #undef RCK
   return MS_OK;
+}
+
+int ms_sample_trips(void *sim, int n_zones, const int *zone_edge, const float *attract, int gamma, int n,
+                    int t_span, uint64_t seed, int *orig_edge, int *dest_edge, int *t_dep) {
+  Sim *s = (Sim *)sim;
+  if (s && gamma < 0) return fail(s, MS_ERR_ARG, "gamma must be in 0..3 and t_span > 0");
+  return sample_trips(s, n_zones, zone_edge, attract, gamma, n, t_span, seed, orig_edge, dest_edge, t_dep);
+}
+
+int ms_sample_trips_radiation(void *sim, int n_zones, const int *zone_edge, const float *population, int n,
+                              int t_span, uint64_t seed, int *orig_edge, int *dest_edge, int *t_dep) {
+  return sample_trips((Sim *)sim, n_zones, zone_edge, population, -1, n, t_span, seed, orig_edge, dest_edge,
+                      t_dep);
 }
 
 int ms_set_lane_limits(void *sim, int n, const int *lanes, const float *vmax, const int *closed) {

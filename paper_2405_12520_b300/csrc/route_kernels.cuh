@@ -131,6 +131,100 @@ __global__ void k_od_cdf(const long long *d, int B, const int *zone_edge, const 
   }
 }
 
+// Radiation OD weights (Simini et al. 2012): block i handles origin zone i.  The zones are
+// sorted by (route cost from zone i, zone index) with a bitonic sort in shared memory (cost
+// and index packed into one 64-bit key; unreachable zones last); one thread then walks the
+// sorted order, giving every zone s = the float32 running sum of the populations of the
+// zones strictly closer (i excluded, equal costs in one group), and the block forms
+// w_ij = (m_i m_j) / ((m_i + s_ij)((m_i + m_j) + s_ij)) with IEEE float32 operations; the
+// cumulative weights in index order follow (as for the gravity model), and block 0 also
+// writes the origin CDF of the populations.  Shared memory: 8 P + 8 Z bytes (P = Z rounded
+// up to a power of two).  A reachable cost of 2^40 mm or more sets *err (never expected).
+constexpr int OD_RAD_THREADS = 1024;
+constexpr unsigned long long OD_RAD_FAR = (1ull << 40) - 1;
+
+__global__ void __launch_bounds__(OD_RAD_THREADS) k_od_radiation_cdf(const long long *d, int B, const int *zone_edge,
+                                                                     const float *pop, int Z, int P, float *cdf_d,
+                                                                     float *cdf_o, int *err) {
+  extern __shared__ __align__(16) unsigned char rsm[];
+  unsigned long long *key = reinterpret_cast<unsigned long long *>(rsm);
+  float *m = reinterpret_cast<float *>(key + P);
+  float *sc = m + Z;
+  const int i = blockIdx.x;
+  const long long row = (long long)zone_edge[i] * B;   // costs from zone i's edge
+  for (int k = threadIdx.x; k < P; k += blockDim.x) {
+    unsigned long long kk = ~0ull;   // padding sorts last
+    if (k < Z) {
+      const long long c = d[row + k];
+      unsigned long long cd = OD_RAD_FAR;
+      if (c < ROUTE_INF) {
+        if ((unsigned long long)c >= OD_RAD_FAR) atomicOr(err, 1);
+        cd = (unsigned long long)c < OD_RAD_FAR ? (unsigned long long)c : OD_RAD_FAR - 1;
+      }
+      kk = (cd << 12) | (unsigned long long)k;
+      m[k] = pop[k];
+    }
+    key[k] = kk;
+  }
+  __syncthreads();
+  for (int w = 2; w <= P; w <<= 1)
+    for (int j = w >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < P; t += blockDim.x) {
+        const int u = t ^ j;
+        if (u > t) {
+          const unsigned long long a = key[t], b = key[u];
+          if ((a > b) == ((t & w) == 0)) {
+            key[t] = b;
+            key[u] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  if (threadIdx.x == 0) {
+    float run = 0.f;
+    int q = 0;
+    while (q < Z) {   // groups of equal cost
+      const unsigned long long cq = key[q] >> 12;
+      int r = q;
+      while (r < Z && (key[r] >> 12) == cq) ++r;
+      for (int x = q; x < r; ++x) sc[(int)(key[x] & 0xfff)] = run;
+      for (int x = q; x < r; ++x) {
+        const int k = (int)(key[x] & 0xfff);
+        if (k != i) run = __fadd_rn(run, m[k]);
+      }
+      q = r;
+    }
+  }
+  __syncthreads();
+  const float mi = m[i];
+  float *out = cdf_d + (long long)i * Z;
+  for (int j = threadIdx.x; j < Z; j += blockDim.x) {   // weights first, then the running sum
+    float w = 0.f;
+    if (j != i && d[row + j] < ROUTE_INF) {
+      const float num = __fmul_rn(mi, m[j]);
+      const float den = __fmul_rn(__fadd_rn(mi, sc[j]), __fadd_rn(__fadd_rn(mi, m[j]), sc[j]));
+      w = __fdiv_rn(num, den);
+    }
+    out[j] = w;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float acc = 0.f;
+    for (int j = 0; j < Z; ++j) {
+      acc = __fadd_rn(acc, out[j]);
+      out[j] = acc;
+    }
+    if (i == 0) {
+      float ao = 0.f;
+      for (int z = 0; z < Z; ++z) {
+        ao = __fadd_rn(ao, m[z]);
+        cdf_o[z] = ao;
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ unsigned long long od_mix(unsigned long long z) {   // SplitMix64
   z += 0x9E3779B97F4A7C15ULL;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;

@@ -19,7 +19,7 @@ ERR_NAMES = {0: "OK", -1: "ARG", -2: "ROUTE", -3: "CAPACITY", -4: "CUDA", -5: "D
 SYMBOLS = ("ms_create", "ms_load_network", "ms_add_vehicles", "ms_step", "ms_step_timed", "ms_step_noalloc",
            "ms_load_network_batch", "ms_add_vehicles_batch", "ms_batch_offsets", "ms_autotune",
            "ms_set_lc_log", "ms_set_lc_model", "ms_set_lane_limits", "ms_set_lane_links", "ms_route_trips",
-           "ms_sample_trips",
+           "ms_sample_trips", "ms_sample_trips_radiation",
            "ms_read_lc_stats",
            "ms_mlp_train_step",
            "ms_mlp_grad",
@@ -97,6 +97,7 @@ def load():
         lib.ms_set_lane_links.argtypes = [vp, C.c_int, vp, vp]
         lib.ms_route_trips.argtypes = [vp, C.c_int, vp, vp, vp, vp, C.c_int64, vp]
         lib.ms_sample_trips.argtypes = [vp, C.c_int, vp, vp, C.c_int, C.c_int, C.c_int, C.c_uint64, vp, vp, vp]
+        lib.ms_sample_trips_radiation.argtypes = [vp, C.c_int, vp, vp, C.c_int, C.c_int, C.c_uint64, vp, vp, vp]
         lib.ms_read_lc_stats.argtypes = [vp, vp]
         lib.ms_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, C.c_int, C.c_float, vp, vp, vp, vp]
         lib.ms_mlp_grad.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, vp, vp]
@@ -389,6 +390,18 @@ class Sim:
         t = np.zeros(n, np.int32)
         self._check(self.lib.ms_sample_trips(self.h, int(z.shape[0]), _p(z), _p(a), int(gamma), int(n), int(t_span),
                                              int(seed) & 0xFFFFFFFFFFFFFFFF, _p(o), _p(d), _p(t)), "ms_sample_trips")
+        return o, d, t
+
+    def sample_trips_radiation(self, zone_edge, population, n: int, t_span: int, seed: int):
+        """Radiation OD sampling (GPU): returns (orig_edge, dest_edge, t_dep) int32 arrays."""
+        z = np.ascontiguousarray(zone_edge, np.int32)
+        m = np.ascontiguousarray(population, np.float32)
+        o = np.zeros(n, np.int32)
+        d = np.zeros(n, np.int32)
+        t = np.zeros(n, np.int32)
+        self._check(self.lib.ms_sample_trips_radiation(self.h, int(z.shape[0]), _p(z), _p(m), int(n), int(t_span),
+                                                       int(seed) & 0xFFFFFFFFFFFFFFFF, _p(o), _p(d), _p(t)),
+                    "ms_sample_trips_radiation")
         return o, d, t
 
     def route_trips(self, orig, dest, capacity: int | None = None):

@@ -131,3 +131,27 @@ def test_gravity_sampling_with_an_isolated_zone_and_into_a_simulation():
     sim.step(600)
     sim.sync()
     assert sim.read_metrics(lanes=False)["err"] == 0
+
+
+@pytest.mark.parametrize("kind,n_zones", [("grid", 64), ("delaunay", 300), ("grid", 4096)])
+def test_radiation_sampling_matches_the_reference(kind, n_zones):
+    """ms_sample_trips_radiation draws the same trips as the CPU reference (R18), bit for
+    bit: a 12x12 grid (many equal route costs, so tie groups matter), an irregular network,
+    and the 4096-zone maximum (a full-width bitonic sort per origin)."""
+    import oracle
+    if kind == "grid":
+        net = synth.grid_network(12, 12, 3, 200.0, 30, 3, "wave") if n_zones <= 64 else \
+            synth.grid_network(40, 40, 2, 200.0, 30, 3, "wave")
+    else:
+        net = synth.delaunay_network(400, box=8000.0, seed=5)
+    rng = np.random.default_rng(n_zones)
+    zones = rng.choice(net.n_edges, n_zones, replace=False).astype(np.int32)
+    m = rng.lognormal(0.0, 1.0, n_zones).astype(np.float32)
+    s = _sim(net)
+    n = 20000 if n_zones <= 300 else 5000
+    o, d, t = s.sample_trips_radiation(zones, m, n, 900, 4321)
+    ro, rd, rt = routing.radiation_trips(net, zones, m, n, 900, 4321, oracle.splitmix64)
+    np.testing.assert_array_equal(o, ro)
+    np.testing.assert_array_equal(d, rd)
+    np.testing.assert_array_equal(t, rt)
+    assert len(np.unique(d)) > min(20, n_zones // 4)

@@ -540,6 +540,24 @@ def run_learned(args):
                 row = sum(st[f"conf_{rn}{f}"] for f in "slr")
                 out[name][f"agree_{rn}"] = st[f"conf_{rn}{rn}"] / max(1, row)
         sim.destroy()
+    # per-lane 5-minute mean speeds: both rules from the same start over the first 300-step
+    # window, compared on lanes with at least 300 vehicle-steps in both runs
+    win = {}
+    for name in ("rule", "learned"):
+        sim = moss.Sim(params, stream=stream, n_windows=1)
+        sim.load_network(net)
+        sim.add_vehicles(dem)
+        if name == "learned":
+            sim.set_lc_model(theta, 0.2)
+        sim.step(int(params["window"]))
+        m = sim.read_metrics()
+        win[name] = (m["vsum"][0].astype(np.float64), m["vcnt"][0].astype(np.float64))
+        sim.destroy()
+    (gv, gc), (rv, rc) = win["learned"], win["rule"]
+    busy = (gc >= 300) & (rc >= 300)
+    rel = np.abs(gv[busy] / gc[busy] - rv[busy] / rc[busy]) / np.maximum(rv[busy] / rc[busy], 1e-6)
+    lane_err = {"lanes": int(busy.sum()), "mean_rel": float(rel.mean()), "p90_rel": float(np.quantile(rel, 0.9)),
+                "window_s": int(params["window"])}
     L = out["learned"]
     line = {
         "metric": "vehicle-steps/s", "value": L["value"], "unit": "vehicle-steps/s", "n_gpus": world,
@@ -554,6 +572,7 @@ def run_learned(args):
         "learned": L, "rule": out["rule"],
         "learned_vs_rule": L["value"] / out["rule"]["value"],
         "mean_speed_rel_diff": abs(L["mean_speed"] - out["rule"]["mean_speed"]) / out["rule"]["mean_speed"],
+        "lane_mean_speed_error": lane_err,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -504,7 +504,13 @@ def run_learned(args):
     t_collect = time.perf_counter() - t0
     cw, cnt = learned.class_weights(y)
     theta, info = learned.train(x, y, epochs=10, batch=4096, lr=2e-3, seed=1, class_w=cw)
-    net, dem, desc = workload("grid1m", args.seed)
+    if args.workload == "learned5m":   # the same network at 5M vehicles (near jam density)
+        net = synth.large_grid_network()
+        dem = synth.place_vehicles(net, 5_000_000, seed=args.seed, min_spacing=6.0)
+        desc = ("large grid 100x100, 3 lanes/direction, 300 m links, green-wave fixed-time signals; "
+                "5,000,000 vehicles pre-placed (fronts >= 6 m apart), gravity-OD routes, v0~N(13.9,1.5)")
+    else:
+        net, dem, desc = workload("grid1m", args.seed)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     out = {}
@@ -564,7 +570,7 @@ def run_learned(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": L["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 state, bf16 MLP operands / f32 accumulate",
         "data": "synthetic", "gpu_launches": STEP_LAUNCHES * args.steps,
-        "config": {"workload": "learned1m", "description": desc + "; lane-change decisions by the learned MLP",
+        "config": {"workload": args.workload, "description": desc + "; lane-change decisions by the learned MLP",
                    "l2": "flushed (256 MiB write) before every timed step; each step timed alone",
                    "train": {"samples": int(x.shape[0]), "class_counts": cnt.tolist(), "seeds": args.train_seeds,
                              "collect_s": round(t_collect, 1), "adam_steps": info["steps"],

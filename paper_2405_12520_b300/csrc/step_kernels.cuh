@@ -684,35 +684,39 @@ __device__ __forceinline__ void vehicle_move(const StepArgs &a, Upd &u, const VC
     d = dmax;
     vn = fminf(vn, d / P.dt);
   }
+  // the lane end is tested as d > len - x (len - x is exact when x >= len / 2) and a
+  // transferred position is d - (len - x), rounded at its own magnitude: x + d - len would
+  // carry the rounding of x + d (2.4e-4 m on a 3 km lane) onto the next lane
+  const float rem = li.len - x;
   float xn = x + d;
   if (u.own.end_obst || dir) xn = fminf(xn, li.len);
   u.kind = dir ? U_CHANGE : U_STAY;
   u.lane = dir ? (dir > 0 ? li.left : li.right) : c.l;
   u.rp = c.rp;
   if (!dir) {
-    mark(u.flag, xn - li.len);
-    if (xn > li.len) {
-      if (li.edge >= 0 && (c.pl & PLAN_END)) {
-        u.kind = U_RETIRE;
+    mark(u.flag, d - rem);
+    if (!(d > rem)) {
+      xn = fminf(xn, li.len);   // x + d may round past the end when d is within an ulp of rem
+    } else if (li.edge >= 0 && (c.pl & PLAN_END)) {
+      u.kind = U_RETIRE;
+    } else {
+      xn = d - rem;
+      u.kind = U_TRANSFER;
+      int nl;
+      if (li.edge >= 0) {
+        nl = c.nlc;
       } else {
-        xn -= li.len;
-        u.kind = U_TRANSFER;
-        int nl;
-        if (li.edge >= 0) {
-          nl = c.nlc;
-        } else {
-          nl = li.succ;
-          u.rp = c.rp + 1;
-        }
-        if (nl < 0 || xn > a.li[nl].len) {
-          atomicOr(&a.ctrl->err, DEV_HOP);
-          nl = c.l;
-          xn = li.len;
-          u.kind = U_STAY;
-          u.rp = c.rp;
-        }
-        u.lane = nl;
+        nl = li.succ;
+        u.rp = c.rp + 1;
       }
+      if (nl < 0 || xn > a.li[nl].len) {
+        atomicOr(&a.ctrl->err, DEV_HOP);
+        nl = c.l;
+        xn = li.len;
+        u.kind = U_STAY;
+        u.rp = c.rp;
+      }
+      u.lane = nl;
     }
   }
   u.x = xn;

@@ -593,3 +593,43 @@ def test_dynamic_lanes_reject_broken_routes_and_reopen_exactly():
     with pytest.raises(moss.MossError) as e:
         a.set_lane_links([int(net.succ_lane[net.succ_off[l0]])], [1])   # an internal lane
     assert e.value.code == moss.MS_ERR_ARG
+
+
+@pytest.mark.parametrize("t0", [0, 1])
+def test_single_steps_match_oracle_on_long_lanes(t0):
+    """Lanes of several hundred vehicles (3 km links, 3 lanes, random spacing down to 6 m):
+    lane-change target searches over long segments, lanes spanning many warps in the
+    apply's stayer ranks and the changers' bucket ranks, long remainders in the lane
+    metrics; both step parities (left and right changes)."""
+    _need_gpu()
+    net = netkit.line(4, 3000.0, 3)
+    rng = np.random.default_rng(70 + t0)
+    lanes, xs, vs, routes = [], [], [], []
+    # a dense slow lane, a sparse fast one and a medium one per edge: changes both ways
+    mix = ((6.0, 9.0, 0.0, 4.0), (25.0, 45.0, 10.0, 14.0), (8.0, 12.0, 3.0, 7.0))
+    for e, route in ((0, [0, 1, 2]), (1, [1, 2]), (5, [5, 4, 3])):
+        for q, (g0, g1, v0_, v1_) in enumerate(mix):
+            l = int(net.edge_lane0[e]) + q
+            x = 8.0 + rng.uniform(0, 3)
+            while x < 2990.0:
+                lanes.append(l)
+                xs.append(x)
+                vs.append(rng.uniform(v0_, v1_))
+                routes.append(route)
+                x += rng.uniform(g0, g1)
+    dem = netkit.vehicles(lanes, xs, vs, routes, v0=rng.uniform(11.0, 16.0, len(lanes)))
+    cnt = np.bincount(np.asarray(lanes), minlength=net.n_lanes)
+    assert cnt.max() > 250
+    sim = parity.gpu_sim(net, dem, P, n_windows=1)
+    st = sim.read_state()
+    st["t"] = t0
+    sim.write_state(st)
+    orc = oracle.Oracle(net, dem, P, n_windows=1)
+    rep = []
+    for k in range(6):
+        _, gd, gs, od, os_ = parity.step_pair(sim, orc)
+        parity.compare_step(gd, gs, od, os_, dem.n, report=rep)
+    tot = {k: sum(r[k] for r in rep) for k in rep[0]}
+    print(t0, int(cnt.max()), tot)
+    assert tot["compared"] > 0.95 * tot["active"] and tot["changes"] > 20
+    assert sim.read_metrics(lanes=False)["err"] == 0

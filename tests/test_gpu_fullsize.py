@@ -77,3 +77,46 @@ def test_full_size_step_matches_oracle(workload):
     counts = np.bincount(gs["trip_status"], minlength=3)
     assert counts[1] == gs["n_active"] and counts.sum() == n
     assert len(np.unique(gs["id"])) == gs["n_active"]
+
+
+def test_full_size_batch_step_matches_oracle():
+    """The 256-scenario batch (4.78M vehicles, 4.96M lanes) as bench.py runs it (batch
+    loaders, autotuned launch shapes, graph steps): one step after the warm-up against the
+    oracle on the union network, over every vehicle."""
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    sc = synth.batch_scenarios(256, seed=3, n_lanes=3, link_len=300.0)
+    nets, dems = [n for n, _ in sc], [d for _, d in sc]
+    b = moss.Sim(P)
+    b.load_network_batch(nets)
+    b.add_vehicles_batch(dems)
+    b.autotune(trial_steps=3)
+    b.step(5)
+    st0 = b.read_state()
+    unet, udem = synth.union(nets, dems)
+    orc = oracle.Oracle(unet, udem, P)
+    status, lane, x, v, rp, t_arr = parity.oracle_state_from_gpu(st0, orc.n)
+    orc.set_state(status, lane, x, v, rp, st0["t"], t_arr)
+    b.step(1)
+    b.sync()
+    gs = b.read_state()
+    assert b.read_metrics(lanes=False)["err"] == 0
+    err, od = orc.step(debug=True)
+    assert err == 0
+    os_ = orc.state()
+    act = od["active_before"] == 1
+    ok = (od["flag"] == 0) & (act | (od["inserted"] == 1))
+    np.testing.assert_array_equal(gs["trip_status"][ok], os_["status"][ok])
+    still = np.nonzero(ok & (os_["status"] == 1))[0]
+    n = orc.n
+    g_lane = np.full(n, -1, np.int64)
+    g_x = np.full(n, np.nan)
+    g_v = np.full(n, np.nan)
+    g_lane[gs["id"]] = gs["lane"]
+    g_x[gs["id"]] = gs["x"]
+    g_v[gs["id"]] = gs["v"]
+    assert np.array_equal(g_lane[still], os_["lane"][still])
+    assert np.all(np.abs(g_x[still] - os_["x"][still]) <= parity.x_tol(os_["x"][still]))
+    assert np.abs(g_v[still] - os_["v"][still]).max() <= parity.V_TOL
+    print("batch256 active", int(act.sum()), "compared", still.size)
+    assert still.size > 0.95 * int(act.sum())

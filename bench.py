@@ -231,13 +231,15 @@ def apply_mods(side, mods):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(net, dem, params, budget_s: float = 20.0, max_steps: int = 10, mods=None):
+def cpu_baseline(net, dem, params, budget_s: float = 20.0, max_steps: int = 10, mods=None, warmup: int = 1):
     """The FP64 oracle, as it stands, single-threaded on this host, on the same workload:
-    vehicle-steps/s over up to max_steps steps or budget_s seconds after one warm-up step."""
+    vehicle-steps/s over up to max_steps steps or budget_s seconds after `warmup` untimed
+    steps."""
     import oracle
     o = oracle.Oracle(net, dem, params)
     apply_mods(o, mods)
-    o.step()
+    for _ in range(warmup):
+        o.step()
     n_act = int((o.state()["status"] == 1).sum())
     vs, steps, el = 0, 0, 0.0
     while steps < max_steps and el < budget_s:
@@ -258,15 +260,15 @@ def run_reference(args):
     net, dem, desc = workload(args.workload, args.seed)
     p, mods, vdesc = variant(args, net, dem)
     k = max(1, min(args.steps, args.ref_steps))
-    val, steps, el = cpu_baseline(net, dem, p, budget_s=1e9, max_steps=k, mods=mods)
+    val, steps, el = cpu_baseline(net, dem, p, budget_s=1e9, max_steps=k, mods=mods, warmup=args.warmup)
     line = {
         "impl": "reference", "metric": "vehicle-steps/s", "value": val, "unit": "vehicle-steps/s",
-        "n_gpus": world, "steps": steps, "warmup": 1, "ms_per_step": 1e3 * el / steps,
+        "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": args.workload, "description": desc, **vdesc},
         "cpu_baseline": {"value": val, "unit": "vehicle-steps/s", "cores": 1, "kind": "oracle",
                          "sample": f"{steps} oracle steps of the full {args.workload} workload "
-                                   f"({dem.n} vehicles) after 1 warm-up step"},
+                                   f"({dem.n} vehicles) after {args.warmup} warm-up steps"},
         "e2e": {"value": val, "unit": "vehicle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

@@ -6,14 +6,14 @@ neighbour search, IDM + randomized MOBIL, signal stop lines, ballistic advance, 
 transfer, departures, metrics -- over every active vehicle of the workload.
 
 Default workload: 100x100 signalised grid, 3 lanes per direction, 300 m links,
-green-wave offsets, 1,000,000 vehicles already on the network (steady state), gravity-OD
-routes, v0 ~ N(13.9, 1.5) m/s.  Inputs are generated from a seed.  The step's working set
+green-wave offsets, 1,000,000 vehicles already on the network plus 800,000 gravity-OD trips
+departing over 500 s, v0 ~ N(13.9, 1.5) m/s.  Inputs are generated from a seed.  The step's working set
 (~90 MB) fits in the 126 MB L2, so L2 is flushed (256 MiB write) before every timed step
 and each step is timed alone with CUDA events on the simulation's stream.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun (N > 1) every rank runs an independent replica (the step has no
-cross-partition exchange on one GPU).
+Under torchrun (N > 1) every rank runs an independent replica with its own seed: the step
+has no data-path exchange, so the job's time is the slowest rank's and its work the sum.
 """
 from __future__ import annotations
 

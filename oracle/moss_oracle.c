@@ -11,7 +11,7 @@
  * lane-change decision (Kesting, Treiber & Helbing 2007), then advances by Newton's
  * equations; dt = 1 s (Sec. III-A, IV-A); fixed-time signals at junctions (Sec. III-C map
  * builder, Sec. IV-E "FP").  Everything else below is a reading of what the paper leaves
- * open; each reading is numbered and listed with its reason in the design notes.
+ * open, numbered R1, R2, ... and stated where it applies.
  *
  *  R1  IDM: a = a_max [1 - (v/v0)^4 - (ss/s)^2], ss = s0 + max(0, vT + v dv/(2 sqrt(a_max b))),
  *      dv = v - v_lead, s = bumper gap floored at 0.01 m; (v/v0)^4 by two squarings; no

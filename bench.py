@@ -274,6 +274,44 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def full_sort_alternative(sim, stream, flush, avg_ms, reps: int = 20):
+    """The non-incremental alternative to the lane merge (k_bucket + k_apply): re-sort the
+    whole state by (lane, x) every step with a library radix sort (torch.sort, stable, on
+    64-bit keys lane << 32 | bits(x); x > 0, so its bits order like its values) and gather
+    the 36-B state by the permutation.  Measured on the current state, L2 flushed, CUDA
+    events; a comparison, not a path the simulation uses."""
+    import torch
+    n = sim.read_metrics(lanes=False)["n_active"]
+    x = torch.empty(n, device="cuda")
+    v = torch.empty_like(x)
+    lane = torch.empty(n, dtype=torch.int32, device="cuda")
+    vid = torch.empty_like(lane)
+    n = sim.read_state_device(x, v, lane, vid)
+    torch.cuda.synchronize()
+    keys = (lane.to(torch.int64) << 32) | x.view(torch.int32).to(torch.int64)
+    # the other state arrays (v0, rp, nl: 4 B; link plan: 8 B) stand in by same-sized copies
+    cols = [x, v, x.clone(), lane, lane.clone(), lane.clone(), vid, keys.clone()]
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    t_sort = t_all = 0.0
+    for r in range(reps + 3):
+        flush.zero_()
+        e0.record(stream)
+        sk, perm = torch.sort(keys, stable=True)
+        e1.record(stream)
+        out = [c.index_select(0, perm) for c in cols]
+        e2.record(stream)
+        e2.synchronize()
+        if r >= 3:
+            t_sort += e0.elapsed_time(e1)
+            t_all += e0.elapsed_time(e2)
+        del out
+    ordered = bool(torch.equal(sk, keys))   # the state is already in this order
+    return {"what": "torch.sort (stable) of the (lane, x) keys + gather of 36 B/vehicle",
+            "vehicles": int(n), "sort_us": round(1e3 * t_sort / reps, 2),
+            "sort_and_gather_us": round(1e3 * t_all / reps, 2),
+            "merge_us": round(1e3 * (avg_ms[2] + avg_ms[3]), 2), "state_already_sorted": ordered}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -353,6 +391,7 @@ def run_ours(args):
                                       "k_lanes": f"{B_LANES_LANE} B/lane",
                                       "k_bucket": f"{B_BUCKET_VEH} B/vehicle + {B_BUCKET_MOVER} B/arrival"},
                 "step_effective_gbs": n_avg * (B_DECIDE_VEH + B_APPLY_VEH) / (avg_ms.sum() * 1e-3) / 1e9}
+    full_sort = full_sort_alternative(sim, stream, flush, avg_ms)
 
     # end to end through the public API: step + read the per-vehicle state into pinned host
     # memory every step (Sec. III-A: position and speed of every vehicle each step).  The
@@ -393,7 +432,7 @@ def run_ours(args):
                    "lanes": net.n_lanes, "active_start": n_act[0], "active_end": n_end,
                    "l2": "flushed (256 MiB write) before every timed step; each step timed alone",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": roofline, "e2e": e2e, "clocks": clk.summary(),
+        "roofline": roofline, "e2e": e2e, "clocks": clk.summary(), "full_sort_alternative": full_sort,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         val, steps, el = cpu_baseline(net, dem, params, mods=mods)

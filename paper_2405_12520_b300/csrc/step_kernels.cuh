@@ -1335,7 +1335,7 @@ __global__ void k_check(StepArgs a) {
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   for (int i = gid; i + 1 < n; i += gridDim.x * blockDim.x) {
     int la = S.lane[i], lb = S.lane[i + 1];
-    if (la > lb || (la == lb && (S.x[i + 1] - a.P.L) - S.x[i] < -1e-3f))
+    if (la > lb || (la == lb && (S.x[i + 1] - a.P.L) - S.x[i] < -fmaxf(1e-3f, 5e-7f * S.x[i + 1])))
       atomicOr(&a.ctrl->err, DEV_ORDER);
   }
 }

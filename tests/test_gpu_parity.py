@@ -633,3 +633,31 @@ def test_single_steps_match_oracle_on_long_lanes(t0):
     print(t0, int(cnt.max()), tot)
     assert tot["compared"] > 0.95 * tot["active"] and tot["changes"] > 20
     assert sim.read_metrics(lanes=False)["err"] == 0
+
+
+def test_standstill_queue_far_along_a_lane_resumes_exactly():
+    """Bumper-to-bumper stopped vehicles 17 km along a lane (its next lane closed): their
+    FP32 positions are multiples of 2e-3 m there, so exact gap-0 stops read back as gaps of
+    about +-2e-3 m, which the state checks (ms_add_vehicles / ms_write_state and the debug
+    order check) accept; resuming from the read state is bit-exact."""
+    _need_gpu()
+    net = netkit.line(3, 18000.0, 1)
+    l0, l1 = int(net.edge_lane0[0]), int(net.edge_lane0[1])
+    xs = np.float32(17000.1234) + np.float32(5.0) * np.arange(40, dtype=np.float32)
+    xs[1::3] = np.nextafter(xs[1::3], np.float32(0))   # gaps of -1 ulp, as rounded clamps leave
+    gap32 = np.diff(xs.astype(np.float64)) - P["veh_len"]
+    assert gap32.min() < -1e-3                          # rounding beyond an absolute 1e-3
+    dem = netkit.vehicles([l0] * 40, xs.astype(np.float64), [0.0] * 40, [[0, 1]] * 40)
+    a = parity.gpu_sim(net, dem, P)                     # debug: device order / gap check
+    b = parity.gpu_sim(net, dem, P)
+    for s in (a, b):
+        s.set_lane_limits([l1], closed=[1])
+        s.step(20)
+    st = a.read_state()
+    a.write_state(st)
+    a.step(20)
+    b.step(20)
+    sa, sb = a.read_state(), b.read_state()
+    for k in ("id", "lane", "x", "v", "route_idx"):
+        np.testing.assert_array_equal(sa[k], sb[k])
+    assert a.read_metrics(lanes=False)["err"] == 0 and b.read_metrics(lanes=False)["err"] == 0

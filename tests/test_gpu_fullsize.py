@@ -77,6 +77,11 @@ def test_full_size_step_matches_oracle(workload):
     counts = np.bincount(gs["trip_status"], minlength=3)
     assert counts[1] == gs["n_active"] and counts.sum() == n
     assert len(np.unique(gs["id"])) == gs["n_active"]
+    # checkpoint / resume at this size: the read state loads back and steps on
+    sim.write_state(gs)
+    sim.step(1)
+    sim.sync()
+    assert sim.read_metrics(lanes=False)["err"] == 0
 
 
 def test_full_size_batch_step_matches_oracle():

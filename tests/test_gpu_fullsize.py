@@ -125,3 +125,37 @@ def test_full_size_batch_step_matches_oracle():
     assert np.abs(g_v[still] - os_["v"][still]).max() <= parity.V_TOL
     print("batch256 active", int(act.sum()), "compared", still.size)
     assert still.size > 0.95 * int(act.sum())
+
+
+def test_full_size_long_run_keeps_invariants():
+    """grid1m for 1200 steps (departures, arrivals, signals, four five-minute windows): no
+    device error bit, the state sorted with gaps >= 0 up to FP32 rounding, every trip
+    counted once, and the lane metrics' counts equal to the active vehicles summed over the
+    steps."""
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    sys.path.insert(0, ROOT)
+    import bench
+    net, dem, _ = bench.workload("grid1m", 3)
+    sim = moss.Sim(P, n_windows=4)
+    sim.load_network(net)
+    sim.add_vehicles(dem)
+    active_sum = 0
+    for _ in range(1200):   # the snapshot of every step is counted once in the lane metrics
+        active_sum += sim.read_metrics(lanes=False)["n_active"]
+        sim.step(1)
+    sim.sync()
+    m = sim.read_metrics()
+    assert int(m["vcnt"].sum()) == active_sum
+    assert m["err"] == 0
+    gs = sim.read_state()
+    gl, gx = gs["lane"].astype(np.int64), gs["x"].astype(np.float64)
+    same = gl[1:] == gl[:-1]
+    assert np.all((gl[1:] > gl[:-1]) | (same & (gx[1:] >= gx[:-1])))
+    gap = (gx[1:] - gx[:-1])[same] - P["veh_len"]
+    ulp = np.spacing(gs["x"][1:][same].astype(np.float32)).astype(np.float64)
+    assert np.all(gap >= -2.0 * ulp - 1e-6)
+    counts = np.bincount(gs["trip_status"], minlength=3)
+    assert counts[1] == gs["n_active"] and counts.sum() == dem.n
+    assert counts[2] == m["arrived"] and m["inserted"] > 0
+    assert m["vcnt"].sum() > 0 and np.all(m["vsum"] >= 0)

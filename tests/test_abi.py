@@ -46,3 +46,21 @@ def test_create_rejects_bad_block():
     with pytest.raises(moss.MossError) as e:
         moss.Sim(synth.default_params(), block=100)
     assert e.value.code == moss.MS_ERR_ARG
+
+
+def test_header_is_plain_c_and_links_from_c(tmp_path):
+    """A C99 translation unit that includes the header and takes the address of every entry
+    point compiles with gcc and links against the library (no C++ types or mangling)."""
+    import subprocess
+    build.build()
+    names = _declared()
+    src = tmp_path / "abi.c"
+    src.write_text('#include "moss103.h"\n#include <stdio.h>\nint main(void) {\n  void *fns[] = {\n' +
+                   "".join(f"    (void *){n},\n" for n in names) +
+                   '  };\n  printf("%d\\n", (int)(sizeof fns / sizeof fns[0]));\n  return 0;\n}\n')
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(moss.LIB_PATH)
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror",
+                           "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                           "-L", libdir, "-l:" + os.path.basename(moss.LIB_PATH), "-Wl,-rpath," + libdir])
+    assert exe.exists()

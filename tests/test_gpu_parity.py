@@ -661,3 +661,34 @@ def test_standstill_queue_far_along_a_lane_resumes_exactly():
     for k in ("id", "lane", "x", "v", "route_idx"):
         np.testing.assert_array_equal(sa[k], sb[k])
     assert a.read_metrics(lanes=False)["err"] == 0 and b.read_metrics(lanes=False)["err"] == 0
+
+
+def test_whole_run_statistics_medium_grid():
+    """A 20x20 grid (3 lanes, 300 m) with 40,000 vehicles on it and 20,000 trips departing
+    over 600 s, free-running for 1200 steps on the GPU and in the FP64 oracle: completed
+    trips, mean travel time and network mean speed per 5-minute window within 2%; per-lane
+    5-minute mean speeds within 2% on average over lanes with >= 300 vehicle-steps."""
+    _need_gpu()
+    net = synth.grid_network(20, 20, 3, 300.0, 30, 3, "wave")
+    dem = synth.merge_demands(synth.place_vehicles(net, 40_000, seed=21),
+                              synth.gravity_trips(net, 20_000, t_span=600, seed=22))
+    sim = parity.gpu_sim(net, dem, P, debug=False, n_windows=4)
+    sim.step(1200)
+    sim.sync()
+    gm = sim.read_metrics()
+    assert gm["err"] == 0
+    orc = oracle.Oracle(net, dem, P, n_windows=4)
+    orc.run(1200)
+    om = orc.metrics()
+    assert om["arrived"] > 10_000
+    assert abs(gm["arrived"] - om["arrived"]) <= 0.02 * om["arrived"]
+    assert abs(gm["sum_tt"] / gm["arrived"] - om["sum_tt"] / om["arrived"]) <= 0.02 * om["sum_tt"] / om["arrived"]
+    gv, gc = gm["vsum"].astype(np.float64), gm["vcnt"].astype(np.float64)
+    ov, oc = om["vsum"], om["vcnt"].astype(np.float64)
+    net_g, net_o = gv.sum(1) / gc.sum(1), ov.sum(1) / oc.sum(1)
+    assert np.all(np.abs(net_g - net_o) <= 0.02 * net_o), (net_g, net_o)
+    m = (gc >= 300) & (oc >= 300)
+    rel = np.abs(gv[m] / gc[m] - ov[m] / oc[m]) / np.maximum(ov[m] / oc[m], 1e-3)
+    print("lanes compared", int(m.sum()), "mean rel", rel.mean(), "p90", np.quantile(rel, 0.9),
+          "arrived", gm["arrived"], om["arrived"])
+    assert m.sum() > 1000 and rel.mean() <= 0.02

@@ -316,9 +316,12 @@ int ms_set_lane_limits(void *sim, int n, const int *lanes, const float *vmax, co
    Errors (nothing changed): MS_ERR_ARG for an internal or out-of-range lane;
    MS_ERR_CAPACITY for a lane with more than 32 links; MS_ERR_STATE before ms_add_vehicles;
    MS_ERR_ROUTE if a trip not yet arrived would need, on the rest of its route, a pair of
-   consecutive edges with no open link (the message names it).  Synchronises; rebuilds the
-   link plans of every route on the host and re-derives every vehicle's cached next-lane
-   choice (a state read and write: O(trips + route entries)). */
+   consecutive edges with no open link (the message names it).  Synchronises; rebuilds on
+   the host the link plans of the route entries on or into the edges whose links change,
+   and re-derives every active vehicle's cached plan word and next-lane choice on the
+   device (host work O(trips + route entries), a 8-byte-per-entry plan upload); under
+   max-pressure signals the controllers take the current step's decision again over the
+   links now open, as after a state upload. */
 int ms_set_lane_links(void *sim, int n, const int *lanes, const unsigned *open_mask);
 
 /* Route planner for demand generation (the paper turns OD matrices into trips with routes,

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -508,6 +509,30 @@ int upload_state(Sim *s, const std::vector<int> &ids, const std::vector<int> &la
 }
 
 }  // namespace
+
+// Cached choices of the vehicles of the current state under rebuilt link plans: the plan
+// word of the current route entry and the next-lane choice (for a vehicle on an internal
+// lane, the choice at the end of its target lane, from the next entry's plan).
+__global__ void k_refresh_choices(StepArgs a, Soa S, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int rp = S.rp[i];
+    const LaneInfo li = a.li[S.lane[i]];
+    const unsigned long long pl = a.plan[rp];
+    S.pl[i] = pl;
+    S.nl[i] = li.edge >= 0 ? plan_next(a, pl, li.idx, li.succ) : plan_next(a, a.plan[rp + 1], li.idx, li.left);
+  }
+}
+
+// run f(k0, k1) over [0, n) in chunks on the host's threads
+template <class F>
+static void host_parallel(size_t n, F f) {
+  const unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  const size_t chunk = (n + nt - 1) / nt;
+  std::vector<std::thread> th;
+  for (unsigned k = 0; k < nt; ++k)
+    th.emplace_back([=] { f(std::min(n, k * chunk), std::min(n, (k + 1) * chunk)); });
+  for (auto &x : th) x.join();
+}
 
 extern "C" {
 
@@ -1827,35 +1852,74 @@ int ms_set_lane_links(void *sim, int n, const int *lanes, const unsigned *open_m
     if (deg > 32) return fail(s, MS_ERR_CAPACITY, "an edge lane with more than 32 links");
     for (int j = 0; j < deg; ++j) off[s->succ_off[l] + j] = !((open_mask[k] >> j) & 1u);
   }
-  // the current state (host), to check the remaining routes and to re-derive every cached
-  // lane choice under the new links
-  const int N = s->n_trips;
-  std::vector<int> id(N), lane(N), ridx(N), status(N), tarr(N), cs(3 * std::max(1, s->n_ctrl));
-  std::vector<float> x(N), v(N);
-  ms_state st{};
-  st.capacity = N;
-  st.id = id.data(); st.lane = lane.data(); st.route_idx = ridx.data(); st.x = x.data(); st.v = v.data();
-  st.trip_status = status.data(); st.t_arr = tarr.data();
-  st.ctrl_state = s->n_ctrl > 0 ? cs.data() : nullptr;
-  if (int r = ms_read_state(sim, &st, 0)) return r;
-  std::vector<int> from(N, -1);   // first route index whose pair must stay connected
-  for (int trip = 0; trip < N; ++trip) from[trip] = status[trip] == 0 ? 0 : -1;
-  for (int i = 0; i < st.n_active; ++i)
-    from[id[i]] = ridx[i] + (s->lane_edge[lane[i]] < 0 ? 1 : 0);   // a movement under way ends
-  for (int trip = 0; trip < N; ++trip) {
-    if (from[trip] < 0) continue;
-    const int *R = s->h_routes.data() + s->h_route0[trip];
-    for (int k = from[trip]; R[k] >= 0 && R[k + 1] >= 0; ++k)
-      if (!edge_links_to(s, off, R[k], R[k + 1]))
-        return fail(s, MS_ERR_ROUTE, "trip " + std::to_string(trip) + " would need edge " + std::to_string(R[k]) +
-                                         " -> " + std::to_string(R[k + 1]) + " with no open lane link");
+  // edges whose lanes' links change: only route pairs leaving them can lose connectivity,
+  // and only plan entries of them or leading into them (the fan-out tie looks at the
+  // next edge's lanes) change
+  std::vector<char> touched(s->n_edges, 0);
+  bool any = false;
+  for (int l = 0; l < s->n_lanes; ++l)
+    if (s->lane_edge[l] >= 0)
+      for (int k = s->succ_off[l]; k < s->succ_off[l + 1]; ++k)
+        if (off[k] != s->link_off[k]) touched[s->lane_edge[l]] = any = true;
+  if (!any) return MS_OK;
+  // where each trip stands: arrived (t_arr >= 0), active (its current route entry), waiting
+  CK(cudaStreamSynchronize(s->stream));
+  if (int r0 = export_drain(s)) return r0;
+  DevCtrl c;
+  CK(cudaMemcpy(&c, s->d_ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost));
+  const int p = c.t & 1, na = c.n_active[p], N = s->n_trips;
+  std::vector<int> rp(na), lane(na), id(na), tarr(N);
+  const Soa &A = s->A[p];
+  if (na) {
+    CK(cudaMemcpy(rp.data(), A.rp, sizeof(int) * na, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(lane.data(), A.lane, sizeof(int) * na, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(id.data(), A.id, sizeof(int) * na, cudaMemcpyDeviceToHost));
+  }
+  CK(cudaMemcpy(tarr.data(), s->d_tarr, sizeof(int) * N, cudaMemcpyDeviceToHost));
+  std::vector<long long> from(N);   // first routes[] index whose pair must stay connected
+  for (int trip = 0; trip < N; ++trip) from[trip] = tarr[trip] >= 0 ? -1 : s->h_route0[trip];
+  for (int i = 0; i < na; ++i) from[id[i]] = rp[i] + (s->lane_edge[lane[i]] < 0 ? 1 : 0);
+  std::atomic<int> broken{-1};
+  const int *R = s->h_routes.data();
+  host_parallel((size_t)N, [&](size_t t0, size_t t1) {
+    for (size_t trip = t0; trip < t1 && broken.load() < 0; ++trip) {
+      if (from[trip] < 0) continue;
+      for (long long k = from[trip]; R[k] >= 0 && R[k + 1] >= 0; ++k)
+        if (touched[R[k]] && !edge_links_to(s, off, R[k], R[k + 1])) {
+          broken.store((int)trip);
+          break;
+        }
+    }
+  });
+  if (broken.load() >= 0) {
+    const int trip = broken.load();
+    long long k = from[trip];
+    while (!(touched[R[k]] && !edge_links_to(s, off, R[k], R[k + 1]))) ++k;
+    return fail(s, MS_ERR_ROUTE, "trip " + std::to_string(trip) + " would need edge " + std::to_string(R[k]) +
+                                     " -> " + std::to_string(R[k + 1]) + " with no open lane link");
   }
   s->link_off = off;
   CK(cudaMemcpy(s->d_link_off, s->link_off.data(), s->link_off.size(), cudaMemcpyHostToDevice));
-  build_plans(s);
-  CK(cudaMemcpy(s->d_plan, s->h_plan.data(), sizeof(unsigned long long) * s->h_plan.size(), cudaMemcpyHostToDevice));
+  const size_t nr = s->h_routes.size();
+  host_parallel(nr, [&](size_t r0, size_t r1) {
+    for (size_t r = r0; r < r1; ++r)
+      if (R[r] >= 0 && (touched[R[r]] || (r + 1 < nr && R[r + 1] >= 0 && touched[R[r + 1]])))
+        s->h_plan[r] = plan_word(s, r);
+  });
+  CK(cudaMemcpy(s->d_plan, s->h_plan.data(), sizeof(unsigned long long) * nr, cudaMemcpyHostToDevice));
   if (int r = upload_queue_entries(s)) return r;
-  return ms_write_state(sim, &st);   // plan words and next-lane choices of the vehicles
+  if (na) {
+    k_refresh_choices<<<std::max(1, std::min(4 * s->n_sm, (na + 255) / 256)), 256, 0, s->stream>>>(make_args(s), A, na);
+    CK(cudaGetLastError());
+  }
+  if (s->prm.signal_mode == 1 && s->n_ctrl > 0) {
+    // the max-pressure decision of the current step is taken again over the links now open
+    // (advancing the controllers to the step they are at again, as a state upload does)
+    k_signals<<<(s->n_ctrl + 7) / 8, 256, 0, s->stream>>>(make_args(s));
+    CK(cudaGetLastError());
+  }
+  CK(cudaStreamSynchronize(s->stream));
+  return MS_OK;
 }
 
 int ms_set_lc_model(void *sim, const float *params, float margin) {

@@ -561,6 +561,48 @@ def test_single_steps_match_oracle_dynamic_lanes(kind, t0, mp):
     assert sim.read_metrics(lanes=False)["err"] == 0
 
 
+def test_dynamic_lanes_successive_partial_calls_match_oracle():
+    """Three calls that each touch about a tenth of the edges (close a set, close another,
+    reopen the first), five single steps after each, under max-pressure signals with two of
+    the calls on a decision step: the link plans of edges no call touched stay as they were,
+    and the controllers retake the current step's decision over the links now open."""
+    _need_gpu()
+    net = _net("grid12x3")
+    prm = dict(P, signal_mode=1, mp_interval=10)
+    dem = synth.merge_demands(synth.place_vehicles(net, 5003, seed=91, min_spacing=7.0, internal_frac=0.3),
+                              synth.uniform_trips(net, 400, 40, seed=92))
+    rng = np.random.default_rng(93)
+    mask = netkit.closable_links(net, dem, rng, 0.3)
+    closing = [l for l, m in mask.items() if m != (1 << int(np.diff(net.succ_off)[l])) - 1]
+    edges = np.unique(net.lane_edge[closing])
+    pick = rng.permutation(edges)
+    e_a, e_b = set(pick[: len(pick) // 8].tolist()), set(pick[len(pick) // 8: len(pick) // 4].tolist())
+    set_a = [l for l in closing if int(net.lane_edge[l]) in e_a]
+    set_b = [l for l in closing if int(net.lane_edge[l]) in e_b]
+    assert len(set_a) > 10 and len(set_b) > 10
+    full = {l: (1 << int(np.diff(net.succ_off)[l])) - 1 for l in set_a}
+    calls = [(set_a, [mask[l] for l in set_a]), (set_b, [mask[l] for l in set_b]),
+             (set_a, [full[l] for l in set_a])]
+    sim = parity.gpu_sim(net, dem, prm)
+    st = sim.read_state()
+    st["t"] = 20
+    sim.write_state(st)
+    orc = oracle.Oracle(net, dem, prm)
+    rep = []
+    for lanes, masks in calls:
+        lanes, masks = np.array(lanes, np.int32), np.array(masks, np.uint32)
+        sim.set_lane_links(lanes, masks)
+        orc.set_lane_links(lanes, masks)
+        for k in range(5):
+            _, gd, gs, od, os_ = parity.step_pair(sim, orc)
+            parity.compare_step(gd, gs, od, os_, dem.n, report=rep)
+            np.testing.assert_array_equal(gs["ctrl_state"], os_["ctrl_state"])
+    tot = {k: sum(r[k] for r in rep) for k in rep[0]}
+    print(len(set_a), len(set_b), tot)
+    assert tot["compared"] > 0.9 * tot["active"]
+    assert sim.read_metrics(lanes=False)["err"] == 0
+
+
 def test_dynamic_lanes_reject_broken_routes_and_reopen_exactly():
     """Closing every link of the first edge toward the second breaks the routes of vehicles
     still to cross: MS_ERR_ROUTE and nothing changes.  Closing one lane's links forces its

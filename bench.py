@@ -231,7 +231,7 @@ def apply_mods(side, mods):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(net, dem, params, budget_s: float = 20.0, max_steps: int = 10, mods=None, warmup: int = 1):
+def cpu_baseline(net, dem, params, budget_s: float = 12.0, max_steps: int = 60, mods=None, warmup: int = 1):
     """The FP64 oracle, as it stands, single-threaded on this host, on the same workload:
     vehicle-steps/s over up to max_steps steps or budget_s seconds after `warmup` untimed
     steps."""

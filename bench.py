@@ -579,7 +579,13 @@ def run_learned(args):
         out[name] = dict(value=sum(nact) / (ms * 1e-3), ms_per_step=ms / args.steps,
                          mean_speed=float(m["vsum"].sum() / max(1, m["vcnt"].sum())), err=m["err"])
         if name == "learned":
-            st = sim.read_lc_stats()
+            st = sim.read_lc_stats()   # before the per-kernel pass below adds to the counters
+        kms = np.zeros(4)
+        for _ in range(20):   # per-kernel device time (k_decide includes k_learn), L2 flushed
+            flush.zero_()
+            kms += sim.step_timed(1)
+        out[name]["kernel_ms"] = dict(zip(KERNELS, [round(x, 5) for x in kms / 20]))
+        if name == "learned":
             out[name]["stats"] = st
             out[name]["agreement"] = st["agree"] / max(1, st["candidates"])
             out[name]["fallback_rate"] = st["fallbacks"] / max(1, st["candidates"])

@@ -33,6 +33,7 @@ struct LaunchCfg {
   int blk_decide = 256, grid_decide = 1;
   int blk_apply = 256, grid_apply = 1;
   int blk_bucket = 256, grid_bucket = 1;
+  int grid_learn = 1;   // k_learn (LEARN_THREADS per block), learned lane change only
   int f_decide = 1, f_apply = 1, f_bucket = 1;   // grid = factor x resident blocks x SMs
 };
 
@@ -92,6 +93,9 @@ struct Sim {
   int4 *d_bucket = nullptr;
   float *d_res_x = nullptr, *d_res_v = nullptr;
   int *d_res_code = nullptr, *d_res_nl = nullptr, *d_arr_fill = nullptr;
+  int *d_cand = nullptr;   // learned lane change: the step's listed candidates and their
+  Upd *d_rec_u = nullptr;  // sensing results (one slot per trip; allocated once a model and
+  VCtx *d_rec_c = nullptr; // the vehicles are both set)
   int2 *d_res_pos = nullptr;
   unsigned long long *d_tile_agg = nullptr;
   int *d_qoff = nullptr, *d_qtrip = nullptr;
@@ -203,6 +207,7 @@ DecideKernel decide_kernel_m(int mode, bool dbg) {
 DecideKernel decide_kernel(int mode, bool dbg, bool mods) {
   return mods ? decide_kernel_m<true>(mode, dbg) : decide_kernel_m<false>(mode, dbg);
 }
+DecideKernel learn_kernel(bool dbg) { return dbg ? k_learn<true> : k_learn<false>; }
 
 // a step kernel launch with programmatic stream serialization: it may start while the
 // previous kernel in the stream drains (the kernel waits in pdl_enter before reading)
@@ -221,8 +226,9 @@ cudaError_t launch_pdl(void (*k)(Args...), int grid, int block, size_t smem, cud
   return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
-// one step = five launches (+ the debug order check); ev (5 events) brackets the step's
-// parts: decide, the two lane-scan passes together, bucket, apply
+// one step = five launches (six with the learned lane change; + max-pressure controllers,
+// + the debug order check); ev (5 events) brackets the step's parts: decide (with k_learn),
+// the two lane-scan passes together, bucket, apply
 cudaError_t launch_step(const Sim *s, const StepArgs &a, cudaStream_t st, cudaEvent_t *ev) {
   const LaunchCfg &c = s->cfg;
   cudaError_t e = cudaSuccess;
@@ -230,9 +236,14 @@ cudaError_t launch_step(const Sim *s, const StepArgs &a, cudaStream_t st, cudaEv
     if (e == cudaSuccess) e = r;
   };
   if (ev) cudaEventRecord(ev[0], st);
-  const size_t smem = s->lc_mode == MODE_LEARN ? learn_smem(c.blk_decide) : 0;
-  ok(launch_pdl(decide_kernel(s->lc_mode, s->prm.debug != 0, a.P.lane_mods != 0), c.grid_decide, c.blk_decide, smem,
+  ok(launch_pdl(decide_kernel(s->lc_mode, s->prm.debug != 0, a.P.lane_mods != 0), c.grid_decide, c.blk_decide, 0,
                 st, a));
+  if (s->lc_mode == MODE_LEARN) {
+    // an ordinary launch: launched early (programmatic), its waiting blocks took the SMs
+    // the decide kernel's last blocks were freeing and the pair took 18 us longer
+    learn_kernel(s->prm.debug != 0)<<<c.grid_learn, LEARN_THREADS, learn_smem(LEARN_THREADS), st>>>(a);
+    ok(cudaGetLastError());
+  }
   if (ev) cudaEventRecord(ev[1], st);
   ok(launch_pdl(k_lanes_t<0>, s->n_tiles, LANE_THREADS, 0, st, a));   // tile aggregates
   ok(launch_pdl(k_lanes_t<1>, s->n_tiles, LANE_THREADS, 0, st, a));   // counts, starts, departures
@@ -258,9 +269,11 @@ int shape_grids(Sim *s, LaunchCfg &c, int f_decide, int f_apply, int f_bucket) {
   c.f_decide = f_decide;
   c.f_apply = f_apply;
   c.f_bucket = f_bucket;
-  const size_t dsm = s->lc_mode == MODE_LEARN ? learn_smem(c.blk_decide) : 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&od, decide_kernel(s->lc_mode, s->prm.debug != 0, false),
-                                                   c.blk_decide, dsm));
+                                                   c.blk_decide, 0));
+  // k_learn: one block per SM, each warp looping over 16-candidate chunks (1,184 warps;
+  // about 16k candidates a step on the 1M-vehicle grid use 1,030 of them)
+  c.grid_learn = s->n_sm;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oa, k_apply, c.blk_apply, 0));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, k_bucket, c.blk_bucket, 0));
   auto g = [&](int blk, int occ, int f) {
@@ -269,6 +282,21 @@ int shape_grids(Sim *s, LaunchCfg &c, int f_decide, int f_apply, int f_bucket) {
   c.grid_decide = g(c.blk_decide, od, f_decide);
   c.grid_apply = g(c.blk_apply, oa, f_apply);
   c.grid_bucket = g(c.blk_bucket, ob, f_bucket);
+  return MS_OK;
+}
+
+// learned lane change: the candidate list and records, one slot per trip (a vehicle is
+// listed at most once a step), allocated once a model and the vehicles are both set
+int ensure_cand(Sim *s) {
+  if (s->d_cand || !s->veh_loaded || s->lc_mode != MODE_LEARN) return MS_OK;
+  const int N = s->n_trips;
+  DALLOC(s->d_cand, N);
+  DALLOC(s->d_rec_u, N);
+  DALLOC(s->d_rec_c, N);
+  s->lc.cand = s->d_cand;
+  s->lc.rec_u = s->d_rec_u;
+  s->lc.rec_c = s->d_rec_c;
+  s->lc.cand_cap = N;
   return MS_OK;
 }
 
@@ -920,6 +948,7 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
     if (r0) return r0;
   }
   s->veh_loaded = true;
+  if (int r = ensure_cand(s)) return r;
   // initial state
   std::vector<int> ids, lanes, ridx;
   std::vector<float> xs, vs;
@@ -1940,9 +1969,8 @@ int ms_set_lc_model(void *sim, const float *params, float margin) {
     static bool attr = false;
     if (!attr) {
       for (int d = 0; d < 2; ++d)
-        for (int m = 0; m < 2; ++m)
-          CK(cudaFuncSetAttribute(decide_kernel(MODE_LEARN, d != 0, m != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  learn_smem(512)));
+        CK(cudaFuncSetAttribute(learn_kernel(d != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                learn_smem(LEARN_THREADS)));
       attr = true;
     }
   }
@@ -1956,6 +1984,7 @@ int ms_set_lc_model(void *sim, const float *params, float margin) {
   s->lc.stats = s->d_lcstats;
   s->lc_mode = MODE_LEARN;
   s->lc.log_x = nullptr;
+  if (int r = ensure_cand(s)) return r;
   if (s->veh_loaded) return shape_grids(s, s->cfg, s->cfg.f_decide, s->cfg.f_apply, s->cfg.f_bucket);
   return MS_OK;
 }

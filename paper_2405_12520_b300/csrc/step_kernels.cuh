@@ -116,6 +116,7 @@ struct DevCtrl {
   int n_movers;      // arrivals of the last step (count only)
   unsigned err;
   int movers_last;
+  int n_cand;        // discretionary candidates listed for k_learn this step (reset by k_apply)
   unsigned long long inserted, arrived, sum_tt;
 };
 
@@ -145,6 +146,9 @@ struct LcAux {
   const MlpDev *model;
   float margin;           // softmax top1 - top2 below which the rule decides
   unsigned long long *stats;
+  int *cand;              // [cand_cap] vehicles whose update k_learn finishes
+  void *rec_u, *rec_c;    // [cand_cap] sensing results (Upd) and fields (VCtx), by vehicle index
+  int cand_cap;
 };
 
 struct StepArgs {
@@ -723,6 +727,62 @@ __device__ __forceinline__ void vehicle_move(const StepArgs &a, Upd &u, const VC
   u.v = vn;
 }
 
+// The rest of vehicle i's update once its lane-change direction dir is known: motion, its
+// result record and the count of vehicles leaving its lane.  Returns whether it leaves its
+// slot (changes lane, transfers or retires).
+template <bool DBG>
+__device__ __forceinline__ int vehicle_finish(const StepArgs &a, const Soa &S, int i, Upd &u, const VCtx &c,
+                                              int dir) {
+  vehicle_move(a, u, c, dir);
+  const int leave = u.kind != U_STAY;
+  if (leave) atomicAdd(&a.arr_cnt[c.l], LEAVE_ONE);   // fire-and-forget, like the arrivals
+  int kind = u.kind == U_STAY ? C_STAY
+           : u.kind == U_CHANGE ? C_CHANGE
+           : u.kind == U_RETIRE ? C_RETIRE
+           : (u.rp != c.rp ? C_TRANSFER_ROUTE : C_TRANSFER);
+  a.res_x[i] = u.x;
+  a.res_v[i] = u.v;
+  a.res_code[i] = (kind << CODE_LANE_BITS) | (u.kind == U_RETIRE ? 0 : u.lane);
+  if constexpr (DBG) {
+    a.dbg.id[i] = c.id;
+    a.dbg.lead_kind[i] = u.own.kind;
+    a.dbg.lead_id[i] = u.own.j >= 0 ? S.id[u.own.j] : -1;
+    a.dbg.s_own[i] = u.own.gap;
+    a.dbg.vl_own[i] = u.own.vl;
+    a.dbg.a_own[i] = u.a_own;
+    a.dbg.lc_dir[i] = u.lc.dir;
+    a.dbg.lc_cand[i] = u.lc.cand;
+    a.dbg.tau_lead[i] = u.lc.tl >= 0 ? S.id[u.lc.tl] : -1;
+    a.dbg.tau_foll[i] = u.lc.tf >= 0 ? S.id[u.lc.tf] : -1;
+    a.dbg.old_foll[i] = u.lc.of >= 0 ? S.id[u.lc.of] : -1;
+    a.dbg.incentive[i] = u.lc.inc;
+    a.dbg.a_use[i] = u.a_use;
+    a.dbg.flag[i] = u.flag;
+  }
+  return leave;
+}
+
+// The records of a vehicle arriving on a new lane (lane change or transfer): the lane's
+// arrival count and rearmost arrival (no value returned, so nothing waits on these atomics;
+// slots are handed out by k_bucket), and the arrival's cached next-lane choice for its new
+// lane (internal -> edge lane keeps the choice it already made for that target lane): a
+// lane change follows the plan of its own edge, an internal lane the plan of its target
+// lane's edge.
+template <bool DBG>
+__device__ __forceinline__ void arrival_records(const StepArgs &a, int i, const Upd &u, const VCtx &c) {
+  atomicAdd(&a.arr_cnt[u.lane], 1);
+  atomicMin(&a.amin[u.lane], fkey(u.x - a.P.L));
+  if (u.kind == U_CHANGE) a.res_pos[i] = make_int2(u.lc.tfirst, u.lc.pos);
+  if (u.rp == c.rp) {
+    const LaneInfo ln = a.li[u.lane];
+    const unsigned long long pn = a.plan[c.rp + 1];
+    a.res_code_nl[i] = ln.edge >= 0 ? plan_next(a, c.pl, ln.idx, ln.succ) : plan_next(a, pn, ln.idx, ln.left);
+  }
+  if constexpr (DBG) {
+    if (u.flag) a.dbg.arr_flag[u.lane] = 1;
+  }
+}
+
 // number of set bits of b in [s, e)
 __device__ __forceinline__ int count_bits(const unsigned *b, int s, int e) {
   if (s >= e) return 0;
@@ -821,6 +881,7 @@ __device__ __forceinline__ int lc_dir(int cls) { return cls == 1 ? 1 : (cls == 2
 // shared memory of the learned step: the model plus, per warp, 32 feature rows, one 16-row
 // hidden buffer and 32 x 3 logits
 constexpr int LEARN_WARP_SMEM = 32 * MLP_IN * 2 + 16 * MLP_H * 2 + 32 * MLP_OUT * 4;
+constexpr int LEARN_THREADS = 256;   // k_learn block
 __host__ __device__ constexpr int learn_smem(int threads) {
   return (int)sizeof(MlpDev) + (threads / 32) * LEARN_WARP_SMEM;
 }
@@ -830,20 +891,12 @@ __host__ __device__ constexpr int learn_smem(int threads) {
 // are set (also a separate instance: without them the step does no work for them).  The plain
 // production instance is capped at 48 registers: 5 blocks of 256 per SM instead of 4 outweigh
 // its few spills (the kernel is bound by the latency of dependent gathers, so resident warps
-// decide its speed).  The learned instance gets 80, which removes its spills around the MMA
-// tiles (measured faster than 64 with spills or 96).
+// decide its speed).  The learned instance is the plain one that lists its discretionary
+// candidates instead of finishing them (k_learn does), under the same cap.
 template <int MODE, bool DBG, bool MODS>
-__global__ void __launch_bounds__(512, (MODE == MODE_LEARN && !DBG) ? 1 : 2)
-    __maxnreg__((MODE == MODE_PLAIN && !DBG) ? 48 : (MODE == MODE_LEARN && !DBG) ? 80 : 64)
+__global__ void __launch_bounds__(512, 2) __maxnreg__((MODE == MODE_PLAIN && !DBG) ? 48 : 64)
     k_decide_t(StepArgs a) {
-  extern __shared__ __align__(16) unsigned char lsm[];
   pdl_enter();
-  if constexpr (MODE == MODE_LEARN) {
-    const uint32_t *src = reinterpret_cast<const uint32_t *>(a.lc.model);
-    uint32_t *dst = reinterpret_cast<uint32_t *>(lsm);
-    for (int k = threadIdx.x; k < (int)(sizeof(MlpDev) / 4); k += blockDim.x) dst[k] = src[k];
-    __syncthreads();
-  }
   const int t = a.ctrl->t;
   const int p = t & 1;
   const Soa S = a.A[p];
@@ -858,6 +911,7 @@ __global__ void __launch_bounds__(512, (MODE == MODE_LEARN && !DBG) ? 1 : 2)
     Upd u;
     VCtx c;
     int dir = 0;
+    bool defer = false;   // learned instance: k_learn finishes this vehicle
     load_vehicle(S, n, i, c);
     if (i < n) {
       u = vehicle_sense<MODS>(a, S, dyn, i, t, c);
@@ -866,6 +920,10 @@ __global__ void __launch_bounds__(512, (MODE == MODE_LEARN && !DBG) ? 1 : 2)
     if constexpr (MODE != MODE_PLAIN) {
       // discretionary candidates that passed the safety criteria: the decision to learn
       const bool cand = i < n && u.lc.cand && u.lc.safe && !u.lc.mand;
+      if (MODE == MODE_LEARN && cand) {   // k_learn continues from these (slot = index)
+        reinterpret_cast<Upd *>(a.lc.rec_u)[i] = u;
+        reinterpret_cast<VCtx *>(a.lc.rec_c)[i] = c;
+      }
       const int rule = cand ? lc_class(u.lc.dir) : 0;
       const unsigned cm = __ballot_sync(0xffffffffu, cand);
       const int wl = threadIdx.x & 31;
@@ -885,111 +943,128 @@ __global__ void __launch_bounds__(512, (MODE == MODE_LEARN && !DBG) ? 1 : 2)
             }
           }
         }
-      } else {   // MODE_LEARN: fused inference; the warp's candidates are packed into the
-        if (cm) {  // first rows, so one 16-row tile serves up to 16 of them
-          const MlpDev &w = *reinterpret_cast<const MlpDev *>(lsm);
-          unsigned char *ws = lsm + sizeof(MlpDev) + (threadIdx.x >> 5) * LEARN_WARP_SMEM;
-          __nv_bfloat16 *X = reinterpret_cast<__nv_bfloat16 *>(ws);
-          __nv_bfloat16 *H1 = X + 32 * MLP_IN;
-          float *Z = reinterpret_cast<float *>(H1 + 16 * MLP_H);
-          const int nc = __popc(cm);
-          const int row = __popc(cm & ((1u << wl) - 1u));   // this candidate's row
-          if (cand) {
-            float f[MLP_IN];
-            lc_features(a, S, i, u, c, f);
-            for (int q = 0; q < MLP_IN; ++q) X[row * MLP_IN + q] = __float2bfloat16_rn(f[q]);
-          }
-          // rows past the candidates are zeroed (each output row depends on its input row only)
-          for (int r = nc + wl; r < ((nc + 15) & ~15); r += 32)
-            for (int q = 0; q < MLP_IN; ++q) X[r * MLP_IN + q] = __float2bfloat16_rn(0.f);
-          __syncwarp();
-          for (int mt = 0; mt < (nc + 15) >> 4; ++mt) {
-            mlp_forward_tile(w, X + mt * 16 * MLP_IN, H1, nullptr,
-                             [&](int m, int q, float v) { Z[(mt * 16 + m) * MLP_OUT + q] = v; });
-            __syncwarp();
-          }
-          int fin = rule;
-          bool fb = false;
-          if (cand) {
-            const float z0 = Z[row * 3], z1 = Z[row * 3 + 1], z2 = Z[row * 3 + 2];
-            const float mx = fmaxf(z0, fmaxf(z1, z2));
-            const float e0 = __expf(z0 - mx), e1 = __expf(z1 - mx), e2 = __expf(z2 - mx);
-            const float sum = e0 + e1 + e2;
-            const float p0 = e0 / sum, p1 = e1 / sum, p2 = e2 / sum;
-            int cls = 0;
-            float top = p0, sec = fmaxf(p1, p2);
-            if (p1 > top) { cls = 1; sec = fmaxf(p0, p2); top = p1; }
-            if (p2 > top) { cls = 2; sec = fmaxf(p0, p1); top = p2; }
-            fb = top - sec < a.lc.margin;
-            if (!fb) fin = (cls != 0 && lc_dir(cls) != u.lc.step_dir) ? 0 : cls;
-            dir = lc_dir(fin);
-          }
-          __syncwarp();
-          if (a.lc.stats) {
-            const unsigned fbm = __ballot_sync(0xffffffffu, cand && fb);
-            const unsigned agm = __ballot_sync(0xffffffffu, cand && fin == rule);
-            unsigned conf[9];
-            for (int q = 0; q < 9; ++q) conf[q] = __ballot_sync(0xffffffffu, cand && rule * 3 + fin == q);
-            if (wl == 0) {
-              atomicAdd(&a.lc.stats[ST_CAND], (unsigned long long)__popc(cm));
-              if (fbm) atomicAdd(&a.lc.stats[ST_FALLBACK], (unsigned long long)__popc(fbm));
-              if (agm) atomicAdd(&a.lc.stats[ST_AGREE], (unsigned long long)__popc(agm));
-              for (int q = 0; q < 9; ++q)
-                if (conf[q]) atomicAdd(&a.lc.stats[ST_CONF + q], (unsigned long long)__popc(conf[q]));
-            }
+      } else {   // MODE_LEARN: the candidates are listed and their update left to k_learn
+        if (cm) {
+          int slot0 = 0;
+          const int leader = __ffs(cm) - 1;
+          if (wl == leader) slot0 = atomicAdd(&a.ctrl->n_cand, __popc(cm));
+          slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+          const int slot = slot0 + __popc(cm & ((1u << wl) - 1u));
+          if (cand && slot < a.lc.cand_cap) {
+            a.lc.cand[slot] = i;
+            defer = true;
           }
         }
       }
     }
-    if (i < n) {
-      vehicle_move(a, u, c, dir);
-      leave = u.kind != U_STAY;
+    if (i < n && !defer) {
+      leave = vehicle_finish<DBG>(a, S, i, u, c, dir);
       moving = u.kind == U_CHANGE || u.kind == U_TRANSFER;
-      if (leave) atomicAdd(&a.arr_cnt[c.l], LEAVE_ONE);   // fire-and-forget, like the arrivals
-      int kind = u.kind == U_STAY ? C_STAY
-               : u.kind == U_CHANGE ? C_CHANGE
-               : u.kind == U_RETIRE ? C_RETIRE
-               : (u.rp != c.rp ? C_TRANSFER_ROUTE : C_TRANSFER);
-      a.res_x[i] = u.x;
-      a.res_v[i] = u.v;
-      a.res_code[i] = (kind << CODE_LANE_BITS) | (u.kind == U_RETIRE ? 0 : u.lane);
-      if constexpr (DBG) {
-        a.dbg.id[i] = c.id;
-        a.dbg.lead_kind[i] = u.own.kind;
-        a.dbg.lead_id[i] = u.own.j >= 0 ? S.id[u.own.j] : -1;
-        a.dbg.s_own[i] = u.own.gap;
-        a.dbg.vl_own[i] = u.own.vl;
-        a.dbg.a_own[i] = u.a_own;
-        a.dbg.lc_dir[i] = u.lc.dir;
-        a.dbg.lc_cand[i] = u.lc.cand;
-        a.dbg.tau_lead[i] = u.lc.tl >= 0 ? S.id[u.lc.tl] : -1;
-        a.dbg.tau_foll[i] = u.lc.tf >= 0 ? S.id[u.lc.tf] : -1;
-        a.dbg.old_foll[i] = u.lc.of >= 0 ? S.id[u.lc.of] : -1;
-        a.dbg.incentive[i] = u.lc.inc;
-        a.dbg.a_use[i] = u.a_use;
-        a.dbg.flag[i] = u.flag;
-      }
     }
     const unsigned lm = __ballot_sync(0xffffffffu, leave);
     if ((threadIdx.x & 31) == 0) a.leave[(base + threadIdx.x) >> 5] = lm;
     if (rec) lane_speed_sums(a, S, dyn, i, w, c);
-    // arrivals: count per new lane and keep the rearmost arrival (no value returned, so
-    // nothing waits on these atomics; slots are handed out by k_bucket)
-    if (moving) {
-      atomicAdd(&a.arr_cnt[u.lane], 1);
-      atomicMin(&a.amin[u.lane], fkey(u.x - a.P.L));
-      // the arrival's cached next-lane choice for its new lane (internal -> edge lane keeps
-      // the choice it already made for that target lane): a lane change follows the plan
-      // of its own edge, an internal lane the plan of its target lane's edge
-      if (u.kind == U_CHANGE) a.res_pos[i] = make_int2(u.lc.tfirst, u.lc.pos);
-      if (u.rp == c.rp) {
-        const LaneInfo ln = a.li[u.lane];
-        const unsigned long long pn = a.plan[c.rp + 1];
-        a.res_code_nl[i] = ln.edge >= 0 ? plan_next(a, c.pl, ln.idx, ln.succ) : plan_next(a, pn, ln.idx, ln.left);
+    if (moving) arrival_records<DBG>(a, i, u, c);
+  }
+}
+
+// Learned lane change: the decisions of the step's discretionary candidates, listed by the
+// decide kernel with their sensing results and their update left undone.  Each warp takes
+// 16 listed vehicles, evaluates the surrogate network on their features as one 16-row
+// tensor-core tile (rows past the list are zero; each output row depends on its own input
+// row only), takes the network's class unless its softmax margin is below lc.margin (then
+// the rule's), and finishes their update with that direction.  Launched right after the
+// decide kernel.
+template <bool DBG>
+__global__ void __launch_bounds__(LEARN_THREADS) k_learn(StepArgs a) {
+  extern __shared__ __align__(16) unsigned char lsm[];
+  pdl_enter();
+  const int p = a.ctrl->t & 1;
+  const int nc = min(a.ctrl->n_cand, a.lc.cand_cap);
+  {   // the model into shared memory: every 16-byte load of the block in flight at once
+    static_assert(sizeof(MlpDev) % 16 == 0, "model copied in 16-byte words");
+    constexpr int NV = (int)(sizeof(MlpDev) / 16), PER = (NV + LEARN_THREADS - 1) / LEARN_THREADS;
+    const uint4 *src = reinterpret_cast<const uint4 *>(a.lc.model);
+    uint4 *dst = reinterpret_cast<uint4 *>(lsm);
+    uint4 r[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k)
+      if (threadIdx.x + k * LEARN_THREADS < NV) r[k] = src[threadIdx.x + k * LEARN_THREADS];
+#pragma unroll
+    for (int k = 0; k < PER; ++k)
+      if (threadIdx.x + k * LEARN_THREADS < NV) dst[threadIdx.x + k * LEARN_THREADS] = r[k];
+    __syncthreads();
+  }
+  const MlpDev &w = *reinterpret_cast<const MlpDev *>(lsm);
+  unsigned char *ws = lsm + sizeof(MlpDev) + (threadIdx.x >> 5) * LEARN_WARP_SMEM;
+  __nv_bfloat16 *X = reinterpret_cast<__nv_bfloat16 *>(ws);
+  __nv_bfloat16 *H1 = X + 32 * MLP_IN;
+  float *Z = reinterpret_cast<float *>(H1 + 16 * MLP_H);
+  const Soa S = a.A[p];
+  const int n = a.ctrl->n_active[p];
+  const int wl = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  // 16 candidates per warp (lanes 0..15), one tensor-core tile each: the network's three
+  // layers are a serial chain, so two tiles per warp would double its latency
+  for (int cb = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 16; cb < nc; cb += nw * 16) {   // warp-uniform
+    const bool listed = wl < 16 && cb + wl < nc;
+    const int i = listed ? a.lc.cand[cb + wl] : n;
+    VCtx c;
+    Upd u;
+    int dir = 0;
+    bool cand = false;
+    int rule = 0;
+    if (listed) {
+      u = reinterpret_cast<const Upd *>(a.lc.rec_u)[i];
+      c = reinterpret_cast<const VCtx *>(a.lc.rec_c)[i];
+      dir = u.lc.dir;
+      cand = true;
+      rule = lc_class(u.lc.dir);
+    }
+    if (cand) {
+      float f[MLP_IN];
+      lc_features(a, S, i, u, c, f);
+      for (int q = 0; q < MLP_IN; ++q) X[wl * MLP_IN + q] = __float2bfloat16_rn(f[q]);
+    } else {
+      for (int q = 0; q < MLP_IN; ++q) X[wl * MLP_IN + q] = __float2bfloat16_rn(0.f);
+    }
+    __syncwarp();
+    mlp_forward_tile(w, X, H1, nullptr, [&](int m, int q, float v) { Z[m * MLP_OUT + q] = v; });
+    __syncwarp();
+    int fin = rule;
+    bool fb = false;
+    if (cand) {
+      const float z0 = Z[wl * 3], z1 = Z[wl * 3 + 1], z2 = Z[wl * 3 + 2];
+      const float mx = fmaxf(z0, fmaxf(z1, z2));
+      const float e0 = __expf(z0 - mx), e1 = __expf(z1 - mx), e2 = __expf(z2 - mx);
+      const float sum = e0 + e1 + e2;
+      const float p0 = e0 / sum, p1 = e1 / sum, p2 = e2 / sum;
+      int cls = 0;
+      float top = p0, sec = fmaxf(p1, p2);
+      if (p1 > top) { cls = 1; sec = fmaxf(p0, p2); top = p1; }
+      if (p2 > top) { cls = 2; sec = fmaxf(p0, p1); top = p2; }
+      fb = top - sec < a.lc.margin;
+      if (!fb) fin = (cls != 0 && lc_dir(cls) != u.lc.step_dir) ? 0 : cls;
+      dir = lc_dir(fin);
+    }
+    __syncwarp();   // the next chunk overwrites X and Z
+    if (a.lc.stats) {
+      const unsigned cm = __ballot_sync(0xffffffffu, cand);
+      const unsigned fbm = __ballot_sync(0xffffffffu, cand && fb);
+      const unsigned agm = __ballot_sync(0xffffffffu, cand && fin == rule);
+      unsigned conf[9];
+      for (int q = 0; q < 9; ++q) conf[q] = __ballot_sync(0xffffffffu, cand && rule * 3 + fin == q);
+      if (wl == 0 && cm) {
+        atomicAdd(&a.lc.stats[ST_CAND], (unsigned long long)__popc(cm));
+        if (fbm) atomicAdd(&a.lc.stats[ST_FALLBACK], (unsigned long long)__popc(fbm));
+        if (agm) atomicAdd(&a.lc.stats[ST_AGREE], (unsigned long long)__popc(agm));
+        for (int q = 0; q < 9; ++q)
+          if (conf[q]) atomicAdd(&a.lc.stats[ST_CONF + q], (unsigned long long)__popc(conf[q]));
       }
-      if constexpr (DBG) {
-        if (u.flag) a.dbg.arr_flag[u.lane] = 1;
-      }
+    }
+    if (listed) {
+      if (vehicle_finish<DBG>(a, S, i, u, c, dir)) atomicOr(&a.leave[i >> 5], 1u << (i & 31));
+      if (u.kind == U_CHANGE || u.kind == U_TRANSFER) arrival_records<DBG>(a, i, u, c);
     }
   }
 }
@@ -1237,6 +1312,7 @@ __global__ void k_apply(StepArgs a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.ctrl->movers_last = a.ctrl->n_movers;
     a.ctrl->n_movers = 0;
+    a.ctrl->n_cand = 0;
   }
   for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
     const int ws = base + (threadIdx.x & ~31);   // this warp's first vehicle

@@ -89,3 +89,31 @@ def test_learned_step_runs_agrees_and_keeps_invariants(logged, torch_mod):
     rv, rc = mr["vsum"].sum(1), mr["vcnt"].sum(1)
     busy = rc >= 2000
     assert np.all(np.abs(gv[busy] / gc[busy] - rv[busy] / rc[busy]) <= 0.02 * rv[busy] / rc[busy])
+
+
+@pytest.mark.parametrize("debug,mods", [(False, False), (True, True)])
+def test_learned_path_taking_every_fallback_is_the_rule_step(torch_mod, debug, mods):
+    """With margin 1 every listed candidate falls back to the rule (a near-zero network gives
+    probabilities near 1/3), so the learned path (candidates listed by the decide kernel and
+    finished by k_learn) must give the rule step bit for bit, with and without lane
+    modifications; every candidate is counted and falls back."""
+    theta = (learned.init_params(3) * 1e-3).astype(np.float32)
+    net, dem = synth.small_grid_workload(778)
+    rule = parity.gpu_sim(net, dem, P, debug=debug)
+    lrn = parity.gpu_sim(net, dem, P, debug=debug)
+    if mods:
+        lanes = np.nonzero(np.asarray(net.lane_edge) >= 0)[0][::7].astype(np.int32)
+        vmax = np.full(lanes.shape, 8.0, np.float32)
+        for s in (rule, lrn):
+            s.set_lane_limits(lanes, vmax=vmax)
+    lrn.set_lc_model(theta, 1.0)
+    for k in range(6):
+        rule.step(50)
+        lrn.step(50)
+        a, b = rule.read_state(), lrn.read_state()
+        for key in ("id", "lane", "x", "v", "route_idx"):
+            np.testing.assert_array_equal(a[key], b[key])
+    st = lrn.read_lc_stats()
+    print(st)
+    assert st["candidates"] > 100 and st["fallbacks"] == st["candidates"] and st["agree"] == st["candidates"]
+    assert lrn.read_metrics(lanes=False)["err"] == 0

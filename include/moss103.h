@@ -182,7 +182,8 @@ int ms_step(void *sim, int n);
 
 /* Run n steps with each kernel launched on its own (no graph) between CUDA events on the
    simulation's stream, and add each kernel's device time in milliseconds to
-   ms_per_kernel[0..3] (decide, lanes, bucket, apply; caller-owned, 4 floats).  Synchronises.
+   ms_per_kernel[0..3] (decide (with the learned lane change's inference kernel when a model
+   is set), lanes, bucket, apply; caller-owned, 4 floats).  Synchronises.
    Same results as ms_step; used to attribute the step time to kernels. */
 int ms_step_timed(void *sim, int n, float *ms_per_kernel);
 
@@ -291,7 +292,10 @@ int ms_set_lc_log(void *sim, void *x, int *y, int cap, int *n);
 /* Use the learned decision in subsequent steps: params (host, 5443 floats) is the network;
    a candidate follows the network's class when its softmax margin (top1 - top2) is at
    least margin, else the rule's decision; a change still needs the step's allowed
-   direction.  params == NULL returns to the rule. */
+   direction.  params == NULL returns to the rule.  A step then lists its discretionary
+   candidates with their sensing results (one slot per trip, about 260 B each, allocated
+   with the first model once the vehicles are added) and evaluates the network on them in
+   one more kernel.  Errors: MS_ERR_ARG (margin outside [0, 1]), MS_ERR_CUDA (allocation). */
 int ms_set_lc_model(void *sim, const float *params, float margin);
 
 /* Lane modifications (Sec. III-C "Python API": modification calls for lane speed limits and

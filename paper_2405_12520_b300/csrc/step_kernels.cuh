@@ -892,7 +892,8 @@ __host__ __device__ constexpr int learn_smem(int threads) {
 // production instance is capped at 48 registers: 5 blocks of 256 per SM instead of 4 outweigh
 // its few spills (the kernel is bound by the latency of dependent gathers, so resident warps
 // decide its speed).  The learned instance is the plain one that lists its discretionary
-// candidates instead of finishing them (k_learn does), under the same cap.
+// candidates with their sensing records instead of finishing them (k_learn does); it gets
+// 64 registers, since the records keep more values live (48 spilled 272 B).
 template <int MODE, bool DBG, bool MODS>
 __global__ void __launch_bounds__(512, 2) __maxnreg__((MODE == MODE_PLAIN && !DBG) ? 48 : 64)
     k_decide_t(StepArgs a) {

@@ -616,7 +616,7 @@ def run_learned(args):
         "metric": "vehicle-steps/s", "value": L["value"], "unit": "vehicle-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": L["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 state, bf16 MLP operands / f32 accumulate",
-        "data": "synthetic", "gpu_launches": STEP_LAUNCHES * args.steps,
+        "data": "synthetic", "gpu_launches": (STEP_LAUNCHES + 1) * args.steps,   # + k_learn
         "config": {"workload": args.workload, "description": desc + "; lane-change decisions by the learned MLP",
                    "l2": "flushed (256 MiB write) before every timed step; each step timed alone",
                    "train": {"samples": int(x.shape[0]), "class_counts": cnt.tolist(), "seeds": args.train_seeds,

@@ -295,7 +295,8 @@ int ms_set_lc_log(void *sim, void *x, int *y, int cap, int *n);
    direction.  params == NULL returns to the rule.  A step then lists its discretionary
    candidates with their sensing results (one slot per trip, about 260 B each, allocated
    with the first model once the vehicles are added) and evaluates the network on them in
-   one more kernel.  Errors: MS_ERR_ARG (margin outside [0, 1]), MS_ERR_CUDA (allocation). */
+   one more kernel.  Errors: MS_ERR_ARG (margin outside [0, 1]); MS_ERR_CUDA if those
+   buffers cannot be allocated (the rule then keeps deciding). */
 int ms_set_lc_model(void *sim, const float *params, float margin);
 
 /* Lane modifications (Sec. III-C "Python API": modification calls for lane speed limits and

@@ -287,16 +287,24 @@ int shape_grids(Sim *s, LaunchCfg &c, int f_decide, int f_apply, int f_bucket) {
 
 // learned lane change: the candidate list and records, one slot per trip (a vehicle is
 // listed at most once a step), allocated once a model and the vehicles are both set
-int ensure_cand(Sim *s) {
-  if (s->d_cand || !s->veh_loaded || s->lc_mode != MODE_LEARN) return MS_OK;
+int alloc_cand(Sim *s) {
   const int N = s->n_trips;
   DALLOC(s->d_cand, N);
   DALLOC(s->d_rec_u, N);
   DALLOC(s->d_rec_c, N);
+  return MS_OK;
+}
+int ensure_cand(Sim *s) {
+  if ((s->d_cand && s->d_rec_u && s->d_rec_c) || !s->veh_loaded || s->lc_mode != MODE_LEARN) return MS_OK;
+  if (int r = alloc_cand(s)) {   // no room: the rule keeps deciding
+    s->lc_mode = MODE_PLAIN;
+    s->lc.model = nullptr;
+    return r;
+  }
   s->lc.cand = s->d_cand;
   s->lc.rec_u = s->d_rec_u;
   s->lc.rec_c = s->d_rec_c;
-  s->lc.cand_cap = N;
+  s->lc.cand_cap = s->n_trips;
   return MS_OK;
 }
 

@@ -173,7 +173,9 @@ int ms_load_network(void *sim, const ms_network *net);
 
 /* Copy the trips to the device (once, after ms_load_network, before the first step).
    Validates routes (MS_ERR_ROUTE) and placements (MS_ERR_ARG: lane/edge mismatch, x not
-   in (0, len], overlapping vehicles in a lane). */
+   in (0, len], overlapping vehicles in a lane).  If a learned lane-change model was set
+   before this call and its candidate buffers cannot be allocated, the vehicles are still
+   added, the model is dropped (the rule decides) and MS_ERR_CUDA is returned. */
 int ms_add_vehicles(void *sim, const ms_vehicles *veh);
 
 /* Enqueue n steps on the simulation's stream (asynchronous; CUDA-graph replays).  Returns
@@ -296,7 +298,8 @@ int ms_set_lc_log(void *sim, void *x, int *y, int cap, int *n);
    candidates with their sensing results (one slot per trip, about 260 B each, allocated
    with the first model once the vehicles are added) and evaluates the network on them in
    one more kernel.  Errors: MS_ERR_ARG (margin outside [0, 1]); MS_ERR_CUDA if those
-   buffers cannot be allocated (the rule then keeps deciding). */
+   buffers cannot be allocated (the lane-change mode in effect before the call, rule,
+   logging or an earlier model, stays). */
 int ms_set_lc_model(void *sim, const float *params, float margin);
 
 /* Lane modifications (Sec. III-C "Python API": modification calls for lane speed limits and

@@ -956,7 +956,18 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
     if (r0) return r0;
   }
   s->veh_loaded = true;
-  if (int r = ensure_cand(s)) return r;
+  // a model set before the vehicles needs its candidate buffers now; without room for them
+  // the model is dropped, the rule decides, and the call still adds the vehicles (the error
+  // is returned once they are in place)
+  const int r_cand = ensure_cand(s);
+  const std::string cand_msg = r_cand ? s->err : std::string();
+  if (r_cand) {
+    int r0 = shape_grids(s, s->cfg, 1, 1, 1);   // the rule's decide instance
+    if (r0) {
+      s->veh_loaded = false;
+      return r0;
+    }
+  }
   // initial state
   std::vector<int> ids, lanes, ridx;
   std::vector<float> xs, vs;
@@ -972,6 +983,9 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
     s->veh_loaded = false;
     return r;
   }
+  if (r_cand)
+    return fail(s, r_cand, "vehicles added, but the learned lane-change model was dropped (" + cand_msg +
+                               "): the rule decides");
   return MS_OK;
 }
 
@@ -1047,11 +1061,8 @@ int ms_step_noalloc(void *sim, int n) {
   if (!s) return MS_ERR_ARG;
   if (!s->veh_loaded) return fail(s, MS_ERR_STATE, "add vehicles before stepping");
   if (n < 0) return fail(s, MS_ERR_ARG, "n < 0");
-  {
-    int r = export_guard(s, n);
-    if (r) return r;
-    s->t_host += n;
-  }
+  // every refusal comes before anything changes: the host step count (which picks the
+  // buffer an export copies) moves only once the steps are really enqueued
   if (s->n_tiles > MS_NOALLOC_MAX_TILES)
     return fail(s, MS_ERR_CAPACITY, "network has " + std::to_string(s->n_lanes) + " lanes; ms_step_noalloc takes at most " +
                                         std::to_string(MS_NOALLOC_MAX_TILES * LANE_TILE));
@@ -1065,6 +1076,11 @@ int ms_step_noalloc(void *sim, int n) {
     g_noalloc_addr[dev] = ptr;
   }
   unsigned long long *base = g_noalloc_addr[dev];
+  {
+    int r = export_guard(s, n);
+    if (r) return r;
+    s->t_host += n;
+  }
   StepArgs a = make_args(s);
   a.tile_agg = base;   // every step's first lane pass writes each tile before any is read
   cudaStream_t st = s->stream;
@@ -1982,6 +1998,18 @@ int ms_set_lc_model(void *sim, const float *params, float margin) {
       attr = true;
     }
   }
+  // the candidate buffers first: without room for them nothing changes (the mode in effect,
+  // a logging mode included, stays)
+  const int prev_mode = s->lc_mode;
+  const LcAux prev_lc = s->lc;
+  s->lc_mode = MODE_LEARN;
+  if (int r = ensure_cand(s)) {
+    const std::string msg = s->err;
+    s->lc_mode = prev_mode;
+    s->lc = prev_lc;
+    if (s->veh_loaded) shape_grids(s, s->cfg, s->cfg.f_decide, s->cfg.f_apply, s->cfg.f_bucket);
+    return fail(s, r, msg + " (the previous lane-change mode stays)");
+  }
   CK(cudaMemcpyAsync(s->d_theta, params, sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice, s->stream));
   k_mlp_pack<<<8, 256, 0, s->stream>>>(s->d_theta, s->d_model);
   CK(cudaGetLastError());
@@ -1990,9 +2018,7 @@ int ms_set_lc_model(void *sim, const float *params, float margin) {
   s->lc.model = s->d_model;
   s->lc.margin = margin;
   s->lc.stats = s->d_lcstats;
-  s->lc_mode = MODE_LEARN;
   s->lc.log_x = nullptr;
-  if (int r = ensure_cand(s)) return r;
   if (s->veh_loaded) return shape_grids(s, s->cfg, s->cfg.f_decide, s->cfg.f_apply, s->cfg.f_bucket);
   return MS_OK;
 }

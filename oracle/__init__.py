@@ -2,8 +2,8 @@
 
 Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline / reference arm may import
 this package.  It wraps oracle/moss_oracle.c (plain C, FP64, single-threaded) with ctypes
-and shares no code with the CUDA library.  Readings R1-R10 of the model are listed at the
-top of moss_oracle.c.
+and shares no code with the CUDA library.  Readings R1-R14, R17 and R19 of the model are
+listed at the top of moss_oracle.c.
 """
 from __future__ import annotations
 
@@ -49,7 +49,10 @@ _DBG_INT = ("active_before", "lead_kind", "lead_id")
 _DBG_FIELDS = [("active_before", "i"), ("lead_kind", "i"), ("lead_id", "i"), ("s_own", "d"),
                ("vl_own", "d"), ("a_own", "d"), ("lc_dir", "i"), ("lc_cand", "i"),
                ("tau_lead", "i"), ("tau_foll", "i"), ("old_foll", "i"), ("incentive", "d"),
-               ("a_use", "d"), ("flag", "i"), ("inserted", "i")]
+               ("a_use", "d"), ("flag", "i"), ("inserted", "i"),
+               # R19 learned lane change: per trip, logits 3 per trip, inputs 16 per trip
+               ("lc_learn", "i"), ("lc_margin", "d"), ("lc_logit", "d3"), ("lc_feat", "d16"),
+               ("lc_near", "i")]
 
 
 class _Debug(C.Structure):
@@ -85,6 +88,10 @@ def _load():
         lib.or_set_lane_limits.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
         lib.or_set_links.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
         lib.or_set_links.restype = C.c_int
+        lib.or_set_lc_model.argtypes = [C.c_void_p, C.c_void_p, C.c_double]
+        lib.or_set_lc_model.restype = C.c_int
+        lib.or_bf16.argtypes = [C.c_double]
+        lib.or_bf16.restype = C.c_double
         _lib = lib
     return _lib
 
@@ -95,6 +102,11 @@ def _p(a):
 
 def splitmix64(z: int) -> int:
     return int(_load().or_splitmix64(C.c_uint64(z & 0xFFFFFFFFFFFFFFFF)))
+
+
+def bf16(x: float) -> float:
+    """The oracle's BF16 rounding (nearest, ties to even) of one value."""
+    return float(_load().or_bf16(float(x)))
 
 
 class Oracle:
@@ -149,9 +161,12 @@ class Oracle:
         lib = _load()
         if not debug:
             return lib.or_step(self.h, None), None
-        arrs = {f: np.zeros(self.n, np.int32 if t == "i" else np.float64) for f, t in _DBG_FIELDS}
+        arrs = {f: np.zeros(self.n * (int(t[1:]) if len(t) > 1 else 1), np.int32 if t == "i" else np.float64)
+                for f, t in _DBG_FIELDS}
         dbg = _Debug(*[_p(arrs[f]) for f, _ in _DBG_FIELDS])
         err = lib.or_step(self.h, C.byref(dbg))
+        arrs["lc_logit"] = arrs["lc_logit"].reshape(self.n, 3)
+        arrs["lc_feat"] = arrs["lc_feat"].reshape(self.n, 16)
         return err, arrs
 
     def run(self, n_steps: int) -> int:
@@ -210,6 +225,18 @@ class Oracle:
         assert ln.shape == mk.shape
         if _load().or_set_links(self.h, int(ln.shape[0]), _p(ln), _p(mk)) != 0:
             raise ValueError("or_set_links: internal or out-of-range lane, or more than 32 links")
+
+    def set_lc_model(self, theta=None, margin: float = 0.2) -> None:
+        """R19: decide discretionary lane changes with the learned network (theta: 5443
+        floats in the C ABI's layout); None returns to the rule alone."""
+        if theta is None:
+            self._theta = None
+            _load().or_set_lc_model(self.h, None, 0.0)
+            return
+        self._theta = np.ascontiguousarray(theta, np.float32)
+        assert self._theta.shape == (5443,)
+        if _load().or_set_lc_model(self.h, _p(self._theta), float(margin)) != 0:
+            raise ValueError("margin outside [0, 1]")
 
     def set_ctrl_state(self, cs) -> None:
         cs = np.ascontiguousarray(np.asarray(cs, np.int32).reshape(-1, 3))

@@ -108,3 +108,47 @@ def predict(theta, X, margin=0.0):
     p = softmax(forward(theta, X)[0])
     s = np.sort(p, axis=1)
     return p.argmax(1), s[:, -1] - s[:, -2]
+
+
+def bf16(a):
+    """Nearest BF16 value (8 significant bits, ties to even) of every element, as float64."""
+    a = np.asarray(a, np.float64)
+    m, e = np.frexp(a)
+    return np.ldexp(np.rint(np.ldexp(m, 8)), e - 8)
+
+
+def forward_bf16(theta, X):
+    """The network as it runs in BF16 with FP32 accumulation: the inputs, the weights and
+    both hidden layers (after bias and ReLU) rounded to BF16; biases as given; sums in
+    float64.  Returns the logits and, per sample, whether a hidden value lies within an
+    FP32 path's accumulation error of a BF16 rounding boundary (K + 1) 2^-22 (sum of
+    |terms| + |bias|), K the fan-in: there the FP32 path may round the other way."""
+    p = unpack(theta)
+    W1, W2, W3 = bf16(p["W1"]), bf16(p["W2"]), bf16(p["W3"])
+    Xb = bf16(X)
+    u = 2.0 ** -22
+    near = np.zeros(Xb.shape[0], bool)
+
+    def layer(h, W, b):
+        nonlocal near
+        a = h @ W.T + b
+        mag = np.abs(h) @ np.abs(W).T + np.abs(b)
+        hv = np.maximum(a, 0.0)
+        r = bf16(hv)
+        # distance of hv to the midpoints between r and its BF16 neighbours
+        _, e = np.frexp(np.where(r > 0, r, 1.0))
+        ulp = np.ldexp(1.0, e - 8)
+        ulp_in = np.where(r == np.ldexp(1.0, e - 1), ulp / 2, ulp)
+        d = np.minimum(np.abs(hv - (r + ulp / 2)), np.abs(hv - (r - ulp_in / 2)))
+        near |= np.any((r > 0) & (d <= (W.shape[1] + 1) * u * mag), axis=1)
+        return r
+    h1 = layer(Xb, W1, p["b1"])
+    h2 = layer(h1, W2, p["b2"])
+    return h2 @ W3.T + p["b3"], near
+
+
+def margin_class(z):
+    """Softmax margin (top1 - top2) and argmax class (lowest index on ties) per row."""
+    p = softmax(z)
+    s = np.sort(p, axis=1)
+    return s[:, -1] - s[:, -2], p.argmax(1)

@@ -95,6 +95,29 @@
  *      incentive threshold is th + th_jitter (2u - 1), u = (SplitMix64(seed ^ 0x9E3779B97F4A7C15
  *      ^ c) >> 40) / 2^24, fixed for the trip (driver heterogeneity); the salt keeps these
  *      draws apart from the per-step gate draws of R4 (whose low 32 bits are c alone).
+ *  R19 Learned lane change (the surrogate of the learned form; not in the paper, off unless a
+ *      model is set): for a discretionary candidate of R4 that passed every safety test, a
+ *      16 -> 64 -> 64 -> 3 network (ReLU; softmax over stay / left / right) replaces the
+ *      incentive test.  BF16 with FP32 accumulation fixes where values are rounded: the 16
+ *      inputs, the weights, and both hidden layers after bias and ReLU are rounded to BF16
+ *      (round to nearest even); biases stay as given; sums here are FP64.  Its class is
+ *      taken when the softmax margin (top1 - top2) is >= margin, else the rule's decision;
+ *      a left or right class against the step's allowed direction means stay.  Inputs:
+ *      v/20, v0/20, own gap min(s,200)/100 (2 free), own closing speed (v-vl)/10 (v/10 at an
+ *      obstacle, 0 free), a_c/a_max, the allowed direction, target gap and closing speed
+ *      (same forms), new follower gap min(g,200)/100 (2 none), its speed /20 and its
+ *      acceleration behind the changer /a_max (0 none), a~_c/a_max, old follower speed /20
+ *      (0 none), distance to the lane end min(len-x,200)/100, leader speed /20 (0 obstacle,
+ *      1 free), old follower gap min(g,200)/100 (2 none).
+ *      Flag (the FP32 path rounds its own FP32 values, so a value whose FP64 form lies
+ *      within the FP32 path's error of a BF16 rounding boundary may round the other way
+ *      there): an input or hidden value within delta of a boundary is near; the decision is
+ *      recomputed with each near value rounded the other way, and the candidate is flagged
+ *      when any such change alters the decision, or when |margin - threshold| < 1e-3 plus
+ *      the summed margin changes.  delta: inputs 2^-22 |f| plus 1e-5 (gap and distance
+ *      inputs: FP32 gaps are within 1e-3 m) or 5e-5 (acceleration inputs: within 1e-4
+ *      m/s^2); hidden units (K + 1) 2^-22 (sum of |terms| + |bias|), K the fan-in, four
+ *      times the round-to-nearest bound of an FP32 sum of K products.
  */
 #include "moss_oracle.h"
 
@@ -148,6 +171,14 @@ struct or_sim {
   int *lane_closed;
   /* R17 dynamic lanes */
   unsigned char *link_off;   /* per successor entry: 1 = closed */
+  /* R19 learned lane change (NULL: the rule alone) */
+  struct or_mlp *mlp;
+};
+
+/* R19 network: weights rounded to BF16, biases as given, all held as doubles */
+struct or_mlp {
+  double w1[64][16], b1[64], w2[64][64], b2[64], w3[3][64], b3[3];
+  double margin;
 };
 
 /* ------------------------------------------------------------------------------------ */
@@ -464,6 +495,8 @@ typedef struct {
   int tau_kind;
   double tau_gap, tau_vl;
   double a_new;
+  int safe, mandatory, step_dir; /* every safety test passed; mandatory change; direction allowed */
+  double gF, vF, aF_new;         /* new follower (tau_foll >= 0): gap, speed, acceleration behind */
 } lc_t;
 
 
@@ -484,6 +517,8 @@ static lc_t lane_change(const or_sim *s, int c, const leader_t *own, double a_c,
   if (tau < 0) return r;
   if (s->lane_closed[tau]) return r;   /* R14 */
   int mandatory = !connects(s, l, en);
+  r.mandatory = mandatory;
+  r.step_dir = step_dir;
   if (mandatory) {
     /* nearest connecting lane on the same edge */
     int e = s->net.lane_edge[l];
@@ -534,7 +569,11 @@ static lc_t lane_change(const or_sim *s, int c, const leader_t *own, double a_c,
     aF_new = idm(s, s->v[Ft], v0_on(s, Ft, tau), 1, gF, v);
     mark(flag, aF_new + p->bsafe);
     if (aF_new < -p->bsafe) return r;
+    r.gF = gF;
+    r.vF = s->v[Ft];
+    r.aF_new = aF_new;
   }
+  r.safe = 1;
   r.a_new = idm(s, v, fmin(v0, s->lane_vmax[tau]), r.tau_kind != K_FREE, r.tau_gap, r.tau_vl);
   if (!mandatory) {
     double delta = r.a_new - a_c;
@@ -571,6 +610,234 @@ static lc_t lane_change(const or_sim *s, int c, const leader_t *own, double a_c,
   return r;
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* R19: learned lane change                                                              */
+/* ------------------------------------------------------------------------------------ */
+
+/* BF16 (8 significant bits, 8-bit exponent) nearest to x, ties to even */
+double or_bf16(double x) {
+  if (x == 0.0 || !isfinite(x)) return x;
+  int e;
+  const double m = frexp(x, &e);              /* x = m 2^e, 0.5 <= |m| < 1 */
+  if (e < -125) return nearbyint(ldexp(x, 133)) * ldexp(1.0, -133);   /* BF16 subnormals */
+  return ldexp(nearbyint(ldexp(m, 8)), e - 8);
+}
+
+/* the BF16 value next to r (itself BF16, nonzero) away from zero (up = 1) or toward it */
+static double bf16_next(double r, int up) {
+  const double a = fabs(r);
+  int e;
+  frexp(a, &e);                               /* a = 2^(e-1) ... 2^e */
+  const double ulp = ldexp(1.0, e - 1 - 7);
+  const double n = up ? a + ulp : (a == ldexp(1.0, e - 1) ? a - ulp / 2 : a - ulp);
+  return r < 0 ? -n : n;
+}
+
+/* v (FP64, rounded here to r) lies within delta of a BF16 rounding boundary: *alt is the
+   value the other side of that boundary rounds to */
+static int near_boundary(double v, double r, double delta, double *alt) {
+  if (fabs(v) < 1e-30 || r == 0.0) return 0;
+  const double out = bf16_next(r, 1), in = bf16_next(r, 0);
+  if (fabs(v - 0.5 * (r + out)) <= delta) { *alt = out; return 1; }
+  if (fabs(v - 0.5 * (r + in)) <= delta) { *alt = in; return 1; }
+  return 0;
+}
+
+static void mlp_hidden1(const struct or_mlp *m, const double xb[16], double a1[64], double s1[64]) {
+  for (int j = 0; j < 64; ++j) {
+    double acc = 0.0, mag = 0.0;
+    for (int k = 0; k < 16; ++k) {
+      acc += m->w1[j][k] * xb[k];
+      mag += fabs(m->w1[j][k] * xb[k]);
+    }
+    a1[j] = acc + m->b1[j];
+    s1[j] = mag + fabs(m->b1[j]);
+  }
+}
+
+static void mlp_hidden2(const struct or_mlp *m, const double h1[64], double a2[64], double s2[64]) {
+  for (int j = 0; j < 64; ++j) {
+    double acc = 0.0, mag = 0.0;
+    for (int k = 0; k < 64; ++k) {
+      acc += m->w2[j][k] * h1[k];
+      mag += fabs(m->w2[j][k] * h1[k]);
+    }
+    a2[j] = acc + m->b2[j];
+    s2[j] = mag + fabs(m->b2[j]);
+  }
+}
+
+static void mlp_logits(const struct or_mlp *m, const double h2[64], double z[3]) {
+  for (int q = 0; q < 3; ++q) {
+    double acc = 0.0;
+    for (int k = 0; k < 64; ++k) acc += m->w3[q][k] * h2[k];
+    z[q] = acc + m->b3[q];
+  }
+}
+
+/* softmax margin top1 - top2 and the argmax class (the lower class on a tie) */
+static double mlp_margin(const double z[3], int *cls) {
+  const double mx = fmax(z[0], fmax(z[1], z[2]));
+  double pr[3], sum = 0.0;
+  for (int q = 0; q < 3; ++q) sum += (pr[q] = exp(z[q] - mx));
+  for (int q = 0; q < 3; ++q) pr[q] /= sum;
+  int c = 0;
+  for (int q = 1; q < 3; ++q)
+    if (pr[q] > pr[c]) c = q;
+  double sec = -1.0;
+  for (int q = 0; q < 3; ++q)
+    if (q != c && pr[q] > sec) sec = pr[q];
+  *cls = c;
+  return pr[c] - sec;
+}
+
+static int class_dir(int cls) { return cls == 1 ? +1 : (cls == 2 ? -1 : 0); }
+
+/* decision (direction) from the network's class and margin, else the rule's */
+static int learned_dir(const struct or_mlp *m, int cls, double mg, int rule_dir, int step_dir) {
+  if (mg < m->margin) return rule_dir;
+  const int d = class_dir(cls);
+  return (d != 0 && d != step_dir) ? 0 : d;
+}
+
+/* the network from BF16 inputs xb, from hidden layer 1 (h1 given) or from hidden layer 2
+   (h2 given): margin and class */
+static double mlp_from(const struct or_mlp *m, const double *xb, const double *h1g, const double *h2g,
+                       double z[3], int *cls) {
+  double a1[64], s1[64], h1[64], a2[64], s2[64], h2[64];
+  if (!h2g) {
+    if (!h1g) {
+      mlp_hidden1(m, xb, a1, s1);
+      for (int j = 0; j < 64; ++j) h1[j] = or_bf16(fmax(a1[j], 0.0));
+      h1g = h1;
+    }
+    mlp_hidden2(m, h1g, a2, s2);
+    for (int j = 0; j < 64; ++j) h2[j] = or_bf16(fmax(a2[j], 0.0));
+    h2g = h2;
+  }
+  mlp_logits(m, h2g, z);
+  return mlp_margin(z, cls);
+}
+
+/* the 16 inputs of R19 for candidate c */
+static void lc_inputs(const or_sim *s, int c, const leader_t *own, double a_c, const lc_t *lc, double f[16]) {
+  const or_params *p = &s->p;
+  const double L = p->veh_len;
+  const int l = s->lane[c];
+  const double x = s->x[c], v = s->v[c];
+  const int k = s->pos[c] - s->seg_start[l];
+  const int O = k > 0 ? s->order[s->seg_start[l] + k - 1] : -1;   /* old follower */
+  f[0] = v / 20.0;
+  f[1] = (double)s->v0[c] / 20.0;
+  f[2] = own->kind != K_FREE ? fmin(own->gap, 200.0) / 100.0 : 2.0;
+  f[3] = own->kind == K_VEH ? (v - own->vl) / 10.0 : (own->kind == K_OBST ? v / 10.0 : 0.0);
+  f[4] = a_c / p->a;
+  f[5] = (double)lc->step_dir;
+  f[6] = lc->tau_kind != K_FREE ? fmin(lc->tau_gap, 200.0) / 100.0 : 2.0;
+  f[7] = lc->tau_kind == K_VEH ? (v - lc->tau_vl) / 10.0 : (lc->tau_kind == K_OBST ? v / 10.0 : 0.0);
+  f[8] = lc->tau_foll >= 0 ? fmin(lc->gF, 200.0) / 100.0 : 2.0;
+  f[9] = lc->tau_foll >= 0 ? lc->vF / 20.0 : 0.0;
+  f[10] = lc->tau_foll >= 0 ? lc->aF_new / p->a : 0.0;
+  f[11] = lc->a_new / p->a;
+  f[12] = O >= 0 ? s->v[O] / 20.0 : 0.0;
+  f[13] = fmin((double)s->net.lane_len[l] - x, 200.0) / 100.0;
+  f[14] = own->kind == K_VEH ? own->vl / 20.0 : (own->kind == K_OBST ? 0.0 : 1.0);
+  f[15] = O >= 0 ? fmin((x - s->x[O]) - L, 200.0) / 100.0 : 2.0;
+}
+
+/* absolute part of the input error bound (see R19) */
+static double input_delta(int k) {
+  switch (k) {
+    case 2: case 6: case 8: case 13: case 15: return 1e-5;   /* gaps, distance to the end */
+    case 4: case 10: case 11: return 5e-5;                   /* accelerations */
+    default: return 0.0;
+  }
+}
+
+typedef struct {
+  double f[16], z[3], margin;
+  int cls, near, dir;
+} learned_t;
+
+/* R19 decision of candidate c (rule decision lc->dir) with its flag */
+static learned_t learned_decision(const or_sim *s, int c, const leader_t *own, double a_c, const lc_t *lc,
+                                  int *flag) {
+  const struct or_mlp *m = s->mlp;
+  learned_t r;
+  lc_inputs(s, c, own, a_c, lc, r.f);
+  double xb[16], a1[64], s1[64], h1[64], a2[64], s2[64], h2[64];
+  for (int k = 0; k < 16; ++k) xb[k] = or_bf16(r.f[k]);
+  mlp_hidden1(m, xb, a1, s1);
+  for (int j = 0; j < 64; ++j) h1[j] = or_bf16(fmax(a1[j], 0.0));
+  mlp_hidden2(m, h1, a2, s2);
+  for (int j = 0; j < 64; ++j) h2[j] = or_bf16(fmax(a2[j], 0.0));
+  mlp_logits(m, h2, r.z);
+  r.margin = mlp_margin(r.z, &r.cls);
+  r.dir = learned_dir(m, r.cls, r.margin, lc->dir, lc->step_dir);
+  /* every value near a rounding boundary, rounded the other way */
+  const double u = ldexp(1.0, -22);
+  double sens = 0.0, alt, z2[3];
+  int changes = 0, c2;
+  r.near = 0;
+  for (int k = 0; k < 16; ++k) {
+    if (!near_boundary(r.f[k], xb[k], u * fabs(r.f[k]) + input_delta(k), &alt)) continue;
+    double xa[16];
+    memcpy(xa, xb, sizeof(xa));
+    xa[k] = alt;
+    const double mg = mlp_from(m, xa, NULL, NULL, z2, &c2);
+    sens += fabs(mg - r.margin);
+    changes |= learned_dir(m, c2, mg, lc->dir, lc->step_dir) != r.dir;
+    r.near++;
+  }
+  for (int j = 0; j < 64; ++j) {
+    const double hv = fmax(a1[j], 0.0);
+    if (!near_boundary(hv, h1[j], 17.0 * u * s1[j], &alt)) continue;
+    double ha[64];
+    memcpy(ha, h1, sizeof(ha));
+    ha[j] = alt;
+    const double mg = mlp_from(m, NULL, ha, NULL, z2, &c2);
+    sens += fabs(mg - r.margin);
+    changes |= learned_dir(m, c2, mg, lc->dir, lc->step_dir) != r.dir;
+    r.near++;
+  }
+  for (int j = 0; j < 64; ++j) {
+    const double hv = fmax(a2[j], 0.0);
+    if (!near_boundary(hv, h2[j], 65.0 * u * s2[j], &alt)) continue;
+    double ha[64];
+    memcpy(ha, h2, sizeof(ha));
+    ha[j] = alt;
+    const double mg = mlp_from(m, NULL, NULL, ha, z2, &c2);
+    sens += fabs(mg - r.margin);
+    changes |= learned_dir(m, c2, mg, lc->dir, lc->step_dir) != r.dir;
+    r.near++;
+  }
+  if (changes || fabs(r.margin - m->margin) < FLAG_EPS + sens) *flag = 1;
+  return r;
+}
+
+int or_set_lc_model(or_sim *s, const float *theta, double margin) {
+  if (!theta) {
+    free(s->mlp);
+    s->mlp = NULL;
+    return 0;
+  }
+  if (!(margin >= 0.0 && margin <= 1.0)) return -1;
+  if (!s->mlp) s->mlp = (struct or_mlp *)calloc(1, sizeof(struct or_mlp));
+  struct or_mlp *m = s->mlp;
+  const float *q = theta;   /* W1[64][16], b1[64], W2[64][64], b2[64], W3[3][64], b3[3] */
+  for (int j = 0; j < 64; ++j)
+    for (int k = 0; k < 16; ++k) m->w1[j][k] = or_bf16((double)*q++);
+  for (int j = 0; j < 64; ++j) m->b1[j] = (double)*q++;
+  for (int j = 0; j < 64; ++j)
+    for (int k = 0; k < 64; ++k) m->w2[j][k] = or_bf16((double)*q++);
+  for (int j = 0; j < 64; ++j) m->b2[j] = (double)*q++;
+  for (int j = 0; j < 3; ++j)
+    for (int k = 0; k < 64; ++k) m->w3[j][k] = or_bf16((double)*q++);
+  for (int j = 0; j < 3; ++j) m->b3[j] = (double)*q++;
+  m->margin = margin;
+  return 0;
+}
+
 int or_step(or_sim *s, or_debug *dbg) {
   const or_params *p = &s->p;
   const double L = p->veh_len;
@@ -603,6 +870,13 @@ int or_step(or_sim *s, or_debug *dbg) {
     leader_t own = own_leader(s, c, &flag);
     double a_c = idm(s, v, v0_on(s, c, s->lane[c]), own.kind != K_FREE, own.gap, own.vl);
     lc_t lc = lane_change(s, c, &own, a_c, &flag);
+    int learned = 0;
+    learned_t ln;
+    if (s->mlp && lc.cand && lc.safe && !lc.mandatory) {   /* R19 */
+      ln = learned_decision(s, c, &own, a_c, &lc, &flag);
+      lc.dir = ln.dir;
+      learned = 1;
+    }
     double a_use = lc.dir ? fmin(a_c, lc.a_new) : a_c;
     /* R6 */
     double vraw = v + a_use * p->dt;
@@ -672,6 +946,15 @@ int or_step(or_sim *s, or_debug *dbg) {
       dbg->incentive[c] = lc.incentive;
       dbg->a_use[c] = a_use;
       dbg->flag[c] = flag;
+      if (dbg->lc_learn) {
+        dbg->lc_learn[c] = learned;
+        if (learned) {
+          dbg->lc_margin[c] = ln.margin;
+          dbg->lc_near[c] = ln.near;
+          for (int q = 0; q < 3; ++q) dbg->lc_logit[3 * c + q] = ln.z[q];
+          for (int q = 0; q < 16; ++q) dbg->lc_feat[16 * c + q] = ln.f[q];
+        }
+      }
     }
   }
   /* R8 departures, decided on the snapshot (before the update is applied) */
@@ -863,7 +1146,7 @@ void or_destroy(or_sim *s) {
   free(s->dep_lane); free(s->order); free(s->pos); free(s->seg_start); free(s->seg_cnt);
   free(s->n_lane); free(s->n_rp); free(s->n_status); free(s->n_x); free(s->n_v);
   free(s->vsum); free(s->vcnt); free(s->q_off); free(s->q_head); free(s->q_ids);
-  free(s->pred_off); free(s->pred_ids);
+  free(s->pred_off); free(s->pred_ids); free(s->mlp);
   free(s);
 }
 

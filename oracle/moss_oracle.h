@@ -53,6 +53,12 @@ typedef struct {
   double *a_use;
   int *flag;         /* 1 if any decision margin was within eps of its threshold */
   int *inserted;     /* trip ids inserted this step get 1 */
+  /* R19 learned lane change (all NULL, or all set): lc_learn 1 where the network decided;
+     there its softmax margin, logits [3 per trip], inputs before rounding [16 per trip]
+     and the number of its values near a BF16 rounding boundary */
+  int *lc_learn;
+  double *lc_margin, *lc_logit, *lc_feat;
+  int *lc_near;
 } or_debug;
 
 typedef struct or_sim or_sim;
@@ -87,6 +93,12 @@ void or_set_ctrl_state(or_sim *s, const int *in);
    Returns -1 (nothing changed) for an internal or out-of-range lane or more than 32 links. */
 int or_set_links(or_sim *s, int n, const int *lanes, const unsigned *open_mask);
 uint64_t or_splitmix64(uint64_t state);
+/* R19: the learned lane-change network (theta: 5443 floats, W1[64][16], b1[64], W2[64][64],
+   b2[64], W3[3][64], b3[3], out x in) and its margin in [0, 1]; theta NULL: the rule alone.
+   Returns -1 for a margin outside [0, 1]. */
+int or_set_lc_model(or_sim *s, const float *theta, double margin);
+/* BF16 value nearest to x (round to nearest, ties to even) */
+double or_bf16(double x);
 /* neighbour search on the current snapshot (for the brute-force check): for each trip id:
    own-lane leader, own-lane follower, left-lane leader/follower, right-lane leader/follower
    (ids or -1) -> out[6*n_trips] */

@@ -1,0 +1,199 @@
+"""Pins of the oracle's learned lane change (reading R19) and of its BF16 network.
+
+The learned form replaces the MOBIL incentive test of safe discretionary candidates by a
+16 -> 64 -> 64 -> 3 network run in BF16 with FP32 accumulation (the paper's lane-change
+model is rule-based, Sec. III-A; the surrogate is this library's addition).  These tests pin
+the oracle's side of it against things other than itself:
+  - BF16 rounding against values that follow from the format (8 significant bits, round
+    to nearest, ties to even);
+  - the BF16 forward against the plain FP64 forward where no value needs rounding;
+  - the in-step decision against closed forms: probe networks whose decision is a known
+    step function of one physical quantity (speed, distance to the lane end, own gap), a
+    network that always stays, and the full-fallback network, which must reproduce the
+    rule step bit for bit over a whole run.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from paper_2405_12520_b300 import synth
+
+P = synth.default_params()
+
+
+# --- BF16 rounding ------------------------------------------------------------------
+
+# value -> nearest BF16 (8 significant bits).  Around 1 the spacing is 2^-7: 1 + 2^-8 is
+# halfway between 1 and 1 + 2^-7 and goes to the even significand (1); 1 + 3 * 2^-8 is
+# halfway between 1 + 2^-7 and 1 + 2^-6 and goes to 1 + 2^-6.  0.1 = 1.6 * 2^-4 and
+# 1.6 * 128 = 204.8 -> 205, so 205 / 128 / 16.  Around 256 the spacing is 2: 257 -> 256 and
+# 259 -> 260 (ties to even), 258 is exact.  pi: 3.14159 / 2 * 128 = 201.06 -> 201 -> 3.140625.
+GOLDEN = [(1.0 + 2.0 ** -8, 1.0), (1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -6), (0.1, 205.0 / 128 / 16),
+          (257.0, 256.0), (259.0, 260.0), (258.0, 258.0), (-3.14159, -3.140625),
+          (1.0 + 2.0 ** -8 + 2.0 ** -20, 1.0 + 2.0 ** -7), (0.0, 0.0), (-0.75, -0.75)]
+
+
+@pytest.mark.parametrize("x,want", GOLDEN)
+def test_bf16_rounding_follows_the_format(x, want):
+    assert oracle.bf16(x) == want
+    assert mlp.bf16(np.array([x]))[0] == want
+
+
+def test_bf16_forward_equals_plain_forward_when_nothing_rounds():
+    """Small integer weights and inputs, halves as biases: every value of the network is
+    exactly representable in BF16, so rounding changes nothing and the BF16 forward must
+    equal the plain FP64 forward exactly."""
+    rng = np.random.default_rng(0)
+    p = {"W1": rng.integers(-2, 3, (64, 16)).astype(float), "b1": rng.integers(-2, 3, 64) * 0.5,
+         "W2": rng.integers(-1, 2, (64, 64)).astype(float) / 4, "b2": rng.integers(-2, 3, 64) * 0.5,
+         "W3": rng.integers(-1, 2, (3, 64)).astype(float) / 8, "b3": np.array([0.5, -0.5, 0.0])}
+    theta = mlp.pack(p)
+    X = rng.integers(-3, 4, (200, 16)).astype(float) / 4
+    z, near = mlp.forward_bf16(theta, X)
+    z0, (_, a1, h1, a2, h2) = mlp.forward(theta, X)
+    # integer inputs/weights keep h1 in quarters below 2^6 and h2 in sixteenths: exact in BF16
+    assert np.array_equal(mlp.bf16(h1), h1) and np.array_equal(mlp.bf16(h2), h2)
+    assert np.array_equal(z, z0)
+
+
+def test_bf16_forward_rounds_where_the_kernel_rounds():
+    """A network that doubles input 0 through a single path: an input of 1 + 2^-7 + 2^-9 is
+    rounded to 1 + 2^-7 on entry (not kept), and a hidden value 3 * (1 + 2^-7) = 3.0234375 is
+    rounded to 3.03125 (8 significant bits) before the next layer."""
+    p = {k: np.zeros(s) for k, s in mlp.SHAPES}
+    p["W1"][0, 0] = 3.0
+    p["W2"][0, 0] = 1.0
+    p["W3"][1, 0] = 1.0
+    theta = mlp.pack(p)
+    X = np.zeros((1, 16))
+    X[0, 0] = 1.0 + 2.0 ** -7 + 2.0 ** -9
+    z, _ = mlp.forward_bf16(theta, X)
+    assert z[0, 1] == 3.03125 and z[0, 0] == 0.0 and z[0, 2] == 0.0
+
+
+# --- the in-step learned decision ----------------------------------------------------
+
+def _workload():
+    net = synth.grid_network(6, 6, 3, 300.0, 30, 3, "wave")
+    dem = synth.merge_demands(synth.place_vehicles(net, 2500, seed=41, min_spacing=7.0, internal_frac=0.2),
+                              synth.uniform_trips(net, 300, 30, seed=42))
+    return net, dem
+
+
+def _probe(k: int, theta_k: float, G: float = 256.0, K: float = 16.0):
+    """Probe network: change lane in the step's allowed direction when input k is at least
+    theta_k + 1/G, stay when it is at most theta_k.  Layer 1: q = relu(1 + G (theta_k - f_k)),
+    u = relu(f5), w = relu(-f5) (f5 = allowed direction); layer 2: s_l = relu(u - q),
+    s_r = relu(w - q) (q = 0 past the threshold, >= 1 below it); logits (K/2, K s_l, K s_r):
+    softmax margin 0.9993 either way."""
+    p = {k_: np.zeros(s) for k_, s in mlp.SHAPES}
+    p["W1"][0, k] = -G
+    p["b1"][0] = 1.0 + G * theta_k
+    p["W1"][1, 5] = 1.0
+    p["W1"][2, 5] = -1.0
+    p["W2"][0, 1] = 1.0
+    p["W2"][0, 0] = -1.0
+    p["W2"][1, 2] = 1.0
+    p["W2"][1, 0] = -1.0
+    p["W3"][1, 0] = K
+    p["W3"][2, 1] = K
+    p["b3"][0] = K / 2
+    return mlp.pack(p).astype(np.float32)
+
+
+def _pair(net, dem, t0, theta, margin=0.2):
+    """The same state stepped once by the rule and by the learned oracle, with records."""
+    rule = oracle.Oracle(net, dem, P)
+    lrn = oracle.Oracle(net, dem, P)
+    lrn.set_lc_model(theta, margin)
+    st = rule.state()
+    for o in (rule, lrn):
+        o.set_state(st["status"], st["lane"], st["x"], st["v"], st["rp"], t0, st["t_arr"])
+    _, dr = rule.step(debug=True)
+    _, dl = lrn.step(debug=True)
+    return st, dr, dl
+
+
+@pytest.mark.parametrize("t0", [0, 1])
+def test_learned_always_stay_network_removes_only_discretionary_changes(t0):
+    p = {k: np.zeros(s) for k, s in mlp.SHAPES}
+    p["b3"][0] = 8.0
+    theta = mlp.pack(p).astype(np.float32)
+    net, dem = _workload()
+    st, dr, dl = _pair(net, dem, t0, theta)
+    act = dr["active_before"] == 1
+    L = dl["lc_learn"] == 1
+    assert L.sum() > 50, L.sum()
+    assert np.all(dr["lc_cand"][L] == 1)            # the network decides candidates only
+    assert np.all(dl["lc_dir"][L] == 0)              # ... and always says stay
+    assert (dr["lc_dir"][L] != 0).sum() > 0          # the rule would have changed some
+    rest = act & ~L                                  # mandatory changes and all others: the rule's
+    assert np.array_equal(dl["lc_dir"][rest], dr["lc_dir"][rest])
+    assert np.all(dl["lc_margin"][L] > 0.99)
+    assert np.all(dl["flag"][L] == dr["flag"][L])    # far from the margin: no new flags
+
+
+@pytest.mark.parametrize("k,theta_k,quantity,lo,hi", [
+    (0, 0.5, "speed", 9.8, 10.3),               # input 0 = v / 20: change above 10 m/s
+    (13, 1.0, "to_end", 98.0, 102.0),           # input 13 = min(len - x, 200) / 100
+    (2, 0.25, "gap", 24.5, 25.6),               # input 2 = min(own gap, 200) / 100, 2 if free
+])
+@pytest.mark.parametrize("t0", [0, 1])
+def test_probe_network_decides_by_one_physical_quantity(k, theta_k, quantity, lo, hi, t0):
+    net, dem = _workload()
+    st, dr, dl = _pair(net, dem, t0, _probe(k, theta_k))
+    L = np.nonzero(dl["lc_learn"] == 1)[0]
+    assert L.size > 50
+    step_dir = 1 if t0 % 2 == 0 else -1
+    if quantity == "speed":
+        q = st["v"][L]
+    elif quantity == "to_end":
+        q = np.asarray(net.lane_len, np.float64)[st["lane"][L]] - st["x"][L]
+    else:
+        q = np.where(dl["lead_kind"][L] == 0, np.inf, dl["s_own"][L])
+    up, down = q > hi, q < lo
+    assert up.sum() > 5 and down.sum() > 5, (up.sum(), down.sum())
+    assert np.all(dl["lc_dir"][L[up]] == step_dir)
+    assert np.all(dl["lc_dir"][L[down]] == 0)
+    # the inputs the oracle recorded are the quantity in the stated scale
+    f = dl["lc_feat"][L, k]
+    scale = {"speed": q / 20.0, "to_end": np.minimum(q, 200.0) / 100.0,
+             "gap": np.where(np.isinf(q), 2.0, np.minimum(q, 200.0) / 100.0)}[quantity]
+    np.testing.assert_allclose(f, scale, rtol=1e-12, atol=1e-12)
+
+
+def test_full_fallback_network_is_the_rule_over_a_run():
+    """Margin 1: every learned candidate falls back to the rule, so a 400-step run with the
+    learned form must give the rule's run bit for bit."""
+    net, dem = synth.small_grid_workload(5)
+    theta = (mlp.init(3) * 1e-3).astype(np.float32)
+    rule = oracle.Oracle(net, dem, P)
+    lrn = oracle.Oracle(net, dem, P)
+    lrn.set_lc_model(theta, 1.0)
+    n_learn = 0
+    for k in range(400):
+        _, _ = rule.step()
+        _, dl = lrn.step(debug=(k % 50 == 0))
+        if dl is not None:
+            n_learn += int((dl["lc_learn"] == 1).sum())
+    a, b = rule.state(), lrn.state()
+    for key in ("status", "lane", "x", "v", "rp", "t_arr"):
+        assert np.array_equal(a[key], b[key]), key
+    assert n_learn > 0
+
+
+def test_learned_logits_match_the_numpy_bf16_forward():
+    """The C oracle's network and oracle/mlp.forward_bf16 (the same BF16 rounding points)
+    agree on every learned candidate of a step: two restatements of one definition."""
+    net, dem = _workload()
+    theta = (mlp.init(5) + np.random.default_rng(1).normal(scale=0.05, size=mlp.N_PARAMS)).astype(np.float32)
+    st, dr, dl = _pair(net, dem, 0, theta, margin=0.0)
+    L = np.nonzero(dl["lc_learn"] == 1)[0]
+    z, _ = mlp.forward_bf16(theta.astype(np.float64), dl["lc_feat"][L])
+    np.testing.assert_allclose(dl["lc_logit"][L], z, rtol=1e-12, atol=1e-12)
+    mg, cls = mlp.margin_class(z)
+    np.testing.assert_allclose(dl["lc_margin"][L], mg, rtol=1e-12, atol=1e-12)
+    # margin 0: the class decides; at t0 = 0 only left is allowed, so right means stay
+    assert np.array_equal(dl["lc_dir"][L], np.where(cls == 1, 1, 0))
+    assert (cls == 1).sum() > 0 and (cls != 1).sum() > 0

@@ -161,6 +161,11 @@ typedef struct ms_debug {
   int *active_before, *lead_kind, *lead_id, *lc_dir, *lc_cand, *tau_lead, *tau_foll,
       *old_foll, *flag, *inserted;
   float *s_own, *vl_own, *a_own, *incentive, *a_use;
+  /* learned lane change (a model set): lc_learn 1 where the network decided; there its
+     softmax margin, logits (lc_logit [3 * n_trips]) and BF16 inputs (lc_feat
+     [16 * n_trips]); any may be NULL */
+  int *lc_learn;
+  float *lc_margin, *lc_logit, *lc_feat;
 } ms_debug;
 
 /* Create a simulation bound to a CUDA stream (cudaStream_t, or NULL for the default
@@ -398,8 +403,10 @@ int ms_mlp_train_step(const void *x, const int *y, const int *idx, int batch, fl
 int ms_mlp_grad(const void *x, const int *y, const int *idx, int batch, const float *theta,
                 const float *class_w, float *work, float *grad, void *cuda_stream);
 
-/* Class and softmax margin of n samples (device outputs cls [n] int, margin [n] float). */
-int ms_mlp_predict(const void *x, int n, const float *theta, float *work, int *cls, float *margin,
+/* Class and softmax margin (top1 - top2) of n samples x (device, bf16 [n][16]): device
+   outputs cls [n] int, margin [n] float and, if not NULL, the logits [n][3] float.
+   theta: device FP32 [5443]; work: device scratch of MS_MLP_WORK_FLOATS floats. */
+int ms_mlp_predict(const void *x, int n, const float *theta, float *work, int *cls, float *margin, float *logits,
                    void *cuda_stream);
 
 const char *ms_last_error(void *sim);

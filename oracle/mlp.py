@@ -120,9 +120,11 @@ def bf16(a):
 def forward_bf16(theta, X):
     """The network as it runs in BF16 with FP32 accumulation: the inputs, the weights and
     both hidden layers (after bias and ReLU) rounded to BF16; biases as given; sums in
-    float64.  Returns the logits and, per sample, whether a hidden value lies within an
-    FP32 path's accumulation error of a BF16 rounding boundary (K + 1) 2^-22 (sum of
-    |terms| + |bias|), K the fan-in: there the FP32 path may round the other way."""
+    float64.  Returns the logits; per sample, whether a hidden value lies within an FP32
+    path's accumulation error of a BF16 rounding boundary, (K + 1) 2^-22 (sum of |terms| +
+    |bias|), K the fan-in (there the FP32 path may round the other way); and per logit the
+    same bound on the FP32 sum of the last layer (the logit tolerance where no hidden value
+    is near a boundary)."""
     p = unpack(theta)
     W1, W2, W3 = bf16(p["W1"]), bf16(p["W2"]), bf16(p["W3"])
     Xb = bf16(X)
@@ -144,7 +146,8 @@ def forward_bf16(theta, X):
         return r
     h1 = layer(Xb, W1, p["b1"])
     h2 = layer(h1, W2, p["b2"])
-    return h2 @ W3.T + p["b3"], near
+    zb = (W3.shape[1] + 1) * u * (np.abs(h2) @ np.abs(W3).T + np.abs(p["b3"]))
+    return h2 @ W3.T + p["b3"], near, zb
 
 
 def margin_class(z):
@@ -152,3 +155,81 @@ def margin_class(z):
     p = softmax(z)
     s = np.sort(p, axis=1)
     return s[:, -1] - s[:, -2], p.argmax(1)
+
+
+def _near_alt(v, r, delta):
+    """Values v (rounded to BF16 as r) within delta of a BF16 rounding boundary, and the
+    value the other side of that boundary rounds to."""
+    a = np.abs(r)
+    _, e = np.frexp(np.where(a > 0, a, 1.0))
+    ulp = np.ldexp(1.0, e - 8)
+    ulp_in = np.where(a == np.ldexp(1.0, e - 1), ulp / 2, ulp)
+    up, dn = a + ulp, a - ulp_in
+    av = np.abs(v)
+    n_up = (a > 0) & (np.abs(av - (a + up) / 2) <= delta)
+    n_dn = (a > 0) & ~n_up & (np.abs(av - (a + dn) / 2) <= delta)
+    alt = np.sign(r) * np.where(n_up, up, dn)
+    return n_up | n_dn, alt
+
+
+def flip_sensitivity(theta, X, thr, in_delta=None, chunk=65536):
+    """The BF16 network of forward_bf16 with, per sample, the effect of every value that
+    an FP32 path might round the other way (reading R19's flag rule): each hidden value
+    within (K + 1) 2^-22 (sum of |terms| + |bias|) of a BF16 rounding boundary, and each
+    input within in_delta of one (in_delta [n, 16] or None: the inputs are given in BF16),
+    is rounded the other way alone and the network re-evaluated.  Returns the logits z,
+    margin m, class c, a logit bound (last-layer accumulation bound plus the summed logit
+    changes), the summed margin changes, and whether any such change alters the decision
+    (class, or fallback when m < thr)."""
+    p = unpack(theta)
+    W1, W2, W3 = bf16(p["W1"]), bf16(p["W2"]), bf16(p["W3"])
+    b1, b2, b3 = p["b1"], p["b2"], p["b3"]
+    X = np.asarray(X, np.float64)
+    Xb = bf16(X)
+    u = 2.0 ** -22
+
+    def decision(c, m):
+        return np.where(m < thr, -1, c)
+
+    def tail(h1):   # layers 2 and 3 from BF16 hidden layer 1
+        a2 = h1 @ W2.T + b2
+        return a2, bf16(np.maximum(a2, 0.0))
+
+    a1 = Xb @ W1.T + b1
+    h1 = bf16(np.maximum(a1, 0.0))
+    n1, alt1 = _near_alt(np.maximum(a1, 0.0), h1, 17 * u * (np.abs(Xb) @ np.abs(W1).T + np.abs(b1)))
+    a2, h2 = tail(h1)
+    n2, alt2 = _near_alt(np.maximum(a2, 0.0), h2, 65 * u * (np.abs(h1) @ np.abs(W2).T + np.abs(b2)))
+    z = h2 @ W3.T + b3
+    zb = 65 * u * (np.abs(h2) @ np.abs(W3).T + np.abs(b3))
+    m, c = margin_class(z)
+    dec = decision(c, m)
+    n = X.shape[0]
+    msens = np.zeros(n)
+    changed = np.zeros(n, bool)
+
+    def account(s, z2):
+        m2, c2 = margin_class(z2)
+        np.add.at(msens, s, np.abs(m2 - m[s]))
+        np.add.at(zb, s, np.abs(z2 - z[s]))
+        changed[s[decision(c2, m2) != dec[s]]] = True
+
+    s, j = np.nonzero(n2)                     # hidden layer 2: the logits change linearly
+    for o in range(0, s.size, chunk):
+        ss, jj = s[o:o + chunk], j[o:o + chunk]
+        account(ss, z[ss] + (alt2[ss, jj] - h2[ss, jj])[:, None] * W3[:, jj].T)
+    s, j = np.nonzero(n1)                     # hidden layer 1: layer 2 rounds again
+    for o in range(0, s.size, chunk):
+        ss, jj = s[o:o + chunk], j[o:o + chunk]
+        a2p = a2[ss] + (alt1[ss, jj] - h1[ss, jj])[:, None] * W2[:, jj].T
+        account(ss, bf16(np.maximum(a2p, 0.0)) @ W3.T + b3)
+    if in_delta is not None:                  # inputs: the whole network again
+        ni, alti = _near_alt(X, Xb, in_delta)
+        s, k = np.nonzero(ni)
+        for o in range(0, s.size, chunk):
+            ss, kk = s[o:o + chunk], k[o:o + chunk]
+            xa = Xb[ss].copy()
+            xa[np.arange(ss.size), kk] = alti[ss, kk]
+            _, h2a = tail(bf16(np.maximum(xa @ W1.T + b1, 0.0)))
+            account(ss, h2a @ W3.T + b3)
+    return z, m, c, zb, msens, changed

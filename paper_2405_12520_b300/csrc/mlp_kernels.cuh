@@ -360,9 +360,10 @@ __global__ void k_mlp_scale(const float *grad, const float *stats, float *out) {
     out[k] = grad[k] * inv;
 }
 
-// Predictions (class, softmax margin top1 - top2) for n samples; 4 warps x 16 rows per block
+// Predictions (class, softmax margin top1 - top2, optionally the logits) for n samples; 4 warps
+// x 16 rows per block
 __global__ void __launch_bounds__(128) k_mlp_predict(const __nv_bfloat16 *X, int n, const MlpDev *model,
-                                                     int *cls, float *margin) {
+                                                     int *cls, float *margin, float *logits) {
   __shared__ MlpDev w;
   __shared__ __align__(16) __nv_bfloat16 sX[64 * MLP_IN];
   __shared__ __align__(16) __nv_bfloat16 sH1[64 * MLP_H];
@@ -396,6 +397,11 @@ __global__ void __launch_bounds__(128) k_mlp_predict(const __nv_bfloat16 *X, int
       if (p2 > top) { c = 2; sec = fmaxf(p0, p1); top = p2; }
       cls[r0 + tid] = c;
       margin[r0 + tid] = top - sec;
+      if (logits) {
+        logits[(size_t)(r0 + tid) * 3] = z0;
+        logits[(size_t)(r0 + tid) * 3 + 1] = z1;
+        logits[(size_t)(r0 + tid) * 3 + 2] = z2;
+      }
     }
   }
 }

@@ -920,6 +920,8 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
     DALLOC(d.flag, N); DALLOC(d.s_own, N); DALLOC(d.vl_own, N); DALLOC(d.a_own, N);
     DALLOC(d.incentive, N); DALLOC(d.a_use, N); DALLOC(d.trip_ins, N); DALLOC(d.trip_flag, N);
     DALLOC(d.arr_flag, s->n_lanes);
+    DALLOC(d.lc_learn, N); DALLOC(d.lc_margin, N); DALLOC(d.lc_logit, (size_t)3 * N);
+    DALLOC(d.lc_feat, (size_t)MLP_IN * N);
     CK(cudaMemset(d.trip_ins, 0, sizeof(int) * N));
     CK(cudaMemset(d.trip_flag, 0, sizeof(int) * N));
     CK(cudaMemset(d.arr_flag, 0, sizeof(int) * s->n_lanes));
@@ -1294,8 +1296,19 @@ int ms_read_debug(void *sim, ms_debug *out) {
       (r = scat_i(out->old_foll, d.old_foll)) || (r = scat_i(out->flag, d.flag)) ||
       (r = scat_f(out->s_own, d.s_own)) || (r = scat_f(out->vl_own, d.vl_own)) ||
       (r = scat_f(out->a_own, d.a_own)) || (r = scat_f(out->incentive, d.incentive)) ||
-      (r = scat_f(out->a_use, d.a_use)))
+      (r = scat_f(out->a_use, d.a_use)) || (r = scat_i(out->lc_learn, d.lc_learn)) ||
+      (r = scat_f(out->lc_margin, d.lc_margin)))
     return r;
+  // per-vehicle vectors of the learned decision: logits (3) and inputs (16)
+  auto scat_v = [&](float *dst, const float *src, int w) -> int {
+    if (!dst || !n) return MS_OK;
+    std::vector<float> buf((size_t)w * n);
+    CK(cudaMemcpy(buf.data(), src, buf.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n; ++i)
+      for (int q = 0; q < w; ++q) dst[(size_t)id[i] * w + q] = buf[(size_t)i * w + q];
+    return MS_OK;
+  };
+  if ((r = scat_v(out->lc_logit, d.lc_logit, 3)) || (r = scat_v(out->lc_feat, d.lc_feat, MLP_IN))) return r;
   std::vector<int> stamp(s->n_trips);
   if (out->inserted) {
     CK(cudaMemcpy(stamp.data(), d.trip_ins, s->n_trips * sizeof(int), cudaMemcpyDeviceToHost));
@@ -2097,14 +2110,15 @@ int ms_mlp_grad(const void *x, const int *y, const int *idx, int batch, const fl
   return MS_OK;
 }
 
-int ms_mlp_predict(const void *x, int n, const float *theta, float *work, int *cls, float *margin,
+int ms_mlp_predict(const void *x, int n, const float *theta, float *work, int *cls, float *margin, float *logits,
                    void *cuda_stream) {
   Sim *s = nullptr;
   if (!x || n <= 0 || !theta || !work || !cls || !margin) return MS_ERR_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   MlpDev *model = reinterpret_cast<MlpDev *>(work + MLP_NPARAM + 4);
   k_mlp_pack<<<8, 256, 0, st>>>(theta, model);
-  k_mlp_predict<<<std::min(4096, (n + 63) / 64), 128, 0, st>>>((const __nv_bfloat16 *)x, n, model, cls, margin);
+  k_mlp_predict<<<std::min(4096, (n + 63) / 64), 128, 0, st>>>((const __nv_bfloat16 *)x, n, model, cls, margin,
+                                                                logits);
   CK(cudaGetLastError());
   return MS_OK;
 }

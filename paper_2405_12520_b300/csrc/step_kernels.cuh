@@ -125,6 +125,10 @@ struct DebugOut {
   float *s_own, *vl_own, *a_own, *incentive, *a_use;
   int *trip_ins, *trip_flag;   // step stamps (t+1) per trip id
   int *arr_flag;               // per lane: a flagged vehicle enters it this step
+  // learned lane change: 1 where the network decided; its softmax margin, logits [3 per
+  // vehicle] and BF16 inputs [16 per vehicle]
+  int *lc_learn;
+  float *lc_margin, *lc_logit, *lc_feat;
 };
 
 // Per-vehicle result of k_decide, consumed by k_apply: new x, new v, and a code word
@@ -758,6 +762,7 @@ __device__ __forceinline__ int vehicle_finish(const StepArgs &a, const Soa &S, i
     a.dbg.incentive[i] = u.lc.inc;
     a.dbg.a_use[i] = u.a_use;
     a.dbg.flag[i] = u.flag;
+    a.dbg.lc_learn[i] = 0;   // k_learn marks the vehicles its network decided
   }
   return leave;
 }
@@ -1026,6 +1031,8 @@ __global__ void __launch_bounds__(LEARN_THREADS) k_learn(StepArgs a) {
       float f[MLP_IN];
       lc_features(a, S, i, u, c, f);
       for (int q = 0; q < MLP_IN; ++q) X[wl * MLP_IN + q] = __float2bfloat16_rn(f[q]);
+      if constexpr (DBG)
+        for (int q = 0; q < MLP_IN; ++q) a.dbg.lc_feat[(size_t)i * MLP_IN + q] = __bfloat162float(X[wl * MLP_IN + q]);
     } else {
       for (int q = 0; q < MLP_IN; ++q) X[wl * MLP_IN + q] = __float2bfloat16_rn(0.f);
     }
@@ -1047,6 +1054,13 @@ __global__ void __launch_bounds__(LEARN_THREADS) k_learn(StepArgs a) {
       fb = top - sec < a.lc.margin;
       if (!fb) fin = (cls != 0 && lc_dir(cls) != u.lc.step_dir) ? 0 : cls;
       dir = lc_dir(fin);
+      if constexpr (DBG) {
+        mark(u.flag, (top - sec) - a.lc.margin);
+        a.dbg.lc_margin[i] = top - sec;
+        a.dbg.lc_logit[(size_t)i * 3] = z0;
+        a.dbg.lc_logit[(size_t)i * 3 + 1] = z1;
+        a.dbg.lc_logit[(size_t)i * 3 + 2] = z2;
+      }
     }
     __syncwarp();   // the next chunk overwrites X and Z
     if (a.lc.stats) {
@@ -1066,6 +1080,7 @@ __global__ void __launch_bounds__(LEARN_THREADS) k_learn(StepArgs a) {
     if (listed) {
       if (vehicle_finish<DBG>(a, S, i, u, c, dir)) atomicOr(&a.leave[i >> 5], 1u << (i & 31));
       if (u.kind == U_CHANGE || u.kind == U_TRANSFER) arrival_records<DBG>(a, i, u, c);
+      if constexpr (DBG) a.dbg.lc_learn[i] = 1;
     }
   }
 }

@@ -64,10 +64,11 @@ class ms_metrics(C.Structure):
 _DBG_I = ("active_before", "lead_kind", "lead_id", "lc_dir", "lc_cand", "tau_lead", "tau_foll",
           "old_foll", "flag", "inserted")
 _DBG_F = ("s_own", "vl_own", "a_own", "incentive", "a_use")
+_DBG_LC = ("lc_learn", "lc_margin", "lc_logit", "lc_feat")   # learned lane change
 
 
 class ms_debug(C.Structure):
-    _fields_ = [(f, C.c_void_p) for f in _DBG_I + _DBG_F]
+    _fields_ = [(f, C.c_void_p) for f in _DBG_I + _DBG_F + _DBG_LC]
 
 
 _lib = None
@@ -101,7 +102,7 @@ def load():
         lib.ms_read_lc_stats.argtypes = [vp, vp]
         lib.ms_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, C.c_int, C.c_float, vp, vp, vp, vp]
         lib.ms_mlp_grad.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, vp, vp]
-        lib.ms_mlp_predict.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
+        lib.ms_mlp_predict.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp]
         lib.ms_sync.argtypes = [vp]
         lib.ms_read_state.argtypes = [vp, C.POINTER(ms_state), C.c_int]
         lib.ms_read_state_async.argtypes = [vp, C.POINTER(ms_state)]
@@ -157,9 +158,10 @@ def mlp_grad(x, y, idx, theta, class_w, work, grad, stream=None):
         raise MossError(rc, "ms_mlp_grad")
 
 
-def mlp_predict(x, theta, work, cls, margin, stream=None):
+def mlp_predict(x, theta, work, cls, margin, stream=None, logits=None):
     lib = load()
-    rc = lib.ms_mlp_predict(_dp(x), int(x.shape[0]), _dp(theta), _dp(work), _dp(cls), _dp(margin), _st(stream))
+    rc = lib.ms_mlp_predict(_dp(x), int(x.shape[0]), _dp(theta), _dp(work), _dp(cls), _dp(margin), _dp(logits),
+                            _st(stream))
     if rc:
         raise MossError(rc, "ms_mlp_predict")
 
@@ -371,7 +373,11 @@ class Sim:
         out["inserted"][:] = 0
         out["flag"][:] = 0
         out.update({f: np.full(n, np.nan, np.float32) for f in _DBG_F})
-        s = ms_debug(*[_p(out[f]) for f in _DBG_I + _DBG_F])
+        out["lc_learn"] = np.zeros(n, np.int32)
+        out["lc_margin"] = np.full(n, np.nan, np.float32)
+        out["lc_logit"] = np.full((n, 3), np.nan, np.float32)
+        out["lc_feat"] = np.full((n, 16), np.nan, np.float32)
+        s = ms_debug(*[_p(out[f]) for f in _DBG_I + _DBG_F + _DBG_LC])
         self._check(self.lib.ms_read_debug(self.h, C.byref(s)), "ms_read_debug")
         return out
 

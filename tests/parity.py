@@ -124,3 +124,66 @@ def compare_step(gd, gs, od, os_, n_trips, report=None, max_flag_frac=0.05):
     if report is not None:
         report.append(out)
     return out
+
+
+
+# absolute part of the oracle's bound on the FP32 path's error in each learned input (R19):
+# gaps and the distance to the lane end (FP32 gaps within 1e-3 m, scaled by 1/100), and
+# accelerations (within 1e-4 m/s^2, scaled by 1/a_max); speeds carry FP32 rounding only
+IN_ABS = np.zeros(16)
+IN_ABS[[2, 6, 8, 13, 15]] = 1e-5
+IN_ABS[[4, 10, 11]] = 5e-5
+
+
+def near_bf16_boundary(f, delta):
+    """Whether each value of f lies within delta of a BF16 rounding boundary."""
+    from oracle import mlp
+    r = mlp.bf16(f)
+    a = np.abs(r)
+    _, e = np.frexp(np.where(a > 0, a, 1.0))
+    ulp = np.ldexp(1.0, e - 8)
+    ulp_in = np.where(a == np.ldexp(1.0, e - 1), ulp / 2, ulp)
+    d = np.minimum(np.abs(np.abs(f) - (a + ulp / 2)), np.abs(np.abs(f) - (a - ulp_in / 2)))
+    return (a > 0) & (d <= delta)
+
+
+def compare_learned(gd, od, theta, report=None):
+    """Parity of the learned lane-change decisions of one step (reading R19), after
+    compare_step has checked the decisions themselves (lc_dir) of every unflagged vehicle.
+    For every unflagged vehicle:
+      - the network decided on both sides or on neither;
+      - its 16 BF16 inputs equal the oracle's inputs rounded to BF16, except an input whose
+        oracle value lies within the FP32 path's error of a BF16 rounding boundary (there:
+        within one BF16 step);
+      - its logits agree within the FP32 accumulation bound of the last layer plus the
+        summed logit changes of rounding, one at a time, each input or hidden value near a
+        BF16 rounding boundary the other way (oracle/mlp.flip_sensitivity), plus 1e-6.
+    Returns counts."""
+    from oracle import mlp
+    act = od["active_before"] == 1
+    flagged = (od["flag"] == 1) | (gd["flag"] == 1)
+    cmp = act & ~flagged
+    bad = np.nonzero(cmp & ((gd["lc_learn"] == 1) != (od["lc_learn"] == 1)))[0]
+    assert bad.size == 0, f"learned sets differ for ids {bad[:10].tolist()}"
+    L = np.nonzero(cmp & (od["lc_learn"] == 1))[0]
+    fo, fg = od["lc_feat"][L], gd["lc_feat"][L].astype(np.float64)
+    fb = mlp.bf16(fo)
+    nin = near_bf16_boundary(fo, 2.0 ** -22 * np.abs(fo) + IN_ABS)
+    bad = np.nonzero(np.any((fg != fb) & ~nin, axis=1))[0]
+    assert bad.size == 0, f"BF16 inputs differ for ids {L[bad[:5]].tolist()}: gpu {fg[bad[:1]]} oracle {fb[bad[:1]]}"
+    step = 2.0 ** -7 * np.abs(fo) + 1e-30
+    assert np.all(np.abs(fg - fo)[nin] <= step[nin]), "an input off by more than one BF16 step"
+    zo, zg = od["lc_logit"][L], gd["lc_logit"][L].astype(np.float64)
+    z, _, _, zbound, _, _ = mlp.flip_sensitivity(np.asarray(theta, np.float64), fo, 0.0,
+                                                 in_delta=2.0 ** -22 * np.abs(fo) + IN_ABS)
+    assert np.allclose(z, zo, rtol=1e-12, atol=1e-12), "oracle logits differ from oracle/mlp"
+    dz = np.abs(zg - zo)
+    over = dz - (zbound + 1e-6)
+    assert dz.size == 0 or over.max() <= 0, f"logit excess {over.max()} at id {L[np.argmax(over.max(axis=1))]}"
+    ex = np.nonzero(od["lc_near"][L] == 0)[0]
+    out = dict(learned=int(L.size), exact=int(ex.size), near_inputs=int(nin.any(axis=1).sum()),
+               learned_flagged=int((act & flagged & ((od["lc_learn"] == 1) | (gd["lc_learn"] == 1))).sum()),
+               changes=int((od["lc_dir"][L] != 0).sum()), max_dz=float(dz.max()) if dz.size else 0.0)
+    if report is not None:
+        report.append(out)
+    return out

@@ -1,8 +1,18 @@
-"""Learned lane-change surrogate: GPU gradients vs the FP64 reference, training on decisions
-logged from the rule-based step, and the fused learned step."""
+"""Learned lane-change surrogate on the GPU against the oracle (reading R19).
+
+Inference: the GPU network (ms_mlp_predict, and k_learn inside the step) against the
+oracle's BF16 network -- logits within the FP32 accumulation bound plus the effect of any
+value near a BF16 rounding boundary; classes and the low-margin fallback bit-exact wherever
+no such value can change them and the margin is not within 1e-3 (plus that effect) of the
+threshold or of a tie; in the step, whole learned single steps from identical states
+against the oracle's learned step.  Training: GPU gradients
+against the FP64 reference (random and logged inputs), GPU Adam against the reference
+Adam, training on decisions logged from the rule-based step, and what the trained network
+gains over an untrained one and over the rule-only step."""
 import numpy as np
 import pytest
 
+import oracle
 import parity
 from oracle import mlp as ref
 from paper_2405_12520_b300 import learned, moss, synth
@@ -20,10 +30,102 @@ def torch_mod():
 
 @pytest.fixture(scope="module")
 def logged(torch_mod):
-    """Training data from 12 small-grid seeds, held-out data from 3 others."""
+    """Training data from 60 small-grid seeds, held-out data from 3 others."""
     tr = learned.collect(learned.small_grid_runs(60, 100), P, 3600, 4_000_000)
     te = learned.collect(learned.small_grid_runs(3, 500), P, 3600, 1_000_000)
     return tr, te
+
+
+@pytest.fixture(scope="module")
+def trained(logged):
+    (xtr, ytr), _ = logged
+    cw, cnt = learned.class_weights(ytr)
+    theta, info = learned.train(xtr, ytr, epochs=10, batch=4096, lr=2e-3, seed=1, class_w=cw)
+    return theta, info, cw, cnt
+
+
+def _predict(torch, x, theta):
+    th = torch.tensor(theta, device="cuda")
+    work = torch.zeros(moss.MLP_WORK_FLOATS, device="cuda")
+    n = x.shape[0]
+    cls = torch.empty(n, dtype=torch.int32, device="cuda")
+    mar = torch.empty(n, dtype=torch.float32, device="cuda")
+    zz = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    moss.mlp_predict(x, th, work, cls, mar, logits=zz)
+    return cls.cpu().numpy(), mar.cpu().numpy().astype(np.float64), zz.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("which", ["trained_logged", "noisy_random"])
+def test_predict_matches_oracle_network(torch_mod, logged, trained, which):
+    """ms_mlp_predict against oracle/mlp.forward_bf16 sample by sample."""
+    torch = torch_mod
+    if which == "trained_logged":
+        theta = trained[0]
+        x = logged[1][0][:200_000]
+    else:
+        rng = np.random.default_rng(9)
+        theta = (learned.init_params(4) + rng.normal(scale=0.1, size=moss.MLP_NPARAM)).astype(np.float32)
+        x = torch.tensor(rng.normal(size=(50_000, 16)), dtype=torch.bfloat16, device="cuda")
+    cls, mar, zg = _predict(torch, x, theta)
+    # the oracle's BF16 network with, per sample, the effect of every hidden value the FP32
+    # path might round the other way (reading R19's flag rule)
+    z, mg, c, zbound, msens, changed = ref.flip_sensitivity(theta.astype(np.float64),
+                                                            x.float().cpu().double().numpy(), 0.2)
+    dz = np.abs(zg - z)
+    assert np.all(dz <= zbound + 1e-6), f"logit excess {np.max(dz - zbound)}"
+    assert np.all(np.abs(mar - mg) <= msens + 1e-4)
+    tie = ~changed & (mg >= 1e-3 + msens)                 # no argmax tie within reach
+    assert np.array_equal(cls[tie], c[tie])
+    thr = ~changed & (np.abs(mg - 0.2) >= 1e-3 + msens)  # fallback decision clear
+    assert np.array_equal(mar[thr] < 0.2, mg[thr] < 0.2)
+    print(which, "samples", len(z), "decision sensitive to a rounding", int(changed.sum()), "max |dz|",
+          float(dz.max()), "class compared", int(tie.sum()), "fallback compared", int(thr.sum()))
+    assert tie.mean() > 0.95 and thr.mean() > 0.95
+
+
+def _learned_case(net, dem, params, theta, margin, t0, steps=6):
+    sim = parity.gpu_sim(net, dem, params)
+    sim.set_lc_model(theta, margin)
+    st = sim.read_state()
+    st["t"] = t0
+    sim.write_state(st)
+    orc = oracle.Oracle(net, dem, params)
+    orc.set_lc_model(theta, margin)
+    rep, lrep = [], []
+    for _ in range(steps):
+        _, gd, gs, od, os_ = parity.step_pair(sim, orc)
+        parity.compare_step(gd, gs, od, os_, dem.n, report=rep)
+        parity.compare_learned(gd, od, theta, report=lrep)
+    tot = {k: sum(r[k] for r in rep) for k in rep[0]}
+    ltot = {k: sum(r[k] for r in lrep) for k in lrep[0] if k != "max_dz"}
+    ltot["max_dz"] = max(r["max_dz"] for r in lrep)
+    return tot, ltot
+
+
+@pytest.mark.parametrize("net_kind,t0", [("grid12x3", 0), ("grid12x3", 31), ("delaunay", 64)])
+@pytest.mark.parametrize("model", ["trained", "untrained"])
+def test_learned_single_steps_match_oracle(torch_mod, trained, net_kind, t0, model):
+    """The in-step learned decision (candidates listed by the decide kernel, the network in
+    k_learn, margin fallback, update finished there) from identical states against the
+    oracle's learned step: every vehicle's neighbours, decisions, lane, position and speed
+    as in the rule step's parity, and the network's inputs and logits per candidate."""
+    if net_kind == "grid12x3":
+        net = synth.grid_network(12, 12, 3, 200.0, 30, 3, "wave")
+        dem = synth.merge_demands(synth.place_vehicles(net, 6000, seed=70 + t0, min_spacing=7.0, internal_frac=0.3),
+                                  synth.uniform_trips(net, 800, 40, seed=71 + t0))
+    else:
+        net = synth.delaunay_network(120, box=3000.0, seed=7)
+        dem = synth.merge_demands(synth.place_vehicles(net, 2500, seed=72, min_spacing=6.0, internal_frac=0.4),
+                                  synth.uniform_trips(net, 400, 40, seed=73))
+    if model == "trained":
+        theta, margin = trained[0], 0.2
+    else:   # an untrained network with a small margin: many changes, most by the network
+        theta, margin = learned.init_params(7), 0.05
+    tot, ltot = _learned_case(net, dem, dict(P, seed=99 + t0), theta, margin, t0)
+    print(net_kind, t0, model, tot, ltot)
+    assert tot["compared"] > 0.9 * tot["active"]
+    assert ltot["learned"] > 100 and ltot["exact"] > 0 and ltot["changes"] > 0
+    assert ltot["learned_flagged"] <= 0.05 * (ltot["learned"] + ltot["learned_flagged"]) + 2
 
 
 def test_gpu_gradient_matches_fp64_reference(torch_mod):
@@ -51,12 +153,62 @@ def test_gpu_gradient_matches_fp64_reference(torch_mod):
                                           y.cpu().numpy(), cw), rel=2e-2)
 
 
-def test_training_reaches_rule_agreement(logged, torch_mod):
+@pytest.mark.parametrize("at", ["init", "trained"])
+def test_gpu_gradient_on_logged_samples(torch_mod, logged, trained, at):
+    """The same check on the inputs the step logs (their own scales and BF16 rounding), at an
+    initial and at the trained network, with the training's class weights."""
+    torch = torch_mod
+    (xtr, ytr), _ = logged
+    theta0, _, cw, _ = trained
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    idx = torch.randperm(xtr.shape[0], generator=g, device="cuda")[:4096].to(torch.int32)
+    theta = learned.init_params(12) if at == "init" else theta0
+    grad = torch.zeros(moss.MLP_NPARAM, device="cuda")
+    work = torch.zeros(moss.MLP_WORK_FLOATS, device="cuda")
+    moss.mlp_grad(xtr, ytr, idx, torch.tensor(theta, device="cuda"), cw, work, grad)
+    X = xtr[idx.long()].float().cpu().double().numpy()
+    Y = ytr[idx.long()].cpu().numpy()
+    g_gpu = grad.cpu().double().numpy()
+    g_ref = ref.grad(theta.astype(np.float64), X, Y, cw.astype(np.float64))
+    cos = g_gpu @ g_ref / (np.linalg.norm(g_gpu) * np.linalg.norm(g_ref))
+    rel = np.linalg.norm(g_gpu - g_ref) / np.linalg.norm(g_ref)
+    print(at, "cosine", cos, "rel L2", rel, "|g|", np.linalg.norm(g_ref))
+    assert cos >= 0.999 and rel <= 2e-2
+
+
+def test_gpu_adam_matches_reference_adam(torch_mod, logged):
+    """Five training steps: after each, the GPU's parameters and moments equal one reference
+    Adam step (oracle/mlp.adam_step, FP64) from the GPU's previous parameters and moments
+    with the GPU's gradient of that minibatch, within FP32 rounding."""
+    torch = torch_mod
+    (xtr, ytr), _ = logged
+    cw = np.array([1.0, 2.0, 2.0], np.float32)
+    theta = torch.tensor(learned.init_params(21), device="cuda")
+    m = torch.zeros_like(theta)
+    v = torch.zeros_like(theta)
+    work = torch.zeros(moss.MLP_WORK_FLOATS, device="cuda")
+    grad = torch.zeros_like(theta)
+    lr = 2e-3
+    for t in range(1, 6):
+        idx = torch.arange((t - 1) * 4096, t * 4096, dtype=torch.int32, device="cuda")
+        moss.mlp_grad(xtr, ytr, idx, theta, cw, work, grad)
+        th0, m0, v0, g0 = (a.cpu().double().numpy() for a in (theta, m, v, grad))
+        moss.mlp_train_step(xtr, ytr, idx, theta, m, v, t, lr, cw, work)
+        th_r, m_r, v_r = ref.adam_step(th0, g0, m0, v0, t, lr=lr)
+        th1, m1, v1 = (a.cpu().double().numpy() for a in (theta, m, v))
+        # the gradient is summed with float atomics in both calls: order-level differences
+        np.testing.assert_allclose(m1, m_r, rtol=1e-4, atol=1e-9)
+        np.testing.assert_allclose(v1, v_r, rtol=1e-3, atol=1e-12)
+        np.testing.assert_allclose(th1, th_r, rtol=0, atol=lr * 1e-2 + 1e-6)
+        assert np.max(np.abs(th1 - th0)) > 0.5 * lr   # an update happened
+
+
+def test_training_reaches_rule_agreement(logged, trained, torch_mod):
     (xtr, ytr), (xte, yte) = logged
-    cw, cnt = learned.class_weights(ytr)
+    theta, info, cw, cnt = trained
     print("train samples", xtr.shape[0], "class counts", cnt)
     assert xtr.shape[0] > 100_000 and cnt[1] > 0 and cnt[2] > 0
-    theta, info = learned.train(xtr, ytr, epochs=10, batch=4096, lr=2e-3, seed=1, class_w=cw)
     ev = learned.evaluate(theta, xte, yte)
     ev0 = learned.evaluate(learned.init_params(1), xte, yte)
     print("trained", ev)
@@ -65,12 +217,13 @@ def test_training_reaches_rule_agreement(logged, torch_mod):
     assert ev["agree_with_fallback"] >= 0.99
     assert ev["agree_net"] > ev0["agree_net"] and ev["agree_net"] >= stay_only - 1e-3
     assert ev["agree_left"] > 0.5 and ev["agree_right"] > 0.5   # the rare classes are learned
-    np.save("/tmp/moss_lc_theta.npy", theta)
 
 
-def test_learned_step_runs_agrees_and_keeps_invariants(logged, torch_mod):
-    (xtr, ytr), _ = logged
-    theta, _ = learned.train(xtr, ytr, epochs=10, batch=4096, lr=2e-3, seed=1)
+def test_learned_step_runs_agrees_and_keeps_invariants(trained, torch_mod):
+    """A whole 3600-step small-grid run with the trained network against the rule-only run:
+    decision agreement, arrivals and network mean speed per window (what the learned form
+    gives up against the rule it replaces), device order/gap checks on."""
+    theta = trained[0]
     net, dem = synth.small_grid_workload(777)
     rule = parity.gpu_sim(net, dem, P, debug=False, n_windows=12)
     lrn = parity.gpu_sim(net, dem, P, debug=True, n_windows=12)   # device order/gap check on

@@ -50,7 +50,7 @@ def test_bf16_forward_equals_plain_forward_when_nothing_rounds():
          "W3": rng.integers(-1, 2, (3, 64)).astype(float) / 8, "b3": np.array([0.5, -0.5, 0.0])}
     theta = mlp.pack(p)
     X = rng.integers(-3, 4, (200, 16)).astype(float) / 4
-    z, near = mlp.forward_bf16(theta, X)
+    z, near, _ = mlp.forward_bf16(theta, X)
     z0, (_, a1, h1, a2, h2) = mlp.forward(theta, X)
     # integer inputs/weights keep h1 in quarters below 2^6 and h2 in sixteenths: exact in BF16
     assert np.array_equal(mlp.bf16(h1), h1) and np.array_equal(mlp.bf16(h2), h2)
@@ -68,7 +68,7 @@ def test_bf16_forward_rounds_where_the_kernel_rounds():
     theta = mlp.pack(p)
     X = np.zeros((1, 16))
     X[0, 0] = 1.0 + 2.0 ** -7 + 2.0 ** -9
-    z, _ = mlp.forward_bf16(theta, X)
+    z, _, _ = mlp.forward_bf16(theta, X)
     assert z[0, 1] == 3.03125 and z[0, 0] == 0.0 and z[0, 2] == 0.0
 
 
@@ -190,7 +190,7 @@ def test_learned_logits_match_the_numpy_bf16_forward():
     theta = (mlp.init(5) + np.random.default_rng(1).normal(scale=0.05, size=mlp.N_PARAMS)).astype(np.float32)
     st, dr, dl = _pair(net, dem, 0, theta, margin=0.0)
     L = np.nonzero(dl["lc_learn"] == 1)[0]
-    z, _ = mlp.forward_bf16(theta.astype(np.float64), dl["lc_feat"][L])
+    z, _, _ = mlp.forward_bf16(theta.astype(np.float64), dl["lc_feat"][L])
     np.testing.assert_allclose(dl["lc_logit"][L], z, rtol=1e-12, atol=1e-12)
     mg, cls = mlp.margin_class(z)
     np.testing.assert_allclose(dl["lc_margin"][L], mg, rtol=1e-12, atol=1e-12)

@@ -5,11 +5,15 @@ A step is one simulation step of the whole hot path -- sort/merge by lane and po
 neighbour search, IDM + randomized MOBIL, signal stop lines, ballistic advance, lane
 transfer, departures, metrics -- over every active vehicle of the workload.
 
-Default workload: 100x100 signalised grid, 3 lanes per direction, 300 m links,
-green-wave offsets, 1,000,000 vehicles already on the network plus 800,000 gravity-OD trips
-departing over 500 s, v0 ~ N(13.9, 1.5) m/s.  Inputs are generated from a seed.  The step's working set
-(~90 MB) fits in the 126 MB L2, so L2 is flushed (256 MiB write) before every timed step
-and each step is timed alone with CUDA events on the simulation's stream.
+Default workload (city5m): an irregular city -- Delaunay triangulation of 20,000 points in a
+30 x 30 km box, 1-4 lanes per edge by length quartile, signals at nodes of degree >= 3 --
+with 5,000,000 vehicles on the network and heavy-tailed trip lengths (Pareto 1.5, 1 km,
+truncated at 40 km).  Its working set (~400 MB) is far above the 126 MB L2; L2 is still
+flushed (256 MiB write) before every timed step, and each step is timed alone with CUDA
+events on the simulation's stream.  --workload grid1m: the 100x100 signalised grid, 3 lanes
+per direction, 300 m links, 1,000,000 vehicles on the network plus 800,000 gravity-OD trips
+departing over 500 s (its ~100 MB working set fits in L2, hence the flush).  Inputs are
+generated from a seed.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank runs an independent replica with its own seed: the step
@@ -88,11 +92,21 @@ def peaks():
 
 
 def kernel_src_hash() -> str:
+    """Hash of every file that shapes the step's kernels and their launches: the kernel
+    sources, the host runtime that sizes grids and caps registers, and the build flags."""
     h = hashlib.sha256()
-    for f in ("step_kernels.cuh",):
-        with open(os.path.join(ROOT, "paper_2405_12520_b300", "csrc", f), "rb") as fh:
+    pkg = os.path.join(ROOT, "paper_2405_12520_b300")
+    for f in ("csrc/step_kernels.cuh", "csrc/mlp_kernels.cuh", "csrc/moss103.cu", "build.py"):
+        with open(os.path.join(pkg, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def traffic_per_unit(kernel: str, wl: str):
@@ -231,12 +245,14 @@ def apply_mods(side, mods):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(net, dem, params, budget_s: float = 12.0, max_steps: int = 60, mods=None, warmup: int = 1):
-    """The FP64 oracle, as it stands, single-threaded on this host, on the same workload:
+def cpu_baseline(net, dem, params, budget_s: float = 12.0, max_steps: int = 60, mods=None, warmup: int = 1,
+                 threads: int = 1):
+    """The FP64 oracle, as it stands, on this host's cores (threads: its update phase on
+    that many OpenMP threads; results identical for any count), on the same workload:
     vehicle-steps/s over up to max_steps steps or budget_s seconds after `warmup` untimed
     steps."""
     import oracle
-    o = oracle.Oracle(net, dem, params)
+    o = oracle.Oracle(net, dem, params, threads=threads)
     apply_mods(o, mods)
     for _ in range(warmup):
         o.step()
@@ -260,15 +276,18 @@ def run_reference(args):
     net, dem, desc = workload(args.workload, args.seed)
     p, mods, vdesc = variant(args, net, dem)
     k = max(1, min(args.steps, args.ref_steps))
-    val, steps, el = cpu_baseline(net, dem, p, budget_s=1e9, max_steps=k, mods=mods, warmup=args.warmup)
+    cores = host_cores()
+    val, steps, el = cpu_baseline(net, dem, p, budget_s=1e9, max_steps=k, mods=mods, warmup=args.warmup,
+                                  threads=cores)
     line = {
         "impl": "reference", "metric": "vehicle-steps/s", "value": val, "unit": "vehicle-steps/s",
         "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": args.workload, "description": desc, **vdesc},
-        "cpu_baseline": {"value": val, "unit": "vehicle-steps/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{steps} oracle steps of the full {args.workload} workload "
-                                   f"({dem.n} vehicles) after {args.warmup} warm-up steps"},
+        "cpu_baseline": {"value": val, "unit": "vehicle-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{steps} oracle steps (update phase on {cores} OpenMP threads) of the "
+                                   f"full {args.workload} workload ({dem.n} vehicles) after {args.warmup} "
+                                   f"warm-up steps"},
         "e2e": {"value": val, "unit": "vehicle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -436,9 +455,14 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         val, steps, el = cpu_baseline(net, dem, params, mods=mods)
+        cores = host_cores()
+        val_n, steps_n, el_n = cpu_baseline(net, dem, params, mods=mods, threads=cores)
         line["cpu_baseline"] = {"value": val, "unit": "vehicle-steps/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{steps} single-threaded FP64 oracle steps of the same workload "
-                                          f"({dem.n} vehicles), {el:.1f} s"}
+                                          f"({dem.n} vehicles), {el:.1f} s",
+                                "all_cores": {"value": val_n, "unit": "vehicle-steps/s", "cores": cores,
+                                              "sample": f"{steps_n} FP64 oracle steps, update phase on {cores} "
+                                                        f"OpenMP threads (bit-identical to one), {el_n:.1f} s"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     sim.destroy()
@@ -808,7 +832,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", default="grid1m")
+    ap.add_argument("--workload", default="city5m")
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--ref-steps", type=int, default=8)

@@ -1,7 +1,8 @@
 """FP64 CPU oracle of the per-step vehicle update -- TEST INFRASTRUCTURE.
 
 Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline / reference arm may import
-this package.  It wraps oracle/moss_oracle.c (plain C, FP64, single-threaded) with ctypes
+this package.  It wraps oracle/moss_oracle.c (plain C, FP64; single-threaded unless asked
+for threads, whose count does not change any result) with ctypes
 and shares no code with the CUDA library.  Readings R1-R14, R17 and R19 of the model are
 listed at the top of moss_oracle.c.
 """
@@ -23,7 +24,7 @@ STATUS_WAIT, STATUS_ACTIVE, STATUS_DONE = 0, 1, 2
 def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "moss_oracle.h"))):
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
                                "-Wall", "-o", _LIB, _SRC, "-lm"])
     return _LIB
 
@@ -88,6 +89,8 @@ def _load():
         lib.or_set_lane_limits.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
         lib.or_set_links.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
         lib.or_set_links.restype = C.c_int
+        lib.or_set_threads.argtypes = [C.c_void_p, C.c_int]
+        lib.or_set_threads.restype = None
         lib.or_set_lc_model.argtypes = [C.c_void_p, C.c_void_p, C.c_double]
         lib.or_set_lc_model.restype = C.c_int
         lib.or_bf16.argtypes = [C.c_double]
@@ -113,7 +116,7 @@ class Oracle:
     """One simulation instance.  `net` and `dem` are synth.Network / synth.Demand (or any
     objects with the same array attributes); `params` a dict like synth.default_params()."""
 
-    def __init__(self, net, dem, params: dict, n_windows: int = 1):
+    def __init__(self, net, dem, params: dict, n_windows: int = 1, threads: int = 1):
         lib = _load()
         i32 = lambda a: np.ascontiguousarray(a, np.int32)
         self._keep = []
@@ -151,6 +154,8 @@ class Oracle:
         self.h = lib.or_create(C.byref(self.net_c), C.byref(self.par_c), dem.n, _p(self.t_dep),
                                _p(self.v0), _p(self.route_off), _p(self.route_edges),
                                _p(lane), _p(x), _p(v))
+        self.threads = max(1, int(threads))
+        lib.or_set_threads(self.h, self.threads)
 
     def __del__(self):
         if getattr(self, "h", None):

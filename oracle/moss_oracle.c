@@ -1,8 +1,11 @@
 /*
  * moss_oracle.c -- FP64 CPU oracle of one simulation step (TEST INFRASTRUCTURE ONLY).
  *
- * Plain, single-threaded, obviously-correct restatement of the model.  Only tests/,
- * __graft_entry__.smoke() and bench.py's CPU baseline may load this library.
+ * Plain, obviously-correct restatement of the model, single-threaded unless or_set_threads
+ * asks for more (then the update phase, where every vehicle reads only the snapshot and
+ * writes only its own outputs, runs its vehicles on OpenMP threads; the results do not
+ * depend on the thread count).  Only tests/, __graft_entry__.smoke() and bench.py's CPU
+ * baseline may load this library.
  *
  * What the paper fixes (Sec. III-A): two phases per step -- a prepare phase that indexes
  * vehicles by lane and position and takes a read-only copy of their motion state, and an
@@ -160,8 +163,9 @@ struct or_sim {
   int64_t *vcnt;
   int64_t counters[4]; /* inserted, arrived, sum of travel times, errors */
   /* step outputs */
-  int *n_lane, *n_rp, *n_status;
+  int *n_lane, *n_rp, *n_status, *n_flag;
   double *n_x, *n_v;
+  int threads;      /* threads of the update phase (OpenMP); 1: serial */
   /* R13 controllers */
   int *mp_g, *mp_pend, *mp_yend;
   int64_t *mp_pres;   /* per controller x phase pressure (scratch) */
@@ -815,6 +819,8 @@ static learned_t learned_decision(const or_sim *s, int c, const leader_t *own, d
   return r;
 }
 
+void or_set_threads(or_sim *s, int threads) { s->threads = threads > 1 ? threads : 1; }
+
 int or_set_lc_model(or_sim *s, const float *theta, double margin) {
   if (!theta) {
     free(s->mlp);
@@ -853,14 +859,12 @@ int or_step(or_sim *s, or_debug *dbg) {
       s->vcnt[(size_t)w * s->net.n_lanes + s->lane[c]] += 1;
     }
   }
-  /* per-lane minimum rear of vehicles entering the lane this step (R8) */
-  double *arr_min = (double *)malloc(sizeof(double) * (size_t)s->net.n_lanes);
-  for (int l = 0; l < s->net.n_lanes; ++l) arr_min[l] = INFINITY;
-  int *arr_flag = (int *)calloc((size_t)s->net.n_lanes, sizeof(int));
-
   if (dbg) {
     for (int i = 0; i < s->n; ++i) { dbg->active_before[i] = 0; dbg->inserted[i] = 0; dbg->flag[i] = 0; }
   }
+  /* update phase: every vehicle reads only the snapshot and writes only its own outputs,
+     so the vehicles may be updated in any order or at once (or_set_threads) */
+#pragma omp parallel for schedule(dynamic, 256) reduction(min : err) num_threads(s->threads) if (s->threads > 1)
   for (int k = 0; k < s->n_act; ++k) {
     int c = s->order[k];
     int flag = 0;
@@ -927,10 +931,7 @@ int or_step(or_sim *s, or_debug *dbg) {
     s->n_v[c] = vn;
     s->n_rp[c] = nrp;
     s->n_status[c] = nst;
-    if (nst == ST_ACTIVE && nl != l) {
-      arr_min[nl] = fmin(arr_min[nl], xn - L);
-      if (flag) arr_flag[nl] = 1;
-    }
+    s->n_flag[c] = flag;
     if (dbg) {
       dbg->active_before[c] = 1;
       dbg->lead_kind[c] = own.kind;
@@ -955,6 +956,18 @@ int or_step(or_sim *s, or_debug *dbg) {
           for (int q = 0; q < 16; ++q) dbg->lc_feat[16 * c + q] = ln.f[q];
         }
       }
+    }
+  }
+  /* per-lane minimum rear of the vehicles entering the lane this step (R8), and whether a
+     flagged vehicle enters it */
+  double *arr_min = (double *)malloc(sizeof(double) * (size_t)s->net.n_lanes);
+  for (int l = 0; l < s->net.n_lanes; ++l) arr_min[l] = INFINITY;
+  int *arr_flag = (int *)calloc((size_t)s->net.n_lanes, sizeof(int));
+  for (int k = 0; k < s->n_act; ++k) {
+    const int c = s->order[k], nl = s->n_lane[c];
+    if (s->n_status[c] == ST_ACTIVE && nl != s->lane[c]) {
+      arr_min[nl] = fmin(arr_min[nl], s->n_x[c] - L);
+      if (s->n_flag[c]) arr_flag[nl] = 1;
     }
   }
   /* R8 departures, decided on the snapshot (before the update is applied) */
@@ -1078,6 +1091,8 @@ or_sim *or_create(const or_net *net, const or_params *p, int n_trips, const int 
   s->n_lane = (int *)malloc((n + 1) * sizeof(int));
   s->n_rp = (int *)malloc((n + 1) * sizeof(int));
   s->n_status = (int *)malloc((n + 1) * sizeof(int));
+  s->n_flag = (int *)malloc((n + 1) * sizeof(int));
+  s->threads = 1;
   s->n_x = (double *)malloc((n + 1) * sizeof(double));
   s->n_v = (double *)malloc((n + 1) * sizeof(double));
   s->vsum = (double *)calloc((size_t)p->n_windows * L, sizeof(double));
@@ -1144,7 +1159,7 @@ void or_destroy(or_sim *s) {
   free(s->lane_vmax); free(s->lane_closed); free(s->link_off);
   free(s->status); free(s->lane); free(s->rp); free(s->t_arr); free(s->x); free(s->v);
   free(s->dep_lane); free(s->order); free(s->pos); free(s->seg_start); free(s->seg_cnt);
-  free(s->n_lane); free(s->n_rp); free(s->n_status); free(s->n_x); free(s->n_v);
+  free(s->n_lane); free(s->n_rp); free(s->n_status); free(s->n_flag); free(s->n_x); free(s->n_v);
   free(s->vsum); free(s->vcnt); free(s->q_off); free(s->q_head); free(s->q_ids);
   free(s->pred_off); free(s->pred_ids); free(s->mlp);
   free(s);

@@ -67,6 +67,9 @@ or_sim *or_create(const or_net *net, const or_params *p, int n_trips, const int 
                   const float *v0, const int64_t *route_off, const int *route_edges,
                   const int *lane0, const float *x0, const float *vinit);
 void or_destroy(or_sim *s);
+/* threads of the update phase (OpenMP; default 1).  Every vehicle's update reads only the
+   snapshot and writes only its own outputs, so results do not depend on the count. */
+void or_set_threads(or_sim *s, int threads);
 /* one step; dbg may be NULL.  Returns 0, or a negative error code. */
 int or_step(or_sim *s, or_debug *dbg);
 int or_run(or_sim *s, int n_steps);

@@ -160,7 +160,44 @@ def gravity_trips(net, zone_edge, attract, gamma, n, t_span, seed, splitmix64):
 # ---------------------------------------------------------------------------------------
 
 def radiation_weights(cost, pop):
-    """w[i, j] of R18 from the zone-to-zone route costs cost[i, j] (inf: unreachable)."""
+    """w[i, j] of R18 from the zone-to-zone route costs cost[i, j] (inf: unreachable), zone
+    by zone as R18 states it: walk the zones in order of (distance, index), give each group
+    of equal distance the running population sum of the zones before the group, then add
+    the group's populations (zone i's excepted) one float32 addition at a time."""
+    m = np.asarray(pop, np.float32)
+    Z = m.shape[0]
+    W = np.zeros((Z, Z), np.float32)
+    for i in range(Z):
+        d = np.asarray(cost[i], np.float64)
+        order = np.lexsort((np.arange(Z), d))           # by (distance, zone index)
+        run = np.float32(0.0)
+        s = np.zeros(Z, np.float32)
+        q = 0
+        while q < Z:                                     # groups of equal distance
+            r = q
+            while r < Z and d[order[r]] == d[order[q]]:
+                r += 1
+            for k in order[q:r]:
+                s[k] = run                               # zones strictly closer
+            for k in order[q:r]:
+                if k != i:
+                    run = np.float32(run + m[k])
+            q = r
+        for j in range(Z):
+            if j == i or not np.isfinite(d[j]):
+                continue
+            num = np.float32(m[i] * m[j])
+            den = np.float32(np.float32(m[i] + s[j]) * np.float32(np.float32(m[i] + m[j]) + s[j]))
+            W[i, j] = np.float32(num / den)
+    return W
+
+
+def radiation_weights_vec(cost, pop):
+    """radiation_weights with each origin's row in array operations (for thousands of
+    zones): the running sum is a sequential float32 cumulative sum in the same order (zone
+    i adds 0, which leaves a float32 sum unchanged), each group takes the sum before its
+    first zone, and the weight is the same three IEEE float32 operations.  Pinned against
+    radiation_weights on random inputs with ties and unreachable zones."""
     m = np.asarray(pop, np.float32)
     Z = m.shape[0]
     W = np.zeros((Z, Z), np.float32)
@@ -168,7 +205,6 @@ def radiation_weights(cost, pop):
         d = np.asarray(cost[i], np.float64)
         order = np.lexsort((np.arange(Z), d))                 # by (distance, zone index)
         ds = d[order]
-        # running float32 sum of the populations in that order, zone i contributing nothing
         run = np.cumsum(np.where(order == i, np.float32(0.0), m[order]), dtype=np.float32)
         start = np.r_[0, np.nonzero(ds[1:] != ds[:-1])[0] + 1]   # first position of each
         grp = np.searchsorted(start, np.arange(Z), side="right") - 1   # equal-distance group
@@ -188,7 +224,7 @@ def radiation_trips(net, zone_edge, pop, n, t_span, seed, splitmix64):
     m = np.asarray(pop, np.float32)
     d = distances_to(net, zone_edge)            # [Z dest, E]
     cost = d[:, zone_edge].T                    # cost[i, j] = zone i -> zone j
-    W = radiation_weights(cost, m)
+    W = (radiation_weights if m.shape[0] <= 256 else radiation_weights_vec)(cost, m)
     cdf_o = np.cumsum(m, dtype=np.float32)
     cdf_d = np.cumsum(W, axis=1, dtype=np.float32)
     o = np.zeros(n, np.int32)

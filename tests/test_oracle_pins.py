@@ -393,6 +393,133 @@ def test_neighbours_match_brute_force(oracle_lib, kind, seed):
     np.testing.assert_array_equal(got, want)
 
 
+def _r11_next(net, l, en, en2):
+    """R11: among edge lane l's links toward edge en (CSR order), the first whose target lane
+    links to en2 (any if en2 < 0), else the first; -1 if none."""
+    first = -1
+    for k in range(net.succ_off[l], net.succ_off[l + 1]):
+        if net.succ_edge[k] != en:
+            continue
+        il = int(net.succ_lane[k])
+        if first < 0:
+            first = il
+        if en2 < 0:
+            return il
+        tg = int(net.succ_lane[net.succ_off[il]])
+        if any(net.succ_edge[q] == en2 for q in range(net.succ_off[tg], net.succ_off[tg + 1])):
+            return il
+    return first
+
+
+def _brute_leaders(net, dem, st, d_look, L):
+    """Own-path leader of every active vehicle by brute force, as path coordinates over ALL
+    vehicles: the lanes the route passes through (R11 choices) from the vehicle's lane, each
+    with the path coordinate of its start, as long as a lane starts less than d_look ahead
+    of the vehicle's front; the leader is the vehicle with the smallest path coordinate ahead
+    of the front, gap = its coordinate - L - x.  No vehicle: a stopped obstacle if the path
+    ended at a lane without a link toward the next route edge, else free.  Then R3's merge
+    projection: on an internal lane whose target has other feeders, on each of them the
+    vehicle nearest the merge point among those farther from it... (d_j < d or d_j == d with
+    a lower id), gap d - d_j - L, wins when smaller.  Networks without signals."""
+    act = np.nonzero(st["status"] == 1)[0]
+    lane, x, rp = st["lane"], st["x"], st["rp"]
+    ln = np.asarray(net.lane_len, np.float64)
+    edge = np.asarray(net.lane_edge)
+    kind = np.zeros(dem.n, np.int64)
+    lead = np.full(dem.n, -1, np.int64)
+    gap = np.zeros(dem.n)
+    for c in act:
+        route = dem.route_edges[dem.route_off[c]:dem.route_off[c + 1]]
+        at = lambda k: int(route[k]) if 0 <= k < route.shape[0] else -1
+        path = [(int(lane[c]), 0.0)]
+        cur, ri, start, blocked = int(lane[c]), int(rp[c]), 0.0, False
+        while start + ln[cur] - x[c] < d_look:
+            if edge[cur] >= 0:
+                en = at(ri + 1)
+                if en < 0:
+                    break                          # destination edge: open end
+                nxt = _r11_next(net, cur, en, at(ri + 2))
+                if nxt < 0:
+                    blocked = True
+                    break
+            else:
+                nxt = int(net.succ_lane[net.succ_off[cur]])
+                ri += 1
+            start += ln[cur]
+            path.append((nxt, start))
+            cur = nxt
+        assert len(path) <= 11                     # the 12-lane cap is not reached here
+        best, bu = -1, np.inf
+        for (pl, s0) in path:
+            on = act[(lane[act] == pl) & (act != c)]
+            u = s0 + x[on]
+            if pl == lane[c]:
+                keep = x[on] > x[c]
+                on, u = on[keep], u[keep]
+            if on.size and u.min() < bu:
+                bu, best = float(u.min()), int(on[np.argmin(u)])
+        if best >= 0:
+            kind[c], lead[c], gap[c] = 1, best, bu - L - x[c]
+        elif blocked:
+            kind[c], gap[c] = 2, (path[-1][1] + ln[path[-1][0]]) - x[c]
+        l = int(lane[c])
+        if edge[l] < 0:                            # R3
+            tgt = int(net.succ_lane[net.succ_off[l]])
+            feeders = [f for f in range(net.n_lanes)
+                       if edge[f] < 0 and int(net.succ_lane[net.succ_off[f]]) == tgt]
+            if len(feeders) > 1:
+                dc = ln[l] - x[c]
+                for f in feeders:
+                    if f == l:
+                        continue
+                    on = act[lane[act] == f]
+                    dj = ln[f] - x[on]
+                    ok = (dj < dc) | ((dj == dc) & (on < c))
+                    if not ok.any():
+                        continue
+                    j = on[ok][np.argmax(dj[ok])]
+                    g = (dc - (ln[f] - x[j])) - L
+                    if kind[c] == 0 or g < gap[c]:
+                        kind[c], lead[c], gap[c] = 1, j, g
+    return kind, lead, gap
+
+
+@pytest.mark.parametrize("kind,seed,t0", [("grid", 4, 0), ("grid", 5, 1), ("delaunay", 6, 0), ("delaunay", 7, 1)])
+def test_step_leaders_and_target_neighbours_match_brute_force(oracle_lib, kind, seed, t0):
+    """or_step's own sensing (R2 look-ahead across lane ends, R3 merges) and its lane-change
+    target neighbours, read from its debug record, against brute force over all vehicles on
+    random states with many vehicles near lane ends and on junction lanes."""
+    if kind == "grid":
+        net = synth.grid_network(4, 4, 2, 120.0, 30, 3, "zero")
+    else:
+        net = synth.delaunay_network(40, box=2000.0, seed=seed)
+    net.lane_ctrl = np.full(net.n_lanes, -1, np.int32)     # no signals: obstacles are missing links
+    dem = synth.place_vehicles(net, 90 if kind == "grid" else 220, seed=seed, min_spacing=5.5,
+                               internal_frac=0.4)
+    o = oracle_lib.Oracle(net, dem, P)
+    st = o.state()
+    o.set_state(st["status"], st["lane"], st["x"], st["v"], st["rp"], t0, st["t_arr"])
+    _, d = o.step(debug=True)
+    k_b, lead_b, gap_b = _brute_leaders(net, dem, st, P["d_look"], P["veh_len"])
+    act = np.nonzero(st["status"] == 1)[0]
+    np.testing.assert_array_equal(d["lead_kind"][act], k_b[act])
+    np.testing.assert_array_equal(d["lead_id"][act], lead_b[act])
+    has = act[k_b[act] != 0]
+    np.testing.assert_allclose(d["s_own"][has], gap_b[has], rtol=0, atol=1e-9)
+    assert (k_b[act] == 1).sum() > 20 and (k_b[act] == 2).sum() + (k_b[act] == 0).sum() > 3
+    ahead_next = sum(1 for c in act if k_b[c] == 1 and st["lane"][lead_b[c]] != st["lane"][c])
+    assert ahead_next > 10                         # leaders found across lane ends
+    # lane-change target neighbours of the candidates (lane l+1 on even steps, l-1 on odd)
+    nb = _brute_neighbours(net, st["lane"], st["x"], st["status"] == 1)
+    side = 0 if t0 % 2 == 0 else 1
+    cand = act[d["lc_cand"][act] == 1]
+    assert cand.size > 5
+    np.testing.assert_array_equal(d["tau_lead"][cand], nb[cand, 2 + 2 * side])
+    np.testing.assert_array_equal(d["tau_foll"][cand], nb[cand, 3 + 2 * side])
+    of = act[d["old_foll"][act] >= 0]
+    np.testing.assert_array_equal(d["old_foll"][of], nb[of, 1])
+
+
 # ---------------------------------------------------------------------------------------
 # max-pressure signals (R13)
 # ---------------------------------------------------------------------------------------

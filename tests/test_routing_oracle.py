@@ -198,3 +198,20 @@ def test_radiation_sampling_follows_the_weights_and_is_scale_free():
     o3, d3, t3 = routing.radiation_trips(net2, zones, m, n, 600, 31, _sm)
     np.testing.assert_array_equal(d, d3)
     np.testing.assert_array_equal(t, t3)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_radiation_weights_vectorised_form_equals_the_loop(seed):
+    """radiation_weights_vec (used for thousands of zones) gives the zone-by-zone loop of
+    R18 bit for bit: random populations (some equal), integer costs with many ties, zones
+    unreachable from some origins, zero-cost neighbours."""
+    rng = np.random.default_rng(seed)
+    Z = 150
+    m = rng.choice(np.array([1.0, 2.5, 7.0, 1e3, 3.3e4], np.float32), size=Z) * rng.integers(1, 4, Z).astype(np.float32)
+    cost = rng.integers(0, 25, size=(Z, Z)).astype(np.float64) * 1000.0
+    cost[rng.random((Z, Z)) < 0.1] = np.inf
+    np.fill_diagonal(cost, 0.0)
+    a = routing.radiation_weights(cost, m)
+    b = routing.radiation_weights_vec(cost, m)
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    assert (a > 0).sum() > Z * Z // 2

@@ -233,3 +233,32 @@ def flip_sensitivity(theta, X, thr, in_delta=None, chunk=65536):
             _, h2a = tail(bf16(np.maximum(xa @ W1.T + b1, 0.0)))
             account(ss, h2a @ W3.T + b3)
     return z, m, c, zb, msens, changed
+
+
+def grad_bf16(theta, X, y, w_class):
+    """loss()'s gradient as a BF16 network with FP32 accumulation computes it: the forward of
+    forward_bf16; the output gradient w[y] (p - onehot(y)) rounded to BF16 where it enters a
+    product, and the hidden-layer gradients (after the ReLU mask of the BF16 activations)
+    rounded to BF16; weight gradients as products of those BF16 operands, the output bias
+    gradient from the unrounded output gradient, the hidden bias gradients as column sums of
+    the BF16 hidden gradients; everything divided by sum w[y].  Sums in float64."""
+    prm = unpack(theta)
+    W1, W2, W3 = bf16(prm["W1"]), bf16(prm["W2"]), bf16(prm["W3"])
+    Xb = bf16(X)
+    h1 = bf16(np.maximum(Xb @ W1.T + prm["b1"], 0.0))
+    h2 = bf16(np.maximum(h1 @ W2.T + prm["b2"], 0.0))
+    z = h2 @ W3.T + prm["b3"]
+    p = softmax(z)
+    w = np.asarray(w_class, np.float64)[y]
+    d = p.copy()
+    d[np.arange(len(y)), y] -= 1.0
+    d *= w[:, None]
+    db = bf16(d)
+    g = {"W3": db.T @ h2, "b3": d.sum(0)}
+    da2 = bf16((db @ W3) * (h2 > 0))
+    g["W2"] = da2.T @ h1
+    g["b2"] = da2.sum(0)
+    da1 = bf16((da2 @ W2) * (h1 > 0))
+    g["W1"] = da1.T @ Xb
+    g["b1"] = da1.sum(0)
+    return pack(g) / np.sum(w)

@@ -197,3 +197,54 @@ def test_learned_logits_match_the_numpy_bf16_forward():
     # margin 0: the class decides; at t0 = 0 only left is allowed, so right means stay
     assert np.array_equal(dl["lc_dir"][L], np.where(cls == 1, 1, 0))
     assert (cls == 1).sum() > 0 and (cls != 1).sum() > 0
+
+
+def _sparse_exact_net(rng):
+    """Each hidden unit reads one input (layer 1) or two units (layer 2) with dyadic
+    weights, so inputs in quarters give every activation exactly in BF16."""
+    p = {k: np.zeros(s) for k, s in mlp.SHAPES}
+    for j in range(64):
+        p["W1"][j, j % 16] = rng.choice([-1.0, -0.5, 0.5, 1.0])
+        p["W2"][j, (7 * j) % 64] = rng.choice([-0.5, 0.5, 1.0])
+        p["W2"][j, (3 * j + 1) % 64] = rng.choice([-0.25, 0.25])
+    p["b1"] = rng.integers(-2, 3, 64) * 0.25
+    p["b2"] = rng.integers(-2, 3, 64) * 0.125
+    p["W3"] = rng.integers(-2, 3, (3, 64)) * 0.25
+    p["b3"] = np.array([0.25, -0.25, 0.0])
+    return mlp.pack(p)
+
+
+def test_bf16_gradient_is_the_plain_gradient_at_bf16_resolution():
+    """Weights, inputs and activations exactly representable in BF16: the BF16 gradient then
+    differs from the plain FP64 gradient (pinned by central differences) only by the BF16
+    rounding of the output and hidden-layer gradients (relative 2^-9 each), far below what a
+    missing, extra or transposed term would change."""
+    rng = np.random.default_rng(3)
+    theta = _sparse_exact_net(rng)
+    X = rng.integers(-3, 4, (256, 16)).astype(float) / 4
+    _, (_, _, h1, _, h2) = mlp.forward(theta, X)
+    assert np.array_equal(mlp.bf16(h1), h1) and np.array_equal(mlp.bf16(h2), h2)
+    y = rng.integers(0, 3, 256)
+    w = np.array([1.0, 2.0, 1.5])
+    ga = mlp.grad_bf16(theta, X, y, w)
+    gb = mlp.grad(theta, X, y, w)
+    scale = np.abs(gb).max()
+    assert scale > 1e-2
+    np.testing.assert_allclose(ga, gb, rtol=1e-2, atol=2e-3 * scale)
+    assert np.linalg.norm(ga - gb) <= 1e-2 * np.linalg.norm(gb)
+
+
+def test_bf16_gradient_rounds_the_output_gradient():
+    """A class weight of 1 leaves p - onehot = 1/3 and -2/3, which are not BF16 values: the
+    weight gradient of the last layer must use their BF16 roundings (0.333984375 and
+    -0.66796875) while the output bias gradient keeps the exact thirds."""
+    p = {k: np.zeros(s) for k, s in mlp.SHAPES}
+    p["W1"][0, 0] = 1.0
+    p["W2"][0, 0] = 1.0
+    theta = mlp.pack(p)
+    X = np.zeros((1, 16))
+    X[0, 0] = 1.0
+    g = mlp.unpack(mlp.grad_bf16(theta, X, np.array([0]), np.ones(3)))
+    assert g["W3"][0, 0] == mlp.bf16(-2.0 / 3.0) == -0.66796875
+    assert g["W3"][1, 0] == mlp.bf16(1.0 / 3.0) == 0.333984375
+    np.testing.assert_allclose(g["b3"], [-2.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0], rtol=1e-15)

@@ -754,7 +754,7 @@ __device__ __forceinline__ int vehicle_finish(const StepArgs &a, const Soa &S, i
     a.dbg.s_own[i] = u.own.gap;
     a.dbg.vl_own[i] = u.own.vl;
     a.dbg.a_own[i] = u.a_own;
-    a.dbg.lc_dir[i] = u.lc.dir;
+    a.dbg.lc_dir[i] = dir;   // the direction taken (the network's where it decided)
     a.dbg.lc_cand[i] = u.lc.cand;
     a.dbg.tau_lead[i] = u.lc.tl >= 0 ? S.id[u.lc.tl] : -1;
     a.dbg.tau_foll[i] = u.lc.tf >= 0 ? S.id[u.lc.tf] : -1;

@@ -155,8 +155,12 @@ def test_gpu_gradient_matches_fp64_reference(torch_mod):
 
 @pytest.mark.parametrize("at", ["init", "trained"])
 def test_gpu_gradient_on_logged_samples(torch_mod, logged, trained, at):
-    """The same check on the inputs the step logs (their own scales and BF16 rounding), at an
-    initial and at the trained network, with the training's class weights."""
+    """Gradients on the inputs the step logs (their own scales), at an initial and at the
+    trained network, with the training's class weights, against the reference computed with
+    the kernel's BF16 rounding points (oracle/mlp.grad_bf16) and against the plain FP64
+    gradient.  At the trained network the gradient is a small residual, and the BF16
+    roundings themselves move it by several per cent from the FP64 value, so the FP64
+    criterion (cosine >= 0.999, relative L2 <= 2e-2) applies at the initial network only."""
     torch = torch_mod
     (xtr, ytr), _ = logged
     theta0, _, cw, _ = trained
@@ -170,11 +174,16 @@ def test_gpu_gradient_on_logged_samples(torch_mod, logged, trained, at):
     X = xtr[idx.long()].float().cpu().double().numpy()
     Y = ytr[idx.long()].cpu().numpy()
     g_gpu = grad.cpu().double().numpy()
-    g_ref = ref.grad(theta.astype(np.float64), X, Y, cw.astype(np.float64))
-    cos = g_gpu @ g_ref / (np.linalg.norm(g_gpu) * np.linalg.norm(g_ref))
-    rel = np.linalg.norm(g_gpu - g_ref) / np.linalg.norm(g_ref)
-    print(at, "cosine", cos, "rel L2", rel, "|g|", np.linalg.norm(g_ref))
-    assert cos >= 0.999 and rel <= 2e-2
+
+    def cmp(g_ref):
+        cos = g_gpu @ g_ref / (np.linalg.norm(g_gpu) * np.linalg.norm(g_ref))
+        return cos, np.linalg.norm(g_gpu - g_ref) / np.linalg.norm(g_ref)
+    cos_b, rel_b = cmp(ref.grad_bf16(theta.astype(np.float64), X, Y, cw.astype(np.float64)))
+    cos_f, rel_f = cmp(ref.grad(theta.astype(np.float64), X, Y, cw.astype(np.float64)))
+    print(at, "vs BF16 reference: cosine", cos_b, "rel L2", rel_b, "| vs FP64: cosine", cos_f, "rel L2", rel_f)
+    assert cos_b >= 0.9995 and rel_b <= 1e-2
+    if at == "init":
+        assert cos_f >= 0.999 and rel_f <= 2e-2
 
 
 def test_gpu_adam_matches_reference_adam(torch_mod, logged):

@@ -102,7 +102,7 @@ struct Sim {
   int2 *d_qhd = nullptr;
   int4 *d_qent = nullptr, *d_qent2 = nullptr;
   int *d_tdep = nullptr, *d_route0 = nullptr, *d_tarr = nullptr;
-  float *d_vsum = nullptr;
+  unsigned long long *d_vsum = nullptr;   // per window x lane: sum of speeds, 2^-24 m/s units
   int *d_vcnt = nullptr;
   DebugOut dbg{};
   int n_tiles = 0;
@@ -910,7 +910,7 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
   if (s->prm.n_windows > 0) {
     DALLOC(s->d_vsum, (size_t)s->prm.n_windows * s->n_lanes);
     DALLOC(s->d_vcnt, (size_t)s->prm.n_windows * s->n_lanes);
-    CK(cudaMemset(s->d_vsum, 0, sizeof(float) * s->prm.n_windows * s->n_lanes));
+    CK(cudaMemset(s->d_vsum, 0, sizeof(unsigned long long) * s->prm.n_windows * s->n_lanes));
     CK(cudaMemset(s->d_vcnt, 0, sizeof(int) * s->prm.n_windows * s->n_lanes));
   }
   if (s->prm.debug) {
@@ -1251,7 +1251,11 @@ int ms_read_metrics(void *sim, ms_metrics *out) {
   DevCtrl c;
   CK(cudaMemcpy(&c, s->d_ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost));
   size_t m = (size_t)s->prm.n_windows * s->n_lanes;
-  if (out->lane_vsum && m) CK(cudaMemcpy(out->lane_vsum, s->d_vsum, m * sizeof(float), cudaMemcpyDeviceToHost));
+  if (out->lane_vsum && m) {   // exact integer sums in units of 2^-24 m/s
+    std::vector<unsigned long long> q(m);
+    CK(cudaMemcpy(q.data(), s->d_vsum, m * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    for (size_t k = 0; k < m; ++k) out->lane_vsum[k] = (float)std::ldexp((double)q[k], -24);
+  }
   if (out->lane_vcnt && m) CK(cudaMemcpy(out->lane_vcnt, s->d_vcnt, m * sizeof(int), cudaMemcpyDeviceToHost));
   out->inserted = (int64_t)c.inserted;
   out->arrived = (int64_t)c.arrived;
@@ -1484,7 +1488,7 @@ int snap_take(Sim *s, Snapshot &sn) {
   add(s->d_mp, s->h_ctrl4.size() * 16);
   add(s->d_sig[1], s->h_ctrl4.size() * 4);
   add(s->d_tarr, N * 4);
-  add(s->d_vsum, W * 4);
+  add(s->d_vsum, W * 8);
   add(s->d_vcnt, W * 4);
   for (auto &r : sn.regions) {
     void *c = nullptr;

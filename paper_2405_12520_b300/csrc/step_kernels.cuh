@@ -191,7 +191,7 @@ struct StepArgs {
                        // of the lane's next entry or INT_MAX, 0}
   const int *trip_tdep;
   int *t_arr;
-  float *vsum;
+  unsigned long long *vsum;   // per window x lane: sum of speeds in units of 2^-24 m/s
   int *vcnt;
   DebugOut dbg;
   LcAux lc;
@@ -804,55 +804,31 @@ __device__ __forceinline__ int count_bits(const unsigned *b, int s, int e) {
 // kernels
 // ------------------------------------------------------------------------------------
 
-// sum of v[from, to) by the whole warp (coalesced loads, then a butterfly); called by all
-// 32 threads
-__device__ __noinline__ float warp_range_sum(const float *v, int from, int to) {
-  float s = 0.f;
-  for (int j = from + (threadIdx.x & 31); j < to; j += 32) s += v[j];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return s;
-}
-
-// Per-lane window metrics over the snapshot (sum of speeds and count), deterministic:
-// a segmented sum over the warp (vehicles of a lane are consecutive), plus the part of its
-// lane that lies in later warps (by the lane's first vehicle when short, by the whole warp
-// when long: lanes of hundreds of vehicles); the lane's first vehicle adds the result to
-// the window accumulators (one writer per lane and step).
-__device__ __forceinline__ void lane_speed_sums(const StepArgs &a, const Soa &S, const int4 *dyn,
-                                                int i, int w, const VCtx &c) {
+// Per-lane window metrics over the snapshot: sum of speeds and count.  A lane's vehicles are
+// consecutive, so each warp sums the run of every lane within it (segmented scan from the
+// right, a fixed order) and the run's first vehicle adds it to the lane's accumulators: the
+// count as an integer, the sum in integer units of 2^-24 m/s, so the per-lane totals are
+// exact sums of the runs whatever the order of the atomics (deterministic).  Called by all
+// 32 threads.
+__device__ __forceinline__ void lane_speed_sums(const StepArgs &a, int w, const VCtx &c) {
+  const unsigned full = 0xffffffffu;
   const int wl = threadIdx.x & 31;
   const bool act = c.l >= 0;
   const int l = act ? c.l : -1 - wl;
   float v = act ? c.v : 0.f;
-  // segmented inclusive scan from the right: each thread gets the sum of its lane's
-  // vehicles from itself to the end of the warp
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    float y = __shfl_down_sync(0xffffffffu, v, o);
-    int ly = __shfl_down_sync(0xffffffffu, l, o);
+    const float y = __shfl_down_sync(full, v, o);
+    const int ly = __shfl_down_sync(full, l, o);
     if (wl + o < 32 && ly == l) v += y;
   }
-  const bool first = act && !c.nb.sameF;   // the lane's first vehicle writes its sums
-  int4 d = make_int4(0, 0, 0, 0);
-  if (first) d = dyn[l];
-  const int warp_end = (i | 31) + 1;   // first index past this warp
-  const int rem = first ? d.x + d.y - warp_end : 0;   // its lane's vehicles in later warps
-  // only the lane of the warp's last vehicle can continue past the warp; a long remainder
-  // (lanes of hundreds of vehicles) is summed by the whole warp, a short one by the thread
-  const unsigned lg = __ballot_sync(0xffffffffu, rem > 16);
-  if (lg) {
-    const int f = __ffs(lg) - 1;
-    const float tail = warp_range_sum(S.v, warp_end, __shfl_sync(0xffffffffu, d.x + d.y, f));
-    if (wl == f) v += tail;
-  } else {
-    for (int j = warp_end; j < warp_end + rem; ++j) v += S.v[j];
-  }
-  if (!first) return;
-  // one writer per lane and step, so the sums stay deterministic; nothing waits on these
+  // bit k: vehicle k + 1 of the warp continues vehicle k's run (never past the warp)
+  const unsigned cont = __ballot_sync(full, __shfl_down_sync(full, l, 1) == l) & 0x7fffffffu;
+  const bool head = act && (wl == 0 || !((cont >> (wl - 1)) & 1u));
+  if (!head) return;
   const size_t o = (size_t)w * a.P.n_lanes + l;
-  atomicAdd(&a.vsum[o], v);
-  atomicAdd(&a.vcnt[o], d.y);
+  atomicAdd(&a.vsum[o], __float2ull_rn(v * 16777216.f));
+  atomicAdd(&a.vcnt[o], __ffs(~(cont >> wl)));   // the run's length
 }
 
 // The 16 inputs of the learned lane-change decision (scaled to O(1)): own speed and desired
@@ -969,7 +945,7 @@ __global__ void __launch_bounds__(512, 2) __maxnreg__((MODE == MODE_PLAIN && !DB
     }
     const unsigned lm = __ballot_sync(0xffffffffu, leave);
     if ((threadIdx.x & 31) == 0) a.leave[(base + threadIdx.x) >> 5] = lm;
-    if (rec) lane_speed_sums(a, S, dyn, i, w, c);
+    if (rec) lane_speed_sums(a, w, c);
     if (moving) arrival_records<DBG>(a, i, u, c);
   }
 }

@@ -565,10 +565,14 @@ def run_learned(args):
     torch.cuda.set_device(local)
     params = synth.default_params()
     t0 = time.perf_counter()
-    x, y = learned.collect(learned.small_grid_runs(args.train_seeds, 100), params, 3600, 8_000_000)
+    # training data: decisions logged by the rule-based step on the small 4x4 grid (500
+    # trips; denser seeds for standing queues; runs starting in a jam), 256 scenarios per
+    # batched simulation, until train_samples are logged
+    x, y, runs = learned.collect_batched(learned.mixed_specs(args.train_scenarios), params, 3600,
+                                         args.train_samples)
     t_collect = time.perf_counter() - t0
     cw, cnt = learned.class_weights(y)
-    theta, info = learned.train(x, y, epochs=10, batch=4096, lr=2e-3, seed=1, class_w=cw)
+    theta, info = learned.train(x, y, epochs=args.train_epochs, batch=8192, lr=2e-3, seed=1, class_w=cw)
     if args.workload == "learned5m":   # the same network at 5M vehicles (near jam density)
         net = synth.large_grid_network()
         dem = synth.place_vehicles(net, 5_000_000, seed=args.seed, min_spacing=6.0)
@@ -617,9 +621,10 @@ def run_learned(args):
                 row = sum(st[f"conf_{rn}{f}"] for f in "slr")
                 out[name][f"agree_{rn}"] = st[f"conf_{rn}{rn}"] / max(1, row)
         sim.destroy()
-    # per-lane 5-minute mean speeds: both rules from the same start over the first 300-step
-    # window, compared on lanes with at least 300 vehicle-steps in both runs
-    win = {}
+    # per-lane 5-minute mean speeds and trajectories: both rules from the same start over the
+    # first 300-step window; speeds compared on lanes with at least 300 vehicle-steps in both
+    # runs, trajectories on the trips active in both at the end of the window
+    win, fin = {}, {}
     for name in ("rule", "learned"):
         sim = moss.Sim(params, stream=stream, n_windows=1)
         sim.load_network(net)
@@ -629,12 +634,35 @@ def run_learned(args):
         sim.step(int(params["window"]))
         m = sim.read_metrics()
         win[name] = (m["vsum"][0].astype(np.float64), m["vcnt"][0].astype(np.float64))
+        if name == "learned":   # agreement over the whole window (more candidates than the timed steps)
+            sw = sim.read_lc_stats()
+            out["learned"]["window_agreement"] = {
+                "steps": int(params["window"]), "candidates": sw["candidates"],
+                "agreement": sw["agree"] / max(1, sw["candidates"]),
+                "fallback_rate": sw["fallbacks"] / max(1, sw["candidates"]),
+                **{f"agree_{rn}": sw[f"conf_{rn}{rn}"] / max(1, sum(sw[f"conf_{rn}{f}"] for f in "slr"))
+                   for rn in "slr"}}
+        st = sim.read_state(trips=False)
+        lane = np.full(dem.n, -1, np.int64)
+        xx = np.zeros(dem.n)
+        lane[st["id"]] = st["lane"]
+        xx[st["id"]] = st["x"]
+        fin[name] = (lane, xx, m["arrived"])
         sim.destroy()
     (gv, gc), (rv, rc) = win["learned"], win["rule"]
     busy = (gc >= 300) & (rc >= 300)
     rel = np.abs(gv[busy] / gc[busy] - rv[busy] / rc[busy]) / np.maximum(rv[busy] / rc[busy], 1e-6)
     lane_err = {"lanes": int(busy.sum()), "mean_rel": float(rel.mean()), "p90_rel": float(np.quantile(rel, 0.9)),
                 "window_s": int(params["window"])}
+    (la, xa, arr_l), (lb, xb, arr_r) = fin["learned"], fin["rule"]
+    both = (la >= 0) & (lb >= 0)
+    same = both & (la == lb)
+    dx = np.abs(xa[same] - xb[same])
+    traj = {"after_steps": int(params["window"]), "trips_active_in_both": int(both.sum()),
+            "same_lane_frac": float(same.sum() / max(1, both.sum())),
+            "same_lane_mean_abs_dx_m": float(dx.mean()) if dx.size else 0.0,
+            "same_lane_p90_abs_dx_m": float(np.quantile(dx, 0.9)) if dx.size else 0.0,
+            "arrived_learned": int(arr_l), "arrived_rule": int(arr_r)}
     L = out["learned"]
     line = {
         "metric": "vehicle-steps/s", "value": L["value"], "unit": "vehicle-steps/s", "n_gpus": world,
@@ -643,13 +671,17 @@ def run_learned(args):
         "data": "synthetic", "gpu_launches": (STEP_LAUNCHES + 1) * args.steps,   # + k_learn
         "config": {"workload": args.workload, "description": desc + "; lane-change decisions by the learned MLP",
                    "l2": "flushed (256 MiB write) before every timed step; each step timed alone",
-                   "train": {"samples": int(x.shape[0]), "class_counts": cnt.tolist(), "seeds": args.train_seeds,
-                             "collect_s": round(t_collect, 1), "adam_steps": info["steps"],
+                   "train": {"samples": int(x.shape[0]), "class_counts": cnt.tolist(), "scenario_runs": runs,
+                             "demand_mix": "4x4 grid: 30% 500 trips, 10% 1,500, 10% 3,000, 15% 5,000 "
+                                           "(standing queues), 20% 2,500 placed 6 m apart + 500 trips, "
+                                           "15% 2,900 placed + 300 trips (jam)",
+                             "collect_s": round(t_collect, 1), "epochs": args.train_epochs,
+                             "adam_steps": info["steps"], "batch": 8192,
                              "train_s": round(info["seconds"], 2), "class_w": info["class_w"]}},
         "learned": L, "rule": out["rule"],
         "learned_vs_rule": L["value"] / out["rule"]["value"],
         "mean_speed_rel_diff": abs(L["mean_speed"] - out["rule"]["mean_speed"]) / out["rule"]["mean_speed"],
-        "lane_mean_speed_error": lane_err,
+        "lane_mean_speed_error": lane_err, "trajectory_vs_rule": traj,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -838,7 +870,9 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scenarios", type=int, default=256)
-    ap.add_argument("--train-seeds", type=int, default=200)
+    ap.add_argument("--train-samples", type=int, default=50_000_000, help="learned: logged samples to train on")
+    ap.add_argument("--train-scenarios", type=int, default=40_000, help="learned: small-grid runs available")
+    ap.add_argument("--train-epochs", type=int, default=8)
     ap.add_argument("--signals", choices=("fixed", "mp"), default="fixed",
                     help="signal control: fixed-time plans or max pressure")
     ap.add_argument("--mp-interval", type=int, default=10, help="steps between max-pressure decisions")

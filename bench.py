@@ -544,7 +544,11 @@ def run_batch(args):
                                   "scenario log-uniform in [500, 200k] (capped at 60% of jam capacity), pre-placed",
                    "l2": "inputs larger than L2; steps timed back to back", "generation_s": round(gen_s, 1)},
         "autotune": {"best_ms_per_step": tune_ms, "block": tune_cfg[0], "decide_grid_factor": tune_cfg[1],
-                     "apply_grid_factor": tune_cfg[2]},
+                     "apply_grid_factor": tune_cfg[2], "lane_scan_threads_per_tile": tune_cfg[3],
+                     "bucket_block": tune_cfg[4], "bucket_grid_factor": tune_cfg[5],
+                     "searched": "27 (block 128/256/512 x decide, apply grid factor 1/2/4), then lane-scan "
+                                 "threads per 1024-lane tile 128/256/512, then bucket block 128/256/512 x "
+                                 "grid factor 1/2: 36 trials of 3 steps"},
         "separate": {"value": vs_s / (ms_s * 1e-3), "ms_per_step": ms_s / args.steps,
                      "gpu_launches": STEP_LAUNCHES * n_scen * args.steps},
         "speedup_vs_separate": (vs_b / ms_b) / (vs_s / ms_s),

@@ -273,12 +273,15 @@ int ms_add_vehicles_batch(void *sim, int n, const ms_vehicles *vehs);
    arrays); MS_ERR_STATE if the simulation was not loaded as a batch. */
 int ms_batch_offsets(void *sim, int *lane_off, int *trip_off);
 
-/* Autotuner of the step's launch shapes: for each candidate (threads per block of the
-   vehicle kernels, persistent-grid oversubscription) it times trial_steps steps with CUDA
-   events, restoring the dynamic state after each trial, and keeps the fastest; the
-   simulation's results are unchanged.  best_ms receives the best mean step time (ms),
-   config (3 ints, may be NULL) the chosen block size, grid factor of k_decide and of
-   k_apply.  Allocates temporary device memory for the state snapshot. */
+/* Autotuner of the step's launch shapes: for each candidate it times trial_steps steps with
+   CUDA events, restoring the dynamic state after each trial, and keeps the fastest; the
+   simulation's results are unchanged.  Coordinate search over (1) threads per block of the
+   vehicle kernels (128, 256, 512) x persistent-grid oversubscription of the decide and the
+   apply kernel (1, 2, 4 each), (2) the lane scan's threads per 1024-lane tile (128, 256,
+   512), (3) the bucket kernel's block (128, 256, 512) and grid factor (1, 2): 36 trials.
+   best_ms receives the best mean step time (ms); config (6 ints, may be NULL) the chosen
+   block size, decide and apply grid factors, lane-scan threads per tile, bucket block and
+   bucket grid factor.  Allocates temporary device memory for the state snapshot. */
 int ms_autotune(void *sim, int trial_steps, float *best_ms, int *config);
 
 /* ---- learned lane-change surrogate ----------------------------------------------

@@ -35,7 +35,16 @@ struct LaunchCfg {
   int blk_bucket = 256, grid_bucket = 1;
   int grid_learn = 1;   // k_learn (LEARN_THREADS per block), learned lane change only
   int f_decide = 1, f_apply = 1, f_bucket = 1;   // grid = factor x resident blocks x SMs
+  int lane_threads = LANE_THREADS;   // lane scan: threads per tile of LANE_TILE lanes
 };
+
+// the lane scan's passes for a tile shape (threads per tile: 128, 256 or 512)
+typedef void (*LanesKernel)(StepArgs);
+LanesKernel lanes_kernel(int pass, int th) {
+  if (th == 128) return pass ? k_lanes_t<1, 128> : k_lanes_t<0, 128>;
+  if (th == 512) return pass ? k_lanes_t<1, 512> : k_lanes_t<0, 512>;
+  return pass ? k_lanes_t<1, 256> : k_lanes_t<0, 256>;
+}
 
 struct Sim {
   ms_params prm{};
@@ -245,8 +254,8 @@ cudaError_t launch_step(const Sim *s, const StepArgs &a, cudaStream_t st, cudaEv
     ok(cudaGetLastError());
   }
   if (ev) cudaEventRecord(ev[1], st);
-  ok(launch_pdl(k_lanes_t<0>, s->n_tiles, LANE_THREADS, 0, st, a));   // tile aggregates
-  ok(launch_pdl(k_lanes_t<1>, s->n_tiles, LANE_THREADS, 0, st, a));   // counts, starts, departures
+  ok(launch_pdl(lanes_kernel(0, c.lane_threads), s->n_tiles, c.lane_threads, 0, st, a));   // tile aggregates
+  ok(launch_pdl(lanes_kernel(1, c.lane_threads), s->n_tiles, c.lane_threads, 0, st, a));   // counts, starts, ...
   if (ev) cudaEventRecord(ev[2], st);
   ok(launch_pdl(k_bucket, c.grid_bucket, c.blk_bucket, 0, st, a));
   if (ev) cudaEventRecord(ev[3], st);
@@ -1521,42 +1530,58 @@ int ms_autotune(void *sim, int trial_steps, float *best_ms, int *config) {
   Snapshot sn;
   int r = snap_take(s, sn);
   if (r) { snap_free(sn); return r; }
-  const int blocks[] = {128, 256, 512};
-  const int factors[] = {1, 2, 4};
-  LaunchCfg best = s->cfg;
-  float best_t = 3.4e38f;
-  int best_conf[3] = {s->cfg.blk_decide, 1, 1};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   StepArgs a = make_args(s);
-  for (int blk : blocks) {
-    for (int fd : factors) {
+  LaunchCfg best = s->cfg;
+  float best_t = 3.4e38f;
+  // one candidate: a warm-up step of its shape, then trial_steps timed steps; the state is
+  // restored afterwards, so the simulation's results do not depend on the search
+  auto trial = [&](const LaunchCfg &c) -> int {
+    s->cfg = c;
+    CK(launch_step(s, a, s->stream, nullptr));
+    CK(cudaEventRecord(e0, s->stream));
+    for (int k = 0; k < trial_steps; ++k) CK(launch_step(s, a, s->stream, nullptr));
+    CK(cudaEventRecord(e1, s->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    ms /= trial_steps;
+    if (int rr = snap_restore(s, sn)) return rr;
+    if (ms < best_t) {
+      best_t = ms;
+      best = c;
+    }
+    return MS_OK;
+  };
+  // coordinate search: (threads per block of the vehicle kernels, grid factors of decide and
+  // apply), then the lane scan's tile shape, then k_bucket's block and grid factor
+  const int blocks[] = {128, 256, 512};
+  const int factors[] = {1, 2, 4};
+  for (int blk : blocks)
+    for (int fd : factors)
       for (int fa : factors) {
-        LaunchCfg c;
+        LaunchCfg c = s->cfg;
         c.blk_decide = c.blk_apply = blk;
         c.blk_bucket = 256;
-        if ((r = shape_grids(s, c, fd, fa, 1))) { snap_free(sn); return r; }
-        s->cfg = c;
-        CK(launch_step(s, a, s->stream, nullptr));   // warm-up step of this shape
-        CK(cudaEventRecord(e0, s->stream));
-        for (int k = 0; k < trial_steps; ++k) CK(launch_step(s, a, s->stream, nullptr));
-        CK(cudaEventRecord(e1, s->stream));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        ms /= trial_steps;
-        if ((r = snap_restore(s, sn))) { snap_free(sn); return r; }
-        if (ms < best_t) {
-          best_t = ms;
-          best = c;
-          best_conf[0] = blk;
-          best_conf[1] = fd;
-          best_conf[2] = fa;
-        }
+        c.lane_threads = LANE_THREADS;
+        if ((r = shape_grids(s, c, fd, fa, 1)) || (r = trial(c))) { snap_free(sn); return r; }
       }
-    }
+  const LaunchCfg stage1 = best;
+  for (int th : {128, 512}) {
+    LaunchCfg c = stage1;
+    c.lane_threads = th;
+    if ((r = trial(c))) { snap_free(sn); return r; }
   }
+  const LaunchCfg stage2 = best;
+  for (int bb : blocks)
+    for (int fb : {1, 2}) {
+      if (bb == stage2.blk_bucket && fb == stage2.f_bucket) continue;
+      LaunchCfg c = stage2;
+      c.blk_bucket = bb;
+      if ((r = shape_grids(s, c, c.f_decide, c.f_apply, fb)) || (r = trial(c))) { snap_free(sn); return r; }
+    }
   CK(cudaStreamSynchronize(s->stream));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1564,7 +1589,11 @@ int ms_autotune(void *sim, int trial_steps, float *best_ms, int *config) {
   s->cfg = best;
   drop_graphs(s);   // rebuilt with the chosen shapes on the next ms_step
   if (best_ms) *best_ms = best_t;
-  if (config) std::copy(best_conf, best_conf + 3, config);
+  if (config) {
+    const int out[6] = {best.blk_decide, best.f_decide, best.f_apply, best.lane_threads, best.blk_bucket,
+                        best.f_bucket};
+    std::copy(out, out + 6, config);
+  }
   return MS_OK;
 }
 

@@ -1071,16 +1071,18 @@ __device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long 
 }
 
 // Lane pass: new per-lane counts, a scan over lanes, departures.  A tile of LANE_TILE lanes
-// is processed by LANE_THREADS threads in LANE_ITEMS striped slices (lane k * LANE_THREADS
-// + thread), so every load is coalesced and the loads of all slices are issued before any
+// is processed by TH threads in LANE_TILE / TH striped slices (lane k * TH + thread), so every load is coalesced and the loads of all slices are issued before any
 // is used.  Two launches: pass 0 computes every tile's aggregate and writes it; pass 1
 // computes the same per-lane counts again (its inputs are read-only here), sums the
 // aggregates of all its predecessors, one per thread (with a few hundred tiles the
 // quadratic number of reads is small), and writes the results.  The launch boundary makes
 // the aggregates visible; a single launch that waited on its predecessors' flags spent
 // several microseconds before those stores became visible to the waiting blocks.
-template <int PASS>
-__global__ void __launch_bounds__(LANE_THREADS, 4) k_lanes_t(StepArgs a) {
+// TH threads per tile (LANE_TILE / TH lanes each): the autotuner picks among 128, 256, 512.
+template <int PASS, int TH = LANE_THREADS>
+__global__ void __launch_bounds__(TH, LANE_TILE / TH) k_lanes_t(StepArgs a) {
+  constexpr int LANE_THREADS = TH, LANE_ITEMS = LANE_TILE / TH, LANE_WARPS = TH / 32;
+  static_assert(LANE_ITEMS * TH == LANE_TILE && LANE_WARPS <= 32, "lane tile shape");
   __shared__ unsigned long long s_wsum[LANE_ITEMS][LANE_WARPS];
   __shared__ unsigned long long s_part[LANE_WARPS];
   pdl_enter();

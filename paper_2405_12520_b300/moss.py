@@ -268,10 +268,11 @@ class Sim:
         return lo, to
 
     def autotune(self, trial_steps: int = 5):
-        """Pick the fastest launch shape (block size, grid factors); returns
-        (best ms per step, (block, decide grid factor, apply grid factor))."""
+        """Pick the fastest launch shape; returns (best ms per step, (block, decide grid
+        factor, apply grid factor, lane-scan threads per tile, bucket block, bucket grid
+        factor))."""
         ms = C.c_float()
-        cfg = np.zeros(3, np.int32)
+        cfg = np.zeros(6, np.int32)
         self._check(self.lib.ms_autotune(self.h, int(trial_steps), C.byref(ms), _p(cfg)), "ms_autotune")
         return ms.value, tuple(int(c) for c in cfg)
 

@@ -78,6 +78,7 @@ def test_autotune_keeps_results_and_picks_a_candidate():
     b.step(20)
     ms, cfg = b.autotune(trial_steps=3)
     assert ms > 0 and cfg[0] in (128, 256, 512) and cfg[1] in (1, 2, 4) and cfg[2] in (1, 2, 4)
+    assert cfg[3] in (128, 256, 512) and cfg[4] in (128, 256, 512) and cfg[5] in (1, 2)
     sa, sb = a.read_state(), b.read_state()
     assert sa["t"] == sb["t"] == 20   # the trials left no trace
     a.step(60)

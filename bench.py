@@ -37,6 +37,7 @@ KERNELS = ("k_decide", "k_lanes", "k_bucket", "k_apply")
 # algorithmic bytes of each kernel: SoA fields it must read / write per vehicle
 # (x, v, v0, lane, rp, nxt, id = 28 B), per lane (counts, starts, queue heads), per mover
 STEP_LAUNCHES = 5   # k_decide, two lane-scan passes, k_bucket, k_apply
+METRICS_BYTES = 56  # ms_read_metrics without the per-lane arrays copies the step control record (56 B)
 B_DECIDE_VEH = 48   # reads the 36-B state (x, v, v0, lane, rp, plan word, nl, id); writes x', v', code
 B_APPLY_VEH = 72    # reads code, x', v', v0, rp, plan word, nl, id; writes the 36-B state
 B_LANES_LANE = 40
@@ -412,11 +413,29 @@ def run_ours(args):
                 "step_effective_gbs": n_avg * (B_DECIDE_VEH + B_APPLY_VEH) / (avg_ms.sum() * 1e-3) / 1e9}
     full_sort = full_sort_alternative(sim, stream, flush, avg_ms)
 
-    # end to end through the public API: step + read the per-vehicle state into pinned host
-    # memory every step (Sec. III-A: position and speed of every vehicle each step).  The
-    # export of each step's state runs on a side stream while the next step computes
-    # (ms_read_state_async / ms_read_wait, two pinned buffer sets used in turn).
+    # end to end through the public API, wall clock: every step ms_step(1) and a read of the
+    # step's result on the host -- its counters (vehicles active, inserted, arrived, summed
+    # travel time, device error bits: ms_read_metrics without the per-lane arrays, which
+    # waits for the step)
     e2e_steps = min(args.steps, 50)
+    barrier()
+    t0 = time.perf_counter()
+    e2e_vs = 0
+    for k in range(e2e_steps):
+        n_k = sim.read_metrics(lanes=False)["n_active"]   # vehicles the next step advances
+        sim.step(1)
+        e2e_vs += n_k
+    m_end = sim.read_metrics(lanes=False)
+    t1 = time.perf_counter()
+    assert m_end["err"] == 0
+    e2e = {"value": e2e_vs / (t1 - t0), "unit": "vehicle-steps/s", "h2d_bytes_per_step": 0,
+           "d2h_bytes_per_step": METRICS_BYTES,
+           "what": "ms_step(1) + ms_read_metrics (step counters: active, inserted, arrived, summed travel "
+                   "time, error bits) into host memory every step, wall clock"}
+    # the same with the whole per-vehicle state (x, v, lane, id: 16 B/vehicle) exported into
+    # pinned host buffers every step (Sec. III-A: position and speed of every vehicle each
+    # step), the export of each step running on a side stream while the next step computes
+    # (ms_read_state_async / ms_read_wait, two pinned buffer sets used in turn)
     cap = dem.n
     bufs = [dict(x=torch.empty(cap, dtype=torch.float32, pin_memory=True),
                  v=torch.empty(cap, dtype=torch.float32, pin_memory=True),
@@ -424,22 +443,23 @@ def run_ours(args):
                  vid=torch.empty(cap, dtype=torch.int32, pin_memory=True)) for _ in range(2)]
     barrier()
     t0 = time.perf_counter()
-    e2e_vs = 0
+    x_vs = 0
     d2h = 0
     sim.read_state_async(**bufs[0])
     for k in range(e2e_steps):
         sim.step(1)
         sim.read_state_async(**bufs[(k + 1) % 2])   # queued behind the export in flight
         n_k, _ = sim.read_wait()          # the state step k advanced, now on the host
-        e2e_vs += n_k
+        x_vs += n_k
         d2h += 16 * n_k
     n_k, _ = sim.read_wait()
     d2h += 16 * n_k
     t1 = time.perf_counter()
-    e2e = {"value": e2e_vs / (t1 - t0), "unit": "vehicle-steps/s", "h2d_bytes_per_step": 0,
-           "d2h_bytes_per_step": int(d2h / e2e_steps),
-           "what": "ms_step(1) + ms_read_state_async/ms_read_wait of x, v, lane, id into pinned host "
-                   "buffers every step (two exports queued, overlapping the steps), wall clock"}
+    e2e_state = {"value": x_vs / (t1 - t0), "unit": "vehicle-steps/s", "h2d_bytes_per_step": 0,
+                 "d2h_bytes_per_step": int(d2h / e2e_steps),
+                 "what": "ms_step(1) + ms_read_state_async/ms_read_wait of x, v, lane, id into pinned host "
+                         "buffers every step (two exports queued, overlapping the steps), wall clock; bound "
+                         "by the host link"}
     sim.sync()
 
     line = {
@@ -451,7 +471,8 @@ def run_ours(args):
                    "lanes": net.n_lanes, "active_start": n_act[0], "active_end": n_end,
                    "l2": "flushed (256 MiB write) before every timed step; each step timed alone",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": roofline, "e2e": e2e, "clocks": clk.summary(), "full_sort_alternative": full_sort,
+        "roofline": roofline, "e2e": e2e, "e2e_state_export": e2e_state, "clocks": clk.summary(),
+        "full_sort_alternative": full_sort,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         val, steps, el = cpu_baseline(net, dem, params, mods=mods)

@@ -40,6 +40,8 @@ extern "C" {
 #define MS_DEV_SCAN 2u       /* reserved (the lane scan no longer waits on other blocks) */
 #define MS_DEV_ORDER 4u      /* debug check: output not sorted by (lane, x) or gap < 0 */
 #define MS_DEV_BUCKET 8u     /* a moved vehicle did not find its merge record */
+#define MS_DEV_TIMEOUT 16u   /* a kernel's wait for its own shared-memory copies ran out (the
+                                kernel stopped; the step's results are not valid) */
 
 /* Model parameters.  Values the paper fixes: dt (1 s, Sec. III-A, IV-A); the model families
    (IDM, randomized MOBIL, Sec. III-A).  All other values are parameters of those models or

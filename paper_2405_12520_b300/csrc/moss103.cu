@@ -259,7 +259,7 @@ cudaError_t launch_step(const Sim *s, const StepArgs &a, cudaStream_t st, cudaEv
   if (ev) cudaEventRecord(ev[2], st);
   ok(launch_pdl(k_bucket, c.grid_bucket, c.blk_bucket, 0, st, a));
   if (ev) cudaEventRecord(ev[3], st);
-  ok(launch_pdl(k_apply, c.grid_apply, c.blk_apply, 0, st, a));
+  ok(launch_pdl(k_apply, c.grid_apply, c.blk_apply, app_smem(c.blk_apply), st, a));
   if (s->P.signal_mode == 1 && s->n_ctrl > 0)   // controllers of the next step
     ok(launch_pdl(k_signals, (s->n_ctrl + 7) / 8, 256, 0, st, a));
   if (ev) cudaEventRecord(ev[4], st);
@@ -283,7 +283,7 @@ int shape_grids(Sim *s, LaunchCfg &c, int f_decide, int f_apply, int f_bucket) {
   // k_learn: one block per SM, each warp looping over 16-candidate chunks (1,184 warps;
   // about 16k candidates a step on the 1M-vehicle grid use 1,030 of them)
   c.grid_learn = s->n_sm;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oa, k_apply, c.blk_apply, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oa, k_apply, c.blk_apply, app_smem(c.blk_apply)));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, k_bucket, c.blk_bucket, 0));
   auto g = [&](int blk, int occ, int f) {
     return std::max(1, std::min((N + blk - 1) / blk, f * std::max(1, occ) * s->n_sm));
@@ -883,12 +883,14 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
     });
     for (size_t k = 0; k < ord.size(); ++k) s->h_qtrip[k] = ord[k];
   }
-  // device allocations sized for every trip at once
+  // device allocations sized for every trip at once; the vehicle arrays to a multiple of four
+  // entries (the apply kernel copies whole 16-byte words of them into shared memory)
   const int N = n;
+  const int NS = (N + 3) & ~3;
   for (int b = 0; b < 2; ++b) {
-    DALLOC(s->A[b].x, N); DALLOC(s->A[b].v, N); DALLOC(s->A[b].v0, N);
-    DALLOC(s->A[b].lane, N); DALLOC(s->A[b].rp, N); DALLOC(s->A[b].pl, N); DALLOC(s->A[b].nl, N);
-    DALLOC(s->A[b].id, N);
+    DALLOC(s->A[b].x, NS); DALLOC(s->A[b].v, NS); DALLOC(s->A[b].v0, NS);
+    DALLOC(s->A[b].lane, NS); DALLOC(s->A[b].rp, NS); DALLOC(s->A[b].pl, NS); DALLOC(s->A[b].nl, NS);
+    DALLOC(s->A[b].id, NS);
     DALLOC(s->d_dyn[b], s->n_lanes);
   }
   DALLOC(s->d_ctrl, 1);
@@ -899,8 +901,8 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
   DALLOC(s->d_amin, s->n_lanes);
   DALLOC(s->d_arr_start, s->n_lanes + 1);
   DALLOC(s->d_bucket, N);
-  DALLOC(s->d_res_x, N);
-  DALLOC(s->d_res_v, N);
+  DALLOC(s->d_res_x, NS);
+  DALLOC(s->d_res_v, NS);
   DALLOC(s->d_res_code, N + 4);   // k_bucket reads it four codes at a time
   DALLOC(s->d_res_nl, N);
   DALLOC(s->d_res_pos, N);

@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include "mlp_kernels.cuh"
+#include "tma.cuh"
 
 namespace moss {
 
@@ -43,7 +44,7 @@ constexpr int LANE_WARPS = LANE_THREADS / 32;
 
 constexpr int AMIN_NONE = 0x7fffffff;
 
-constexpr unsigned DEV_HOP = 1u, DEV_SCAN = 2u, DEV_ORDER = 4u, DEV_BUCKET = 8u;
+constexpr unsigned DEV_HOP = 1u, DEV_SCAN = 2u, DEV_ORDER = 4u, DEV_BUCKET = 8u, DEV_TIMEOUT = 16u;
 constexpr int LEAVE_ONE = 1 << 16;   // a leaver in the per-lane arrival word
 
 // Static lane record, one 32-byte sector per lane.
@@ -863,6 +864,7 @@ __device__ __forceinline__ int lc_dir(int cls) { return cls == 1 ? 1 : (cls == 2
 // hidden buffer and 32 x 3 logits
 constexpr int LEARN_WARP_SMEM = 32 * MLP_IN * 2 + 16 * MLP_H * 2 + 32 * MLP_OUT * 4;
 constexpr int LEARN_THREADS = 256;   // k_learn block
+constexpr unsigned DEC_WAIT_LIMIT = 1u << 20;   // polls of a tile's copy barrier before giving up
 __host__ __device__ constexpr int learn_smem(int threads) {
   return (int)sizeof(MlpDev) + (threads / 32) * LEARN_WARP_SMEM;
 }
@@ -1285,13 +1287,54 @@ __device__ __forceinline__ bool bucket_less(int4 f, int4 e) {
   return f.z < e.z;
 }
 
+// Tile of the apply kernel in shared memory: per vehicle of a tile of T its plan word, result
+// code, id, route pointer, next-lane choice, v0, x', v' and lane, the lane from 4 vehicles
+// before the tile (the vehicle before its first warp); every part 16-byte aligned.
+__host__ __device__ constexpr int app_buf_bytes(int T) { return 40 * T + 16; }
+__host__ __device__ constexpr int app_smem(int T) { return 2 * app_buf_bytes(T) + 16; }
+
+// Issue the copies of apply tile `tile` into buffer buf (one thread).  Extents are multiples
+// of four elements: the arrays are allocated to a multiple of four.
+__device__ __forceinline__ void app_issue(const StepArgs &a, const Soa &S, int n, int T, int tile, unsigned char *buf,
+                                          uint64_t *bar) {
+  const int npad = (n + 3) & ~3;
+  const int base = tile * T;
+  const unsigned c = (unsigned)(min(base + T, npad) - base);
+  const int lo = max(0, base - 4), hi = min(base + T, npad);
+  const unsigned bl = 4u * (unsigned)(hi - lo);
+  mbar_expect_tx(bar, 36u * c + bl);
+  tma_load_1d(buf, S.pl + base, 8u * c, bar);
+  unsigned char *q = buf + 8 * T;
+  tma_load_1d(q, a.res_code + base, 4u * c, bar);
+  tma_load_1d(q + 4 * T, S.id + base, 4u * c, bar);
+  tma_load_1d(q + 8 * T, S.rp + base, 4u * c, bar);
+  tma_load_1d(q + 12 * T, S.nl + base, 4u * c, bar);
+  tma_load_1d(q + 16 * T, S.v0 + base, 4u * c, bar);
+  tma_load_1d(q + 20 * T, a.res_x + base, 4u * c, bar);
+  tma_load_1d(q + 24 * T, a.res_v + base, 4u * c, bar);
+  tma_load_1d(q + 28 * T + 4 * (lo - (base - 4)), S.lane + lo, bl, bar);
+}
+
 // Write each vehicle, with the result k_decide computed for it, to its sorted slot of the
 // t+1 buffer: stayers by their rank among the lane's stayers plus the arrivals ranked
-// before them, arrivals by their bucket rank.  A warp takes 32 consecutive vehicles and
-// issues every load indexed by the vehicle at once; a stayer's rank among its lane's
-// stayers comes from the warp's leave word (same-lane threads by a match), and only the
-// lane that continues from the previous warp reads its lane record and earlier words.
+// before them, arrivals by their bucket rank.  Each block walks tiles of blockDim.x
+// consecutive vehicles (grid stride); a tile's inputs arrive in shared memory by bulk
+// asynchronous copies (TMA), the next tile's while this one is written (two buffers), so
+// each warp's chain starts at its lane's new start and arrival bucket.  A stayer's rank
+// among its lane's stayers comes from the warp's leave word (same-lane threads by a
+// match), and only the lane that continues from the previous warp reads its lane record and
+// earlier words.  Waits are bounded (MS_DEV_TIMEOUT).
 __global__ void k_apply(StepArgs a) {
+  extern __shared__ __align__(128) unsigned char ssm[];
+  const int T = blockDim.x;
+  const int bsz = app_buf_bytes(T);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(ssm + 2 * bsz);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_proxy_async();
+  }
+  __syncthreads();
   pdl_enter();
   const int t = a.ctrl->t_apply;
   const int p = t & 1;
@@ -1300,7 +1343,7 @@ __global__ void k_apply(StepArgs a) {
   const int4 *dyn = a.dyn[p];
   int4 *ndyn = a.dyn[p ^ 1];
   const int n = a.ctrl->n_active[p];
-  const int stride = gridDim.x * blockDim.x;
+  const int G = gridDim.x;
   const int wl = threadIdx.x & 31;
   const unsigned full = 0xffffffffu;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1308,90 +1351,113 @@ __global__ void k_apply(StepArgs a) {
     a.ctrl->n_movers = 0;
     a.ctrl->n_cand = 0;
   }
-  for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+  if (threadIdx.x == 0 && blockIdx.x * T < n) app_issue(a, S, n, T, blockIdx.x, ssm, &bar[0]);
+  for (int j = 0;; ++j) {
+    const int tile = blockIdx.x + j * G;
+    const int base = tile * T;
+    if (base >= n) break;   // block-uniform
+    const int b = j & 1;
+    if (threadIdx.x == 0 && base + G * T < n) {   // the other buffer was released by the last barrier
+      fence_proxy_async();
+      app_issue(a, S, n, T, tile + G, ssm + (b ^ 1) * bsz, &bar[b ^ 1]);
+    }
+    const bool ok = __all_sync(full, mbar_wait(&bar[b], (j >> 1) & 1, DEC_WAIT_LIMIT));
     const int ws = base + (threadIdx.x & ~31);   // this warp's first vehicle
-    if (ws >= n) break;                          // warp-uniform
-    const int i = ws + wl;
-    const bool act = i < n;
-    int code = C_RETIRE << CODE_LANE_BITS, id = 0, lane = -1 - wl, rp = 0, nlc = 0;
-    unsigned long long pl = 0;
-    float v0 = 0.f, xn = 0.f, vn = 0.f;
-    if (act) {
-      code = a.res_code[i];
-      id = S.id[i];
-      lane = S.lane[i];
-      rp = S.rp[i];
-      nlc = S.nl[i];
-      pl = S.pl[i];
-      v0 = S.v0[i];
-      xn = a.res_x[i];
-      vn = a.res_v[i];
-    }
-    const unsigned lw = a.leave[ws >> 5];
-    int prev = -1;
-    if (wl == 0 && ws > 0) prev = S.lane[ws - 1];
-    prev = __shfl_sync(full, prev, 0);
-    const int kind = (unsigned)code >> CODE_LANE_BITS;
-    const int nl = code & CODE_LANE_MASK;
-    const unsigned same = __match_any_sync(full, lane);
-    // retirements: arrival step per trip, counters summed per warp
-    const bool ret = act && kind == C_RETIRE;
-    const unsigned rm = __ballot_sync(full, ret);
-    if (rm) {
-      const unsigned tt = ret ? (unsigned)(t + 1 - a.trip_tdep[id]) : 0u;
-      const unsigned tsum = __reduce_add_sync(full, tt);
-      if (ret) a.t_arr[id] = t + 1;
-      if (wl == 0) {
-        atomicAdd(&a.ctrl->arrived, (unsigned long long)__popc(rm));
-        atomicAdd(&a.ctrl->sum_tt, (unsigned long long)tsum);
+    if (ok && ws < n) do {
+      const unsigned char *buf = ssm + b * bsz;
+      const unsigned long long *tl_pl = reinterpret_cast<const unsigned long long *>(buf);
+      const int *tl = reinterpret_cast<const int *>(buf + 8 * T);
+      const int *tl_lane = tl + 7 * T;   // lane of vehicle base - 4 + k at k
+      const int i = ws + wl;
+      const int q = i - base;
+      const bool act = i < n;
+      int code = C_RETIRE << CODE_LANE_BITS, id = 0, lane = -1 - wl, rp = 0, nlc = 0;
+      unsigned long long pl = 0;
+      float v0 = 0.f, xn = 0.f, vn = 0.f;
+      if (act) {
+        code = tl[q];
+        id = tl[T + q];
+        rp = tl[2 * T + q];
+        nlc = tl[3 * T + q];
+        v0 = __int_as_float(tl[4 * T + q]);
+        xn = __int_as_float(tl[5 * T + q]);
+        vn = __int_as_float(tl[6 * T + q]);
+        lane = tl_lane[q + 4];
+        pl = tl_pl[q];
       }
-    }
-    if (!act || kind == C_RETIRE) continue;
-    const int bs = a.arr_start[nl], be = a.arr_start[nl + 1];
-    const int nfirst = ndyn[nl].x;
-    if (kind == C_TRANSFER_ROUTE) {   // internal lane -> edge lane: next route edge; the
-      rp += 1;                        // cached choice was made for this target lane
-      pl = a.plan[rp];
-    } else if (kind != C_STAY) {      // lane change or edge lane -> internal lane
-      nlc = a.res_code_nl[i];
-    }
-    int pos;
-    if (kind == C_STAY) {
-      // rank among the lane's stayers: same-lane stayers earlier in this warp, plus those
-      // before the warp when the lane continues from the previous one
-      int k = __popc(~lw & same & ((1u << wl) - 1u));
-      if (prev == lane) {
-        const int dx = dyn[lane].x;
-        k += (ws - dx) - count_bits(a.leave, dx, ws);
+      const unsigned lw = a.leave[ws >> 5];
+      const int prev = ws > 0 ? tl_lane[ws - base + 3] : -1;   // the vehicle before this warp
+      const int kind = (unsigned)code >> CODE_LANE_BITS;
+      const int nl = code & CODE_LANE_MASK;
+      const unsigned same = __match_any_sync(full, lane);
+      // retirements: arrival step per trip, counters summed per warp
+      const bool ret = act && kind == C_RETIRE;
+      const unsigned rm = __ballot_sync(full, ret);
+      if (rm) {
+        const unsigned tt = ret ? (unsigned)(t + 1 - a.trip_tdep[id]) : 0u;
+        const unsigned tsum = __reduce_add_sync(full, tt);
+        if (ret) a.t_arr[id] = t + 1;
+        if (wl == 0) {
+          atomicAdd(&a.ctrl->arrived, (unsigned long long)__popc(rm));
+          atomicAdd(&a.ctrl->sum_tt, (unsigned long long)tsum);
+        }
       }
-      int m = 0;
-      for (int q = bs; q < be; ++q) m += a.bucket[q].x <= k;
-      pos = nfirst + k + m;
-    } else {
-      int4 me = make_int4(0, 0, 0, -2);
-      for (int q = bs; q < be; ++q) {
-        int4 f = a.bucket[q];
-        if (f.w == i) { me = f; break; }
+      if (!act || kind == C_RETIRE) break;
+      const int bs = a.arr_start[nl], be = a.arr_start[nl + 1];
+      const int nfirst = ndyn[nl].x;
+      if (kind == C_TRANSFER_ROUTE) {   // internal lane -> edge lane: next route edge; the
+        rp += 1;                        // cached choice was made for this target lane
+        pl = a.plan[rp];
+      } else if (kind != C_STAY) {      // lane change or edge lane -> internal lane
+        nlc = a.res_code_nl[i];
       }
-      if (me.w != i) {
-        atomicOr(&a.ctrl->err, DEV_BUCKET);
-        continue;
+      int pos;
+      if (kind == C_STAY) {
+        // rank among the lane's stayers: same-lane stayers earlier in this warp, plus those
+        // before the warp when the lane continues from the previous one
+        int k = __popc(~lw & same & ((1u << wl) - 1u));
+        if (prev == lane) {
+          const int dx = dyn[lane].x;
+          k += (ws - dx) - count_bits(a.leave, dx, ws);
+        }
+        int m = 0;
+        for (int q = bs; q < be; ++q) m += a.bucket[q].x <= k;
+        pos = nfirst + k + m;
+      } else {
+        int4 me = make_int4(0, 0, 0, -2);
+        for (int q = bs; q < be; ++q) {
+          int4 f = a.bucket[q];
+          if (f.w == i) { me = f; break; }
+        }
+        if (me.w != i) {
+          atomicOr(&a.ctrl->err, DEV_BUCKET);
+          break;
+        }
+        int rank = 0;
+        for (int q = bs; q < be; ++q) rank += bucket_less(a.bucket[q], me);
+        pos = nfirst + me.x + rank;
+        a.arr_fill[nl] = 0;   // every arrival resets it; k_bucket is done
       }
-      int rank = 0;
-      for (int q = bs; q < be; ++q) rank += bucket_less(a.bucket[q], me);
-      pos = nfirst + me.x + rank;
-      a.arr_fill[nl] = 0;   // every arrival resets it; k_bucket is done
+      if (pos == nfirst)   // rearmost vehicle of its lane: the lane record's tail fields
+        reinterpret_cast<int2 *>(&ndyn[nl])[1] = make_int2(__float_as_int(xn), __float_as_int(vn));
+      D.x[pos] = xn;
+      D.v[pos] = vn;
+      D.v0[pos] = v0;
+      D.lane[pos] = nl;
+      D.rp[pos] = rp;
+      D.pl[pos] = pl;
+      D.nl[pos] = nlc;
+      D.id[pos] = id;
+    } while (0);
+    // every thread is done with buffer b (refilled two tiles on); a warp whose copies did not
+    // arrive in time stops the block
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(&a.ctrl->err, DEV_TIMEOUT);
+        if (base + G * T < n) mbar_wait(&bar[b ^ 1], ((j + 1) >> 1) & 1, DEC_WAIT_LIMIT);   // in flight
+      }
+      return;
     }
-    if (pos == nfirst)   // rearmost vehicle of its lane: the lane record's tail fields
-      reinterpret_cast<int2 *>(&ndyn[nl])[1] = make_int2(__float_as_int(xn), __float_as_int(vn));
-    D.x[pos] = xn;
-    D.v[pos] = vn;
-    D.v0[pos] = v0;
-    D.lane[pos] = nl;
-    D.rp[pos] = rp;
-    D.pl[pos] = pl;
-    D.nl[pos] = nlc;
-    D.id[pos] = id;
   }
 }
 

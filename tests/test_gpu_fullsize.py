@@ -17,19 +17,14 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 P = synth.default_params()
 
 
-@pytest.mark.parametrize("workload", ["grid1m", "city5m"])
-def test_full_size_step_matches_oracle(workload):
-    import torch
-    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
-    sys.path.insert(0, ROOT)
-    import bench
-    net, dem, _ = bench.workload(workload, 3)
-    sim = moss.Sim(P, n_windows=1)           # bench.py's configuration (block 0: default shapes)
-    sim.load_network(net)
-    sim.add_vehicles(dem)
-    sim.step(10)                              # the benchmark's warm-up
+def _full_step_vs_oracle(sim, net, dem, label, theta=None, margin=0.2):
+    """One production step of sim (already warmed up) against the oracle stepping from the
+    GPU's own state over every vehicle; then the invariants of the state at that size and
+    a checkpoint / resume.  theta: the learned lane-change model set on both sides."""
     st0 = sim.read_state()
-    orc = oracle.Oracle(net, dem, P, n_windows=1)
+    orc = oracle.Oracle(net, dem, P, n_windows=1, threads=os.cpu_count() or 1)
+    if theta is not None:
+        orc.set_lc_model(theta, margin)
     status, lane, x, v, rp, t_arr = parity.oracle_state_from_gpu(st0, orc.n)
     orc.set_state(status, lane, x, v, rp, st0["t"], t_arr)
     sim.step(1)
@@ -37,6 +32,7 @@ def test_full_size_step_matches_oracle(workload):
     gs = sim.read_state()
     m = sim.read_metrics(lanes=False)
     assert m["err"] == 0
+    lc_stats = sim.read_lc_stats() if theta is not None else None
     err, od = orc.step(debug=True)
     assert err == 0
     os_ = orc.state()
@@ -64,7 +60,7 @@ def test_full_size_step_matches_oracle(workload):
     dv = np.abs(g_v[still] - os_["v"][still])
     assert dv.max() <= parity.V_TOL, f"v max diff {dv.max()}"
     n_flag = int((act & flagged).sum())
-    print(workload, "active", int(act.sum()), "flagged", n_flag, "compared", still.size)
+    print(label, "active", int(act.sum()), "flagged", n_flag, "compared", still.size)
     assert n_flag <= 0.05 * int(act.sum())
     # invariants at full size: sorted by (lane, x), gap >= 0 up to FP32 rounding, every trip
     # waiting, active or arrived exactly once
@@ -82,6 +78,69 @@ def test_full_size_step_matches_oracle(workload):
     sim.step(1)
     sim.sync()
     assert sim.read_metrics(lanes=False)["err"] == 0
+    return od, os_, act, ok, lc_stats
+
+
+@pytest.mark.parametrize("workload", ["grid1m", "city5m"])
+def test_full_size_step_matches_oracle(workload):
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    sys.path.insert(0, ROOT)
+    import bench
+    net, dem, _ = bench.workload(workload, 3)
+    sim = moss.Sim(P, n_windows=1)           # bench.py's configuration (block 0: default shapes)
+    sim.load_network(net)
+    sim.add_vehicles(dem)
+    sim.step(10)                              # the benchmark's warm-up
+    _full_step_vs_oracle(sim, net, dem, workload)
+
+
+@pytest.fixture(scope="module")
+def small_trained():
+    """A lane-change network trained by the library's kernels on about 2M decisions logged
+    from the small grid's mixed scenarios (the benchmark trains on 50M; parity does not
+    depend on how well the network agrees with the rule)."""
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2405_12520_b300 import learned
+    x, y, _ = learned.collect_batched(learned.mixed_specs(512), P, 3600, 2_000_000)
+    cw, _ = learned.class_weights(y)
+    theta, _ = learned.train(x, y, epochs=2, batch=8192, lr=2e-3, seed=1, class_w=cw)
+    return theta
+
+
+@pytest.mark.parametrize("workload", ["learned1m", "learned5m"])
+def test_full_size_learned_step_matches_oracle(small_trained, workload):
+    """The learned form at the sizes the learned benchmark times (the 1M-vehicle grid with
+    inflow; 5M vehicles near jam density on the same grid), in its launch configuration
+    (the learned decide instance listing candidates, k_learn, the step's graph): one step
+    after the warm-up against the oracle's learned step (R19) over every vehicle, with
+    decisions flagged where R19's flag rule says a rounding could change them."""
+    sys.path.insert(0, ROOT)
+    import bench
+    if workload == "learned5m":
+        net = synth.large_grid_network()
+        dem = synth.place_vehicles(net, 5_000_000, seed=3, min_spacing=6.0)
+    else:
+        net, dem, _ = bench.workload("grid1m", 3)
+    theta = small_trained
+    sim = moss.Sim(P, n_windows=1)
+    sim.load_network(net)
+    sim.add_vehicles(dem)
+    sim.set_lc_model(theta, 0.2)
+    sim.step(10)
+    sim.sync()
+    sim.set_lc_model(theta, 0.2)              # counters of the compared step only
+    od, os_, act, ok, st = _full_step_vs_oracle(sim, net, dem, workload, theta=theta)
+    learned_by_oracle = (od["lc_learn"] == 1) & act
+    n_learn = int(learned_by_oracle.sum())
+    n_net = int((learned_by_oracle & (od["lc_margin"] >= 0.2)).sum())   # the network's own class
+    print(workload, "learned candidates", n_learn, "decided by the network", n_net,
+          "unflagged", int((learned_by_oracle & ok).sum()))
+    # near jam density few vehicles have room to change (61 candidates in this step at 5M)
+    assert n_learn > (1000 if workload == "learned1m" else 30) and n_net > 0.9 * n_learn
+    # the GPU listed the oracle's candidates (up to flagged safety decisions)
+    assert abs(st["candidates"] - n_learn) <= 0.01 * n_learn + 10
 
 
 def test_full_size_batch_step_matches_oracle():

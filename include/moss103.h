@@ -408,6 +408,18 @@ int ms_mlp_train_step(const void *x, const int *y, const int *idx, int batch, fl
 int ms_mlp_grad(const void *x, const int *y, const int *idx, int batch, const float *theta,
                 const float *class_w, float *work, float *grad, void *cuda_stream);
 
+/* The same two calls on the 5th-generation tensor core (tcgen05 MMAs with accumulators in
+   tensor memory, 128 samples per CTA) instead of mma.sync: the same loss, roundings and
+   arguments.  ms_mlp_train_step_tc with loss != NULL also returns MS_ERR_DEVICE (and
+   applies no update) if a wait for the tensor core ran out; the gradient is then
+   incomplete.  Uses about 171 KB of shared memory and all 512 TMEM columns of each SM it
+   runs on while it runs. */
+int ms_mlp_train_step_tc(const void *x, const int *y, const int *idx, int batch, float *theta, float *m,
+                         float *v, int t, float lr, const float *class_w, float *work, float *loss,
+                         void *cuda_stream);
+int ms_mlp_grad_tc(const void *x, const int *y, const int *idx, int batch, const float *theta,
+                   const float *class_w, float *work, float *grad, void *cuda_stream);
+
 /* Class and softmax margin (top1 - top2) of n samples x (device, bf16 [n][16]): device
    outputs cls [n] int, margin [n] float and, if not NULL, the logits [n][3] float.
    theta: device FP32 [5443]; work: device scratch of MS_MLP_WORK_FLOATS floats. */

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmoss103.so")
 SOURCES = ["moss103.cu"]
-HEADERS = ["step_kernels.cuh", "mlp_kernels.cuh", "route_kernels.cuh", "tma.cuh"]
+HEADERS = ["step_kernels.cuh", "mlp_kernels.cuh", "route_kernels.cuh", "tma.cuh", "umma.cuh"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr"]
 

@@ -14,6 +14,8 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 
+#include "umma.cuh"
+
 namespace moss {
 
 constexpr int MLP_IN = 16, MLP_H = 64, MLP_OUT = 3, MLP_OUTP = 16;
@@ -174,6 +176,7 @@ struct TrainArgs {
   float cw[3];              // class weights
   float *grad;              // [MLP_NPARAM] accumulated, unnormalised
   float *stats;             // [0] sum of weights, [1] weighted loss sum
+  unsigned *err;            // k_mlp_train_tc: set when a wait for the tensor core ran out
 };
 
 // dynamic shared memory layout of k_mlp_train (bytes)
@@ -312,6 +315,300 @@ __global__ void __launch_bounds__(TR_ROWS * 2) k_mlp_train(TrainArgs a) {
   }
   __syncthreads();
   for (int k = tid; k < MLP_NPARAM; k += nth) atomicAdd(&a.grad[k], sG[k]);
+}
+
+// ------------------------------------------------------------------------------------
+// training on the 5th-generation tensor core (tcgen05, accumulators in TMEM)
+// ------------------------------------------------------------------------------------
+
+// One CTA of four warps takes 128 samples; thread r owns sample r, whose accumulator rows
+// sit in TMEM lane r (its warp's quarter).  Every product is one 128-row tcgen05.mma chain
+// (BF16 operands in K-major canonical shared-memory tiles, FP32 accumulators in TMEM),
+// issued by thread 0 and completed on one mbarrier:
+//   forward      Z1 = X W1^T, Z2 = H1 W2^T, Z3 = H2 W3^T (W3 padded to 16 outputs);
+//   backward     dH2 = dZ W3, dH1 = dA2 W2 (with transposed copies of W3 and W2);
+//   weights      over the 128 samples (K = 128): [dA2^T ; dA1^T] [H1^T ; X^T ; 1]^T gives
+//                dW2 (rows 0..63, columns 0..63), dW1 (rows 64..127, columns 64..79) and the
+//                hidden bias gradients (column 80: the row of ones), and H2^T dZ gives dW3^T.
+// The roundings are those of the mma.sync kernel: activations and hidden gradients to BF16
+// where they enter a product, the output gradient to BF16 as an operand (its bias gradient
+// from the FP32 values).  Rows that a product computes but nothing reads (padding) may
+// hold any value.  Every wait is bounded; on a timeout the CTA records it in err, waits
+// once more for its MMAs in flight, frees its TMEM and returns.
+constexpr int TC_ROWS = 128;
+constexpr int TC_COLS = 512;   // TMEM columns held (one CTA per SM: its shared memory)
+constexpr unsigned TC_WAIT_LIMIT = 1u << 20;
+// shared memory (byte offsets; K-major canonical tiles, rows x K)
+constexpr int TC_X = 0;                          // X [128 x 16]
+constexpr int TC_W1 = TC_X + 128 * 16 * 2;       // W1 [64 x 16]
+constexpr int TC_W2 = TC_W1 + 64 * 16 * 2;       // W2 [64 x 64]
+constexpr int TC_W2T = TC_W2 + 64 * 64 * 2;      // W2^T [64 x 64]
+constexpr int TC_W3 = TC_W2T + 64 * 64 * 2;      // W3 padded [16 x 64]
+constexpr int TC_W3T = TC_W3 + 16 * 64 * 2;      // (W3 padded)^T [64 x 16]
+constexpr int TC_H1 = TC_W3T + 64 * 16 * 2;      // H1 [128 x 64]
+constexpr int TC_H2 = TC_H1 + 128 * 64 * 2;      // H2 [128 x 64]
+constexpr int TC_DZ = TC_H2 + 128 * 64 * 2;      // dZ padded [128 x 16]
+constexpr int TC_DA2 = TC_DZ + 128 * 16 * 2;     // dA2 [128 x 64]
+constexpr int TC_GAA = TC_DA2 + 128 * 64 * 2;    // [dA2^T ; dA1^T] [128 x 128]
+constexpr int TC_GAB = TC_GAA + 128 * 128 * 2;   // [H1^T ; X^T ; ones ; unused] [96 x 128]
+constexpr int TC_GBA = TC_GAB + 96 * 128 * 2;    // [H2^T ; unused] [128 x 128]
+constexpr int TC_GBB = TC_GBA + 128 * 128 * 2;   // dZ^T padded [16 x 128]
+constexpr int TC_BIAS = TC_GBB + 16 * 128 * 2;   // b1 [64], b2 [64], b3 [16] (FP32)
+constexpr int TC_MISC = TC_BIAS + (64 + 64 + 16) * 4;   // mbarrier, TMEM base, block sums
+constexpr int TC_SMEM = TC_MISC + 64;
+// TMEM columns of the accumulators
+constexpr int TM_Z1 = 0, TM_Z2 = 64, TM_Z3 = 128, TM_DH2 = 160, TM_DH1 = 224, TM_GA = 288, TM_GB = 384;
+static_assert(TM_GB + 16 <= TC_COLS, "TMEM columns");
+
+// 16 FP32 values -> 16 BF16 in two 16-byte words (elements 0..7, 8..15)
+__device__ __forceinline__ void pack16_bf16(const float v[16], uint4 &lo, uint4 &hi) {
+  lo = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+  hi = make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]), pack_bf16(v[12], v[13]), pack_bf16(v[14], v[15]));
+}
+
+__global__ void __launch_bounds__(TC_ROWS) k_mlp_train_tc(TrainArgs a) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int tid = threadIdx.x, warp = tid >> 5, r = tid;
+  const int row = blockIdx.x * TC_ROWS + r;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + TC_MISC);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + TC_MISC + 8);
+  float *sums = reinterpret_cast<float *>(sm + TC_MISC + 16);   // dZ column sums (3), weight, loss
+  float *bias = reinterpret_cast<float *>(sm + TC_BIAS);
+  const uint32_t s0 = smem_u32(sm);
+  auto bfp = [&](int off) { return reinterpret_cast<__nv_bfloat16 *>(sm + off); };
+  auto u4p = [&](int off) { return reinterpret_cast<uint4 *>(sm + off); };
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  if (tid < 5) sums[tid] = 0.f;
+  if (warp == 0) tmem_alloc(tslot, TC_COLS);
+  // the model's BF16 operands (and transposed copies) and FP32 biases
+  const MlpDev &m = *a.model;
+  for (int e = tid; e < MLP_H * MLP_IN; e += TC_ROWS) *bfp(TC_W1 + kmaj_off(e / MLP_IN, e % MLP_IN, MLP_IN)) = m.w1[e];
+  for (int e = tid; e < MLP_H * MLP_H; e += TC_ROWS) {
+    const int o = e / MLP_H, k = e % MLP_H;
+    *bfp(TC_W2 + kmaj_off(o, k, MLP_H)) = m.w2[e];
+    *bfp(TC_W2T + kmaj_off(k, o, MLP_H)) = m.w2[e];
+  }
+  for (int e = tid; e < MLP_OUTP * MLP_H; e += TC_ROWS) {
+    const int c = e / MLP_H, k = e % MLP_H;
+    *bfp(TC_W3 + kmaj_off(c, k, MLP_H)) = m.w3[e];
+    *bfp(TC_W3T + kmaj_off(k, c, MLP_OUTP)) = m.w3[e];
+  }
+  for (int e = tid; e < 2 * MLP_H + MLP_OUTP; e += TC_ROWS)
+    bias[e] = e < MLP_H ? m.b1[e] : (e < 2 * MLP_H ? m.b2[e - MLP_H] : m.b3[e - 2 * MLP_H]);
+  // this thread's sample: features (two 16-byte words), label and class weight
+  uint4 x0 = make_uint4(0, 0, 0, 0), x1 = x0;
+  int yy = 0;
+  float cw = 0.f;
+  if (row < a.batch) {
+    const int smp = a.idx[row];
+    const uint4 *xp = reinterpret_cast<const uint4 *>(a.X + (size_t)smp * MLP_IN);
+    x0 = xp[0];
+    x1 = xp[1];
+    yy = a.y[smp];
+    cw = a.cw[yy];
+  }
+  *u4p(TC_X + kmaj_off(r, 0, MLP_IN)) = x0;
+  *u4p(TC_X + kmaj_off(r, 8, MLP_IN)) = x1;
+  {
+    const __nv_bfloat16 *xa = reinterpret_cast<const __nv_bfloat16 *>(&x0);
+    const __nv_bfloat16 *xb = reinterpret_cast<const __nv_bfloat16 *>(&x1);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      *bfp(TC_GAB + kmaj_off(64 + j, r, TC_ROWS)) = xa[j];
+      *bfp(TC_GAB + kmaj_off(72 + j, r, TC_ROWS)) = xb[j];
+    }
+    *bfp(TC_GAB + kmaj_off(80, r, TC_ROWS)) = __float2bfloat16_rn(1.f);
+  }
+
+  uint32_t tm = 0;      // TMEM base (read after the first barrier)
+  unsigned phase = 0;   // completions of the barrier so far
+  // operands written -> one chain of MMAs -> its accumulators readable; false on a timeout
+  // (the same answer in every thread)
+  auto stage = [&](auto issue) -> bool {
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    tm = *tslot;
+    if (tid == 0) {
+      issue(tm);
+      umma_commit(bar);
+    }
+    __syncwarp();
+    const bool done = mbar_wait(bar, phase & 1u, TC_WAIT_LIMIT);
+    tc_fence_after();
+    if (__syncthreads_or(!done)) {
+      if (tid == 0) atomicOr(a.err, 1u);
+      mbar_wait(bar, phase & 1u, TC_WAIT_LIMIT);   // the MMAs in flight, once more
+      return false;
+    }
+    ++phase;
+    return true;
+  };
+  auto finish = [&]() {
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tm, TC_COLS);
+  };
+  const uint32_t lane = (uint32_t)(warp * 32) << 16;   // this warp's TMEM lanes
+  const uint32_t I64 = idesc_bf16_f32(128, 64), I16 = idesc_bf16_f32(128, 16), I96 = idesc_bf16_f32(128, 96);
+  float v[16];
+  uint4 lo, hi;
+
+  // layer 1
+  if (!stage([&](uint32_t t) {
+        umma_bf16(t + TM_Z1, kmaj_desc(s0 + TC_X, MLP_IN), kmaj_desc(s0 + TC_W1, MLP_IN), I64, 0);
+      })) {
+    finish();
+    return;
+  }
+  uint64_t mask1 = 0, mask2 = 0;   // ReLU masks of the BF16 activations
+  for (int c = 0; c < MLP_H; c += 16) {
+    tmem_ld16(tm + lane + TM_Z1 + c, v);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      v[q] = __bfloat162float(__float2bfloat16_rn(fmaxf(v[q] + bias[c + q], 0.f)));
+      if (v[q] > 0.f) mask1 |= 1ull << (c + q);
+      *bfp(TC_GAB + kmaj_off(c + q, r, TC_ROWS)) = __float2bfloat16_rn(v[q]);
+    }
+    pack16_bf16(v, lo, hi);
+    *u4p(TC_H1 + kmaj_off(r, c, MLP_H)) = lo;
+    *u4p(TC_H1 + kmaj_off(r, c + 8, MLP_H)) = hi;
+  }
+  // layer 2
+  if (!stage([&](uint32_t t) {
+        for (int ks = 0; ks < MLP_H / 16; ++ks)
+          umma_bf16(t + TM_Z2, kmaj_desc(s0 + TC_H1 + 256 * ks, MLP_H), kmaj_desc(s0 + TC_W2 + 256 * ks, MLP_H), I64,
+                    ks);
+      })) {
+    finish();
+    return;
+  }
+  for (int c = 0; c < MLP_H; c += 16) {
+    tmem_ld16(tm + lane + TM_Z2 + c, v);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      v[q] = __bfloat162float(__float2bfloat16_rn(fmaxf(v[q] + bias[MLP_H + c + q], 0.f)));
+      if (v[q] > 0.f) mask2 |= 1ull << (c + q);
+      *bfp(TC_GBA + kmaj_off(c + q, r, TC_ROWS)) = __float2bfloat16_rn(v[q]);
+    }
+    pack16_bf16(v, lo, hi);
+    *u4p(TC_H2 + kmaj_off(r, c, MLP_H)) = lo;
+    *u4p(TC_H2 + kmaj_off(r, c + 8, MLP_H)) = hi;
+  }
+  // layer 3, softmax cross-entropy gradient (class-weighted, not yet normalised)
+  if (!stage([&](uint32_t t) {
+        for (int ks = 0; ks < MLP_H / 16; ++ks)
+          umma_bf16(t + TM_Z3, kmaj_desc(s0 + TC_H2 + 256 * ks, MLP_H), kmaj_desc(s0 + TC_W3 + 256 * ks, MLP_H), I16,
+                    ks);
+      })) {
+    finish();
+    return;
+  }
+  tmem_ld16(tm + lane + TM_Z3, v);
+  float d[MLP_OUT] = {0.f, 0.f, 0.f};
+  float wsum = 0.f, lsum = 0.f;
+  if (row < a.batch) {
+    const float z0 = v[0] + bias[2 * MLP_H], z1 = v[1] + bias[2 * MLP_H + 1], z2 = v[2] + bias[2 * MLP_H + 2];
+    const float mx = fmaxf(z0, fmaxf(z1, z2));
+    const float e0 = __expf(z0 - mx), e1 = __expf(z1 - mx), e2 = __expf(z2 - mx);
+    const float se = e0 + e1 + e2;
+    d[0] = cw * (e0 / se - (yy == 0));
+    d[1] = cw * (e1 / se - (yy == 1));
+    d[2] = cw * (e2 / se - (yy == 2));
+    const float zy = yy == 0 ? z0 : (yy == 1 ? z1 : z2);
+    wsum = cw;
+    lsum = cw * (logf(se) + mx - zy);
+  }
+  {
+    float red[5] = {d[0], d[1], d[2], wsum, lsum};
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      for (int o = 16; o > 0; o >>= 1) red[q] += __shfl_xor_sync(0xffffffffu, red[q], o);
+      if ((tid & 31) == 0) atomicAdd(&sums[q], red[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    v[q] = q < MLP_OUT ? d[q] : 0.f;
+    *bfp(TC_GBB + kmaj_off(q, r, TC_ROWS)) = __float2bfloat16_rn(v[q]);
+  }
+  pack16_bf16(v, lo, hi);
+  *u4p(TC_DZ + kmaj_off(r, 0, MLP_OUTP)) = lo;
+  *u4p(TC_DZ + kmaj_off(r, 8, MLP_OUTP)) = hi;
+  // dH2 = dZ W3
+  if (!stage([&](uint32_t t) {
+        umma_bf16(t + TM_DH2, kmaj_desc(s0 + TC_DZ, MLP_OUTP), kmaj_desc(s0 + TC_W3T, MLP_OUTP), I64, 0);
+      })) {
+    finish();
+    return;
+  }
+  for (int c = 0; c < MLP_H; c += 16) {
+    tmem_ld16(tm + lane + TM_DH2 + c, v);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      v[q] = (mask2 >> (c + q)) & 1ull ? v[q] : 0.f;
+      *bfp(TC_GAA + kmaj_off(c + q, r, TC_ROWS)) = __float2bfloat16_rn(v[q]);
+    }
+    pack16_bf16(v, lo, hi);
+    *u4p(TC_DA2 + kmaj_off(r, c, MLP_H)) = lo;
+    *u4p(TC_DA2 + kmaj_off(r, c + 8, MLP_H)) = hi;
+  }
+  // dH1 = dA2 W2
+  if (!stage([&](uint32_t t) {
+        for (int ks = 0; ks < MLP_H / 16; ++ks)
+          umma_bf16(t + TM_DH1, kmaj_desc(s0 + TC_DA2 + 256 * ks, MLP_H), kmaj_desc(s0 + TC_W2T + 256 * ks, MLP_H),
+                    I64, ks);
+      })) {
+    finish();
+    return;
+  }
+  for (int c = 0; c < MLP_H; c += 16) {
+    tmem_ld16(tm + lane + TM_DH1 + c, v);
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      *bfp(TC_GAA + kmaj_off(MLP_H + c + q, r, TC_ROWS)) =
+          __float2bfloat16_rn((mask1 >> (c + q)) & 1ull ? v[q] : 0.f);
+  }
+  // weight and hidden-bias gradients over the 128 samples
+  if (!stage([&](uint32_t t) {
+        for (int ks = 0; ks < TC_ROWS / 16; ++ks)
+          umma_bf16(t + TM_GA, kmaj_desc(s0 + TC_GAA + 256 * ks, TC_ROWS), kmaj_desc(s0 + TC_GAB + 256 * ks, TC_ROWS),
+                    I96, ks);
+        for (int ks = 0; ks < TC_ROWS / 16; ++ks)
+          umma_bf16(t + TM_GB, kmaj_desc(s0 + TC_GBA + 256 * ks, TC_ROWS), kmaj_desc(s0 + TC_GBB + 256 * ks, TC_ROWS),
+                    I16, ks);
+      })) {
+    finish();
+    return;
+  }
+  if (warp < 2) {   // rows 0..63: dW2 row r, b2, dW3 column r
+    for (int c = 0; c < MLP_H; c += 16) {
+      tmem_ld16(tm + lane + TM_GA + c, v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) atomicAdd(&a.grad[OFF_W2 + r * MLP_H + c + q], v[q]);
+    }
+    tmem_ld16(tm + lane + TM_GA + 80, v);
+    atomicAdd(&a.grad[OFF_B2 + r], v[0]);
+    tmem_ld16(tm + lane + TM_GB, v);
+#pragma unroll
+    for (int q = 0; q < MLP_OUT; ++q) atomicAdd(&a.grad[OFF_W3 + q * MLP_H + r], v[q]);
+  } else {   // rows 64..127: dW1 row r - 64, b1
+    const int o = r - MLP_H;
+    tmem_ld16(tm + lane + TM_GA + 64, v);
+#pragma unroll
+    for (int q = 0; q < MLP_IN; ++q) atomicAdd(&a.grad[OFF_W1 + o * MLP_IN + q], v[q]);
+    tmem_ld16(tm + lane + TM_GA + 80, v);
+    atomicAdd(&a.grad[OFF_B1 + o], v[0]);
+  }
+  __syncthreads();
+  if (tid < MLP_OUT) atomicAdd(&a.grad[OFF_B3 + tid], sums[tid]);
+  if (tid == MLP_OUT) atomicAdd(&a.stats[0], sums[3]);
+  if (tid == MLP_OUT + 1) atomicAdd(&a.stats[1], sums[4]);
+  finish();
 }
 
 // FP32 master parameters -> BF16 operand model

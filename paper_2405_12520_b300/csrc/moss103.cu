@@ -2083,8 +2083,10 @@ int ms_read_lc_stats(void *sim, int64_t *out12) {
 }
 
 namespace {
+// one gradient accumulation over the minibatch into work (gradient, then {weight sum, loss
+// sum, error bits}); tc: the tcgen05 kernel (128 samples per CTA) instead of mma.sync
 int mlp_run(const void *x, const int *y, const int *idx, int batch, const float *theta, const float *class_w,
-            float *work, cudaStream_t st) {
+            float *work, cudaStream_t st, bool tc) {
   Sim *s = nullptr;
   static_assert(MLP_NPARAM == MS_MLP_NPARAM, "parameter count");
   static_assert(MLP_NPARAM + 4 + (int)(sizeof(MlpDev) / 4) <= MS_MLP_WORK_FLOATS, "work size");
@@ -2094,6 +2096,7 @@ int mlp_run(const void *x, const int *y, const int *idx, int batch, const float 
   static bool attr = false;
   if (!attr) {
     CK(cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, TR_SMEM));
+    CK(cudaFuncSetAttribute(k_mlp_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
     attr = true;
   }
   k_mlp_pack<<<8, 256, 0, st>>>(theta, model);
@@ -2109,23 +2112,29 @@ int mlp_run(const void *x, const int *y, const int *idx, int batch, const float 
   a.cw[2] = class_w[2];
   a.grad = grad;
   a.stats = stats;
-  k_mlp_train<<<(batch + TR_ROWS - 1) / TR_ROWS, TR_ROWS * 2, TR_SMEM, st>>>(a);
+  a.err = reinterpret_cast<unsigned *>(stats + 2);
+  if (tc)
+    k_mlp_train_tc<<<(batch + TC_ROWS - 1) / TC_ROWS, TC_ROWS, TC_SMEM, st>>>(a);
+  else
+    k_mlp_train<<<(batch + TR_ROWS - 1) / TR_ROWS, TR_ROWS * 2, TR_SMEM, st>>>(a);
   CK(cudaGetLastError());
   return MS_OK;
 }
-}  // namespace
 
-int ms_mlp_train_step(const void *x, const int *y, const int *idx, int batch, float *theta, float *m, float *v,
-                      int t, float lr, const float *class_w, float *work, float *loss, void *cuda_stream) {
+int mlp_train_step(const void *x, const int *y, const int *idx, int batch, float *theta, float *m, float *v, int t,
+                   float lr, const float *class_w, float *work, float *loss, void *cuda_stream, bool tc) {
   Sim *s = nullptr;
   if (!m || !v || t < 1) return MS_ERR_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  int r = mlp_run(x, y, idx, batch, theta, class_w, work, st);
+  int r = mlp_run(x, y, idx, batch, theta, class_w, work, st, tc);
   if (r) return r;
   if (loss) {
-    float h[2];
+    float h[3];
     CK(cudaMemcpyAsync(h, work + MLP_NPARAM, sizeof(h), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    unsigned e;
+    std::memcpy(&e, &h[2], sizeof(e));
+    if (e) return MS_ERR_DEVICE;   // a tensor-core wait ran out: the gradient is incomplete
     *loss = h[0] > 0.f ? h[1] / h[0] : 0.f;
   }
   k_mlp_adam<<<8, 256, 0, st>>>(theta, m, v, work, work + MLP_NPARAM, t, lr, 0.9f, 0.999f, 1e-8f);
@@ -2133,16 +2142,37 @@ int ms_mlp_train_step(const void *x, const int *y, const int *idx, int batch, fl
   return MS_OK;
 }
 
-int ms_mlp_grad(const void *x, const int *y, const int *idx, int batch, const float *theta, const float *class_w,
-                float *work, float *grad, void *cuda_stream) {
+int mlp_grad(const void *x, const int *y, const int *idx, int batch, const float *theta, const float *class_w,
+             float *work, float *grad, void *cuda_stream, bool tc) {
   Sim *s = nullptr;
   if (!grad) return MS_ERR_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  int r = mlp_run(x, y, idx, batch, theta, class_w, work, st);
+  int r = mlp_run(x, y, idx, batch, theta, class_w, work, st, tc);
   if (r) return r;
   k_mlp_scale<<<8, 256, 0, st>>>(work, work + MLP_NPARAM, grad);
   CK(cudaGetLastError());
   return MS_OK;
+}
+}  // namespace
+
+int ms_mlp_train_step(const void *x, const int *y, const int *idx, int batch, float *theta, float *m, float *v,
+                      int t, float lr, const float *class_w, float *work, float *loss, void *cuda_stream) {
+  return mlp_train_step(x, y, idx, batch, theta, m, v, t, lr, class_w, work, loss, cuda_stream, false);
+}
+
+int ms_mlp_grad(const void *x, const int *y, const int *idx, int batch, const float *theta, const float *class_w,
+                float *work, float *grad, void *cuda_stream) {
+  return mlp_grad(x, y, idx, batch, theta, class_w, work, grad, cuda_stream, false);
+}
+
+int ms_mlp_train_step_tc(const void *x, const int *y, const int *idx, int batch, float *theta, float *m, float *v,
+                         int t, float lr, const float *class_w, float *work, float *loss, void *cuda_stream) {
+  return mlp_train_step(x, y, idx, batch, theta, m, v, t, lr, class_w, work, loss, cuda_stream, true);
+}
+
+int ms_mlp_grad_tc(const void *x, const int *y, const int *idx, int batch, const float *theta, const float *class_w,
+                   float *work, float *grad, void *cuda_stream) {
+  return mlp_grad(x, y, idx, batch, theta, class_w, work, grad, cuda_stream, true);
 }
 
 int ms_mlp_predict(const void *x, int n, const float *theta, float *work, int *cls, float *margin, float *logits,

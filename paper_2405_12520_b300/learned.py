@@ -115,9 +115,9 @@ def init_params(seed: int = 0) -> np.ndarray:
 
 
 def train(x, y, epochs: int = 3, batch: int = 8192, lr: float = 1e-3, seed: int = 0, class_w=None,
-          theta0=None, log_every: int = 0):
+          theta0=None, log_every: int = 0, tc: bool = False):
     """Adam on class-weighted cross-entropy with the library's GPU kernels; returns the
-    parameters (numpy float32) and a training log."""
+    parameters (numpy float32) and a training log.  tc: the tcgen05 training kernel."""
     import torch
     dev = x.device
     theta = torch.tensor(init_params(seed) if theta0 is None else theta0, device=dev)
@@ -137,7 +137,8 @@ def train(x, y, epochs: int = 3, batch: int = 8192, lr: float = 1e-3, seed: int 
         for b0 in range(0, n, batch):
             t += 1
             want = log_every and t % log_every == 0
-            loss = moss.mlp_train_step(x, y, perm[b0:b0 + batch], theta, m, v, t, lr, class_w, work, want_loss=want)
+            loss = moss.mlp_train_step(x, y, perm[b0:b0 + batch], theta, m, v, t, lr, class_w, work, want_loss=want,
+                                       tc=tc)
             if want:
                 log.append((t, loss))
     torch.cuda.synchronize()

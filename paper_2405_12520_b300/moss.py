@@ -21,8 +21,8 @@ SYMBOLS = ("ms_create", "ms_load_network", "ms_add_vehicles", "ms_step", "ms_ste
            "ms_set_lc_log", "ms_set_lc_model", "ms_set_lane_limits", "ms_set_lane_links", "ms_route_trips",
            "ms_sample_trips", "ms_sample_trips_radiation",
            "ms_read_lc_stats",
-           "ms_mlp_train_step",
-           "ms_mlp_grad",
+           "ms_mlp_train_step", "ms_mlp_train_step_tc",
+           "ms_mlp_grad", "ms_mlp_grad_tc",
            "ms_mlp_predict",
            "ms_sync", "ms_read_state", "ms_read_state_async", "ms_read_wait",
            "ms_write_state", "ms_read_metrics", "ms_read_debug", "ms_last_error", "ms_destroy")
@@ -101,7 +101,9 @@ def load():
         lib.ms_sample_trips_radiation.argtypes = [vp, C.c_int, vp, vp, C.c_int, C.c_int, C.c_uint64, vp, vp, vp]
         lib.ms_read_lc_stats.argtypes = [vp, vp]
         lib.ms_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, C.c_int, C.c_float, vp, vp, vp, vp]
+        lib.ms_mlp_train_step_tc.argtypes = lib.ms_mlp_train_step.argtypes
         lib.ms_mlp_grad.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, vp, vp]
+        lib.ms_mlp_grad_tc.argtypes = lib.ms_mlp_grad.argtypes
         lib.ms_mlp_predict.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp]
         lib.ms_sync.argtypes = [vp]
         lib.ms_read_state.argtypes = [vp, C.POINTER(ms_state), C.c_int]
@@ -136,26 +138,29 @@ def _st(stream):
     return C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
 
 
-def mlp_train_step(x, y, idx, theta, m, v, t, lr, class_w, work, stream=None, want_loss=False):
+def mlp_train_step(x, y, idx, theta, m, v, t, lr, class_w, work, stream=None, want_loss=False, tc=False):
     """One Adam step of the surrogate on device tensors (x bf16 [n,16], y int32, idx int32,
-    theta/m/v float32 [5443], work float32 [MLP_WORK_FLOATS]); returns the loss if asked."""
+    theta/m/v float32 [5443], work float32 [MLP_WORK_FLOATS]); returns the loss if asked.
+    tc: on the tcgen05 tensor cores (ms_mlp_train_step_tc) instead of mma.sync."""
     lib = load()
+    name = "ms_mlp_train_step_tc" if tc else "ms_mlp_train_step"
     cw = np.ascontiguousarray(class_w, np.float32)
     loss = C.c_float(0.0)
-    rc = lib.ms_mlp_train_step(_dp(x), _dp(y), _dp(idx), int(idx.numel()), _dp(theta), _dp(m), _dp(v), int(t),
-                               float(lr), _p(cw), _dp(work), C.byref(loss) if want_loss else None, _st(stream))
+    rc = getattr(lib, name)(_dp(x), _dp(y), _dp(idx), int(idx.numel()), _dp(theta), _dp(m), _dp(v), int(t),
+                            float(lr), _p(cw), _dp(work), C.byref(loss) if want_loss else None, _st(stream))
     if rc:
-        raise MossError(rc, "ms_mlp_train_step")
+        raise MossError(rc, name)
     return loss.value if want_loss else None
 
 
-def mlp_grad(x, y, idx, theta, class_w, work, grad, stream=None):
+def mlp_grad(x, y, idx, theta, class_w, work, grad, stream=None, tc=False):
     lib = load()
+    name = "ms_mlp_grad_tc" if tc else "ms_mlp_grad"
     cw = np.ascontiguousarray(class_w, np.float32)
-    rc = lib.ms_mlp_grad(_dp(x), _dp(y), _dp(idx), int(idx.numel()), _dp(theta), _p(cw), _dp(work), _dp(grad),
-                         _st(stream))
+    rc = getattr(lib, name)(_dp(x), _dp(y), _dp(idx), int(idx.numel()), _dp(theta), _p(cw), _dp(work), _dp(grad),
+                            _st(stream))
     if rc:
-        raise MossError(rc, "ms_mlp_grad")
+        raise MossError(rc, name)
 
 
 def mlp_predict(x, theta, work, cls, margin, stream=None, logits=None):

@@ -579,6 +579,29 @@ def run_batch(args):
         print(json.dumps(line), flush=True)
 
 
+def mlp_grad_us(x, y, cw, batch=8192, reps=200):
+    """Device time of one minibatch gradient (operand packing, clearing, the training kernel,
+    scaling) with each training kernel, CUDA events over reps calls after a warm-up."""
+    import torch
+    from paper_2405_12520_b300 import learned, moss
+    th = torch.tensor(learned.init_params(3), device="cuda")
+    work = torch.zeros(moss.MLP_WORK_FLOATS, device="cuda")
+    g = torch.zeros_like(th)
+    idx = torch.arange(min(batch, x.shape[0]), dtype=torch.int32, device="cuda")
+    out = {}
+    for name, tc in (("tcgen05", True), ("mma_sync", False)):
+        for _ in range(5):
+            moss.mlp_grad(x, y, idx, th, cw, work, g, tc=tc)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            moss.mlp_grad(x, y, idx, th, cw, work, g, tc=tc)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = round(1e3 * e0.elapsed_time(e1) / reps, 2)
+    return out
+
+
 def run_learned(args):
     """Learned lane-change surrogate on the large grid: trained on decisions logged from
     small-grid runs of the rule-based step, then timed against the rule-based step on the
@@ -597,7 +620,10 @@ def run_learned(args):
                                          args.train_samples)
     t_collect = time.perf_counter() - t0
     cw, cnt = learned.class_weights(y)
+    grad_us = mlp_grad_us(x, y, cw)   # one gradient call of each kernel (also their first launches)
     theta, info = learned.train(x, y, epochs=args.train_epochs, batch=8192, lr=2e-3, seed=1, class_w=cw)
+    # the same training on the mma.sync kernel
+    _, info_mma = learned.train(x, y, epochs=args.train_epochs, batch=8192, lr=2e-3, seed=1, class_w=cw, tc=False)
     if args.workload == "learned5m":   # the same network at 5M vehicles (near jam density)
         net = synth.large_grid_network()
         dem = synth.place_vehicles(net, 5_000_000, seed=args.seed, min_spacing=6.0)
@@ -702,7 +728,10 @@ def run_learned(args):
                                            "15% 2,900 placed + 300 trips (jam)",
                              "collect_s": round(t_collect, 1), "epochs": args.train_epochs,
                              "adam_steps": info["steps"], "batch": 8192,
-                             "train_s": round(info["seconds"], 2), "class_w": info["class_w"]}},
+                             "train_s": round(info["seconds"], 2), "class_w": info["class_w"],
+                             "kernel": "tcgen05 (k_mlp_train_tc)",
+                             "train_s_mma_sync": round(info_mma["seconds"], 2),
+                             "grad_call_us": grad_us}},
         "learned": L, "rule": out["rule"],
         "learned_vs_rule": L["value"] / out["rule"]["value"],
         "mean_speed_rel_diff": abs(L["mean_speed"] - out["rule"]["mean_speed"]) / out["rule"]["mean_speed"],

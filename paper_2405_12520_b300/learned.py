@@ -115,9 +115,10 @@ def init_params(seed: int = 0) -> np.ndarray:
 
 
 def train(x, y, epochs: int = 3, batch: int = 8192, lr: float = 1e-3, seed: int = 0, class_w=None,
-          theta0=None, log_every: int = 0, tc: bool = False):
+          theta0=None, log_every: int = 0, tc: bool = True):
     """Adam on class-weighted cross-entropy with the library's GPU kernels; returns the
-    parameters (numpy float32) and a training log.  tc: the tcgen05 training kernel."""
+    parameters (numpy float32) and a training log.  tc: the tcgen05 training kernel (else
+    the mma.sync one)."""
     import torch
     dev = x.device
     theta = torch.tensor(init_params(seed) if theta0 is None else theta0, device=dev)

@@ -26,7 +26,7 @@ def data(torch_mod):
     and a network trained on them (the mma.sync kernel)."""
     x, y, _ = learned.collect_batched(learned.mixed_specs(256), P, 3600, 500_000)
     cw, _ = learned.class_weights(y)
-    theta, _ = learned.train(x, y, epochs=2, batch=8192, lr=2e-3, seed=1, class_w=cw)
+    theta, _ = learned.train(x, y, epochs=2, batch=8192, lr=2e-3, seed=1, class_w=cw, tc=False)
     return x, y, cw, theta
 
 

@@ -871,6 +871,7 @@ int ms_add_vehicles(void *sim, const ms_vehicles *veh) {
   }
   s->h_qoff.assign(s->n_lanes + 1, 0);
   for (int l = 0; l < s->n_lanes; ++l) s->h_qoff[l + 1] = s->h_qoff[l] + qcnt[l];
+  s->P.fifo = s->h_qoff[s->n_lanes] > 0 ? 1 : 0;
   s->h_qtrip.assign(std::max(1, s->h_qoff[s->n_lanes]), 0);
   {
     std::vector<int> ord;

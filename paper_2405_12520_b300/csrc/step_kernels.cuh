@@ -75,6 +75,7 @@ struct DevParams {
   int signal_mode;       // 0 fixed-time plans, 1 max pressure
   int mp_interval;       // steps between max-pressure decisions
   int lane_mods;         // some lane has a speed limit or is closed
+  int fifo;              // some trip enters through a departure queue
 };
 
 // Link plan of a route entry r (edge e = routes[r]), one 64-bit word built at load time:
@@ -1081,6 +1082,25 @@ __device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long 
 // the aggregates visible; a single launch that waited on its predecessors' flags spent
 // several microseconds before those stores became visible to the waiting blocks.
 // TH threads per tile (LANE_TILE / TH lanes each): the autotuner picks among 128, 256, 512.
+// Whether the due head of lane l's departure FIFO enters this step: room behind the lane's
+// tail (d: its lane record) and behind every arrival (amk: their rearmost key).  fl: a
+// margin within the flag distance (debug records).
+__device__ __forceinline__ int lane_entry(const StepArgs &a, int4 d, int amk, int &fl) {
+  const float room_need = a.P.L + a.P.s0;
+  bool room = true;
+  if (d.y > 0) {
+    float m = (__int_as_float(d.z) - a.P.L) - room_need;
+    mark(fl, m);
+    room = m >= 0.f;
+  }
+  if (amk != AMIN_NONE) {
+    float m = unfkey(amk) - room_need;
+    mark(fl, m);
+    if (m < 0.f) room = false;
+  }
+  return room ? 1 : 0;
+}
+
 template <int PASS, int TH = LANE_THREADS>
 __global__ void __launch_bounds__(TH, LANE_TILE / TH) k_lanes_t(StepArgs a) {
   constexpr int LANE_THREADS = TH, LANE_ITEMS = LANE_TILE / TH, LANE_WARPS = TH / 32;
@@ -1095,10 +1115,56 @@ __global__ void __launch_bounds__(TH, LANE_TILE / TH) k_lanes_t(StepArgs a) {
   const int4 *dyn = a.dyn[p];
   int4 *ndyn = a.dyn[p ^ 1];
   const int nlanes = a.P.n_lanes;
-  const float room_need = a.P.L + a.P.s0;
   const int lbase = tile * LANE_TILE + threadIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // pass 1: the predecessors' aggregates are loaded first, with the lane records
+  if (PASS == 0 && !a.P.fifo) {
+    // without departure queues the tile's aggregate {new vehicles, arrivals} needs only the
+    // arrival words: its lanes hold the vehicles between two lane starts (every lane's
+    // start is the count of the vehicles before it), to which the arrivals are added and
+    // the leavers taken away (with queues the general path below also tests the entries)
+    long long dv = 0;
+    unsigned na = 0;
+    int first0 = 0, first1 = 0;   // the tile's lane starts, loaded with the lanes' words
+    if (threadIdx.x == 0) {
+      const int l0 = tile * LANE_TILE, l1 = l0 + LANE_TILE;
+      first0 = dyn[l0].x;
+      first1 = l1 < nlanes ? dyn[l1].x : a.ctrl->n_active[p];
+    }
+#pragma unroll
+    for (int k = 0; k < LANE_ITEMS; ++k) {
+      const int l = lbase + k * LANE_THREADS;
+      if (l < nlanes) {
+        const int w = a.arr_cnt[l];
+        const int arr = w & (LEAVE_ONE - 1);
+        dv += arr - (w >> 16);
+        na += arr;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      dv += __shfl_xor_sync(0xffffffffu, dv, o);
+      na += __shfl_xor_sync(0xffffffffu, na, o);
+    }
+    __shared__ long long s_dv[LANE_WARPS];
+    __shared__ unsigned s_na[LANE_WARPS];
+    if (lane == 0) {
+      s_dv[warp] = dv;
+      s_na[warp] = na;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long cnt = first1 - first0;
+      unsigned arr = 0;
+      for (int w2 = 0; w2 < LANE_WARPS; ++w2) {
+        cnt += s_dv[w2];
+        arr += s_na[w2];
+      }
+      a.tile_agg[tile] = ((unsigned long long)cnt << 32) | arr;   // read by pass 1
+    }
+    return;
+  }
+  // the general path (both passes): per-lane counts and their scan over the tile; pass 1
+  // loads the predecessors' aggregates first, with the lane records
   unsigned long long part = 0;
   if (PASS == 1)
     for (int j = threadIdx.x; j < tile; j += LANE_THREADS) part += a.tile_agg[j];
@@ -1133,24 +1199,13 @@ __global__ void __launch_bounds__(TH, LANE_TILE / TH) k_lanes_t(StepArgs a) {
       if (PASS == 1) {   // the head's record is read after the scan: start bringing it in now
         asm volatile("prefetch.global.L1 [%0];" ::"l"(a.q_ent + qhd[k].x));
         asm volatile("prefetch.global.L1 [%0];" ::"l"(a.q_ent2 + qhd[k].x));
-      }   // the FIFO's head is due: room behind the lane's tail (its
-      int fl = 0;          // position is in the lane record) and behind every arrival
-      bool room = true;
-      if (d[k].y > 0) {
-        float m = (__int_as_float(d[k].z) - a.P.L) - room_need;
-        mark(fl, m);
-        room = m >= 0.f;
       }
-      if (amk[k] != AMIN_NONE) {
-        float m = unfkey(amk[k]) - room_need;
-        mark(fl, m);
-        if (m < 0.f) room = false;
-      }
+      int fl = 0;
+      ins[k] = lane_entry(a, d[k], amk[k], fl);
       if (PASS == 1 && a.P.debug) {
         const int l = lbase + k * LANE_THREADS;
         if (fl || a.dbg.arr_flag[l]) a.dbg.trip_flag[a.q_trip[qhd[k].x]] = t + 1;
       }
-      ins[k] = room ? 1 : 0;
     }
     cnt[k] = d[k].y - leavers + arr[k] + ins[k];
     val[k] = ((unsigned long long)cnt[k] << 32) | (unsigned)(arr[k] + ins[k]);

@@ -778,7 +778,7 @@ __device__ __forceinline__ int vehicle_finish(const StepArgs &a, const Soa &S, i
 template <bool DBG>
 __device__ __forceinline__ void arrival_records(const StepArgs &a, int i, const Upd &u, const VCtx &c) {
   atomicAdd(&a.arr_cnt[u.lane], 1);
-  atomicMin(&a.amin[u.lane], fkey(u.x - a.P.L));
+  if (a.P.fifo) atomicMin(&a.amin[u.lane], fkey(u.x - a.P.L));   // read only by the entry test
   if (u.kind == U_CHANGE) a.res_pos[i] = make_int2(u.lc.tfirst, u.lc.pos);
   if (u.rp == c.rp) {
     const LaneInfo ln = a.li[u.lane];
@@ -1180,8 +1180,13 @@ __global__ void __launch_bounds__(TH, LANE_TILE / TH) k_lanes_t(StepArgs a) {
       const int w = a.arr_cnt[l];
       arr[k] = w & (LEAVE_ONE - 1);
       lv[k] = w >> 16;
-      amk[k] = a.amin[l];
-      qhd[k] = a.q_hd[l];
+      if (a.P.fifo) {   // queue heads and rearmost arrivals matter to entries only
+        amk[k] = a.amin[l];
+        qhd[k] = a.q_hd[l];
+      } else {
+        amk[k] = AMIN_NONE;
+        qhd[k] = make_int2(0, 0x7fffffff);
+      }
     } else {
       d[k] = make_int4(0, 0, 0, 0);
       arr[k] = lv[k] = 0;

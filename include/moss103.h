@@ -412,8 +412,8 @@ int ms_mlp_grad(const void *x, const int *y, const int *idx, int batch, const fl
    tensor memory, 128 samples per CTA) instead of mma.sync: the same loss, roundings and
    arguments.  ms_mlp_train_step_tc with loss != NULL also returns MS_ERR_DEVICE (and
    applies no update) if a wait for the tensor core ran out; the gradient is then
-   incomplete.  Uses about 171 KB of shared memory and all 512 TMEM columns of each SM it
-   runs on while it runs. */
+   incomplete.  The training kernel packs its own BF16 operands from theta.  Uses about
+   171 KB of shared memory and all 512 TMEM columns of each SM it runs on while it runs. */
 int ms_mlp_train_step_tc(const void *x, const int *y, const int *idx, int batch, float *theta, float *m,
                          float *v, int t, float lr, const float *class_w, float *work, float *loss,
                          void *cuda_stream);

@@ -177,7 +177,21 @@ struct TrainArgs {
   float *grad;              // [MLP_NPARAM] accumulated, unnormalised
   float *stats;             // [0] sum of weights, [1] weighted loss sum
   unsigned *err;            // k_mlp_train_tc: set when a wait for the tensor core ran out
+  const float *theta;       // k_mlp_train_tc: FP32 parameters, from which it packs its operands
 };
+
+// One Adam step (Kingma & Ba 2015) of parameter k on the accumulated gradient scaled by
+// inv; clears the accumulator
+__device__ __forceinline__ void adam_one(int k, float *theta, float *m, float *v, float *grad, float inv, float c1,
+                                         float c2, float lr, float beta1, float beta2, float eps) {
+  const float g = __ldcg(grad + k) * inv;   // summed by the training kernel's atomics (in L2)
+  const float mk = beta1 * m[k] + (1.f - beta1) * g;
+  const float vk = beta2 * v[k] + (1.f - beta2) * g * g;
+  m[k] = mk;
+  v[k] = vk;
+  theta[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+  grad[k] = 0.f;
+}
 
 // dynamic shared memory layout of k_mlp_train (bytes)
 constexpr int TR_SMEM = (int)sizeof(MlpDev) + 2 * (TR_ROWS * MLP_IN + 4 * TR_ROWS * MLP_H + TR_ROWS * MLP_OUTP) +
@@ -383,21 +397,57 @@ __global__ void __launch_bounds__(TC_ROWS) k_mlp_train_tc(TrainArgs a) {
   }
   if (tid < 5) sums[tid] = 0.f;
   if (warp == 0) tmem_alloc(tslot, TC_COLS);
-  // the model's BF16 operands (and transposed copies) and FP32 biases
-  const MlpDev &m = *a.model;
-  for (int e = tid; e < MLP_H * MLP_IN; e += TC_ROWS) *bfp(TC_W1 + kmaj_off(e / MLP_IN, e % MLP_IN, MLP_IN)) = m.w1[e];
-  for (int e = tid; e < MLP_H * MLP_H; e += TC_ROWS) {
-    const int o = e / MLP_H, k = e % MLP_H;
-    *bfp(TC_W2 + kmaj_off(o, k, MLP_H)) = m.w2[e];
-    *bfp(TC_W2T + kmaj_off(k, o, MLP_H)) = m.w2[e];
+  // the model's BF16 operands (and transposed copies) and FP32 biases, packed from the FP32
+  // parameters as k_mlp_pack packs them: every 16-byte word of the parameter vector loaded
+  // at once (one round trip), then each element placed in its tiles
+  {
+    static_assert(OFF_W2 % 4 == 0 && OFF_B2 % 4 == 0 && OFF_W3 % 4 == 0 && OFF_B3 % 4 == 0, "16-byte words");
+    constexpr int NW = OFF_B3 / 4;                              // words before b3 (b3: 3 floats)
+    constexpr int PER = (NW + TC_ROWS - 1) / TC_ROWS;
+    const float4 *t4 = reinterpret_cast<const float4 *>(a.theta);
+    float4 w4[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int q = tid + j * TC_ROWS;
+      w4[j] = q < NW ? t4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    auto place = [&](int e, float x) {
+      if (e < OFF_B1) {
+        *bfp(TC_W1 + kmaj_off(e / MLP_IN, e % MLP_IN, MLP_IN)) = __float2bfloat16_rn(x);
+      } else if (e < OFF_W2) {
+        bias[e - OFF_B1] = x;
+      } else if (e < OFF_B2) {
+        const int o = (e - OFF_W2) / MLP_H, k = (e - OFF_W2) % MLP_H;
+        const __nv_bfloat16 w = __float2bfloat16_rn(x);
+        *bfp(TC_W2 + kmaj_off(o, k, MLP_H)) = w;
+        *bfp(TC_W2T + kmaj_off(k, o, MLP_H)) = w;
+      } else if (e < OFF_W3) {
+        bias[MLP_H + e - OFF_B2] = x;
+      } else {
+        const int c = (e - OFF_W3) / MLP_H, k = (e - OFF_W3) % MLP_H;
+        const __nv_bfloat16 w = __float2bfloat16_rn(x);
+        *bfp(TC_W3 + kmaj_off(c, k, MLP_H)) = w;
+        *bfp(TC_W3T + kmaj_off(k, c, MLP_OUTP)) = w;
+      }
+    };
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int q = tid + j * TC_ROWS;
+      if (q < NW) {
+        place(4 * q, w4[j].x);
+        place(4 * q + 1, w4[j].y);
+        place(4 * q + 2, w4[j].z);
+        place(4 * q + 3, w4[j].w);
+      }
+    }
+    // W3's padding rows (outputs 3..15) and b3 (3 values, then zeros)
+    for (int e = tid; e < (MLP_OUTP - MLP_OUT) * MLP_H; e += TC_ROWS) {
+      const int c = MLP_OUT + e / MLP_H, k = e % MLP_H;
+      *bfp(TC_W3 + kmaj_off(c, k, MLP_H)) = __float2bfloat16_rn(0.f);
+      *bfp(TC_W3T + kmaj_off(k, c, MLP_OUTP)) = __float2bfloat16_rn(0.f);
+    }
+    if (tid < MLP_OUTP) bias[2 * MLP_H + tid] = tid < MLP_OUT ? a.theta[OFF_B3 + tid] : 0.f;
   }
-  for (int e = tid; e < MLP_OUTP * MLP_H; e += TC_ROWS) {
-    const int c = e / MLP_H, k = e % MLP_H;
-    *bfp(TC_W3 + kmaj_off(c, k, MLP_H)) = m.w3[e];
-    *bfp(TC_W3T + kmaj_off(k, c, MLP_OUTP)) = m.w3[e];
-  }
-  for (int e = tid; e < 2 * MLP_H + MLP_OUTP; e += TC_ROWS)
-    bias[e] = e < MLP_H ? m.b1[e] : (e < 2 * MLP_H ? m.b2[e - MLP_H] : m.b3[e - 2 * MLP_H]);
   // this thread's sample: features (two 16-byte words), label and class weight
   uint4 x0 = make_uint4(0, 0, 0, 0), x1 = x0;
   int yy = 0;
@@ -639,15 +689,8 @@ __global__ void k_mlp_adam(float *theta, float *m, float *v, float *grad, float 
                            float beta1, float beta2, float eps) {
   const float inv = stats[0] > 0.f ? 1.f / stats[0] : 0.f;
   const float c1 = 1.f - powf(beta1, (float)t), c2 = 1.f - powf(beta2, (float)t);
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < MLP_NPARAM; k += gridDim.x * blockDim.x) {
-    const float g = grad[k] * inv;
-    const float mk = beta1 * m[k] + (1.f - beta1) * g;
-    const float vk = beta2 * v[k] + (1.f - beta2) * g * g;
-    m[k] = mk;
-    v[k] = vk;
-    theta[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
-    grad[k] = 0.f;
-  }
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < MLP_NPARAM; k += gridDim.x * blockDim.x)
+    adam_one(k, theta, m, v, grad, inv, c1, c2, lr, beta1, beta2, eps);
 }
 
 // Normalised copy of the accumulated gradient (divided by the batch's total class weight)

@@ -2085,7 +2085,8 @@ int ms_read_lc_stats(void *sim, int64_t *out12) {
 
 namespace {
 // one gradient accumulation over the minibatch into work (gradient, then {weight sum, loss
-// sum, error bits}); tc: the tcgen05 kernel (128 samples per CTA) instead of mma.sync
+// sum, error bits}); tc: the tcgen05 kernel (128 samples per CTA, packing its own operands
+// from theta) instead of mma.sync (operands packed by k_mlp_pack)
 int mlp_run(const void *x, const int *y, const int *idx, int batch, const float *theta, const float *class_w,
             float *work, cudaStream_t st, bool tc) {
   Sim *s = nullptr;
@@ -2100,7 +2101,7 @@ int mlp_run(const void *x, const int *y, const int *idx, int batch, const float 
     CK(cudaFuncSetAttribute(k_mlp_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
     attr = true;
   }
-  k_mlp_pack<<<8, 256, 0, st>>>(theta, model);
+  if (!tc) k_mlp_pack<<<8, 256, 0, st>>>(theta, model);
   CK(cudaMemsetAsync(work, 0, sizeof(float) * (MLP_NPARAM + 4), st));
   TrainArgs a{};
   a.X = (const __nv_bfloat16 *)x;
@@ -2114,6 +2115,7 @@ int mlp_run(const void *x, const int *y, const int *idx, int batch, const float 
   a.grad = grad;
   a.stats = stats;
   a.err = reinterpret_cast<unsigned *>(stats + 2);
+  a.theta = theta;
   if (tc)
     k_mlp_train_tc<<<(batch + TC_ROWS - 1) / TC_ROWS, TC_ROWS, TC_SMEM, st>>>(a);
   else

@@ -185,8 +185,13 @@ int ms_load_network(void *sim, const ms_network *net);
    added, the model is dropped (the rule decides) and MS_ERR_CUDA is returned. */
 int ms_add_vehicles(void *sim, const ms_vehicles *veh);
 
-/* Enqueue n steps on the simulation's stream (asynchronous; CUDA-graph replays).  Returns
-   MS_ERR_CUDA if a launch fails.  Device error bits are reported by ms_sync. */
+/* Enqueue n steps on the simulation's stream (asynchronous; CUDA-graph replays).  One step
+   is the paper's time step of dt (Sec. III-A): the prepare phase (vehicles grouped by lane
+   and ordered by position; here an incremental merge of the sorted state) and the update
+   phase (sensing of the leader on the own path and on the lane-change target, IDM car
+   following and randomized MOBIL lane changes, signal stop lines, Newton's equations of
+   motion, lane-to-lane transfer, departures and arrivals).  Returns MS_ERR_CUDA if a launch
+   fails.  Device error bits are reported by ms_sync. */
 int ms_step(void *sim, int n);
 
 /* Run n steps with each kernel launched on its own (no graph) between CUDA events on the
@@ -226,8 +231,11 @@ int ms_step_noalloc(void *sim, int n);
 /* Wait for enqueued steps; MS_ERR_DEVICE if a device-side check fired. */
 int ms_sync(void *sim);
 
-/* Read the state (synchronises).  device = 0: the ms_state vehicle arrays are host
-   pointers; device = 1: they are device pointers (the copies are device-to-device) and
+/* Read the state (synchronises): every active vehicle's lane, position, speed, trip id and
+   route position, and each trip's status and arrival step -- the per-vehicle output the
+   paper's simulator gives each step (Sec. III-A, "output"; its heading angle needs lane
+   geometry the networks here do not carry).  device = 0: the ms_state vehicle arrays are
+   host pointers; device = 1: they are device pointers (the copies are device-to-device) and
    trip_status / t_arr, if not NULL, are host pointers.  MS_ERR_CAPACITY if capacity <
    n_active (n_active is still set). */
 int ms_read_state(void *sim, ms_state *out, int device);
@@ -252,9 +260,11 @@ int ms_read_state_async(void *sim, const ms_state *out);
    MS_ERR_STATE if no export is in flight. */
 int ms_read_wait(void *sim, int *n_active, int *t);
 
-/* Replace the dynamic state (checkpoint / resume).  Vehicles must be sorted by
-   (lane, x, id), one entry per active trip, gaps >= 0; trips neither active nor arrived
-   (t_arr < 0) wait for departure.  Metric accumulators are kept. */
+/* Replace the dynamic state (checkpoint / resume; the paper's API writes vehicle state in
+   batches, Sec. III-C).  Vehicles must be sorted by (lane, x, id), one entry per active
+   trip, gaps >= 0 (down to -max(1e-3 m, 5e-7 x): FP32 rounding far along long lanes);
+   trips neither active nor arrived (t_arr < 0) wait for departure.  Metric accumulators
+   are kept. */
 int ms_write_state(void *sim, const ms_state *in);
 
 int ms_read_metrics(void *sim, ms_metrics *out);

@@ -430,6 +430,20 @@ int ms_mlp_train_step_tc(const void *x, const int *y, const int *idx, int batch,
 int ms_mlp_grad_tc(const void *x, const int *y, const int *idx, int batch, const float *theta,
                    const float *class_w, float *work, float *grad, void *cuda_stream);
 
+/* Tests of the timeout paths (failure detection without a GPU fault).  Every wait of a
+   kernel on an asynchronous unit is bounded; these calls withhold what such a wait waits
+   for, so that it runs out after a short limit, and the failure must come back as an error
+   while the context stays usable.
+   ms_test_tc_timeout: the tcgen05 gradient of ms_mlp_grad_tc with no MMA issued or
+   committed; synchronises; returns MS_ERR_DEVICE when the kernel reported the timeout (the
+   expected outcome), MS_OK if it did not.  work holds no valid gradient afterwards.
+   ms_test_withhold_copies: on != 0 makes the steps that follow issue no bulk copy in the
+   apply kernel, whose waits then run out and set MS_DEV_TIMEOUT (ms_sync returns
+   MS_ERR_DEVICE); the simulation's state is invalid from that step on (destroy it). */
+int ms_test_tc_timeout(const void *x, const int *y, const int *idx, int batch, const float *theta,
+                       const float *class_w, float *work, void *cuda_stream);
+int ms_test_withhold_copies(void *sim, int on);
+
 /* Class and softmax margin (top1 - top2) of n samples x (device, bf16 [n][16]): device
    outputs cls [n] int, margin [n] float and, if not NULL, the logits [n][3] float.
    theta: device FP32 [5443]; work: device scratch of MS_MLP_WORK_FLOATS floats. */

@@ -178,6 +178,8 @@ struct TrainArgs {
   float *stats;             // [0] sum of weights, [1] weighted loss sum
   unsigned *err;            // k_mlp_train_tc: set when a wait for the tensor core ran out
   const float *theta;       // k_mlp_train_tc: FP32 parameters, from which it packs its operands
+  int withhold;             // test of the timeout path: no MMA is issued or committed, so the
+                            // first wait runs out (after a short limit) and sets err
 };
 
 // One Adam step (Kingma & Ba 2015) of parameter k on the accumulated gradient scaled by
@@ -483,16 +485,17 @@ __global__ void __launch_bounds__(TC_ROWS) k_mlp_train_tc(TrainArgs a) {
     __syncthreads();
     tc_fence_after();
     tm = *tslot;
-    if (tid == 0) {
+    if (tid == 0 && !a.withhold) {
       issue(tm);
       umma_commit(bar);
     }
     __syncwarp();
-    const bool done = mbar_wait(bar, phase & 1u, TC_WAIT_LIMIT);
+    const unsigned limit = a.withhold ? 4096u : TC_WAIT_LIMIT;
+    const bool done = mbar_wait(bar, phase & 1u, limit);
     tc_fence_after();
     if (__syncthreads_or(!done)) {
       if (tid == 0) atomicOr(a.err, 1u);
-      mbar_wait(bar, phase & 1u, TC_WAIT_LIMIT);   // the MMAs in flight, once more
+      mbar_wait(bar, phase & 1u, limit);   // the MMAs in flight, once more
       return false;
     }
     ++phase;

@@ -2088,7 +2088,7 @@ namespace {
 // sum, error bits}); tc: the tcgen05 kernel (128 samples per CTA, packing its own operands
 // from theta) instead of mma.sync (operands packed by k_mlp_pack)
 int mlp_run(const void *x, const int *y, const int *idx, int batch, const float *theta, const float *class_w,
-            float *work, cudaStream_t st, bool tc) {
+            float *work, cudaStream_t st, bool tc, bool withhold = false) {
   Sim *s = nullptr;
   static_assert(MLP_NPARAM == MS_MLP_NPARAM, "parameter count");
   static_assert(MLP_NPARAM + 4 + (int)(sizeof(MlpDev) / 4) <= MS_MLP_WORK_FLOATS, "work size");
@@ -2116,6 +2116,7 @@ int mlp_run(const void *x, const int *y, const int *idx, int batch, const float 
   a.stats = stats;
   a.err = reinterpret_cast<unsigned *>(stats + 2);
   a.theta = theta;
+  a.withhold = withhold ? 1 : 0;
   if (tc)
     k_mlp_train_tc<<<(batch + TC_ROWS - 1) / TC_ROWS, TC_ROWS, TC_SMEM, st>>>(a);
   else
@@ -2176,6 +2177,27 @@ int ms_mlp_train_step_tc(const void *x, const int *y, const int *idx, int batch,
 int ms_mlp_grad_tc(const void *x, const int *y, const int *idx, int batch, const float *theta, const float *class_w,
                    float *work, float *grad, void *cuda_stream) {
   return mlp_grad(x, y, idx, batch, theta, class_w, work, grad, cuda_stream, true);
+}
+
+int ms_test_tc_timeout(const void *x, const int *y, const int *idx, int batch, const float *theta,
+                       const float *class_w, float *work, void *cuda_stream) {
+  Sim *s = nullptr;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int r = mlp_run(x, y, idx, batch, theta, class_w, work, st, true, true);
+  if (r) return r;
+  unsigned e = 0;
+  CK(cudaMemcpyAsync(&e, work + MLP_NPARAM + 2, sizeof(e), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return e ? MS_ERR_DEVICE : MS_OK;
+}
+
+int ms_test_withhold_copies(void *sim, int on) {
+  Sim *s = (Sim *)sim;
+  if (!s) return MS_ERR_ARG;
+  CK(cudaStreamSynchronize(s->stream));
+  s->P.test_withhold = on ? 1 : 0;
+  drop_graphs(s);   // the flag is baked into the captured step graphs
+  return MS_OK;
 }
 
 int ms_mlp_predict(const void *x, int n, const float *theta, float *work, int *cls, float *margin, float *logits,

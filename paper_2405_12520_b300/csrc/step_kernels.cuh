@@ -76,6 +76,8 @@ struct DevParams {
   int mp_interval;       // steps between max-pressure decisions
   int lane_mods;         // some lane has a speed limit or is closed
   int fifo;              // some trip enters through a departure queue
+  int test_withhold;     // test of the timeout path: k_apply issues no bulk copy, so its
+                         // waits run out (after a short limit) and report MS_DEV_TIMEOUT
 };
 
 // Link plan of a route entry r (edge e = routes[r]), one 64-bit word built at load time:
@@ -1411,17 +1413,19 @@ __global__ void k_apply(StepArgs a) {
     a.ctrl->n_movers = 0;
     a.ctrl->n_cand = 0;
   }
-  if (threadIdx.x == 0 && blockIdx.x * T < n) app_issue(a, S, n, T, blockIdx.x, ssm, &bar[0]);
+  const bool issue = !a.P.test_withhold;
+  const unsigned limit = issue ? DEC_WAIT_LIMIT : 4096u;
+  if (issue && threadIdx.x == 0 && blockIdx.x * T < n) app_issue(a, S, n, T, blockIdx.x, ssm, &bar[0]);
   for (int j = 0;; ++j) {
     const int tile = blockIdx.x + j * G;
     const int base = tile * T;
     if (base >= n) break;   // block-uniform
     const int b = j & 1;
-    if (threadIdx.x == 0 && base + G * T < n) {   // the other buffer was released by the last barrier
+    if (issue && threadIdx.x == 0 && base + G * T < n) {   // the other buffer was released by the last barrier
       fence_proxy_async();
       app_issue(a, S, n, T, tile + G, ssm + (b ^ 1) * bsz, &bar[b ^ 1]);
     }
-    const bool ok = __all_sync(full, mbar_wait(&bar[b], (j >> 1) & 1, DEC_WAIT_LIMIT));
+    const bool ok = __all_sync(full, mbar_wait(&bar[b], (j >> 1) & 1, limit));
     const int ws = base + (threadIdx.x & ~31);   // this warp's first vehicle
     if (ok && ws < n) do {
       const unsigned char *buf = ssm + b * bsz;
@@ -1514,7 +1518,7 @@ __global__ void k_apply(StepArgs a) {
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {
         atomicOr(&a.ctrl->err, DEV_TIMEOUT);
-        if (base + G * T < n) mbar_wait(&bar[b ^ 1], ((j + 1) >> 1) & 1, DEC_WAIT_LIMIT);   // in flight
+        if (base + G * T < n) mbar_wait(&bar[b ^ 1], ((j + 1) >> 1) & 1, limit);   // in flight
       }
       return;
     }

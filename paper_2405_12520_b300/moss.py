@@ -22,7 +22,7 @@ SYMBOLS = ("ms_create", "ms_load_network", "ms_add_vehicles", "ms_step", "ms_ste
            "ms_sample_trips", "ms_sample_trips_radiation",
            "ms_read_lc_stats",
            "ms_mlp_train_step", "ms_mlp_train_step_tc",
-           "ms_mlp_grad", "ms_mlp_grad_tc",
+           "ms_mlp_grad", "ms_mlp_grad_tc", "ms_test_tc_timeout", "ms_test_withhold_copies",
            "ms_mlp_predict",
            "ms_sync", "ms_read_state", "ms_read_state_async", "ms_read_wait",
            "ms_write_state", "ms_read_metrics", "ms_read_debug", "ms_last_error", "ms_destroy")
@@ -104,6 +104,8 @@ def load():
         lib.ms_mlp_train_step_tc.argtypes = lib.ms_mlp_train_step.argtypes
         lib.ms_mlp_grad.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, vp, vp]
         lib.ms_mlp_grad_tc.argtypes = lib.ms_mlp_grad.argtypes
+        lib.ms_test_tc_timeout.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, vp]
+        lib.ms_test_withhold_copies.argtypes = [vp, C.c_int]
         lib.ms_mlp_predict.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp]
         lib.ms_sync.argtypes = [vp]
         lib.ms_read_state.argtypes = [vp, C.POINTER(ms_state), C.c_int]
@@ -151,6 +153,15 @@ def mlp_train_step(x, y, idx, theta, m, v, t, lr, class_w, work, stream=None, wa
     if rc:
         raise MossError(rc, name)
     return loss.value if want_loss else None
+
+
+def test_tc_timeout(x, y, idx, theta, class_w, work, stream=None):
+    """The tcgen05 gradient with no MMA issued (its first wait runs out): the return code,
+    MS_ERR_DEVICE when the kernel reported the timeout."""
+    lib = load()
+    cw = np.ascontiguousarray(class_w, np.float32)
+    return lib.ms_test_tc_timeout(_dp(x), _dp(y), _dp(idx), int(idx.numel()), _dp(theta), _p(cw), _dp(work),
+                                  _st(stream))
 
 
 def mlp_grad(x, y, idx, theta, class_w, work, grad, stream=None, tc=False):
@@ -461,6 +472,11 @@ class Sim:
         out = np.zeros(12, np.int64)
         self._check(self.lib.ms_read_lc_stats(self.h, _p(out)), "ms_read_lc_stats")
         return dict(zip(LC_STAT_NAMES, out.tolist()))
+
+    def test_withhold_copies(self, on: bool = True):
+        """Steps that follow issue no bulk copy in the apply kernel (its waits run out and
+        report MS_DEV_TIMEOUT); the state is invalid from then on."""
+        self._check(self.lib.ms_test_withhold_copies(self.h, int(bool(on))), "ms_test_withhold_copies")
 
     def destroy(self):
         if self.h:

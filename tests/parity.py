@@ -154,7 +154,7 @@ def compare_learned(gd, od, theta, report=None):
       - the network decided on both sides or on neither;
       - its 16 BF16 inputs equal the oracle's inputs rounded to BF16, except an input whose
         oracle value lies within the FP32 path's error of a BF16 rounding boundary (there:
-        within one BF16 step);
+        within one BF16 step plus that error);
       - its logits agree within the FP32 accumulation bound of the last layer plus the
         summed logit changes of rounding, one at a time, each input or hidden value near a
         BF16 rounding boundary the other way (oracle/mlp.flip_sensitivity), plus 1e-6.
@@ -171,8 +171,14 @@ def compare_learned(gd, od, theta, report=None):
     nin = near_bf16_boundary(fo, 2.0 ** -22 * np.abs(fo) + IN_ABS)
     bad = np.nonzero(np.any((fg != fb) & ~nin, axis=1))[0]
     assert bad.size == 0, f"BF16 inputs differ for ids {L[bad[:5]].tolist()}: gpu {fg[bad[:1]]} oracle {fb[bad[:1]]}"
-    step = 2.0 ** -7 * np.abs(fo) + 1e-30
-    assert np.all(np.abs(fg - fo)[nin] <= step[nin]), "an input off by more than one BF16 step"
+    # near a boundary the FP32 value itself may differ from the FP64 one by up to delta (R19),
+    # and then round the other way: one BF16 step of the value plus delta (near zero, where a
+    # BF16 step is tiny, delta dominates)
+    step = 2.0 ** -7 * np.abs(fo) + 2.0 ** -22 * np.abs(fo) + IN_ABS
+    over = np.argwhere(nin & (np.abs(fg - fo) > step))
+    assert over.size == 0, ("an input off by more than one BF16 step and its FP32 error: (candidate id, "
+                            "input, gpu, oracle) "
+                            + str([(int(L[r]), int(q), float(fg[r, q]), float(fo[r, q])) for r, q in over[:5]]))
     zo, zg = od["lc_logit"][L], gd["lc_logit"][L].astype(np.float64)
     z, _, _, zbound, _, _ = mlp.flip_sensitivity(np.asarray(theta, np.float64), fo, 0.0,
                                                  in_delta=2.0 ** -22 * np.abs(fo) + IN_ABS)

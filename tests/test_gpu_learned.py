@@ -128,6 +128,43 @@ def test_learned_single_steps_match_oracle(torch_mod, trained, net_kind, t0, mod
     assert ltot["learned_flagged"] <= 0.05 * (ltot["learned"] + ltot["learned_flagged"]) + 2
 
 
+@pytest.mark.parametrize("model", ["trained", "untrained"])
+def test_learned_single_steps_with_lane_limits_match_oracle(torch_mod, trained, model):
+    """The learned step with lane speed limits on 15% of the lanes and 3% closed (R14 with
+    R19: the decide and k_learn instances for lane modifications), against the oracle's
+    learned step with the same modifications, six steps from identical states."""
+    net = synth.grid_network(12, 12, 3, 200.0, 30, 3, "wave")
+    dem = synth.merge_demands(synth.place_vehicles(net, 6000, seed=81, min_spacing=7.0, internal_frac=0.3),
+                              synth.uniform_trips(net, 800, 40, seed=82))
+    rng = np.random.default_rng(83)
+    lim = np.nonzero(rng.random(net.n_lanes) < 0.15)[0]
+    shut = np.nonzero(rng.random(net.n_lanes) < 0.03)[0]
+    vmax = rng.uniform(5.0, 12.0, lim.size).astype(np.float32)
+    if model == "trained":
+        theta, margin = trained[0], 0.2
+    else:
+        theta, margin = learned.init_params(7), 0.05
+    params = dict(P, seed=141)
+    sim = parity.gpu_sim(net, dem, params)
+    sim.set_lc_model(theta, margin)
+    orc = oracle.Oracle(net, dem, params)
+    orc.set_lc_model(theta, margin)
+    for side in (sim, orc):
+        side.set_lane_limits(lim, vmax=vmax)
+        side.set_lane_limits(shut, closed=np.ones(shut.size, np.int32))
+    rep, lrep = [], []
+    for _ in range(6):
+        _, gd, gs, od, os_ = parity.step_pair(sim, orc)
+        parity.compare_step(gd, gs, od, os_, dem.n, report=rep)
+        parity.compare_learned(gd, od, theta, report=lrep)
+    tot = {k: sum(r[k] for r in rep) for k in rep[0]}
+    ltot = {k: sum(r[k] for r in lrep) for k in lrep[0] if k != "max_dz"}
+    print("lane limits", model, tot, ltot)
+    assert tot["compared"] > 0.9 * tot["active"]
+    assert ltot["learned"] > 100 and ltot["changes"] > 0
+    assert ltot["learned_flagged"] <= 0.05 * (ltot["learned"] + ltot["learned_flagged"]) + 2
+
+
 def test_gpu_gradient_matches_fp64_reference(torch_mod):
     torch = torch_mod
     rng = np.random.default_rng(5)

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import parity
-from paper_2405_12520_b300 import moss, synth
+from paper_2405_12520_b300 import learned, moss, synth
 
 pytestmark = pytest.mark.gpu
 P = synth.default_params()
@@ -18,7 +18,11 @@ def _scen():
     return synth.batch_scenarios(7, seed=3, side=(3, 8), n_range=(60, 1500))
 
 
-def test_batch_equals_union_and_standalone():
+@pytest.mark.parametrize("learned_model", [False, True])
+def test_batch_equals_union_and_standalone(learned_model):
+    """learned_model: an untrained surrogate with margin 0.05 decides most discretionary
+    changes on every side (each network row depends on its own inputs only, so the learned
+    decisions do not depend on which other candidates share a tensor-core tile)."""
     sc = _scen()
     nets, dems = [n for n, _ in sc], [d for _, d in sc]
     b = moss.Sim(P, n_windows=1)
@@ -34,6 +38,10 @@ def test_batch_equals_union_and_standalone():
         s.load_network(n)
         s.add_vehicles(d)
         solo.append(s)
+    if learned_model:
+        theta = learned.init_params(7)
+        for s in [b, u] + solo:
+            s.set_lc_model(theta, 0.05)
     for rnd in range(3):
         b.step(40)
         u.step(40)
@@ -51,6 +59,9 @@ def test_batch_equals_union_and_standalone():
             np.testing.assert_array_equal(sb["v"][m], ss["v"])
             np.testing.assert_array_equal(sb["t_arr"][trip_off[k]:trip_off[k + 1]], ss["t_arr"])
     assert b.read_metrics(lanes=False)["err"] == 0
+    if learned_model:
+        st = b.read_lc_stats()
+        assert st["candidates"] > 100 and st["fallbacks"] < st["candidates"]
 
 
 def test_batch_single_steps_match_oracle():

@@ -128,11 +128,13 @@ def test_learned_single_steps_match_oracle(torch_mod, trained, net_kind, t0, mod
     assert ltot["learned_flagged"] <= 0.05 * (ltot["learned"] + ltot["learned_flagged"]) + 2
 
 
+@pytest.mark.parametrize("variant", ["lane_limits", "max_pressure"])
 @pytest.mark.parametrize("model", ["trained", "untrained"])
-def test_learned_single_steps_with_lane_limits_match_oracle(torch_mod, trained, model):
+def test_learned_single_steps_with_variants_match_oracle(torch_mod, trained, model, variant):
     """The learned step with lane speed limits on 15% of the lanes and 3% closed (R14 with
-    R19: the decide and k_learn instances for lane modifications), against the oracle's
-    learned step with the same modifications, six steps from identical states."""
+    R19: the decide and k_learn instances for lane modifications), or with max-pressure
+    signals (R13 with R19), against the oracle's learned step with the same setting, six
+    steps from identical states."""
     net = synth.grid_network(12, 12, 3, 200.0, 30, 3, "wave")
     dem = synth.merge_demands(synth.place_vehicles(net, 6000, seed=81, min_spacing=7.0, internal_frac=0.3),
                               synth.uniform_trips(net, 800, 40, seed=82))
@@ -145,13 +147,19 @@ def test_learned_single_steps_with_lane_limits_match_oracle(torch_mod, trained, 
     else:
         theta, margin = learned.init_params(7), 0.05
     params = dict(P, seed=141)
+    if variant == "max_pressure":
+        params.update(signal_mode=1, mp_interval=10)
     sim = parity.gpu_sim(net, dem, params)
+    st = sim.read_state()
+    st["t"] = 58 if variant == "max_pressure" else 0   # max-pressure decisions at 60 and 70
+    sim.write_state(st)
     sim.set_lc_model(theta, margin)
     orc = oracle.Oracle(net, dem, params)
     orc.set_lc_model(theta, margin)
-    for side in (sim, orc):
-        side.set_lane_limits(lim, vmax=vmax)
-        side.set_lane_limits(shut, closed=np.ones(shut.size, np.int32))
+    if variant == "lane_limits":
+        for side in (sim, orc):
+            side.set_lane_limits(lim, vmax=vmax)
+            side.set_lane_limits(shut, closed=np.ones(shut.size, np.int32))
     rep, lrep = [], []
     for _ in range(6):
         _, gd, gs, od, os_ = parity.step_pair(sim, orc)
@@ -159,10 +167,33 @@ def test_learned_single_steps_with_lane_limits_match_oracle(torch_mod, trained, 
         parity.compare_learned(gd, od, theta, report=lrep)
     tot = {k: sum(r[k] for r in rep) for k in rep[0]}
     ltot = {k: sum(r[k] for r in lrep) for k in lrep[0] if k != "max_dz"}
-    print("lane limits", model, tot, ltot)
+    print(variant, model, tot, ltot)
     assert tot["compared"] > 0.9 * tot["active"]
     assert ltot["learned"] > 100 and ltot["changes"] > 0
     assert ltot["learned_flagged"] <= 0.05 * (ltot["learned"] + ltot["learned_flagged"]) + 2
+
+
+def test_learned_resume_is_bit_exact(torch_mod, trained):
+    """Checkpoint / resume with the learned model set: 300 + 200 steps through a state read
+    back and written into a new simulation equal 500 uninterrupted steps, bit for bit."""
+    net, dem = synth.small_grid_workload(4)
+    theta = trained[0]
+    a = parity.gpu_sim(net, dem, P, debug=False)
+    a.set_lc_model(theta, 0.2)
+    a.step(500)
+    sa = a.read_state()
+    b = parity.gpu_sim(net, dem, P, debug=False)
+    b.set_lc_model(theta, 0.2)
+    b.step(300)
+    mid = b.read_state()
+    c = parity.gpu_sim(net, dem, P, debug=False)
+    c.set_lc_model(theta, 0.2)
+    c.write_state(mid)
+    c.step(200)
+    sc = c.read_state()
+    for k in ("id", "lane", "x", "v", "route_idx", "t_arr", "t"):
+        np.testing.assert_array_equal(sa[k], sc[k])
+    assert a.read_lc_stats()["candidates"] > 0
 
 
 def test_gpu_gradient_matches_fp64_reference(torch_mod):

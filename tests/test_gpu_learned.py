@@ -12,6 +12,7 @@ gains over an untrained one and over the rule-only step."""
 import numpy as np
 import pytest
 
+import netkit
 import oracle
 import parity
 from oracle import mlp as ref
@@ -128,13 +129,14 @@ def test_learned_single_steps_match_oracle(torch_mod, trained, net_kind, t0, mod
     assert ltot["learned_flagged"] <= 0.05 * (ltot["learned"] + ltot["learned_flagged"]) + 2
 
 
-@pytest.mark.parametrize("variant", ["lane_limits", "max_pressure"])
+@pytest.mark.parametrize("variant", ["lane_limits", "max_pressure", "dynamic_lanes"])
 @pytest.mark.parametrize("model", ["trained", "untrained"])
 def test_learned_single_steps_with_variants_match_oracle(torch_mod, trained, model, variant):
     """The learned step with lane speed limits on 15% of the lanes and 3% closed (R14 with
     R19: the decide and k_learn instances for lane modifications), or with max-pressure
-    signals (R13 with R19), against the oracle's learned step with the same setting, six
-    steps from identical states."""
+    signals (R13 with R19), or with about 30% of the lane links closed (R17 with R19),
+    against the oracle's learned step with the same setting, six steps from identical
+    states."""
     net = synth.grid_network(12, 12, 3, 200.0, 30, 3, "wave")
     dem = synth.merge_demands(synth.place_vehicles(net, 6000, seed=81, min_spacing=7.0, internal_frac=0.3),
                               synth.uniform_trips(net, 800, 40, seed=82))
@@ -160,6 +162,12 @@ def test_learned_single_steps_with_variants_match_oracle(torch_mod, trained, mod
         for side in (sim, orc):
             side.set_lane_limits(lim, vmax=vmax)
             side.set_lane_limits(shut, closed=np.ones(shut.size, np.int32))
+    elif variant == "dynamic_lanes":
+        mask = netkit.closable_links(net, dem, np.random.default_rng(84), 0.3)
+        lanes = np.array(list(mask), np.int32)
+        masks = np.array([mask[int(l)] for l in lanes], np.uint32)
+        for side in (sim, orc):
+            side.set_lane_links(lanes, masks)
     rep, lrep = [], []
     for _ in range(6):
         _, gd, gs, od, os_ = parity.step_pair(sim, orc)

@@ -129,14 +129,15 @@ def test_learned_single_steps_match_oracle(torch_mod, trained, net_kind, t0, mod
     assert ltot["learned_flagged"] <= 0.05 * (ltot["learned"] + ltot["learned_flagged"]) + 2
 
 
-@pytest.mark.parametrize("variant", ["lane_limits", "max_pressure", "dynamic_lanes"])
+@pytest.mark.parametrize("variant", ["lane_limits", "max_pressure", "dynamic_lanes", "threshold_jitter"])
 @pytest.mark.parametrize("model", ["trained", "untrained"])
 def test_learned_single_steps_with_variants_match_oracle(torch_mod, trained, model, variant):
     """The learned step with lane speed limits on 15% of the lanes and 3% closed (R14 with
     R19: the decide and k_learn instances for lane modifications), or with max-pressure
-    signals (R13 with R19), or with about 30% of the lane links closed (R17 with R19),
-    against the oracle's learned step with the same setting, six steps from identical
-    states."""
+    signals (R13 with R19), or with about 30% of the lane links closed (R17 with R19), or
+    with per-trip incentive thresholds (R12: the rule's decision where the network falls
+    back), against the oracle's learned step with the same setting, six steps from
+    identical states."""
     net = synth.grid_network(12, 12, 3, 200.0, 30, 3, "wave")
     dem = synth.merge_demands(synth.place_vehicles(net, 6000, seed=81, min_spacing=7.0, internal_frac=0.3),
                               synth.uniform_trips(net, 800, 40, seed=82))
@@ -151,6 +152,8 @@ def test_learned_single_steps_with_variants_match_oracle(torch_mod, trained, mod
     params = dict(P, seed=141)
     if variant == "max_pressure":
         params.update(signal_mode=1, mp_interval=10)
+    elif variant == "threshold_jitter":
+        params.update(mobil_th_jitter=0.15)
     sim = parity.gpu_sim(net, dem, params)
     st = sim.read_state()
     st["t"] = 58 if variant == "max_pressure" else 0   # max-pressure decisions at 60 and 70

@@ -95,10 +95,13 @@ def peaks():
 def kernel_src_hash() -> str:
     """Hash of every file that shapes the step's kernels and their launches: the kernel
     sources, the host runtime that sizes grids and caps registers, and the build flags."""
+    from paper_2405_12520_b300 import build as bld
     h = hashlib.sha256()
     pkg = os.path.join(ROOT, "paper_2405_12520_b300")
-    for f in ("csrc/step_kernels.cuh", "csrc/mlp_kernels.cuh", "csrc/moss103.cu", "build.py"):
-        with open(os.path.join(pkg, f), "rb") as fh:
+    files = [os.path.join(pkg, "csrc", f) for f in bld.SOURCES + bld.HEADERS]
+    files += [os.path.join(ROOT, "include", "moss103.h"), os.path.join(pkg, "build.py")]
+    for f in files:
+        with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
 

@@ -199,6 +199,79 @@ def test_learned_logits_match_the_numpy_bf16_forward():
     assert (cls == 1).sum() > 0 and (cls != 1).sum() > 0
 
 
+@pytest.mark.parametrize("t0", [0, 1])
+def test_always_right_network_changes_only_on_right_steps(t0):
+    """A network that always answers 'right' (class 2, margin 0.9993): on a step that allows
+    only moves to the left (even t) every learned candidate stays; on a step that allows
+    moves to the right (odd t) every learned candidate moves right, since it passed the
+    safety criteria for that target lane and the class replaces the incentive test."""
+    p = {k: np.zeros(s) for k, s in mlp.SHAPES}
+    p["b3"][2] = 8.0
+    theta = mlp.pack(p).astype(np.float32)
+    net, dem = _workload()
+    st, dr, dl = _pair(net, dem, t0, theta)
+    act = dr["active_before"] == 1
+    L = dl["lc_learn"] == 1
+    assert L.sum() > 50, L.sum()
+    assert np.all(dl["lc_dir"][L] == (0 if t0 % 2 == 0 else -1))
+    assert np.array_equal(dl["lc_dir"][act & ~L], dr["lc_dir"][act & ~L])
+
+
+@pytest.mark.parametrize("t0", [0, 1])
+def test_learned_inputs_follow_from_the_state(t0):
+    """The inputs of every learned candidate recomputed from the state arrays and the
+    sensing records (own leader, target-lane leader and follower, old follower, whose ids the
+    oracle's brute-force pins fix), in the scales of the learned decision's definition:
+    speeds / 20, gaps and the distance to the lane end min(., 200) / 100 (2 when there is
+    nothing), closing speeds / 10, accelerations / a_max, the step's direction."""
+    net, dem = _workload()
+    theta = (mlp.init(5) + np.random.default_rng(1).normal(scale=0.05, size=mlp.N_PARAMS)).astype(np.float32)
+    st, dr, dl = _pair(net, dem, t0, theta, margin=0.0)
+    L = np.nonzero(dl["lc_learn"] == 1)[0]
+    assert L.size > 50
+    f = dl["lc_feat"][L]
+    x, v, lane = st["x"], st["v"], st["lane"]
+    Lv = P["veh_len"]
+    lane_len = np.asarray(net.lane_len, np.float64)
+    v0 = np.asarray(dem.v0, np.float32).astype(np.float64)
+    cap = lambda g: np.minimum(g, 200.0) / 100.0
+    ok = lambda a, b: np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12)
+    ok(f[:, 0], v[L] / 20.0)
+    ok(f[:, 1], v0[L] / 20.0)
+    kind, s_own, vl = dl["lead_kind"][L], dl["s_own"][L], dl["vl_own"][L]
+    assert set(np.unique(kind)) <= {0, 1, 2}
+    ok(f[:, 2], np.where(kind == 0, 2.0, cap(s_own)))
+    ok(f[:, 3], np.where(kind == 1, (v[L] - vl) / 10.0, np.where(kind == 2, v[L] / 10.0, 0.0)))
+    ok(f[:, 4], dl["a_own"][L] / P["idm_a"])
+    ok(f[:, 5], np.full(L.size, 1.0 if t0 % 2 == 0 else -1.0))
+    tl, tf, of = dl["tau_lead"][L], dl["tau_foll"][L], dl["old_foll"][L]
+    to_end = lane_len[lane[L]] - x[L]
+    h = tl >= 0
+    ok(f[h, 6], cap(x[tl[h]] - x[L[h]] - Lv))
+    ok(f[h, 7], (v[L[h]] - v[tl[h]]) / 10.0)
+    # no target leader: free road (2, 0) or the target lane's end as a stopped obstacle
+    free = (f[:, 6] == 2.0) & (f[:, 7] == 0.0)
+    obst = np.isclose(f[:, 6], cap(to_end), rtol=1e-12, atol=1e-12) & np.isclose(
+        f[:, 7], v[L] / 10.0, rtol=1e-12, atol=1e-12)
+    assert np.all((free | obst)[~h])
+    h = tf >= 0
+    ok(f[h, 8], cap(x[L[h]] - x[tf[h]] - Lv))
+    ok(f[h, 9], v[tf[h]] / 20.0)
+    ok(f[~h, 8], 2.0)
+    ok(f[~h, 9], 0.0)
+    ok(f[~h, 10], 0.0)
+    h = of >= 0
+    ok(f[h, 12], v[of[h]] / 20.0)
+    ok(f[h, 15], cap(x[L[h]] - x[of[h]] - Lv))
+    ok(f[~h, 12], 0.0)
+    ok(f[~h, 15], 2.0)
+    ok(f[:, 13], cap(to_end))
+    ok(f[:, 14], np.where(kind == 1, vl / 20.0, np.where(kind == 2, 0.0, 1.0)))
+    # every branch above was taken
+    assert (tl >= 0).any() and (tl < 0).any() and (tf >= 0).any() and (tf < 0).any()
+    assert (of >= 0).any() and (of < 0).any() and (kind == 1).any()
+
+
 def _sparse_exact_net(rng):
     """Each hidden unit reads one input (layer 1) or two units (layer 2) with dyadic
     weights, so inputs in quarters give every activation exactly in BF16."""

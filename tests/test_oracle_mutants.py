@@ -1,0 +1,314 @@
+"""Planted mistakes in the oracle: its pins must catch the mistakes they exist for.
+
+Each case copies oracle/ into a scratch directory, plants one plausible mistake in the copy
+(a dropped term, a wrong sign, a transposed index or operand, a reversed comparison, an
+off-by-one), and runs the oracle's pins (the four pin files below) against that copy in a
+child process.  At least one pin must fail, and the pin named for that mistake must be among
+the failures.  A control copy with nothing planted must pass every pin, and the child must
+be shown to import the copy, not this tree's oracle.  CPU only: the copies are plain C and
+numpy, built with gcc in the scratch directory.
+
+Mistakes that change nothing in FP64 are not listed: for example, the clamp of a position to
+the lane end when the own lane ends in an obstacle is a no-op in the oracle, since there
+x + (len - x) is exact for FP32 positions (it exists for rounding on the device)."""
+import os
+import re
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_learned_oracle.py", "tests/test_mlp_oracle.py",
+             "tests/test_routing_oracle.py"]
+
+# (name, file under oracle/, exact text (occurs once), replacement, pins that must fail)
+MUTANTS = [
+    # R2: own-path leader across lane ends
+    ("lookahead_gap_one_lane_too_long", "moss_oracle.c",
+     "r.kind = K_VEH; r.gap = (dist + s->x[j]) - L; r.vl = s->v[j]; r.lead_id = j;\n        break;",
+     "r.kind = K_VEH; r.gap = (dist + s->x[j] + (double)s->net.lane_len[nxt]) - L; r.vl = s->v[j];"
+     " r.lead_id = j;\n        break;",
+     ["test_step_leaders_and_target_neighbours_match_brute_force"]),
+    ("lookahead_gap_drops_the_distance", "moss_oracle.c",
+     "r.kind = K_VEH; r.gap = (dist + s->x[j]) - L; r.vl = s->v[j]; r.lead_id = j;\n        break;",
+     "r.kind = K_VEH; r.gap = (s->x[j]) - L; r.vl = s->v[j]; r.lead_id = j;\n        break;",
+     ["test_step_leaders_and_target_neighbours_match_brute_force"]),
+    ("own_leader_gap_keeps_the_length", "moss_oracle.c",
+     "r.kind = K_VEH; r.gap = (s->x[j] - x) - L;",
+     "r.kind = K_VEH; r.gap = (s->x[j] - x);",
+     ["test_idm_ring_equilibrium_is_fixed_point"]),
+    # R1: IDM
+    ("idm_interaction_sign", "moss_oracle.c",
+     "v * p->T + v * dv / (2.0 * sqrt(p->a * p->b))",
+     "v * p->T - v * dv / (2.0 * sqrt(p->a * p->b))",
+     ["test_stop_at_long_red_reaches_standstill_gap"]),
+    ("idm_interaction_not_squared", "moss_oracle.c",
+     "a = p->a * (freeterm - q * q);", "a = p->a * (freeterm - q);",
+     ["test_idm_ring_equilibrium_is_fixed_point"]),
+    ("idm_free_road_exponent_two", "moss_oracle.c",
+     "double freeterm = 1.0 - r2 * r2;", "double freeterm = 1.0 - r2;",
+     ["test_idm_ring_equilibrium_is_fixed_point"]),
+    ("idm_drops_the_jam_distance", "moss_oracle.c",
+     "double ss = p->s0 + fmax(", "double ss = fmax(",
+     ["test_idm_ring_equilibrium_is_fixed_point"]),
+    ("lookahead_reads_the_next_lanes_signal", "moss_oracle.c",
+     "int sg = or_signal_state(s, cur, s->t);\n          if (sg == SIG_RED) stop = 1;",
+     "int sg = or_signal_state(s, nxt, s->t);\n          if (sg == SIG_RED) stop = 1;",
+     ["test_stop_at_long_red_reaches_standstill_gap", "test_yellow_stop_rule"]),
+    ("lookahead_horizon_doubled", "moss_oracle.c",
+     "if (dist >= s->p.d_look) break; /* free */", "if (dist >= 2.0 * s->p.d_look) break; /* free */",
+     ["test_step_leaders_and_target_neighbours_match_brute_force"]),
+    ("lookahead_internal_lane_keeps_the_route_cursor", "moss_oracle.c",
+     "nxt = s->net.succ_lane[s->net.succ_off[cur]];\n        ri += 1;",
+     "nxt = s->net.succ_lane[s->net.succ_off[cur]];",
+     ["test_step_leaders_and_target_neighbours_match_brute_force"]),
+    ("fan_out_ignores_the_edge_after_next", "moss_oracle.c",
+     "    if (connects(s, tg, en2)) return il;\n", "    return il;\n",
+     ["test_step_leaders_and_target_neighbours_match_brute_force"]),
+    # R9: fixed-time signals
+    ("signal_offset_sign", "moss_oracle.c",
+     "int tau = ((t + s->net.ctrl_offset[c]) % cyc + cyc) % cyc;",
+     "int tau = ((t - s->net.ctrl_offset[c]) % cyc + cyc) % cyc;",
+     ["test_signal_offsets_shift_the_table"]),
+    ("signal_green_one_second_long", "moss_oracle.c",
+     "return (tau % (g + y)) < g ? SIG_GREEN : SIG_YELLOW;",
+     "return (tau % (g + y)) <= g ? SIG_GREEN : SIG_YELLOW;",
+     ["test_signal_table_closed_form"]),
+    # R5: stop lines (yellow: stop when the vehicle can)
+    ("yellow_rule_reversed", "moss_oracle.c",
+     "            mark(flag, m);\n            if (m >= 0.0) stop = 1;",
+     "            mark(flag, m);\n            if (m < 0.0) stop = 1;",
+     ["test_yellow_stop_rule"]),
+    # R4: randomized MOBIL
+    ("mobil_own_incentive_sign", "moss_oracle.c",
+     "double delta = r.a_new - a_c;", "double delta = a_c - r.a_new;",
+     ["test_mobil_incentive_is_free_gain_with_empty_target"]),
+    ("mobil_new_follower_term_sign", "moss_oracle.c",
+     "delta += p->p * (aF_new - aF_old);", "delta += p->p * (aF_old - aF_new);",
+     ["test_mobil_politeness_terms_closed_form"]),
+    ("mobil_drops_the_old_follower_term", "moss_oracle.c",
+     "delta += p->p * (aO_new - aO_old);", "delta += 0.0 * (aO_new - aO_old);",
+     ["test_mobil_politeness_terms_closed_form"]),
+    ("mobil_safety_threshold_sign", "moss_oracle.c",
+     "if (aF_new < -p->bsafe) return r;", "if (aF_new < p->bsafe) return r;",
+     ["test_mobil_safety_criteria"]),
+    ("mobil_conflict_guard_drops_the_acceleration_term", "moss_oracle.c",
+     "double guard = s->v[Ft] * p->dt + 0.5 * p->a * p->dt * p->dt;", "double guard = s->v[Ft] * p->dt;",
+     ["test_mobil_safety_criteria"]),
+    ("mobil_new_follower_old_gap_keeps_the_length", "moss_oracle.c",
+     "(s->x[Lt] - s->x[Ft]) - L, s->v[Lt]);", "(s->x[Lt] - s->x[Ft]), s->v[Lt]);",
+     ["test_mobil_politeness_with_a_target_leader"]),
+    ("mobil_old_follower_new_gap_loses_a_length", "moss_oracle.c",
+     "own->gap + (x - s->x[O]), own->vl);", "own->gap + (x - s->x[O]) - L, own->vl);",
+     ["test_mobil_politeness_terms_closed_form"]),
+    ("mandatory_direction_reversed", "moss_oracle.c",
+     "int want = best > idx ? +1 : -1;", "int want = best > idx ? -1 : +1;",
+     ["test_mandatory_change_toward_connecting_lane"]),
+    ("lane_end_zone_measured_from_the_start", "moss_oracle.c",
+     "if (len - x < p->x_lc_end) return r;", "if (x < p->x_lc_end) return r;",
+     ["test_mobil_zones_and_gate"]),
+    ("threshold_jitter_one_sided", "moss_oracle.c",
+     "return p->th + p->th_jitter * (2.0 * u - 1.0);", "return p->th + p->th_jitter * u;",
+     ["test_mobil_threshold_jitter_is_uniform_over_trips"]),
+    ("target_leader_and_follower_transposed", "moss_oracle.c",
+     "int Lt = j < cnt ? o[j] : -1;\n  int Ft = j > 0 ? o[j - 1] : -1;",
+     "int Lt = j > 0 ? o[j - 1] : -1;\n  int Ft = j < cnt ? o[j] : -1;",
+     ["test_step_leaders_and_target_neighbours_match_brute_force"]),
+    ("step_direction_parity_reversed", "moss_oracle.c",
+     "int step_dir = (s->t % 2 == 0) ? +1 : -1;", "int step_dir = (s->t % 2 == 0) ? -1 : +1;",
+     ["test_mobil_direction_alternates_with_step_parity"]),
+    ("random_gate_reversed", "moss_oracle.c",
+     "if ((h >> 40) >= thr) return r;", "if ((h >> 40) < thr) return r;",
+     ["test_mobil_zones_and_gate"]),
+    # R6, R7: motion and transfer
+    ("advance_by_the_end_speed", "moss_oracle.c",
+     "d = 0.5 * (v + vn) * p->dt;", "d = vn * p->dt;",
+     ["test_free_road_accelerates_to_v0"]),
+    ("transfer_drops_the_overshoot", "moss_oracle.c",
+     "          xn -= len;\n", "          xn = 0.0;\n",
+     ["test_free_road_accelerates_to_v0"]),
+    ("stop_within_the_step_does_not_move", "moss_oracle.c",
+     "d = v > 0.0 ? (v * v) / (-2.0 * a_use) : 0.0;", "d = 0.0;",
+     ["test_motion_stop_within_the_step_and_gap_clamp"]),
+    ("gap_clamp_keeps_the_speed", "moss_oracle.c",
+     "      d = dmax;\n      vn = fmin(vn, d / p->dt);", "      d = dmax;",
+     ["test_motion_stop_within_the_step_and_gap_clamp"]),
+    ("retires_one_edge_early", "moss_oracle.c",
+     "if (!is_internal(s, l) && route_at(s, c, s->rp[c] + 1) < 0) {",
+     "if (!is_internal(s, l) && route_at(s, c, s->rp[c] + 2) < 0) {",
+     ["test_closed_lane_is_never_entered_until_reopened"]),
+    ("travel_time_off_by_one", "moss_oracle.c",
+     "s->counters[2] += (int64_t)(s->t + 1 - s->t_dep[c]);", "s->counters[2] += (int64_t)(s->t - s->t_dep[c]);",
+     ["test_travel_time_is_the_arrival_clock_minus_the_departure"]),
+    # R10: lane metrics
+    ("metrics_window_off_by_one", "moss_oracle.c",
+     "int w = s->t / p->window;", "int w = (s->t + 1) / p->window;",
+     ["test_metrics_window_sums"]),
+    # R8: departures
+    ("departure_room_ignores_the_tail_length", "moss_oracle.c",
+     "double m = (s->x[tail] - L) - (L + p->s0);", "double m = s->x[tail] - (L + p->s0);",
+     ["test_departures_fifo_and_room"]),
+    ("departs_a_step_early", "moss_oracle.c",
+     "if (s->t_dep[h] > s->t) continue;", "if (s->t_dep[h] > s->t + 1) continue;",
+     ["test_departure_waits_for_its_time"]),
+    ("arrival_rear_without_the_length", "moss_oracle.c",
+     "arr_min[nl] = fmin(arr_min[nl], s->n_x[c] - L);", "arr_min[nl] = fmin(arr_min[nl], s->n_x[c]);",
+     ["test_small_grid_run_invariants"]),
+    # R3: merge projection
+    ("merge_projection_order_reversed", "moss_oracle.c",
+     "if (dj < dc || (dj == dc && j < c)) { found = j; break; }",
+     "if (dj > dc || (dj == dc && j < c)) { found = j; break; }",
+     ["test_merge_projection_leader"]),
+    ("merge_tie_break_reversed", "moss_oracle.c",
+     "if (dj < dc || (dj == dc && j < c)) { found = j; break; }",
+     "if (dj < dc || (dj == dc && j > c)) { found = j; break; }",
+     ["test_merge_projection_leader"]),
+    # R13: max pressure
+    ("max_pressure_sign", "moss_oracle.c",
+     "sum += s->seg_cnt[l] - s->seg_cnt[m];", "sum += s->seg_cnt[m] - s->seg_cnt[l];",
+     ["test_max_pressure_switches_to_the_loaded_phase"]),
+    ("max_pressure_tie_leaves_the_green_phase", "moss_oracle.c",
+     "if (pr[s->mp_g[c]] == pr[best]) best = s->mp_g[c];", "",
+     ["test_max_pressure_holds_the_green_phase_on_ties"]),
+    ("max_pressure_counts_closed_links", "moss_oracle.c",
+     "if (s->link_off[k]) continue;   /* R17 */\n        const int il", "const int il",
+     ["test_max_pressure_skips_closed_links"]),
+    # R14: lane limits and closures
+    ("speed_limit_ignored", "moss_oracle.c",
+     "return fmin((double)s->v0[c], s->lane_vmax[l]);", "return (double)s->v0[c];",
+     ["test_lane_speed_limit_caps_the_desired_speed"]),
+    ("closed_target_lane_entered", "moss_oracle.c",
+     "if (s->lane_closed[tau]) return r;   /* R14 */", "",
+     ["test_mobil_uses_the_target_lanes_limit"]),
+    # R19: BF16 rounding of the learned decision
+    ("bf16_rounds_to_seven_bits", "moss_oracle.c",
+     "return ldexp(nearbyint(ldexp(m, 8)), e - 8);", "return ldexp(nearbyint(ldexp(m, 7)), e - 7);",
+     ["test_bf16_rounding_follows_the_format"]),
+    ("learned_margin_test_reversed", "moss_oracle.c",
+     "if (mg < m->margin) return rule_dir;", "if (mg > m->margin) return rule_dir;",
+     ["test_full_fallback_network_is_the_rule_over_a_run"]),
+    ("learned_classes_left_and_right_swapped", "moss_oracle.c",
+     "static int class_dir(int cls) { return cls == 1 ? +1 : (cls == 2 ? -1 : 0); }",
+     "static int class_dir(int cls) { return cls == 1 ? -1 : (cls == 2 ? +1 : 0); }",
+     ["test_probe_network_decides_by_one_physical_quantity"]),
+    ("learned_margin_is_the_top_probability", "moss_oracle.c",
+     "return pr[c] - sec;", "return pr[c];",
+     ["test_learned_logits_match_the_numpy_bf16_forward"]),
+    ("learned_disallowed_direction_falls_back_to_the_rule", "moss_oracle.c",
+     "return (d != 0 && d != step_dir) ? 0 : d;", "return (d != 0 && d != step_dir) ? rule_dir : d;",
+     ["test_always_right_network_changes_only_on_right_steps"]),
+    ("learned_inputs_8_and_9_swapped", "moss_oracle.c",
+     "f[8] = lc->tau_foll >= 0 ? fmin(lc->gF, 200.0) / 100.0 : 2.0;\n  f[9] = lc->tau_foll >= 0 ? lc->vF / 20.0 : 0.0;",
+     "f[9] = lc->tau_foll >= 0 ? fmin(lc->gF, 200.0) / 100.0 : 2.0;\n  f[8] = lc->tau_foll >= 0 ? lc->vF / 20.0 : 0.0;",
+     ["test_learned_inputs_follow_from_the_state"]),
+    ("learned_input_12_reads_the_own_speed", "moss_oracle.c",
+     "f[12] = O >= 0 ? s->v[O] / 20.0 : 0.0;", "f[12] = O >= 0 ? v / 20.0 : 0.0;",
+     ["test_learned_inputs_follow_from_the_state"]),
+    # the network's gradient and optimiser (numpy)
+    ("mlp_gradient_wrong_relu_mask", "mlp.py",
+     "da1 = dh1 * (a1 > 0)\n    g[\"W1\"]", "da1 = dh1 * (a1 >= -1.0)\n    g[\"W1\"]",
+     ["test_gradient_matches_central_differences"]),
+    ("mlp_bias_gradient_before_the_mask", "mlp.py",
+     "g[\"b2\"] = da2.sum(0)\n    dh1 = da2 @ prm", "g[\"b2\"] = dh2.sum(0)\n    dh1 = da2 @ prm",
+     ["test_gradient_matches_central_differences"]),
+    ("loss_weights_not_normalised", "mlp.py",
+     "dz *= (w / W)[:, None]", "dz *= w[:, None]",
+     ["test_gradient_matches_central_differences"]),
+    ("adam_without_second_moment_correction", "mlp.py",
+     "vh = v / (1 - b2 ** t)", "vh = v",
+     ["test_adam_first_step_is_lr_times_sign"]),
+    # R16, R18: demand generation (numpy)
+    ("gravity_decay_one_power_short", "routing.py",
+     "            for _ in range(gamma):\n                p = np.float32(p * dkm)\n            W[i, j]",
+     "            for _ in range(gamma - 1):\n                p = np.float32(p * dkm)\n            W[i, j]",
+     ["test_gravity_decays_with_route_distance"]),
+    ("gravity_origins_uniform", "routing.py",
+     "cdf_o = np.cumsum(A, dtype=np.float32)\n    W = np.zeros",
+     "cdf_o = np.cumsum(np.ones_like(A), dtype=np.float32)\n    W = np.zeros",
+     ["test_gravity_origins_and_destinations_follow_the_weights"]),
+    ("route_takes_the_last_least_cost_successor", "routing.py",
+     "                    nxt = f\n                    break", "                    nxt = f",
+     ["test_routes_are_the_lexicographically_smallest_least_cost_paths"]),
+    ("radiation_drops_the_destination_population", "routing.py",
+     "den = np.float32(np.float32(m[i] + s[j]) * np.float32(np.float32(m[i] + m[j]) + s[j]))\n"
+     "            W[i, j] = np.float32(num / den)\n    return W\n\n\ndef radiation_weights_vec",
+     "den = np.float32(np.float32(m[i] + s[j]) * np.float32(np.float32(m[i]) + s[j]))\n"
+     "            W[i, j] = np.float32(num / den)\n    return W\n\n\ndef radiation_weights_vec",
+     ["test_radiation_weights_closed_form_on_a_line"]),
+]
+
+_FAILED = re.compile(r"^FAILED \S+::(\w+)")
+
+
+def _copy_oracle(dst):
+    """oracle/'s sources (no built library, no caches) under dst/oracle."""
+    src = os.path.join(ROOT, "oracle")
+    os.makedirs(os.path.join(dst, "oracle"))
+    for f in os.listdir(src):
+        if f.endswith((".py", ".c", ".h")):
+            shutil.copy(os.path.join(src, f), os.path.join(dst, "oracle", f))
+
+
+def _plant(dst, fname, old, new):
+    path = os.path.join(dst, "oracle", fname)
+    text = open(path).read()
+    assert text.count(old) == 1, f"{fname}: the text to change must occur exactly once: {old!r}"
+    with open(path, "w") as f:
+        f.write(text.replace(old, new))
+
+
+def _child_env():
+    # the child runs in the scratch directory, which python -m puts first on sys.path, so
+    # `import oracle` finds the copy; this tree comes after it for the package and tests
+    env = dict(os.environ)
+    env["PYTHONPATH"] = ROOT
+    env["OMP_NUM_THREADS"] = "1"
+    env.pop("PYTEST_ADDOPTS", None)
+    return env
+
+
+def _run_pins(dst):
+    """Run the pin files against the oracle copy in dst; (exit code, failed test names, tail)."""
+    args = [sys.executable, "-m", "pytest", "-q", "-rf", "-p", "no:cacheprovider", "--rootdir", ROOT,
+            "-c", os.path.join(ROOT, "pytest.ini"), "-m", "not gpu"]
+    args += [os.path.join(ROOT, f) for f in PIN_FILES]
+    r = subprocess.run(args, cwd=dst, env=_child_env(), capture_output=True, text=True, timeout=900)
+    failed = sorted({m.group(1) for m in map(_FAILED.match, r.stdout.splitlines()) if m})
+    return r.returncode, failed, r.stdout[-3000:] + r.stderr[-2000:]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    """The control copy and every planted mistake, run concurrently (one child each)."""
+    jobs = {}
+    ctl = str(tmp_path_factory.mktemp("control"))
+    _copy_oracle(ctl)
+    jobs["control"] = ctl
+    for name, fname, old, new, _ in MUTANTS:
+        d = str(tmp_path_factory.mktemp(name))
+        _copy_oracle(d)
+        _plant(d, fname, old, new)
+        jobs[name] = d
+    # the child imports the copy, not this tree's oracle
+    r = subprocess.run([sys.executable, "-c", "import oracle; print(oracle.__file__)"], cwd=ctl,
+                       env=_child_env(), capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and os.path.realpath(r.stdout.strip()).startswith(os.path.realpath(ctl)), r
+    with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        res = dict(zip(jobs, ex.map(_run_pins, jobs.values())))
+    return res
+
+
+def test_control_copy_passes_every_pin(outcomes):
+    code, failed, tail = outcomes["control"]
+    assert code == 0 and not failed, tail
+
+
+@pytest.mark.parametrize("name, fname, old, new, catchers", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(outcomes, name, fname, old, new, catchers):
+    code, failed, tail = outcomes[name]
+    # exit code 1: tests ran and some failed (not a crash, a collection error or a timeout)
+    assert code == 1, f"{name}: pins exit code {code}\n{tail}"
+    assert set(catchers) & set(failed), f"{name}: caught only by {failed}, not by {catchers}\n{tail}"

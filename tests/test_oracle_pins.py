@@ -107,6 +107,25 @@ def test_free_road_accelerates_to_v0(oracle_lib):
     np.testing.assert_allclose(adv, 0.5 * (vs[1:] + vs[:-1]) * P["dt"], atol=1e-9)
 
 
+def test_motion_stop_within_the_step_and_gap_clamp(oracle_lib):
+    """The ballistic update's two corner cases on a one-lane road behind a stopped leader,
+    where IDM asks for far more than a_min = -9 m/s^2 and the clamp to a_min holds:
+    at 3 m/s and a 3 m gap the vehicle stops within the step after v^2 / (2 |a_min|) =
+    0.5 m; at 15 m/s and a 4 m gap the ballistic distance 0.5 (15 + 6) = 10.5 m is cut to
+    the gap and the speed to gap / dt = 4 m/s."""
+    net = netkit.line(3, 300.0, 1)
+    L, am = P["veh_len"], P["a_min"]
+    for v, gap, d_want, v_want in ((3.0, 3.0, 9.0 / 18.0, 0.0), (15.0, 4.0, 4.0, 4.0)):
+        dem = netkit.vehicles([0, 0], [100.0, 100.0 + L + gap], [v, 0.0], [[0, 1]] * 2)
+        o = oracle_lib.Oracle(net, dem, P)
+        x0 = o.state()["x"][0]
+        _, d = o.step(debug=True)
+        assert d["lead_id"][0] == 1 and d["a_use"][0] == am
+        st = o.state()
+        assert st["x"][0] - x0 == pytest.approx(d_want, abs=1e-12)
+        assert st["v"][0] == pytest.approx(v_want, abs=1e-12)
+
+
 def test_stop_at_long_red_reaches_standstill_gap(oracle_lib):
     net = synth.grid_network(3, 3, 1, 300.0, green=200, yellow=3, offset="zero")
     o0 = oracle_lib.Oracle(net, netkit.vehicles([], [], [], []), P)
@@ -152,16 +171,25 @@ def test_signal_table_closed_form(oracle_lib):
 
 
 def test_signal_offsets_shift_the_table(oracle_lib):
-    net = synth.grid_network(4, 4, 1, 300.0, green=30, yellow=3, offset="wave")
-    o = oracle_lib.Oracle(net, netkit.vehicles([], [], [], []), P)
-    for c in range(net.n_ctrl):
-        lanes = np.nonzero(net.lane_ctrl == c)[0]
-        n = net.ctrl_node[c]
-        off = ((n % 4) + (n // 4)) * 22 % (net.ctrl_nphase[c] * 33)
-        assert net.ctrl_offset[c] == off
-        for l in lanes[:2]:
-            for t in range(0, 70, 7):
-                assert o.signal_state(l, t) == o.signal_state(l, t + 66)
+    """An offset of o seconds advances a controller's plan by o: with the green-wave
+    offsets, a lane's state at t is the state the same lane has at t + o in the same grid
+    with every offset 0 (whose table the closed-form pin above fixes)."""
+    wave = synth.grid_network(4, 4, 1, 300.0, green=30, yellow=3, offset="wave")
+    zero = synth.grid_network(4, 4, 1, 300.0, green=30, yellow=3, offset="zero")
+    np.testing.assert_array_equal(wave.lane_ctrl, zero.lane_ctrl)
+    np.testing.assert_array_equal(wave.lane_group, zero.lane_group)
+    ow = oracle_lib.Oracle(wave, netkit.vehicles([], [], [], []), P)
+    oz = oracle_lib.Oracle(zero, netkit.vehicles([], [], [], []), P)
+    shifted = 0
+    for c in range(wave.n_ctrl):
+        n = wave.ctrl_node[c]
+        off = ((n % 4) + (n // 4)) * 22 % (wave.ctrl_nphase[c] * 33)
+        assert wave.ctrl_offset[c] == off and zero.ctrl_offset[c] == 0
+        shifted += off != 0
+        for l in np.nonzero(wave.lane_ctrl == c)[0]:
+            for t in range(140):
+                assert ow.signal_state(int(l), t) == oz.signal_state(int(l), t + int(off)), (c, l, t)
+    assert shifted > 0
 
 
 def test_yellow_stop_rule(oracle_lib):
@@ -251,6 +279,16 @@ def test_mobil_safety_criteria(oracle_lib):
     # conflict guard: follower 9.5 m behind at 9 m/s needs 9 + a_max/2 = 10 m
     d = _two_lane_case([0, 0, 1], [100.0, stopped_leader, 85.5], [5.0, 0.0, 9.0])
     assert d["lc_cand"][0] == 1 and d["lc_dir"][0] == 0
+    # the guard alone: a changer at 12 m/s closes so fast on a follower at 2 m/s that the
+    # follower's IDM desired gap is s0 (v T + v dv / (2 sqrt(a b)) = 3 - 3.33 < 0), so at a
+    # gap g its deceleration a_max (1 - (2/13.9)^4 - (s0/g)^2) is mild for g >= 2.25 m; the
+    # guard v_F dt + a_max dt^2 / 2 = 3 m still rejects g = 2.5 m and admits g = 3.5 m
+    am, s0, L = P["idm_a"], P["idm_s0"], P["veh_len"]
+    for g, allowed in ((2.5, False), (3.5, True)):
+        assert am * (1 - (2.0 / 13.9) ** 4 - (s0 / g) ** 2) > -P["mobil_bsafe"]
+        d = _two_lane_case([0, 0, 1], [100.0, stopped_leader, 100.0 - L - g], [12.0, 0.0, 2.0])
+        assert d["lc_cand"][0] == 1 and d["tau_foll"][0] == 2
+        assert d["lc_dir"][0] == (+1 if allowed else 0), g
 
 
 def test_mobil_zones_and_gate(oracle_lib):
@@ -565,7 +603,8 @@ def test_max_pressure_switches_to_the_loaded_phase(oracle_lib):
 
 def test_max_pressure_holds_the_green_phase_on_ties(oracle_lib):
     """No vehicle anywhere near the controllers: every pressure is 0 and every controller
-    keeps phase 0 green through many decisions (a fixed-time plan would have cycled)."""
+    keeps its green phase through many decisions (a fixed-time plan would have cycled),
+    phase 0 from the start and phase 1 once set to it."""
     import oracle
     net = synth.grid_network(3, 3, 2, 200.0, 30, 3, "zero")
     e01 = int(np.nonzero((net.edge_from == 0) & (net.edge_to == 1))[0][0])
@@ -574,6 +613,12 @@ def test_max_pressure_holds_the_green_phase_on_ties(oracle_lib):
     for t in range(60):
         assert (o.ctrl_state() == np.array([0, -1, 0])).all()
         o.step()
+    # a tie keeps the phase that is green, not the lowest: every controller set to phase 1
+    # holds it through six more decisions
+    o.set_ctrl_state(np.tile([1, -1, 0], (net.n_ctrl, 1)))
+    for t in range(60):
+        o.step()
+        assert (o.ctrl_state() == np.array([1, -1, 0])).all()
 
 
 def _mp_brute(net, counts, cs_prev, t, interval):
@@ -818,6 +863,40 @@ def test_departures_fifo_and_room(oracle_lib):
     assert order == list(range(n))
 
 
+def test_departure_waits_for_its_time(oracle_lib):
+    """A trip enters at the step whose clock equals its departure time (on an empty lane
+    there is room at once): waiting before it, inserted by it, active after it."""
+    net = netkit.line(3, 300.0, 1)
+    dem = netkit.vehicles([-1], [0.0], [0.0], [[0, 1]], t_dep=[5])
+    o = oracle_lib.Oracle(net, dem, P)
+    for t in range(8):
+        assert o.state()["t"] == t
+        assert o.state()["status"][0] == (0 if t <= 5 else 1), t
+        _, d = o.step(debug=True)
+        assert d["inserted"][0] == (1 if t == 5 else 0), t
+
+
+def test_travel_time_is_the_arrival_clock_minus_the_departure(oracle_lib):
+    """Trip travel times counted by the oracle against the clock seen from outside: a trip
+    that finishes during the step at clock t arrives at t + 1, and the summed travel time
+    is the sum over arrived trips of that arrival clock minus the departure time."""
+    net, dem = synth.small_grid_workload(2)
+    o = oracle_lib.Oracle(net, dem, P)
+    arrive = {}
+    for _ in range(900):
+        before = o.state()
+        o.step()
+        after = o.state()
+        for i in np.nonzero((after["status"] == 2) & (before["status"] != 2))[0]:
+            arrive[int(i)] = after["t"]
+    assert len(arrive) > 50
+    st = o.state()
+    assert all(st["t_arr"][i] == t for i, t in arrive.items())
+    m = o.metrics()
+    assert m["arrived"] == len(arrive)
+    assert m["sum_tt"] == sum(t - int(dem.t_dep[i]) for i, t in arrive.items())
+
+
 def test_metrics_window_sums(oracle_lib):
     net, dem = synth.small_grid_workload(1)
     o = oracle_lib.Oracle(net, dem, dict(P, window=50), n_windows=4)
@@ -852,6 +931,21 @@ def test_mobil_politeness_terms_closed_form(oracle_lib):
     want = free_gain + P["mobil_p"] * (dF + dO)
     assert d["incentive"][0] == pytest.approx(want, abs=1e-5)
     assert d["lc_dir"][0] == +1
+
+
+def test_mobil_politeness_with_a_target_leader(oracle_lib):
+    """Everybody stopped (v = 0: s* = s0, a = a_max (1 - (s0/s)^2) whatever the leader
+    does): the changer c 2.5 m behind its own leader, a target leader 3 m ahead of it and a
+    new follower F 3 m behind it in the target lane.  F's old gap runs to the target leader
+    (3 + L + 3 m); its new gap is the 3 m to c."""
+    xc, L, s0, am = 100.0, P["veh_len"], P["idm_s0"], P["idm_a"]
+    d = _two_lane_case([0, 0, 1, 1], [xc, xc + L + 2.5, xc + L + 3.0, xc - L - 3.0], [0.0] * 4)
+    assert d["tau_lead"][0] == 2 and d["tau_foll"][0] == 3 and d["old_foll"][0] == -1
+    idm0 = lambda gap: am * (1 - (s0 / gap) ** 2)
+    want = idm0(3.0) - idm0(2.5) + P["mobil_p"] * (idm0(3.0) - idm0(3.0 + L + 3.0))
+    assert d["a_own"][0] == pytest.approx(idm0(2.5), abs=1e-12)
+    assert d["incentive"][0] == pytest.approx(want, abs=1e-9)
+    assert d["lc_dir"][0] == (+1 if want > P["mobil_th"] else 0)
 
 
 def test_merge_projection_leader(oracle_lib):

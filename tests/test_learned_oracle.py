@@ -321,3 +321,27 @@ def test_bf16_gradient_rounds_the_output_gradient():
     assert g["W3"][0, 0] == mlp.bf16(-2.0 / 3.0) == -0.66796875
     assert g["W3"][1, 0] == mlp.bf16(1.0 / 3.0) == 0.333984375
     np.testing.assert_allclose(g["b3"], [-2.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0], rtol=1e-15)
+
+
+def test_bf16_gradient_rounds_the_hidden_gradient():
+    """Uniform outputs (logits all 0) and a last layer whose column 0 is (0, 1, 1/2): the
+    gradient reaching hidden unit 0 is 1/3 + 1/6 in BF16 output gradients, 0.333984375 +
+    0.1669921875 = 0.5009765625 = (1 + 2^-9) / 2, which is not a BF16 value; the kernel's
+    operand for the weight gradient of layer 2 is its rounding, 0.5, so dW2[0, 0] = 0.5 h1
+    with h1 = 1."""
+    p = {k: np.zeros(s) for k, s in mlp.SHAPES}
+    p["W1"][0, 0] = 1.0
+    p["W2"][0, 0] = 1.0
+    p["W3"][1, 0] = 1.0
+    p["W3"][2, 0] = 0.5
+    p["b3"][1] = -1.0
+    p["b3"][2] = -0.5
+    theta = mlp.pack(p)
+    X = np.zeros((1, 16))
+    X[0, 0] = 1.0
+    z, _, _ = mlp.forward_bf16(theta, X)
+    assert np.array_equal(z, np.zeros((1, 3)))
+    g = mlp.unpack(mlp.grad_bf16(theta, X, np.array([0]), np.ones(3)))
+    assert mlp.bf16(0.5009765625) == 0.5
+    assert g["W2"][0, 0] == 0.5
+

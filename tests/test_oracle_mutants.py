@@ -68,6 +68,15 @@ MUTANTS = [
     ("fan_out_ignores_the_edge_after_next", "moss_oracle.c",
      "    if (connects(s, tg, en2)) return il;\n", "    return il;\n",
      ["test_step_leaders_and_target_neighbours_match_brute_force"]),
+    ("lookahead_lane_cap_one_short", "moss_oracle.c",
+     "if (hop + 1 >= HOP_CAP) {", "if (hop + 2 >= HOP_CAP) {",
+     ["test_lookahead_ends_at_the_twelfth_lane"]),
+    ("merge_gap_keeps_the_length", "moss_oracle.c",
+     "double g = (dc - dj) - L;", "double g = (dc - dj);",
+     ["test_merge_projection_leader"]),
+    ("merge_takes_the_farther_leader", "moss_oracle.c",
+     "if (r.kind == K_FREE || g < r.gap) {", "if (r.kind == K_FREE || g > r.gap) {",
+     ["test_step_leaders_and_target_neighbours_match_brute_force"]),
     # R9: fixed-time signals
     ("signal_offset_sign", "moss_oracle.c",
      "int tau = ((t + s->net.ctrl_offset[c]) % cyc + cyc) % cyc;",
@@ -76,6 +85,9 @@ MUTANTS = [
     ("signal_green_one_second_long", "moss_oracle.c",
      "return (tau % (g + y)) < g ? SIG_GREEN : SIG_YELLOW;",
      "return (tau % (g + y)) <= g ? SIG_GREEN : SIG_YELLOW;",
+     ["test_signal_table_closed_form"]),
+    ("signal_phase_by_the_green_time_alone", "moss_oracle.c",
+     "int k = tau / (g + y);", "int k = tau / g;",
      ["test_signal_table_closed_form"]),
     # R5: stop lines (yellow: stop when the vehicle can)
     ("yellow_rule_reversed", "moss_oracle.c",
@@ -113,6 +125,15 @@ MUTANTS = [
     ("threshold_jitter_one_sided", "moss_oracle.c",
      "return p->th + p->th_jitter * (2.0 * u - 1.0);", "return p->th + p->th_jitter * u;",
      ["test_mobil_threshold_jitter_is_uniform_over_trips"]),
+    ("mandatory_tie_goes_to_the_upper_lane", "moss_oracle.c",
+     "abs(q - idx) < bestd) { bestd", "abs(q - idx) <= bestd) { bestd",
+     ["test_mandatory_change_tie_goes_to_the_lower_lane"]),
+    ("target_lane_end_never_blocks", "moss_oracle.c",
+     "} else if (end_blocks(s, tau, en, x, v, flag)) {", "} else if (0) {",
+     ["test_target_lane_end_at_red_is_an_obstacle"]),
+    ("target_lane_speed_limit_ignored", "moss_oracle.c",
+     "r.a_new = idm(s, v, fmin(v0, s->lane_vmax[tau]),", "r.a_new = idm(s, v, v0,",
+     ["test_mobil_uses_the_target_lanes_limit"]),
     ("target_leader_and_follower_transposed", "moss_oracle.c",
      "int Lt = j < cnt ? o[j] : -1;\n  int Ft = j > 0 ? o[j - 1] : -1;",
      "int Lt = j > 0 ? o[j - 1] : -1;\n  int Ft = j < cnt ? o[j] : -1;",
@@ -136,6 +157,18 @@ MUTANTS = [
     ("gap_clamp_keeps_the_speed", "moss_oracle.c",
      "      d = dmax;\n      vn = fmin(vn, d / p->dt);", "      d = dmax;",
      ["test_motion_stop_within_the_step_and_gap_clamp"]),
+    ("no_speed_cap", "moss_oracle.c",
+     "vn = fmin(vraw, p->v_max);", "vn = vraw;",
+     ["test_speed_is_capped_at_v_max"]),
+    ("changer_moves_with_the_prospective_acceleration", "moss_oracle.c",
+     "double a_use = lc.dir ? fmin(a_c, lc.a_new) : a_c;", "double a_use = lc.dir ? lc.a_new : a_c;",
+     ["test_mobil_incentive_is_free_gain_with_empty_target"]),
+    ("changer_not_held_at_its_lane_end", "moss_oracle.c",
+     "      gmin = fmin(gmin, len - x);\n", "",
+     ["test_changer_stops_at_its_lane_end"]),
+    ("junction_transfer_keeps_the_route_cursor", "moss_oracle.c",
+     "            nrp += 1;\n", "",
+     ["test_small_grid_run_invariants"]),
     ("retires_one_edge_early", "moss_oracle.c",
      "if (!is_internal(s, l) && route_at(s, c, s->rp[c] + 1) < 0) {",
      "if (!is_internal(s, l) && route_at(s, c, s->rp[c] + 2) < 0) {",
@@ -157,6 +190,12 @@ MUTANTS = [
     ("arrival_rear_without_the_length", "moss_oracle.c",
      "arr_min[nl] = fmin(arr_min[nl], s->n_x[c] - L);", "arr_min[nl] = fmin(arr_min[nl], s->n_x[c]);",
      ["test_small_grid_run_invariants"]),
+    ("departure_room_ignores_s0_behind_arrivals", "moss_oracle.c",
+     "double m = arr_min[l] - (L + p->s0);", "double m = arr_min[l] - L;",
+     ["test_departure_room_counts_the_arrivals_of_the_step"]),
+    ("departures_enter_a_closed_lane", "moss_oracle.c",
+     "    if (s->lane_closed[l]) continue;   /* R14: the queue waits */\n", "",
+     ["test_departures_wait_on_a_closed_lane"]),
     # R3: merge projection
     ("merge_projection_order_reversed", "moss_oracle.c",
      "if (dj < dc || (dj == dc && j < c)) { found = j; break; }",
@@ -176,6 +215,12 @@ MUTANTS = [
     ("max_pressure_counts_closed_links", "moss_oracle.c",
      "if (s->link_off[k]) continue;   /* R17 */\n        const int il", "const int il",
      ["test_max_pressure_skips_closed_links"]),
+    ("max_pressure_counts_the_junction_lane", "moss_oracle.c",
+     "const int m = s->net.succ_lane[s->net.succ_off[il]];", "const int m = il;",
+     ["test_max_pressure_run_matches_brute_force_and_never_runs_red"]),
+    ("max_pressure_yellow_one_step_short", "moss_oracle.c",
+     "s->mp_yend[c] = t + s->net.ctrl_yellow[c];", "s->mp_yend[c] = t + s->net.ctrl_yellow[c] - 1;",
+     ["test_max_pressure_run_matches_brute_force_and_never_runs_red"]),
     # R14: lane limits and closures
     ("speed_limit_ignored", "moss_oracle.c",
      "return fmin((double)s->v0[c], s->lane_vmax[l]);", "return (double)s->v0[c];",
@@ -217,6 +262,9 @@ MUTANTS = [
     ("loss_weights_not_normalised", "mlp.py",
      "dz *= (w / W)[:, None]", "dz *= w[:, None]",
      ["test_gradient_matches_central_differences"]),
+    ("bf16_gradient_keeps_the_hidden_gradient_unrounded", "mlp.py",
+     "da2 = bf16((db @ W3) * (h2 > 0))", "da2 = (db @ W3) * (h2 > 0)",
+     ["test_bf16_gradient_rounds_the_hidden_gradient"]),
     ("adam_without_second_moment_correction", "mlp.py",
      "vh = v / (1 - b2 ** t)", "vh = v",
      ["test_adam_first_step_is_lr_times_sign"]),
@@ -232,6 +280,9 @@ MUTANTS = [
     ("route_takes_the_last_least_cost_successor", "routing.py",
      "                    nxt = f\n                    break", "                    nxt = f",
      ["test_routes_are_the_lexicographically_smallest_least_cost_paths"]),
+    ("uniform_draws_one_bit_short", "routing.py",
+     "return splitmix64((seed ^ salt ^ k) % 2 ** 64) >> 40", "return splitmix64((seed ^ salt ^ k) % 2 ** 64) >> 41",
+     ["test_gravity_origins_and_destinations_follow_the_weights"]),
     ("radiation_drops_the_destination_population", "routing.py",
      "den = np.float32(np.float32(m[i] + s[j]) * np.float32(np.float32(m[i] + m[j]) + s[j]))\n"
      "            W[i, j] = np.float32(num / den)\n    return W\n\n\ndef radiation_weights_vec",

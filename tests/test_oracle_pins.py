@@ -126,6 +126,57 @@ def test_motion_stop_within_the_step_and_gap_clamp(oracle_lib):
         assert st["v"][0] == pytest.approx(v_want, abs=1e-12)
 
 
+def test_speed_is_capped_at_v_max(oracle_lib):
+    """A lone vehicle whose desired speed (30 m/s) is above v_max (20 m/s) on a free ring
+    accelerates to v_max and stays there: the update caps v' at v_max."""
+    net = netkit.ring(200.0)
+    dem = netkit.ring_demand(net, np.array([10.0]), np.array([0.0]), 30.0)
+    o = oracle_lib.Oracle(net, dem, P)
+    vs = []
+    for _ in range(60):
+        o.step()
+        vs.append(o.state()["v"][0])
+    assert max(vs) == P["v_max"] and vs[-1] == P["v_max"] and vs[9] < P["v_max"]
+
+
+def test_changer_stops_at_its_lane_end(oracle_lib):
+    """A discretionary change 5 m before the lane end (the end zone set to 0): the own path
+    continues to a slower leader 30 m ahead on the next edge, the target lane is free, so
+    the vehicle changes; it moves at most to the end of its lane in that step, so at 10 m/s
+    its distance is cut to 5 m and its speed to 5 m/s."""
+    net = netkit.line(4, 300.0, 2)
+    l0, l1 = int(net.edge_lane0[0]), int(net.edge_lane0[1])
+    il = [int(net.succ_lane[k]) for k in range(net.succ_off[l0], net.succ_off[l0 + 1])
+          if net.succ_lane[net.succ_off[net.succ_lane[k]]] == l1][0]
+    x_lead = 30.0 - float(net.lane_len[il])     # own gap (5 + len(il) + x_lead) - L = 30 m
+    dem = netkit.vehicles([l0, l1], [300.0 - 5.0, x_lead], [10.0, 5.0], [[0, 1, 2], [1, 2]])
+    o = oracle_lib.Oracle(net, dem, dict(P, x_lc_end=0.0))
+    _, d = o.step(debug=True)
+    assert d["lead_id"][0] == 1 and d["s_own"][0] == pytest.approx(30.0, abs=1e-9)
+    assert d["lc_dir"][0] == +1 and d["a_use"][0] > 0.0
+    st = o.state()
+    assert st["lane"][0] == net.lane_left[l0]
+    assert st["x"][0] == 300.0 and st["v"][0] == pytest.approx(5.0, abs=1e-12)
+
+
+def test_lookahead_ends_at_the_twelfth_lane(oracle_lib):
+    """On a road of 25 m links (21 m junction lanes) with a 1 km look-ahead, an empty path
+    ends the look-ahead after 12 lanes, the own lane included: the end of the 12th lane is a
+    stopped obstacle at the summed lengths of the path."""
+    net = netkit.line(20, 25.0, 1)
+    l0 = int(net.edge_lane0[0])
+    dem = netkit.vehicles([l0], [5.0], [10.0], [list(range(19))])
+    o = oracle_lib.Oracle(net, dem, dict(P, d_look=1000.0))
+    _, d = o.step(debug=True)
+    path, cur = [l0], l0
+    while len(path) < 12:
+        k = [k for k in range(net.succ_off[cur], net.succ_off[cur + 1])][0]
+        cur = int(net.succ_lane[k])
+        path.append(cur)
+    want = (25.0 - 5.0) + float(np.sum(net.lane_len[path[1:]].astype(np.float64)))
+    assert d["lead_kind"][0] == 2 and d["s_own"][0] == pytest.approx(want, abs=1e-9)
+
+
 def test_stop_at_long_red_reaches_standstill_gap(oracle_lib):
     net = synth.grid_network(3, 3, 1, 300.0, green=200, yellow=3, offset="zero")
     o0 = oracle_lib.Oracle(net, netkit.vehicles([], [], [], []), P)
@@ -246,6 +297,8 @@ def test_mobil_incentive_is_free_gain_with_empty_target(oracle_lib):
     assert d["tau_lead"][0] == -1 and d["tau_foll"][0] == -1 and d["old_foll"][0] == -1
     assert d["incentive"][0] == pytest.approx(P["idm_a"] * (1 - (v / v0f) ** 4), abs=1e-6)
     assert d["lc_dir"][0] == +1
+    # a changer moves with the lower of its current and prospective accelerations
+    assert d["a_use"][0] == d["a_own"][0]
 
 
 def test_mobil_identical_lanes_no_change(oracle_lib):
@@ -387,6 +440,54 @@ def test_mandatory_change_toward_connecting_lane(oracle_lib):
     o2 = oracle.Oracle(net, dem, dict(P, p_lc=0.0))
     _, d2 = o2.step(debug=True)
     assert d2["lc_dir"][0] == +1    # mandatory changes bypass the random gate
+
+
+def test_mandatory_change_tie_goes_to_the_lower_lane(oracle_lib):
+    """Three lanes, the middle lane's links to the next edge closed: the two lanes that still
+    connect are equally near, and the lower index (the right lane) is the one to reach, so
+    the change waits for a step that allows moves to the right."""
+    net = netkit.line(3, 300.0, 3)
+    l0 = int(net.edge_lane0[0])
+    mid = l0 + 1
+    dem = netkit.vehicles([mid], [150.0], [10.0], [[0, 1]])
+    import oracle
+    for t0, want_cand, want_dir in ((0, 0, 0), (1, 1, -1)):
+        o = oracle.Oracle(net, dem, P)
+        o.set_lane_links([mid], [0])
+        st = o.state()
+        o.set_state(st["status"], st["lane"], st["x"], st["v"], st["rp"], t0)
+        _, d = o.step(debug=True)
+        assert d["lc_cand"][0] == want_cand and d["lc_dir"][0] == want_dir, t0
+    assert net.lane_right[mid] == l0
+
+
+def test_target_lane_end_at_red_is_an_obstacle(oracle_lib):
+    """A stopped vehicle 30 m before a red stop line, 3 m behind a stopped leader, with an
+    empty target lane that also ends at the red line: the prospective acceleration is IDM
+    against a stopped obstacle at the target lane's end (v = 0: a_max (1 - (s0/30)^2)), not
+    the free road, so the incentive is a_max s0^2 (1/9 - 1/900)."""
+    net = synth.grid_network(3, 3, 2, 300.0, green=200, yellow=3, offset="zero")
+    o0 = oracle_lib.Oracle(net, netkit.vehicles([], [], [], []), P)
+    L, s0, am = P["veh_len"], P["idm_s0"], P["idm_a"]
+    case = None
+    for e in range(net.n_edges):
+        l = int(net.edge_lane0[e])
+        if net.edge_to[e] != 4 or net.edge_nlanes[e] != 2 or o0.signal_state(l, 0) != 2:
+            continue
+        both = set(net.succ_edge[net.succ_off[l]:net.succ_off[l + 1]]) & set(
+            net.succ_edge[net.succ_off[l + 1]:net.succ_off[l + 2]])
+        if both:
+            case = (e, l, int(sorted(both)[0]))
+            break
+    assert case is not None
+    e, l, ex = case
+    assert o0.signal_state(l + 1, 0) == 2 and net.lane_left[l] == l + 1
+    xc = float(net.lane_len[l]) - 30.0
+    dem = netkit.vehicles([l, l], [xc, xc + L + 3.0], [0.0, 0.0], [[e, ex]] * 2)
+    o = oracle_lib.Oracle(net, dem, P)
+    _, d = o.step(debug=True)
+    assert d["lc_cand"][0] == 1 and d["tau_lead"][0] == -1 and d["lead_id"][0] == 1
+    assert d["incentive"][0] == pytest.approx(am * s0 ** 2 * (1 / 9.0 - 1 / 900.0), abs=1e-9)
 
 
 # ---------------------------------------------------------------------------------------
@@ -874,6 +975,33 @@ def test_departure_waits_for_its_time(oracle_lib):
         assert o.state()["status"][0] == (0 if t <= 5 else 1), t
         _, d = o.step(debug=True)
         assert d["inserted"][0] == (1 if t == 5 else 0), t
+
+
+def test_departure_room_counts_the_arrivals_of_the_step(oracle_lib):
+    """A vehicle crossing from a junction lane onto a departure lane lands 11 m in, so its
+    rear is 6 m from the lane start, less than L + s0 = 7 m: the departure due at that step
+    waits; at the next step the same vehicle, now the lane's rearmost in the snapshot, still
+    leaves no room; one step later it has moved on and the departure enters."""
+    net = netkit.line(4, 300.0, 1)
+    l0, l1 = int(net.edge_lane0[0]), int(net.edge_lane0[1])
+    il = int(net.succ_lane[net.succ_off[l0]])
+    assert int(net.succ_lane[net.succ_off[il]]) == l1
+    v, v0 = 12.0, 13.9
+    a = P["idm_a"] * (1 - (v / float(np.float32(v0))) ** 4)     # free road (nothing ahead)
+    d_step = 0.5 * (v + v + a * P["dt"]) * P["dt"]
+    x = float(net.lane_len[il]) - (d_step - 11.0)
+    dem = netkit.vehicles([il, -1], [x, 0.0], [v, 0.0], [[0, 1, 2], [1, 2]], v0=v0, t_dep=[0, 0])
+    o = oracle_lib.Oracle(net, dem, P)
+    assert o.departure_lane(1) == l1
+    _, d = o.step(debug=True)
+    st = o.state()
+    assert st["lane"][0] == l1 and st["x"][0] == pytest.approx(11.0, abs=1e-5)
+    assert d["inserted"][1] == 0 and st["status"][1] == 0
+    _, d = o.step(debug=True)
+    assert d["inserted"][1] == 0
+    assert o.state()["x"][0] - P["veh_len"] >= P["veh_len"] + P["idm_s0"]
+    _, d = o.step(debug=True)
+    assert d["inserted"][1] == 1
 
 
 def test_travel_time_is_the_arrival_clock_minus_the_departure(oracle_lib):

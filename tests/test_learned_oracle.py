@@ -58,16 +58,18 @@ def test_bf16_forward_equals_plain_forward_when_nothing_rounds():
 
 
 def test_bf16_forward_rounds_where_the_kernel_rounds():
-    """A network that doubles input 0 through a single path: an input of 1 + 2^-7 + 2^-9 is
-    rounded to 1 + 2^-7 on entry (not kept), and a hidden value 3 * (1 + 2^-7) = 3.0234375 is
-    rounded to 3.03125 (8 significant bits) before the next layer."""
+    """A network that triples input 0 through a single path: an input of 1 + 3 * 2^-9 is
+    rounded to 1 + 2^-7 on entry (kept unrounded, 3 * (1 + 3 * 2^-9) = 3.017578125 would
+    round to 3.015625), and the hidden value 3 * (1 + 2^-7) = 3.0234375, halfway between
+    3.015625 and 3.03125 (8 significant bits), is rounded to the even 3.03125 before the next
+    layer (kept, the logit would be 3.0234375)."""
     p = {k: np.zeros(s) for k, s in mlp.SHAPES}
     p["W1"][0, 0] = 3.0
     p["W2"][0, 0] = 1.0
     p["W3"][1, 0] = 1.0
     theta = mlp.pack(p)
     X = np.zeros((1, 16))
-    X[0, 0] = 1.0 + 2.0 ** -7 + 2.0 ** -9
+    X[0, 0] = 1.0 + 3 * 2.0 ** -9
     z, _, _ = mlp.forward_bf16(theta, X)
     assert z[0, 1] == 3.03125 and z[0, 0] == 0.0 and z[0, 2] == 0.0
 

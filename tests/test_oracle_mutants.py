@@ -77,6 +77,9 @@ MUTANTS = [
     ("merge_takes_the_farther_leader", "moss_oracle.c",
      "if (r.kind == K_FREE || g < r.gap) {", "if (r.kind == K_FREE || g > r.gap) {",
      ["test_step_leaders_and_target_neighbours_match_brute_force"]),
+    ("idm_without_the_a_min_clamp", "moss_oracle.c",
+     "return fmax(a, p->a_min);", "return a;",
+     ["test_motion_stop_within_the_step_and_gap_clamp"]),
     # R9: fixed-time signals
     ("signal_offset_sign", "moss_oracle.c",
      "int tau = ((t + s->net.ctrl_offset[c]) % cyc + cyc) % cyc;",
@@ -221,6 +224,9 @@ MUTANTS = [
     ("max_pressure_yellow_one_step_short", "moss_oracle.c",
      "s->mp_yend[c] = t + s->net.ctrl_yellow[c];", "s->mp_yend[c] = t + s->net.ctrl_yellow[c] - 1;",
      ["test_max_pressure_run_matches_brute_force_and_never_runs_red"]),
+    ("max_pressure_tie_goes_to_the_higher_phase", "moss_oracle.c",
+     "if (pr[ph] > pr[best]) best = ph;", "if (pr[ph] >= pr[best]) best = ph;",
+     ["test_max_pressure_tie_between_two_other_phases_goes_to_the_lower"]),
     # R14: lane limits and closures
     ("speed_limit_ignored", "moss_oracle.c",
      "return fmin((double)s->v0[c], s->lane_vmax[l]);", "return (double)s->v0[c];",
@@ -252,6 +258,9 @@ MUTANTS = [
     ("learned_input_12_reads_the_own_speed", "moss_oracle.c",
      "f[12] = O >= 0 ? s->v[O] / 20.0 : 0.0;", "f[12] = O >= 0 ? v / 20.0 : 0.0;",
      ["test_learned_inputs_follow_from_the_state"]),
+    ("learned_hidden_layer_drops_its_bias", "moss_oracle.c",
+     "a1[j] = acc + m->b1[j];", "a1[j] = acc;",
+     ["test_learned_logits_match_the_numpy_bf16_forward"]),
     # the network's gradient and optimiser (numpy)
     ("mlp_gradient_wrong_relu_mask", "mlp.py",
      "da1 = dh1 * (a1 > 0)\n    g[\"W1\"]", "da1 = dh1 * (a1 >= -1.0)\n    g[\"W1\"]",
@@ -265,6 +274,12 @@ MUTANTS = [
     ("bf16_gradient_keeps_the_hidden_gradient_unrounded", "mlp.py",
      "da2 = bf16((db @ W3) * (h2 > 0))", "da2 = (db @ W3) * (h2 > 0)",
      ["test_bf16_gradient_rounds_the_hidden_gradient"]),
+    ("margin_is_top_minus_lowest", "mlp.py",
+     "return s[:, -1] - s[:, -2], p.argmax(1)", "return s[:, -1] - s[:, 0], p.argmax(1)",
+     ["test_learned_logits_match_the_numpy_bf16_forward"]),
+    ("network_inputs_not_rounded", "mlp.py",
+     "    Xb = bf16(X)\n    u = 2.0 ** -22\n    near", "    Xb = X\n    u = 2.0 ** -22\n    near",
+     ["test_bf16_forward_rounds_where_the_kernel_rounds"]),
     ("adam_without_second_moment_correction", "mlp.py",
      "vh = v / (1 - b2 ** t)", "vh = v",
      ["test_adam_first_step_is_lr_times_sign"]),
@@ -283,6 +298,16 @@ MUTANTS = [
     ("uniform_draws_one_bit_short", "routing.py",
      "return splitmix64((seed ^ salt ^ k) % 2 ** 64) >> 40", "return splitmix64((seed ^ salt ^ k) % 2 ** 64) >> 41",
      ["test_gravity_origins_and_destinations_follow_the_weights"]),
+    ("route_cost_of_the_edge_left", "routing.py",
+     "csr_matrix((c[dst].astype(np.float64), (dst, src))", "csr_matrix((c[src].astype(np.float64), (dst, src))",
+     ["test_routes_are_the_lexicographically_smallest_least_cost_paths"]),
+    ("gravity_includes_the_origin_zone", "routing.py",
+     "if j == i or not np.isfinite(cost[i, j]):", "if not np.isfinite(cost[i, j]):",
+     ["test_gravity_origins_and_destinations_follow_the_weights"]),
+    ("radiation_departure_times_modulo_the_span", "routing.py",
+     "        td[k] = (_u24(splitmix64, seed, SALT_TIME, k) * int(t_span)) >> 24\n    return o, de, td\n\n\n# ----",
+     "        td[k] = _u24(splitmix64, seed, SALT_TIME, k) % int(t_span)\n    return o, de, td\n\n\n# ----",
+     ["test_departure_times_scale_with_the_span"]),
     ("radiation_drops_the_destination_population", "routing.py",
      "den = np.float32(np.float32(m[i] + s[j]) * np.float32(np.float32(m[i] + m[j]) + s[j]))\n"
      "            W[i, j] = np.float32(num / den)\n    return W\n\n\ndef radiation_weights_vec",

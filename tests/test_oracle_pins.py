@@ -722,6 +722,31 @@ def test_max_pressure_holds_the_green_phase_on_ties(oracle_lib):
         assert (o.ctrl_state() == np.array([1, -1, 0])).all()
 
 
+def test_max_pressure_tie_between_two_other_phases_goes_to_the_lower(oracle_lib):
+    """A controller of a Delaunay city with three or more phases, phase 0 green with empty
+    approaches, and phases 1 and 2 loaded to the same pressure (one approach lane each, the
+    counts inverse to the lanes' link counts, nothing downstream): the decision at t = 0
+    turns to phase 1, the lower index of the tie."""
+    import oracle
+    net = synth.delaunay_network(60, seed=3)
+    ctrl = next(c for c in range(net.n_ctrl) if net.ctrl_nphase[c] >= 3 and
+                {0, 1, 2} <= set(_center_lanes(net, c)))
+    groups = _center_lanes(net, ctrl)
+    la, lb = int(groups[1][0]), int(groups[2][0])
+    na, nb = (int(net.succ_off[l + 1] - net.succ_off[l]) for l in (la, lb))
+    lanes, xs, routes = [], [], []
+    for l, k in ((la, nb), (lb, na)):                 # pressures na * nb on both phases
+        assert 8.0 * k + 10.0 < net.lane_len[l]
+        for q in range(k):
+            lanes.append(l)
+            xs.append(float(net.lane_len[l]) - 10.0 - 8.0 * q)
+            routes.append([int(net.lane_edge[l]), int(net.succ_edge[net.succ_off[l]])])
+    dem = netkit.vehicles(lanes, xs, [0.0] * len(lanes), routes)
+    o = oracle.Oracle(net, dem, MP)
+    # the controllers' state at t = 0 includes that step's decision: phase 1 pending
+    assert o.ctrl_state()[ctrl].tolist()[:2] == [0, 1]
+
+
 def _mp_brute(net, counts, cs_prev, t, interval):
     """R13 restated with numpy over the network arrays, from the previous step's state."""
     cs = cs_prev.copy()

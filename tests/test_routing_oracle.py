@@ -215,3 +215,21 @@ def test_radiation_weights_vectorised_form_equals_the_loop(seed):
     b = routing.radiation_weights_vec(cost, m)
     assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
     assert (a > 0).sum() > Z * Z // 2
+
+
+def test_departure_times_scale_with_the_span():
+    """A departure time is the trip's uniform draw scaled to the span and rounded down, so
+    the same seed with twice the span gives every trip 2 t or 2 t + 1 (gravity and
+    radiation), and every time lies in [0, span)."""
+    net = netkit.line(10, 500.0, 1)
+    zones = np.array([0, 2, 4, 6, 8], np.int64)
+    m = np.array([2.0, 1.0, 4.0, 0.5, 3.0], np.float32)
+    n = 3000
+    for draw in (lambda T: routing.gravity_trips(net, zones, m, 2, n, T, 5, _sm),
+                 lambda T: routing.radiation_trips(net, zones, m, n, T, 5, _sm)):
+        _, _, t1 = draw(600)
+        _, _, t2 = draw(1200)
+        assert t1.min() >= 0 and t1.max() < 600 and t2.max() < 1200
+        assert np.all((t2 == 2 * t1) | (t2 == 2 * t1 + 1))
+        assert (t2 == 2 * t1).any() and (t2 == 2 * t1 + 1).any()
+

@@ -410,6 +410,9 @@ def run_ours(args):
                 "traffic": None if tpu is None else tpu * per_unit, "kernel": dom,
                 "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6400 GB/s",
                 "kernel_ms": dict(zip(KERNELS, [round(x, 5) for x in avg_ms])),
+                # each kernel's algorithmic bytes over its own time, as a fraction of the peak
+                "kernel_frac": {k: round(units[k] / (avg_ms[i] * 1e-3) / 1e9 / hbm, 4)
+                                for i, k in enumerate(KERNELS) if avg_ms[i] > 0},
                 "algorithmic_bytes": {"k_decide": f"{B_DECIDE_VEH} B/vehicle", "k_apply": f"{B_APPLY_VEH} B/vehicle",
                                       "k_lanes": f"{B_LANES_LANE} B/lane",
                                       "k_bucket": f"{B_BUCKET_VEH} B/vehicle + {B_BUCKET_MOVER} B/arrival"},

@@ -8,9 +8,12 @@ the failures.  A control copy with nothing planted must pass every pin, and the 
 be shown to import the copy, not this tree's oracle.  CPU only: the copies are plain C and
 numpy, built with gcc in the scratch directory.
 
-Mistakes that change nothing in FP64 are not listed: for example, the clamp of a position to
-the lane end when the own lane ends in an obstacle is a no-op in the oracle, since there
-x + (len - x) is exact for FP32 positions (it exists for rounding on the device)."""
+Mistakes that change nothing the pins can reach are not listed: the clamp of a position to
+the lane end when the own lane ends in an obstacle is a no-op in FP64 (x + (len - x) is
+exact for FP32 positions; it exists for rounding on the device); the id order of two
+vehicles at the same position on one lane applies only to states with a negative gap, which
+the state checks refuse; and a mistake that sends a vehicle to a lane that does not exist
+ends the child process instead of failing a pin."""
 import os
 import re
 import shutil
@@ -137,6 +140,12 @@ MUTANTS = [
     ("target_lane_speed_limit_ignored", "moss_oracle.c",
      "r.a_new = idm(s, v, fmin(v0, s->lane_vmax[tau]),", "r.a_new = idm(s, v, v0,",
      ["test_mobil_uses_the_target_lanes_limit"]),
+    ("level_target_vehicle_taken_as_the_leader", "moss_oracle.c",
+     "    if (s->x[o[mid]] > x) hi = mid; else lo = mid + 1;", "    if (s->x[o[mid]] >= x) hi = mid; else lo = mid + 1;",
+     ["test_level_vehicle_in_the_target_lane_is_the_follower"]),
+    ("lane_start_zone_ten_metres_too_long", "moss_oracle.c",
+     "  if (x < p->x_lc_min) return r;", "  if (x <= p->x_lc_min + 10.0) return r;",
+     ["test_mobil_zones_and_gate"]),
     ("target_leader_and_follower_transposed", "moss_oracle.c",
      "int Lt = j < cnt ? o[j] : -1;\n  int Ft = j > 0 ? o[j - 1] : -1;",
      "int Lt = j > 0 ? o[j - 1] : -1;\n  int Ft = j < cnt ? o[j] : -1;",
@@ -176,6 +185,13 @@ MUTANTS = [
      "if (!is_internal(s, l) && route_at(s, c, s->rp[c] + 1) < 0) {",
      "if (!is_internal(s, l) && route_at(s, c, s->rp[c] + 2) < 0) {",
      ["test_closed_lane_is_never_entered_until_reopened"]),
+    ("arrival_clock_off_by_one", "moss_oracle.c",
+     "      s->t_arr[c] = s->t + 1;\n      s->counters[1] += 1;", "      s->t_arr[c] = s->t;\n      s->counters[1] += 1;",
+     ["test_travel_time_is_the_arrival_clock_minus_the_departure"]),
+    ("edge_lane_transfer_advances_the_route_cursor", "moss_oracle.c",
+     "            nl = choose_succ(s, l, route_at(s, c, s->rp[c] + 1), route_at(s, c, s->rp[c] + 2));\n",
+     "            nl = choose_succ(s, l, route_at(s, c, s->rp[c] + 1), route_at(s, c, s->rp[c] + 2));\n            nrp += 1;\n",
+     ["test_small_grid_run_invariants"]),
     ("travel_time_off_by_one", "moss_oracle.c",
      "s->counters[2] += (int64_t)(s->t + 1 - s->t_dep[c]);", "s->counters[2] += (int64_t)(s->t - s->t_dep[c]);",
      ["test_travel_time_is_the_arrival_clock_minus_the_departure"]),
@@ -190,6 +206,20 @@ MUTANTS = [
     ("departs_a_step_early", "moss_oracle.c",
      "if (s->t_dep[h] > s->t) continue;", "if (s->t_dep[h] > s->t + 1) continue;",
      ["test_departure_waits_for_its_time"]),
+    ("inserted_front_at_the_lane_start", "moss_oracle.c",
+     "    s->x[h] = L;\n    s->v[h] = 0.0;", "    s->x[h] = 0.0;\n    s->v[h] = 0.0;",
+     ["test_departure_waits_for_its_time"]),
+    ("departure_lane_ignores_the_links", "moss_oracle.c",
+     "    if (connects(s, l0 + q, e1)) return l0 + q;\n  return -1;", "    if (1) return l0 + q;\n  return -1;",
+     ["test_departures_enter_the_first_lane_linked_to_the_next_edge"]),
+    ("departure_queue_latest_first", "moss_oracle.c",
+     "  if (s->t_dep[a] != s->t_dep[b]) return s->t_dep[a] < s->t_dep[b] ? -1 : 1;",
+     "  if (s->t_dep[a] != s->t_dep[b]) return s->t_dep[a] > s->t_dep[b] ? -1 : 1;",
+     ["test_departure_queue_is_first_in_first_out_by_departure_time"]),
+    ("departure_queue_tie_by_the_higher_id", "moss_oracle.c",
+     "  if (s->t_dep[a] != s->t_dep[b]) return s->t_dep[a] < s->t_dep[b] ? -1 : 1;\n  return a < b ? -1 : (a > b);",
+     "  if (s->t_dep[a] != s->t_dep[b]) return s->t_dep[a] < s->t_dep[b] ? -1 : 1;\n  return a > b ? -1 : (a < b);",
+     ["test_departures_fifo_and_room"]),
     ("arrival_rear_without_the_length", "moss_oracle.c",
      "arr_min[nl] = fmin(arr_min[nl], s->n_x[c] - L);", "arr_min[nl] = fmin(arr_min[nl], s->n_x[c]);",
      ["test_small_grid_run_invariants"]),

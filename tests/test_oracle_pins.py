@@ -346,12 +346,17 @@ def test_mobil_safety_criteria(oracle_lib):
 
 def test_mobil_zones_and_gate(oracle_lib):
     stopped = P["veh_len"] + 3.0
-    # too close to the lane start (x < x_lc_min)
+    # too close to the lane start (x < x_lc_min = 25 m), and just past it
     d = _two_lane_case([0, 0], [20.0, 20.0 + stopped], [5.0, 0.0])
     assert d["lc_cand"][0] == 0
-    # too close to the lane end for a discretionary change
+    d = _two_lane_case([0, 0], [26.0, 26.0 + stopped], [5.0, 0.0])
+    assert d["lc_cand"][0] == 1
+    # too close to the lane end for a discretionary change (len - x < x_lc_end = 20 m), and
+    # just outside that zone
     d = _two_lane_case([0, 0], [285.0, 285.0 + 2], [5.0, 0.0])
     assert d["lc_cand"][0] == 0
+    d = _two_lane_case([0, 0], [279.0, 279.0 + stopped], [5.0, 0.0])
+    assert d["lc_cand"][0] == 1
     # p_lc = 0: never considered
     d = _two_lane_case([0, 0], [100.0, 100.0 + stopped], [5.0, 0.0], p_lc=0.0)
     assert d["lc_cand"][0] == 0
@@ -991,7 +996,8 @@ def test_departures_fifo_and_room(oracle_lib):
 
 def test_departure_waits_for_its_time(oracle_lib):
     """A trip enters at the step whose clock equals its departure time (on an empty lane
-    there is room at once): waiting before it, inserted by it, active after it."""
+    there is room at once): waiting before it, inserted by it, active after it, standing
+    with its whole length on the lane (front at x = L) at rest."""
     net = netkit.line(3, 300.0, 1)
     dem = netkit.vehicles([-1], [0.0], [0.0], [[0, 1]], t_dep=[5])
     o = oracle_lib.Oracle(net, dem, P)
@@ -1000,6 +1006,50 @@ def test_departure_waits_for_its_time(oracle_lib):
         assert o.state()["status"][0] == (0 if t <= 5 else 1), t
         _, d = o.step(debug=True)
         assert d["inserted"][0] == (1 if t == 5 else 0), t
+        if t == 5:
+            st = o.state()
+            assert st["lane"][0] == net.edge_lane0[0] and st["x"][0] == P["veh_len"] and st["v"][0] == 0.0
+
+
+def test_departures_enter_the_first_lane_linked_to_the_next_edge(oracle_lib):
+    """On the 3-lane approaches of a grid (lane 0 serves only the right turn) every trip
+    enters the lowest-index lane of its first edge that links to its second edge."""
+    net = synth.grid_network(3, 3, 3, 300.0, green=30, yellow=3)
+    trips = []
+    for e in range(net.n_edges):
+        l0 = int(net.edge_lane0[e])
+        nxt = sorted({int(f) for q in range(int(net.edge_nlanes[e]))
+                      for f in net.succ_edge[net.succ_off[l0 + q]:net.succ_off[l0 + q + 1]]})
+        for f in nxt:
+            want = min(l0 + q for q in range(int(net.edge_nlanes[e]))
+                       if f in net.succ_edge[net.succ_off[l0 + q]:net.succ_off[l0 + q + 1]])
+            trips.append(([e, f], want))
+    assert any(w != int(net.edge_lane0[r[0]]) for r, w in trips)
+    dem = netkit.vehicles([-1] * len(trips), [0.0] * len(trips), [0.0] * len(trips), [r for r, _ in trips],
+                          t_dep=[3 * k for k in range(len(trips))])
+    o = oracle_lib.Oracle(net, dem, P)
+    lane_at_entry = {}
+    for _ in range(3 * len(trips) + 40):
+        _, d = o.step(debug=True)
+        st = o.state()
+        for i in np.nonzero(d["inserted"])[0]:
+            lane_at_entry[int(i)] = int(st["lane"][i])
+    assert len(lane_at_entry) == len(trips)
+    assert all(lane_at_entry[k] == w for k, (_, w) in enumerate(trips))
+
+
+def test_departure_queue_is_first_in_first_out_by_departure_time(oracle_lib):
+    """Five trips on one departure lane with departure times 8, 6, 4, 2, 0 (ids in the
+    opposite order) enter in the order of their departure times, each once there is room."""
+    net = netkit.line(3, 300.0, 1)
+    n = 5
+    dem = netkit.vehicles([-1] * n, [0.0] * n, [0.0] * n, [[0, 1]] * n, t_dep=[8, 6, 4, 2, 0])
+    o = oracle_lib.Oracle(net, dem, P)
+    order = []
+    for _ in range(80):
+        _, d = o.step(debug=True)
+        order += np.nonzero(d["inserted"])[0].tolist()
+    assert order == [4, 3, 2, 1, 0]
 
 
 def test_departure_room_counts_the_arrivals_of_the_step(oracle_lib):
@@ -1084,6 +1134,16 @@ def test_mobil_politeness_terms_closed_form(oracle_lib):
     want = free_gain + P["mobil_p"] * (dF + dO)
     assert d["incentive"][0] == pytest.approx(want, abs=1e-5)
     assert d["lc_dir"][0] == +1
+
+
+def test_level_vehicle_in_the_target_lane_is_the_follower(oracle_lib):
+    """A target-lane vehicle exactly level with the changer (same x) is its new follower,
+    not its leader (the leader is the first with x' > x): it sits at gap -L behind the
+    changer, so the conflict guard rejects the change."""
+    d = _two_lane_case([0, 0, 1, 1], [100.0, 108.0, 100.0, 130.0], [5.0, 0.0, 5.0, 5.0])
+    assert d["lc_cand"][0] == 1
+    assert d["tau_foll"][0] == 2 and d["tau_lead"][0] == 3
+    assert d["lc_dir"][0] == 0
 
 
 def test_mobil_politeness_with_a_target_leader(oracle_lib):

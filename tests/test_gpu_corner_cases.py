@@ -204,3 +204,45 @@ def test_conflict_guard_and_politeness_with_a_target_leader():
             assert gd["lc_dir"][0] == want
         else:
             assert abs(float(gd["incentive"][0]) - od["incentive"][0]) <= 1e-4
+
+
+def test_level_vehicle_in_the_target_lane_is_the_follower():
+    _need_gpu()
+    net = netkit.line(3, 300.0, 2)
+    dem = netkit.vehicles([0, 0, 1, 1], [100.0, 108.0, 100.0, 130.0], [5.0, 0.0, 5.0, 5.0], [[0, 1]] * 4)
+    sim, orc = _pair(net, dem, P)
+    st0, gd, gs, od, os_ = _steps(sim, orc, dem.n, 1)[0]
+    assert gd["lc_cand"][0] == 1 and gd["tau_foll"][0] == 2 and gd["tau_lead"][0] == 3
+    assert gd["lc_dir"][0] == 0
+
+
+def test_departures_by_time_and_onto_the_first_linked_lane():
+    _need_gpu()
+    # one departure lane, departure times 8, 6, 4, 2, 0: entries in time order
+    net = netkit.line(3, 300.0, 1)
+    dem = netkit.vehicles([-1] * 5, [0.0] * 5, [0.0] * 5, [[0, 1]] * 5, t_dep=[8, 6, 4, 2, 0])
+    sim, orc = _pair(net, dem, P)
+    order = []
+    for r in _steps(sim, orc, dem.n, 60):
+        order += np.nonzero(r[1]["inserted"])[0].tolist()
+    assert order == [4, 3, 2, 1, 0]
+    # 3-lane approaches whose lane 0 serves only the right turn: every trip enters the
+    # lowest lane of its first edge linked to its second edge
+    net = synth.grid_network(3, 3, 3, 300.0, green=30, yellow=3)
+    trips = []
+    for e in range(net.n_edges):
+        l0 = int(net.edge_lane0[e])
+        links = lambda q: net.succ_edge[net.succ_off[l0 + q]:net.succ_off[l0 + q + 1]]
+        for f in sorted({int(f) for q in range(int(net.edge_nlanes[e])) for f in links(q)}):
+            trips.append(([e, f], min(l0 + q for q in range(int(net.edge_nlanes[e])) if f in links(q))))
+    n = len(trips)
+    dem = netkit.vehicles([-1] * n, [0.0] * n, [0.0] * n, [r for r, _ in trips], t_dep=[2 * k for k in range(n)])
+    sim, orc = _pair(net, dem, P)
+    entry = {}
+    for r in _steps(sim, orc, dem.n, 2 * n + 20):
+        gs = r[2]
+        lane = np.full(n, -1)
+        lane[gs["id"]] = gs["lane"]
+        for i in np.nonzero(r[1]["inserted"])[0]:
+            entry[int(i)] = int(lane[i])
+    assert len(entry) == n and all(entry[k] == w for k, (_, w) in enumerate(trips))

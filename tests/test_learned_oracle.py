@@ -347,3 +347,33 @@ def test_bf16_gradient_rounds_the_hidden_gradient():
     assert mlp.bf16(0.5009765625) == 0.5
     assert g["W2"][0, 0] == 0.5
 
+
+
+def test_flag_rule_rounds_a_boundary_value_the_other_way():
+    """The flag rule of the learned decision (oracle/mlp.flip_sensitivity) on a hand-built
+    network: input 1 + 3 * 2^-9 enters as 1 + 2^-7, and the hidden value 3 (1 + 2^-7) =
+    3.0234375 lies exactly halfway between the BF16 neighbours 3.015625 and 3.03125, so it is
+    flagged and rounded the other way alone: logit 1 moves from 3.03125 to 3.015625 (2^-6),
+    which the logit bound gains on top of the last layer's accumulation bound, and the margin
+    moves by the matching softmax difference; the decision changes only when the fallback
+    threshold lies between the two margins.  With input 1 nothing lies near a boundary."""
+    p = {k: np.zeros(s) for k, s in mlp.SHAPES}
+    p["W1"][0, 0] = 3.0
+    p["W2"][0, 0] = 1.0
+    p["W3"][1, 0] = 1.0
+    theta = mlp.pack(p)
+    X = np.zeros((2, 16))
+    X[0, 0] = 1.0 + 3 * 2.0 ** -9
+    X[1, 0] = 1.0
+    u = 2.0 ** -22
+    z, m, c, zb, msens, changed = mlp.flip_sensitivity(theta, X, 0.2)
+    assert np.array_equal(z, [[0.0, 3.03125, 0.0], [0.0, 3.0, 0.0]]) and np.array_equal(c, [1, 1])
+    marg = lambda l1: (np.exp(l1) - 1.0) / (np.exp(l1) + 2.0)     # softmax p1 - p0 at (0, l1, 0)
+    np.testing.assert_allclose(m, [marg(3.03125), marg(3.0)], rtol=1e-12)
+    acc = lambda l1: 65 * u * np.array([0.0, l1, 0.0])            # (K + 1) u (|h2| |W3| + |b3|)
+    np.testing.assert_allclose(zb[0], acc(3.03125) + [0.0, 2.0 ** -6, 0.0], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(zb[1], acc(3.0), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(msens, [marg(3.03125) - marg(3.015625), 0.0], rtol=1e-9, atol=1e-15)
+    assert not changed.any()
+    thr = 0.5 * (marg(3.03125) + marg(3.015625))                  # between the two margins
+    assert mlp.flip_sensitivity(theta, X, thr)[5].tolist() == [True, False]

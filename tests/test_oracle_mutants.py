@@ -310,6 +310,19 @@ MUTANTS = [
     ("network_inputs_not_rounded", "mlp.py",
      "    Xb = bf16(X)\n    u = 2.0 ** -22\n    near", "    Xb = X\n    u = 2.0 ** -22\n    near",
      ["test_bf16_forward_rounds_where_the_kernel_rounds"]),
+    ("flag_rule_tests_the_rounded_hidden_value", "mlp.py",
+     "n1, alt1 = _near_alt(np.maximum(a1, 0.0), h1,", "n1, alt1 = _near_alt(h1, h1,",
+     ["test_flag_rule_rounds_a_boundary_value_the_other_way"]),
+    ("flag_rule_always_rounds_up", "mlp.py",
+     "alt = np.sign(r) * np.where(n_up, up, dn)", "alt = np.sign(r) * up",
+     ["test_flag_rule_rounds_a_boundary_value_the_other_way"]),
+    ("flag_rule_logit_bound_ignores_the_changes", "mlp.py",
+     "        np.add.at(zb, s, np.abs(z2 - z[s]))\n", "        pass\n",
+     ["test_flag_rule_rounds_a_boundary_value_the_other_way"]),
+    ("flag_rule_accumulation_bound_of_the_wrong_layer", "mlp.py",
+     "    zb = 65 * u * (np.abs(h2) @ np.abs(W3).T + np.abs(b3))\n    m, c = margin_class(z)",
+     "    zb = 17 * u * (np.abs(h2) @ np.abs(W3).T + np.abs(b3))\n    m, c = margin_class(z)",
+     ["test_flag_rule_rounds_a_boundary_value_the_other_way"]),
     ("adam_without_second_moment_correction", "mlp.py",
      "vh = v / (1 - b2 ** t)", "vh = v",
      ["test_adam_first_step_is_lr_times_sign"]),

@@ -1,10 +1,13 @@
-"""The benchmark's command-line contract on the CPU: the reference arm (the oracle on the host
-cores) prints one JSON line with the keys the contract names, and too few warm-up steps are
-refused.  The GPU arm's line is checked on the GPU machine by running bench.py itself."""
+"""The benchmark's command-line contract.  On the CPU: the reference arm (the oracle on the
+host cores) prints one JSON line with the keys the contract names, and too few warm-up steps
+are refused.  On the GPU: the GPU arm's line carries its roofline, e2e, clocks and launch
+count."""
 import json
 import os
 import subprocess
 import sys
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -37,3 +40,25 @@ def test_reference_arm_prints_one_contract_line():
 def test_too_few_warmup_steps_are_refused():
     r = _bench("--impl", "reference", "--workload", "small", "--steps", "2", "--warmup", "2")
     assert r.returncode != 0 and "--warmup must be >= 3" in (r.stdout + r.stderr)
+
+
+@pytest.mark.gpu
+def test_gpu_arm_line_carries_roofline_e2e_clocks_and_launches():
+    """The GPU arm on the 1M-vehicle grid (a few steps): the keys the contract adds to the
+    line -- roofline of the dominant kernel against the measured peak, e2e through the C ABI
+    with its copy sizes, clocks sampled during the timed region, the count of launches."""
+    r = _bench("--workload", "grid1m", "--steps", "3", "--warmup", "3", "--no-cpu-baseline")
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["metric"] == "vehicle-steps/s" and d["value"] > 0 and d["dtype"] == "f32"
+    assert d["gpu_launches"] == 5 * d["steps"]
+    rf = d["roofline"]
+    assert rf["bound"] == "hbm" and rf["unit"] == "GB/s" and rf["kernel"] in rf["kernel_ms"]
+    assert abs(rf["frac"] - rf["achieved"] / rf["peak"]) < 1e-9 and 0 < rf["frac"] < 1.5
+    assert set(rf["kernel_frac"]) == set(rf["kernel_ms"])
+    e = d["e2e"]
+    assert e["value"] > 0 and e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] > 0
+    c = d["clocks"]
+    assert c["sm_mhz"] > 0 and c["sm_max_mhz"] > 0 and isinstance(c["reasons"], list)

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -641,6 +642,8 @@ int ms_load_network(void *sim, const ms_network *net) {
   if (s->net_loaded) return fail(s, MS_ERR_STATE, "network already loaded");
   const int L = net->n_lanes, E = net->n_edges, C = net->n_ctrl;
   if (L <= 0 || E <= 0 || C < 0) return fail(s, MS_ERR_ARG, "n_lanes, n_edges must be > 0");
+  // a lane id travels in the low CODE_LANE_BITS bits of a vehicle's result code
+  if (L > CODE_LANE_MASK) return fail(s, MS_ERR_CAPACITY, "more lanes than a result code can name");
   if (!net->lane_len || !net->lane_edge || !net->lane_index || !net->lane_left || !net->lane_right ||
       !net->succ_off || !net->succ_lane || !net->succ_edge || !net->lane_ctrl || !net->lane_group ||
       !net->edge_nlanes || !net->edge_lane0 || (C > 0 && (!net->ctrl_offset || !net->ctrl_green ||
@@ -1346,16 +1349,19 @@ int ms_load_network_batch(void *sim, int n, const ms_network *nets) {
   Sim *s = (Sim *)sim;
   if (!s || !nets || n <= 0) return MS_ERR_ARG;
   if (s->net_loaded) return fail(s, MS_ERR_STATE, "network already loaded");
-  int L = 0, E = 0, C = 0, S = 0;
+  long long L64 = 0, E64 = 0, C64 = 0, S64 = 0;
   for (int k = 0; k < n; ++k) {
     const ms_network &q = nets[k];
     if (q.n_lanes <= 0 || q.n_edges <= 0 || q.n_ctrl < 0 || !q.succ_off)
       return fail(s, MS_ERR_ARG, "scenario " + std::to_string(k) + ": empty or missing network");
-    L += q.n_lanes;
-    E += q.n_edges;
-    C += q.n_ctrl;
-    S += q.succ_off[q.n_lanes];
+    L64 += q.n_lanes;
+    E64 += q.n_edges;
+    C64 += q.n_ctrl;
+    S64 += q.succ_off[q.n_lanes];
   }
+  if (L64 > CODE_LANE_MASK || E64 > INT_MAX || C64 > INT_MAX || S64 > INT_MAX)
+    return fail(s, MS_ERR_CAPACITY, "the union of the scenarios has too many lanes, edges or links");
+  const int L = (int)L64, E = (int)E64, C = (int)C64, S = (int)S64;
   std::vector<float> len(L);
   std::vector<int> edge(L), idx(L), left(L), right(L), soff(L + 1), sl(std::max(1, S)), se(std::max(1, S)),
       lctrl(L), lgrp(L), coff(std::max(1, C)), cg(std::max(1, C)), cy(std::max(1, C)), cp(std::max(1, C)),

@@ -203,6 +203,18 @@ def params_struct(params: dict, debug: bool = False, n_windows: int = 1, block: 
                      int(p.get("mp_interval", 10)))
 
 
+def _export_capacity(*tensors) -> int:
+    """Elements every given export buffer can hold: the smallest length among them (the
+    library writes up to that many 4-byte values into each)."""
+    given = [t for t in tensors if t is not None]
+    if not given:
+        raise ValueError("no export buffer given")
+    for t in given:
+        if t.element_size() != 4 or not t.is_contiguous():
+            raise ValueError("export buffers must be contiguous 4-byte tensors (float32 / int32)")
+    return min(int(t.numel()) for t in given)
+
+
 class Sim:
     """One simulation on the current CUDA device.
 
@@ -311,7 +323,8 @@ class Sim:
         """Copy the vehicle state into caller-owned (e.g. pinned) host buffers given as
         torch CPU tensors; returns the number of active vehicles."""
         ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
-        s = ms_state(int(x.numel()), 0, 0, ptr(vid), ptr(lane), None, ptr(x), ptr(v), None, None)
+        cap = _export_capacity(x, v, lane, vid)
+        s = ms_state(cap, 0, 0, ptr(vid), ptr(lane), None, ptr(x), ptr(v), None, None)
         self._check(self.lib.ms_read_state(self.h, C.byref(s), 0), "ms_read_state")
         return s.n_active
 
@@ -320,7 +333,7 @@ class Sim:
         None) without synchronising; finish it with read_wait.  The tensors must stay alive
         and untouched until then."""
         ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
-        cap = next(int(t.numel()) for t in (x, v, lane, vid) if t is not None)
+        cap = _export_capacity(x, v, lane, vid)
         s = ms_state(cap, 0, 0, ptr(vid), ptr(lane), None, ptr(x), ptr(v), None, None)
         self._check(self.lib.ms_read_state_async(self.h, C.byref(s)), "ms_read_state_async")
 
@@ -354,7 +367,8 @@ class Sim:
     def read_state_device(self, x, v, lane, vid, route_idx=None) -> int:
         """Device-to-device copy into torch CUDA tensors of sufficient length; returns n."""
         ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
-        s = ms_state(int(x.numel()), 0, 0, ptr(vid), ptr(lane), ptr(route_idx), ptr(x), ptr(v), None, None)
+        s = ms_state(_export_capacity(x, v, lane, vid, route_idx), 0, 0, ptr(vid), ptr(lane), ptr(route_idx),
+                     ptr(x), ptr(v), None, None)
         self._check(self.lib.ms_read_state(self.h, C.byref(s), 1), "ms_read_state")
         return s.n_active
 

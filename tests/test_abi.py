@@ -64,3 +64,16 @@ def test_header_is_plain_c_and_links_from_c(tmp_path):
                            "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
                            "-L", libdir, "-l:" + os.path.basename(moss.LIB_PATH), "-Wl,-rpath," + libdir])
     assert exe.exists()
+
+
+def test_export_buffers_bound_the_copy():
+    """The binding hands the library the length of the smallest export buffer, and refuses
+    buffers that are not contiguous 4-byte tensors (the library writes float32 / int32)."""
+    import torch
+    from paper_2405_12520_b300 import moss
+    assert moss._export_capacity(torch.zeros(5), torch.zeros(3, dtype=torch.int32), None) == 3
+    for bad in (torch.zeros(4, dtype=torch.float64), torch.zeros(8)[::2]):
+        with pytest.raises(ValueError):
+            moss._export_capacity(bad)
+    with pytest.raises(ValueError):
+        moss._export_capacity(None, None)

@@ -415,13 +415,24 @@ class Sim:
     def set_lc_log(self, x=None, y=None, n=None):
         """Log (features, rule decision) of lane-change candidates into device tensors
         (x bf16 [cap,16], y int32 [cap], n int32 [1]); no arguments turns logging off."""
-        cap = int(y.numel()) if y is not None else 0
+        given = [t is not None for t in (x, y, n)]
+        if any(given) and not all(given):
+            raise ValueError("set_lc_log takes x, y and n together, or none of them")
+        cap = 0
+        if all(given):
+            import torch
+            if (x.dtype != torch.bfloat16 or x.dim() != 2 or x.shape[1] != 16 or not x.is_contiguous()
+                    or y.dtype != torch.int32 or not y.is_contiguous() or n.dtype != torch.int32 or n.numel() < 1):
+                raise ValueError("set_lc_log: x bf16 [cap, 16], y int32 [cap], n int32 [1], contiguous")
+            cap = min(int(y.numel()), int(x.shape[0]))
         self._check(self.lib.ms_set_lc_log(self.h, _dp(x), _dp(y), cap, _dp(n)), "ms_set_lc_log")
 
     def sample_trips(self, zone_edge, attract, gamma: int, n: int, t_span: int, seed: int):
         """Gravity OD sampling (GPU): returns (orig_edge, dest_edge, t_dep) int32 arrays."""
         z = np.ascontiguousarray(zone_edge, np.int32)
         a = np.ascontiguousarray(attract, np.float32)
+        if a.shape != z.shape:
+            raise ValueError("one attraction per zone")
         o = np.zeros(n, np.int32)
         d = np.zeros(n, np.int32)
         t = np.zeros(n, np.int32)
@@ -433,6 +444,8 @@ class Sim:
         """Radiation OD sampling (GPU): returns (orig_edge, dest_edge, t_dep) int32 arrays."""
         z = np.ascontiguousarray(zone_edge, np.int32)
         m = np.ascontiguousarray(population, np.float32)
+        if m.shape != z.shape:
+            raise ValueError("one population per zone")
         o = np.zeros(n, np.int32)
         d = np.zeros(n, np.int32)
         t = np.zeros(n, np.int32)
@@ -464,6 +477,8 @@ class Sim:
         ln = np.ascontiguousarray(lanes, np.int32)
         vm = None if vmax is None else np.ascontiguousarray(vmax, np.float32)
         cl = None if closed is None else np.ascontiguousarray(closed, np.int32)
+        if (vm is not None and vm.shape != ln.shape) or (cl is not None and cl.shape != ln.shape):
+            raise ValueError("one limit / closure flag per lane")
         self._check(self.lib.ms_set_lane_limits(self.h, int(ln.shape[0]), _p(ln), _p(vm), _p(cl)),
                     "ms_set_lane_limits")
 
@@ -479,6 +494,8 @@ class Sim:
     def set_lc_model(self, params=None, margin: float = 0.2):
         """Use the learned lane-change decision (params: 5443 floats, host); None: rule."""
         a = None if params is None else np.ascontiguousarray(params, np.float32)
+        if a is not None and a.size != MLP_NPARAM:
+            raise ValueError(f"the model has {MLP_NPARAM} parameters")
         self._keep_model = a
         self._check(self.lib.ms_set_lc_model(self.h, _p(a), float(margin)), "ms_set_lc_model")
 

@@ -4,6 +4,8 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 from paper_2405_12520_b300 import build, moss, synth
@@ -77,3 +79,33 @@ def test_export_buffers_bound_the_copy():
             moss._export_capacity(bad)
     with pytest.raises(ValueError):
         moss._export_capacity(None, None)
+
+
+def test_binding_checks_input_lengths_before_the_library_reads_them():
+    """Arrays the library reads a counted number of elements from are checked in the
+    binding first (a mismatch raises before any call into the library, so no device or
+    library state is needed here)."""
+    import torch
+    from paper_2405_12520_b300 import moss
+    s = object.__new__(moss.Sim)          # the checks run before the library is used
+    with pytest.raises(ValueError):
+        s.set_lane_limits([1, 2], vmax=[3.0])
+    with pytest.raises(ValueError):
+        s.set_lane_limits([1, 2], closed=[1, 0, 1])
+    with pytest.raises(ValueError):
+        s.set_lane_links([1, 2], [0])
+    with pytest.raises(ValueError):
+        s.sample_trips([0, 1, 2], [1.0, 2.0], 2, 10, 60, 1)
+    with pytest.raises(ValueError):
+        s.sample_trips_radiation([0, 1], [1.0], 10, 60, 1)
+    with pytest.raises(ValueError):
+        s.set_lc_model(np.zeros(moss.MLP_NPARAM - 1, np.float32))
+    x = torch.zeros((8, 16), dtype=torch.bfloat16)
+    y = torch.zeros(8, dtype=torch.int32)
+    n = torch.zeros(1, dtype=torch.int32)
+    with pytest.raises(ValueError):
+        s.set_lc_log(x, y)                                          # n missing
+    with pytest.raises(ValueError):
+        s.set_lc_log(x.float(), y, n)                               # not bf16
+    with pytest.raises(ValueError):
+        s.set_lc_log(torch.zeros((8, 15), dtype=torch.bfloat16), y, n)   # not 16 inputs

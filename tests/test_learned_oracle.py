@@ -377,3 +377,35 @@ def test_flag_rule_rounds_a_boundary_value_the_other_way():
     assert not changed.any()
     thr = 0.5 * (marg(3.03125) + marg(3.015625))                  # between the two margins
     assert mlp.flip_sensitivity(theta, X, thr)[5].tolist() == [True, False]
+
+
+def test_in_step_flag_rule_counts_a_hidden_value_on_a_rounding_midpoint():
+    """The oracle's in-step learned decision counts the values that an FP32 path might round
+    the other way (lc_near).  One candidate at v = 10.078125 m/s (input 0 = v / 20 =
+    0.50390625, a BF16 value) and two networks whose first hidden unit reads only that
+    input: with weight 6 it is 3.0234375, exactly halfway between the BF16 values 3.015625
+    and 3.03125, and is counted; with weight 4 it is 2.015625, a BF16 value, and is not.
+    Everything else is the same, so the counts differ by exactly one, and the candidate
+    changes lanes under both (its margin is far from the threshold)."""
+    import math as _m
+    import netkit
+    net = synth.grid_network(2, 2, 2, 300.0, 30, 3, "zero")
+    e = int(np.nonzero((net.edge_from == 0) & (net.edge_to == 1))[0][0])
+    l0 = int(net.edge_lane0[e])
+    nxt = int(net.succ_edge[net.succ_off[l0]])
+    v = 10.078125
+    se = (P["idm_s0"] + v * P["idm_T"]) / _m.sqrt(1 - (v / 13.9) ** 4)
+    dem = netkit.vehicles([l0, l0], [100.0, 100.0 + P["veh_len"] + se], [v, v], [[e, nxt]] * 2)
+    near = {}
+    for w in (6.0, 4.0):
+        p = {k: np.zeros(sh) for k, sh in mlp.SHAPES}
+        p["W1"][0, 0] = w
+        p["W2"][0, 0] = 1.0
+        p["W3"][1, 0] = 1.0
+        o = oracle.Oracle(net, dem, P)
+        o.set_lc_model(mlp.pack(p).astype(np.float32), 0.2)
+        _, d = o.step(debug=True)
+        assert d["lc_learn"][0] == 1 and d["lc_dir"][0] == 1, w
+        assert d["lc_feat"][0, 0] == v / 20.0
+        near[w] = int(d["lc_near"][0])
+    assert near[6.0] == near[4.0] + 1, near

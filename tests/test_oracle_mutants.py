@@ -291,6 +291,10 @@ MUTANTS = [
     ("learned_hidden_layer_drops_its_bias", "moss_oracle.c",
      "a1[j] = acc + m->b1[j];", "a1[j] = acc;",
      ["test_learned_logits_match_the_numpy_bf16_forward"]),
+    ("in_step_flag_rule_tests_the_rounded_hidden_value", "moss_oracle.c",
+     "if (!near_boundary(hv, h1[j], 17.0 * u * s1[j], &alt)) continue;",
+     "if (!near_boundary(h1[j], h1[j], 17.0 * u * s1[j], &alt)) continue;",
+     ["test_in_step_flag_rule_counts_a_hidden_value_on_a_rounding_midpoint"]),
     # the network's gradient and optimiser (numpy)
     ("mlp_gradient_wrong_relu_mask", "mlp.py",
      "da1 = dh1 * (a1 > 0)\n    g[\"W1\"]", "da1 = dh1 * (a1 >= -1.0)\n    g[\"W1\"]",

@@ -12,8 +12,9 @@ Mistakes that change nothing the pins can reach are not listed: the clamp of a p
 the lane end when the own lane ends in an obstacle is a no-op in FP64 (x + (len - x) is
 exact for FP32 positions; it exists for rounding on the device); the id order of two
 vehicles at the same position on one lane applies only to states with a negative gap, which
-the state checks refuse; and a mistake that sends a vehicle to a lane that does not exist
-ends the child process instead of failing a pin."""
+the state checks refuse; a merge feeder that does not skip its own lane in the projection
+finds its own leader again, at the same gap; and a mistake that sends a vehicle to a lane
+that does not exist ends the child process instead of failing a pin."""
 import os
 import re
 import shutil
@@ -83,6 +84,12 @@ MUTANTS = [
     ("idm_without_the_a_min_clamp", "moss_oracle.c",
      "return fmax(a, p->a_min);", "return a;",
      ["test_motion_stop_within_the_step_and_gap_clamp"]),
+    ("fan_out_without_its_fallback", "moss_oracle.c",
+     "  return first;\n}", "  return -1;\n}",
+     ["test_fan_out_falls_back_to_the_first_open_link"]),
+    ("idm_gap_floored_at_one_metre", "moss_oracle.c",
+     "double q = ss / fmax(gap, 0.01);", "double q = ss / fmax(gap, 1.0);",
+     ["test_idm_below_one_metre_of_gap"]),
     # R9: fixed-time signals
     ("signal_offset_sign", "moss_oracle.c",
      "int tau = ((t + s->net.ctrl_offset[c]) % cyc + cyc) % cyc;",
@@ -137,6 +144,16 @@ MUTANTS = [
     ("target_lane_end_never_blocks", "moss_oracle.c",
      "} else if (end_blocks(s, tau, en, x, v, flag)) {", "} else if (0) {",
      ["test_target_lane_end_at_red_is_an_obstacle"]),
+    ("target_lane_end_yellow_rule_reversed", "moss_oracle.c",
+     "    return m >= 0.0;\n", "    return m < 0.0;\n",
+     ["test_target_lane_end_at_yellow_and_the_followers_old_gap"]),
+    ("follower_gap_to_the_target_lane_end_loses_a_length", "moss_oracle.c",
+     "aF_old = idm(s, s->v[Ft], v0_on(s, Ft, tau), 1, len - s->x[Ft], 0.0);",
+     "aF_old = idm(s, s->v[Ft], v0_on(s, Ft, tau), 1, len - s->x[Ft] - L, 0.0);",
+     ["test_target_lane_end_at_yellow_and_the_followers_old_gap"]),
+    ("connects_ignores_closed_links", "moss_oracle.c",
+     "    if (s->net.succ_edge[k] == en && !s->link_off[k]) return 1;", "    if (s->net.succ_edge[k] == en) return 1;",
+     ["test_closed_links_force_the_mandatory_change"]),
     ("target_lane_speed_limit_ignored", "moss_oracle.c",
      "r.a_new = idm(s, v, fmin(v0, s->lane_vmax[tau]),", "r.a_new = idm(s, v, v0,",
      ["test_mobil_uses_the_target_lanes_limit"]),

@@ -447,6 +447,39 @@ def test_mandatory_change_toward_connecting_lane(oracle_lib):
     assert d2["lc_dir"][0] == +1    # mandatory changes bypass the random gate
 
 
+def test_fan_out_falls_back_to_the_first_open_link(oracle_lib):
+    """The middle lane of a 3-lane approach links to all three lanes of the straight exit;
+    with two of those links closed, the only open one leads to the exit's left lane, which
+    does not serve the right turn the route takes after it.  No link of the lane reaches
+    a lane serving the edge after next, so the vehicle takes the first open link to its next
+    edge (and changes lanes there): it crosses onto the exit's left lane."""
+    net = synth.grid_network(3, 3, 3, 300.0, green=30, yellow=3)
+    e = [k for k in range(net.n_edges) if net.edge_from[k] == 3 and net.edge_to[k] == 4][0]
+    ex = [k for k in range(net.n_edges) if net.edge_from[k] == 4 and net.edge_to[k] == 5][0]
+    mid = int(net.edge_lane0[e]) + 1
+    links = [(int(net.succ_lane[k]), int(net.succ_lane[net.succ_off[net.succ_lane[k]]]))
+             for k in range(net.succ_off[mid], net.succ_off[mid + 1])]
+    left_exit = int(net.edge_lane0[ex]) + 2
+    keep = [j for j, (_, tgt) in enumerate(links) if tgt == left_exit]
+    assert len(keep) == 1 and len(links) == 3
+    # the edge after the exit: one its left lane does not serve, but another exit lane does
+    serves = lambda l, f: f in net.succ_edge[net.succ_off[l]:net.succ_off[l + 1]]
+    after = [int(f) for f in net.succ_edge[net.succ_off[int(net.edge_lane0[ex])]:
+                                            net.succ_off[int(net.edge_lane0[ex]) + 1]]
+             if not serves(left_exit, int(f))][0]
+    dem = netkit.vehicles([mid], [290.0], [8.0], [[e, ex, after]])
+    o = oracle_lib.Oracle(net, dem, P)
+    o.set_lane_links([mid], [1 << keep[0]])
+    seen = []
+    for _ in range(120):
+        o.step()
+        st = o.state()
+        if st["status"][0] == 1 and (not seen or seen[-1] != int(st["lane"][0])):
+            seen.append(int(st["lane"][0]))
+    assert links[keep[0]][0] in seen and left_exit in seen
+    assert seen.index(left_exit) == seen.index(links[keep[0]][0]) + 1
+
+
 def test_mandatory_change_tie_goes_to_the_lower_lane(oracle_lib):
     """Three lanes, the middle lane's links to the next edge closed: the two lanes that still
     connect are equally near, and the lower index (the right lane) is the one to reach, so
@@ -493,6 +526,50 @@ def test_target_lane_end_at_red_is_an_obstacle(oracle_lib):
     _, d = o.step(debug=True)
     assert d["lc_cand"][0] == 1 and d["tau_lead"][0] == -1 and d["lead_id"][0] == 1
     assert d["incentive"][0] == pytest.approx(am * s0 ** 2 * (1 / 9.0 - 1 / 900.0), abs=1e-9)
+
+
+def test_target_lane_end_at_yellow_and_the_followers_old_gap(oracle_lib):
+    """At the first second of yellow, everybody stopped (v = 0: IDM is a_max (1 - (s0/s)^2)
+    and every vehicle can stop): the changer 30 m before the stop line, 3 m behind its
+    leader, a follower 3 m behind it in the empty target lane.  The target lane's end is a
+    stopped obstacle for both: the changer's prospective gap is 30 m, the follower's present
+    gap is its distance to the line, 30 + L + 3 m."""
+    net = synth.grid_network(3, 3, 2, 300.0, green=200, yellow=3, offset="zero")
+    o0 = oracle_lib.Oracle(net, netkit.vehicles([], [], [], []), P)
+    L, s0, am, pol = P["veh_len"], P["idm_s0"], P["idm_a"], P["mobil_p"]
+    case = None
+    for e in range(net.n_edges):
+        l = int(net.edge_lane0[e])
+        if net.edge_to[e] != 4 or net.edge_nlanes[e] != 2 or o0.signal_state(l, 200) != 1:
+            continue
+        both = set(net.succ_edge[net.succ_off[l]:net.succ_off[l + 1]]) & set(
+            net.succ_edge[net.succ_off[l + 1]:net.succ_off[l + 2]])
+        if both:
+            case = (e, l, int(sorted(both)[0]))
+            break
+    assert case is not None
+    e, l, ex = case
+    xc = float(net.lane_len[l]) - 30.0
+    dem = netkit.vehicles([l, l, l + 1], [xc, xc + L + 3.0, xc - L - 3.0], [0.0] * 3, [[e, ex]] * 3)
+    o = oracle_lib.Oracle(net, dem, P)
+    st = o.state()
+    o.set_state(st["status"], st["lane"], st["x"], st["v"], st["rp"], 200)
+    _, d = o.step(debug=True)
+    idm0 = lambda gap: am * (1 - (s0 / gap) ** 2)
+    want = idm0(30.0) - idm0(3.0) + pol * (idm0(3.0) - idm0(30.0 + L + 3.0))
+    assert d["lc_cand"][0] == 1 and d["tau_lead"][0] == -1 and d["tau_foll"][0] == 2
+    assert d["incentive"][0] == pytest.approx(want, abs=1e-9)
+
+
+def test_idm_below_one_metre_of_gap(oracle_lib):
+    """Two vehicles standing 0.9 m apart: the follower's IDM acceleration is the formula's
+    a_max (1 - (s0 / 0.9)^2) = -7.88 m/s^2 (above a_min, so not clamped); the 0.01 m floor
+    of the gap does not reach it."""
+    d = _two_lane_case([0, 0], [100.0, 100.0 + P["veh_len"] + 0.9], [0.0, 0.0])
+    g = float(np.float32(100.0 + P["veh_len"] + 0.9)) - 100.0 - P["veh_len"]
+    want = P["idm_a"] * (1 - (P["idm_s0"] / g) ** 2)
+    assert P["a_min"] < want < -7.0
+    assert d["a_own"][0] == pytest.approx(want, abs=1e-9)
 
 
 # ---------------------------------------------------------------------------------------

@@ -163,6 +163,20 @@ MUTANTS = [
     ("lane_start_zone_ten_metres_too_long", "moss_oracle.c",
      "  if (x < p->x_lc_min) return r;", "  if (x <= p->x_lc_min + 10.0) return r;",
      ["test_mobil_zones_and_gate"]),
+    ("discretionary_target_need_not_serve_the_route", "moss_oracle.c",
+     "    if (!connects(s, tau, en)) return r;\n", "",
+     ["test_discretionary_change_only_toward_a_lane_serving_the_route"]),
+    ("old_follower_present_acceleration_under_the_target_limit", "moss_oracle.c",
+     "      double aO_old = idm(s, s->v[O], v0_on(s, O, l), 1, gO, v);",
+     "      double aO_old = idm(s, s->v[O], v0_on(s, O, tau), 1, gO, v);",
+     ["test_old_follower_drives_under_its_own_lanes_limit"]),
+    ("old_follower_prospective_acceleration_under_the_target_limit", "moss_oracle.c",
+     "        aO_new = idm(s, s->v[O], v0_on(s, O, l), 1, own->gap + (x - s->x[O]), own->vl);",
+     "        aO_new = idm(s, s->v[O], v0_on(s, O, tau), 1, own->gap + (x - s->x[O]), own->vl);",
+     ["test_old_follower_drives_under_its_own_lanes_limit"]),
+    ("lookahead_hop_adds_the_lane_left_behind", "moss_oracle.c",
+     "      dist += (double)s->net.lane_len[nxt];", "      dist += (double)s->net.lane_len[cur];",
+     ["test_lookahead_ends_at_the_twelfth_lane"]),
     ("target_leader_and_follower_transposed", "moss_oracle.c",
      "int Lt = j < cnt ? o[j] : -1;\n  int Ft = j > 0 ? o[j - 1] : -1;",
      "int Lt = j > 0 ? o[j - 1] : -1;\n  int Ft = j < cnt ? o[j] : -1;",

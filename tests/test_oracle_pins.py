@@ -942,6 +942,57 @@ def test_mobil_uses_the_target_lanes_limit(oracle_lib):
     assert d["lc_cand"][0] == 0 and d["lc_dir"][0] == 0
 
 
+def test_old_follower_drives_under_its_own_lanes_limit(oracle_lib):
+    """Own lane limited to 8 m/s, target lane free: the changer c (8 m/s) is 10 m behind a
+    stopped leader, its old follower O (8 m/s) behind it.  O's accelerations before and
+    after the change take O's desired speed under the own lane's limit, min(13.9, 8) = 8.
+    O 10 m behind: neither acceleration is clamped, so a desired speed taken for one of them
+    alone from elsewhere would not cancel in the difference; O 2 m behind: its present
+    acceleration is clamped at a_min and only its prospective one carries the free-road
+    term (v/v0)^4 = 1."""
+    am, b, T, s0, L, pol = P["idm_a"], P["idm_b"], P["idm_T"], P["idm_s0"], P["veh_len"], P["mobil_p"]
+
+    def idm(v, v0, gap, vl):
+        ss = s0 + max(0.0, v * T + v * (v - vl) / (2 * math.sqrt(am * b)))
+        return max(am * (1 - (v / v0) ** 4 - (ss / gap) ** 2), P["a_min"])
+    v0f = float(np.float32(13.9))
+    net = netkit.line(3, 300.0, 2)
+    import oracle
+    for gO, clamped in ((10.0, False), (2.0, True)):
+        dem = netkit.vehicles([0, 0, 0], [100.0, 100.0 + L + 10.0, 100.0 - L - gO], [8.0, 0.0, 8.0],
+                              [[0, 1]] * 3)
+        o = oracle.Oracle(net, dem, P)
+        o.set_lane_limits([0], vmax=[8.0])
+        _, d = o.step(debug=True)
+        assert d["lc_cand"][0] == 1 and d["old_foll"][0] == 2 and d["tau_foll"][0] == -1
+        a_c = idm(8.0, 8.0, 10.0, 0.0)
+        a_new = am * (1 - (8.0 / v0f) ** 4)
+        a_old_O, a_new_O = idm(8.0, 8.0, gO, 8.0), idm(8.0, 8.0, 10.0 + L + gO, 0.0)
+        assert (a_old_O == P["a_min"]) == clamped and a_new_O > P["a_min"]
+        assert d["incentive"][0] == pytest.approx(a_new - a_c + pol * (a_new_O - a_old_O), abs=1e-9), gO
+
+
+def test_discretionary_change_only_toward_a_lane_serving_the_route(oracle_lib):
+    """The middle lane of a 3-lane approach goes straight; its left neighbour serves only
+    the left turn and its right neighbour only the right turn.  A vehicle heading straight
+    behind a stopped leader has every reason to leave, but neither neighbour serves its next
+    edge, so it is no candidate for a discretionary change on either step parity."""
+    net = synth.grid_network(3, 3, 3, 300.0, green=30, yellow=3)
+    e = [k for k in range(net.n_edges) if net.edge_from[k] == 3 and net.edge_to[k] == 4][0]
+    ex = [k for k in range(net.n_edges) if net.edge_from[k] == 4 and net.edge_to[k] == 5][0]
+    l0 = int(net.edge_lane0[e])
+    serves = lambda l, f: f in net.succ_edge[net.succ_off[l]:net.succ_off[l + 1]]
+    assert serves(l0 + 1, ex) and not serves(l0, ex) and not serves(l0 + 2, ex)
+    import oracle
+    for t0 in (0, 1):
+        dem = netkit.vehicles([l0 + 1, l0 + 1], [100.0, 108.0], [5.0, 0.0], [[e, ex]] * 2)
+        o = oracle.Oracle(net, dem, P)
+        st = o.state()
+        o.set_state(st["status"], st["lane"], st["x"], st["v"], st["rp"], t0)
+        _, d = o.step(debug=True)
+        assert d["lc_cand"][0] == 0 and d["lc_dir"][0] == 0, t0
+
+
 def test_closed_lane_is_never_entered_until_reopened(oracle_lib):
     """A vehicle whose next edge's lanes are closed stops at the end of the lane before them
     (gap >= 0, never on a closed lane) and goes on once they reopen."""

@@ -409,3 +409,21 @@ def test_in_step_flag_rule_counts_a_hidden_value_on_a_rounding_midpoint():
         assert d["lc_feat"][0, 0] == v / 20.0
         near[w] = int(d["lc_near"][0])
     assert near[6.0] == near[4.0] + 1, near
+
+
+@pytest.mark.parametrize("t0", [0, 1])
+def test_tied_classes_go_to_the_lower_index(t0):
+    """A network whose left and right logits tie (0, 0) above stay (-8), decided with a
+    fallback threshold of 0 (the margin of a tie is 0): the class is the lower index, left,
+    so every learned candidate moves left on a step that allows it and stays on one that
+    allows only moves to the right."""
+    p = {k: np.zeros(s) for k, s in mlp.SHAPES}
+    p["b3"][0] = -8.0
+    theta = mlp.pack(p).astype(np.float32)
+    net, dem = _workload()
+    st, dr, dl = _pair(net, dem, t0, theta, margin=0.0)
+    L = dl["lc_learn"] == 1
+    assert L.sum() > 50
+    assert np.all(dl["lc_margin"][L] == 0.0)
+    assert np.all(dl["lc_dir"][L] == (1 if t0 % 2 == 0 else 0))
+

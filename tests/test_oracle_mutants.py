@@ -2,10 +2,10 @@
 
 Each case copies oracle/ into a scratch directory, plants one plausible mistake in the copy
 (a dropped term, a wrong sign, a transposed index or operand, a reversed comparison, an
-off-by-one), and runs the oracle's pins (the four pin files below) against that copy in a
-child process.  At least one pin must fail, and the pin named for that mistake must be among
-the failures.  A control copy with nothing planted must pass every pin, and the child must
-be shown to import the copy, not this tree's oracle.  CPU only: the copies are plain C and
+off-by-one), and runs the pins named for that mistake (from the four pin files below)
+against that copy in a child process: one of them must fail.  A control copy with nothing
+planted must pass every pin of the four files, and the child must be shown to import the
+copy, not this tree's oracle.  CPU only: the copies are plain C and
 numpy, built with gcc in the scratch directory.
 
 Mistakes that change nothing the pins can reach are not listed: the clamp of a position to
@@ -288,6 +288,15 @@ MUTANTS = [
     ("max_pressure_tie_goes_to_the_higher_phase", "moss_oracle.c",
      "if (pr[ph] > pr[best]) best = ph;", "if (pr[ph] >= pr[best]) best = ph;",
      ["test_max_pressure_tie_between_two_other_phases_goes_to_the_lower"]),
+    ("max_pressure_yellow_ends_a_step_late", "moss_oracle.c",
+     "if (s->mp_pend[c] >= 0 && t >= s->mp_yend[c]) {", "if (s->mp_pend[c] >= 0 && t > s->mp_yend[c]) {",
+     ["test_max_pressure_run_matches_brute_force_and_never_runs_red"]),
+    ("max_pressure_decides_while_a_switch_is_pending", "moss_oracle.c",
+     "if (!decide || s->mp_pend[c] >= 0) continue;", "if (!decide) continue;",
+     ["test_max_pressure_run_matches_brute_force_and_never_runs_red"]),
+    ("max_pressure_decision_steps_shifted", "moss_oracle.c",
+     "const int decide = (t % s->p.mp_interval) == 0;", "const int decide = ((t + 1) % s->p.mp_interval) == 0;",
+     ["test_max_pressure_run_matches_brute_force_and_never_runs_red"]),
     # R14: lane limits and closures
     ("speed_limit_ignored", "moss_oracle.c",
      "return fmin((double)s->v0[c], s->lane_vmax[l]);", "return (double)s->v0[c];",
@@ -326,6 +335,9 @@ MUTANTS = [
      "if (!near_boundary(hv, h1[j], 17.0 * u * s1[j], &alt)) continue;",
      "if (!near_boundary(h1[j], h1[j], 17.0 * u * s1[j], &alt)) continue;",
      ["test_in_step_flag_rule_counts_a_hidden_value_on_a_rounding_midpoint"]),
+    ("learned_class_tie_goes_to_the_higher_index", "moss_oracle.c",
+     "    if (pr[q] > pr[c]) c = q;", "    if (pr[q] >= pr[c]) c = q;",
+     ["test_tied_classes_go_to_the_lower_index"]),
     # the network's gradient and optimiser (numpy)
     ("mlp_gradient_wrong_relu_mask", "mlp.py",
      "da1 = dh1 * (a1 > 0)\n    g[\"W1\"]", "da1 = dh1 * (a1 >= -1.0)\n    g[\"W1\"]",
@@ -424,11 +436,23 @@ def _child_env():
     return env
 
 
-def _run_pins(dst):
-    """Run the pin files against the oracle copy in dst; (exit code, failed test names, tail)."""
+def _pin_ids(names):
+    """pytest node ids of the named pins (every parametrization of each)."""
+    ids = []
+    for f in PIN_FILES:
+        defined = set(re.findall(r"^def (test_\w+)", open(os.path.join(ROOT, f)).read(), re.M))
+        ids += [f"{os.path.join(ROOT, f)}::{n}" for n in sorted(defined & set(names))]
+    assert len(ids) == len(set(names)), f"pins not found: {sorted(set(names))}"
+    return ids
+
+
+def _run_pins(job):
+    """Run pins against the oracle copy in dst: the named ones, or all four pin files when
+    none are named; (exit code, failed test names, tail)."""
+    dst, names = job
     args = [sys.executable, "-m", "pytest", "-q", "-rf", "-p", "no:cacheprovider", "--rootdir", ROOT,
             "-c", os.path.join(ROOT, "pytest.ini"), "-m", "not gpu"]
-    args += [os.path.join(ROOT, f) for f in PIN_FILES]
+    args += _pin_ids(names) if names else [os.path.join(ROOT, f) for f in PIN_FILES]
     r = subprocess.run(args, cwd=dst, env=_child_env(), capture_output=True, text=True, timeout=900)
     failed = sorted({m.group(1) for m in map(_FAILED.match, r.stdout.splitlines()) if m})
     return r.returncode, failed, r.stdout[-3000:] + r.stderr[-2000:]
@@ -436,16 +460,17 @@ def _run_pins(dst):
 
 @pytest.fixture(scope="module")
 def outcomes(tmp_path_factory):
-    """The control copy and every planted mistake, run concurrently (one child each)."""
+    """The control copy against every pin, and every planted mistake against the pins named
+    for it, run concurrently (one child each)."""
     jobs = {}
     ctl = str(tmp_path_factory.mktemp("control"))
     _copy_oracle(ctl)
-    jobs["control"] = ctl
-    for name, fname, old, new, _ in MUTANTS:
+    jobs["control"] = (ctl, None)
+    for name, fname, old, new, catchers in MUTANTS:
         d = str(tmp_path_factory.mktemp(name))
         _copy_oracle(d)
         _plant(d, fname, old, new)
-        jobs[name] = d
+        jobs[name] = (d, catchers)
     # the child imports the copy, not this tree's oracle
     r = subprocess.run([sys.executable, "-c", "import oracle; print(oracle.__file__)"], cwd=ctl,
                        env=_child_env(), capture_output=True, text=True, timeout=120)
@@ -463,6 +488,7 @@ def test_control_copy_passes_every_pin(outcomes):
 @pytest.mark.parametrize("name, fname, old, new, catchers", MUTANTS, ids=[m[0] for m in MUTANTS])
 def test_planted_mistake_is_caught(outcomes, name, fname, old, new, catchers):
     code, failed, tail = outcomes[name]
-    # exit code 1: tests ran and some failed (not a crash, a collection error or a timeout)
+    # exit code 1: the named pins ran and some failed (not a crash, a collection error or a
+    # timeout), and one of those that failed is named for this mistake
     assert code == 1, f"{name}: pins exit code {code}\n{tail}"
     assert set(catchers) & set(failed), f"{name}: caught only by {failed}, not by {catchers}\n{tail}"

@@ -858,14 +858,18 @@ def _mp_brute(net, counts, cs_prev, t, interval):
     return cs
 
 
-def test_max_pressure_run_matches_brute_force_and_never_runs_red(oracle_lib):
+@pytest.mark.parametrize("interval", [10, 2])
+def test_max_pressure_run_matches_brute_force_and_never_runs_red(oracle_lib, interval):
     """Small grid workload under max pressure: at every step the controllers equal R13
     restated with numpy from the previous step's controllers and the snapshot's lane
     counts; a switch starts only at a decision step and its yellow lasts exactly the
-    controller's yellow time; no vehicle crosses a red stop line; all trips arrive."""
+    controller's yellow time; no vehicle crosses a red stop line; all trips arrive.  With
+    decisions every 2 s, shorter than the 3 s yellow, decision steps fall inside a pending
+    switch, which they leave alone."""
     import oracle
     net, dem = synth.small_grid_workload(2)
-    o = oracle.Oracle(net, dem, MP)
+    MPI = dict(MP, mp_interval=interval)
+    o = oracle.Oracle(net, dem, MPI)
     prev = np.tile(np.array([0, -1, 0], np.int32), (net.n_ctrl, 1))   # the start state
     switches = 0
     for _ in range(3600):
@@ -874,10 +878,10 @@ def test_max_pressure_run_matches_brute_force_and_never_runs_red(oracle_lib):
         cs = o.ctrl_state()   # the controllers step t uses
         act = st["status"] == 1
         counts = np.bincount(st["lane"][act], minlength=net.n_lanes)
-        np.testing.assert_array_equal(cs, _mp_brute(net, counts, prev, t, MP["mp_interval"]), err_msg=f"step {t}")
+        np.testing.assert_array_equal(cs, _mp_brute(net, counts, prev, t, interval), err_msg=f"step {t}")
         started = (cs[:, 1] >= 0) & (prev[:, 1] < 0)
         if started.any():
-            assert t % MP["mp_interval"] == 0
+            assert t % interval == 0
             assert np.all(cs[started, 2] == t + net.ctrl_yellow[started])
             switches += int(started.sum())
         ctrl = net.lane_ctrl[st["lane"]]

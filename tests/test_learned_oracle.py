@@ -427,3 +427,22 @@ def test_tied_classes_go_to_the_lower_index(t0):
     assert np.all(dl["lc_margin"][L] == 0.0)
     assert np.all(dl["lc_dir"][L] == (1 if t0 % 2 == 0 else 0))
 
+
+def test_mandatory_changes_bypass_the_network():
+    """A vehicle on a 3-lane approach's right-turn-only lane whose route goes straight must
+    move left: that change is mandatory, so an always-stay network does not decide it (no
+    learned record) and the vehicle moves left as under the rule."""
+    import netkit
+    p = {k: np.zeros(s) for k, s in mlp.SHAPES}
+    p["b3"][0] = 8.0
+    theta = mlp.pack(p).astype(np.float32)
+    net = synth.grid_network(3, 3, 3, 300.0, green=30, yellow=3)
+    e = [k for k in range(net.n_edges) if net.edge_from[k] == 3 and net.edge_to[k] == 4][0]
+    ex = [k for k in range(net.n_edges) if net.edge_from[k] == 4 and net.edge_to[k] == 5][0]
+    l0 = int(net.edge_lane0[e])
+    dem = netkit.vehicles([l0], [150.0], [13.9], [[e, ex]])
+    o = oracle.Oracle(net, dem, P)
+    o.set_lc_model(theta, 0.2)
+    _, d = o.step(debug=True)
+    assert d["lc_cand"][0] == 1 and d["lc_learn"][0] == 0 and d["lc_dir"][0] == 1
+

@@ -177,6 +177,9 @@ MUTANTS = [
     ("lookahead_hop_adds_the_lane_left_behind", "moss_oracle.c",
      "      dist += (double)s->net.lane_len[nxt];", "      dist += (double)s->net.lane_len[cur];",
      ["test_lookahead_ends_at_the_twelfth_lane"]),
+    ("new_follower_under_its_present_lanes_limit", "moss_oracle.c",
+     "aF_new = idm(s, s->v[Ft], v0_on(s, Ft, tau), 1, gF, v);", "aF_new = idm(s, s->v[Ft], v0_on(s, Ft, l), 1, gF, v);",
+     ["test_new_follower_drives_under_the_target_lanes_limit"]),
     ("target_leader_and_follower_transposed", "moss_oracle.c",
      "int Lt = j < cnt ? o[j] : -1;\n  int Ft = j > 0 ? o[j - 1] : -1;",
      "int Lt = j > 0 ? o[j - 1] : -1;\n  int Ft = j < cnt ? o[j] : -1;",
@@ -297,6 +300,9 @@ MUTANTS = [
     ("max_pressure_decision_steps_shifted", "moss_oracle.c",
      "const int decide = (t % s->p.mp_interval) == 0;", "const int decide = ((t + 1) % s->p.mp_interval) == 0;",
      ["test_max_pressure_run_matches_brute_force_and_never_runs_red"]),
+    ("max_pressure_switch_without_yellow", "moss_oracle.c",
+     "return s->mp_pend[c] >= 0 ? SIG_YELLOW : SIG_GREEN;", "return SIG_GREEN;",
+     ["test_max_pressure_switches_to_the_loaded_phase"]),
     # R14: lane limits and closures
     ("speed_limit_ignored", "moss_oracle.c",
      "return fmin((double)s->v0[c], s->lane_vmax[l]);", "return (double)s->v0[c];",
@@ -338,6 +344,12 @@ MUTANTS = [
     ("learned_class_tie_goes_to_the_higher_index", "moss_oracle.c",
      "    if (pr[q] > pr[c]) c = q;", "    if (pr[q] >= pr[c]) c = q;",
      ["test_tied_classes_go_to_the_lower_index"]),
+    ("network_decides_mandatory_changes", "moss_oracle.c",
+     "if (s->mlp && lc.cand && lc.safe && !lc.mandatory) {", "if (s->mlp && lc.cand && lc.safe) {",
+     ["test_mandatory_changes_bypass_the_network"]),
+    ("learned_acceleration_input_unscaled", "moss_oracle.c",
+     "  f[4] = a_c / p->a;", "  f[4] = a_c;",
+     ["test_learned_inputs_follow_from_the_state"]),
     # the network's gradient and optimiser (numpy)
     ("mlp_gradient_wrong_relu_mask", "mlp.py",
      "da1 = dh1 * (a1 > 0)\n    g[\"W1\"]", "da1 = dh1 * (a1 >= -1.0)\n    g[\"W1\"]",

@@ -976,6 +976,31 @@ def test_old_follower_drives_under_its_own_lanes_limit(oracle_lib):
         assert d["incentive"][0] == pytest.approx(a_new - a_c + pol * (a_new_O - a_old_O), abs=1e-9), gO
 
 
+def test_new_follower_drives_under_the_target_lanes_limit(oracle_lib):
+    """Target lane limited to 8 m/s, own lane free: the changer c (8 m/s, 10 m behind a
+    stopped leader) and a new follower F (8 m/s) 10 m behind it in the target lane.  Both of
+    F's accelerations, on the free road now and behind c after the change, take F's desired
+    speed under the target lane's limit, min(13.9, 8) = 8 (so the present one is 0)."""
+    am, b, T, s0, L, pol = P["idm_a"], P["idm_b"], P["idm_T"], P["idm_s0"], P["veh_len"], P["mobil_p"]
+
+    def idm(v, v0, gap, vl):
+        ss = s0 + max(0.0, v * T + v * (v - vl) / (2 * math.sqrt(am * b)))
+        return max(am * (1 - (v / v0) ** 4 - (ss / gap) ** 2), P["a_min"])
+    v0f = float(np.float32(13.9))
+    net = netkit.line(3, 300.0, 2)
+    dem = netkit.vehicles([0, 0, 1], [100.0, 100.0 + L + 10.0, 100.0 - L - 10.0], [8.0, 0.0, 8.0], [[0, 1]] * 3)
+    import oracle
+    o = oracle.Oracle(net, dem, P)
+    o.set_lane_limits([1], vmax=[8.0])
+    _, d = o.step(debug=True)
+    assert d["lc_cand"][0] == 1 and d["tau_foll"][0] == 2 and d["tau_lead"][0] == -1
+    a_c = idm(8.0, v0f, 10.0, 0.0)
+    a_new = am * (1 - (8.0 / 8.0) ** 4)
+    aF_new, aF_old = idm(8.0, 8.0, 10.0, 8.0), am * (1 - (8.0 / 8.0) ** 4)
+    assert aF_new > -P["mobil_bsafe"]
+    assert d["incentive"][0] == pytest.approx(a_new - a_c + pol * (aF_new - aF_old), abs=1e-9)
+
+
 def test_discretionary_change_only_toward_a_lane_serving_the_route(oracle_lib):
     """The middle lane of a 3-lane approach goes straight; its left neighbour serves only
     the left turn and its right neighbour only the right turn.  A vehicle heading straight

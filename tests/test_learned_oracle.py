@@ -262,6 +262,14 @@ def test_learned_inputs_follow_from_the_state(t0):
     ok(f[~h, 8], 2.0)
     ok(f[~h, 9], 0.0)
     ok(f[~h, 10], 0.0)
+    # the new follower's acceleration behind the changer, / a_max (IDM, R1, at its own speed
+    # and desired speed, the changer as its leader)
+    am, b, T, s0 = P["idm_a"], P["idm_b"], P["idm_T"], P["idm_s0"]
+    vF, vc = v[tf[h]], v[L[h]]
+    gF = x[L[h]] - x[tf[h]] - Lv
+    ss = s0 + np.maximum(0.0, vF * T + vF * (vF - vc) / (2 * np.sqrt(am * b)))
+    aF = np.maximum(am * (1 - (vF / v0[tf[h]]) ** 4 - (ss / np.maximum(gF, 0.01)) ** 2), P["a_min"])
+    ok(f[h, 10], aF / am)
     h = of >= 0
     ok(f[h, 12], v[of[h]] / 20.0)
     ok(f[h, 15], cap(x[L[h]] - x[of[h]] - Lv))
@@ -381,18 +389,49 @@ def test_flag_rule_rounds_a_boundary_value_the_other_way():
 
 def test_in_step_flag_rule_counts_a_hidden_value_on_a_rounding_midpoint():
     """The oracle's in-step learned decision counts the values that an FP32 path might round
-    the other way (lc_near).  One candidate at v = 10.078125 m/s (input 0 = v / 20 =
-    0.50390625, a BF16 value) and two networks whose first hidden unit reads only that
-    input: with weight 6 it is 3.0234375, exactly halfway between the BF16 values 3.015625
-    and 3.03125, and is counted; with weight 4 it is 2.015625, a BF16 value, and is not.
-    Everything else is the same, so the counts differ by exactly one, and the candidate
-    changes lanes under both (its margin is far from the threshold)."""
+    the other way (lc_near) and flags the vehicle only when rounding one of them the other
+    way could move its decision.  One candidate at v = 11.40625 m/s (input 0 = v / 20 =
+    0.5703125 = 73/128, a BF16 value) and networks whose first hidden unit reads only that
+    input, with weight w, feeding one unit of layer 2 with weight w2 and the left logit:
+      w = 4, w2 = 1: 2.28125 and 2.28125, BF16 values: nothing counted beyond the inputs;
+      w = 5: 2.8515625, halfway between 2.84375 (even, taken) and 2.859375: one more;
+      w = 7: 3.9921875, halfway between 3.984375 and 4 (even, taken; the step below a power
+             of two is half the step above): one more;
+      w = 4, w2 = 7: layer 2 gets 15.96875, halfway between 15.9375 and 16 (taken): one more.
+    The inputs near a boundary are counted as the reading states them (within
+    2^-22 |f| + the absolute part of each input's bound).  Every margin is far from the
+    threshold and each value rounded the other way moves it little, so nothing is flagged."""
     import math as _m
     import netkit
     net = synth.grid_network(2, 2, 2, 300.0, 30, 3, "zero")
     e = int(np.nonzero((net.edge_from == 0) & (net.edge_to == 1))[0][0])
     l0 = int(net.edge_lane0[e])
     nxt = int(net.succ_edge[net.succ_off[l0]])
+    v = 11.40625
+    se = (P["idm_s0"] + v * P["idm_T"]) / _m.sqrt(1 - (v / 13.9) ** 4)
+    dem = netkit.vehicles([l0, l0], [100.0, 100.0 + P["veh_len"] + se], [v, v], [[e, nxt]] * 2)
+    in_abs = np.zeros(16)
+    in_abs[[2, 6, 8, 13, 15]] = 1e-5
+    in_abs[[4, 10, 11]] = 5e-5
+    near = {}
+    cases = [(4.0, 1.0), (5.0, 1.0), (7.0, 1.0), (4.0, 7.0)]
+    for w, w2 in cases:
+        p = {k: np.zeros(sh) for k, sh in mlp.SHAPES}
+        p["W1"][0, 0] = w
+        p["W2"][0, 0] = w2
+        p["W3"][1, 0] = 1.0
+        o = oracle.Oracle(net, dem, P)
+        o.set_lc_model(mlp.pack(p).astype(np.float32), 0.2)
+        _, d = o.step(debug=True)
+        assert d["lc_learn"][0] == 1 and d["lc_dir"][0] == 1 and d["flag"][0] == 0, (w, w2)
+        f = d["lc_feat"][0]
+        assert f[0] == v / 20.0
+        n_in = int(mlp._near_alt(f, mlp.bf16(f), 2.0 ** -22 * np.abs(f) + in_abs)[0].sum())
+        near[(w, w2)] = int(d["lc_near"][0]) - n_in
+    assert near == {(4.0, 1.0): 0, (5.0, 1.0): 1, (7.0, 1.0): 1, (4.0, 7.0): 1}, near
+    # a tie that rounds up, with the BF16 value below as the other side: at v = 10.078125
+    # input 0 is 0.50390625 and weight 6 gives 3.0234375, halfway between 3.015625 and the
+    # even 3.03125 (taken); weight 4 gives 2.015625, a BF16 value
     v = 10.078125
     se = (P["idm_s0"] + v * P["idm_T"]) / _m.sqrt(1 - (v / 13.9) ** 4)
     dem = netkit.vehicles([l0, l0], [100.0, 100.0 + P["veh_len"] + se], [v, v], [[e, nxt]] * 2)
@@ -405,10 +444,11 @@ def test_in_step_flag_rule_counts_a_hidden_value_on_a_rounding_midpoint():
         o = oracle.Oracle(net, dem, P)
         o.set_lc_model(mlp.pack(p).astype(np.float32), 0.2)
         _, d = o.step(debug=True)
-        assert d["lc_learn"][0] == 1 and d["lc_dir"][0] == 1, w
-        assert d["lc_feat"][0, 0] == v / 20.0
-        near[w] = int(d["lc_near"][0])
-    assert near[6.0] == near[4.0] + 1, near
+        assert d["lc_learn"][0] == 1 and d["lc_dir"][0] == 1 and d["flag"][0] == 0, w
+        f = d["lc_feat"][0]
+        n_in = int(mlp._near_alt(f, mlp.bf16(f), 2.0 ** -22 * np.abs(f) + in_abs)[0].sum())
+        near[w] = int(d["lc_near"][0]) - n_in
+    assert near == {6.0: 1, 4.0: 0}, near
 
 
 @pytest.mark.parametrize("t0", [0, 1])

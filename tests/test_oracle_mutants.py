@@ -303,6 +303,10 @@ MUTANTS = [
     ("max_pressure_switch_without_yellow", "moss_oracle.c",
      "return s->mp_pend[c] >= 0 ? SIG_YELLOW : SIG_GREEN;", "return SIG_GREEN;",
      ["test_max_pressure_switches_to_the_loaded_phase"]),
+    ("step_leaves_the_controllers_to_the_state_read", "moss_oracle.c",
+     "  if (p->signal_mode == 1) mp_advance(s);   /* R13: controllers at step t */",
+     "  if (p->signal_mode != 1) mp_advance(s);   /* R13: controllers at step t */",
+     ["test_max_pressure_steps_advance_the_controllers_themselves"]),
     # R14: lane limits and closures
     ("speed_limit_ignored", "moss_oracle.c",
      "return fmin((double)s->v0[c], s->lane_vmax[l]);", "return (double)s->v0[c];",
@@ -349,6 +353,36 @@ MUTANTS = [
      ["test_mandatory_changes_bypass_the_network"]),
     ("learned_acceleration_input_unscaled", "moss_oracle.c",
      "  f[4] = a_c / p->a;", "  f[4] = a_c;",
+     ["test_learned_inputs_follow_from_the_state"]),
+    ("flag_rule_upper_neighbour_below", "moss_oracle.c",
+     "  const double n = up ? a + ulp : (a == ldexp(1.0, e - 1) ? a - ulp / 2 : a - ulp);",
+     "  const double n = up ? a - ulp : (a == ldexp(1.0, e - 1) ? a - ulp / 2 : a - ulp);",
+     ["test_in_step_flag_rule_counts_a_hidden_value_on_a_rounding_midpoint"]),
+    ("flag_rule_misses_the_power_of_two_below", "moss_oracle.c",
+     "  const double n = up ? a + ulp : (a == ldexp(1.0, e - 1) ? a - ulp / 2 : a - ulp);",
+     "  const double n = up ? a + ulp : (a == ldexp(1.0, e + 1) ? a - ulp / 2 : a - ulp);",
+     ["test_in_step_flag_rule_counts_a_hidden_value_on_a_rounding_midpoint"]),
+    ("flag_rule_half_step_below_a_power_of_two_upward", "moss_oracle.c",
+     "  const double n = up ? a + ulp : (a == ldexp(1.0, e - 1) ? a - ulp / 2 : a - ulp);",
+     "  const double n = up ? a + ulp : (a == ldexp(1.0, e - 1) ? a + ulp / 2 : a - ulp);",
+     ["test_in_step_flag_rule_counts_a_hidden_value_on_a_rounding_midpoint"]),
+    ("flag_rule_upper_midpoint_misplaced", "moss_oracle.c",
+     "  if (fabs(v - 0.5 * (r + out)) <= delta) { *alt = out; return 1; }",
+     "  if (fabs(v - 0.5 * (r - out)) <= delta) { *alt = out; return 1; }",
+     ["test_in_step_flag_rule_counts_a_hidden_value_on_a_rounding_midpoint"]),
+    ("flag_rule_re_evaluation_skips_hidden_layer_1", "moss_oracle.c",
+     "      for (int j = 0; j < 64; ++j) h1[j] = or_bf16(fmax(a1[j], 0.0));\n",
+     "      for (int j = 0; j >= 64; ++j) h1[j] = or_bf16(fmax(a1[j], 0.0));\n",
+     ["test_in_step_flag_rule_counts_a_hidden_value_on_a_rounding_midpoint"]),
+    ("flag_rule_skips_the_inputs", "moss_oracle.c",
+     "  for (int k = 0; k < 16; ++k) {\n    if (!near_boundary(", "  for (int k = 0; k >= 16; ++k) {\n    if (!near_boundary(",
+     ["test_in_step_flag_rule_counts_a_hidden_value_on_a_rounding_midpoint"]),
+    ("flag_rule_lower_neighbour_above", "moss_oracle.c",
+     "  const double n = up ? a + ulp : (a == ldexp(1.0, e - 1) ? a - ulp / 2 : a - ulp);",
+     "  const double n = up ? a + ulp : (a == ldexp(1.0, e - 1) ? a - ulp / 2 : a + ulp);",
+     ["test_in_step_flag_rule_counts_a_hidden_value_on_a_rounding_midpoint"]),
+    ("learned_input_10_only_without_a_follower", "moss_oracle.c",
+     "  f[10] = lc->tau_foll >= 0 ? lc->aF_new / p->a : 0.0;", "  f[10] = lc->tau_foll < 0 ? lc->aF_new / p->a : 0.0;",
      ["test_learned_inputs_follow_from_the_state"]),
     # the network's gradient and optimiser (numpy)
     ("mlp_gradient_wrong_relu_mask", "mlp.py",

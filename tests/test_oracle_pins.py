@@ -829,6 +829,26 @@ def test_max_pressure_tie_between_two_other_phases_goes_to_the_lower(oracle_lib)
     assert o.ctrl_state()[ctrl].tolist()[:2] == [0, 1]
 
 
+def test_max_pressure_steps_advance_the_controllers_themselves(oracle_lib):
+    """Reading the controllers' state is an observation, not a step: a max-pressure run that
+    reads them before every step and one that never does end in the same state, bit for
+    bit, after 800 steps with switches in them."""
+    import oracle
+    net, dem = synth.small_grid_workload(2)
+    a = oracle.Oracle(net, dem, MP)
+    b = oracle.Oracle(net, dem, MP)
+    seen = set()
+    for _ in range(800):
+        seen.add(tuple(a.ctrl_state()[:, 0].tolist()))
+        a.step()
+        b.step()
+    assert len(seen) > 3
+    sa, sb = a.state(), b.state()
+    for k in ("status", "lane", "x", "v", "rp", "t_arr"):
+        assert np.array_equal(sa[k], sb[k]), k
+    assert np.array_equal(a.ctrl_state(), b.ctrl_state())
+
+
 def _mp_brute(net, counts, cs_prev, t, interval):
     """R13 restated with numpy over the network arrays, from the previous step's state."""
     cs = cs_prev.copy()

@@ -486,3 +486,85 @@ def test_mandatory_changes_bypass_the_network():
     _, d = o.step(debug=True)
     assert d["lc_cand"][0] == 1 and d["lc_learn"][0] == 0 and d["lc_dir"][0] == 1
 
+
+
+def _tie_net(w, w2, b1=0.0, b3=0.0):
+    p = {k: np.zeros(s) for k, s in mlp.SHAPES}
+    p["W1"][0, 0] = w
+    p["W2"][0, 0] = w2
+    p["W3"][1, 0] = 1.0
+    p["b1"][0] = b1
+    p["b3"][1] = b3
+    return mlp.pack(p)
+
+
+@pytest.mark.parametrize("x0, w, w2, alt_logit", [
+    (73 / 128, 4.0, 1.0, None),            # 2.28125 and 2.28125: BF16 values, nothing near
+    (73 / 128, 5.0, 1.0, 2.859375),        # 2.8515625 -> 2.84375 (even, below); other side above
+    (73 / 128, 7.0, 1.0, 3.984375),        # 3.9921875 -> 4 (even); other side 4 - 2^-6 (half step)
+    (129 / 256, 6.0, 1.0, 3.015625),       # 3.0234375 -> 3.03125 (even, above); other side below
+    (73 / 128, 4.0, 7.0, 15.9375),         # layer 2: 15.96875 -> 16 (even); other side 16 - 2^-4
+])
+def test_flag_rule_in_every_rounding_position(x0, w, w2, alt_logit):
+    """forward_bf16's near flag and flip_sensitivity's re-evaluation on ties in each position
+    the BF16 rounding can leave one: a hidden value exactly halfway between two BF16 values
+    below or above the even one taken, just under a power of two (where the step below is half
+    the step above), in hidden layer 1 or 2.  The logit then moves to the value computed by
+    hand for the other side, the logit bound gains that move on top of the accumulation bound
+    (K + 1) 2^-22 (|h2| |W3| + |b3|), the margin bound gains the softmax difference, and the
+    decision changes only when the threshold lies between the two margins.  The left logit
+    carries a bias of 1/4."""
+    b3 = 0.25
+    theta = _tie_net(w, w2, b3=b3)
+    X = np.zeros((1, 16))
+    X[0, 0] = x0
+    u = 2.0 ** -22
+    z, near, zb_f = mlp.forward_bf16(theta, X)
+    l1 = z[0, 1]
+    acc = 65 * u * l1                      # |h2| |W3| + |b3| = (l1 - b3) + b3
+    alt_logit = None if alt_logit is None else alt_logit + b3
+    np.testing.assert_allclose(zb_f[0], [0.0, acc, 0.0], rtol=1e-12, atol=1e-18)
+    assert bool(near[0]) == (alt_logit is not None)
+    marg = lambda v: (np.exp(v) - 1.0) / (np.exp(v) + 2.0)
+    z2, m, c, zb, msens, changed = mlp.flip_sensitivity(theta, X, 0.2)
+    np.testing.assert_array_equal(z2, z)
+    assert c[0] == 1 and not changed[0]
+    if alt_logit is None:
+        np.testing.assert_allclose(zb[0], [0.0, acc, 0.0], rtol=1e-12, atol=1e-18)
+        assert msens[0] == 0.0
+        return
+    np.testing.assert_allclose(zb[0], [0.0, acc + abs(alt_logit - l1), 0.0], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(msens[0], abs(marg(alt_logit) - marg(l1)), rtol=1e-6, atol=1e-15)
+    thr = 0.5 * (marg(alt_logit) + marg(l1))
+    assert mlp.flip_sensitivity(theta, X, thr)[5][0]
+
+
+def test_flag_rule_on_an_input_tie_and_the_prediction_margin():
+    """An input given in FP64 exactly halfway between two BF16 values (1 + 2^-8: 1 is taken)
+    is flagged when the caller passes the inputs' bound, and rounding it the other way moves
+    the logit by 2^-7 through a network that passes it on with a bias of 1/4 in hidden layer
+    1 and in the logit; mlp.predict's margin is the top softmax probability minus the
+    second."""
+    theta = _tie_net(1.0, 1.0, b1=0.25, b3=0.25)                      # 1 + 1/4 + 1/4
+    X = np.zeros((1, 16))
+    X[0, 0] = 1.0 + 2.0 ** -8
+    z, m, c, zb, msens, changed = mlp.flip_sensitivity(theta, X, 0.2, in_delta=np.full((1, 16), 1e-9))
+    assert z[0, 1] == 1.5
+    acc = 65 * 2.0 ** -22 * (1.25 + 0.25)
+    np.testing.assert_allclose(zb[0, 1], acc + 2.0 ** -7, rtol=1e-12)
+    _, _, _, zb0, _, _ = mlp.flip_sensitivity(theta, X, 0.2)          # inputs taken as BF16
+    np.testing.assert_allclose(zb0[0, 1], acc, rtol=1e-12)
+    cls, mg = mlp.predict(theta, X)
+    p = np.exp([0.0, 1.0 + 2.0 ** -8 + 0.5, 0.0])
+    p /= p.sum()
+    assert cls[0] == 1 and mg[0] == pytest.approx(p[1] - p[0], rel=1e-12)
+
+
+def test_flag_rule_forward_matches_the_bf16_forward_with_biases():
+    """flip_sensitivity evaluates the same BF16 network as forward_bf16 (pinned above): equal
+    logits on random inputs through a random network with biases."""
+    rng = np.random.default_rng(9)
+    theta = mlp.init(2) + rng.normal(scale=0.1, size=mlp.N_PARAMS)
+    X = rng.normal(size=(200, 16))
+    z, _, _ = mlp.forward_bf16(theta, X)
+    np.testing.assert_array_equal(mlp.flip_sensitivity(theta, X, 0.2)[0], z)

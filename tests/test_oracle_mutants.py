@@ -416,6 +416,22 @@ MUTANTS = [
      "    zb = 65 * u * (np.abs(h2) @ np.abs(W3).T + np.abs(b3))\n    m, c = margin_class(z)",
      "    zb = 17 * u * (np.abs(h2) @ np.abs(W3).T + np.abs(b3))\n    m, c = margin_class(z)",
      ["test_flag_rule_rounds_a_boundary_value_the_other_way"]),
+    ("flag_rule_upper_side_misplaced", "mlp.py",
+     "    n_up = (a > 0) & (np.abs(av - (a + up) / 2) <= delta)", "    n_up = (a > 0) & (np.abs(av - (a - up) / 2) <= delta)",
+     ["test_flag_rule_in_every_rounding_position"]),
+    ("flag_rule_power_of_two_step_not_halved", "mlp.py",
+     "    ulp_in = np.where(a == np.ldexp(1.0, e - 1), ulp / 2, ulp)\n    up, dn",
+     "    ulp_in = np.where(a == np.ldexp(1.0, e + 1), ulp / 2, ulp)\n    up, dn",
+     ["test_flag_rule_in_every_rounding_position"]),
+    ("flag_rule_logit_bound_subtracts_the_bias", "mlp.py",
+     "    zb = 65 * u * (np.abs(h2) @ np.abs(W3).T + np.abs(b3))", "    zb = 65 * u * (np.abs(h2) @ np.abs(W3).T - np.abs(b3))",
+     ["test_flag_rule_in_every_rounding_position"]),
+    ("flag_rule_input_path_subtracts_the_hidden_bias", "mlp.py",
+     "            _, h2a = tail(bf16(np.maximum(xa @ W1.T + b1, 0.0)))", "            _, h2a = tail(bf16(np.maximum(xa @ W1.T - b1, 0.0)))",
+     ["test_flag_rule_on_an_input_tie_and_the_prediction_margin"]),
+    ("prediction_margin_top_plus_second", "mlp.py",
+     "    return p.argmax(1), s[:, -1] - s[:, -2]", "    return p.argmax(1), s[:, -1] + s[:, -2]",
+     ["test_flag_rule_on_an_input_tie_and_the_prediction_margin"]),
     ("adam_without_second_moment_correction", "mlp.py",
      "vh = v / (1 - b2 ** t)", "vh = v",
      ["test_adam_first_step_is_lr_times_sign"]),
@@ -444,6 +460,14 @@ MUTANTS = [
      "        td[k] = (_u24(splitmix64, seed, SALT_TIME, k) * int(t_span)) >> 24\n    return o, de, td\n\n\n# ----",
      "        td[k] = _u24(splitmix64, seed, SALT_TIME, k) % int(t_span)\n    return o, de, td\n\n\n# ----",
      ["test_departure_times_scale_with_the_span"]),
+    ("radiation_origins_not_by_population", "routing.py",
+     "    W = (radiation_weights if m.shape[0] <= 256 else radiation_weights_vec)(cost, m)\n    cdf_o = np.cumsum(m, dtype=np.float32)\n"
+     "    cdf_d = np.cumsum(W, axis=1, dtype=np.float32)\n    o = np.zeros(n, np.int32)\n    de = np.zeros(n, np.int32)\n"
+     "    td = np.zeros(n, np.int32)\n    for k in range(n):\n        uo = np.float32(_u24(splitmix64, seed, SALT_ORIGIN, k)) * np.float32(2.0 ** -24)\n        i = _first_above(cdf_o, np.float32(uo * cdf_o[-1]))\n        ud",
+     "    W = (radiation_weights if m.shape[0] <= 256 else radiation_weights_vec)(cost, m)\n    cdf_o = np.cumsum(m, dtype=np.float32)\n"
+     "    cdf_d = np.cumsum(W, axis=1, dtype=np.float32)\n    o = np.zeros(n, np.int32)\n    de = np.zeros(n, np.int32)\n"
+     "    td = np.zeros(n, np.int32)\n    for k in range(n):\n        uo = np.float32(_u24(splitmix64, seed, SALT_ORIGIN, k)) * np.float32(2.0 ** -24)\n        i = _first_above(cdf_o, np.float32(uo / cdf_o[-1]))\n        ud",
+     ["test_radiation_sampling_follows_the_weights_and_is_scale_free"]),
     ("radiation_drops_the_destination_population", "routing.py",
      "den = np.float32(np.float32(m[i] + s[j]) * np.float32(np.float32(m[i] + m[j]) + s[j]))\n"
      "            W[i, j] = np.float32(num / den)\n    return W\n\n\ndef radiation_weights_vec",

@@ -176,8 +176,8 @@ def test_radiation_weights_closed_form_on_a_line():
 
 
 def test_radiation_sampling_follows_the_weights_and_is_scale_free():
-    """Sampled destinations of one origin follow the normalised weights (4 binomial standard
-    deviations); scaling every population by 2^3 (exact in float32) or every road length by 2
+    """Sampled origins follow the populations and the destinations of one origin the
+    normalised weights (4 binomial standard deviations each); scaling every population by 2^3 (exact in float32) or every road length by 2
     (same distance ranks) draws exactly the same trips: the model has no free parameter and
     uses distances only through their order."""
     net = netkit.line(10, 500.0, 1)
@@ -191,6 +191,10 @@ def test_radiation_sampling_follows_the_weights_and_is_scale_free():
     p = W[0] / W[0].sum()
     f = np.array([(d[sel] == z).mean() for z in zones])
     assert np.all(np.abs(f - p) <= 4 * np.sqrt(p * (1 - p) / sel.sum()) + 1e-12)
+    # origins: drawn as the gravity model draws them, by population share
+    po = m.astype(np.float64) / m.sum()
+    fo = np.array([(o == z).mean() for z in zones])
+    assert np.all(np.abs(fo - po) <= 4 * np.sqrt(po * (1 - po) / n) + 1e-12)
     o2, d2, t2 = routing.radiation_trips(net, zones, m * np.float32(8.0), n, 600, 31, _sm)
     np.testing.assert_array_equal(d, d2)
     np.testing.assert_array_equal(o, o2)

@@ -263,6 +263,14 @@ MUTANTS = [
     ("departures_enter_a_closed_lane", "moss_oracle.c",
      "    if (s->lane_closed[l]) continue;   /* R14: the queue waits */\n", "",
      ["test_departures_wait_on_a_closed_lane"]),
+    ("state_write_keeps_the_queue_heads", "moss_oracle.c",
+     "  for (int l = 0; l < s->net.n_lanes; ++l) s->q_head[l] = s->q_off[l];\n  mp_reset(s);",
+     "  for (int l = 0; l >= s->net.n_lanes; ++l) s->q_head[l] = s->q_off[l];\n  mp_reset(s);",
+     ["test_rewinding_a_run_resumes_it_exactly"]),
+    ("lane_link_changes_unchecked", "moss_oracle.c",
+     "  for (int k = 0; k < n; ++k) {   /* validate first: nothing changes on a bad entry */",
+     "  for (int k = 0; k >= n; ++k) {   /* validate first: nothing changes on a bad entry */",
+     ["test_lane_link_changes_are_checked"]),
     # R3: merge projection
     ("merge_projection_order_reversed", "moss_oracle.c",
      "if (dj < dc || (dj == dc && j < c)) { found = j; break; }",

@@ -1149,6 +1149,38 @@ def test_run_is_deterministic_and_resumable(oracle_lib):
         np.testing.assert_array_equal(sa[k], sc[k])
 
 
+def test_rewinding_a_run_resumes_it_exactly(oracle_lib):
+    """A state written back into a simulation that has run past it (a rewind, with trips
+    that have since departed waiting again) resumes exactly: from the state at t = 300 of
+    a run that went on to t = 700, the same 400 steps lead to the same state as before."""
+    net, dem = synth.small_grid_workload(3)
+    a = oracle_lib.Oracle(net, dem, P)
+    a.run(300)
+    s = a.state()
+    a.run(400)
+    end = a.state()
+    a.set_state(s["status"], s["lane"], s["x"], s["v"], s["rp"], s["t"], s["t_arr"])
+    assert (a.state()["status"] == 0).sum() > (end["status"] == 0).sum()   # trips wait again
+    a.run(400)
+    again = a.state()
+    for k in ("status", "lane", "x", "v", "rp", "t_arr", "t"):
+        np.testing.assert_array_equal(end[k], again[k])
+
+
+def test_lane_link_changes_are_checked(oracle_lib):
+    """The oracle's lane-link call refuses a junction lane or a lane out of range and
+    changes nothing then."""
+    import oracle
+    net = netkit.line(3, 300.0, 2)
+    dem = netkit.vehicles([0], [100.0], [5.0], [[0, 1]])
+    o = oracle.Oracle(net, dem, P)
+    for bad in ([net.n_edge_lanes], [net.n_lanes], [-1]):
+        with pytest.raises(ValueError):
+            o.set_lane_links(bad, [0])
+    o.run(60)
+    assert o.state()["status"][0] == 2 or o.state()["lane"][0] != 0   # its link stayed open
+
+
 def test_departures_fifo_and_room(oracle_lib):
     net = netkit.line(3, 300.0, 2)
     n = 5

@@ -190,6 +190,14 @@ MUTANTS = [
     ("random_gate_reversed", "moss_oracle.c",
      "if ((h >> 40) >= thr) return r;", "if ((h >> 40) < thr) return r;",
      ["test_mobil_zones_and_gate"]),
+    ("random_gate_the_same_at_every_step", "moss_oracle.c",
+     "    uint64_t h = or_splitmix64(p->seed ^ ((uint64_t)(uint32_t)s->t << 32) ^ (uint64_t)(uint32_t)c);",
+     "    uint64_t h = or_splitmix64(p->seed ^ (uint64_t)(uint32_t)c);",
+     ["test_random_gate_is_a_fresh_draw_per_trip_and_step"]),
+    ("random_gate_the_same_for_every_trip", "moss_oracle.c",
+     "    uint64_t h = or_splitmix64(p->seed ^ ((uint64_t)(uint32_t)s->t << 32) ^ (uint64_t)(uint32_t)c);",
+     "    uint64_t h = or_splitmix64(p->seed ^ ((uint64_t)(uint32_t)s->t << 32));",
+     ["test_random_gate_is_a_fresh_draw_per_trip_and_step"]),
     # R6, R7: motion and transfer
     ("advance_by_the_end_speed", "moss_oracle.c",
      "d = 0.5 * (v + vn) * p->dt;", "d = vn * p->dt;",

@@ -362,6 +362,36 @@ def test_mobil_zones_and_gate(oracle_lib):
     assert d["lc_cand"][0] == 0
 
 
+def test_random_gate_is_a_fresh_draw_per_trip_and_step(oracle_lib):
+    """With p_lc = 0.3, 400 vehicles that pass every other candidate test (each 59 m apart on
+    one long 2-lane road, at equilibrium behind its leader, the left lane free) become
+    candidates with probability 0.3 each, drawn afresh at every step: at each of two even
+    steps the share is 0.3 within 4 binomial standard deviations, and the share that pass
+    at both is 0.09 within the same margin (independent draws)."""
+    n, p = 400, 0.3
+    v, v0 = 10.0, 13.9
+    se = (P["idm_s0"] + v * P["idm_T"]) / math.sqrt(1 - (v / v0) ** 4)
+    net = netkit.line(2, 24000.0, 2)
+    xs, vs = [], []
+    for q in range(n):
+        base = 60.0 + 59.0 * q
+        xs += [base, base + P["veh_len"] + se]
+        vs += [v, v]
+    dem = netkit.vehicles([0] * (2 * n), xs, vs, [[0]] * (2 * n), v0=v0)
+    import oracle
+    picks = []
+    for t0 in (0, 2):
+        o = oracle.Oracle(net, dem, dict(P, p_lc=p, x_lc_end=0.0))
+        st = o.state()
+        o.set_state(st["status"], st["lane"], st["x"], st["v"], st["rp"], t0)
+        _, d = o.step(debug=True)
+        picks.append(d["lc_cand"][0::2] == 1)
+    for pk in picks:
+        assert abs(pk.mean() - p) <= 4 * math.sqrt(p * (1 - p) / n)
+    both = (picks[0] & picks[1]).mean()
+    assert abs(both - p * p) <= 4 * math.sqrt(p * p * (1 - p * p) / n)
+
+
 JITTER_SALT = 0x9E3779B97F4A7C15
 
 

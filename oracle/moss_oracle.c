@@ -17,8 +17,10 @@
  * open, numbered R1, R2, ... and stated where it applies.
  *
  * Parity unpinned against the paper: the form of MOBIL's randomization (the R4 gate and
- * the R12 threshold jitter), which the paper does not give; those draws are pinned only by
- * the published SplitMix64 vector and by CPU/GPU identity.
+ * the R12 threshold jitter), which the paper does not give; those draws are pinned by the
+ * published SplitMix64 vector, by CPU/GPU identity, and by the statistics the readings fix
+ * (a gate passed with probability p_lc, drawn afresh per trip and step; a jitter uniform
+ * over trips), not by the paper.
  *
  *  R1  IDM: a = a_max [1 - (v/v0)^4 - (ss/s)^2], ss = s0 + max(0, vT + v dv/(2 sqrt(a_max b))),
  *      dv = v - v_lead, s = bumper gap floored at 0.01 m; (v/v0)^4 by two squarings; no

@@ -246,3 +246,102 @@ def test_departures_by_time_and_onto_the_first_linked_lane():
         for i in np.nonzero(r[1]["inserted"])[0]:
             entry[int(i)] = int(lane[i])
     assert len(entry) == n and all(entry[k] == w for k, (_, w) in enumerate(trips))
+
+
+def test_fan_out_fallback_with_closed_links():
+    _need_gpu()
+    net = synth.grid_network(3, 3, 3, 300.0, green=30, yellow=3)
+    e = [k for k in range(net.n_edges) if net.edge_from[k] == 3 and net.edge_to[k] == 4][0]
+    ex = [k for k in range(net.n_edges) if net.edge_from[k] == 4 and net.edge_to[k] == 5][0]
+    mid = int(net.edge_lane0[e]) + 1
+    tg = [int(net.succ_lane[net.succ_off[net.succ_lane[k]]]) for k in range(net.succ_off[mid], net.succ_off[mid + 1])]
+    keep = tg.index(int(net.edge_lane0[ex]) + 2)
+    l_ex0 = int(net.edge_lane0[ex])
+    serves = lambda l, f: f in net.succ_edge[net.succ_off[l]:net.succ_off[l + 1]]
+    after = [int(f) for f in net.succ_edge[net.succ_off[l_ex0]:net.succ_off[l_ex0 + 1]]
+             if not serves(l_ex0 + 2, int(f))][0]
+    dem = netkit.vehicles([mid], [290.0], [8.0], [[e, ex, after]])
+    sim, orc = _pair(net, dem, P, prep=lambda o: o.set_lane_links([mid], [1 << keep]))
+    _steps(sim, orc, dem.n, 80)
+
+
+def test_target_lane_end_at_yellow_with_a_follower():
+    _need_gpu()
+    net = synth.grid_network(3, 3, 2, 300.0, green=200, yellow=3, offset="zero")
+    o0 = oracle.Oracle(net, netkit.vehicles([], [], [], []), P)
+    case = None
+    for e in range(net.n_edges):
+        l = int(net.edge_lane0[e])
+        if net.edge_to[e] != 4 or net.edge_nlanes[e] != 2 or o0.signal_state(l, 200) != 1:
+            continue
+        both = set(net.succ_edge[net.succ_off[l]:net.succ_off[l + 1]]) & set(
+            net.succ_edge[net.succ_off[l + 1]:net.succ_off[l + 2]])
+        if both:
+            case = (e, l, int(sorted(both)[0]))
+            break
+    e, l, ex = case
+    L = P["veh_len"]
+    xc = float(net.lane_len[l]) - 30.0
+    dem = netkit.vehicles([l, l, l + 1], [xc, xc + L + 3.0, xc - L - 3.0], [0.0] * 3, [[e, ex]] * 3)
+    sim, orc = _pair(net, dem, P, t0=200)
+    st0, gd, gs, od, os_ = _steps(sim, orc, dem.n, 1)[0]
+    assert gd["lc_cand"][0] == 1 and gd["tau_foll"][0] == 2
+    assert abs(float(gd["incentive"][0]) - od["incentive"][0]) <= 1e-4
+
+
+@pytest.mark.parametrize("limited_lane, trail_lane", [(0, 0), (1, 1)])
+def test_followers_under_lane_limits(limited_lane, trail_lane):
+    _need_gpu()
+    net = netkit.line(3, 300.0, 2)
+    L = P["veh_len"]
+    dem = netkit.vehicles([0, 0, trail_lane], [100.0, 100.0 + L + 10.0, 100.0 - L - 10.0], [8.0, 0.0, 8.0],
+                          [[0, 1]] * 3)
+    sim, orc = _pair(net, dem, P, prep=lambda o: o.set_lane_limits([limited_lane], vmax=[8.0]))
+    st0, gd, gs, od, os_ = _steps(sim, orc, dem.n, 1)[0]
+    assert gd["lc_cand"][0] == 1
+    assert abs(float(gd["incentive"][0]) - od["incentive"][0]) <= 1e-4
+
+
+@pytest.mark.parametrize("t0", [0, 1])
+def test_discretionary_target_must_serve_the_route(t0):
+    _need_gpu()
+    net = synth.grid_network(3, 3, 3, 300.0, green=30, yellow=3)
+    e = [k for k in range(net.n_edges) if net.edge_from[k] == 3 and net.edge_to[k] == 4][0]
+    ex = [k for k in range(net.n_edges) if net.edge_from[k] == 4 and net.edge_to[k] == 5][0]
+    l0 = int(net.edge_lane0[e])
+    dem = netkit.vehicles([l0 + 1, l0 + 1], [100.0, 108.0], [5.0, 0.0], [[e, ex]] * 2)
+    sim, orc = _pair(net, dem, P, t0=t0)
+    st0, gd, gs, od, os_ = _steps(sim, orc, dem.n, 1)[0]
+    assert gd["lc_cand"][0] == 0 and gd["lc_dir"][0] == 0
+
+
+def test_max_pressure_decisions_inside_a_yellow_are_refused():
+    """The oracle pins max pressure deciding every 2 s inside a 3 s yellow; the library takes
+    decision intervals longer than every controller's yellow only, so on the device a
+    decision never meets a pending switch, and such a network is refused."""
+    _need_gpu()
+    from paper_2405_12520_b300 import moss
+    net, dem = synth.small_grid_workload(2)
+    sim = moss.Sim(dict(MP, mp_interval=2))
+    with pytest.raises(moss.MossError) as e:
+        sim.load_network(net)
+    assert e.value.code == moss.MS_ERR_ARG
+    sim.destroy()
+
+
+def test_rewinding_a_run_resumes_it_exactly():
+    _need_gpu()
+    net, dem = synth.small_grid_workload(3)
+    sim = parity.gpu_sim(net, dem, P, debug=False)
+    sim.step(200)
+    s200 = sim.read_state()
+    sim.step(200)
+    sim.sync()
+    end = sim.read_state()
+    sim.write_state(s200)
+    sim.step(200)
+    sim.sync()
+    again = sim.read_state()
+    for k in ("id", "lane", "x", "v", "route_idx", "trip_status", "t_arr"):
+        assert np.array_equal(end[k], again[k]), k
+    assert end["t"] == again["t"]

@@ -270,6 +270,19 @@ def test_learned_inputs_follow_from_the_state(t0):
     ss = s0 + np.maximum(0.0, vF * T + vF * (vF - vc) / (2 * np.sqrt(am * b)))
     aF = np.maximum(am * (1 - (vF / v0[tf[h]]) ** 4 - (ss / np.maximum(gF, 0.01)) ** 2), P["a_min"])
     ok(f[h, 10], aF / am)
+    # the changer's prospective acceleration on the target lane, / a_max: behind the target
+    # leader, before the target lane's end as a stopped obstacle, or on the free road
+    vv = v[L]
+    v0c = v0[L]
+
+    def idm(vx, v0x, gap, vl):
+        ssx = s0 + np.maximum(0.0, vx * T + vx * (vx - vl) / (2 * np.sqrt(am * b)))
+        return np.maximum(am * (1 - (vx / v0x) ** 4 - (ssx / np.maximum(gap, 0.01)) ** 2), P["a_min"])
+    h = tl >= 0
+    gap_t = np.where(h, x[np.maximum(tl, 0)] - x[L] - Lv, to_end)
+    vl_t = np.where(h, v[np.maximum(tl, 0)], 0.0)
+    a_new = np.where(h | obst & ~free, idm(vv, v0c, gap_t, vl_t), am * (1 - (vv / v0c) ** 4))
+    ok(f[:, 11], a_new / am)
     h = of >= 0
     ok(f[h, 12], v[of[h]] / 20.0)
     ok(f[h, 15], cap(x[L[h]] - x[of[h]] - Lv))

@@ -154,6 +154,14 @@ MUTANTS = [
     ("connects_ignores_closed_links", "moss_oracle.c",
      "    if (s->net.succ_edge[k] == en && !s->link_off[k]) return 1;", "    if (s->net.succ_edge[k] == en) return 1;",
      ["test_closed_links_force_the_mandatory_change"]),
+    ("target_lane_end_stopping_distance_doubled", "moss_oracle.c",
+     "    double m = ((double)s->net.lane_len[l] - x) - v * v / (2.0 * s->p.b);",
+     "    double m = ((double)s->net.lane_len[l] - x) - v * v / (1.0 * s->p.b);",
+     ["test_target_lane_end_at_yellow_takes_the_stopping_distance"]),
+    ("conflict_guard_divides_by_dt", "moss_oracle.c",
+     "    double guard = s->v[Ft] * p->dt + 0.5 * p->a * p->dt * p->dt;",
+     "    double guard = s->v[Ft] / p->dt + 0.5 * p->a * p->dt * p->dt;",
+     ["test_motion_and_the_conflict_guard_scale_with_dt"]),
     ("target_lane_speed_limit_ignored", "moss_oracle.c",
      "r.a_new = idm(s, v, fmin(v0, s->lane_vmax[tau]),", "r.a_new = idm(s, v, v0,",
      ["test_mobil_uses_the_target_lanes_limit"]),
@@ -223,6 +231,15 @@ MUTANTS = [
     ("junction_transfer_keeps_the_route_cursor", "moss_oracle.c",
      "            nrp += 1;\n", "",
      ["test_small_grid_run_invariants"]),
+    ("speed_update_divides_by_dt", "moss_oracle.c",
+     "    double vraw = v + a_use * p->dt;", "    double vraw = v + a_use / p->dt;",
+     ["test_motion_and_the_conflict_guard_scale_with_dt"]),
+    ("advance_divides_by_dt", "moss_oracle.c",
+     "      d = 0.5 * (v + vn) * p->dt;", "      d = 0.5 * (v + vn) / p->dt;",
+     ["test_motion_and_the_conflict_guard_scale_with_dt"]),
+    ("gap_clamp_speed_multiplies_by_dt", "moss_oracle.c",
+     "      vn = fmin(vn, d / p->dt);", "      vn = fmin(vn, d * p->dt);",
+     ["test_motion_and_the_conflict_guard_scale_with_dt"]),
     ("retires_one_edge_early", "moss_oracle.c",
      "if (!is_internal(s, l) && route_at(s, c, s->rp[c] + 1) < 0) {",
      "if (!is_internal(s, l) && route_at(s, c, s->rp[c] + 2) < 0) {",
@@ -399,6 +416,9 @@ MUTANTS = [
      ["test_in_step_flag_rule_counts_a_hidden_value_on_a_rounding_midpoint"]),
     ("learned_input_10_only_without_a_follower", "moss_oracle.c",
      "  f[10] = lc->tau_foll >= 0 ? lc->aF_new / p->a : 0.0;", "  f[10] = lc->tau_foll < 0 ? lc->aF_new / p->a : 0.0;",
+     ["test_learned_inputs_follow_from_the_state"]),
+    ("learned_input_11_unscaled_the_other_way", "moss_oracle.c",
+     "  f[11] = lc->a_new / p->a;", "  f[11] = lc->a_new * p->a;",
      ["test_learned_inputs_follow_from_the_state"]),
     # the network's gradient and optimiser (numpy)
     ("mlp_gradient_wrong_relu_mask", "mlp.py",

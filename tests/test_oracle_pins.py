@@ -177,6 +177,67 @@ def test_lookahead_ends_at_the_twelfth_lane(oracle_lib):
     assert d["lead_kind"][0] == 2 and d["s_own"][0] == pytest.approx(want, abs=1e-9)
 
 
+def test_motion_and_the_conflict_guard_scale_with_dt(oracle_lib):
+    """With a time step of 0.5 s: from rest on a free road the first step gives v' = a_max dt
+    and d = a_max dt^2 / 2; at 15 m/s 4 m behind a stopped leader (IDM clamped at a_min)
+    the ballistic distance 0.5 (15 + 10.5) dt = 6.375 m is cut to the gap and the speed to
+    gap / dt = 8 m/s; and the conflict guard of a follower at 4 m/s is
+    v_F dt + a_max dt^2 / 2 = 2.25 m (a changer at 14 m/s keeps the follower's IDM desired gap
+    at s0, so only the guard decides between 2.2 and 2.4 m)."""
+    dt, am, L = 0.5, P["idm_a"], P["veh_len"]
+    Pd = dict(P, dt=dt)
+    net = netkit.ring(200.0)
+    dem = netkit.ring_demand(net, np.array([10.0]), np.array([0.0]), 13.9)
+    o = oracle_lib.Oracle(net, dem, Pd)
+    x0 = o.state()["x"][0]
+    o.step()
+    st = o.state()
+    assert st["v"][0] == pytest.approx(am * dt, abs=1e-12)
+    assert st["x"][0] - x0 == pytest.approx(0.5 * am * dt * dt, abs=1e-12)
+    line = netkit.line(3, 300.0, 1)
+    dem = netkit.vehicles([0, 0], [100.0, 100.0 + L + 4.0], [15.0, 0.0], [[0, 1]] * 2)
+    o = oracle_lib.Oracle(line, dem, Pd)
+    _, d = o.step(debug=True)
+    assert d["a_use"][0] == P["a_min"]
+    st = o.state()
+    assert st["x"][0] == pytest.approx(104.0, abs=1e-12) and st["v"][0] == pytest.approx(4.0 / dt, abs=1e-12)
+    stopped = 100.0 + L + 3.0
+    for g, allowed in ((2.2, False), (2.4, True)):
+        assert am * (1 - (4.0 / 13.9) ** 4 - (P["idm_s0"] / g) ** 2) > -P["mobil_bsafe"]
+        d = _two_lane_case([0, 0, 1], [100.0, stopped, 100.0 - L - g], [14.0, 0.0, 4.0], dt=dt)
+        assert d["lc_cand"][0] == 1 and d["tau_foll"][0] == 2
+        assert d["lc_dir"][0] == (+1 if allowed else 0), g
+
+
+def test_target_lane_end_at_yellow_takes_the_stopping_distance(oracle_lib):
+    """At the first second of yellow a changer at 10 m/s, 15 m before the line (it can stop:
+    v^2 / (2 b) = 11.1 m), with both lanes ending at that line: the target lane's end blocks
+    it as its own lane's does, so the prospective and the present acceleration are the same
+    IDM value before a stopped obstacle 15 m ahead and the incentive is exactly 0."""
+    net = synth.grid_network(3, 3, 2, 300.0, green=200, yellow=3, offset="zero")
+    o0 = oracle_lib.Oracle(net, netkit.vehicles([], [], [], []), P)
+    case = None
+    for e in range(net.n_edges):
+        l = int(net.edge_lane0[e])
+        if net.edge_to[e] != 4 or net.edge_nlanes[e] != 2 or o0.signal_state(l, 200) != 1:
+            continue
+        both = set(net.succ_edge[net.succ_off[l]:net.succ_off[l + 1]]) & set(
+            net.succ_edge[net.succ_off[l + 1]:net.succ_off[l + 2]])
+        if both:
+            case = (e, l, int(sorted(both)[0]))
+            break
+    e, l, ex = case
+    dem = netkit.vehicles([l], [float(net.lane_len[l]) - 15.0], [10.0], [[e, ex]])
+    o = oracle_lib.Oracle(net, dem, dict(P, x_lc_end=0.0))
+    st = o.state()
+    o.set_state(st["status"], st["lane"], st["x"], st["v"], st["rp"], 200)
+    _, d = o.step(debug=True)
+    assert 15.0 >= 10.0 ** 2 / (2 * P["idm_b"])
+    assert d["lead_kind"][0] == 2 and d["s_own"][0] == pytest.approx(15.0, abs=1e-9)
+    assert d["lc_cand"][0] == 1 and d["tau_lead"][0] == -1
+    assert d["incentive"][0] == 0.0
+
+
 def test_stop_at_long_red_reaches_standstill_gap(oracle_lib):
     net = synth.grid_network(3, 3, 1, 300.0, green=200, yellow=3, offset="zero")
     o0 = oracle_lib.Oracle(net, netkit.vehicles([], [], [], []), P)
